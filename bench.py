@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of filtered top-K retrieval on one B300 (or N independent replicas).
+
+Workload: N = 10,000,000 jobs, d = 128 FP32 L2-normalised Gaussian embeddings (5.12 GB, larger than
+the 126 MB L2, so no flush is needed between steps); V = 16,384 terms, Poisson(40) distinct Zipf(1.1)
+terms per job, stored as posting lists plus dense bitmaps of the 256 most frequent terms; query
+batches of B filters (default 32) with equal shares of the 0.1 %, 1 %, 10 % and 50 % selectivity
+bands; K = 1000; cosine score.  All data are synthetic and seeded.
+
+A step = one lr_search call on one batch (filter compile, threshold sample, fused predicate + scoring
+scan, selection, exact fallback check).  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BANDS = (0.001, 0.01, 0.10, 0.50)
+METRIC = "filtered top-K QPS @10M×128 vs plain FP32; HBM GB/s % of peak; p99 ms"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--batch", type=int, default=32)
+    p.add_argument("--n", type=int, default=10_000_000)
+    p.add_argument("--dim", type=int, default=128)
+    p.add_argument("--k", type=int, default=1000)
+    p.add_argument("--n-batches", type=int, default=4)
+    p.add_argument("--plan", default="auto")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--cpu-queries", type=int, default=8)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload(args, rank=0):
+    import datagen
+
+    t0 = time.time()
+    c = datagen.corpus(args.seed, args.n, args.dim, 16384, 40.0, 1.1)
+    po, pid = c.postings()
+    per = max(1, args.batch // len(BANDS))
+    nb = args.n_batches
+    band_f = [datagen.filters_in_band(args.seed + 1000 * rank, per * nb, c.V, 1.1, c.df, c.n, s,
+                                      stream_offset=(i + 1) * 100_000_000) for i, s in enumerate(BANDS)]
+    batches = []
+    for j in range(nb):
+        qs = []
+        for i in range(len(BANDS)):
+            sub = band_f[i].subset(range(j * per, (j + 1) * per))
+            qs.extend(sub.clauses(b) for b in range(sub.n))
+        qs = qs[: args.batch] + qs[: max(0, args.batch - len(qs))]
+        batches.append(datagen.Filters.from_lists(qs))
+    Q = datagen.query_embeddings(args.seed + 1000 * rank, args.batch * nb, args.dim)
+    return dict(corpus=c, post_off=po, post_ids=pid, filters=batches, Q=Q.reshape(nb, args.batch, args.dim),
+                gen_s=time.time() - t0)
+
+
+def workload_config(args):
+    return {"workload": "filtered top-K, N=%d jobs x d=%d FP32 cosine, V=16384 Poisson(40) Zipf(1.1) terms as "
+                        "posting lists + 256 dense bitmaps, batch %d (bands 0.1/1/10/50%%), K=%d"
+                        % (args.n, args.dim, args.batch, args.k),
+            "n_jobs": args.n, "dim": args.dim, "batch": args.batch, "k": args.k, "vocab": 16384,
+            "selectivity_bands": list(BANDS), "l2": "inputs larger than L2 (5.12 GB embeddings), no flush"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
+    """Bytes the main scan must move per launch: rows that pass some query of the launch (each read
+    once at d_pad*4 bytes) plus, per distinct term, the cheaper of its bitmap and its posting list."""
+    import torch
+
+    d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
+    n = corpus.n
+    df = corpus.df
+    per_launch = []
+    B = filters.n
+    for q0 in range(0, B, 8):
+        sub = filters.subset(range(q0, min(B, q0 + 8)))
+        _, bm = lr.lr_filter_count(idx, sub, bitmap=True)
+        union = bm[0].clone()
+        for i in range(1, sub.n):
+            union |= bm[i]
+        words = union.view(torch.int32).cpu().numpy().view(np.uint32)
+        rows = int(np.unpackbits(words.view(np.uint8)).sum())
+        terms = {int(t) for t in sub.terms}
+        p = sum(min(n / 8.0, 4.0 * float(df[t])) for t in terms)
+        per_launch.append(rows * d_pad * 4 + p)
+    return per_launch
+
+
+def cpu_oracle_sample(wl, args, n_queries, batch_index=0):
+    """Time the CPU oracle on the first n_queries of one batch over the full index."""
+    import oracle
+
+    f = wl["filters"][batch_index]
+    sel = list(range(min(n_queries, f.n)))
+    fs = f.subset(sel)
+    Q = wl["Q"][batch_index][sel]
+    c = wl["corpus"]
+    t0 = time.perf_counter()
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, fs, args.k, metric="cosine")
+    dt = time.perf_counter() - t0
+    cores = min(oracle.num_threads(), len(sel))
+    return ref, sel, dt, cores
+
+
+# ----------------------------------------------------------------------------- arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args)
+    per_step = max(1, args.cpu_queries // 2)
+    times = []
+    nq = 0
+    for i in range(args.warmup + args.steps):
+        j = i % len(wl["filters"])
+        _, sel, dt, cores = cpu_oracle_sample(wl, args, per_step, j)
+        if i >= args.warmup:
+            times.append(dt)
+            nq += len(sel)
+    total = sum(times)
+    value = nq / total
+    out = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+           "impl": "reference", "config": workload_config(args),
+           "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                            "sample": "%d queries per step (first of each batch) over the full %d-job index"
+                                      % (per_step, args.n)},
+           "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_2402_13435_b300 as lr
+
+    wl = make_workload(args, rank)
+    c = wl["corpus"]
+    t0 = time.time()
+    idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), c.V, post_off=wl["post_off"], post_ids=wl["post_ids"],
+                             n_dense_terms=256, metric="cosine", max_batch=max(args.batch, 32), max_k=args.k)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    nb = len(wl["filters"])
+    Qd = [torch.from_numpy(np.ascontiguousarray(wl["Q"][j])).cuda() for j in range(nb)]
+    B, K = args.batch, args.k
+    out_ids = torch.empty((B, K), dtype=torch.int32, device="cuda")
+    out_sc = torch.empty((B, K), dtype=torch.float32, device="cuda")
+    out_cnt = torch.empty(B, dtype=torch.int32, device="cuda")
+
+    def step(i, probe=None):
+        j = i % nb
+        lr.lr_search(idx, Qd[j], wl["filters"][j], K, out_ids=out_ids, out_scores=out_sc, out_count=out_cnt,
+                     plan=args.plan, probe=probe)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    lr.lr_index_sync(idx)
+    # ---- timed region (device time)
+    probes = [lr.Probe(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for p in probes:  # materialise the event handles
+        p.start.record()
+        p.stop.record()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for i in range(args.steps):
+            step(i, probes[i])
+        ev1.record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    step_ms = []
+    lr.lr_index_sync(idx)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    scan_ms = float(np.mean([p.start.elapsed_time(p.stop) for p in probes]))
+    n_scan = probes[0].n_scan_launches
+    launches = int(sum(p.n_launches for p in probes))
+    value = world * B * args.steps / (ms / 1e3)
+
+    # ---- per-step latency distribution (separate, synchronised steps)
+    lat = []
+    for i in range(min(args.steps, 20)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(i)
+        e1.record()
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    step_ms = lat
+
+    # ---- roofline of the dominant kernel (the main scan)
+    per_launch = algorithmic_scan_bytes(lr, idx, wl["filters"][0], c, args)
+    peak, peak_kind = peaks()
+    # scan_ms covers n_scan launches of batch i % nb; use batch 0's bytes as the per-launch average
+    achieved = (sum(per_launch) / 1e9) / (scan_ms / 1e3)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_scan_gemv (main scan, %d launches per step)" % n_scan,
+            "algorithmic_bytes_per_launch": float(np.mean(per_launch)), "launch_ms": scan_ms / max(n_scan, 1),
+            "peak_kind": peak_kind}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hq = [torch.from_numpy(np.ascontiguousarray(wl["Q"][j])).pin_memory() for j in range(nb)]
+        h_ids = torch.empty((B, K), dtype=torch.int32).pin_memory()
+        h_sc = torch.empty((B, K), dtype=torch.float32).pin_memory()
+        h_cnt = torch.empty(B, dtype=torch.int32).pin_memory()
+        for i in range(args.warmup):
+            lr.lr_search(idx, hq[i % nb], wl["filters"][i % nb], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            j = i % nb
+            lr.lr_search(idx, hq[j], wl["filters"][j], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        f0 = wl["filters"][0]
+        h2d = B * args.dim * 4 + f0.q_off.nbytes + f0.c_off.nbytes + f0.terms.nbytes
+        d2h = B * K * 8 + B * 4
+        e2e = {"value": world * B * args.steps / dt, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # ---- CPU oracle baseline and parity of the sampled queries
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle.compare import check_topk
+
+        ref, sel, dt, cores = cpu_oracle_sample(wl, args, args.cpu_queries, 0)
+        step(0)
+        torch.cuda.synchronize()
+        ids, sc, cnt = out_ids.cpu().numpy(), out_sc.cpu().numpy(), out_cnt.cpu().numpy()
+        try:
+            moved = check_topk(ids, sc, cnt, ref, c.X, wl["Q"][0], c.job_off, c.job_terms, wl["filters"][0],
+                               queries=sel)
+            parity = {"queries": len(sel), "ok": True, "id_positions_in_tie_band": moved}
+        except AssertionError as e:
+            parity = {"queries": len(sel), "ok": False, "error": str(e)[:300]}
+        cpu = {"value": len(sel) / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d queries of batch 0 over the full %d-job index (%.1f s)" % (len(sel), args.n, dt)}
+
+    if rank == 0:
+        p50, p99 = (float(np.percentile(step_ms, 50)), float(np.percentile(step_ms, 99))) if step_ms else (None, None)
+        out = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, paper-shaped)",
+               "config": workload_config(args), "p50_ms": p50, "p99_ms": p99, "clocks": clk.summary(),
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "parity": parity,
+               "setup_s": {"generate": round(wl["gen_s"], 1), "index_build": round(build_s, 1)}}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * lr.h -- C ABI of a single-GPU (B300, sm_103a) filtered top-K retrieval library.
+ *
+ * The operation is the on-GPU hybrid retrieval of "Learning to Retrieve for Job
+ * Matching" (Sec. 5.3, "System Implementation"; appendix "Optimizing System on
+ * GPU"): a term-based filter in conjunctive normal form (F-TBR) fused with a
+ * full scan of job embeddings (F-EBR) and a per-query top-K selection, with
+ * several queries served by one scan ("Batch Inference").
+ *
+ * Conventions shared by every entry point:
+ *   - Status: every call returns lr_status; LR_OK is 0.  No C++ exception and
+ *     no abort crosses the ABI.  lr_last_error_message() describes the last
+ *     failure of the calling thread.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and return before the GPU finishes
+ *     unless a pointer argument is host memory, in which case the call copies
+ *     through it and synchronises the stream before returning.
+ *   - Pointer kinds: arguments documented "host or device" are classified with
+ *     cudaPointerGetAttributes (pinned or pageable host memory, device memory,
+ *     managed memory).  Arguments documented "host" must be host memory.
+ *   - Ownership: the index copies everything it needs into device memory it
+ *     owns; the caller keeps ownership of every pointer it passes.
+ *   - Scores are FP32 and higher is better.  Ties are broken by ascending job
+ *     id, so every result is a deterministic total order.
+ *   - Job ids are 0-based row indices below 2^32 - 1.
+ */
+#ifndef LR_H_
+#define LR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lr_status {
+  LR_OK = 0,
+  LR_ERR_INVALID = 1,     /* argument or input data violates the contract          */
+  LR_ERR_NOMEM = 2,       /* device or pinned host allocation failed (create only)  */
+  LR_ERR_WORKSPACE = 3,   /* request exceeds what the index's workspace was sized for */
+  LR_ERR_CUDA = 4,        /* a CUDA runtime call failed                             */
+  LR_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                     */
+  LR_ERR_UNSUPPORTED = 6  /* valid request this build does not implement            */
+} lr_status;
+
+typedef enum lr_dtype { LR_F32 = 0, LR_BF16 = 1, LR_FP8_E4M3 = 2 } lr_dtype;
+
+/* LR_DOT: s = <q, x_j>.  LR_COSINE: s = <q, x_j> / (|q| |x_j|), evaluated as the
+ * dot product of vectors normalised in FP32 (job rows at create, queries at
+ * search); a zero vector scores 0.  (Sec. 5.2 uses cosine similarity.) */
+typedef enum lr_metric { LR_DOT = 0, LR_COSINE = 1 } lr_metric;
+
+/* Scoring plan.  AUTO picks by batch size. */
+typedef enum lr_plan {
+  LR_PLAN_AUTO = 0,
+  LR_PLAN_GEMV = 1,  /* SIMT FP32 matrix-vector scan, HBM-bound at small batches */
+  LR_PLAN_TC = 2     /* tcgen05 tensor-core tiles (3xTF32 split), large batches  */
+} lr_plan;
+
+typedef struct lr_index lr_index;
+
+/*
+ * Index description (appendix "TBR", "Storing Dense Matrix", "Memory
+ * Pre-Allocation").
+ *
+ *   n_jobs, dim      rows and columns of the embedding matrix (dim <= 512).
+ *   dtype            LR_F32 (the plain method).  Other types: LR_ERR_UNSUPPORTED.
+ *   metric           lr_metric.
+ *   emb              [n_jobs][dim] row-major FP32, host or device.  Must be finite
+ *                    (checked; LR_ERR_INVALID otherwise).
+ *   vocab            term ids are in [0, vocab).
+ *   bitsets          optional [n_jobs][ceil(vocab/64)] uint64 job-major term sets
+ *                    (bit t%64 of word t/64 set iff the job holds term t), host or
+ *                    device.  Every term becomes a dense term-major bitmap.
+ *   post_off,        optional term-major CSR posting lists, host memory:
+ *   post_ids         post_ids[post_off[t] .. post_off[t+1]) are the jobs holding
+ *                    term t.  Exactly one of bitsets / postings must be given.
+ *   n_dense_terms    with postings: the n most frequent terms are kept as dense
+ *                    bitmaps (n_jobs bits each); the others stay posting lists and
+ *                    are expanded into per-batch bitmaps at search time.  -1 = all.
+ *   max_batch        largest batch lr_search accepts (workspace sizing).
+ *   max_k            largest K lr_search accepts (<= 4096).
+ *   max_batch_terms  total term occurrences over all filters of one batch that
+ *                    the workspace holds (0: 16 per query).
+ *   max_sparse_terms distinct posting-list terms one batch may use (0: 256).
+ */
+typedef struct lr_index_desc {
+  int64_t n_jobs;
+  int32_t dim;
+  int32_t dtype;
+  int32_t metric;
+  int32_t vocab;
+  const float *emb;
+  const uint64_t *bitsets;
+  const int64_t *post_off;
+  const uint32_t *post_ids;
+  int32_t n_dense_terms;
+  int32_t max_batch;
+  int32_t max_k;
+  int32_t max_batch_terms;
+  int32_t max_sparse_terms;
+} lr_index_desc;
+
+/*
+ * A batch of B filters in conjunctive normal form (Sec. 5.3: "Each TBR query is
+ * transformed into Conjunctive Normal Form"), host memory:
+ *   clauses of query b: q_off[b] .. q_off[b+1]   (q_off[0] = 0, non-decreasing)
+ *   terms of clause c:  c_off[c] .. c_off[c+1]   (c_off[0] = 0, increasing)
+ *   term ids:           terms[i] < vocab
+ * A query with zero clauses is unfiltered.  A clause with zero terms is
+ * LR_ERR_INVALID (it could never be satisfied).  Terms may repeat or appear in
+ * any order.
+ */
+typedef struct lr_filters {
+  const int32_t *q_off;
+  const int32_t *c_off;
+  const uint32_t *terms;
+} lr_filters;
+
+/* Search options; a zero-initialised struct (or NULL) means defaults. */
+typedef struct lr_search_opts {
+  int32_t plan;           /* lr_plan                                                  */
+  int32_t sample_stride;  /* threshold sample: every n-th 256-row group (0 = auto,
+                             -1 = no sample: every passing job is a candidate)        */
+  int32_t cand_cap;       /* candidate slots per query (0 = auto; capped by workspace) */
+  int32_t force_exact_fallback; /* 1: also run the exact radix fallback for every query */
+} lr_search_opts;
+
+/* Per-call statistics and instrumentation (every field optional).  Arrays may be
+ * device or host memory; a host array makes the call synchronise the stream. */
+typedef struct lr_search_stats {
+  int64_t *pass_count;   /* [B] jobs passing each filter                            */
+  int32_t *cand_count;   /* [B] candidates gathered by the threshold pass           */
+  int32_t *fallback;     /* [B] 1 if the exact radix fallback produced the result   */
+  int32_t *n_launches;   /* host, 1 value: kernels this call launched               */
+  void *scan_start;      /* cudaEvent_t recorded on the stream right before the     */
+  void *scan_stop;       /* main scan launches, and right after them                */
+  int32_t *n_scan_launches; /* host, 1 value: launches between scan_start/stop     */
+} lr_search_stats;
+
+/* Build an index (allocates every device buffer it will ever use: appendix
+ * "Memory Pre-Allocation").  *out receives the handle.  Errors: LR_ERR_INVALID
+ * (bad description, non-finite embeddings, term id >= vocab, job id >= n_jobs),
+ * LR_ERR_NOMEM, LR_ERR_CUDA.  Synchronises `stream` before returning. */
+lr_status lr_index_create(const lr_index_desc *desc, void *stream, lr_index **out);
+
+/* Free an index and its workspace.  NULL is accepted.  The caller must make
+ * sure no search on it is still running. */
+lr_status lr_index_destroy(lr_index *index);
+
+/* Bytes of device memory held by the index (embeddings, term bitmaps, posting
+ * lists, workspace).  Returns 0 for NULL. */
+size_t lr_index_device_bytes(const lr_index *index);
+
+/*
+ * Filtered top-K search: for each query b the K[b] passing jobs with the
+ * highest score, ordered by (score desc, job id asc).
+ *
+ *   q           [B][dim] FP32 query embeddings, host or device.
+ *   B           1 <= B <= max_batch.
+ *   f           B CNF filters (host).
+ *   k           [B] per-query K (host) or NULL to use k_all for every query;
+ *               1 <= K <= max_k.
+ *   k_all       K when k is NULL; also the row stride of the outputs, which
+ *               must be >= every K.
+ *   out_ids     [B][k_all] int32, host or device: job ids, -1 past out_count.
+ *   out_scores  [B][k_all] FP32, host or device: scores, -inf past out_count.
+ *   out_count   [B] int32, host or device (nullable): min(K[b], #passing).
+ *   opts        NULL for defaults.
+ *   stats       NULL or per-query statistics.
+ *
+ * The result is exact: candidates are gathered above a threshold estimated from
+ * a sample of the index, and a query whose candidate set cannot prove it holds
+ * the top K is finished by an exact radix selection over the whole index.
+ * Errors: LR_ERR_INVALID, LR_ERR_WORKSPACE (batch larger than the workspace),
+ * LR_ERR_CUDA.
+ */
+lr_status lr_search(lr_index *index, const float *q, int32_t B, const lr_filters *f, const int32_t *k,
+                    int32_t k_all, int32_t *out_ids, float *out_scores, int32_t *out_count, void *stream);
+
+lr_status lr_search_ex(lr_index *index, const float *q, int32_t B, const lr_filters *f, const int32_t *k,
+                       int32_t k_all, int32_t *out_ids, float *out_scores, int32_t *out_count,
+                       const lr_search_opts *opts, const lr_search_stats *stats, void *stream);
+
+/*
+ * Exact term filter only (F-TBR, Sec. 5.3 and appendix "TBR"): for each query the
+ * number of passing jobs and, optionally, the pass bitmap.
+ *   out_pass    [B] int64, host or device: number of jobs passing each filter.
+ *   out_bitmap  nullable [B][ceil(n_jobs/32)] uint32, host or device: bit j%32 of
+ *               word j/32 of row b set iff job j passes filter b.
+ */
+lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64_t *out_pass,
+                          uint32_t *out_bitmap, void *stream);
+
+/* Wait for `stream` and report any error the library's kernels recorded on the
+ * device for this index (LR_ERR_TIMEOUT for a bounded wait that gave up). */
+lr_status lr_index_sync(lr_index *index, void *stream);
+
+/* Human-readable description of the calling thread's last failure. */
+const char *lr_last_error_message(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int32_t lr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LR_H_ */

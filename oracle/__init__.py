@@ -53,6 +53,8 @@ def _load():
         L.oracle_search.restype = ctypes.c_int
         L.oracle_pair_scores.argtypes = [i32, vp, vp, i64, vp, vp, i32, vp]
         L.oracle_pair_scores.restype = ctypes.c_int
+        L.oracle_pair_pass.argtypes = [i64, vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
+        L.oracle_pair_pass.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
@@ -137,6 +139,19 @@ def pair_scores(X, Q, qi, ji, metric: str = "cosine") -> np.ndarray:
     out = np.empty(qi.shape[0], dtype=np.float64)
     _load().oracle_pair_scores(X.shape[1], _p(X), _p(Q), qi.shape[0], _p(qi), _p(ji), METRICS[metric], _p(out))
     return out
+
+
+def pair_pass(job_off, job_terms, n: int, f, qi, ji) -> np.ndarray:
+    """Predicate value (bool) of (query qi[p], job ji[p]) pairs under CNF filters ``f``."""
+    job_off, job_terms = _c(job_off, np.int64), _c(job_terms, np.int32)
+    q_off, c_off, terms = _c(f.q_off, np.int32), _c(f.c_off, np.int32), _c(f.terms, np.uint32)
+    qi, ji = _c(qi, np.int64), _c(ji, np.int64)
+    out = np.zeros(qi.shape[0], dtype=np.uint8)
+    rc = _load().oracle_pair_pass(n, _p(job_off), _p(job_terms), int(q_off.shape[0] - 1), _p(q_off), _p(c_off),
+                                  _p(terms), qi.shape[0], _p(qi), _p(ji), _p(out))
+    if rc:
+        raise RuntimeError("oracle_pair_pass: index out of range")
+    return out.astype(bool)
 
 
 def recall_at_k(retrieved: Sequence[Sequence[int]], relevant: Sequence[Sequence[int]]) -> float:

@@ -250,6 +250,35 @@ int oracle_pair_scores(int32_t d, const float *X, const float *Q, int64_t npairs
   return 0;
 }
 
+/* pass(q, j) of given (query, job) pairs, same definition as above. */
+int oracle_pair_pass(int64_t n, const int64_t *job_off, const int32_t *job_terms, int32_t B, const int32_t *q_off,
+                     const int32_t *c_off, const uint32_t *terms, int64_t npairs, const int64_t *qi,
+                     const int64_t *ji, uint8_t *out) {
+  cnf_t *C = (cnf_t *)malloc(sizeof(cnf_t) * (size_t)(B > 0 ? B : 1));
+  if (!C) return 1;
+  for (int32_t b = 0; b < B; ++b) cnf_build(&C[b], b, q_off, c_off, terms);
+  int err = 0;
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < npairs; ++p) {
+    const int64_t j = ji[p];
+    if (j < 0 || j >= n || qi[p] < 0 || qi[p] >= B) { err = 1; out[p] = 0; continue; }
+    /* T_j for this one job, sorted and de-duplicated */
+    int64_t len = job_off[j + 1] - job_off[j];
+    uint32_t *tj = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(len > 0 ? len : 1));
+    for (int64_t i = 0; i < len; ++i) tj[i] = (uint32_t)job_terms[job_off[j] + i];
+    len = sort_unique(tj, len);
+    const cnf_t *c = &C[qi[p]];
+    int pass = 1;
+    for (int32_t k = 0; k < c->nc && pass; ++k)
+      pass = sorted_intersect(c->t + c->coff[k], c->coff[k + 1] - c->coff[k], tj, len);
+    out[p] = (uint8_t)pass;
+    free(tj);
+  }
+  for (int32_t b = 0; b < B; ++b) cnf_free(&C[b]);
+  free(C);
+  return err;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -1,0 +1,301 @@
+"""Python binding of the B300 filtered top-K retrieval library (``liblr.so``, C ABI in ``include/lr.h``).
+
+Argument marshalling only: every step of the retrieval path runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  If the compiled library is missing, importing the
+binding raises -- there is no CPU fallback.
+
+Entry points mirror the C ABI names:
+  lr_index_create, lr_index_destroy, lr_index_device_bytes, lr_search, lr_filter_count,
+  lr_index_sync, lr_last_error_message, lr_version.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblr.so")
+
+LR_OK, LR_ERR_INVALID, LR_ERR_NOMEM, LR_ERR_WORKSPACE, LR_ERR_CUDA, LR_ERR_TIMEOUT, LR_ERR_UNSUPPORTED = range(7)
+LR_F32, LR_BF16, LR_FP8_E4M3 = 0, 1, 2
+LR_DOT, LR_COSINE = 0, 1
+LR_PLAN_AUTO, LR_PLAN_GEMV, LR_PLAN_TC = 0, 1, 2
+_METRIC = {"dot": LR_DOT, "cosine": LR_COSINE}
+_PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC}
+
+SYMBOLS = ("lr_index_create", "lr_index_destroy", "lr_index_device_bytes", "lr_search", "lr_search_ex",
+           "lr_filter_count", "lr_index_sync", "lr_last_error_message", "lr_version")
+
+
+class LRError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__("%s failed (status %d): %s" % (where, status, message))
+        self.status = status
+
+
+class lr_index_desc(ctypes.Structure):
+    _fields_ = [("n_jobs", ctypes.c_int64), ("dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("metric", ctypes.c_int32), ("vocab", ctypes.c_int32), ("emb", ctypes.c_void_p),
+                ("bitsets", ctypes.c_void_p), ("post_off", ctypes.c_void_p), ("post_ids", ctypes.c_void_p),
+                ("n_dense_terms", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_k", ctypes.c_int32),
+                ("max_batch_terms", ctypes.c_int32), ("max_sparse_terms", ctypes.c_int32)]
+
+
+class lr_filters(ctypes.Structure):
+    _fields_ = [("q_off", ctypes.c_void_p), ("c_off", ctypes.c_void_p), ("terms", ctypes.c_void_p)]
+
+
+class lr_search_opts(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_int32), ("sample_stride", ctypes.c_int32), ("cand_cap", ctypes.c_int32),
+                ("force_exact_fallback", ctypes.c_int32)]
+
+
+class lr_search_stats(ctypes.Structure):
+    _fields_ = [("pass_count", ctypes.c_void_p), ("cand_count", ctypes.c_void_p), ("fallback", ctypes.c_void_p),
+                ("n_launches", ctypes.c_void_p), ("scan_start", ctypes.c_void_p), ("scan_stop", ctypes.c_void_p),
+                ("n_scan_launches", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("CUDA library %s is not built (run __graft_entry__.build() or "
+                          "python paper_2402_13435_b300/build.py); there is no CPU fallback" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    L.lr_index_create.argtypes = [ctypes.POINTER(lr_index_desc), vp, ctypes.POINTER(vp)]
+    L.lr_index_destroy.argtypes = [vp]
+    L.lr_index_device_bytes.argtypes = [vp]
+    L.lr_index_device_bytes.restype = ctypes.c_size_t
+    L.lr_search.argtypes = [vp, vp, i32, ctypes.POINTER(lr_filters), vp, i32, vp, vp, vp, vp]
+    L.lr_search_ex.argtypes = [vp, vp, i32, ctypes.POINTER(lr_filters), vp, i32, vp, vp, vp,
+                               ctypes.POINTER(lr_search_opts), ctypes.POINTER(lr_search_stats), vp]
+    L.lr_filter_count.argtypes = [vp, ctypes.POINTER(lr_filters), i32, vp, vp, vp]
+    L.lr_index_sync.argtypes = [vp, vp]
+    L.lr_last_error_message.argtypes = []
+    L.lr_last_error_message.restype = ctypes.c_char_p
+    L.lr_version.argtypes = []
+    L.lr_version.restype = i32
+    for name in ("lr_index_create", "lr_index_destroy", "lr_search", "lr_search_ex", "lr_filter_count",
+                 "lr_index_sync"):
+        getattr(L, name).restype = ctypes.c_int
+    return L
+
+
+_lib = _load()
+
+
+def lr_version() -> int:
+    return int(_lib.lr_version())
+
+
+def lr_last_error_message() -> str:
+    m = _lib.lr_last_error_message()
+    return m.decode() if m else ""
+
+
+def _check(st: int, where: str):
+    if st != LR_OK:
+        raise LRError(st, where, lr_last_error_message())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x) -> Optional[int]:
+    """Address of a torch tensor or numpy array (host or device); None for None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr()
+
+
+def _host_i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+class Filters:
+    """Host CSR arrays of a CNF batch (q_off int32[B+1], c_off int32[C+1], terms uint32[T])."""
+
+    def __init__(self, q_off, c_off, terms):
+        self.q_off = _host_i32(q_off)
+        self.c_off = _host_i32(c_off) if len(c_off) else np.zeros(1, dtype=np.int32)
+        self.terms = np.ascontiguousarray(np.asarray(terms), dtype=np.uint32)
+        if self.terms.size == 0:
+            self.terms = np.zeros(1, dtype=np.uint32)
+
+    @classmethod
+    def of(cls, f) -> "Filters":
+        return f if isinstance(f, Filters) else cls(f.q_off, f.c_off, f.terms)
+
+    @property
+    def n(self) -> int:
+        return int(self.q_off.shape[0] - 1)
+
+    def c(self) -> lr_filters:
+        return lr_filters(self.q_off.ctypes.data, self.c_off.ctypes.data, self.terms.ctypes.data)
+
+
+class Index:
+    """An lr_index handle plus the host arrays the call needs to keep alive."""
+
+    def __init__(self, handle: int, n: int, dim: int, max_batch: int, max_k: int, metric: int):
+        self.handle = handle
+        self.n, self.dim, self.max_batch, self.max_k, self.metric = n, dim, max_batch, max_k, metric
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.lr_index_destroy(ctypes.c_void_p(self.handle))
+                self.handle = None
+        except Exception:
+            pass
+
+
+def lr_index_create(emb, vocab: int, *, bitsets=None, post_off=None, post_ids=None, n_dense_terms: int = -1,
+                    metric: str = "cosine", max_batch: int = 256, max_k: int = 1000, max_batch_terms: int = 0,
+                    max_sparse_terms: int = 0, stream=None) -> Index:
+    """Build an index over job embeddings ``emb`` [n][dim] FP32 (torch or numpy, host or device) and
+    per-job terms given either as job-major ``bitsets`` [n][ceil(vocab/64)] uint64 or as posting lists
+    (``post_off`` int64[vocab+1], ``post_ids`` uint32[nnz])."""
+    n, dim = int(emb.shape[0]), int(emb.shape[1])
+    keep = []
+    if isinstance(emb, np.ndarray):
+        emb = np.ascontiguousarray(emb, dtype=np.float32)
+    if bitsets is not None and isinstance(bitsets, np.ndarray):
+        bitsets = np.ascontiguousarray(bitsets, dtype=np.uint64)
+    if post_off is not None:
+        post_off = np.ascontiguousarray(np.asarray(post_off), dtype=np.int64)
+        post_ids = np.ascontiguousarray(np.asarray(post_ids), dtype=np.uint32) if isinstance(post_ids, np.ndarray) \
+            or not hasattr(post_ids, "data_ptr") else post_ids
+    keep += [emb, bitsets, post_off, post_ids]
+    d = lr_index_desc(n_jobs=n, dim=dim, dtype=LR_F32, metric=_METRIC[metric], vocab=int(vocab), emb=_ptr(emb),
+                      bitsets=_ptr(bitsets), post_off=_ptr(post_off), post_ids=_ptr(post_ids),
+                      n_dense_terms=int(n_dense_terms), max_batch=int(max_batch), max_k=int(max_k),
+                      max_batch_terms=int(max_batch_terms), max_sparse_terms=int(max_sparse_terms))
+    h = ctypes.c_void_p()
+    _check(_lib.lr_index_create(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "lr_index_create")
+    del keep
+    return Index(h.value, n, dim, int(max_batch), int(max_k), _METRIC[metric])
+
+
+def lr_index_destroy(index: Index) -> None:
+    if index.handle:
+        _check(_lib.lr_index_destroy(ctypes.c_void_p(index.handle)), "lr_index_destroy")
+        index.handle = None
+
+
+def lr_index_device_bytes(index: Index) -> int:
+    return int(_lib.lr_index_device_bytes(ctypes.c_void_p(index.handle)))
+
+
+def lr_index_sync(index: Index, stream=None) -> None:
+    _check(_lib.lr_index_sync(ctypes.c_void_p(index.handle), _stream_ptr(stream)), "lr_index_sync")
+
+
+class Probe:
+    """Instrumentation of one lr_search call without synchronising: kernel launch counts and a pair of
+    CUDA events (torch.cuda.Event with timing) recorded around the main scan launches."""
+
+    def __init__(self, start=None, stop=None):
+        self.start, self.stop = start, stop
+        self._n = np.zeros(1, dtype=np.int32)
+        self._ns = np.zeros(1, dtype=np.int32)
+
+    @property
+    def n_launches(self) -> int:
+        return int(self._n[0])
+
+    @property
+    def n_scan_launches(self) -> int:
+        return int(self._ns[0])
+
+    def c(self) -> lr_search_stats:
+        return lr_search_stats(None, None, None, self._n.ctypes.data,
+                               self.start.cuda_event if self.start is not None else None,
+                               self.stop.cuda_event if self.stop is not None else None, self._ns.ctypes.data)
+
+
+def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out_count=None, plan: str = "auto",
+              sample_stride: int = 0, cand_cap: int = 0, force_exact_fallback: bool = False, stats: bool = False,
+              probe: Optional[Probe] = None, stream=None):
+    """Filtered top-K for the query batch ``q`` [B][dim] FP32 (torch tensor or numpy array, host or device).
+
+    ``k`` is an int or a per-query sequence.  Outputs default to new device tensors on q's device
+    (host numpy arrays when q is a numpy array).  Returns (ids [B][kmax] int32, scores [B][kmax] FP32,
+    count [B] int32) and, with ``stats=True``, a dict of per-query statistics.  ``probe`` collects
+    launch counts and scan-phase CUDA events without a synchronisation.
+    """
+    import torch
+
+    f = Filters.of(filters)
+    B = int(q.shape[0])
+    if f.n != B:
+        raise ValueError("filters describe %d queries, q has %d" % (f.n, B))
+    if np.isscalar(k):
+        k_arr, k_all = None, int(k)
+    else:
+        k_arr = _host_i32(k)
+        k_all = int(k_arr.max())
+    host = isinstance(q, np.ndarray)
+    if host:
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        if out_ids is None:
+            out_ids = np.empty((B, k_all), dtype=np.int32)
+            out_scores = np.empty((B, k_all), dtype=np.float32)
+            out_count = np.empty(B, dtype=np.int32)
+    else:
+        if out_ids is None:
+            out_ids = torch.empty((B, k_all), dtype=torch.int32, device=q.device)
+            out_scores = torch.empty((B, k_all), dtype=torch.float32, device=q.device)
+            out_count = torch.empty(B, dtype=torch.int32, device=q.device)
+    opts = lr_search_opts(plan=_PLAN[plan], sample_stride=int(sample_stride), cand_cap=int(cand_cap),
+                          force_exact_fallback=int(bool(force_exact_fallback)))
+    st = None
+    st_arrays = None
+    if stats:
+        st_arrays = dict(pass_count=np.zeros(B, dtype=np.int64), cand_count=np.zeros(B, dtype=np.int32),
+                         fallback=np.zeros(B, dtype=np.int32))
+        st = lr_search_stats(st_arrays["pass_count"].ctypes.data, st_arrays["cand_count"].ctypes.data,
+                             st_arrays["fallback"].ctypes.data)
+    elif probe is not None:
+        st = probe.c()
+    fc = f.c()
+    rc = _lib.lr_search_ex(ctypes.c_void_p(index.handle), _ptr(q), B, ctypes.byref(fc),
+                           None if k_arr is None else k_arr.ctypes.data, k_all, _ptr(out_ids), _ptr(out_scores),
+                           _ptr(out_count), ctypes.byref(opts), ctypes.byref(st) if st is not None else None,
+                           _stream_ptr(stream))
+    _check(rc, "lr_search")
+    if stats:
+        return out_ids, out_scores, out_count, st_arrays
+    return out_ids, out_scores, out_count
+
+
+def lr_filter_count(index: Index, filters, *, bitmap: bool = False, device=None, stream=None):
+    """Exact CNF filter: pass counts int64[B] and, with ``bitmap=True``, the [B][ceil(n/32)] pass bitmap."""
+    import torch
+
+    f = Filters.of(filters)
+    B = f.n
+    dev = device if device is not None else torch.device("cuda")
+    out_pass = torch.empty(B, dtype=torch.int64, device=dev)
+    bm = torch.empty((B, (index.n + 31) // 32), dtype=torch.int32, device=dev) if bitmap else None
+    fc = f.c()
+    _check(_lib.lr_filter_count(ctypes.c_void_p(index.handle), ctypes.byref(fc), B, _ptr(out_pass), _ptr(bm),
+                                _stream_ptr(stream)), "lr_filter_count")
+    return (out_pass, bm) if bitmap else out_pass

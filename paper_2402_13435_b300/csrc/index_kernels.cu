@@ -1,0 +1,214 @@
+// Index construction and per-batch preparation kernels.
+//
+// Term storage (appendix "TBR", "Storing Dense Matrix"): the paper keeps a
+// fixed-width attribute matrix per document and intersects sorted vectors.  On
+// B300 the predicate becomes word-wise bit logic, so terms are stored
+// term-major: term t owns a bitmap with bit j set iff job j holds t, padded to
+// whole 256-row groups.  Frequent terms keep a resident bitmap; rare terms keep
+// their posting list and are expanded into a workspace bitmap only when a batch
+// uses them.
+#include "lr_internal.h"
+
+namespace lr {
+namespace {
+
+// One warp per row: copy a job row into the index layout [n][d_pad] (zero
+// padded), normalised in FP32 for the cosine metric; non-finite values set err.
+__global__ void k_rows_to_index(const float *in, float *out, int64_t n, int dim, int d_pad, int cosine,
+                                uint32_t *err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float *src = in + (size_t)row * (size_t)dim;
+  float *dst = out + (size_t)row * (size_t)d_pad;
+  float ss = 0.f;
+  bool bad = false;
+  for (int k = lane; k < dim; k += 32) {
+    const float v = src[k];
+    bad |= !isfinite(v);
+    ss = fmaf(v, v, ss);
+  }
+  for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, off);
+  if (__any_sync(0xFFFFFFFFu, bad)) {
+    if (lane == 0) atomicOr(err, 1u);
+  }
+  float scale = 1.f;
+  if (cosine) scale = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+  for (int k = lane; k < d_pad; k += 32) dst[k] = k < dim ? src[k] * scale : 0.f;
+}
+
+// Job-major 64-bit bitsets -> term-major 32-bit bitmap words.  Thread (jw, tw)
+// reads the 32 jobs of word jw for terms [64*tw, 64*tw+64) and writes one word
+// for each of those 64 terms.
+__global__ void k_bitsets_to_termmajor(const uint64_t *bits, int64_t n, int vocab, uint32_t *out, int64_t n_words) {
+  const int64_t jw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tw = blockIdx.y;
+  const int64_t W = (vocab + 63) / 64;
+  if (jw >= n_words) return;
+  uint64_t v[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int64_t row = jw * 32 + j;
+    v[j] = row < n ? bits[(size_t)row * (size_t)W + tw] : 0ull;
+  }
+  for (int t = 0; t < 64; ++t) {
+    const int term = tw * 64 + t;
+    if (term >= vocab) break;
+    uint32_t w = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) w |= (uint32_t)((v[j] >> t) & 1ull) << j;
+    out[(size_t)term * (size_t)n_words + jw] = w;
+  }
+}
+
+// Expand posting lists into bitmaps: bitmap i receives the postings of
+// terms[i].  Lanes that hit the same word combine their bits before one atomic.
+__global__ void k_scatter_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *terms,
+                                   int n_terms, uint32_t *bitmaps, int64_t n_words, int64_t n, uint32_t *err) {
+  const int i = blockIdx.y;
+  if (i >= n_terms) return;
+  const int32_t t = terms[i];
+  const int64_t b = post_off[t], e = post_off[t + 1];
+  uint32_t *bm = bitmaps + (size_t)i * (size_t)n_words;
+  const int lane = threadIdx.x & 31;
+  for (int64_t p0 = b + ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)); p0 < e;
+       p0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = p0 + lane;
+    const bool valid = p < e;
+    uint32_t id = valid ? post_ids[p] : 0u;
+    if (valid && (int64_t)id >= n) {
+      atomicOr(err, 4u);
+      id = 0u;
+    }
+    const bool ok = valid && (int64_t)id < n;
+    const unsigned act = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok) {
+      const uint32_t word = id >> 5;
+      const unsigned peers = __match_any_sync(act, word);
+      const uint32_t bits = __reduce_or_sync(peers, 1u << (id & 31u));
+      if (lane == __ffs(peers) - 1) atomicOr(bm + word, bits);
+    }
+    __syncwarp();
+  }
+}
+
+// One warp per query: copy into [B][d_pad] (zero padded), FP32-normalised for cosine.
+__global__ void k_prep_queries(const float *in, float *out, int B, int dim, int d_pad, int cosine, uint32_t *err) {
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= B) return;
+  const float *src = in + (size_t)q * (size_t)dim;
+  float ss = 0.f;
+  bool bad = false;
+  for (int k = lane; k < dim; k += 32) {
+    const float v = src[k];
+    bad |= !isfinite(v);
+    ss = fmaf(v, v, ss);
+  }
+  for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, off);
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(err, 8u);
+  float scale = 1.f;
+  if (cosine) scale = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+  for (int k = lane; k < d_pad; k += 32) out[(size_t)q * (size_t)d_pad + k] = k < dim ? src[k] * scale : 0.f;
+}
+
+// Exact filter export (lr_filter_count): per 256-row group and query, the 8
+// pass words; counts per query and optional bitmap rows.
+__global__ void __launch_bounds__(kScanThreads) k_filter_eval(const ScanArgs a, unsigned long long *pass_cnt,
+                                                              uint32_t *out_bitmap, int64_t out_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  uint32_t *sw = smem + (size_t)warp * (size_t)a.n_slots * 8;
+  const bool qlive = lane < a.nq;
+  unsigned long long my = 0;
+  for (int64_t g = (int64_t)blockIdx.x * wpc + warp; g < a.n_groups; g += (int64_t)gridDim.x * wpc) {
+    for (int s = lane; s < a.n_slots; s += 32) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.slot_bm[s] + g * kGroupWords);
+      uint4 *dst = reinterpret_cast<uint4 *>(sw + s * 8);
+      dst[0] = __ldg(src);
+      dst[1] = __ldg(src + 1);
+    }
+    __syncwarp();
+    if (qlive) {
+      uint32_t pw[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) pw[w] = 0xFFFFFFFFu;
+      for (int c = a.qc_off[lane]; c < a.qc_off[lane + 1]; ++c) {
+        uint32_t cw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int t = a.cl_off[c]; t < a.cl_off[c + 1]; ++t) {
+          const uint32_t *s = sw + a.cl_slot[t] * 8;
+#pragma unroll
+          for (int w = 0; w < 8; ++w) cw[w] |= s[w];
+        }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) pw[w] &= cw[w];
+      }
+      const int64_t r0 = g * kGroupRows;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const int64_t left = a.n - (r0 + w * 32);
+        const uint32_t valid = left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u);
+        pw[w] &= valid;
+        my += (unsigned long long)__popc(pw[w]);
+        const int64_t word = g * kGroupWords + w;
+        if (out_bitmap != nullptr && word < out_words)
+          out_bitmap[(size_t)(a.q_base + lane) * (size_t)out_words + word] = pw[w];
+      }
+    }
+    __syncwarp();
+  }
+  if (qlive) atomicAdd(&pass_cnt[a.q_base + lane], my);
+}
+
+}  // namespace
+
+cudaError_t launch_rows_to_index(const float *in, float *out, int64_t n, int dim, int d_pad, int cosine,
+                                 uint32_t *err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int wpb = 8;
+  k_rows_to_index<<<(unsigned)((n + wpb - 1) / wpb), wpb * 32, 0, s>>>(in, out, n, dim, d_pad, cosine, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bitsets_to_termmajor(const uint64_t *bits, int64_t n, int vocab, uint32_t *out, int64_t n_words,
+                                        cudaStream_t s) {
+  if (n_words <= 0 || vocab <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((n_words + 127) / 128), (unsigned)((vocab + 63) / 64));
+  k_bitsets_to_termmajor<<<grid, 128, 0, s>>>(bits, n, vocab, out, n_words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *terms,
+                                    int n_terms, uint32_t *bitmaps, int64_t n_words, int64_t n, uint32_t *err,
+                                    cudaStream_t s) {
+  for (int t0 = 0; t0 < n_terms; t0 += 65535) {  // grid.y is limited to 65535
+    const int nt = n_terms - t0 < 65535 ? n_terms - t0 : 65535;
+    dim3 grid(64, (unsigned)nt);
+    k_scatter_postings<<<grid, 256, 0, s>>>(post_off, post_ids, terms + t0, nt, bitmaps + (size_t)t0 * n_words,
+                                            n_words, n, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,
+                                uint32_t *err, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const int wpb = 8;
+  k_prep_queries<<<(B + wpb - 1) / wpb, wpb * 32, 0, s>>>(q_in, q_out, B, dim, d_pad, cosine, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_eval(const ScanArgs &a, unsigned long long *pass_cnt, uint32_t *out_bitmap,
+                               int64_t out_words, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)(kScanThreads / 32) * (size_t)a.n_slots * 8 * sizeof(uint32_t);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_filter_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_filter_eval<<<grid, kScanThreads, smem, s>>>(a, pass_cnt, out_bitmap, out_words);
+  return cudaGetLastError();
+}
+
+}  // namespace lr

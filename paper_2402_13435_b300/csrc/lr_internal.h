@@ -1,0 +1,152 @@
+// Internal declarations of the filtered top-K library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lr.h"
+
+namespace lr {
+
+// ---------------------------------------------------------------- constants
+constexpr int kGroupRows = 256;     // rows per predicate group: 8 bitmap words of 32 jobs
+constexpr int kGroupWords = 8;
+constexpr int kMaxK = 4096;         // largest K (bitonic sort of the survivors in shared memory)
+constexpr int kMaxDim = 512;
+constexpr int kGemvMaxQ = 8;        // queries per GEMV launch (held in registers)
+constexpr int kGemvMaxSlots = 256;  // distinct terms per GEMV launch (shared-memory word table)
+constexpr int kFbBits = 11;         // radix digit of the exact fallback selection
+constexpr int kFbBins = 1 << kFbBits;
+constexpr int kFbPasses = 6;        // 5 x 11 + 9 = 64 key bits
+constexpr int kScanThreads = 256;
+
+// ------------------------------------------------------------- score keys
+// A candidate is one 64-bit key: the high word orders FP32 scores (larger key =
+// larger score; -0.0 is folded onto +0.0), the low word is ~job_id so that at
+// equal scores the smaller id has the larger key.  All keys of one query are
+// distinct, so "top K by key" is the (score desc, id asc) order.
+__host__ __device__ __forceinline__ uint32_t score_key(float s) {
+  s = s + 0.0f;  // -0.0 -> +0.0 (round-to-nearest)
+  uint32_t u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(s);
+#else
+  __builtin_memcpy(&u, &s, 4);
+#endif
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ __forceinline__ float key_score(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  float s;
+#ifdef __CUDA_ARCH__
+  s = __uint_as_float(u);
+#else
+  __builtin_memcpy(&s, &u, 4);
+#endif
+  return s;
+}
+
+__host__ __device__ __forceinline__ uint64_t make_key(float s, uint32_t id) {
+  return ((uint64_t)score_key(s) << 32) | (uint64_t)(0xFFFFFFFFu - id);
+}
+
+__host__ __device__ __forceinline__ uint32_t key_id(uint64_t k) { return 0xFFFFFFFFu - (uint32_t)k; }
+
+// ------------------------------------------------------------ scan launch
+enum ScanMode : int {
+  kCollect = 0,  // append keys >= tau[q] to the query's buffer
+  kHist = 1,     // histogram one radix digit of the keys that match prefix[q]
+};
+
+// Device view of one compiled sub-batch of filters and the per-query state.
+struct ScanArgs {
+  const float *X;        // [n][d_pad] FP32
+  int64_t n;
+  int32_t d_pad;
+  const float *Q;        // [B][d_pad] FP32 (the whole batch)
+  int32_t q_base, nq;    // this launch serves queries q_base .. q_base+nq-1
+  // compiled filters of this launch (query and slot ids are launch-local)
+  const uint32_t *const *slot_bm;  // [n_slots] term-major bitmap per distinct term
+  int32_t n_slots;
+  const int32_t *qc_off;  // [nq+1] clause ranges
+  const int32_t *cl_off;  // [n_clauses+1] slot ranges
+  const int32_t *cl_slot; // slot ids
+  // 256-row groups visited: g = g_begin + i * g_step, g < n_groups
+  int64_t g_begin, g_step, n_groups;
+  int32_t mode;
+  // per-query state, indexed by the batch-global query id
+  const uint64_t *tau;
+  uint64_t *buf;
+  int64_t buf_cap;
+  uint32_t *buf_cnt;
+  uint32_t *overflow;
+  unsigned long long *pass_cnt;  // nullable
+  const uint32_t *active;        // nullable: per-query participation
+  const uint32_t *any_active;    // nullable: the launch returns at once when *any_active == 0
+  // kHist mode
+  uint64_t *prefix;              // [B] key bits fixed so far
+  int32_t *krem;                 // [B] rank still to find below the prefix
+  uint32_t *hist;                // [B][kFbBins]
+  uint32_t *done_ctr;            // grid-completion counter (last CTA applies the digit step)
+  int32_t hist_pass;             // 0 .. kFbPasses-1
+  int32_t batch;                 // B (for the last-CTA step)
+  uint32_t *err;                 // device error word
+};
+
+struct SelectArgs {
+  int32_t mode;                  // 0: threshold from a sample, 1: final top-K
+  const uint64_t *buf;
+  int64_t cap;
+  const uint32_t *cnt;
+  const uint32_t *overflow;
+  // threshold mode
+  const int32_t *rank;           // [B] r: tau = r-th largest sample key (0 if fewer)
+  uint64_t *tau;                 // [B]
+  // final mode
+  const int32_t *k;              // [B]
+  const unsigned long long *pass_cnt;  // [B]
+  int32_t k_stride;
+  int32_t *out_ids;
+  float *out_scores;
+  int32_t *out_count;            // nullable
+  uint32_t *flag;                // [B] set when the candidate set cannot prove exactness
+  uint32_t *n_flagged;
+  const uint32_t *only;          // nullable: process only queries with only[q] != 0
+  const uint32_t *any;           // nullable: early exit when *any == 0
+  int32_t *cand_count_out;       // nullable stats
+  int32_t *fallback_out;         // nullable stats
+  int32_t fallback_round;        // 1 when this launch finishes fallback queries
+  int32_t force_flag;            // 1: flag every query (exercise the exact fallback)
+  uint32_t *err;                 // device error word
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s);
+cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
+cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,
+                                uint32_t *err, cudaStream_t s);
+cudaError_t launch_scatter_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *terms,
+                                    int n_terms, uint32_t *bitmaps, int64_t n_words, int64_t n, uint32_t *err,
+                                    cudaStream_t s);
+cudaError_t launch_rows_to_index(const float *in, float *out, int64_t n, int dim, int d_pad, int cosine,
+                                 uint32_t *err, cudaStream_t s);
+cudaError_t launch_bitsets_to_termmajor(const uint64_t *bits, int64_t n, int vocab, uint32_t *out, int64_t n_words,
+                                        cudaStream_t s);
+cudaError_t launch_filter_eval(const ScanArgs &a, unsigned long long *pass_cnt, uint32_t *out_bitmap,
+                               int64_t out_words, int grid, cudaStream_t s);
+cudaError_t launch_fallback_prepare(const unsigned long long *pass_cnt, const int32_t *k, const uint32_t *flag,
+                                    uint64_t *prefix, int32_t *krem, uint32_t *cnt, uint32_t *overflow,
+                                    uint32_t *hist, int B, const uint32_t *any, cudaStream_t s);
+cudaError_t launch_fallback_finish(const uint64_t *prefix, const uint32_t *flag, uint64_t *tau, int B,
+                                   const uint32_t *any, cudaStream_t s);
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+lr_status fail(lr_status st, const std::string &msg);
+lr_status cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace lr

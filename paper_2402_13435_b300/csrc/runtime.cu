@@ -1,0 +1,883 @@
+// Host runtime of the filtered top-K library: index construction with a
+// workspace sized once (appendix "Memory Pre-Allocation"), the per-batch filter
+// compiler, the launch plan of a search and the C ABI entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "lr_internal.h"
+
+namespace lr {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+lr_status fail(lr_status st, const std::string &msg) {
+  set_error(msg);
+  return st;
+}
+
+lr_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return LR_ERR_CUDA;
+}
+
+}  // namespace lr
+
+using namespace lr;
+
+#define LR_CK(call)                                     \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// a kernel launch of the search path, counted for the caller's statistics
+#define LR_LAUNCH(call) \
+  do {                  \
+    ++n_launch;         \
+    LR_CK(call);        \
+  } while (0)
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int64_t pow2_ceil(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Bump allocator over one device allocation.
+struct Carver {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    off = align_up(off, 256);
+    size_t at = off;
+    off += count * sizeof(T);
+    return at;
+  }
+};
+
+// One GEMV launch worth of compiled filters (device offsets into the filter region).
+struct SubBatch {
+  int q_base, nq, n_slots;
+  size_t off_slots, off_qc, off_cl, off_cs;
+};
+
+}  // namespace
+
+struct lr_index {
+  int device = 0, num_sms = 0;
+  int64_t n = 0;
+  int dim = 0, d_pad = 0, metric = 0, vocab = 0;
+  int64_t n_groups = 0, n_words = 0;
+  float *X = nullptr;
+  // term storage
+  uint32_t *dense_bm = nullptr;
+  int n_dense = 0;
+  std::vector<int32_t> term_dense;  // [vocab] dense bitmap index or -1
+  bool has_postings = false;
+  std::vector<int64_t> post_off_h;
+  int64_t *post_off_d = nullptr;
+  uint32_t *post_ids_d = nullptr;
+  // limits
+  int max_batch = 0, max_k = 0, max_batch_terms = 0, max_sparse = 0;
+  int auto_stride = 0;
+  int64_t samp_cap = 0, cand_cap = 0;
+  // workspace
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  float *q_raw = nullptr, *q_ws = nullptr;
+  uint32_t *sparse_bm = nullptr;
+  char *state = nullptr;
+  size_t state_bytes = 0;
+  uint64_t *tau = nullptr, *prefix = nullptr;
+  unsigned long long *pass = nullptr;
+  uint32_t *cnt = nullptr, *ovf = nullptr, *scnt = nullptr, *sovf = nullptr, *flag = nullptr;
+  int32_t *krem = nullptr, *kq = nullptr, *rank = nullptr;
+  uint32_t *n_flag = nullptr, *done_ctr = nullptr, *err = nullptr;
+  uint32_t *hist = nullptr;
+  uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
+  int32_t *o_ids = nullptr, *o_cnt = nullptr, *o_cand = nullptr, *o_fb = nullptr;
+  float *o_sc = nullptr;
+  char *filt_d = nullptr;
+  size_t filt_bytes = 0;
+  // pinned host staging (double-buffered) and its reuse events
+  char *filt_h[2] = {nullptr, nullptr};
+  cudaEvent_t filt_ev[2] = {nullptr, nullptr};
+  bool filt_ev_live[2] = {false, false};
+  int filt_turn = 0;
+  // host-side scratch of the filter compiler: term -> batch sparse id and
+  // term -> launch-local slot id, each valid while its stamp equals the
+  // current generation
+  std::vector<int32_t> sparse_stamp, sparse_id, local_stamp, local_id;
+  int32_t gen = 0;
+  size_t device_bytes = 0;
+};
+
+namespace {
+
+void free_index(lr_index *ix) {
+  if (!ix) return;
+  cudaFree(ix->X);
+  cudaFree(ix->dense_bm);
+  cudaFree(ix->post_off_d);
+  cudaFree(ix->post_ids_d);
+  cudaFree(ix->ws);
+  for (int i = 0; i < 2; ++i) {
+    if (ix->filt_h[i]) cudaFreeHost(ix->filt_h[i]);
+    if (ix->filt_ev[i]) cudaEventDestroy(ix->filt_ev[i]);
+  }
+  delete ix;
+}
+
+lr_status check_err_word(lr_index *ix, cudaStream_t s, const char *where) {
+  uint32_t e = 0;
+  LR_CK(cudaMemcpyAsync(&e, ix->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  LR_CK(cudaStreamSynchronize(s));
+  if (e != 0u) {
+    LR_CK(cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), s));
+    std::string m = std::string(where) + ": ";
+    if (e & 1u) m += "non-finite job embedding; ";
+    if (e & 4u) m += "posting id >= n_jobs; ";
+    if (e & 8u) m += "non-finite query embedding; ";
+    if (e & 2u) m += "inconsistent exact-selection state; ";
+    return fail((e & 2u) ? LR_ERR_CUDA : LR_ERR_INVALID, m);
+  }
+  return LR_OK;
+}
+
+// Threshold-sample geometry for a given stride: number of sampled groups and
+// the rank of the threshold in the sample for a given K.
+struct SamplePlan {
+  int stride = 0;          // 0: no sample
+  int64_t sampled_groups = 0;
+  int64_t sampled_rows = 0;
+  double frac = 1.0;
+};
+
+SamplePlan make_sample_plan(const lr_index *ix, int stride) {
+  SamplePlan p;
+  if (stride <= 0) return p;
+  p.stride = stride;
+  const int64_t begin = stride / 2;
+  p.sampled_groups = ix->n_groups > begin ? (ix->n_groups - begin + stride - 1) / stride : 0;
+  int64_t rows = 0;
+  if (p.sampled_groups > 0) {
+    // every sampled group is full except possibly the last group of the index
+    const int64_t last = begin + (p.sampled_groups - 1) * (int64_t)stride;
+    rows = (p.sampled_groups - 1) * kGroupRows + std::min<int64_t>(kGroupRows, ix->n - last * kGroupRows);
+  }
+  p.sampled_rows = rows;
+  p.frac = ix->n > 0 ? (double)rows / (double)ix->n : 1.0;
+  return p;
+}
+
+// rank r of the threshold in the sample: the expected number of index keys at or
+// above the r-th sample key is r / frac, kept >= 4K and r >= 64 so that fewer
+// than K candidates is a > 6-sigma event on exchangeable data.
+int32_t sample_rank(const SamplePlan &p, int K) {
+  if (p.stride == 0 || p.frac <= 0.0) return 0;
+  const double r = std::max(64.0, std::ceil(4.0 * (double)K * p.frac));
+  return (int32_t)r;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lr_version(void) { return 100; }
+
+const char *lr_last_error_message(void) { return g_last_error.c_str(); }
+
+size_t lr_index_device_bytes(const lr_index *index) { return index ? index->device_bytes : 0; }
+
+lr_status lr_index_destroy(lr_index *index) {
+  if (!index) return LR_OK;
+  cudaSetDevice(index->device);
+  free_index(index);
+  return LR_OK;
+}
+
+lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) {
+  if (!d || !out) return fail(LR_ERR_INVALID, "lr_index_create: null argument");
+  *out = nullptr;
+  if (d->n_jobs < 1 || d->n_jobs >= 0xFFFFFFFFll) return fail(LR_ERR_INVALID, "n_jobs must be in [1, 2^32-2]");
+  if (d->dim < 1 || d->dim > 256) return fail(LR_ERR_UNSUPPORTED, "dim must be in [1, 256]");
+  if (d->dtype != LR_F32) return fail(LR_ERR_UNSUPPORTED, "only LR_F32 storage is implemented");
+  if (d->metric != LR_DOT && d->metric != LR_COSINE) return fail(LR_ERR_INVALID, "unknown metric");
+  if (d->vocab < 1) return fail(LR_ERR_INVALID, "vocab must be >= 1");
+  if (!d->emb) return fail(LR_ERR_INVALID, "emb is null");
+  const bool have_bits = d->bitsets != nullptr;
+  const bool have_post = d->post_off != nullptr || d->post_ids != nullptr;
+  if (have_bits == have_post) return fail(LR_ERR_INVALID, "give exactly one of bitsets or posting lists");
+  if (have_post && (!d->post_off || !d->post_ids)) return fail(LR_ERR_INVALID, "post_off and post_ids both needed");
+  if (d->max_batch < 1) return fail(LR_ERR_INVALID, "max_batch must be >= 1");
+  if (d->max_k < 1 || d->max_k > kMaxK) return fail(LR_ERR_INVALID, "max_k must be in [1, 4096]");
+
+  cudaStream_t s = (cudaStream_t)stream;
+  lr_index *ix = new lr_index();
+  LR_CK(cudaGetDevice(&ix->device));
+  LR_CK(cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, ix->device));
+  ix->n = d->n_jobs;
+  ix->dim = d->dim;
+  ix->d_pad = d->dim <= 32 ? 32 : d->dim <= 64 ? 64 : d->dim <= 128 ? 128 : 256;
+  ix->metric = d->metric;
+  ix->vocab = d->vocab;
+  ix->n_groups = (ix->n + kGroupRows - 1) / kGroupRows;
+  ix->n_words = ix->n_groups * kGroupWords;
+  ix->max_batch = d->max_batch;
+  ix->max_k = d->max_k;
+  ix->max_batch_terms = d->max_batch_terms > 0 ? d->max_batch_terms : 16 * d->max_batch;
+  ix->max_sparse = d->max_sparse_terms > 0 ? d->max_sparse_terms : 256;
+
+  auto cleanup = [&](lr_status st) {
+    free_index(ix);
+    return st;
+  };
+#define CK2(call)                                                 \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, #call)); \
+  } while (0)
+
+  // ---- embeddings
+  const size_t xbytes = (size_t)ix->n * (size_t)ix->d_pad * sizeof(float);
+  if (cudaMalloc(&ix->X, xbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(LR_ERR_NOMEM, "cannot allocate the embedding matrix"));
+  }
+  ix->device_bytes += xbytes;
+  uint32_t *err_tmp = nullptr;
+  CK2(cudaMalloc(&err_tmp, sizeof(uint32_t)));
+  CK2(cudaMemsetAsync(err_tmp, 0, sizeof(uint32_t), s));
+  const bool cos = d->metric == LR_COSINE;
+  if (is_device_ptr(d->emb)) {
+    CK2(launch_rows_to_index(d->emb, ix->X, ix->n, ix->dim, ix->d_pad, cos, err_tmp, s));
+  } else {
+    const int64_t chunk = std::max<int64_t>(1, (64ll << 20) / ((int64_t)ix->dim * 4));
+    float *tmp = nullptr;
+    CK2(cudaMalloc(&tmp, (size_t)std::min<int64_t>(chunk, ix->n) * ix->dim * sizeof(float)));
+    for (int64_t r = 0; r < ix->n; r += chunk) {
+      const int64_t m = std::min<int64_t>(chunk, ix->n - r);
+      CK2(cudaMemcpyAsync(tmp, d->emb + (size_t)r * ix->dim, (size_t)m * ix->dim * sizeof(float),
+                          cudaMemcpyHostToDevice, s));
+      CK2(launch_rows_to_index(tmp, ix->X + (size_t)r * ix->d_pad, m, ix->dim, ix->d_pad, cos, err_tmp, s));
+      CK2(cudaStreamSynchronize(s));
+    }
+    cudaFree(tmp);
+  }
+
+  // ---- term storage
+  ix->term_dense.assign(ix->vocab, -1);
+  const size_t bm_bytes = (size_t)ix->n_words * sizeof(uint32_t);
+  if (have_bits) {
+    ix->n_dense = ix->vocab;
+    if (cudaMalloc(&ix->dense_bm, bm_bytes * ix->n_dense) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(fail(LR_ERR_NOMEM, "cannot allocate term bitmaps"));
+    }
+    ix->device_bytes += bm_bytes * ix->n_dense;
+    CK2(cudaMemsetAsync(ix->dense_bm, 0, bm_bytes * ix->n_dense, s));
+    for (int t = 0; t < ix->vocab; ++t) ix->term_dense[t] = t;
+    const int64_t W = (ix->vocab + 63) / 64;
+    const uint64_t *bits = d->bitsets;
+    uint64_t *tmpb = nullptr;
+    if (!is_device_ptr(bits)) {
+      CK2(cudaMalloc(&tmpb, (size_t)ix->n * W * sizeof(uint64_t)));
+      CK2(cudaMemcpyAsync(tmpb, bits, (size_t)ix->n * W * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+      bits = tmpb;
+    }
+    // bits past vocab in the last word would name terms >= vocab
+    CK2(launch_bitsets_to_termmajor(bits, ix->n, ix->vocab, ix->dense_bm, ix->n_words, s));
+    CK2(cudaStreamSynchronize(s));
+    if (tmpb) cudaFree(tmpb);
+  } else {
+    ix->has_postings = true;
+    ix->post_off_h.assign(d->post_off, d->post_off + ix->vocab + 1);
+    const std::vector<int64_t> &po = ix->post_off_h;
+    if (po[0] != 0) return cleanup(fail(LR_ERR_INVALID, "post_off[0] must be 0"));
+    for (int t = 0; t < ix->vocab; ++t)
+      if (po[t + 1] < po[t]) return cleanup(fail(LR_ERR_INVALID, "post_off must be non-decreasing"));
+    const int64_t nnz = po[ix->vocab];
+    std::vector<int32_t> order(ix->vocab);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return po[a + 1] - po[a] > po[b + 1] - po[b]; });
+    ix->n_dense = d->n_dense_terms < 0 ? ix->vocab : std::min(d->n_dense_terms, ix->vocab);
+    std::vector<int32_t> dense_terms(order.begin(), order.begin() + ix->n_dense);
+    for (int i = 0; i < ix->n_dense; ++i) ix->term_dense[dense_terms[i]] = i;
+    CK2(cudaMalloc(&ix->post_off_d, (size_t)(ix->vocab + 1) * sizeof(int64_t)));
+    CK2(cudaMalloc(&ix->post_ids_d, (size_t)std::max<int64_t>(nnz, 1) * sizeof(uint32_t)));
+    ix->device_bytes += (size_t)(ix->vocab + 1) * sizeof(int64_t) + (size_t)std::max<int64_t>(nnz, 1) * 4;
+    CK2(cudaMemcpyAsync(ix->post_off_d, po.data(), (size_t)(ix->vocab + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                        s));
+    if (nnz > 0)
+      CK2(cudaMemcpyAsync(ix->post_ids_d, d->post_ids, (size_t)nnz * sizeof(uint32_t),
+                          is_device_ptr(d->post_ids) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (ix->n_dense > 0) {
+      if (cudaMalloc(&ix->dense_bm, bm_bytes * ix->n_dense) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(LR_ERR_NOMEM, "cannot allocate dense term bitmaps"));
+      }
+      ix->device_bytes += bm_bytes * ix->n_dense;
+      CK2(cudaMemsetAsync(ix->dense_bm, 0, bm_bytes * ix->n_dense, s));
+      int32_t *terms_d = nullptr;
+      CK2(cudaMalloc(&terms_d, sizeof(int32_t) * ix->n_dense));
+      CK2(cudaMemcpyAsync(terms_d, dense_terms.data(), sizeof(int32_t) * ix->n_dense, cudaMemcpyHostToDevice, s));
+      CK2(launch_scatter_postings(ix->post_off_d, ix->post_ids_d, terms_d, ix->n_dense, ix->dense_bm, ix->n_words,
+                                  ix->n, err_tmp, s));
+      CK2(cudaStreamSynchronize(s));
+      cudaFree(terms_d);
+    }
+  }
+
+  // ---- sampling geometry and candidate capacities
+  ix->auto_stride = ix->n_groups >= 256 ? (int)std::min<int64_t>(64, ix->n_groups / 16) : 0;
+  const SamplePlan sp = make_sample_plan(ix, ix->auto_stride);
+  int64_t samp_rows = sp.sampled_rows;
+  samp_rows = std::max<int64_t>(samp_rows, std::min<int64_t>(ix->n_groups * kGroupRows / 2 + kGroupRows, 1 << 16));
+  ix->samp_cap = samp_rows;
+  int64_t cap = 0;
+  if (sp.stride > 0) {
+    const double r = std::max(64.0, std::ceil(4.0 * ix->max_k * sp.frac));
+    cap = pow2_ceil((int64_t)std::ceil(4.0 * r / sp.frac));
+  }
+  cap = std::max<int64_t>(cap, std::min<int64_t>(ix->n, 1 << 16));
+  cap = std::max<int64_t>(cap, ix->max_k);
+  ix->cand_cap = cap;
+
+  // ---- workspace, one allocation
+  const int B = ix->max_batch;
+  const int nsp = (ix->has_postings && ix->n_dense < ix->vocab) ? ix->max_sparse : 0;
+  ix->filt_bytes = align_up((size_t)B * 16 + (size_t)ix->max_batch_terms * 32 + (size_t)nsp * 4 + 65536, 256);
+  Carver cv;
+  const size_t o_qraw = cv.take<float>((size_t)B * ix->dim);
+  const size_t o_qws = cv.take<float>((size_t)B * ix->d_pad);
+  const size_t o_sparse = cv.take<uint32_t>((size_t)nsp * ix->n_words);
+  // per-query state block (cleared by one memset per search)
+  const size_t o_state = cv.take<char>(0);
+  const size_t o_tau = cv.take<uint64_t>(B);
+  const size_t o_pre = cv.take<uint64_t>(B);
+  const size_t o_pass = cv.take<unsigned long long>(B);
+  const size_t o_cnt = cv.take<uint32_t>(B);
+  const size_t o_ovf = cv.take<uint32_t>(B);
+  const size_t o_scnt = cv.take<uint32_t>(B);
+  const size_t o_sovf = cv.take<uint32_t>(B);
+  const size_t o_flag = cv.take<uint32_t>(B);
+  const size_t o_krem = cv.take<int32_t>(B);
+  const size_t o_nflag = cv.take<uint32_t>(1);
+  const size_t o_state_end = cv.take<char>(0);
+  const size_t o_done = cv.take<uint32_t>(1);
+  const size_t o_err = cv.take<uint32_t>(1);
+  const size_t o_kq = cv.take<int32_t>(B);
+  const size_t o_rank = cv.take<int32_t>(B);
+  const size_t o_hist = cv.take<uint32_t>((size_t)B * kFbBins);
+  const size_t o_samp = cv.take<uint64_t>((size_t)B * ix->samp_cap);
+  const size_t o_cand = cv.take<uint64_t>((size_t)B * ix->cand_cap);
+  const size_t o_oids = cv.take<int32_t>((size_t)B * ix->max_k);
+  const size_t o_osc = cv.take<float>((size_t)B * ix->max_k);
+  const size_t o_ocnt = cv.take<int32_t>(B);
+  const size_t o_ocand = cv.take<int32_t>(B);
+  const size_t o_ofb = cv.take<int32_t>(B);
+  const size_t o_filt = cv.take<char>(ix->filt_bytes);
+  ix->ws_bytes = align_up(cv.off, 256);
+  if (cudaMalloc(&ix->ws, ix->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(LR_ERR_NOMEM, "cannot allocate the search workspace (" + std::to_string(ix->ws_bytes) +
+                                          " bytes); lower max_batch, max_k or max_sparse_terms"));
+  }
+  ix->device_bytes += ix->ws_bytes;
+  char *w = ix->ws;
+  ix->q_raw = (float *)(w + o_qraw);
+  ix->q_ws = (float *)(w + o_qws);
+  ix->sparse_bm = nsp ? (uint32_t *)(w + o_sparse) : nullptr;
+  ix->state = w + o_state;
+  ix->state_bytes = o_state_end - o_state;
+  ix->tau = (uint64_t *)(w + o_tau);
+  ix->prefix = (uint64_t *)(w + o_pre);
+  ix->pass = (unsigned long long *)(w + o_pass);
+  ix->cnt = (uint32_t *)(w + o_cnt);
+  ix->ovf = (uint32_t *)(w + o_ovf);
+  ix->scnt = (uint32_t *)(w + o_scnt);
+  ix->sovf = (uint32_t *)(w + o_sovf);
+  ix->flag = (uint32_t *)(w + o_flag);
+  ix->krem = (int32_t *)(w + o_krem);
+  ix->n_flag = (uint32_t *)(w + o_nflag);
+  ix->done_ctr = (uint32_t *)(w + o_done);
+  ix->err = (uint32_t *)(w + o_err);
+  ix->kq = (int32_t *)(w + o_kq);
+  ix->rank = (int32_t *)(w + o_rank);
+  ix->hist = (uint32_t *)(w + o_hist);
+  ix->samp_buf = (uint64_t *)(w + o_samp);
+  ix->cand_buf = (uint64_t *)(w + o_cand);
+  ix->o_ids = (int32_t *)(w + o_oids);
+  ix->o_sc = (float *)(w + o_osc);
+  ix->o_cnt = (int32_t *)(w + o_ocnt);
+  ix->o_cand = (int32_t *)(w + o_ocand);
+  ix->o_fb = (int32_t *)(w + o_ofb);
+  ix->filt_d = w + o_filt;
+  CK2(cudaMemsetAsync(ix->done_ctr, 0, sizeof(uint32_t), s));
+  CK2(cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), s));
+  CK2(cudaMemsetAsync(ix->hist, 0, (size_t)B * kFbBins * sizeof(uint32_t), s));
+  for (int i = 0; i < 2; ++i) {
+    CK2(cudaHostAlloc((void **)&ix->filt_h[i], ix->filt_bytes, cudaHostAllocDefault));
+    CK2(cudaEventCreateWithFlags(&ix->filt_ev[i], cudaEventDisableTiming));
+  }
+  ix->sparse_stamp.assign(ix->vocab, 0);
+  ix->sparse_id.assign(ix->vocab, -1);
+  ix->local_stamp.assign(ix->vocab, 0);
+  ix->local_id.assign(ix->vocab, -1);
+
+  // ---- input validity recorded by the build kernels
+  uint32_t e = 0;
+  CK2(cudaMemcpyAsync(&e, err_tmp, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CK2(cudaStreamSynchronize(s));
+  cudaFree(err_tmp);
+  if (e & 1u) return cleanup(fail(LR_ERR_INVALID, "non-finite value in the job embeddings"));
+  if (e & 4u) return cleanup(fail(LR_ERR_INVALID, "posting list names a job id >= n_jobs"));
+  *out = ix;
+  return LR_OK;
+#undef CK2
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------------- filter compiler
+namespace {
+
+struct Compiled {
+  std::vector<SubBatch> subs;
+  std::vector<int32_t> sparse_terms;  // distinct posting-list terms of the batch
+  size_t off_k = 0, off_rank = 0, off_sparse = 0, bytes = 0;
+};
+
+// Validate the CNF batch and lay out, in the pinned staging buffer, the
+// per-launch slot tables and clause lists.  Slot pointers are device addresses
+// of dense index bitmaps or of workspace bitmaps for posting-list terms.
+lr_status compile_filters(lr_index *ix, const lr_filters *f, int B, int max_q_per_launch, char *stage,
+                          Compiled &C) {
+  if (!f || !f->q_off || (!f->c_off && B > 0)) return fail(LR_ERR_INVALID, "filters: null arrays");
+  const int32_t *qo = f->q_off, *co = f->c_off;
+  if (qo[0] != 0) return fail(LR_ERR_INVALID, "filters: q_off[0] must be 0");
+  for (int b = 0; b < B; ++b)
+    if (qo[b + 1] < qo[b]) return fail(LR_ERR_INVALID, "filters: q_off must be non-decreasing");
+  const int nC = qo[B];
+  if (nC > 0 && !f->terms) return fail(LR_ERR_INVALID, "filters: terms is null");
+  if (nC > 0 && co[0] != 0) return fail(LR_ERR_INVALID, "filters: c_off[0] must be 0");
+  for (int c = 0; c < nC; ++c)
+    if (co[c + 1] <= co[c]) return fail(LR_ERR_INVALID, "filters: a clause with zero terms can never pass");
+  const int nT = nC > 0 ? co[nC] : 0;
+  if (nT > ix->max_batch_terms) return fail(LR_ERR_WORKSPACE, "filters: more term occurrences than max_batch_terms");
+  for (int i = 0; i < nT; ++i)
+    if (f->terms[i] >= (uint32_t)ix->vocab) return fail(LR_ERR_INVALID, "filters: term id >= vocab");
+
+  // batch-level: distinct posting-list terms get a workspace bitmap each
+  const int32_t bgen = ++ix->gen;
+  C.sparse_terms.clear();
+  for (int i = 0; i < nT; ++i) {
+    const int32_t t = (int32_t)f->terms[i];
+    if (ix->term_dense[t] >= 0 || ix->sparse_stamp[t] == bgen) continue;
+    ix->sparse_stamp[t] = bgen;
+    ix->sparse_id[t] = (int32_t)C.sparse_terms.size();
+    C.sparse_terms.push_back(t);
+  }
+  if ((int)C.sparse_terms.size() > ix->max_sparse)
+    return fail(LR_ERR_WORKSPACE, "filters: more distinct posting-list terms than max_sparse_terms");
+
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t al) {
+    off = align_up(off, al);
+    size_t at = off;
+    off += bytes;
+    return at;
+  };
+  C.off_k = take(sizeof(int32_t) * B, 16);
+  C.off_rank = take(sizeof(int32_t) * B, 16);
+  C.off_sparse = take(sizeof(int32_t) * std::max<size_t>(C.sparse_terms.size(), 1), 16);
+  if (off > ix->filt_bytes) return fail(LR_ERR_WORKSPACE, "filters: staging area too small");
+  if (!C.sparse_terms.empty())
+    std::memcpy(stage + C.off_sparse, C.sparse_terms.data(), sizeof(int32_t) * C.sparse_terms.size());
+
+  // launch-level: runs of up to max_q_per_launch queries whose distinct terms
+  // fit the kernel's shared-memory word table (kGemvMaxSlots)
+  const size_t bm_words = (size_t)ix->n_words;
+  C.subs.clear();
+  int b = 0;
+  while (b < B) {
+    const int32_t lgen = ++ix->gen;
+    std::vector<int32_t> slots;  // distinct terms of this launch in first-use order
+    int e = b;
+    while (e < B && e - b < max_q_per_launch) {
+      const size_t before = slots.size();
+      for (int c = qo[e]; c < qo[e + 1]; ++c)
+        for (int i = co[c]; i < co[c + 1]; ++i) {
+          const int32_t t = (int32_t)f->terms[i];
+          if (ix->local_stamp[t] == lgen) continue;
+          ix->local_stamp[t] = lgen;
+          ix->local_id[t] = (int32_t)slots.size();
+          slots.push_back(t);
+        }
+      if ((int)slots.size() > kGemvMaxSlots) {
+        if (e == b) return fail(LR_ERR_UNSUPPORTED, "a single filter uses more than 256 distinct terms");
+        for (size_t i = before; i < slots.size(); ++i) ix->local_stamp[slots[i]] = 0;  // query e starts the next run
+        slots.resize(before);
+        break;
+      }
+      ++e;
+    }
+    SubBatch sb;
+    sb.q_base = b;
+    sb.nq = e - b;
+    sb.n_slots = (int)slots.size();
+    const int ncl = qo[e] - qo[b];
+    const int ntm = ncl > 0 ? co[qo[e]] - co[qo[b]] : 0;
+    sb.off_slots = take(sizeof(uint64_t) * std::max<size_t>(slots.size(), 1), 16);
+    sb.off_qc = take(sizeof(int32_t) * (sb.nq + 1), 16);
+    sb.off_cl = take(sizeof(int32_t) * (ncl + 1), 16);
+    sb.off_cs = take(sizeof(int32_t) * std::max(ntm, 1), 16);
+    if (off > ix->filt_bytes) return fail(LR_ERR_WORKSPACE, "filters: staging area too small");
+    uint64_t *sp = (uint64_t *)(stage + sb.off_slots);
+    for (size_t i = 0; i < slots.size(); ++i) {
+      const int32_t t = slots[i];
+      const uint32_t *ptr = ix->term_dense[t] >= 0 ? ix->dense_bm + (size_t)ix->term_dense[t] * bm_words
+                                                   : ix->sparse_bm + (size_t)ix->sparse_id[t] * bm_words;
+      sp[i] = (uint64_t)(uintptr_t)ptr;
+    }
+    int32_t *qc = (int32_t *)(stage + sb.off_qc);
+    int32_t *cl = (int32_t *)(stage + sb.off_cl);
+    int32_t *cs = (int32_t *)(stage + sb.off_cs);
+    int ci = 0, ti = 0;
+    qc[0] = 0;
+    cl[0] = 0;
+    for (int qq = b; qq < e; ++qq) {
+      for (int c = qo[qq]; c < qo[qq + 1]; ++c) {
+        for (int i = co[c]; i < co[c + 1]; ++i) cs[ti++] = ix->local_id[(int32_t)f->terms[i]];
+        cl[++ci] = ti;
+      }
+      qc[qq - b + 1] = ci;
+    }
+    C.subs.push_back(sb);
+    b = e;
+  }
+  C.bytes = off;
+  return LR_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ search
+namespace {
+
+lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, const int32_t *k, int k_all,
+                     int32_t *out_ids, float *out_scores, int32_t *out_count, const lr_search_opts *opts,
+                     const lr_search_stats *stats, cudaStream_t s) {
+  if (B < 1) return fail(LR_ERR_INVALID, "B must be >= 1");
+  if (B > ix->max_batch) return fail(LR_ERR_WORKSPACE, "B exceeds max_batch");
+  if (!q || !out_ids || !out_scores) return fail(LR_ERR_INVALID, "null query or output pointer");
+  if (k_all < 1) return fail(LR_ERR_INVALID, "k_all must be >= 1");
+  if (k_all > ix->max_k && k == nullptr) return fail(LR_ERR_INVALID, "K exceeds max_k");
+  lr_search_opts o{};
+  if (opts) o = *opts;
+  if (o.plan == LR_PLAN_TC) return fail(LR_ERR_UNSUPPORTED, "tensor-core plan not available in this build");
+
+  // pick and wait for a staging buffer
+  const int turn = ix->filt_turn;
+  ix->filt_turn ^= 1;
+  if (ix->filt_ev_live[turn]) LR_CK(cudaEventSynchronize(ix->filt_ev[turn]));
+  char *stage = ix->filt_h[turn];
+  Compiled C;
+  lr_status st = compile_filters(ix, f, B, kGemvMaxQ, stage, C);
+  if (st != LR_OK) return st;
+  int32_t *ks = (int32_t *)(stage + C.off_k);
+  for (int b = 0; b < B; ++b) {
+    const int kb = k ? k[b] : k_all;
+    if (kb < 1 || kb > ix->max_k || kb > k_all)
+      return fail(LR_ERR_INVALID, "K must be in [1, min(max_k, k_all)]");
+    ks[b] = kb;
+  }
+  // threshold sample plan
+  int stride = ix->auto_stride;
+  if (o.sample_stride > 0) stride = o.sample_stride;
+  if (o.sample_stride < 0) stride = 0;
+  const SamplePlan sp = make_sample_plan(ix, stride);
+  if (sp.stride > 0 && sp.sampled_rows > ix->samp_cap)
+    return fail(LR_ERR_WORKSPACE, "sample stride too small for the sample workspace");
+  int32_t *rk = (int32_t *)(stage + C.off_rank);
+  for (int b = 0; b < B; ++b) rk[b] = sample_rank(sp, ks[b]);
+  int64_t cap = ix->cand_cap;
+  if (o.cand_cap > 0) cap = std::min<int64_t>(cap, std::max<int64_t>(o.cand_cap, 1));
+
+  // ---- device work
+  int32_t n_launch = 0, n_scan = 0;
+  LR_CK(cudaMemcpyAsync(ix->filt_d, stage, C.bytes, cudaMemcpyHostToDevice, s));
+  LR_CK(cudaEventRecord(ix->filt_ev[turn], s));
+  ix->filt_ev_live[turn] = true;
+  LR_CK(cudaMemsetAsync(ix->state, 0, ix->state_bytes, s));
+  LR_CK(cudaMemcpyAsync(ix->kq, ix->filt_d + C.off_k, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  LR_CK(cudaMemcpyAsync(ix->rank, ix->filt_d + C.off_rank, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  const float *qsrc = q;
+  if (!is_device_ptr(q)) {
+    LR_CK(cudaMemcpyAsync(ix->q_raw, q, sizeof(float) * (size_t)B * ix->dim, cudaMemcpyHostToDevice, s));
+    qsrc = ix->q_raw;
+  }
+  LR_LAUNCH(launch_prep_queries(qsrc, ix->q_ws, B, ix->dim, ix->d_pad, ix->metric == LR_COSINE, ix->err, s));
+  if (!C.sparse_terms.empty()) {
+    const size_t words = (size_t)ix->n_words * C.sparse_terms.size();
+    LR_CK(cudaMemsetAsync(ix->sparse_bm, 0, words * sizeof(uint32_t), s));
+    LR_LAUNCH(launch_scatter_postings(ix->post_off_d, ix->post_ids_d, (const int32_t *)(ix->filt_d + C.off_sparse),
+                                  (int)C.sparse_terms.size(), ix->sparse_bm, ix->n_words, ix->n, ix->err, s));
+  }
+
+  auto scan_args = [&](const SubBatch &sb) {
+    ScanArgs a{};
+    a.X = ix->X;
+    a.n = ix->n;
+    a.d_pad = ix->d_pad;
+    a.Q = ix->q_ws;
+    a.q_base = sb.q_base;
+    a.nq = sb.nq;
+    a.slot_bm = (const uint32_t *const *)(ix->filt_d + sb.off_slots);
+    a.n_slots = sb.n_slots;
+    a.qc_off = (const int32_t *)(ix->filt_d + sb.off_qc);
+    a.cl_off = (const int32_t *)(ix->filt_d + sb.off_cl);
+    a.cl_slot = (const int32_t *)(ix->filt_d + sb.off_cs);
+    a.n_groups = ix->n_groups;
+    a.g_begin = 0;
+    a.g_step = 1;
+    a.mode = kCollect;
+    a.err = ix->err;
+    a.done_ctr = ix->done_ctr;
+    a.batch = B;
+    return a;
+  };
+  const int vec = ix->d_pad / 32;
+  auto nq_tmpl = [](int nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : nq <= 4 ? 4 : 8; };
+  auto grid_for = [&](int64_t groups) {
+    const int64_t warps = (groups + 0);
+    const int64_t want = (warps + (kScanThreads / 32) - 1) / (kScanThreads / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ix->num_sms * 4));
+  };
+
+  // 1. threshold sample
+  if (sp.stride > 0) {
+    for (const SubBatch &sb : C.subs) {
+      ScanArgs a = scan_args(sb);
+      a.g_begin = sp.stride / 2;
+      a.g_step = sp.stride;
+      a.tau = nullptr;  // keep every passing key of the sampled groups
+      a.buf = ix->samp_buf;
+      a.buf_cap = ix->samp_cap;
+      a.buf_cnt = ix->scnt;
+      a.overflow = ix->sovf;
+      LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(sp.sampled_groups), s));
+    }
+    SelectArgs t{};
+    t.mode = 0;
+    t.buf = ix->samp_buf;
+    t.cap = ix->samp_cap;
+    t.cnt = ix->scnt;
+    t.overflow = ix->sovf;
+    t.rank = ix->rank;
+    t.tau = ix->tau;
+    LR_LAUNCH(launch_select(t, B, s));
+  }
+  // 2. main scan: candidates at or above the threshold, pass counts
+  if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
+  for (const SubBatch &sb : C.subs) {
+    ScanArgs a = scan_args(sb);
+    a.tau = ix->tau;
+    a.buf = ix->cand_buf;
+    a.buf_cap = cap;
+    a.buf_cnt = ix->cnt;
+    a.overflow = ix->ovf;
+    a.pass_cnt = ix->pass;
+    LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(ix->n_groups), s));
+    ++n_scan;
+  }
+  if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
+  // 3. final selection into the caller's device outputs, or into workspace
+  //    rows that are copied back when the outputs are host memory
+  const bool dev_out = is_device_ptr(out_ids) && is_device_ptr(out_scores) &&
+                       (out_count == nullptr || is_device_ptr(out_count));
+  if (!dev_out && k_all > ix->max_k) return fail(LR_ERR_INVALID, "host outputs need k_all <= max_k");
+  SelectArgs fa{};
+  fa.mode = 1;
+  fa.buf = ix->cand_buf;
+  fa.cap = cap;
+  fa.cnt = ix->cnt;
+  fa.overflow = ix->ovf;
+  fa.k = ix->kq;
+  fa.pass_cnt = ix->pass;
+  fa.k_stride = k_all;
+  fa.out_ids = dev_out ? out_ids : ix->o_ids;
+  fa.out_scores = dev_out ? out_scores : ix->o_sc;
+  fa.out_count = dev_out ? out_count : ix->o_cnt;
+  fa.flag = ix->flag;
+  fa.n_flagged = ix->n_flag;
+  fa.cand_count_out = ix->o_cand;
+  fa.fallback_out = ix->o_fb;
+  fa.fallback_round = 0;
+  fa.force_flag = o.force_exact_fallback ? 1 : 0;
+  fa.err = ix->err;
+  LR_LAUNCH(launch_select(fa, B, s));
+  // 4. exact fallback for flagged queries (each launch returns at once when none is flagged)
+  LR_LAUNCH(launch_fallback_prepare(ix->pass, ix->kq, ix->flag, ix->prefix, ix->krem, ix->cnt, ix->ovf, ix->hist, B,
+                                ix->n_flag, s));
+  for (int p = 0; p < kFbPasses; ++p) {
+    for (const SubBatch &sb : C.subs) {
+      ScanArgs a = scan_args(sb);
+      a.mode = kHist;
+      a.hist_pass = p;
+      a.prefix = ix->prefix;
+      a.krem = ix->krem;
+      a.hist = ix->hist;
+      a.active = ix->flag;
+      a.any_active = ix->n_flag;
+      LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(ix->n_groups), s));
+    }
+  }
+  LR_LAUNCH(launch_fallback_finish(ix->prefix, ix->flag, ix->tau, B, ix->n_flag, s));
+  for (const SubBatch &sb : C.subs) {
+    ScanArgs a = scan_args(sb);
+    a.tau = ix->tau;
+    a.buf = ix->cand_buf;
+    a.buf_cap = ix->cand_cap;
+    a.buf_cnt = ix->cnt;
+    a.overflow = ix->ovf;
+    a.active = ix->flag;
+    a.any_active = ix->n_flag;
+    LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(ix->n_groups), s));
+  }
+  SelectArgs fb = fa;
+  fb.cap = ix->cand_cap;
+  fb.only = ix->flag;
+  fb.any = ix->n_flag;
+  fb.fallback_round = 1;
+  fb.force_flag = 0;
+  LR_LAUNCH(launch_select(fb, B, s));
+
+  // 5. host outputs and statistics
+  bool need_sync = false;
+  if (!dev_out) {
+    LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
+    LR_CK(cudaMemcpyAsync(out_scores, ix->o_sc, sizeof(float) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
+    if (out_count) LR_CK(cudaMemcpyAsync(out_count, ix->o_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
+    need_sync = true;
+  }
+  if (stats) {
+    if (stats->n_launches) *stats->n_launches = n_launch;
+    if (stats->n_scan_launches) *stats->n_scan_launches = n_scan;
+    struct { void *dst; const void *src; size_t bytes; } cp[3] = {
+        {stats->pass_count, ix->pass, sizeof(int64_t) * B},
+        {stats->cand_count, ix->o_cand, sizeof(int32_t) * B},
+        {stats->fallback, ix->o_fb, sizeof(int32_t) * B}};
+    for (auto &c : cp) {
+      if (!c.dst) continue;
+      LR_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, s));
+      need_sync |= !is_device_ptr(c.dst);
+    }
+  }
+  if (need_sync) LR_CK(cudaStreamSynchronize(s));
+  return LR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lr_status lr_search_ex(lr_index *index, const float *q, int32_t B, const lr_filters *f, const int32_t *k,
+                       int32_t k_all, int32_t *out_ids, float *out_scores, int32_t *out_count,
+                       const lr_search_opts *opts, const lr_search_stats *stats, void *stream) {
+  if (!index) return fail(LR_ERR_INVALID, "index is null");
+  return run_search(index, q, B, f, k, k_all, out_ids, out_scores, out_count, opts, stats, (cudaStream_t)stream);
+}
+
+lr_status lr_search(lr_index *index, const float *q, int32_t B, const lr_filters *f, const int32_t *k,
+                    int32_t k_all, int32_t *out_ids, float *out_scores, int32_t *out_count, void *stream) {
+  return lr_search_ex(index, q, B, f, k, k_all, out_ids, out_scores, out_count, nullptr, nullptr, stream);
+}
+
+lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64_t *out_pass, uint32_t *out_bitmap,
+                          void *stream) {
+  if (!index) return fail(LR_ERR_INVALID, "index is null");
+  if (!out_pass) return fail(LR_ERR_INVALID, "out_pass is null");
+  if (B < 1) return fail(LR_ERR_INVALID, "B must be >= 1");
+  if (B > index->max_batch) return fail(LR_ERR_WORKSPACE, "B exceeds max_batch");
+  lr_index *ix = index;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int turn = ix->filt_turn;
+  ix->filt_turn ^= 1;
+  if (ix->filt_ev_live[turn]) LR_CK(cudaEventSynchronize(ix->filt_ev[turn]));
+  char *stage = ix->filt_h[turn];
+  Compiled C;
+  lr_status st = compile_filters(ix, f, B, 32, stage, C);
+  if (st != LR_OK) return st;
+  LR_CK(cudaMemcpyAsync(ix->filt_d, stage, C.bytes, cudaMemcpyHostToDevice, s));
+  LR_CK(cudaEventRecord(ix->filt_ev[turn], s));
+  ix->filt_ev_live[turn] = true;
+  LR_CK(cudaMemsetAsync(ix->state, 0, ix->state_bytes, s));
+  if (!C.sparse_terms.empty()) {
+    const size_t words = (size_t)ix->n_words * C.sparse_terms.size();
+    LR_CK(cudaMemsetAsync(ix->sparse_bm, 0, words * sizeof(uint32_t), s));
+    LR_CK(launch_scatter_postings(ix->post_off_d, ix->post_ids_d, (const int32_t *)(ix->filt_d + C.off_sparse),
+                                  (int)C.sparse_terms.size(), ix->sparse_bm, ix->n_words, ix->n, ix->err, s));
+  }
+  const int64_t out_words = (ix->n + 31) / 32;
+  const bool bm_dev = out_bitmap && is_device_ptr(out_bitmap);
+  uint32_t *bm = nullptr;
+  if (out_bitmap) {
+    if (bm_dev) {
+      bm = out_bitmap;
+    } else {
+      LR_CK(cudaMallocAsync((void **)&bm, sizeof(uint32_t) * (size_t)B * out_words, s));
+    }
+  }
+  for (const SubBatch &sb : C.subs) {
+    ScanArgs a{};
+    a.n = ix->n;
+    a.q_base = sb.q_base;
+    a.nq = sb.nq;
+    a.slot_bm = (const uint32_t *const *)(ix->filt_d + sb.off_slots);
+    a.n_slots = sb.n_slots;
+    a.qc_off = (const int32_t *)(ix->filt_d + sb.off_qc);
+    a.cl_off = (const int32_t *)(ix->filt_d + sb.off_cl);
+    a.cl_slot = (const int32_t *)(ix->filt_d + sb.off_cs);
+    a.n_groups = ix->n_groups;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ix->n_groups + 7) / 8, (int64_t)ix->num_sms * 4));
+    LR_CK(launch_filter_eval(a, ix->pass, bm, out_words, grid, s));
+  }
+  LR_CK(cudaMemcpyAsync(out_pass, ix->pass, sizeof(int64_t) * B, cudaMemcpyDefault, s));
+  if (out_bitmap && !bm_dev) {
+    LR_CK(cudaMemcpyAsync(out_bitmap, bm, sizeof(uint32_t) * (size_t)B * out_words, cudaMemcpyDeviceToHost, s));
+    LR_CK(cudaFreeAsync(bm, s));
+  }
+  if (!is_device_ptr(out_pass) || (out_bitmap && !bm_dev)) LR_CK(cudaStreamSynchronize(s));
+  return LR_OK;
+}
+
+lr_status lr_index_sync(lr_index *index, void *stream) {
+  if (!index) return fail(LR_ERR_INVALID, "index is null");
+  return check_err_word(index, (cudaStream_t)stream, "lr_index_sync");
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// Per-query selection over candidate buffers (appendix "Fast Top K Selection").
+//
+// The paper selects with a score-bucket histogram that needs known score bounds.
+// Here every candidate is a distinct 64-bit key (ordered score, ~job id), so an
+// exact radix selection needs no bounds: 8 passes of an 8-bit digit histogram
+// in shared memory find the r-th largest key; the keys at or above it are then
+// gathered and sorted by a bitonic network in shared memory.
+//
+//   mode 0 (threshold): tau[q] = r-th largest key of the sample buffer, or 0
+//                       when the sample holds fewer than r keys.
+//   mode 1 (final):     top min(K, #passing) keys of the candidate buffer,
+//                       written as (id, score) rows; a query whose buffer cannot
+//                       prove it holds the top K (overflow, or fewer than K
+//                       candidates above a non-zero threshold) is flagged for the
+//                       exact fallback instead.
+#include "lr_internal.h"
+
+namespace lr {
+namespace {
+
+constexpr int kSelThreads = 512;
+constexpr int kSmemKeys = 8192;  // candidate keys staged in shared memory when they fit
+
+struct SelShared {
+  uint32_t hist[256];
+  uint32_t digit;
+  uint32_t krem;
+  uint32_t n_out;
+};
+
+// r-th largest (1-based) of n distinct keys; keys may be in shared or global memory.
+__device__ uint64_t block_kth(const uint64_t *keys, int64_t n, uint32_t r, SelShared &sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t prefix = 0;
+  uint32_t krem = r;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    const int top = shift + 8;
+    for (int i = tid; i < 256; i += blockDim.x) sh.hist[i] = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < n; i += blockDim.x) {
+      const uint64_t key = keys[i];
+      if (top >= 64 || (key >> top) == (prefix >> top)) atomicAdd(&sh.hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t c[8], cs = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) { c[j] = sh.hist[255 - 8 * lane - j]; cs += c[j]; }
+      uint32_t incl = cs;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += t;
+      }
+      const uint32_t excl = incl - cs;
+      const unsigned hit = __ballot_sync(0xFFFFFFFFu, excl < krem && krem <= incl);
+      if (hit == 0u) {
+        if (lane == 0) { sh.digit = 0u; sh.krem = 1u; }  // unreachable for r <= n
+      } else if (lane == __ffs(hit) - 1) {
+        uint32_t cum = excl;
+        int d = 255 - 8 * lane;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (cum + c[j] >= krem) { d = 255 - 8 * lane - j; break; }
+          cum += c[j];
+        }
+        sh.digit = (uint32_t)d;
+        sh.krem = krem - cum;
+      }
+    }
+    __syncthreads();
+    prefix |= (uint64_t)sh.digit << shift;
+    krem = sh.krem;
+    __syncthreads();
+  }
+  return prefix;
+}
+
+__device__ void bitonic_desc(uint64_t *s, int P) {
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+        const int pos = 2 * i - (i & (stride - 1));
+        const int par = pos + stride;
+        const bool desc = (pos & size) == 0;
+        const uint64_t x = s[pos], y = s[par];
+        if ((x < y) == desc) { s[pos] = y; s[par] = x; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
+  const int q = blockIdx.x;
+  if (a.any != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any) == 0u) return;
+  if (a.only != nullptr && a.only[q] == 0u) return;
+  extern __shared__ __align__(16) uint64_t sbuf[];  // [kSmemKeys] keys, then [kMaxK] sort area
+  __shared__ SelShared sh;
+  const int tid = threadIdx.x;
+  const uint32_t cnt = a.cnt[q];
+  const bool ovf = a.overflow[q] != 0u;
+  const int64_t n = (int64_t)cnt < a.cap ? (int64_t)cnt : a.cap;
+  const uint64_t *gkeys = a.buf + (size_t)q * (size_t)a.cap;
+
+  const uint64_t *keys = gkeys;
+  if (n <= kSmemKeys) {
+    for (int64_t i = tid; i < n; i += blockDim.x) sbuf[i] = __ldcg(gkeys + i);
+    __syncthreads();
+    keys = sbuf;
+  }
+
+  if (a.mode == 0) {
+    const int32_t r = a.rank[q];
+    uint64_t t = 0;
+    if (r > 0 && !ovf && n >= r) t = block_kth(keys, n, (uint32_t)r, sh);
+    if (tid == 0) a.tau[q] = t;
+    return;
+  }
+
+  const int32_t K = a.k[q];
+  const unsigned long long P = a.pass_cnt[q];
+  const int32_t kp = (int32_t)((unsigned long long)K < P ? (unsigned long long)K : P);
+  const bool exact = !ovf && (n >= K || (unsigned long long)n == P);
+  int32_t *ids = a.out_ids + (size_t)q * (size_t)a.k_stride;
+  float *sc = a.out_scores + (size_t)q * (size_t)a.k_stride;
+  if (a.fallback_round == 0 && (!exact || a.force_flag)) {
+    if (tid == 0) {
+      a.flag[q] = 1u;
+      atomicAdd(a.n_flagged, 1u);
+    }
+    return;
+  }
+  if (!exact) {  // the exact fallback always gathers exactly min(K, #passing) keys
+    if (tid == 0) atomicOr(a.err, 2u);
+    return;
+  }
+  uint64_t *sort = sbuf + kSmemKeys;
+  int P2 = 1;
+  while (P2 < kp) P2 <<= 1;
+  if (kp > 0) {
+    const uint64_t kth = block_kth(keys, n, (uint32_t)kp, sh);
+    if (tid == 0) sh.n_out = 0u;
+    for (int i = tid; i < P2; i += blockDim.x) sort[i] = 0ull;
+    __syncthreads();
+    for (int64_t i = tid; i < n; i += blockDim.x) {
+      const uint64_t key = keys[i];
+      if (key >= kth) {
+        const uint32_t pos = atomicAdd(&sh.n_out, 1u);
+        if (pos < (uint32_t)P2) sort[pos] = key;
+      }
+    }
+    __syncthreads();
+    bitonic_desc(sort, P2);
+  }
+  for (int i = tid; i < a.k_stride; i += blockDim.x) {
+    if (i < kp) {
+      const uint64_t key = sort[i];
+      ids[i] = (int32_t)key_id(key);
+      sc[i] = key_score((uint32_t)(key >> 32));
+    } else {
+      ids[i] = -1;
+      sc[i] = -INFINITY;
+    }
+  }
+  if (tid == 0) {
+    if (a.out_count) a.out_count[q] = kp;
+    if (a.cand_count_out) a.cand_count_out[q] = (int32_t)cnt;
+    if (a.fallback_out) a.fallback_out[q] = a.fallback_round;
+  }
+}
+
+// Fallback set-up: for flagged queries start the radix selection of the
+// min(K, #passing)-th key from an empty prefix and clear the candidate buffer.
+__global__ void k_fallback_prepare(const unsigned long long *pass_cnt, const int32_t *k, const uint32_t *flag,
+                                   uint64_t *prefix, int32_t *krem, uint32_t *cnt, uint32_t *overflow, int B,
+                                   const uint32_t *any) {
+  if (*reinterpret_cast<const volatile uint32_t *>(any) == 0u) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B || flag[q] == 0u) return;
+  const unsigned long long P = pass_cnt[q];
+  prefix[q] = 0ull;
+  krem[q] = (int32_t)((unsigned long long)k[q] < P ? (unsigned long long)k[q] : P);
+  cnt[q] = 0u;
+  overflow[q] = 0u;
+}
+
+__global__ void k_fallback_finish(const uint64_t *prefix, const uint32_t *flag, uint64_t *tau, int B,
+                                  const uint32_t *any) {
+  if (*reinterpret_cast<const volatile uint32_t *>(any) == 0u) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B || flag[q] == 0u) return;
+  tau[q] = prefix[q];
+}
+
+}  // namespace
+
+cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(kSmemKeys + kMaxK) * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_select<<<B, kSelThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fallback_prepare(const unsigned long long *pass_cnt, const int32_t *k, const uint32_t *flag,
+                                    uint64_t *prefix, int32_t *krem, uint32_t *cnt, uint32_t *overflow,
+                                    uint32_t * /*hist*/, int B, const uint32_t *any, cudaStream_t s) {
+  k_fallback_prepare<<<(B + 127) / 128, 128, 0, s>>>(pass_cnt, k, flag, prefix, krem, cnt, overflow, B, any);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fallback_finish(const uint64_t *prefix, const uint32_t *flag, uint64_t *tau, int B,
+                                   const uint32_t *any, cudaStream_t s) {
+  k_fallback_finish<<<(B + 127) / 128, 128, 0, s>>>(prefix, flag, tau, B, any);
+  return cudaGetLastError();
+}
+
+}  // namespace lr

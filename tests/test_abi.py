@@ -1,0 +1,82 @@
+"""The C ABI library: builds, loads without a GPU, exports every declared entry point, and validates
+arguments before touching the device.  No compute call runs here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lr.h")
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2402_13435_b300 import build
+
+    return build.build()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(lr_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lr_index_create", "lr_index_destroy", "lr_search", "lr_search_ex", "lr_filter_count",
+                 "lr_index_sync", "lr_last_error_message", "lr_version", "lr_index_device_bytes"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    L = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_loads_and_reports_version(lib_path):
+    import paper_2402_13435_b300 as lr
+
+    assert lr.lr_version() == 100
+    assert set(lr.SYMBOLS) <= set(declared_functions())
+
+
+def test_invalid_arguments_fail_before_any_device_work(lib_path):
+    import paper_2402_13435_b300 as lr
+
+    emb = np.zeros((10, 4), dtype=np.float32)
+    with pytest.raises(lr.LRError) as e:  # neither bitsets nor postings
+        lr.lr_index_create(emb, 8)
+    assert e.value.status == lr.LR_ERR_INVALID
+    with pytest.raises(lr.LRError) as e:
+        lr.lr_index_create(emb, 8, bitsets=np.zeros((10, 1), dtype=np.uint64), max_k=5000)
+    assert e.value.status == lr.LR_ERR_INVALID
+    with pytest.raises(lr.LRError) as e:
+        lr.lr_index_create(np.zeros((10, 300), dtype=np.float32), 8, bitsets=np.zeros((10, 1), dtype=np.uint64))
+    assert e.value.status == lr.LR_ERR_UNSUPPORTED
+    assert "dim" in lr.lr_last_error_message()
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    import paper_2402_13435_b300 as lr
+
+    monkeypatch.setattr(lr, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        lr._load()
+
+
+def test_key_encoding_host_logic(tmp_path):
+    exe = tmp_path / "keys"
+    subprocess.check_call(["nvcc", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I",
+                           os.path.join(ROOT, "paper_2402_13435_b300", "csrc"),
+                           os.path.join(ROOT, "tests", "cpp", "keys_host_test.cu"), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and "OK" in r.stdout, r.stdout
