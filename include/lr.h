@@ -184,6 +184,41 @@ lr_status lr_search_ex(lr_index *index, const float *q, int32_t B, const lr_filt
                        const lr_search_opts *opts, const lr_search_stats *stats, void *stream);
 
 /*
+ * Allocation-free variant of lr_search.  The paper has no counterpart: it exists
+ * for callers that may not call cudaMalloc (a plugin whose host framework owns
+ * all device memory through its own pool, or a serving thread where an
+ * allocation could block or fail mid-request).  Such callers cannot build an
+ * lr_index, so the embeddings, queries, filters (as pass bitmaps) and outputs
+ * all come from the caller, and every intermediate lives in one fixed
+ * file-scope device array of about 10 MiB that each GPU loading the library
+ * keeps until the process exits.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ *
+ *   X            device [n_jobs][dim] FP32, dim in {32, 64, 128, 256}; the score
+ *                is the plain inner product (normalise beforehand for cosine).
+ *   n_jobs       1 .. 16,777,216.
+ *   q            device [B][dim] FP32, 1 <= B <= 8.
+ *   pass_bitmap  device, nullable (NULL = every job passes).  Row b starts at
+ *                pass_bitmap + b * bitmap_stride_words; bit j%32 of word j/32 is
+ *                set iff job j may be returned for query b.  The row stride must
+ *                be a multiple of 8 words and at least ceil(n_jobs/256)*8 words,
+ *                and the base 32-byte aligned (whole 256-job groups are read;
+ *                bits past n_jobs are ignored).
+ *   k            1 .. 1024; outputs are [B][k] (ids -1 / scores -inf past
+ *                out_count) and out_count [B] (nullable), device memory.
+ * Results equal lr_search's for the same data and the LR_DOT metric.
+ * Sizes beyond these limits return LR_ERR_WORKSPACE (LR_ERR_UNSUPPORTED for
+ * dim).  The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array and keep the last call's contents (each call clears
+ * what must start at zero), so calls that overlap on the GPU race: serialise
+ * them.  Returns after enqueueing the work on `stream`.
+ */
+lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t dim, const float *q, int32_t B,
+                            const uint32_t *pass_bitmap, int64_t bitmap_stride_words, int32_t k, int32_t *out_ids,
+                            float *out_scores, int32_t *out_count, void *stream);
+
+/*
  * Exact term filter only (F-TBR, Sec. 5.3 and appendix "TBR"): for each query the
  * number of passing jobs and, optionally, the pass bitmap.
  *   out_pass    [B] int64, host or device: number of jobs passing each filter.

@@ -299,3 +299,23 @@ def lr_filter_count(index: Index, filters, *, bitmap: bool = False, device=None,
     _check(_lib.lr_filter_count(ctypes.c_void_p(index.handle), ctypes.byref(fc), B, _ptr(out_pass), _ptr(bm),
                                 _stream_ptr(stream)), "lr_filter_count")
     return (out_pass, bm) if bitmap else out_pass
+
+
+_lib.lr_search_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+_lib.lr_search_noalloc.restype = ctypes.c_int
+
+
+def lr_search_noalloc(X, q, k: int, *, pass_bitmap=None, out_ids, out_scores, out_count=None, stream=None) -> None:
+    """Allocation-free top-K (see include/lr.h): every argument is a caller-owned CUDA tensor.
+
+    X [n][dim] and q [B][dim] FP32 with dim in {32, 64, 128, 256}; pass_bitmap [B][stride] int32 with
+    stride a multiple of 8 covering ceil(n/256)*8 words, or None; outputs [B][k] int32 / FP32 and [B]
+    int32.  Scores are plain inner products.  Nothing is allocated by the library or by this wrapper.
+    """
+    n, dim = int(X.shape[0]), int(X.shape[1])
+    B = int(q.shape[0])
+    stride = int(pass_bitmap.shape[1]) if pass_bitmap is not None else 0
+    _check(_lib.lr_search_noalloc(_ptr(X), n, dim, _ptr(q), B, _ptr(pass_bitmap), stride, int(k), _ptr(out_ids),
+                                  _ptr(out_scores), _ptr(out_count), _stream_ptr(stream)), "lr_search_noalloc")
