@@ -92,6 +92,7 @@ struct ScanArgs {
   int32_t *krem;                 // [B] rank still to find below the prefix
   uint32_t *hist;                // [B][kFbBins]
   uint32_t *done_ctr;            // grid-completion counter (last CTA applies the digit step)
+  uint32_t *work_ctr;            // dynamic work distribution (reset by the last CTA)
   int32_t hist_pass;             // 0 .. kFbPasses-1
   int32_t batch;                 // B (for the last-CTA step)
   uint32_t *err;                 // device error word

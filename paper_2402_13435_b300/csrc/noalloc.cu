@@ -42,7 +42,7 @@ constexpr size_t kOffNflag = kOffKrem + 4 * kNaMaxB;
 constexpr size_t kStateBytes = kOffNflag + 4;        // cleared by every call
 constexpr size_t kOffDone = al(kStateBytes);
 constexpr size_t kOffErr = kOffDone + 4;
-constexpr size_t kOffK = al(kOffErr + 4);
+constexpr size_t kOffK = al(kOffErr + 8);  // after the error word and the work counter
 constexpr size_t kOffRank = kOffK + 4 * kNaMaxB;
 constexpr size_t kOffSlots = al(kOffRank + 4 * kNaMaxB);
 constexpr size_t kOffQc = al(kOffSlots + 8 * kNaMaxB);
@@ -164,7 +164,7 @@ extern "C" lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t d
   } while (0)
 
   NA_CK(cudaMemsetAsync(base, 0, kStateBytes, s));
-  NA_CK(cudaMemsetAsync(done, 0, 8, s));  // completion counter and error word
+  NA_CK(cudaMemsetAsync(done, 0, 12, s));  // completion counter, error word, work counter
   NA_CK(cudaMemsetAsync(hist, 0, kHistBytes, s));
   k_noalloc_setup<<<1, 32, 0, s>>>(base, pass_bitmap, bitmap_stride_words, B, k, rank);
   NA_CK(cudaGetLastError());
@@ -187,12 +187,13 @@ extern "C" lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t d
   a.mode = kCollect;
   a.err = err;
   a.done_ctr = done;
+  a.work_ctr = done + 2;
   a.batch = B;
   const int vec = dim / 32;
   const int nqt = B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8;
   auto grid_for = [&](int64_t groups) {
-    int64_t want = (groups + 7) / 8;
-    int64_t cap = (int64_t)sms * 4;
+    int64_t want = (groups + 3) / 4;
+    int64_t cap = (int64_t)sms;
     return (int)(want < 1 ? 1 : (want < cap ? want : cap));
   };
 

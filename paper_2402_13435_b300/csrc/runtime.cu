@@ -114,7 +114,7 @@ struct lr_index {
   unsigned long long *pass = nullptr;
   uint32_t *cnt = nullptr, *ovf = nullptr, *scnt = nullptr, *sovf = nullptr, *flag = nullptr;
   int32_t *krem = nullptr, *kq = nullptr, *rank = nullptr;
-  uint32_t *n_flag = nullptr, *done_ctr = nullptr, *err = nullptr;
+  uint32_t *n_flag = nullptr, *done_ctr = nullptr, *work_ctr = nullptr, *err = nullptr;
   uint32_t *hist = nullptr;
   uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
   int32_t *o_ids = nullptr, *o_cnt = nullptr, *o_cand = nullptr, *o_fb = nullptr;
@@ -387,7 +387,7 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   const size_t o_krem = cv.take<int32_t>(B);
   const size_t o_nflag = cv.take<uint32_t>(1);
   const size_t o_state_end = cv.take<char>(0);
-  const size_t o_done = cv.take<uint32_t>(1);
+  const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
   const size_t o_err = cv.take<uint32_t>(1);
   const size_t o_kq = cv.take<int32_t>(B);
   const size_t o_rank = cv.take<int32_t>(B);
@@ -424,6 +424,7 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   ix->krem = (int32_t *)(w + o_krem);
   ix->n_flag = (uint32_t *)(w + o_nflag);
   ix->done_ctr = (uint32_t *)(w + o_done);
+  ix->work_ctr = ix->done_ctr + 1;
   ix->err = (uint32_t *)(w + o_err);
   ix->kq = (int32_t *)(w + o_kq);
   ix->rank = (int32_t *)(w + o_rank);
@@ -436,7 +437,7 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   ix->o_cand = (int32_t *)(w + o_ocand);
   ix->o_fb = (int32_t *)(w + o_ofb);
   ix->filt_d = w + o_filt;
-  CK2(cudaMemsetAsync(ix->done_ctr, 0, sizeof(uint32_t), s));
+  CK2(cudaMemsetAsync(ix->done_ctr, 0, 2 * sizeof(uint32_t), s));
   CK2(cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), s));
   CK2(cudaMemsetAsync(ix->hist, 0, (size_t)B * kFbBins * sizeof(uint32_t), s));
   for (int i = 0; i < 2; ++i) {
@@ -667,15 +668,15 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.mode = kCollect;
     a.err = ix->err;
     a.done_ctr = ix->done_ctr;
+    a.work_ctr = ix->work_ctr;
     a.batch = B;
     return a;
   };
   const int vec = ix->d_pad / 32;
   auto nq_tmpl = [](int nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : nq <= 4 ? 4 : 8; };
-  auto grid_for = [&](int64_t groups) {
-    const int64_t warps = (groups + 0);
-    const int64_t want = (warps + (kScanThreads / 32) - 1) / (kScanThreads / 32);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ix->num_sms * 4));
+  auto grid_for = [&](int64_t groups) {  // persistent: one CTA per SM, fewer for small scans
+    const int64_t want = (groups + 3) / 4;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ix->num_sms));
   };
 
   // 1. threshold sample

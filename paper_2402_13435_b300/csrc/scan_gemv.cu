@@ -1,70 +1,40 @@
-// SIMT scan for small query batches: fused term predicate (F-TBR) + FP32 scoring
+// Scan for small query batches: fused term predicate (F-TBR) + FP32 scoring
 // (F-EBR) + candidate gathering, one pass over the job embeddings.
 //
 // Sec. 5.3 ("F-TBR and F-EBR are integrated in the same program") and the
-// appendix paragraphs "TBR", "EBR" ("skip rows") and "Batch Inference" describe
-// the method; this kernel is a B300 design of it:
+// appendix paragraphs "TBR", "EBR" ("skip rows"), "Message Passing between
+// Layers" and "Batch Inference" describe the method; this kernel is a B300
+// design of it:
 //
-//   * The index is cut into groups of 256 rows.  A warp owns one group at a time.
-//     For each distinct term of the launch it loads the group's 8 bitmap words
-//     (32 contiguous bytes of a term-major bitmap) into shared memory, and lane q
-//     evaluates query q's CNF (AND over clauses of OR over terms) word-wise,
-//     giving 8 pass words per query.
-//   * Rows no query of the launch passes are never read from HBM ("skip rows").
-//   * A passing row is read once (lane L holds dims [L*VEC, L*VEC+VEC), 16-byte
-//     vector loads, one 512-byte coalesced request per row at d = 128), and its
-//     dot products with all NQ queries (held in registers) are reduced across
-//     the warp by a transpose butterfly: NQ-1 + 5-log2(NQ) shuffles for NQ sums.
-//     The butterfly visits lane pairs in the same order for every query, so a
-//     score does not depend on which other queries share the launch.
-//   * Candidate handling (mode kCollect): the 64-bit key (score, ~id) of each
-//     passing pair is compared with the query's threshold and appended to the
-//     query's buffer when it is not below it.  Mode kHist instead histograms one
-//     11-bit digit of the keys that match the query's prefix (exact radix
-//     selection); the last CTA to finish fixes the digit for every query.
+//   * The index is cut into 256-row groups handed out by a global work counter.
+//     For each distinct term of the launch the group's 8 bitmap words (32
+//     contiguous bytes of a term-major bitmap) are prefetched into shared
+//     memory, and lane q evaluates query q's CNF (AND over clauses of OR over
+//     terms) word-wise.
+//   * Rows nobody passes are never read from HBM ("skip rows").  Passing rows
+//     are compacted into 32-row batches (the messenger: job id + mask of the
+//     queries that pass it) and fetched asynchronously.
+//   * Lane i scores row i of a batch against every query of the launch: a
+//     sequential FP32 FMA chain over the dimensions, row data from shared
+//     memory (rows sit 16 bytes apart beyond their length, so the 32 lanes'
+//     16-byte loads hit distinct banks) and query values broadcast from shared
+//     memory.  A score is therefore computed the same way whatever other
+//     queries share the launch.
+//   * Candidates (mode kCollect): the 64-bit key (score, ~id) of each passing
+//     pair is compared with the query's threshold and appended to the query's
+//     buffer when it is not below it.  Mode kHist instead histograms one 11-bit
+//     digit of the keys that match the query's prefix (exact radix selection);
+//     the last CTA to finish fixes the digit for every query.
+//
+// Every mbarrier wait is bounded (ptx.h); a wait that gives up records
+// LR_ERR_TIMEOUT in the error word.
 #include "lr_internal.h"
+#include "ptx.h"
 
 namespace lr {
 namespace {
 
-__device__ __forceinline__ uint4 ld_nc_v4(const void *p) {
-  uint4 r;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "l"(p));
-  return r;
-}
-
-__device__ __forceinline__ float4 ld_stream_f4(const float *p) {
-  float4 r;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-               : "l"(p));
-  return r;
-}
-
-__device__ __forceinline__ float2 ld_stream_f2(const float *p) {
-  float2 r;
-  asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
-  return r;
-}
-
-template <int VEC>
-__device__ __forceinline__ void load_row(const float *p, float (&x)[VEC]) {
-  if constexpr (VEC % 4 == 0) {
-#pragma unroll
-    for (int v = 0; v < VEC; v += 4) {
-      float4 t = ld_stream_f4(p + v);
-      x[v] = t.x; x[v + 1] = t.y; x[v + 2] = t.z; x[v + 3] = t.w;
-    }
-  } else if constexpr (VEC == 2) {
-    float2 t = ld_stream_f2(p);
-    x[0] = t.x; x[1] = t.y;
-  } else {
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) x[v] = __ldcs(p + v);
-  }
-}
+constexpr int kChunkGroups = 2;  // groups handed out per work-counter grab
 
 // CNF of launch-local query q over the current group's words (sw: [slot][8]).
 __device__ __forceinline__ void eval_cnf(const ScanArgs &a, int q, const uint32_t *sw, uint32_t (&pw)[8]) {
@@ -84,70 +54,6 @@ __device__ __forceinline__ void eval_cnf(const ScanArgs &a, int q, const uint32_
     }
 #pragma unroll
     for (int w = 0; w < 8; ++w) pw[w] &= cw[w];
-  }
-}
-
-template <int NQ>
-struct Log2 { static constexpr int v = (NQ <= 1) ? 0 : 1 + Log2<NQ / 2>::v; };
-template <>
-struct Log2<1> { static constexpr int v = 0; };
-
-// Per-row work: NQ dot products, butterfly, owner lanes test and record.
-template <int VEC, int NQ>
-__device__ __forceinline__ void score_row(const ScanArgs &a, const float (&x)[VEC], const float (&qv)[NQ][VEC],
-                                          uint32_t my_pw, int bit, uint32_t row, uint64_t my_tau,
-                                          uint64_t my_pre, int lane, int top, int shift, uint32_t dmask) {
-  constexpr int M = Log2<NQ>::v;
-  float p[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    float acc = x[0] * qv[q][0];
-#pragma unroll
-    for (int v = 1; v < VEC; ++v) acc = fmaf(x[v], qv[q][v], acc);
-    p[q] = acc;
-  }
-  // transpose stages: offsets 16, 8, ... keep half of the values each time
-#pragma unroll
-  for (int st = 0; st < M; ++st) {
-    const int off = 16 >> st;
-    const int half = NQ >> (st + 1);
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float send = up ? p[i] : p[i + half];
-      const float keep = up ? p[i + half] : p[i];
-      p[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, off);
-    }
-  }
-  float z = p[0];
-#pragma unroll
-  for (int off = (16 >> M); off >= 1; off >>= 1) z += __shfl_xor_sync(0xFFFFFFFFu, z, off);
-
-  const int qidx = (lane >> (5 - M)) & (NQ - 1);
-  const uint32_t pwq = __shfl_sync(0xFFFFFFFFu, my_pw, qidx);
-  const bool owner = (lane & ((1 << (5 - M)) - 1)) == 0;
-  if (a.mode == kCollect) {
-    const uint64_t tq = __shfl_sync(0xFFFFFFFFu, my_tau, qidx);
-    if (owner && ((pwq >> bit) & 1u)) {
-      const uint64_t key = make_key(z, row);
-      if (key >= tq) {
-        const int gq = a.q_base + qidx;
-        const uint32_t pos = atomicAdd(&a.buf_cnt[gq], 1u);
-        if ((int64_t)pos < a.buf_cap)
-          a.buf[(size_t)gq * (size_t)a.buf_cap + pos] = key;
-        else
-          atomicOr(&a.overflow[gq], 1u);
-      }
-    }
-  } else {
-    const uint64_t pq = __shfl_sync(0xFFFFFFFFu, my_pre, qidx);
-    if (owner && ((pwq >> bit) & 1u)) {
-      const uint64_t key = make_key(z, row);
-      if (top >= 64 || (key >> top) == (pq >> top)) {
-        const int gq = a.q_base + qidx;
-        atomicAdd(&a.hist[(size_t)gq * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
-      }
-    }
   }
 }
 
@@ -196,124 +102,278 @@ __device__ void hist_step(const ScanArgs &a, int top, int shift) {
   }
 }
 
-template <int VEC, int NQ>
-__global__ void __launch_bounds__(kScanThreads) k_scan_gemv(const ScanArgs a) {
+// Per-warp pipeline (every warp of the CTA runs one independently):
+//   * take 256-row groups from the global work counter (chunks of kChunkGroups);
+//   * term words of the next group are prefetched with cp.async while the
+//     current group is processed (one commit group per prefetch);
+//   * lane q evaluates query q's CNF over the group's 8 words;
+//   * passing rows are packed into 32-row batches -- the paper's messenger: a
+//     slot holds the job id and the bit mask of the queries that pass it -- and
+//     each row is fetched by one warp-wide cp.async (16 bytes per lane, one
+//     coalesced request per row) into a padded shared-memory slot;
+//   * completion of a batch's copies is counted on the batch buffer's mbarrier
+//     (cp.async.mbarrier.arrive.noinc from every lane), and the previous batch is
+//     scored while the current one is in flight (double buffering).
+struct WarpLayout {
+  size_t row_stride, buf_bytes, per_warp, bars, meta, slots, rows, queries, total;
+};
+
+__host__ __device__ inline size_t w_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline WarpLayout warp_layout(int d_pad, int nq_tmpl, int n_slots, int warps) {
+  WarpLayout L;
+  L.row_stride = (size_t)d_pad * 4 + 16;  // +16 bytes: the 32 lanes' 16-byte loads hit distinct banks
+  L.buf_bytes = 32 * L.row_stride;
+  // per-warp region: 2 barriers | meta (row, qmask) x 2 buffers | 2 term tables | 2 row buffers
+  L.bars = 0;
+  L.meta = 16;
+  L.slots = w_align(L.meta + 2 * 32 * 8, 16);
+  L.rows = w_align(L.slots + (size_t)2 * (n_slots > 0 ? n_slots : 1) * 32, 16);
+  L.per_warp = w_align(L.rows + 2 * L.buf_bytes, 128);
+  L.queries = (size_t)warps * L.per_warp;
+  L.total = L.queries + (size_t)nq_tmpl * d_pad * 4;
+  return L;
+}
+
+template <int DP, int NQ>
+__device__ __forceinline__ void score_batch(const ScanArgs &a, const unsigned char *buf, const uint32_t *meta_row,
+                                            const uint32_t *meta_qm, uint32_t n, const float *qs,
+                                            const uint64_t (&tq)[NQ], int lane, int top, int shift,
+                                            uint32_t dmask, size_t row_stride) {
+  if ((uint32_t)lane >= n) return;
+  const uint32_t row = meta_row[lane];
+  const uint32_t qm = meta_qm[lane];
+  const float *xr = reinterpret_cast<const float *>(buf + (size_t)lane * row_stride);
+  float acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < DP; k += 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(xr + k);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float4 v = *reinterpret_cast<const float4 *>(qs + q * DP + k);
+      acc[q] = fmaf(x.x, v.x, acc[q]);
+      acc[q] = fmaf(x.y, v.y, acc[q]);
+      acc[q] = fmaf(x.z, v.z, acc[q]);
+      acc[q] = fmaf(x.w, v.w, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (!((qm >> q) & 1u)) continue;
+    const uint64_t key = make_key(acc[q], row);
+    const int g2 = a.q_base + q;
+    if (a.mode == kCollect) {
+      if (key >= tq[q]) {
+        const uint32_t p = atomicAdd(&a.buf_cnt[g2], 1u);
+        if ((int64_t)p < a.buf_cap)
+          a.buf[(size_t)g2 * (size_t)a.buf_cap + p] = key;
+        else
+          atomicOr(&a.overflow[g2], 1u);
+      }
+    } else if (top >= 64 || (key >> top) == (tq[q] >> top)) {
+      atomicAdd(&a.hist[(size_t)g2 * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
+    }
+  }
+}
+
+template <int DP, int NQ>
+__global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
-  extern __shared__ __align__(16) uint32_t smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int kChunks = DP / 4;  // 16-byte chunks per row
+  const int warps = blockDim.x >> 5;
+  const WarpLayout L = warp_layout(DP, NQ, a.n_slots, warps);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int wpc = blockDim.x >> 5;
-  uint32_t *sw = smem + (size_t)warp * (size_t)a.n_slots * 8;
+  unsigned char *wbase = smem + (size_t)warp * L.per_warp;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + L.bars);
+  uint32_t *meta = reinterpret_cast<uint32_t *>(wbase + L.meta);  // [buf][row 32 | qmask 32]
+  uint32_t *slot_tab = reinterpret_cast<uint32_t *>(wbase + L.slots);
+  unsigned char *rows = wbase + L.rows;
+  float *qs = reinterpret_cast<float *>(smem + L.queries);
+  __shared__ bool s_last;
 
-  const int gq = a.q_base + lane;
-  const bool qlive = lane < a.nq && (a.active == nullptr || a.active[gq] != 0u);
-  uint64_t my_tau = 0, my_pre = 0;
-  if (qlive) {
-    if (a.mode == kCollect) my_tau = a.tau ? a.tau[gq] : 0ull;
-    else my_pre = a.prefix[gq];
+  for (int i = threadIdx.x; i < NQ * DP; i += blockDim.x) {
+    const int q = i / DP;
+    qs[i] = q < a.nq ? a.Q[(size_t)(a.q_base + q) * DP + (i % DP)] : 0.f;
   }
+  if (lane == 0) {
+    mbar_init(&bar[0], 32);
+    mbar_init(&bar[1], 32);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
   const int top = 64 - kFbBits * a.hist_pass;
   const int shift = top - kFbBits > 0 ? top - kFbBits : 0;
   const uint32_t dmask = (1u << (top - shift)) - 1u;
+  const int gq = a.q_base + lane;
+  const bool qlive = lane < a.nq && (a.active == nullptr || a.active[gq] != 0u);
+  uint64_t tq[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int g2 = a.q_base + q;
+    const bool live = q < a.nq && (a.active == nullptr || a.active[g2] != 0u);
+    tq[q] = !live ? 0ull : (a.mode == kCollect ? (a.tau ? a.tau[g2] : 0ull) : a.prefix[g2]);
+  }
 
-  float qv[NQ][VEC];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q)
-#pragma unroll
-    for (int v = 0; v < VEC; ++v)
-      qv[q][v] = (q < a.nq) ? a.Q[(size_t)(a.q_base + q) * (size_t)a.d_pad + (size_t)lane * VEC + v] : 0.f;
+  const int64_t n_items = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
+  int64_t item = 0, item_end = 0;
+  auto next_group = [&]() -> int64_t {
+    if (item + 1 < item_end) return a.g_begin + (++item) * a.g_step;
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(a.work_ctr, 1u);
+    c = __shfl_sync(0xFFFFFFFFu, c, 0);
+    item = (int64_t)c * kChunkGroups;
+    item_end = item + kChunkGroups < n_items ? item + kChunkGroups : n_items;
+    return item < n_items ? a.g_begin + item * a.g_step : -1;
+  };
+  auto prefetch = [&](int64_t g, int t) {
+    uint32_t *dst = slot_tab + (size_t)t * a.n_slots * 8;
+    for (int i = lane; i < 2 * a.n_slots; i += 32) {
+      const int s = i >> 1, h = i & 1;
+      cp_async16(dst + s * 8 + h * 4, a.slot_bm[s] + g * kGroupWords + h * 4);
+    }
+    cp_async_commit();
+  };
 
   unsigned long long my_pass = 0;
-  const int64_t gw = (int64_t)blockIdx.x * wpc + warp;
-  const int64_t nw = (int64_t)gridDim.x * wpc;
-  for (int64_t it = gw;; it += nw) {
-    const int64_t g = a.g_begin + it * a.g_step;
-    if (g >= a.n_groups) break;
-    for (int s = lane; s < a.n_slots; s += 32) {
-      const uint32_t *src = a.slot_bm[s] + g * kGroupWords;
-      const uint4 w0 = ld_nc_v4(src), w1 = ld_nc_v4(src + 4);
-      uint4 *dst = reinterpret_cast<uint4 *>(sw + s * 8);
-      dst[0] = w0;
-      dst[1] = w1;
+  bool ok = true;
+  int fb = 0;          // buffer being filled
+  uint32_t fill = 0;   // rows placed in it
+  bool prev = false;   // a closed batch waits in buffer fb ^ 1
+  uint32_t prev_n = 0;
+  uint32_t phase[2] = {0u, 0u};
+  auto close_and_score_prev = [&]() {
+    // hand the filled buffer's copies to its barrier, then score the previous batch
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[fb])) : "memory");
+    if (prev) {
+      const int pb = fb ^ 1;
+      if (!mbar_wait(&bar[pb], phase[pb])) ok = false;
+      phase[pb] ^= 1u;
+      __syncwarp();
+      score_batch<DP, NQ>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs, tq,
+                          lane, top, shift, dmask, L.row_stride);
+      __syncwarp();
     }
+    prev = true;
+    prev_n = fill;
+    fb ^= 1;
+    fill = 0;
+  };
+
+  int t = 0;
+  int64_t g = next_group();
+  if (g >= 0) prefetch(g, 0);
+  int64_t gn = g >= 0 ? next_group() : -1;
+  if (gn >= 0) prefetch(gn, 1);
+  else cp_async_commit();
+  while (g >= 0 && ok) {
+    cp_async_wait_group<1>();  // term words of g have landed
     __syncwarp();
     uint32_t pw[8];
     if (qlive) {
-      eval_cnf(a, lane, sw, pw);
+      eval_cnf(a, lane, slot_tab + (size_t)t * a.n_slots * 8, pw);
     } else {
 #pragma unroll
       for (int w = 0; w < 8; ++w) pw[w] = 0u;
     }
+    __syncwarp();
+    const int64_t gnn = gn >= 0 ? next_group() : -1;
+    if (gnn >= 0) prefetch(gnn, t);  // the table of g is free again
+    else cp_async_commit();
     const int64_t r0 = g * kGroupRows;
-#pragma unroll
+#pragma unroll 1
     for (int w = 0; w < 8; ++w) {
       const int64_t left = a.n - (r0 + w * 32);
-      const uint32_t valid = left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u);
-      pw[w] &= valid;
-      my_pass += (unsigned long long)__popc(pw[w]);
-    }
-    __syncwarp();
+      uint32_t p = pw[w] & (left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u));
+      my_pass += (unsigned long long)__popc(p);
+      const uint32_t U = __reduce_or_sync(0xFFFFFFFFu, p);
+      if (U == 0u) continue;
+      uint32_t qm = 0;  // lane r: mask of the queries that pass row r of the word
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      uint32_t u = __reduce_or_sync(0xFFFFFFFFu, pw[w]);
-      while (u != 0u) {
-        int rb[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          rb[r] = -1;
-          if (u != 0u) { rb[r] = __ffs(u) - 1; u &= u - 1u; }
+      for (int q = 0; q < NQ; ++q) qm |= ((__shfl_sync(0xFFFFFFFFu, p, q) >> lane) & 1u) << q;
+      const uint32_t n = __popc(U);
+      const uint32_t rank = __popc(U & ((1u << lane) - 1u));
+      const int64_t wrow = r0 + w * 32;
+      uint32_t done = 0;
+      while (done < n) {
+        const uint32_t take = (32u - fill) < (n - done) ? (32u - fill) : (n - done);
+        uint32_t *mrow = meta + fb * 64;
+        if (((U >> lane) & 1u) && rank >= done && rank < done + take) {
+          mrow[fill + rank - done] = (uint32_t)(wrow + lane);
+          mrow[32 + fill + rank - done] = qm;
         }
-        float xv[4][VEC];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (rb[r] >= 0)
-            load_row<VEC>(a.X + (size_t)(r0 + w * 32 + rb[r]) * (size_t)a.d_pad + (size_t)lane * VEC, xv[r]);
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (rb[r] >= 0)
-            score_row<VEC, NQ>(a, xv[r], qv, pw[w], rb[r], (uint32_t)(r0 + w * 32 + rb[r]), my_tau, my_pre, lane,
-                               top, shift, dmask);
+        __syncwarp();  // the slots' job ids are visible to every lane
+        unsigned char *dst = rows + (size_t)fb * L.buf_bytes;
+        for (uint32_t i = lane; i < take * kChunks; i += 32) {
+          const uint32_t k = i / kChunks, c = i % kChunks;
+          cp_async16(dst + (size_t)(fill + k) * L.row_stride + c * 16, a.X + (size_t)mrow[fill + k] * DP + c * 4);
+        }
+        fill += take;
+        done += take;
+        if (fill == 32u) close_and_score_prev();
       }
     }
+    g = gn;
+    gn = gnn;
+    t ^= 1;
   }
+  // drain: close the partial batch, score what remains
+  if (fill > 0u) close_and_score_prev();
+  if (prev) {
+    const int pb = fb ^ 1;
+    if (!mbar_wait(&bar[pb], phase[pb])) ok = false;
+    __syncwarp();
+    score_batch<DP, NQ>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs, tq, lane,
+                        top, shift, dmask, L.row_stride);
+  }
+  cp_async_wait_all();
+  if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
   if (qlive && a.pass_cnt != nullptr) atomicAdd(&a.pass_cnt[gq], my_pass);
 
-  if (a.mode == kHist) {
-    __shared__ bool s_last;
+  // grid completion: the last CTA resets the work counter and, in kHist mode,
+  // fixes this pass's digit for every participating query
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(a.done_ctr, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (a.mode == kHist) hist_step(a, top, shift);
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
-      s_last = atomicAdd(a.done_ctr, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      hist_step(a, top, shift);
-      __syncthreads();
-      if (threadIdx.x == 0) *a.done_ctr = 0u;
+      *a.work_ctr = 0u;
+      *a.done_ctr = 0u;
     }
   }
 }
 
-template <int VEC, int NQ>
+template <int DP, int NQ>
 cudaError_t launch_one(const ScanArgs &a, int grid, cudaStream_t s) {
-  const size_t smem = (size_t)(kScanThreads / 32) * (size_t)a.n_slots * 8 * sizeof(uint32_t);
-  auto *fn = k_scan_gemv<VEC, NQ>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  fn<<<grid, kScanThreads, smem, s>>>(a);
+  const size_t budget = 220u * 1024u;
+  int warps = 8;
+  while (warps > 1 && warp_layout(DP, NQ, a.n_slots, warps).total > budget) --warps;
+  const WarpLayout L = warp_layout(DP, NQ, a.n_slots, warps);
+  if (L.total > budget) return cudaErrorInvalidValue;
+  auto *fn = k_scan_gemv<DP, NQ>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, warps * 32, L.total, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int VEC>
+template <int DP>
 cudaError_t dispatch_nq(const ScanArgs &a, int nq_tmpl, int grid, cudaStream_t s) {
   switch (nq_tmpl) {
-    case 1: return launch_one<VEC, 1>(a, grid, s);
-    case 2: return launch_one<VEC, 2>(a, grid, s);
-    case 4: return launch_one<VEC, 4>(a, grid, s);
-    case 8: return launch_one<VEC, 8>(a, grid, s);
+    case 1: return launch_one<DP, 1>(a, grid, s);
+    case 2: return launch_one<DP, 2>(a, grid, s);
+    case 4: return launch_one<DP, 4>(a, grid, s);
+    case 8: return launch_one<DP, 8>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -322,11 +382,10 @@ cudaError_t dispatch_nq(const ScanArgs &a, int nq_tmpl, int grid, cudaStream_t s
 
 cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s) {
   switch (vec) {
-    case 1: return dispatch_nq<1>(a, nq_tmpl, grid, s);
-    case 2: return dispatch_nq<2>(a, nq_tmpl, grid, s);
-    case 4: return dispatch_nq<4>(a, nq_tmpl, grid, s);
-    case 8: return dispatch_nq<8>(a, nq_tmpl, grid, s);
-    case 16: return dispatch_nq<16>(a, nq_tmpl, grid, s);
+    case 1: return dispatch_nq<32>(a, nq_tmpl, grid, s);
+    case 2: return dispatch_nq<64>(a, nq_tmpl, grid, s);
+    case 4: return dispatch_nq<128>(a, nq_tmpl, grid, s);
+    case 8: return dispatch_nq<256>(a, nq_tmpl, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
