@@ -17,7 +17,9 @@ constexpr int kGroupWords = 8;
 constexpr int kMaxK = 4096;         // largest K (bitonic sort of the survivors in shared memory)
 constexpr int kMaxDim = 512;
 constexpr int kGemvMaxQ = 8;        // queries per GEMV launch (held in registers)
-constexpr int kGemvMaxSlots = 256;  // distinct terms per GEMV launch (shared-memory word table)
+constexpr int kGemvMaxSlots = 256;  // distinct terms per scan launch (shared-memory word table)
+constexpr int kTcMaxQ = 64;         // queries per tensor-core launch (MMA N <= 64)
+constexpr int kTcMinBatch = 16;     // batches from this size use the tensor-core plan by default
 constexpr int kFbBits = 11;         // radix digit of the exact fallback selection
 constexpr int kFbBins = 1 << kFbBits;
 constexpr int kFbPasses = 6;        // 5 x 11 + 9 = 64 key bits
@@ -127,6 +129,7 @@ struct SelectArgs {
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s);
+cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
 cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,
                                 uint32_t *err, cudaStream_t s);

@@ -1,6 +1,8 @@
 // Host runtime of the filtered top-K library: index construction with a
 // workspace sized once (appendix "Memory Pre-Allocation"), the per-batch filter
 // compiler, the launch plan of a search and the C ABI entry points.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -132,6 +134,9 @@ struct lr_index {
   std::vector<int32_t> sparse_stamp, sparse_id, local_stamp, local_id;
   int32_t gen = 0;
   size_t device_bytes = 0;
+  // TMA descriptor of X for the tensor-core plan (128 rows x 32 floats, 128-byte swizzle)
+  alignas(64) CUtensorMap tmap_x;
+  bool have_tmap = false;
 };
 
 namespace {
@@ -164,6 +169,35 @@ lr_status check_err_word(lr_index *ix, cudaStream_t s, const char *where) {
     return fail((e & 2u) ? LR_ERR_CUDA : LR_ERR_INVALID, m);
   }
   return LR_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to
+// the driver library is needed).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool make_x_tensor_map(lr_index *ix) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ix->n >= (int64_t(1) << 31)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ix->d_pad, (cuuint64_t)ix->n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ix->d_pad * sizeof(float)};
+  const cuuint32_t box[2] = {32u, 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(&ix->tmap_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ix->X, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Threshold-sample geometry for a given stride: number of sampled groups and
@@ -456,6 +490,7 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   cudaFree(err_tmp);
   if (e & 1u) return cleanup(fail(LR_ERR_INVALID, "non-finite value in the job embeddings"));
   if (e & 4u) return cleanup(fail(LR_ERR_INVALID, "posting list names a job id >= n_jobs"));
+  ix->have_tmap = make_x_tensor_map(ix);
   *out = ix;
   return LR_OK;
 #undef CK2
@@ -599,7 +634,6 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (k_all > ix->max_k && k == nullptr) return fail(LR_ERR_INVALID, "K exceeds max_k");
   lr_search_opts o{};
   if (opts) o = *opts;
-  if (o.plan == LR_PLAN_TC) return fail(LR_ERR_UNSUPPORTED, "tensor-core plan not available in this build");
 
   // pick and wait for a staging buffer
   const int turn = ix->filt_turn;
@@ -607,7 +641,14 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (ix->filt_ev_live[turn]) LR_CK(cudaEventSynchronize(ix->filt_ev[turn]));
   char *stage = ix->filt_h[turn];
   Compiled C;
-  lr_status st = compile_filters(ix, f, B, kGemvMaxQ, stage, C);
+  // scoring plan: SIMT matrix-vector scan for small batches, tensor-core tiles
+  // (3xTF32) once a launch serves enough queries to be a real contraction
+  int plan = o.plan;
+  if (plan == LR_PLAN_AUTO) plan = B >= kTcMinBatch ? LR_PLAN_TC : LR_PLAN_GEMV;
+  if (plan == LR_PLAN_TC && !ix->have_tmap)
+    return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable (no TMA descriptor for this index)");
+  const int max_q = plan == LR_PLAN_TC ? (ix->d_pad <= 128 ? kTcMaxQ : kTcMaxQ / 2) : kGemvMaxQ;
+  lr_status st = compile_filters(ix, f, B, max_q, stage, C);
   if (st != LR_OK) return st;
   int32_t *ks = (int32_t *)(stage + C.off_k);
   for (int b = 0; b < B; ++b) {
@@ -675,8 +716,12 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   const int vec = ix->d_pad / 32;
   auto nq_tmpl = [](int nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : nq <= 4 ? 4 : 8; };
   auto grid_for = [&](int64_t groups) {  // persistent: one CTA per SM, fewer for small scans
-    const int64_t want = (groups + 3) / 4;
+    const int64_t want = plan == LR_PLAN_TC ? groups : (groups + 3) / 4;
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ix->num_sms));
+  };
+  auto launch_scan = [&](const ScanArgs &a, int64_t groups) {
+    return plan == LR_PLAN_TC ? launch_scan_tc(a, &ix->tmap_x, grid_for(groups), s)
+                              : launch_scan_gemv(a, nq_tmpl(a.nq), vec, grid_for(groups), s);
   };
 
   // 1. threshold sample
@@ -690,7 +735,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       a.buf_cap = ix->samp_cap;
       a.buf_cnt = ix->scnt;
       a.overflow = ix->sovf;
-      LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(sp.sampled_groups), s));
+      LR_LAUNCH(launch_scan(a, sp.sampled_groups));
     }
     SelectArgs t{};
     t.mode = 0;
@@ -712,7 +757,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.buf_cnt = ix->cnt;
     a.overflow = ix->ovf;
     a.pass_cnt = ix->pass;
-    LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(ix->n_groups), s));
+    LR_LAUNCH(launch_scan(a, ix->n_groups));
     ++n_scan;
   }
   if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
@@ -754,7 +799,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       a.hist = ix->hist;
       a.active = ix->flag;
       a.any_active = ix->n_flag;
-      LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(ix->n_groups), s));
+      LR_LAUNCH(launch_scan(a, ix->n_groups));
     }
   }
   LR_LAUNCH(launch_fallback_finish(ix->prefix, ix->flag, ix->tau, B, ix->n_flag, s));
@@ -767,7 +812,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.overflow = ix->ovf;
     a.active = ix->flag;
     a.any_active = ix->n_flag;
-    LR_LAUNCH(launch_scan_gemv(a, nq_tmpl(sb.nq), vec, grid_for(ix->n_groups), s));
+    LR_LAUNCH(launch_scan(a, ix->n_groups));
   }
   SelectArgs fb = fa;
   fb.cap = ix->cand_cap;

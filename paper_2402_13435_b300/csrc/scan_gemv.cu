@@ -30,77 +30,12 @@
 // LR_ERR_TIMEOUT in the error word.
 #include "lr_internal.h"
 #include "ptx.h"
+#include "scan_common.cuh"
 
 namespace lr {
 namespace {
 
 constexpr int kChunkGroups = 2;  // groups handed out per work-counter grab
-
-// CNF of launch-local query q over the current group's words (sw: [slot][8]).
-__device__ __forceinline__ void eval_cnf(const ScanArgs &a, int q, const uint32_t *sw, uint32_t (&pw)[8]) {
-#pragma unroll
-  for (int w = 0; w < 8; ++w) pw[w] = 0xFFFFFFFFu;
-  const int c0 = a.qc_off[q], c1 = a.qc_off[q + 1];
-  for (int c = c0; c < c1; ++c) {
-    uint32_t cw[8];
-#pragma unroll
-    for (int w = 0; w < 8; ++w) cw[w] = 0u;
-    const int t0 = a.cl_off[c], t1 = a.cl_off[c + 1];
-    for (int t = t0; t < t1; ++t) {
-      const uint4 *s = reinterpret_cast<const uint4 *>(sw + a.cl_slot[t] * 8);
-      const uint4 lo = s[0], hi = s[1];
-      cw[0] |= lo.x; cw[1] |= lo.y; cw[2] |= lo.z; cw[3] |= lo.w;
-      cw[4] |= hi.x; cw[5] |= hi.y; cw[6] |= hi.z; cw[7] |= hi.w;
-    }
-#pragma unroll
-    for (int w = 0; w < 8; ++w) pw[w] &= cw[w];
-  }
-}
-
-// Digit step of the exact fallback: for every participating query find the
-// digit whose bin holds the krem-th largest key, fix it in the prefix and clear
-// the histogram.  Runs in the last CTA of a kHist launch.
-__device__ void hist_step(const ScanArgs &a, int top, int shift) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  const int nb = 1 << (top - shift);
-  const int per = nb / 32;
-  for (int q = warp; q < a.nq; q += wpc) {
-    const int gq = a.q_base + q;
-    if (a.active && a.active[gq] == 0) continue;
-    uint32_t *h = a.hist + (size_t)gq * kFbBins;
-    const uint32_t krem = (uint32_t)a.krem[gq];
-    if (krem == 0u) {  // nothing passes this filter: no rank to find
-      for (int i = lane; i < nb; i += 32) h[i] = 0u;
-      continue;
-    }
-    const int hi_bin = nb - 1 - lane * per;  // this lane's chunk: [hi_bin-per+1, hi_bin]
-    uint32_t csum = 0;
-    for (int i = 0; i < per; ++i) csum += __ldcg(h + hi_bin - i);
-    uint32_t incl = csum;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-      if (lane >= off) incl += t;
-    }
-    const uint32_t excl = incl - csum;
-    const unsigned hit = __ballot_sync(0xFFFFFFFFu, excl < krem && krem <= incl);
-    if (hit == 0u) {
-      if (lane == 0) atomicOr(a.err, 2u);  // rank beyond the histogram total: inconsistent state
-    } else if (lane == __ffs(hit) - 1) {
-      uint32_t cum = excl;
-      int digit = hi_bin;
-      for (int i = 0; i < per; ++i) {
-        const uint32_t c = __ldcg(h + hi_bin - i);
-        if (cum + c >= krem) { digit = hi_bin - i; break; }
-        cum += c;
-      }
-      a.prefix[gq] |= (uint64_t)digit << shift;
-      a.krem[gq] = (int32_t)(krem - cum);
-    }
-    __syncwarp();
-    for (int i = lane; i < nb; i += 32) h[i] = 0u;
-  }
-}
 
 // Per-warp pipeline (every warp of the CTA runs one independently):
 //   * take 256-row groups from the global work counter (chunks of kChunkGroups);

@@ -1,0 +1,96 @@
+"""Parity of the tensor-core (tcgen05, 3xTF32) scan plan with the CPU oracle (needs a GPU)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from datagen import Filters
+from oracle.compare import check_topk
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_13435_b300 as m
+
+    return m
+
+
+def _run(lr, idx, Q, f, K, **kw):
+    ids, sc, cnt = lr.lr_search(idx, torch.from_numpy(Q).cuda(), f, K, **kw)
+    torch.cuda.synchronize()
+    lr.lr_index_sync(idx)
+    return ids.cpu().numpy(), sc.cpu().numpy(), cnt.cpu().numpy()
+
+
+def test_tc_dyadic_scores_are_bit_exact():
+    import paper_2402_13435_b300 as lr
+
+    rng = np.random.default_rng(8)
+    n, d, V, B, K = 3_000, 64, 32, 20, 200
+    X = (rng.integers(-2, 3, size=(n, d)) / 4.0).astype(np.float32)  # exact in TF32: x_lo = 0
+    Q = (rng.integers(-2, 3, size=(B, d)) / 4.0).astype(np.float32)
+    off, terms = datagen.job_terms(4, n, V, 5.0, 1.1)
+    f = datagen.filters(4, B, V, 1.1, cmax=2)
+    idx = lr.lr_index_create(X, V, bitsets=datagen.bitsets(n, V, off, terms), metric="dot", max_batch=32, max_k=256)
+    ids, sc, cnt = _run(lr, idx, Q, f, K, plan="tc")
+    ref = oracle.search(X, off, terms, Q, f, K, metric="dot")
+    assert np.array_equal(cnt, ref.count)
+    for b in range(B):
+        c = cnt[b]
+        assert np.array_equal(ids[b, :c], ref.ids[b, :c])
+        assert np.array_equal(sc[b, :c].astype(np.float64), ref.scores[b, :c])
+
+
+@pytest.mark.parametrize("d", [64, 128])
+@pytest.mark.parametrize("B", [1, 16, 40, 64, 70])
+def test_tc_plan_matches_oracle(lr, d, B):
+    n, V, K = 41_003, 1024, 60
+    c = datagen.corpus(31 + d, n, d, V, 14.0, 1.1)
+    f = datagen.filters(200 + B, B, V, 1.1)
+    qs = [f.clauses(b) for b in range(B)]
+    if B > 3:
+        qs[0] = []
+        qs[2] = qs[2] + [[0, 1]]
+    f = Filters.from_lists(qs)
+    Q = datagen.query_embeddings(200 + B, B, d)
+    po, pid = c.postings()
+    idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), V, post_off=po, post_ids=pid, n_dense_terms=40,
+                             metric="cosine", max_batch=80, max_k=64)
+    ids, sc, cnt = _run(lr, idx, Q, f, K, plan="tc")
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
+
+
+def test_tc_sample_overflow_fallback_give_identical_rows(lr):
+    n, d, V, B, K = 60_000, 128, 512, 24, 50
+    c = datagen.corpus(5, n, d, V, 12.0, 1.1)
+    f = datagen.filters(5, B, V, 1.1)
+    Q = datagen.query_embeddings(5, B, d)
+    idx = lr.lr_index_create(c.X, V, bitsets=c.bitsets(), metric="cosine", max_batch=32, max_k=64)
+    base = _run(lr, idx, Q, f, K, plan="tc", sample_stride=-1)
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    check_topk(*base, ref, c.X, Q, c.job_off, c.job_terms, f)
+    for kw in (dict(sample_stride=2), dict(cand_cap=55), dict(force_exact_fallback=True),
+               dict(sample_stride=3, cand_cap=64)):
+        got = _run(lr, idx, Q, f, K, plan="tc", **kw)
+        assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1]), kw
+    # the GEMV plan agrees with the oracle on the same queries (scores may differ in the last bits)
+    gv = _run(lr, idx, Q, f, K, plan="gemv")
+    check_topk(*gv, ref, c.X, Q, c.job_off, c.job_terms, f)
+
+
+def test_tc_alone_and_in_a_batch_give_identical_rows(lr):
+    n, d, V, B, K = 20_000, 128, 256, 32, 20
+    c = datagen.corpus(6, n, d, V, 10.0, 1.1)
+    f = datagen.filters(6, B, V, 1.1)
+    Q = datagen.query_embeddings(6, B, d)
+    idx = lr.lr_index_create(c.X, V, bitsets=c.bitsets(), metric="cosine", max_batch=32, max_k=32)
+    batch = _run(lr, idx, Q, f, K, plan="tc")
+    for b in (0, 17, 31):
+        alone = _run(lr, idx, Q[b:b + 1].copy(), f.subset([b]), K, plan="tc")
+        assert np.array_equal(alone[0][0], batch[0][b]) and np.array_equal(alone[1][0], batch[1][b])
