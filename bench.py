@@ -32,7 +32,7 @@ METRIC = "filtered top-K QPS @10M×128 vs plain FP32; HBM GB/s % of peak; p99 ms
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--batch", type=int, default=32)
@@ -82,57 +82,104 @@ def workload_config(args):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    """Samples the SM clock and the clock-event reasons every few milliseconds while the timed region
+    runs (read-only NVML queries; falls back to nvidia-smi when NVML is unavailable)."""
 
-    def __init__(self, gpu: int):
+    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
+               ("hw_power_brake_slowdown", "nvmlClocksEventReasonHwPowerBrakeSlowdown"))
+
+    def __init__(self, gpu: int, period_s: float = 0.005):
         self.gpu = gpu
+        self.period = period_s
+        self.samples = []  # (sm_mhz, max_mhz, reasons bitmask, host time)
+        self.window = (0.0, float("inf"))
+        self.names = []
+        self.stop = threading.Event()
+        self.nv = None
         self.proc = None
-        self.lines = []
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except OSError:
-            self.proc = None
+            import pynvml as nv
+
+            nv.nvmlInit()
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            ids = [x for x in vis.split(",") if x.strip() != ""]
+            phys = int(ids[self.gpu]) if ids and ids[self.gpu].strip().isdigit() else self.gpu
+            self.h = nv.nvmlDeviceGetHandleByIndex(phys)
+            self.nv = nv
+            self.names = [(nm, getattr(nv, attr)) for nm, attr in self.REASONS if hasattr(nv, attr)]
+            self.t = threading.Thread(target=self._poll_nvml, daemon=True)
+        except Exception:
+            self.nv = None
+            self.t = threading.Thread(target=self._poll_smi, daemon=True)
+        self.t.start()
         return self
 
-    def _read(self):
+    def _poll_nvml(self):
+        nv, h = self.nv, self.h
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while not self.stop.is_set():
+            try:
+                self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), mx,
+                                     nv.nvmlDeviceGetCurrentClocksEventReasons(h), time.perf_counter()))
+            except Exception:
+                pass
+            self.stop.wait(self.period)
+
+    def _poll_smi(self):
+        fields = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.names = [(nm, 1 << i) for i, (nm, _) in enumerate(self.REASONS[:4])]
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + fields,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                bits = sum(1 << i for i, v in enumerate(parts[2:6]) if v.lower() in ("active", "1"))
+                self.samples.append((float(parts[0]), float(parts[1]), bits, time.perf_counter()))
+            except (ValueError, IndexError):
+                continue
+
+    def wait_first(self, timeout_s: float = 5.0):
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < timeout_s:
+            time.sleep(0.01)
 
     def __exit__(self, *exc):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        self.t.join(timeout=5)
+        if self.nv is not None:
+            try:
+                self.nv.nvmlShutdown()
+            except Exception:
+                pass
+
+    def mark(self, t0: float, t1: float):
+        """Keep only the samples taken between host times t0 and t1 (the timed region)."""
+        self.window = (t0, t1)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() in ("active", "1"):
-                    reasons.add(nm)
-        if not sm:
+        got = [x for x in self.samples if self.window[0] <= x[3] <= self.window[1]]
+        if not got:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        sm = [x[0] for x in got]
+        reasons = sorted({nm for _, _, bits, _ in got for nm, b in self.names if bits & b})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(x[1] for x in got)),
+                "sm_min_mhz": float(min(sm)), "reasons": reasons, "samples": len(sm)}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -145,18 +192,29 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def scan_plan(args):
+    """The scan kernel the runtime picks for this batch and the queries one launch of it serves
+    (tensor-core tiles from 16 queries up, 64 per launch at d <= 128 and 32 above; SIMT
+    matrix-vector scan below that, 8 per launch)."""
+    d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
+    plan = args.plan if args.plan != "auto" else ("tc" if args.batch >= 16 else "gemv")
+    if plan == "tc":
+        return "k_scan_tc", (64 if d_pad <= 128 else 32), d_pad
+    return "k_scan_gemv", 8, d_pad
+
+
 def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
     """Bytes the main scan must move per launch: rows that pass some query of the launch (each read
     once at d_pad*4 bytes) plus, per distinct term, the cheaper of its bitmap and its posting list."""
     import torch
 
-    d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
+    _, per, d_pad = scan_plan(args)
     n = corpus.n
     df = corpus.df
     per_launch = []
     B = filters.n
-    for q0 in range(0, B, 8):
-        sub = filters.subset(range(q0, min(B, q0 + 8)))
+    for q0 in range(0, B, per):
+        sub = filters.subset(range(q0, min(B, q0 + per)))
         _, bm = lr.lr_filter_count(idx, sub, bitmap=True)
         union = bm[0].clone()
         for i in range(1, sub.n):
@@ -255,17 +313,20 @@ def run_ours(args):
         p.start.record()
         p.stop.record()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        h0 = time.perf_counter()
         ev0.record()
         for i in range(args.steps):
             step(i, probes[i])
         ev1.record()
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+        clk.mark(h0, time.perf_counter())
+        if world > 1:
+            dist.barrier()
     ms = ev0.elapsed_time(ev1)
     step_ms = []
     lr.lr_index_sync(idx)
@@ -295,7 +356,7 @@ def run_ours(args):
     # scan_ms covers n_scan launches of batch i % nb; use batch 0's bytes as the per-launch average
     achieved = (sum(per_launch) / 1e9) / (scan_ms / 1e3)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_scan_gemv (main scan, %d launches per step)" % n_scan,
+            "traffic": None, "kernel": "%s (main scan, %d launches per step)" % (scan_plan(args)[0], n_scan),
             "algorithmic_bytes_per_launch": float(np.mean(per_launch)), "launch_ms": scan_ms / max(n_scan, 1),
             "peak_kind": peak_kind}
 

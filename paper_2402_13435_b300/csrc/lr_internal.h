@@ -77,6 +77,7 @@ struct ScanArgs {
   const int32_t *qc_off;  // [nq+1] clause ranges
   const int32_t *cl_off;  // [n_clauses+1] slot ranges
   const int32_t *cl_slot; // slot ids
+  int32_t n_cl, n_tm;     // clauses and slot ids of the launch (sizes of cl_off - 1 and cl_slot)
   // 256-row groups visited: g = g_begin + i * g_step, g < n_groups
   int64_t g_begin, g_step, n_groups;
   int32_t mode;

@@ -81,7 +81,7 @@ struct Carver {
 
 // One GEMV launch worth of compiled filters (device offsets into the filter region).
 struct SubBatch {
-  int q_base, nq, n_slots;
+  int q_base, nq, n_slots, n_cl, n_tm;
   size_t off_slots, off_qc, off_cl, off_cs;
 };
 
@@ -587,6 +587,8 @@ lr_status compile_filters(lr_index *ix, const lr_filters *f, int B, int max_q_pe
     sb.n_slots = (int)slots.size();
     const int ncl = qo[e] - qo[b];
     const int ntm = ncl > 0 ? co[qo[e]] - co[qo[b]] : 0;
+    sb.n_cl = ncl;
+    sb.n_tm = ntm;
     sb.off_slots = take(sizeof(uint64_t) * std::max<size_t>(slots.size(), 1), 16);
     sb.off_qc = take(sizeof(int32_t) * (sb.nq + 1), 16);
     sb.off_cl = take(sizeof(int32_t) * (ncl + 1), 16);
@@ -703,6 +705,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.qc_off = (const int32_t *)(ix->filt_d + sb.off_qc);
     a.cl_off = (const int32_t *)(ix->filt_d + sb.off_cl);
     a.cl_slot = (const int32_t *)(ix->filt_d + sb.off_cs);
+    a.n_cl = sb.n_cl;
+    a.n_tm = sb.n_tm;
     a.n_groups = ix->n_groups;
     a.g_begin = 0;
     a.g_step = 1;

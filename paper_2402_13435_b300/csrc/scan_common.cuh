@@ -6,25 +6,34 @@
 namespace lr {
 namespace {
 
-// CNF of launch-local query q over the current group's words (sw: [slot][8]).
-__device__ __forceinline__ void eval_cnf(const ScanArgs &a, int q, const uint32_t *sw, uint32_t (&pw)[8]) {
+// CNF of launch-local query q over the current group's words (sw: [slot][8]),
+// from the launch's clause lists qc (clause ranges per query), cl (slot ranges
+// per clause) and cs (slot ids), which may sit in shared or global memory.
+__device__ __forceinline__ void eval_cnf_lists(const int32_t *qc, const int32_t *cl, const int32_t *cs, int q,
+                                               const uint32_t *sw, uint32_t (&pw)[8]) {
 #pragma unroll
   for (int w = 0; w < 8; ++w) pw[w] = 0xFFFFFFFFu;
-  const int c0 = a.qc_off[q], c1 = a.qc_off[q + 1];
+  const int c0 = qc[q], c1 = qc[q + 1];
+  int t0 = cl[c0];
   for (int c = c0; c < c1; ++c) {
     uint32_t cw[8];
 #pragma unroll
     for (int w = 0; w < 8; ++w) cw[w] = 0u;
-    const int t0 = a.cl_off[c], t1 = a.cl_off[c + 1];
+    const int t1 = cl[c + 1];
     for (int t = t0; t < t1; ++t) {
-      const uint4 *s = reinterpret_cast<const uint4 *>(sw + a.cl_slot[t] * 8);
+      const uint4 *s = reinterpret_cast<const uint4 *>(sw + cs[t] * 8);
       const uint4 lo = s[0], hi = s[1];
       cw[0] |= lo.x; cw[1] |= lo.y; cw[2] |= lo.z; cw[3] |= lo.w;
       cw[4] |= hi.x; cw[5] |= hi.y; cw[6] |= hi.z; cw[7] |= hi.w;
     }
 #pragma unroll
     for (int w = 0; w < 8; ++w) pw[w] &= cw[w];
+    t0 = t1;
   }
+}
+
+__device__ __forceinline__ void eval_cnf(const ScanArgs &a, int q, const uint32_t *sw, uint32_t (&pw)[8]) {
+  eval_cnf_lists(a.qc_off, a.cl_off, a.cl_slot, q, sw, pw);
 }
 
 // Digit step of the exact fallback: for every participating query find the

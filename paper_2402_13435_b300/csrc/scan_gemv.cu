@@ -75,9 +75,11 @@ __device__ __forceinline__ void score_batch(const ScanArgs &a, const unsigned ch
                                             const uint32_t *meta_qm, uint32_t n, const float *qs,
                                             const uint64_t (&tq)[NQ], int lane, int top, int shift,
                                             uint32_t dmask, size_t row_stride) {
-  if ((uint32_t)lane >= n) return;
-  const uint32_t row = meta_row[lane];
-  const uint32_t qm = meta_qm[lane];
+  // every lane takes part (the appends below are warp-aggregated); lanes past
+  // the batch score a stale slot of the buffer and pass no query
+  const bool live = (uint32_t)lane < n;
+  const uint32_t row = live ? meta_row[lane] : 0u;
+  const uint32_t qm = live ? meta_qm[lane] : 0u;
   const float *xr = reinterpret_cast<const float *>(buf + (size_t)lane * row_stride);
   float acc[NQ];
 #pragma unroll
@@ -96,18 +98,25 @@ __device__ __forceinline__ void score_batch(const ScanArgs &a, const unsigned ch
   }
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    if (!((qm >> q) & 1u)) continue;
+    const bool pass = (qm >> q) & 1u;
     const uint64_t key = make_key(acc[q], row);
     const int g2 = a.q_base + q;
     if (a.mode == kCollect) {
-      if (key >= tq[q]) {
-        const uint32_t p = atomicAdd(&a.buf_cnt[g2], 1u);
+      // one counter reservation per warp and query
+      const bool take = pass && key >= tq[q];
+      const uint32_t want = __ballot_sync(0xFFFFFFFFu, take);
+      if (want == 0u) continue;
+      uint32_t base = 0;
+      if (lane == __ffs(want) - 1) base = atomicAdd(&a.buf_cnt[g2], (uint32_t)__popc(want));
+      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(want) - 1);
+      if (take) {
+        const uint32_t p = base + (uint32_t)__popc(want & ((1u << lane) - 1u));
         if ((int64_t)p < a.buf_cap)
           a.buf[(size_t)g2 * (size_t)a.buf_cap + p] = key;
         else
           atomicOr(&a.overflow[g2], 1u);
       }
-    } else if (top >= 64 || (key >> top) == (tq[q] >> top)) {
+    } else if (pass && (top >= 64 || (key >> top) == (tq[q] >> top))) {
       atomicAdd(&a.hist[(size_t)g2 * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
     }
   }

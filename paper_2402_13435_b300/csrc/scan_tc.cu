@@ -8,8 +8,8 @@
 // memory.  FP32 accuracy comes from the 3xTF32 split
 //     x = x_hi + x_lo,  x_hi = x with the low 13 mantissa bits cleared,
 //     x.q ~= x_hi.q_hi + x_hi.q_lo + x_lo.q_hi     (x_lo.q_lo dropped, < 2^-20 |x q|)
-// where every operand handed to the tensor core is exactly representable in
-// TF32, so no rounding mode of the unit is relied on.
+// where x_hi and q_hi are exact in TF32; the unit truncates x_lo and q_lo to
+// TF32 (11 significant bits of their 13), an error below 2^-22 |x q| per term.
 //
 // One CTA per SM, ten warps with fixed roles:
 //   warp 0     producer: takes 256-row groups from the work counter, prefetches
@@ -66,7 +66,7 @@ struct TileMeta {
 
 struct TcLayout {
   int S, C, N;
-  size_t raw, q, meta, slots, taus, cand, ccnt, bars, holder, total;
+  size_t raw, q, meta, slots, taus, cand, ccnt, cq, bars, holder, total;
 };
 
 __host__ __device__ inline size_t tc_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -86,11 +86,13 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int N, int n_slots, int
   T.slots = tc_align(off, 16);
   off = T.slots + (size_t)2 * (n_slots > 0 ? n_slots : 1) * 32;
   T.taus = tc_align(off, 16);
-  off = T.taus + (size_t)N * 12;  // 64-bit thresholds, then their high words
+  off = T.taus + (size_t)N * 12;  // 64-bit thresholds, then their score words as floats
   T.cand = tc_align(off, 16);     // per epilogue warp: keys, then query indices (bytes)
   off = T.cand + (size_t)4 * kWarpCand * 9;
   T.ccnt = tc_align(off, 16);
   off = T.ccnt + 16;
+  T.cq = off;  // per epilogue warp: per-query counts, then reserved bases, of one flush
+  off = T.cq + (size_t)4 * 2 * N * 4;
   T.bars = tc_align(off, 16);
   off = T.bars + (size_t)(2 * S + 2 * kABufs + 4 + 2 * kMetaDepth + 1) * 8;
   T.holder = tc_align(off, 16);
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   TileMeta *meta = reinterpret_cast<TileMeta *>(smem + T.meta);
   uint32_t *slot_tab = reinterpret_cast<uint32_t *>(smem + T.slots);
   uint64_t *taus = reinterpret_cast<uint64_t *>(smem + T.taus);
-  uint32_t *tau_hi = reinterpret_cast<uint32_t *>(taus + N);
+  float *thr = reinterpret_cast<float *>(taus + N);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + T.bars);
   uint64_t *raw_full = bars, *raw_empty = bars + S;
   uint64_t *a_full = bars + 2 * S, *a_empty = a_full + kABufs;
@@ -181,7 +183,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int g2 = a.q_base + q;
     const bool live = q < a.nq && (a.active == nullptr || a.active[g2] != 0u);
     taus[q] = !live ? 0ull : (a.mode == kCollect ? (a.tau ? a.tau[g2] : 0ull) : a.prefix[g2]);
-    tau_hi[q] = (uint32_t)(taus[q] >> 32);
+    // score_key(s) >= h  <=>  s >= thr[q] for every non-NaN score s
+    const uint32_t h = (uint32_t)(taus[q] >> 32);
+    thr[q] = h <= score_key(-INFINITY) ? -INFINITY
+             : h > score_key(INFINITY) ? __uint_as_float(0x7FFFFFFFu)  // NaN: no score passes
+                                       : key_score(h);
   }
   fence_proxy_async();
   if (warp == 1) {
@@ -430,40 +436,50 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int ew = warp - kEpiWarp0;
     uint64_t pm = 0, pa = 0;
     // Candidates are recorded in a per-warp shared-memory list by the lanes that
-    // find them (a shared-memory atomic each) and flushed to the query buffers
-    // with several global atomics in flight per lane, so no epilogue step waits
-    // on an L2 round trip.
+    // find them (a shared-memory atomic each).  A flush tests them exactly,
+    // counts them per query, reserves each query's range of its buffer with one
+    // global atomic and scatters the keys, so a query with many candidates (a
+    // broad filter in the threshold sample) does not serialise on its counter.
+    // The flush stays inline: an out-of-line call in this loop, between the
+    // warp-collective tensor-memory loads, has faulted.
     uint64_t *ckey = reinterpret_cast<uint64_t *>(smem + T.cand) + (size_t)ew * kWarpCand;
     uint8_t *cqry = reinterpret_cast<uint8_t *>(smem + T.cand + (size_t)4 * kWarpCand * 8) + (size_t)ew * kWarpCand;
     uint32_t *ccnt = reinterpret_cast<uint32_t *>(smem + T.ccnt) + ew;
+    uint32_t *cq = reinterpret_cast<uint32_t *>(smem + T.cq) + (size_t)ew * 2 * N;
+    uint32_t *cb = cq + N;
     if (lane == 0) *ccnt = 0u;
     __syncwarp();
     auto flush = [&]() {
       __syncwarp();
       const uint32_t n = *ccnt < (uint32_t)kWarpCand ? *ccnt : (uint32_t)kWarpCand;
-      for (uint32_t e0 = lane; e0 < n; e0 += 128) {
-        uint32_t pos[4];
-        int g2[4];
-        bool take[4];
+      for (int i = lane; i < N; i += 32) cq[i] = 0u;
+      __syncwarp();
+      uint32_t rk[kWarpCand / 32];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {  // exact test, then up to four atomics in flight
-          const uint32_t e = e0 + 32 * u;
-          take[u] = false;
-          if (e < n) {
-            const int q = cqry[e];
-            g2[u] = a.q_base + q;
-            take[u] = ckey[e] >= taus[q];
-            if (take[u]) pos[u] = atomicAdd(&a.buf_cnt[g2[u]], 1u);
-          }
+      for (int u = 0; u < kWarpCand / 32; ++u) {
+        const uint32_t e = (uint32_t)lane + 32u * (uint32_t)u;
+        rk[u] = 0xFFFFFFFFu;
+        if (e < n) {
+          const int q = cqry[e];
+          if (ckey[e] >= taus[q]) rk[u] = atomicAdd(&cq[q], 1u);
         }
+      }
+      __syncwarp();
+      for (int i = lane; i < N; i += 32) {
+        const uint32_t c = cq[i];
+        cb[i] = c != 0u ? atomicAdd(&a.buf_cnt[a.q_base + i], c) : 0u;
+      }
+      __syncwarp();
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (!take[u]) continue;
-          if ((int64_t)pos[u] < a.buf_cap)
-            a.buf[(size_t)g2[u] * (size_t)a.buf_cap + pos[u]] = ckey[e0 + 32 * u];
-          else
-            atomicOr(&a.overflow[g2[u]], 1u);
-        }
+      for (int u = 0; u < kWarpCand / 32; ++u) {
+        if (rk[u] == 0xFFFFFFFFu) continue;
+        const uint32_t e = (uint32_t)lane + 32u * (uint32_t)u;
+        const int q = cqry[e];
+        const uint32_t pos = cb[q] + rk[u];
+        if ((int64_t)pos < a.buf_cap)
+          a.buf[(size_t)(a.q_base + q) * (size_t)a.buf_cap + pos] = ckey[e];
+        else
+          atomicOr(&a.overflow[a.q_base + q], 1u);
       }
       __syncwarp();
       if (lane == 0) *ccnt = 0u;
@@ -485,34 +501,55 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 2 * N);
       const uint64_t qmask = meta[m].qm[quarter * 32 + lane];
       const uint32_t grow = (uint32_t)(meta[m].row0 + quarter * 32 + lane);
-#pragma unroll
+#pragma unroll 1
       for (int j = 0; j < N / 16; ++j) {
         const uint32_t bm = (uint32_t)(qmask >> (16 * j)) & 0xFFFFu;
         if (!__any_sync(0xFFFFFFFFu, bm != 0u)) continue;  // no lane needs this block of 16 queries
+        __syncwarp();
         uint32_t rh[16], rl[16];
         tmem_ld16(taddr + (uint32_t)(16 * j), rh);      // x_hi.q_hi + x_lo.q_hi
         tmem_ld16(taddr + (uint32_t)(N + 16 * j), rl);  // x_hi.q_lo
         tmem_ld_wait();
         if (a.mode == kCollect) {
-          // a key can reach the threshold only if its score word does: lanes
-          // record their hits on the spot, exact key tests run at the flush
+          // A key can reach the threshold only if its score word does, i.e. the
+          // score reaches the float threshold: a branch-free test builds the
+          // lane's hit mask, and only warps with a hit record candidates (the
+          // exact key tests run at the flush).
+          float sc[16];
+          uint32_t hit = 0;
+          const float4 *tv = reinterpret_cast<const float4 *>(thr + 16 * j);
 #pragma unroll
-          for (int b = 0; b < 16; ++b) {
-            const uint32_t sk = score_key(__uint_as_float(rh[b]) + __uint_as_float(rl[b]));
-            if (((bm >> b) & 1u) && sk >= tau_hi[16 * j + b]) {
-              const uint32_t e = atomicAdd(ccnt, 1u);
-              if (e < (uint32_t)kWarpCand) {
-                ckey[e] = ((uint64_t)sk << 32) | (uint64_t)(0xFFFFFFFFu - grow);
-                cqry[e] = (uint8_t)(16 * j + b);
-              }
+          for (int v = 0; v < 4; ++v) {
+            const float4 t = tv[v];
+            const float tt[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int b = 4 * v + u;
+              sc[b] = __uint_as_float(rh[b]) + __uint_as_float(rl[b]);
+              hit |= (sc[b] >= tt[u] ? 1u : 0u) << b;
             }
-            if (b == 7) {  // at most 256 entries are added between two checks
+          }
+          hit &= bm;
+          if (__any_sync(0xFFFFFFFFu, hit != 0u)) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // at most 256 entries are added between two checks
+              const uint32_t hh = (hit >> (8 * h)) & 0xFFu;
+              if (!__any_sync(0xFFFFFFFFu, hh != 0u)) continue;
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                if ((hh >> u) & 1u) {
+                  const int b = 8 * h + u;
+                  const uint32_t e = atomicAdd(ccnt, 1u);
+                  if (e < (uint32_t)kWarpCand) {
+                    ckey[e] = make_key(sc[b], grow);
+                    cqry[e] = (uint8_t)(16 * j + b);
+                  }
+                }
+              }
               __syncwarp();
               if (*ccnt > (uint32_t)(kWarpCand / 2)) flush();
             }
           }
-          __syncwarp();
-          if (*ccnt > (uint32_t)(kWarpCand / 2)) flush();
         } else {
 #pragma unroll
           for (int b = 0; b < 16; ++b) {

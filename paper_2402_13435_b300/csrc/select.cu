@@ -76,6 +76,47 @@ __device__ uint64_t block_kth(const uint64_t *keys, int64_t n, uint32_t r, SelSh
   return prefix;
 }
 
+constexpr int kPilot = 4096;  // keys of the strided pilot sample (kPilot <= kSmemKeys)
+
+// r-th largest of n > kSmemKeys distinct keys in global memory.  The r-th largest
+// key of a strided pilot of kPilot keys, taken with a margin of three standard
+// deviations, gives a bound t0 that usually has between r and kSmemKeys keys at
+// or above it; those keys are gathered into shared memory (one coalesced pass)
+// and selected there.  When the gathered count misses that window the radix
+// passes run over global memory, so the result is exact either way.
+__device__ uint64_t kth_large(const uint64_t *g, int64_t n, uint32_t r, uint64_t *sbuf, SelShared &sh) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kPilot; i += blockDim.x) sbuf[i] = __ldcg(g + (int64_t)i * n / kPilot);
+  __syncthreads();
+  const double e = (double)r * (double)kPilot / (double)n;
+  double want = ceil(e + 3.0 * sqrt(e) + 8.0);
+  const uint32_t rp = want > (double)kPilot ? (uint32_t)kPilot : (uint32_t)want;
+  const uint64_t t0 = block_kth(sbuf, kPilot, rp, sh);
+  if (tid == 0) sh.n_out = 0u;
+  __syncthreads();
+  constexpr int kU = 4;  // loads in flight per thread
+  for (int64_t b = tid; b < n; b += (int64_t)kU * blockDim.x) {
+    uint64_t v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = b + (int64_t)u * blockDim.x;
+      v[u] = i < n ? __ldcg(g + i) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (b + (int64_t)u * blockDim.x < n && v[u] >= t0) {
+        const uint32_t pos = atomicAdd(&sh.n_out, 1u);
+        if (pos < (uint32_t)kSmemKeys) sbuf[pos] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t c = sh.n_out;
+  __syncthreads();
+  if (c >= r && c <= (uint32_t)kSmemKeys) return block_kth(sbuf, c, r, sh);
+  return block_kth(g, n, r, sh);
+}
+
 __device__ void bitonic_desc(uint64_t *s, int P) {
   for (int size = 2; size <= P; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -113,7 +154,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   if (a.mode == 0) {
     const int32_t r = a.rank[q];
     uint64_t t = 0;
-    if (r > 0 && !ovf && n >= r) t = block_kth(keys, n, (uint32_t)r, sh);
+    if (r > 0 && !ovf && n >= r)
+      t = n <= kSmemKeys ? block_kth(keys, n, (uint32_t)r, sh) : kth_large(gkeys, n, (uint32_t)r, sbuf, sh);
     if (tid == 0) a.tau[q] = t;
     return;
   }
@@ -139,7 +181,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   int P2 = 1;
   while (P2 < kp) P2 <<= 1;
   if (kp > 0) {
-    const uint64_t kth = block_kth(keys, n, (uint32_t)kp, sh);
+    const uint64_t kth =
+        n <= kSmemKeys ? block_kth(keys, n, (uint32_t)kp, sh) : kth_large(gkeys, n, (uint32_t)kp, sbuf, sh);
     if (tid == 0) sh.n_out = 0u;
     for (int i = tid; i < P2; i += blockDim.x) sort[i] = 0ull;
     __syncthreads();
