@@ -65,7 +65,18 @@ typedef struct lr_index lr_index;
  * Pre-Allocation").
  *
  *   n_jobs, dim      rows and columns of the embedding matrix (dim <= 512).
- *   dtype            LR_F32 (the plain method).  Other types: LR_ERR_UNSUPPORTED.
+ *   dtype            LR_F32: the plain method, FP32 rows.
+ *                    LR_BF16 / LR_FP8_E4M3: the precision form.  The index keeps
+ *                    the FP32 rows and a low-precision copy (BF16 rounded to
+ *                    nearest even; or e4m3 with a per-row FP32 scale
+ *                    max|x|/448) that the scan reads.  A search then gathers the
+ *                    top oversample*K candidates per query by the low-precision
+ *                    score, rescores them in FP32 from the FP32 rows, keeps the
+ *                    top K, and re-ranks the candidates within the FP32 error
+ *                    band of the K-th score by an FP64 dot product.  The
+ *                    returned scores are FP32 dot products (FP64 ones rounded to
+ *                    FP32 inside the band).  (Appendix "Quantization": a coarse
+ *                    low-precision pass followed by exact rescoring.)
  *   metric           lr_metric.
  *   emb              [n_jobs][dim] row-major FP32, host or device.  Must be finite
  *                    (checked; LR_ERR_INVALID otherwise).
@@ -80,10 +91,13 @@ typedef struct lr_index lr_index;
  *                    bitmaps (n_jobs bits each); the others stay posting lists and
  *                    are expanded into per-batch bitmaps at search time.  -1 = all.
  *   max_batch        largest batch lr_search accepts (workspace sizing).
- *   max_k            largest K lr_search accepts (<= 4096).
+ *   max_k            largest K lr_search accepts (<= 4096; precision form:
+ *                    oversample * max_k <= 4096).
  *   max_batch_terms  total term occurrences over all filters of one batch that
  *                    the workspace holds (0: 16 per query).
  *   max_sparse_terms distinct posting-list terms one batch may use (0: 256).
+ *   oversample       precision form: candidates per query = oversample * K
+ *                    (0: 4).  Ignored for LR_F32.
  */
 typedef struct lr_index_desc {
   int64_t n_jobs;
@@ -100,6 +114,7 @@ typedef struct lr_index_desc {
   int32_t max_k;
   int32_t max_batch_terms;
   int32_t max_sparse_terms;
+  int32_t oversample;
 } lr_index_desc;
 
 /*
@@ -137,6 +152,7 @@ typedef struct lr_search_stats {
   void *scan_start;      /* cudaEvent_t recorded on the stream right before the     */
   void *scan_stop;       /* main scan launches, and right after them                */
   int32_t *n_scan_launches; /* host, 1 value: launches between scan_start/stop     */
+  int32_t *rescore_ties; /* [B] precision form: candidates re-ranked in FP64         */
 } lr_search_stats;
 
 /* Build an index (allocates every device buffer it will ever use: appendix

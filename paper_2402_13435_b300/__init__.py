@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "liblr.so")
 
 LR_OK, LR_ERR_INVALID, LR_ERR_NOMEM, LR_ERR_WORKSPACE, LR_ERR_CUDA, LR_ERR_TIMEOUT, LR_ERR_UNSUPPORTED = range(7)
 LR_F32, LR_BF16, LR_FP8_E4M3 = 0, 1, 2
+_DTYPE = {"f32": LR_F32, "bf16": LR_BF16, "fp8": LR_FP8_E4M3}
 LR_DOT, LR_COSINE = 0, 1
 LR_PLAN_AUTO, LR_PLAN_GEMV, LR_PLAN_TC = 0, 1, 2
 _METRIC = {"dot": LR_DOT, "cosine": LR_COSINE}
@@ -41,7 +42,8 @@ class lr_index_desc(ctypes.Structure):
                 ("metric", ctypes.c_int32), ("vocab", ctypes.c_int32), ("emb", ctypes.c_void_p),
                 ("bitsets", ctypes.c_void_p), ("post_off", ctypes.c_void_p), ("post_ids", ctypes.c_void_p),
                 ("n_dense_terms", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_k", ctypes.c_int32),
-                ("max_batch_terms", ctypes.c_int32), ("max_sparse_terms", ctypes.c_int32)]
+                ("max_batch_terms", ctypes.c_int32), ("max_sparse_terms", ctypes.c_int32),
+                ("oversample", ctypes.c_int32)]
 
 
 class lr_filters(ctypes.Structure):
@@ -56,7 +58,7 @@ class lr_search_opts(ctypes.Structure):
 class lr_search_stats(ctypes.Structure):
     _fields_ = [("pass_count", ctypes.c_void_p), ("cand_count", ctypes.c_void_p), ("fallback", ctypes.c_void_p),
                 ("n_launches", ctypes.c_void_p), ("scan_start", ctypes.c_void_p), ("scan_stop", ctypes.c_void_p),
-                ("n_scan_launches", ctypes.c_void_p)]
+                ("n_scan_launches", ctypes.c_void_p), ("rescore_ties", ctypes.c_void_p)]
 
 
 def _load():
@@ -169,10 +171,11 @@ class Index:
 
 def lr_index_create(emb, vocab: int, *, bitsets=None, post_off=None, post_ids=None, n_dense_terms: int = -1,
                     metric: str = "cosine", max_batch: int = 256, max_k: int = 1000, max_batch_terms: int = 0,
-                    max_sparse_terms: int = 0, stream=None) -> Index:
+                    max_sparse_terms: int = 0, dtype: str = "f32", oversample: int = 0, stream=None) -> Index:
     """Build an index over job embeddings ``emb`` [n][dim] FP32 (torch or numpy, host or device) and
     per-job terms given either as job-major ``bitsets`` [n][ceil(vocab/64)] uint64 or as posting lists
-    (``post_off`` int64[vocab+1], ``post_ids`` uint32[nnz])."""
+    (``post_off`` int64[vocab+1], ``post_ids`` uint32[nnz]).  ``dtype`` "bf16" or "fp8" selects the
+    precision form (low-precision scan of ``oversample`` x K candidates, FP32 rescore, FP64 near ties)."""
     n, dim = int(emb.shape[0]), int(emb.shape[1])
     keep = []
     if isinstance(emb, np.ndarray):
@@ -184,10 +187,11 @@ def lr_index_create(emb, vocab: int, *, bitsets=None, post_off=None, post_ids=No
         post_ids = np.ascontiguousarray(np.asarray(post_ids), dtype=np.uint32) if isinstance(post_ids, np.ndarray) \
             or not hasattr(post_ids, "data_ptr") else post_ids
     keep += [emb, bitsets, post_off, post_ids]
-    d = lr_index_desc(n_jobs=n, dim=dim, dtype=LR_F32, metric=_METRIC[metric], vocab=int(vocab), emb=_ptr(emb),
+    d = lr_index_desc(n_jobs=n, dim=dim, dtype=_DTYPE[dtype], metric=_METRIC[metric], vocab=int(vocab), emb=_ptr(emb),
                       bitsets=_ptr(bitsets), post_off=_ptr(post_off), post_ids=_ptr(post_ids),
                       n_dense_terms=int(n_dense_terms), max_batch=int(max_batch), max_k=int(max_k),
-                      max_batch_terms=int(max_batch_terms), max_sparse_terms=int(max_sparse_terms))
+                      max_batch_terms=int(max_batch_terms), max_sparse_terms=int(max_sparse_terms),
+                      oversample=int(oversample))
     h = ctypes.c_void_p()
     _check(_lib.lr_index_create(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "lr_index_create")
     del keep
@@ -270,9 +274,10 @@ def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out
     st_arrays = None
     if stats:
         st_arrays = dict(pass_count=np.zeros(B, dtype=np.int64), cand_count=np.zeros(B, dtype=np.int32),
-                         fallback=np.zeros(B, dtype=np.int32))
+                         fallback=np.zeros(B, dtype=np.int32), rescore_ties=np.zeros(B, dtype=np.int32))
         st = lr_search_stats(st_arrays["pass_count"].ctypes.data, st_arrays["cand_count"].ctypes.data,
-                             st_arrays["fallback"].ctypes.data)
+                             st_arrays["fallback"].ctypes.data, None, None, None, None,
+                             st_arrays["rescore_ties"].ctypes.data)
     elif probe is not None:
         st = probe.c()
     fc = f.c()

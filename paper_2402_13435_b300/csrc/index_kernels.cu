@@ -7,6 +7,9 @@
 // whole 256-row groups.  Frequent terms keep a resident bitmap; rare terms keep
 // their posting list and are expanded into a workspace bitmap only when a batch
 // uses them.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "lr_internal.h"
 
 namespace lr {
@@ -35,6 +38,31 @@ __global__ void k_rows_to_index(const float *in, float *out, int64_t n, int dim,
   float scale = 1.f;
   if (cosine) scale = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
   for (int k = lane; k < d_pad; k += 32) dst[k] = k < dim ? src[k] * scale : 0.f;
+}
+
+// Low-precision copy of the index rows (precision form).  BF16: each value
+// rounded to nearest even.  FP8 e4m3: per-row scale = max_k |x_k| / 448 (1 for
+// an all-zero row) and x8_k = e4m3(x_k / scale), round to nearest even with
+// saturation to the finite range, so that scale * x8 approximates x with the
+// row's largest magnitude mapped onto e4m3's largest finite value.  One warp
+// per row.
+__global__ void k_quantize_rows(const float *X, int64_t n, int d_pad, int elem, void *Xq, float *scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float *x = X + (size_t)row * d_pad;
+  if (elem == kElemBF16) {
+    __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(Xq) + (size_t)row * d_pad;
+    for (int k = lane; k < d_pad; k += 32) o[k] = __float2bfloat16_rn(x[k]);
+    return;
+  }
+  float amax = 0.f;
+  for (int k = lane; k < d_pad; k += 32) amax = fmaxf(amax, fabsf(x[k]));
+  for (int off = 16; off >= 1; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, off));
+  const float sc = amax > 0.f ? amax / kFp8Max : 1.f;
+  __nv_fp8_storage_t *o = reinterpret_cast<__nv_fp8_storage_t *>(Xq) + (size_t)row * d_pad;
+  for (int k = lane; k < d_pad; k += 32) o[k] = __nv_cvt_float_to_fp8(x[k] / sc, __NV_SATFINITE, __NV_E4M3);
+  if (lane == 0) scale[row] = sc;
 }
 
 // Job-major 64-bit bitsets -> term-major 32-bit bitmap words.  Thread (jw, tw)
@@ -167,6 +195,14 @@ cudaError_t launch_rows_to_index(const float *in, float *out, int64_t n, int dim
   if (n <= 0) return cudaSuccess;
   const int wpb = 8;
   k_rows_to_index<<<(unsigned)((n + wpb - 1) / wpb), wpb * 32, 0, s>>>(in, out, n, dim, d_pad, cosine, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_rows(const float *X, int64_t n, int d_pad, int elem, void *Xq, float *scale,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int wpb = 8;
+  k_quantize_rows<<<(unsigned)((n + wpb - 1) / wpb), wpb * 32, 0, s>>>(X, n, d_pad, elem, Xq, scale);
   return cudaGetLastError();
 }
 

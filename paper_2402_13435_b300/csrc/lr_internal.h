@@ -58,6 +58,10 @@ __host__ __device__ __forceinline__ uint64_t make_key(float s, uint32_t id) {
 
 __host__ __device__ __forceinline__ uint32_t key_id(uint64_t k) { return 0xFFFFFFFFu - (uint32_t)k; }
 
+// ------------------------------------------------------------ row storage
+enum ElemType : int { kElemF32 = 0, kElemBF16 = 1, kElemFP8 = 2 };
+constexpr float kFp8Max = 448.0f;  // largest finite e4m3 magnitude
+
 // ------------------------------------------------------------ scan launch
 enum ScanMode : int {
   kCollect = 0,  // append keys >= tau[q] to the query's buffer
@@ -67,6 +71,9 @@ enum ScanMode : int {
 // Device view of one compiled sub-batch of filters and the per-query state.
 struct ScanArgs {
   const float *X;        // [n][d_pad] FP32
+  const void *Xq;        // [n][d_pad] BF16 or FP8 e4m3 rows when elem != kElemF32
+  const float *xscale;   // [n] per-row scale of FP8 rows (score = scale * <q, x8>)
+  int32_t elem;          // kElemF32 / kElemBF16 / kElemFP8
   int64_t n;
   int32_t d_pad;
   const float *Q;        // [B][d_pad] FP32 (the whole batch)
@@ -132,6 +139,27 @@ struct SelectArgs {
 cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s);
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
+
+// FP32 rescore of the low-precision candidates with an FP64 re-rank of the
+// near ties at the K-th score (precision form).
+struct RescoreArgs {
+  const float *X;          // [n][d_pad] FP32 rows (normalised for cosine)
+  int32_t d_pad, dim;
+  const float *Q;          // [B][d_pad] FP32 queries (normalised for cosine)
+  const int32_t *cid;      // [B][c_stride] candidate ids from the low-precision selection
+  const int32_t *ccnt;     // [B] candidates per query
+  int32_t c_stride;
+  const int32_t *k;        // [B] final K per query
+  int32_t k_stride;
+  int32_t *out_ids;
+  float *out_scores;
+  int32_t *out_count;      // nullable
+  int32_t *tie_count;      // nullable [B]: candidates re-ranked in FP64
+  uint32_t *err;
+};
+cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s);
+cudaError_t launch_quantize_rows(const float *X, int64_t n, int d_pad, int elem, void *Xq, float *scale,
+                                 cudaStream_t s);
 cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,
                                 uint32_t *err, cudaStream_t s);
 cudaError_t launch_scatter_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *terms,

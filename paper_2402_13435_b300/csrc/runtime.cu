@@ -93,6 +93,12 @@ struct lr_index {
   int dim = 0, d_pad = 0, metric = 0, vocab = 0;
   int64_t n_groups = 0, n_words = 0;
   float *X = nullptr;
+  // precision form: low-precision copy of X that the scan reads
+  int elem = kElemF32;
+  void *Xq = nullptr;
+  float *xscale = nullptr;
+  int oversample = 1;
+  int max_kq = 0;  // candidates per query of the low-precision selection (oversample * max_k)
   // term storage
   uint32_t *dense_bm = nullptr;
   int n_dense = 0;
@@ -120,6 +126,8 @@ struct lr_index {
   uint32_t *hist = nullptr;
   uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
   int32_t *o_ids = nullptr, *o_cnt = nullptr, *o_cand = nullptr, *o_fb = nullptr;
+  int32_t *c_ids = nullptr, *c_cnt = nullptr, *kfin = nullptr, *o_ties = nullptr;  // precision form
+  float *c_sc = nullptr;
   float *o_sc = nullptr;
   char *filt_d = nullptr;
   size_t filt_bytes = 0;
@@ -144,6 +152,8 @@ namespace {
 void free_index(lr_index *ix) {
   if (!ix) return;
   cudaFree(ix->X);
+  cudaFree(ix->Xq);
+  cudaFree(ix->xscale);
   cudaFree(ix->dense_bm);
   cudaFree(ix->post_off_d);
   cudaFree(ix->post_ids_d);
@@ -166,7 +176,10 @@ lr_status check_err_word(lr_index *ix, cudaStream_t s, const char *where) {
     if (e & 4u) m += "posting id >= n_jobs; ";
     if (e & 8u) m += "non-finite query embedding; ";
     if (e & 2u) m += "inconsistent exact-selection state; ";
-    return fail((e & 2u) ? LR_ERR_CUDA : LR_ERR_INVALID, m);
+    if (e & 16u) m += "a bounded device wait timed out; ";
+    if (e & 32u) m += "more than 1024 candidates inside the FP64 near-tie band; ";
+    const lr_status st = (e & 16u) ? LR_ERR_TIMEOUT : (e & 2u) ? LR_ERR_CUDA : (e & 32u) ? LR_ERR_WORKSPACE : LR_ERR_INVALID;
+    return fail(st, m);
   }
   return LR_OK;
 }
@@ -257,7 +270,8 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   *out = nullptr;
   if (d->n_jobs < 1 || d->n_jobs >= 0xFFFFFFFFll) return fail(LR_ERR_INVALID, "n_jobs must be in [1, 2^32-2]");
   if (d->dim < 1 || d->dim > 256) return fail(LR_ERR_UNSUPPORTED, "dim must be in [1, 256]");
-  if (d->dtype != LR_F32) return fail(LR_ERR_UNSUPPORTED, "only LR_F32 storage is implemented");
+  if (d->dtype != LR_F32 && d->dtype != LR_BF16 && d->dtype != LR_FP8_E4M3) return fail(LR_ERR_INVALID, "unknown dtype");
+  const int oversample = d->dtype == LR_F32 ? 1 : (d->oversample > 0 ? d->oversample : 4);
   if (d->metric != LR_DOT && d->metric != LR_COSINE) return fail(LR_ERR_INVALID, "unknown metric");
   if (d->vocab < 1) return fail(LR_ERR_INVALID, "vocab must be >= 1");
   if (!d->emb) return fail(LR_ERR_INVALID, "emb is null");
@@ -267,6 +281,7 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   if (have_post && (!d->post_off || !d->post_ids)) return fail(LR_ERR_INVALID, "post_off and post_ids both needed");
   if (d->max_batch < 1) return fail(LR_ERR_INVALID, "max_batch must be >= 1");
   if (d->max_k < 1 || d->max_k > kMaxK) return fail(LR_ERR_INVALID, "max_k must be in [1, 4096]");
+  if ((int64_t)oversample * d->max_k > kMaxK) return fail(LR_ERR_INVALID, "oversample * max_k must be <= 4096");
 
   cudaStream_t s = (cudaStream_t)stream;
   lr_index *ix = new lr_index();
@@ -281,6 +296,9 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   ix->n_words = ix->n_groups * kGroupWords;
   ix->max_batch = d->max_batch;
   ix->max_k = d->max_k;
+  ix->elem = d->dtype == LR_BF16 ? kElemBF16 : d->dtype == LR_FP8_E4M3 ? kElemFP8 : kElemF32;
+  ix->oversample = oversample;
+  ix->max_kq = oversample * d->max_k;
   ix->max_batch_terms = d->max_batch_terms > 0 ? d->max_batch_terms : 16 * d->max_batch;
   ix->max_sparse = d->max_sparse_terms > 0 ? d->max_sparse_terms : 256;
 
@@ -319,6 +337,19 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
       CK2(cudaStreamSynchronize(s));
     }
     cudaFree(tmp);
+  }
+  if (ix->elem != kElemF32) {  // low-precision copy read by the scan (precision form)
+    const size_t qbytes = (size_t)ix->n * ix->d_pad * (ix->elem == kElemBF16 ? 2 : 1);
+    if (cudaMalloc(&ix->Xq, qbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(fail(LR_ERR_NOMEM, "cannot allocate the low-precision embedding copy"));
+    }
+    ix->device_bytes += qbytes;
+    if (ix->elem == kElemFP8) {
+      CK2(cudaMalloc(&ix->xscale, (size_t)ix->n * sizeof(float)));
+      ix->device_bytes += (size_t)ix->n * sizeof(float);
+    }
+    CK2(launch_quantize_rows(ix->X, ix->n, ix->d_pad, ix->elem, ix->Xq, ix->xscale, s));
   }
 
   // ---- term storage
@@ -393,11 +424,11 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   ix->samp_cap = samp_rows;
   int64_t cap = 0;
   if (sp.stride > 0) {
-    const double r = std::max(64.0, std::ceil(4.0 * ix->max_k * sp.frac));
+    const double r = std::max(64.0, std::ceil(4.0 * ix->max_kq * sp.frac));
     cap = pow2_ceil((int64_t)std::ceil(4.0 * r / sp.frac));
   }
   cap = std::max<int64_t>(cap, std::min<int64_t>(ix->n, 1 << 16));
-  cap = std::max<int64_t>(cap, ix->max_k);
+  cap = std::max<int64_t>(cap, ix->max_kq);
   ix->cand_cap = cap;
 
   // ---- workspace, one allocation
@@ -433,6 +464,12 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   const size_t o_ocnt = cv.take<int32_t>(B);
   const size_t o_ocand = cv.take<int32_t>(B);
   const size_t o_ofb = cv.take<int32_t>(B);
+  const bool lowp = ix->elem != kElemF32;
+  const size_t o_cids = cv.take<int32_t>(lowp ? (size_t)B * ix->max_kq : 0);
+  const size_t o_csc = cv.take<float>(lowp ? (size_t)B * ix->max_kq : 0);
+  const size_t o_ccnt = cv.take<int32_t>(lowp ? B : 0);
+  const size_t o_kfin = cv.take<int32_t>(lowp ? B : 0);
+  const size_t o_ties = cv.take<int32_t>(lowp ? B : 0);
   const size_t o_filt = cv.take<char>(ix->filt_bytes);
   ix->ws_bytes = align_up(cv.off, 256);
   if (cudaMalloc(&ix->ws, ix->ws_bytes) != cudaSuccess) {
@@ -470,6 +507,13 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   ix->o_cnt = (int32_t *)(w + o_ocnt);
   ix->o_cand = (int32_t *)(w + o_ocand);
   ix->o_fb = (int32_t *)(w + o_ofb);
+  if (lowp) {
+    ix->c_ids = (int32_t *)(w + o_cids);
+    ix->c_sc = (float *)(w + o_csc);
+    ix->c_cnt = (int32_t *)(w + o_ccnt);
+    ix->kfin = (int32_t *)(w + o_kfin);
+    ix->o_ties = (int32_t *)(w + o_ties);
+  }
   ix->filt_d = w + o_filt;
   CK2(cudaMemsetAsync(ix->done_ctr, 0, 2 * sizeof(uint32_t), s));
   CK2(cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), s));
@@ -504,7 +548,7 @@ namespace {
 struct Compiled {
   std::vector<SubBatch> subs;
   std::vector<int32_t> sparse_terms;  // distinct posting-list terms of the batch
-  size_t off_k = 0, off_rank = 0, off_sparse = 0, bytes = 0;
+  size_t off_k = 0, off_kfin = 0, off_rank = 0, off_sparse = 0, bytes = 0;
 };
 
 // Validate the CNF batch and lay out, in the pinned staging buffer, the
@@ -548,6 +592,7 @@ lr_status compile_filters(lr_index *ix, const lr_filters *f, int B, int max_q_pe
     return at;
   };
   C.off_k = take(sizeof(int32_t) * B, 16);
+  C.off_kfin = take(sizeof(int32_t) * B, 16);
   C.off_rank = take(sizeof(int32_t) * B, 16);
   C.off_sparse = take(sizeof(int32_t) * std::max<size_t>(C.sparse_terms.size(), 1), 16);
   if (off > ix->filt_bytes) return fail(LR_ERR_WORKSPACE, "filters: staging area too small");
@@ -646,18 +691,25 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // scoring plan: SIMT matrix-vector scan for small batches, tensor-core tiles
   // (3xTF32) once a launch serves enough queries to be a real contraction
   int plan = o.plan;
-  if (plan == LR_PLAN_AUTO) plan = B >= kTcMinBatch ? LR_PLAN_TC : LR_PLAN_GEMV;
+  const bool lowp = ix->elem != kElemF32;
+  if (plan == LR_PLAN_AUTO) plan = (B >= kTcMinBatch && !lowp) ? LR_PLAN_TC : LR_PLAN_GEMV;
+  if (plan == LR_PLAN_TC && lowp)
+    return fail(LR_ERR_UNSUPPORTED, "the tensor-core plan reads FP32 rows only; use the GEMV plan");
   if (plan == LR_PLAN_TC && !ix->have_tmap)
     return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable (no TMA descriptor for this index)");
   const int max_q = plan == LR_PLAN_TC ? (ix->d_pad <= 128 ? kTcMaxQ : kTcMaxQ / 2) : kGemvMaxQ;
   lr_status st = compile_filters(ix, f, B, max_q, stage, C);
   if (st != LR_OK) return st;
+  // ks: the K the scan and the selection work with (oversample x K for the
+  // precision form); kf: the K the caller asked for
   int32_t *ks = (int32_t *)(stage + C.off_k);
+  int32_t *kf = (int32_t *)(stage + C.off_kfin);
   for (int b = 0; b < B; ++b) {
     const int kb = k ? k[b] : k_all;
     if (kb < 1 || kb > ix->max_k || kb > k_all)
       return fail(LR_ERR_INVALID, "K must be in [1, min(max_k, k_all)]");
-    ks[b] = kb;
+    kf[b] = kb;
+    ks[b] = lowp ? std::min(kb * ix->oversample, ix->max_kq) : kb;
   }
   // threshold sample plan
   int stride = ix->auto_stride;
@@ -679,6 +731,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   LR_CK(cudaMemsetAsync(ix->state, 0, ix->state_bytes, s));
   LR_CK(cudaMemcpyAsync(ix->kq, ix->filt_d + C.off_k, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
   LR_CK(cudaMemcpyAsync(ix->rank, ix->filt_d + C.off_rank, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  if (lowp)
+    LR_CK(cudaMemcpyAsync(ix->kfin, ix->filt_d + C.off_kfin, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
   const float *qsrc = q;
   if (!is_device_ptr(q)) {
     LR_CK(cudaMemcpyAsync(ix->q_raw, q, sizeof(float) * (size_t)B * ix->dim, cudaMemcpyHostToDevice, s));
@@ -695,6 +749,9 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   auto scan_args = [&](const SubBatch &sb) {
     ScanArgs a{};
     a.X = ix->X;
+    a.Xq = ix->Xq;
+    a.xscale = ix->xscale;
+    a.elem = ix->elem;
     a.n = ix->n;
     a.d_pad = ix->d_pad;
     a.Q = ix->q_ws;
@@ -778,10 +835,10 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.overflow = ix->ovf;
   fa.k = ix->kq;
   fa.pass_cnt = ix->pass;
-  fa.k_stride = k_all;
-  fa.out_ids = dev_out ? out_ids : ix->o_ids;
-  fa.out_scores = dev_out ? out_scores : ix->o_sc;
-  fa.out_count = dev_out ? out_count : ix->o_cnt;
+  fa.k_stride = lowp ? ix->max_kq : k_all;
+  fa.out_ids = lowp ? ix->c_ids : dev_out ? out_ids : ix->o_ids;
+  fa.out_scores = lowp ? ix->c_sc : dev_out ? out_scores : ix->o_sc;
+  fa.out_count = lowp ? ix->c_cnt : dev_out ? out_count : ix->o_cnt;
   fa.flag = ix->flag;
   fa.n_flagged = ix->n_flag;
   fa.cand_count_out = ix->o_cand;
@@ -825,8 +882,27 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fb.fallback_round = 1;
   fb.force_flag = 0;
   LR_LAUNCH(launch_select(fb, B, s));
+  // 5. precision form: FP32 rescore of the candidates, FP64 re-rank of the near ties
+  if (lowp) {
+    RescoreArgs ra{};
+    ra.X = ix->X;
+    ra.d_pad = ix->d_pad;
+    ra.dim = ix->dim;
+    ra.Q = ix->q_ws;
+    ra.cid = ix->c_ids;
+    ra.ccnt = ix->c_cnt;
+    ra.c_stride = ix->max_kq;
+    ra.k = ix->kfin;
+    ra.k_stride = k_all;
+    ra.out_ids = dev_out ? out_ids : ix->o_ids;
+    ra.out_scores = dev_out ? out_scores : ix->o_sc;
+    ra.out_count = dev_out ? out_count : ix->o_cnt;
+    ra.tie_count = ix->o_ties;
+    ra.err = ix->err;
+    LR_LAUNCH(launch_rescore(ra, B, s));
+  }
 
-  // 5. host outputs and statistics
+  // 6. host outputs and statistics
   bool need_sync = false;
   if (!dev_out) {
     LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
@@ -837,10 +913,11 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (stats) {
     if (stats->n_launches) *stats->n_launches = n_launch;
     if (stats->n_scan_launches) *stats->n_scan_launches = n_scan;
-    struct { void *dst; const void *src; size_t bytes; } cp[3] = {
+    struct { void *dst; const void *src; size_t bytes; } cp[4] = {
         {stats->pass_count, ix->pass, sizeof(int64_t) * B},
         {stats->cand_count, ix->o_cand, sizeof(int32_t) * B},
-        {stats->fallback, ix->o_fb, sizeof(int32_t) * B}};
+        {stats->fallback, ix->o_fb, sizeof(int32_t) * B},
+        {lowp ? stats->rescore_ties : nullptr, ix->o_ties, sizeof(int32_t) * B}};
     for (auto &c : cp) {
       if (!c.dst) continue;
       LR_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, s));

@@ -28,6 +28,9 @@
 //
 // Every mbarrier wait is bounded (ptx.h); a wait that gives up records
 // LR_ERR_TIMEOUT in the error word.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "lr_internal.h"
 #include "ptx.h"
 #include "scan_common.cuh"
@@ -55,9 +58,11 @@ struct WarpLayout {
 
 __host__ __device__ inline size_t w_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline WarpLayout warp_layout(int d_pad, int nq_tmpl, int n_slots, int warps) {
+__host__ __device__ constexpr int elem_bytes(int e) { return e == kElemF32 ? 4 : e == kElemBF16 ? 2 : 1; }
+
+__host__ __device__ inline WarpLayout warp_layout(int d_pad, int esz, int nq_tmpl, int n_slots, int warps) {
   WarpLayout L;
-  L.row_stride = (size_t)d_pad * 4 + 16;  // +16 bytes: the 32 lanes' 16-byte loads hit distinct banks
+  L.row_stride = (size_t)d_pad * esz + 16;  // +16 bytes: the 32 lanes' 16-byte loads hit distinct banks
   L.buf_bytes = 32 * L.row_stride;
   // per-warp region: 2 barriers | meta (row, qmask) x 2 buffers | 2 term tables | 2 row buffers
   L.bars = 0;
@@ -70,7 +75,36 @@ __host__ __device__ inline WarpLayout warp_layout(int d_pad, int nq_tmpl, int n_
   return L;
 }
 
-template <int DP, int NQ>
+// Row element (E) values of one 16-byte chunk as FP32 (exact: BF16 and e4m3
+// values are FP32 values).
+template <int E>
+__device__ __forceinline__ void chunk_to_f32(const uint4 &r, float (&x)[16 / elem_bytes(E)]) {
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+  if constexpr (E == kElemF32) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = __uint_as_float(w[i]);
+  } else if constexpr (E == kElemBF16) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[2 * i] = __uint_as_float(w[i] << 16);
+      x[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const __half2_raw hr =
+            __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+        x[4 * i + 2 * h] = f.x;
+        x[4 * i + 2 * h + 1] = f.y;
+      }
+    }
+  }
+}
+
+template <int DP, int NQ, int E>
 __device__ __forceinline__ void score_batch(const ScanArgs &a, const unsigned char *buf, const uint32_t *meta_row,
                                             const uint32_t *meta_qm, uint32_t n, const float *qs,
                                             const uint64_t (&tq)[NQ], int lane, int top, int shift,
@@ -80,21 +114,31 @@ __device__ __forceinline__ void score_batch(const ScanArgs &a, const unsigned ch
   const bool live = (uint32_t)lane < n;
   const uint32_t row = live ? meta_row[lane] : 0u;
   const uint32_t qm = live ? meta_qm[lane] : 0u;
-  const float *xr = reinterpret_cast<const float *>(buf + (size_t)lane * row_stride);
+  constexpr int kPer = 16 / elem_bytes(E);  // values per 16-byte chunk
+  const unsigned char *xr = buf + (size_t)lane * row_stride;
   float acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
 #pragma unroll 4
-  for (int k = 0; k < DP; k += 4) {
-    const float4 x = *reinterpret_cast<const float4 *>(xr + k);
+  for (int k = 0; k < DP; k += kPer) {
+    float x[kPer];
+    chunk_to_f32<E>(*reinterpret_cast<const uint4 *>(xr + (size_t)k * elem_bytes(E)), x);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      const float4 v = *reinterpret_cast<const float4 *>(qs + q * DP + k);
-      acc[q] = fmaf(x.x, v.x, acc[q]);
-      acc[q] = fmaf(x.y, v.y, acc[q]);
-      acc[q] = fmaf(x.z, v.z, acc[q]);
-      acc[q] = fmaf(x.w, v.w, acc[q]);
+#pragma unroll
+      for (int v4 = 0; v4 < kPer / 4; ++v4) {
+        const float4 v = *reinterpret_cast<const float4 *>(qs + q * DP + k + 4 * v4);
+        acc[q] = fmaf(x[4 * v4 + 0], v.x, acc[q]);
+        acc[q] = fmaf(x[4 * v4 + 1], v.y, acc[q]);
+        acc[q] = fmaf(x[4 * v4 + 2], v.z, acc[q]);
+        acc[q] = fmaf(x[4 * v4 + 3], v.w, acc[q]);
+      }
     }
+  }
+  if constexpr (E == kElemFP8) {  // per-row scale of the e4m3 row
+    const float sc = live ? __ldg(a.xscale + row) : 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] *= sc;
   }
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -122,13 +166,16 @@ __device__ __forceinline__ void score_batch(const ScanArgs &a, const unsigned ch
   }
 }
 
-template <int DP, int NQ>
+template <int DP, int NQ, int E>
 __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int kChunks = DP / 4;  // 16-byte chunks per row
+  constexpr int kRowBytes = DP * elem_bytes(E);
+  constexpr int kChunks = kRowBytes / 16;  // 16-byte chunks per row
   const int warps = blockDim.x >> 5;
-  const WarpLayout L = warp_layout(DP, NQ, a.n_slots, warps);
+  const WarpLayout L = warp_layout(DP, elem_bytes(E), NQ, a.n_slots, warps);
+  const unsigned char *xsrc =
+      reinterpret_cast<const unsigned char *>(E == kElemF32 ? static_cast<const void *>(a.X) : a.Xq);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   unsigned char *wbase = smem + (size_t)warp * L.per_warp;
@@ -198,8 +245,8 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
       if (!mbar_wait(&bar[pb], phase[pb])) ok = false;
       phase[pb] ^= 1u;
       __syncwarp();
-      score_batch<DP, NQ>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs, tq,
-                          lane, top, shift, dmask, L.row_stride);
+      score_batch<DP, NQ, E>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs,
+                             tq, lane, top, shift, dmask, L.row_stride);
       __syncwarp();
     }
     prev = true;
@@ -254,7 +301,8 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
         unsigned char *dst = rows + (size_t)fb * L.buf_bytes;
         for (uint32_t i = lane; i < take * kChunks; i += 32) {
           const uint32_t k = i / kChunks, c = i % kChunks;
-          cp_async16(dst + (size_t)(fill + k) * L.row_stride + c * 16, a.X + (size_t)mrow[fill + k] * DP + c * 4);
+          cp_async16(dst + (size_t)(fill + k) * L.row_stride + c * 16,
+                     xsrc + (size_t)mrow[fill + k] * kRowBytes + (size_t)c * 16);
         }
         fill += take;
         done += take;
@@ -271,8 +319,8 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
     const int pb = fb ^ 1;
     if (!mbar_wait(&bar[pb], phase[pb])) ok = false;
     __syncwarp();
-    score_batch<DP, NQ>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs, tq, lane,
-                        top, shift, dmask, L.row_stride);
+    score_batch<DP, NQ, E>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs, tq,
+                           lane, top, shift, dmask, L.row_stride);
   }
   cp_async_wait_all();
   if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
@@ -297,27 +345,37 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
   }
 }
 
-template <int DP, int NQ>
+template <int DP, int NQ, int E>
 cudaError_t launch_one(const ScanArgs &a, int grid, cudaStream_t s) {
   const size_t budget = 220u * 1024u;
   int warps = 8;
-  while (warps > 1 && warp_layout(DP, NQ, a.n_slots, warps).total > budget) --warps;
-  const WarpLayout L = warp_layout(DP, NQ, a.n_slots, warps);
+  while (warps > 1 && warp_layout(DP, elem_bytes(E), NQ, a.n_slots, warps).total > budget) --warps;
+  const WarpLayout L = warp_layout(DP, elem_bytes(E), NQ, a.n_slots, warps);
   if (L.total > budget) return cudaErrorInvalidValue;
-  auto *fn = k_scan_gemv<DP, NQ>;
+  auto *fn = k_scan_gemv<DP, NQ, E>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
   if (e != cudaSuccess) return e;
   fn<<<grid, warps * 32, L.total, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int DP>
+template <int DP, int E>
 cudaError_t dispatch_nq(const ScanArgs &a, int nq_tmpl, int grid, cudaStream_t s) {
   switch (nq_tmpl) {
-    case 1: return launch_one<DP, 1>(a, grid, s);
-    case 2: return launch_one<DP, 2>(a, grid, s);
-    case 4: return launch_one<DP, 4>(a, grid, s);
-    case 8: return launch_one<DP, 8>(a, grid, s);
+    case 1: return launch_one<DP, 1, E>(a, grid, s);
+    case 2: return launch_one<DP, 2, E>(a, grid, s);
+    case 4: return launch_one<DP, 4, E>(a, grid, s);
+    case 8: return launch_one<DP, 8, E>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int DP>
+cudaError_t dispatch_elem(const ScanArgs &a, int nq_tmpl, int grid, cudaStream_t s) {
+  switch (a.elem) {
+    case kElemF32: return dispatch_nq<DP, kElemF32>(a, nq_tmpl, grid, s);
+    case kElemBF16: return dispatch_nq<DP, kElemBF16>(a, nq_tmpl, grid, s);
+    case kElemFP8: return dispatch_nq<DP, kElemFP8>(a, nq_tmpl, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -326,10 +384,10 @@ cudaError_t dispatch_nq(const ScanArgs &a, int nq_tmpl, int grid, cudaStream_t s
 
 cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s) {
   switch (vec) {
-    case 1: return dispatch_nq<32>(a, nq_tmpl, grid, s);
-    case 2: return dispatch_nq<64>(a, nq_tmpl, grid, s);
-    case 4: return dispatch_nq<128>(a, nq_tmpl, grid, s);
-    case 8: return dispatch_nq<256>(a, nq_tmpl, grid, s);
+    case 1: return dispatch_elem<32>(a, nq_tmpl, grid, s);
+    case 2: return dispatch_elem<64>(a, nq_tmpl, grid, s);
+    case 4: return dispatch_elem<128>(a, nq_tmpl, grid, s);
+    case 8: return dispatch_elem<256>(a, nq_tmpl, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

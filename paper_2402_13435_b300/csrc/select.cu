@@ -213,6 +213,154 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- rescore
+// Precision form: the low-precision scan has gathered each query's top c
+// candidates (c = oversample x K, by the scaled BF16/FP8 score).  Here every
+// candidate is rescored in FP32 from the FP32 copy of its row, and the top K
+// are kept by (FP32 score desc, id asc).  Candidates whose FP32 score lies
+// within w of the K-th FP32 score s_K are re-ranked by an FP64 dot product:
+//   w = max(1e-5 max(|s_K|, 1e-6), 2 g),  g = (d + 8) 2^-24 max_j sum_k |q_k x_jk|
+// g bounds the FP32 rounding error of any candidate's dot product, so every
+// candidate above the band truly outscores every candidate below it, and only
+// the order inside the band needs more precision.  Band members' FP64 scores
+// are reported rounded to FP32 (capped by the last score above the band so the
+// reported scores stay non-increasing).
+constexpr int kRsThreads = 512;
+constexpr int kMaxTie = 1024;
+
+struct TieShared {
+  double s[kMaxTie];
+  int32_t id[kMaxTie];
+  uint32_t n_tie, n_above, gmax_bits;
+};
+
+__global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
+  const int q = blockIdx.x;
+  extern __shared__ __align__(16) uint64_t sbuf[];  // [kMaxK] FP32 keys, then [kMaxK] sort area
+  __shared__ SelShared sh;
+  __shared__ TieShared ts;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int n = a.ccnt[q] < a.c_stride ? a.ccnt[q] : a.c_stride;
+  const int K = a.k[q] < n ? a.k[q] : n;
+  const int32_t *cid = a.cid + (size_t)q * a.c_stride;
+  const float *qv = a.Q + (size_t)q * a.d_pad;
+  uint64_t *keys = sbuf;
+  uint64_t *sortb = sbuf + kMaxK;
+  int32_t *ids = a.out_ids + (size_t)q * a.k_stride;
+  float *sc = a.out_scores + (size_t)q * a.k_stride;
+  if (tid == 0) {
+    ts.n_tie = 0u;
+    ts.n_above = 0u;
+    ts.gmax_bits = 0u;
+  }
+  __syncthreads();
+  // 1. FP32 scores, one warp per candidate (lane-strided partial sums, tree reduction)
+  for (int i = warp; i < n; i += nw) {
+    const int32_t id = cid[i];
+    const float *x = a.X + (size_t)id * a.d_pad;
+    float p = 0.f, m = 0.f;
+    for (int k = lane; k < a.d_pad; k += 32) {
+      const float v = qv[k], xv = x[k];
+      p = fmaf(v, xv, p);
+      m = fmaf(fabsf(v), fabsf(xv), m);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      p += __shfl_xor_sync(0xFFFFFFFFu, p, off);
+      m += __shfl_xor_sync(0xFFFFFFFFu, m, off);
+    }
+    if (lane == 0) {
+      keys[i] = make_key(p, (uint32_t)id);
+      atomicMax(&ts.gmax_bits, __float_as_uint(m));  // non-negative floats order as their bits
+    }
+  }
+  __syncthreads();
+  int n_tie = 0, n_above = 0;
+  float s_above_last = INFINITY;
+  if (K > 0) {
+    // 2. the K-th FP32 key and the near-tie band around it
+    const uint64_t kth = block_kth(keys, n, (uint32_t)K, sh);
+    const float sK = key_score((uint32_t)(kth >> 32));
+    const float g = (float)(a.dim + 8) * 5.9604645e-8f * __uint_as_float(ts.gmax_bits) * 1.0001f;
+    const float w = fmaxf(1e-5f * fmaxf(fabsf(sK), 1e-6f), 2.f * g);
+    for (int i = tid; i < n; i += blockDim.x) {
+      const float si = key_score((uint32_t)(keys[i] >> 32));
+      if (si > sK + w) {
+        const uint32_t pos = atomicAdd(&ts.n_above, 1u);
+        if (pos < (uint32_t)kMaxK) sortb[pos] = keys[i];
+      } else if (si >= sK - w) {
+        const uint32_t t = atomicAdd(&ts.n_tie, 1u);
+        if (t < (uint32_t)kMaxTie) ts.id[t] = (int32_t)key_id(keys[i]);
+      }
+    }
+    __syncthreads();
+    n_above = (int)ts.n_above;
+    const int ties_all = (int)ts.n_tie;
+    n_tie = ties_all < kMaxTie ? ties_all : kMaxTie;
+    // 3. candidates above the band: FP32 order
+    int P2 = 1;
+    while (P2 < n_above) P2 <<= 1;
+    for (int i = n_above + tid; i < P2; i += blockDim.x) sortb[i] = 0ull;
+    __syncthreads();
+    if (n_above > 1) bitonic_desc(sortb, P2);
+    for (int i = tid; i < n_above; i += blockDim.x) {
+      ids[i] = (int32_t)key_id(sortb[i]);
+      sc[i] = key_score((uint32_t)(sortb[i] >> 32));
+    }
+    if (n_above > 0) s_above_last = key_score((uint32_t)(sortb[n_above - 1] >> 32));
+    // 4. the band: FP64 dot products, then (score desc, id asc)
+    if (ties_all > kMaxTie && tid == 0) atomicOr(a.err, 32u);  // band larger than the FP64 re-rank holds
+    for (int t = warp; t < n_tie; t += nw) {
+      const float *x = a.X + (size_t)ts.id[t] * a.d_pad;
+      double p = 0.0;
+      for (int k = lane; k < a.d_pad; k += 32) p = fma((double)qv[k], (double)x[k], p);
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) p += __shfl_xor_sync(0xFFFFFFFFu, p, off);
+      if (lane == 0) ts.s[t] = p;
+    }
+    int T2 = 1;
+    while (T2 < n_tie) T2 <<= 1;
+    for (int i = n_tie + tid; i < T2; i += blockDim.x) {
+      ts.s[i] = -INFINITY;
+      ts.id[i] = 0x7FFFFFFF;
+    }
+    __syncthreads();
+    for (int size = 2; size <= T2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = tid; i < T2 / 2; i += blockDim.x) {
+          const int pos = 2 * i - (i & (stride - 1));
+          const int par = pos + stride;
+          const bool desc = (pos & size) == 0;
+          const double x0 = ts.s[pos], x1 = ts.s[par];
+          const int32_t i0 = ts.id[pos], i1 = ts.id[par];
+          const bool first_better = x0 > x1 || (x0 == x1 && i0 < i1);
+          if (first_better != desc) {
+            ts.s[pos] = x1;
+            ts.s[par] = x0;
+            ts.id[pos] = i1;
+            ts.id[par] = i0;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    const int need = K - n_above;
+    for (int i = tid; i < need; i += blockDim.x) {
+      const bool have = i < n_tie;
+      ids[n_above + i] = have ? ts.id[i] : -1;
+      sc[n_above + i] = have ? fminf((float)ts.s[i], s_above_last) : -INFINITY;
+    }
+  }
+  for (int i = K + tid; i < a.k_stride; i += blockDim.x) {
+    ids[i] = -1;
+    sc[i] = -INFINITY;
+  }
+  if (tid == 0) {
+    if (a.out_count) a.out_count[q] = K;
+    if (a.tie_count) a.tie_count[q] = n_tie;
+  }
+}
+
 // Fallback set-up: for flagged queries start the radix selection of the
 // min(K, #passing)-th key from an empty prefix and clear the candidate buffer.
 __global__ void k_fallback_prepare(const unsigned long long *pass_cnt, const int32_t *k, const uint32_t *flag,
@@ -244,6 +392,15 @@ cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_select<<<B, kSelThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const size_t smem = (size_t)2 * kMaxK * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(k_rescore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_rescore<<<B, kRsThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,14 @@ def test_invalid_arguments_fail_before_any_device_work(lib_path):
         lr.lr_index_create(np.zeros((10, 300), dtype=np.float32), 8, bitsets=np.zeros((10, 1), dtype=np.uint64))
     assert e.value.status == lr.LR_ERR_UNSUPPORTED
     assert "dim" in lr.lr_last_error_message()
+    bits = np.zeros((10, 1), dtype=np.uint64)
+    with pytest.raises(lr.LRError) as e:  # precision form: oversample * max_k must fit the selection
+        lr.lr_index_create(emb, 8, bitsets=bits, max_k=2000, dtype="fp8", oversample=4)
+    assert e.value.status == lr.LR_ERR_INVALID
+    assert "oversample" in lr.lr_last_error_message()
+    with pytest.raises(lr.LRError) as e:  # the plain form ignores oversample
+        lr.lr_index_create(emb, 8, bitsets=bits, max_k=5000, dtype="f32", oversample=4)
+    assert "max_k" in lr.lr_last_error_message()
 
 
 def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
