@@ -145,6 +145,8 @@ struct lr_index {
   // TMA descriptor of X for the tensor-core plan (128 rows x 32 floats, 128-byte swizzle)
   alignas(64) CUtensorMap tmap_x;
   bool have_tmap = false;
+  alignas(64) CUtensorMap tmap_xq;  // low-precision rows (precision form)
+  bool have_tmap_q = false;
 };
 
 namespace {
@@ -199,6 +201,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
       cudaGetLastError();
   }
   return fn;
+}
+
+// TMA descriptor of the low-precision rows: 128-row tiles of 64 values, BF16
+// with the 128-byte swizzle (128-byte rows), e4m3 as bytes with the 64-byte
+// swizzle (64-byte rows).  Needs d_pad >= 64.
+bool make_xq_tensor_map(lr_index *ix) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ix->elem == kElemF32 || ix->d_pad < 64 || ix->n >= (int64_t(1) << 31)) return false;
+  const bool bf = ix->elem == kElemBF16;
+  const cuuint64_t dims[2] = {(cuuint64_t)ix->d_pad, (cuuint64_t)ix->n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ix->d_pad * (bf ? 2u : 1u)};
+  const cuuint32_t box[2] = {64u, 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(&ix->tmap_xq, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ix->Xq, dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool make_x_tensor_map(lr_index *ix) {
@@ -535,6 +554,7 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   if (e & 1u) return cleanup(fail(LR_ERR_INVALID, "non-finite value in the job embeddings"));
   if (e & 4u) return cleanup(fail(LR_ERR_INVALID, "posting list names a job id >= n_jobs"));
   ix->have_tmap = make_x_tensor_map(ix);
+  ix->have_tmap_q = make_xq_tensor_map(ix);
   *out = ix;
   return LR_OK;
 #undef CK2
@@ -692,11 +712,11 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // (3xTF32) once a launch serves enough queries to be a real contraction
   int plan = o.plan;
   const bool lowp = ix->elem != kElemF32;
-  if (plan == LR_PLAN_AUTO) plan = (B >= kTcMinBatch && !lowp) ? LR_PLAN_TC : LR_PLAN_GEMV;
-  if (plan == LR_PLAN_TC && lowp)
-    return fail(LR_ERR_UNSUPPORTED, "the tensor-core plan reads FP32 rows only; use the GEMV plan");
-  if (plan == LR_PLAN_TC && !ix->have_tmap)
-    return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable (no TMA descriptor for this index)");
+  const bool tc_ok = lowp ? ix->have_tmap_q : ix->have_tmap;
+  if (plan == LR_PLAN_AUTO) plan = (B >= kTcMinBatch && tc_ok) ? LR_PLAN_TC : LR_PLAN_GEMV;
+  if (plan == LR_PLAN_TC && !tc_ok)
+    return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable for this index (no TMA descriptor; "
+                                    "low-precision rows need dim > 32)");
   const int max_q = plan == LR_PLAN_TC ? (ix->d_pad <= 128 ? kTcMaxQ : kTcMaxQ / 2) : kGemvMaxQ;
   lr_status st = compile_filters(ix, f, B, max_q, stage, C);
   if (st != LR_OK) return st;
@@ -781,7 +801,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ix->num_sms));
   };
   auto launch_scan = [&](const ScanArgs &a, int64_t groups) {
-    return plan == LR_PLAN_TC ? launch_scan_tc(a, &ix->tmap_x, grid_for(groups), s)
+    return plan == LR_PLAN_TC ? launch_scan_tc(a, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(groups), s)
                               : launch_scan_gemv(a, nq_tmpl(a.nq), vec, grid_for(groups), s);
   };
 

@@ -36,6 +36,8 @@
 // producer lets issued copies land, the MMA warp waits for its MMAs, and the
 // tensor memory is freed before the CTA exits.
 #include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "lr_internal.h"
 #include "ptx.h"
@@ -49,7 +51,13 @@ constexpr int kConvWarp0 = 2;
 constexpr int kEpiWarp0 = 6;
 constexpr int kMetaDepth = 4;
 constexpr int kTileRows = 128;
-constexpr int kChunkBytes = kTileRows * 128;  // one 32-float column block of a tile
+constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile of 128-byte rows
+
+// Row elements per raw chunk and the bytes of a chunk's row: FP32 rows come in
+// 32-float (128-byte) column blocks; BF16 in 64-value (128-byte) blocks; FP8
+// e4m3 in 64-value (64-byte) blocks.
+__host__ __device__ constexpr int tc_epc(int e) { return e == kElemF32 ? 32 : 64; }
+__host__ __device__ constexpr int tc_row_bytes(int e) { return e == kElemFP8 ? 64 : 128; }
 constexpr int kTcGroupChunk = 2;              // groups per work-counter grab
 constexpr int kWarpCand = 512;                // candidates staged per epilogue warp (flushed past 256)
 constexpr int kABufs = 4;                     // x_hi/x_lo chunk buffers in tensor memory
@@ -65,22 +73,23 @@ struct TileMeta {
 };
 
 struct TcLayout {
-  int S, C, N;
+  int S, C, C32, N;
   size_t raw, q, meta, slots, taus, cand, ccnt, cq, bars, holder, total;
 };
 
 __host__ __device__ inline size_t tc_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int d_pad, int N, int n_slots, int S) {
+__host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int n_slots, int S) {
   TcLayout T;
   T.S = S;
-  T.C = d_pad / 32;
+  T.C = d_pad / epc;   // raw chunks per tile
+  T.C32 = d_pad / 32;  // 32-value chunks of the query operand
   T.N = N;
   size_t off = 0;
   T.raw = off;
   off += (size_t)S * kChunkBytes;
   T.q = off;  // per chunk: 2N rows (N rows of q_hi, then N rows of q_lo), 128 bytes each
-  off += (size_t)T.C * 2 * N * 128;
+  off += (size_t)T.C32 * 2 * N * 128;
   T.meta = tc_align(off, 16);
   off = T.meta + (size_t)kMetaDepth * sizeof(TileMeta);
   T.slots = tc_align(off, 16);
@@ -122,15 +131,16 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
   return __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
 }
 
-template <int N>
+template <int N, int E>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned for the swizzle atoms
-  const TcLayout T = tc_layout(a.d_pad, N, a.n_slots, S);
+  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, a.n_slots, S);
   const int C = T.C;
+  const int C32 = T.C32;
   unsigned char *raw = smem + T.raw;
   float *qop = reinterpret_cast<float *>(smem + T.q);
   TileMeta *meta = reinterpret_cast<TileMeta *>(smem + T.meta);
@@ -170,7 +180,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     fence_mbar_init();
   }
   // queries of the launch in the K-major 128-byte swizzle layout, split into hi/lo
-  for (int i = threadIdx.x; i < C * N * 32; i += blockDim.x) {
+  for (int i = threadIdx.x; i < C32 * N * 32; i += blockDim.x) {
     const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
     const float v = r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 32 + k] : 0.f;
     const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
@@ -295,8 +305,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           if (lane == 0) {
-            mbar_arrive_expect_tx(&raw_full[s], (uint32_t)kChunkBytes);
-            tma_load_2d(raw + (size_t)s * kChunkBytes, &tmap, c * 32, (int)row0, &raw_full[s]);
+            mbar_arrive_expect_tx(&raw_full[s], (uint32_t)(kTileRows * tc_row_bytes(E)));
+            tma_load_2d(raw + (size_t)s * kChunkBytes, &tmap, c * tc_epc(E), (int)row0, &raw_full[s]);
           }
           ++pr;
         }
@@ -355,13 +365,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           tc_fence_after();
           const uint32_t ah = tmem_base + acol0 + (uint32_t)(l * 64), al = ah + 32u;
-          const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
+          if constexpr (E == kElemF32) {
+            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            // D[0,2N) += x_hi . [q_hi ; q_lo]^T, then D[0,N) += x_lo . q_hi^T
-            mma_tf32_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc2,
-                            (c | ks) != 0 ? 1u : 0u);
-            mma_tf32_tmem_a(d, al + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc1, 1u);
+            for (int ks = 0; ks < 4; ++ks) {
+              // D[0,2N) += x_hi . [q_hi ; q_lo]^T, then D[0,N) += x_lo . q_hi^T
+              mma_tf32_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc2,
+                              (c | ks) != 0 ? 1u : 0u);
+              mma_tf32_tmem_a(d, al + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc1, 1u);
+            }
+          } else {
+            // BF16 / e4m3 values are exact in TF32: one MMA per 8-wide K step,
+            // D[0,2N) += x . [q_hi ; q_lo]^T over the chunk's 64 values (two
+            // 32-value chunks of the query operand)
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+              const uint32_t qa = smem_u32(qop) + (uint32_t)((2 * c + (ks >> 2)) * 2 * N * 128) +
+                                  (uint32_t)(ks & 3) * 32u;
+              mma_tf32_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa), idesc2, (c | ks) != 0 ? 1u : 0u);
+            }
+            (void)al;
+            (void)idesc1;
           }
           issued = true;
           mma_commit(&a_empty[l]);
@@ -397,17 +421,49 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           ok = false;
           break;
         }
-        uint32_t hi[32], lo[32];
-        const unsigned char *rowp = raw + (size_t)s * kChunkBytes + (size_t)r * 128;
+        uint32_t hi[32], lo[32];  // FP32 rows: x_hi, x_lo; BF16/FP8 rows: values 0-31, 32-63
+        const unsigned char *rowp = raw + (size_t)s * kChunkBytes + (size_t)r * tc_row_bytes(E);
+        if constexpr (E == kElemF32) {
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {  // 16-byte chunk cc of the row sits at slot cc ^ (r % 8)
-          const float4 v = *reinterpret_cast<const float4 *>(rowp + (((cc ^ (r & 7)) & 7) << 4));
-          const float e[4] = {v.x, v.y, v.z, v.w};
+          for (int cc = 0; cc < 8; ++cc) {  // 16-byte chunk cc of the row sits at slot cc ^ (r % 8)
+            const float4 v = *reinterpret_cast<const float4 *>(rowp + (((cc ^ (r & 7)) & 7) << 4));
+            const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t hb = __float_as_uint(e[u]) & 0xFFFFE000u;
-            hi[cc * 4 + u] = hb;
-            lo[cc * 4 + u] = __float_as_uint(e[u] - __uint_as_float(hb));
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t hb = __float_as_uint(e[u]) & 0xFFFFE000u;
+              hi[cc * 4 + u] = hb;
+              lo[cc * 4 + u] = __float_as_uint(e[u] - __uint_as_float(hb));
+            }
+          }
+        } else if constexpr (E == kElemBF16) {
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {  // 128-byte swizzle: 8 values per 16-byte chunk
+            const uint4 v = *reinterpret_cast<const uint4 *>(rowp + (((cc ^ (r & 7)) & 7) << 4));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            uint32_t *dst = cc < 4 ? hi : lo;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              dst[(cc & 3) * 8 + 2 * u] = w[u] << 16;
+              dst[(cc & 3) * 8 + 2 * u + 1] = w[u] & 0xFFFF0000u;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {  // 64-byte swizzle: chunk cc of row r at slot cc ^ ((r / 2) % 4)
+            const uint4 v = *reinterpret_cast<const uint4 *>(rowp + (((cc ^ (r >> 1)) & 3) << 4));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            uint32_t *dst = cc < 2 ? hi : lo;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const __half2_raw hr =
+                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[u] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+                dst[(cc & 1) * 16 + 4 * u + 2 * h] = __float_as_uint(f.x);
+                dst[(cc & 1) * 16 + 4 * u + 2 * h + 1] = __float_as_uint(f.y);
+              }
+            }
           }
         }
         __syncwarp();
@@ -501,6 +557,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 2 * N);
       const uint64_t qmask = meta[m].qm[quarter * 32 + lane];
       const uint32_t grow = (uint32_t)(meta[m].row0 + quarter * 32 + lane);
+      float xs = 1.f;  // FP8 rows: score = scale * <q, x8>
+      if constexpr (E == kElemFP8) xs = (int64_t)grow < a.n ? __ldg(a.xscale + grow) : 0.f;
 #pragma unroll 1
       for (int j = 0; j < N / 16; ++j) {
         const uint32_t bm = (uint32_t)(qmask >> (16 * j)) & 0xFFFFu;
@@ -525,7 +583,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int b = 4 * v + u;
-              sc[b] = __uint_as_float(rh[b]) + __uint_as_float(rl[b]);
+              sc[b] = (__uint_as_float(rh[b]) + __uint_as_float(rl[b])) * xs;
               hit |= (sc[b] >= tt[u] ? 1u : 0u) << b;
             }
           }
@@ -555,7 +613,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int b = 0; b < 16; ++b) {
             if (!((bm >> b) & 1u)) continue;
             const int q = 16 * j + b;
-            const uint64_t key = make_key(__uint_as_float(rh[b]) + __uint_as_float(rl[b]), grow);
+            const uint64_t key = make_key((__uint_as_float(rh[b]) + __uint_as_float(rl[b])) * xs, grow);
             if (top >= 64 || (key >> top) == (taus[q] >> top))
               atomicAdd(&a.hist[(size_t)(a.q_base + q) * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
           }
@@ -597,15 +655,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-template <int N>
+template <int N, int E>
 cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cudaStream_t s) {
   static_assert(4 * N + 64 * kABufs <= (int)kTmemCols, "tensor memory budget");
   const size_t budget = 220u * 1024u;
   int S = 12;
-  while (S > 2 && tc_layout(a.d_pad, N, a.n_slots, S).total + 1024 > budget) --S;
-  const TcLayout T = tc_layout(a.d_pad, N, a.n_slots, S);
+  if (a.d_pad % tc_epc(E) != 0) return cudaErrorInvalidValue;
+  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, a.n_slots, S).total + 1024 > budget) --S;
+  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, a.n_slots, S);
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
-  auto *fn = k_scan_tc<N>;
+  auto *fn = k_scan_tc<N, E>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(T.total + 1024));
   if (e != cudaSuccess) return e;
   fn<<<grid, kTcThreads, T.total + 1024, s>>>(a, tmap, S);
@@ -617,11 +676,19 @@ cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cuda
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s) {
   const CUtensorMap &tm = *static_cast<const CUtensorMap *>(tmap_x);
   const int n16 = (a.nq + 15) / 16 * 16;
-  switch (n16) {
-    case 16: return launch_tc<16>(a, tm, grid, s);
-    case 32: return launch_tc<32>(a, tm, grid, s);
-    case 48: return launch_tc<48>(a, tm, grid, s);
-    case 64: return launch_tc<64>(a, tm, grid, s);
+  switch (a.elem * 4 + n16 / 16 - 1) {
+    case kElemF32 * 4 + 0: return launch_tc<16, kElemF32>(a, tm, grid, s);
+    case kElemF32 * 4 + 1: return launch_tc<32, kElemF32>(a, tm, grid, s);
+    case kElemF32 * 4 + 2: return launch_tc<48, kElemF32>(a, tm, grid, s);
+    case kElemF32 * 4 + 3: return launch_tc<64, kElemF32>(a, tm, grid, s);
+    case kElemBF16 * 4 + 0: return launch_tc<16, kElemBF16>(a, tm, grid, s);
+    case kElemBF16 * 4 + 1: return launch_tc<32, kElemBF16>(a, tm, grid, s);
+    case kElemBF16 * 4 + 2: return launch_tc<48, kElemBF16>(a, tm, grid, s);
+    case kElemBF16 * 4 + 3: return launch_tc<64, kElemBF16>(a, tm, grid, s);
+    case kElemFP8 * 4 + 0: return launch_tc<16, kElemFP8>(a, tm, grid, s);
+    case kElemFP8 * 4 + 1: return launch_tc<32, kElemFP8>(a, tm, grid, s);
+    case kElemFP8 * 4 + 2: return launch_tc<48, kElemFP8>(a, tm, grid, s);
+    case kElemFP8 * 4 + 3: return launch_tc<64, kElemFP8>(a, tm, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -41,9 +41,10 @@ def corpus():
     return datagen.corpus(5, 120_000, 128, 4096, 20.0, 1.1)
 
 
-@pytest.mark.parametrize("dtype,dim", [("bf16", 128), ("fp8", 64), ("fp8", 128)])
+@pytest.mark.parametrize("plan", ["gemv", "tc"])
+@pytest.mark.parametrize("dtype,dim", [("bf16", 128), ("fp8", 64), ("fp8", 128), ("bf16", 64)])
 @pytest.mark.parametrize("metric", ["cosine", "dot"])
-def test_precision_recall_and_scores(lr, corpus, dtype, dim, metric):
+def test_precision_recall_and_scores(lr, corpus, dtype, dim, metric, plan):
     c = corpus
     X = np.ascontiguousarray(c.X[:, :dim])
     po, pid = c.postings()
@@ -53,7 +54,7 @@ def test_precision_recall_and_scores(lr, corpus, dtype, dim, metric):
     idx = lr.lr_index_create(X, c.V, post_off=po, post_ids=pid, n_dense_terms=128, metric=metric, max_batch=16,
                              max_k=256, dtype=dtype, oversample=4)
     try:
-        ids, sc, cnt, st = _run(lr, idx, Q, f, K, stats=True)
+        ids, sc, cnt, st = _run(lr, idx, Q, f, K, stats=True, plan=plan)
     finally:
         lr.lr_index_destroy(idx)
     ref = oracle.search(X, c.job_off, c.job_terms, Q, f, K, metric=metric)
@@ -77,17 +78,19 @@ def test_precision_dyadic_is_exact(lr):
         idx = lr.lr_index_create(X, V, bitsets=datagen.bitsets(n, V, off, terms), metric="dot", max_batch=16,
                                  max_k=256, dtype=dtype)
         try:
-            ids, sc, cnt = _run(lr, idx, Q, f, K)
+            for plan in ("gemv", "tc"):
+                ids, sc, cnt = _run(lr, idx, Q, f, K, plan=plan)
+                assert np.array_equal(cnt, ref.count), (dtype, plan)
+                for b in range(B):
+                    k = cnt[b]
+                    assert np.array_equal(ids[b, :k], ref.ids[b, :k]), (dtype, plan, b)
+                    assert np.array_equal(sc[b, :k].astype(np.float64), ref.scores[b, :k]), (dtype, plan, b)
         finally:
             lr.lr_index_destroy(idx)
-        assert np.array_equal(cnt, ref.count), dtype
-        for b in range(B):
-            k = cnt[b]
-            assert np.array_equal(ids[b, :k], ref.ids[b, :k]), (dtype, b)
-            assert np.array_equal(sc[b, :k].astype(np.float64), ref.scores[b, :k]), (dtype, b)
 
 
-def test_precision_alone_and_in_a_batch_give_identical_rows(lr, corpus):
+@pytest.mark.parametrize("plan", ["gemv", "tc"])
+def test_precision_alone_and_in_a_batch_give_identical_rows(lr, corpus, plan):
     c = corpus
     X = np.ascontiguousarray(c.X[:, :64])
     B, K = 6, 50
@@ -95,10 +98,10 @@ def test_precision_alone_and_in_a_batch_give_identical_rows(lr, corpus):
     Q = datagen.query_embeddings(42, B, 64)
     idx = lr.lr_index_create(X, c.V, bitsets=c.bitsets(), metric="cosine", max_batch=8, max_k=128, dtype="fp8")
     try:
-        ids, sc, cnt = _run(lr, idx, Q, f, K)
+        ids, sc, cnt = _run(lr, idx, Q, f, K, plan=plan)
         for b in range(B):
             fb = f.subset([b])
-            i1, s1, c1 = _run(lr, idx, Q[b:b + 1], fb, K)
+            i1, s1, c1 = _run(lr, idx, Q[b:b + 1], fb, K, plan=plan)
             assert c1[0] == cnt[b]
             assert np.array_equal(i1[0], ids[b]) and np.array_equal(s1[0], sc[b]), b
     finally:
