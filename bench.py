@@ -25,7 +25,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BANDS = (0.001, 0.01, 0.10, 0.50)
 METRIC = "filtered top-K QPS @10M×128 vs plain FP32; HBM GB/s % of peak; p99 ms"
 
 
@@ -45,7 +44,17 @@ def parse():
     p.add_argument("--cpu-queries", type=int, default=8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    return p.parse_args()
+    # workload shape (defaults: the plain method at scale); the precision form of the same study is
+    # e.g. --n 50000000 --dim 64 --vocab 4096 --lam 20 --bands 0.01,0.1 --batch 1024 --dtype fp8
+    p.add_argument("--dtype", choices=("f32", "bf16", "fp8"), default="f32")
+    p.add_argument("--oversample", type=int, default=4)
+    p.add_argument("--vocab", type=int, default=16384)
+    p.add_argument("--lam", type=float, default=40.0)
+    p.add_argument("--n-dense", type=int, default=256)
+    p.add_argument("--bands", default="0.001,0.01,0.1,0.5")
+    a = p.parse_args()
+    a.band_list = tuple(float(x) for x in a.bands.split(","))
+    return a
 
 
 # ----------------------------------------------------------------------------- workload
@@ -53,16 +62,17 @@ def make_workload(args, rank=0):
     import datagen
 
     t0 = time.time()
-    c = datagen.corpus(args.seed, args.n, args.dim, 16384, 40.0, 1.1)
+    c = datagen.corpus(args.seed, args.n, args.dim, args.vocab, args.lam, 1.1)
     po, pid = c.postings()
-    per = max(1, args.batch // len(BANDS))
+    bands = args.band_list
+    per = max(1, args.batch // len(bands))
     nb = args.n_batches
     band_f = [datagen.filters_in_band(args.seed + 1000 * rank, per * nb, c.V, 1.1, c.df, c.n, s,
-                                      stream_offset=(i + 1) * 100_000_000) for i, s in enumerate(BANDS)]
+                                      stream_offset=(i + 1) * 100_000_000) for i, s in enumerate(bands)]
     batches = []
     for j in range(nb):
         qs = []
-        for i in range(len(BANDS)):
+        for i in range(len(bands)):
             sub = band_f[i].subset(range(j * per, (j + 1) * per))
             qs.extend(sub.clauses(b) for b in range(sub.n))
         qs = qs[: args.batch] + qs[: max(0, args.batch - len(qs))]
@@ -72,12 +82,25 @@ def make_workload(args, rank=0):
                 gen_s=time.time() - t0)
 
 
+def row_bytes(args):
+    """Bytes the scan reads per job row: d_pad values of the stored type (+ the FP8 row scale)."""
+    d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
+    return d_pad * {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype] + (4 if args.dtype == "fp8" else 0)
+
+
 def workload_config(args):
-    return {"workload": "filtered top-K, N=%d jobs x d=%d FP32 cosine, V=16384 Poisson(40) Zipf(1.1) terms as "
-                        "posting lists + 256 dense bitmaps, batch %d (bands 0.1/1/10/50%%), K=%d"
-                        % (args.n, args.dim, args.batch, args.k),
-            "n_jobs": args.n, "dim": args.dim, "batch": args.batch, "k": args.k, "vocab": 16384,
-            "selectivity_bands": list(BANDS), "l2": "inputs larger than L2 (5.12 GB embeddings), no flush"}
+    form = {"f32": "FP32", "bf16": "BF16 rows + FP32 rescore", "fp8": "FP8 e4m3 rows + row scale + FP32 rescore"}
+    gb = args.n * row_bytes(args) / 1e9
+    cfg = {"workload": "filtered top-K, N=%d jobs x d=%d %s cosine, V=%d Poisson(%g) Zipf(1.1) terms as "
+                       "posting lists + %d dense bitmaps, batch %d (bands %s), K=%d"
+                       % (args.n, args.dim, form[args.dtype], args.vocab, args.lam, args.n_dense, args.batch,
+                          "/".join("%g%%" % (100 * b) for b in args.band_list), args.k),
+           "n_jobs": args.n, "dim": args.dim, "batch": args.batch, "k": args.k, "vocab": args.vocab,
+           "selectivity_bands": list(args.band_list), "rows": args.dtype,
+           "l2": "inputs larger than L2 (%.2f GB of scanned rows), no flush" % gb}
+    if args.dtype != "f32":
+        cfg["oversample"] = args.oversample
+    return cfg
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -198,6 +221,8 @@ def scan_plan(args):
     matrix-vector scan below that, 8 per launch)."""
     d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
     plan = args.plan if args.plan != "auto" else ("tc" if args.batch >= 16 else "gemv")
+    if plan == "tc" and args.dtype != "f32" and d_pad < 64:
+        plan = "gemv"  # low-precision rows reach the tensor cores from 64 values up
     if plan == "tc":
         return "k_scan_tc", (64 if d_pad <= 128 else 32), d_pad
     return "k_scan_gemv", 8, d_pad
@@ -216,7 +241,7 @@ def measured_traffic(args):
             digest = hashlib.sha256(fh.read()).hexdigest()
     except (OSError, KeyError, ValueError):
         return None
-    if digest != rec["source_sha256"] or (args.n, args.dim, args.batch) != (10_000_000, 128, 32):
+    if digest != rec["source_sha256"] or (args.n, args.dim, args.batch, args.dtype) != (10_000_000, 128, 32, "f32"):
         return None
     return float(rec["traffic_per_launch_10M"])
 
@@ -227,6 +252,7 @@ def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
     import torch
 
     _, per, d_pad = scan_plan(args)
+    rb = row_bytes(args)
     n = corpus.n
     df = corpus.df
     per_launch = []
@@ -241,7 +267,7 @@ def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
         rows = int(np.unpackbits(words.view(np.uint8)).sum())
         terms = {int(t) for t in sub.terms}
         p = sum(min(n / 8.0, 4.0 * float(df[t])) for t in terms)
-        per_launch.append(rows * d_pad * 4 + p)
+        per_launch.append(rows * rb + p)
     return per_launch
 
 
@@ -322,7 +348,8 @@ def run_ours(args):
     c = wl["corpus"]
     t0 = time.time()
     idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), c.V, post_off=wl["post_off"], post_ids=wl["post_ids"],
-                             n_dense_terms=256, metric="cosine", max_batch=max(args.batch, 32), max_k=args.k)
+                             n_dense_terms=args.n_dense, metric="cosine", max_batch=max(args.batch, 32),
+                             max_k=args.k, dtype=args.dtype, oversample=args.oversample)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     nb = len(wl["filters"])
@@ -427,12 +454,21 @@ def run_ours(args):
         step(0)
         torch.cuda.synchronize()
         ids, sc, cnt = out_ids.cpu().numpy(), out_sc.cpu().numpy(), out_cnt.cpu().numpy()
+        import oracle
+
+        rec = oracle.recall_at_k([ids[b, :cnt[b]] for b in sel], [ref.ids[i, :ref.count[i]] for i in range(len(sel))])
+        err = 0.0
+        for i, b in enumerate(sel):
+            m = min(int(cnt[b]), int(ref.count[i]))
+            if m:
+                err = max(err, float(np.max(np.abs(sc[b, :m].astype(np.float64) - ref.scores[i, :m]))))
         try:
             moved = check_topk(ids, sc, cnt, ref, c.X, wl["Q"][0], c.job_off, c.job_terms, wl["filters"][0],
                                queries=sel)
             parity = {"queries": len(sel), "ok": True, "id_positions_in_tie_band": moved}
         except AssertionError as e:
             parity = {"queries": len(sel), "ok": False, "error": str(e)[:300]}
+        parity.update({"recall_at_k": rec, "max_abs_score_err_vs_fp64": err})
         cpu = {"value": len(sel) / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
                "sample": "first %d queries of batch 0 over the full %d-job index (%.1f s)" % (len(sel), args.n, dt)}
 
