@@ -248,6 +248,39 @@ lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64
  * device for this index (LR_ERR_TIMEOUT for a bounded wait that gave up). */
 lr_status lr_index_sync(lr_index *index, void *stream);
 
+/*
+ * Masked in-batch / sampled softmax loss of the two towers (Sec. 5.1, Eq. 1
+ * and Eq. 2) and its gradients, on the tensor cores (BF16 operands, FP32
+ * accumulation), recomputing the B x M logits instead of storing them.
+ *
+ *   z_ij  = inv_tau <Q_i, J_j> for j allowed for query i: bit j of row i of
+ *           mask_bits is set (the job meets the query's term constraint), or
+ *           j = pos[i] (the positive is always allowed); other columns are
+ *           excluded from the softmax (logit -inf).
+ *   loss  = (1/B) sum_i ( log sum_{j allowed} exp z_ij  -  z_i,pos[i] )
+ *   lse   = [B] the log-sum-exp of each row, saved for the backward pass.
+ *   dQ    = d loss / dQ [B][d] FP32,  dJ = d loss / dJ [M][d] FP32, scaled by
+ *           *dloss (NULL: 1).
+ *
+ *   Q [B][d], J [M][d] row-major, dtype LR_BF16 (used as is) or LR_F32 (rounded
+ *   to BF16 first); 1 <= d <= 128.  pos [B] int32 in [0, M).  mask_bits
+ *   [B][ceil(M/32)] uint32, or NULL (every column allowed).  All pointers are
+ *   device memory; workspace holds lr_score_workspace_size(B, M, d) bytes and
+ *   is owned by the caller (nothing is allocated).  Stream-ordered and
+ *   asynchronous; a positive outside [0, M) makes the loss NaN; a timed-out
+ *   device wait is reported by lr_score_status.
+ */
+size_t lr_score_workspace_size(int32_t B, int32_t M, int32_t d);
+lr_status lr_score_forward(const void *Q, const void *J, int32_t B, int32_t M, int32_t d, int32_t dtype,
+                           const int32_t *pos, const uint32_t *mask_bits, float inv_tau, float *loss, float *lse,
+                           void *workspace, size_t workspace_bytes, void *stream);
+lr_status lr_score_backward(const void *Q, const void *J, int32_t B, int32_t M, int32_t d, int32_t dtype,
+                            const int32_t *pos, const uint32_t *mask_bits, float inv_tau, const float *lse,
+                            const float *dloss, float *dQ, float *dJ, void *workspace, size_t workspace_bytes,
+                            void *stream);
+/* Synchronise `stream` and report (then clear) a device wait timeout of the last loss call on `workspace`. */
+lr_status lr_score_status(void *workspace, int32_t B, int32_t M, int32_t d, void *stream);
+
 /* Human-readable description of the calling thread's last failure. */
 const char *lr_last_error_message(void);
 

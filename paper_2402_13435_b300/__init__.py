@@ -324,3 +324,120 @@ def lr_search_noalloc(X, q, k: int, *, pass_bitmap=None, out_ids, out_scores, ou
     stride = int(pass_bitmap.shape[1]) if pass_bitmap is not None else 0
     _check(_lib.lr_search_noalloc(_ptr(X), n, dim, _ptr(q), B, _ptr(pass_bitmap), stride, int(k), _ptr(out_ids),
                                   _ptr(out_scores), _ptr(out_count), _stream_ptr(stream)), "lr_search_noalloc")
+
+
+# ----------------------------------------------------------------------------- loss (Sec. 5.1, Eq. 1-2)
+_vp, _i32 = ctypes.c_void_p, ctypes.c_int32
+_lib.lr_score_workspace_size.argtypes = [_i32, _i32, _i32]
+_lib.lr_score_workspace_size.restype = ctypes.c_size_t
+_lib.lr_score_forward.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, ctypes.c_float, _vp, _vp, _vp,
+                                  ctypes.c_size_t, _vp]
+_lib.lr_score_forward.restype = ctypes.c_int
+_lib.lr_score_backward.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _vp,
+                                   _vp, ctypes.c_size_t, _vp]
+_lib.lr_score_backward.restype = ctypes.c_int
+_lib.lr_score_status.argtypes = [_vp, _i32, _i32, _i32, _vp]
+_lib.lr_score_status.restype = ctypes.c_int
+_DT = {"torch.bfloat16": LR_BF16, "torch.float32": LR_F32}
+
+
+def pack_mask(allowed):
+    """Bool [B][M] (True: the job meets the query's term constraint) -> uint32 words [B][ceil(M/32)] as int32,
+    bit j % 32 of word j // 32."""
+    import torch
+
+    B, M = allowed.shape
+    W = (M + 31) // 32
+    pad = torch.zeros((B, W * 32), dtype=torch.bool, device=allowed.device)
+    pad[:, :M] = allowed
+    w = pad.view(B, W, 32).to(torch.int64) << torch.arange(32, device=allowed.device, dtype=torch.int64)
+    w = w.sum(dim=2)
+    return torch.where(w >= 2 ** 31, w - 2 ** 32, w).to(torch.int32).contiguous()
+
+
+def _loss_shapes(Q, J, pos, mask_bits):
+    B, d = int(Q.shape[0]), int(Q.shape[1])
+    M = int(J.shape[0])
+    if int(J.shape[1]) != d or int(pos.shape[0]) != B:
+        raise ValueError("Q [B][d], J [M][d] and pos [B] disagree")
+    if str(Q.dtype) != str(J.dtype) or str(Q.dtype) not in _DT:
+        raise ValueError("Q and J must both be bfloat16 or both float32")
+    if mask_bits is not None and tuple(mask_bits.shape) != (B, (M + 31) // 32):
+        raise ValueError("mask_bits must be [B][ceil(M/32)]")
+    return B, M, d, _DT[str(Q.dtype)]
+
+
+def loss_workspace(B: int, M: int, d: int, device=None):
+    import torch
+
+    n = int(_lib.lr_score_workspace_size(int(B), int(M), int(d)))
+    if n == 0:
+        raise ValueError("unsupported loss shape (d must be in [1, 128])")
+    return torch.empty(n, dtype=torch.uint8, device=device if device is not None else "cuda")
+
+
+def lr_score_forward(Q, J, pos, mask_bits=None, inv_tau: float = 20.0, workspace=None, stream=None):
+    """Masked softmax loss: returns (loss [1] FP32, lse [B] FP32), device tensors."""
+    import torch
+
+    B, M, d, dt = _loss_shapes(Q, J, pos, mask_bits)
+    ws = workspace if workspace is not None else loss_workspace(B, M, d, Q.device)
+    loss = torch.empty(1, dtype=torch.float32, device=Q.device)
+    lse = torch.empty(B, dtype=torch.float32, device=Q.device)
+    _check(_lib.lr_score_forward(_ptr(Q), _ptr(J), B, M, d, dt, _ptr(pos), _ptr(mask_bits), float(inv_tau),
+                                 _ptr(loss), _ptr(lse), _ptr(ws), ws.numel(), _stream_ptr(stream)), "lr_score_forward")
+    return loss, lse
+
+
+def lr_score_backward(Q, J, pos, mask_bits, inv_tau: float, lse, dloss=None, workspace=None, stream=None):
+    """Gradients of the masked softmax loss: returns (dQ [B][d], dJ [M][d]) FP32 device tensors."""
+    import torch
+
+    B, M, d, dt = _loss_shapes(Q, J, pos, mask_bits)
+    ws = workspace if workspace is not None else loss_workspace(B, M, d, Q.device)
+    dQ = torch.empty((B, d), dtype=torch.float32, device=Q.device)
+    dJ = torch.empty((M, d), dtype=torch.float32, device=Q.device)
+    if dloss is not None:
+        dloss = dloss.reshape(1).to(torch.float32).contiguous()
+    _check(_lib.lr_score_backward(_ptr(Q), _ptr(J), B, M, d, dt, _ptr(pos), _ptr(mask_bits), float(inv_tau),
+                                  _ptr(lse), _ptr(dloss), _ptr(dQ), _ptr(dJ), _ptr(ws), ws.numel(),
+                                  _stream_ptr(stream)), "lr_score_backward")
+    return dQ, dJ
+
+
+def lr_score_status(workspace, B: int, M: int, d: int, stream=None) -> None:
+    _check(_lib.lr_score_status(_ptr(workspace), int(B), int(M), int(d), _stream_ptr(stream)), "lr_score_status")
+
+
+def _autograd_function():
+    import torch
+
+    class MaskedSoftmaxLoss(torch.autograd.Function):
+        """Loss of Sec. 5.1 (Eq. 2) with the term-constraint mask; both passes run in the library's kernels."""
+
+        @staticmethod
+        def forward(ctx, Q, J, pos, mask_bits, inv_tau):
+            Q, J = Q.contiguous(), J.contiguous()
+            ws = loss_workspace(Q.shape[0], J.shape[0], Q.shape[1], Q.device)
+            loss, lse = lr_score_forward(Q, J, pos, mask_bits, inv_tau, ws)
+            ctx.save_for_backward(Q, J, pos, lse)
+            ctx.mask_bits, ctx.inv_tau, ctx.ws = mask_bits, inv_tau, ws
+            return loss.reshape(())
+
+        @staticmethod
+        def backward(ctx, g):
+            Q, J, pos, lse = ctx.saved_tensors
+            dQ, dJ = lr_score_backward(Q, J, pos, ctx.mask_bits, ctx.inv_tau, lse, g, ctx.ws)
+            return dQ.to(Q.dtype), dJ.to(J.dtype), None, None, None
+
+    return MaskedSoftmaxLoss
+
+
+def masked_softmax_loss(Q, J, pos, mask_bits=None, inv_tau: float = 20.0):
+    """Differentiable masked in-batch / sampled softmax loss (mean over queries)."""
+    global _MSL
+    try:
+        fn = _MSL
+    except NameError:
+        fn = _MSL = _autograd_function()
+    return fn.apply(Q, J, pos, mask_bits, inv_tau)

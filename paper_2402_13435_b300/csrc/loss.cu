@@ -1,0 +1,458 @@
+// Masked in-batch / sampled softmax loss of the retrieval towers and its
+// gradients on the tensor cores (Sec. 5.1, Eq. 1 and Eq. 2).
+//
+//   z_ij = inv_tau <q_i, j_j>, over the columns j allowed for query i (the job
+//          satisfies the query's term constraint, or j is the query's positive)
+//   L    = (1/B) sum_i ( logsumexp_j z_ij - z_i,pos(i) )
+//   dZ_ij = (dL/B) (softmax_ij - [j = pos(i)]) on allowed columns, 0 elsewhere
+//   dQ = inv_tau dZ J,   dJ = inv_tau dZ^T Q
+//
+// The B x M logits are never stored: every pass recomputes its score tile on
+// the tensor cores (BF16 operands, FP32 accumulation in tensor memory).  One
+// kernel template serves three passes over tiles of a resident 128-row
+// operand R against streamed 64-row tiles of an operand C:
+//   kFwd: R = queries, C = jobs; online log-sum-exp per query row.
+//   kDq:  R = queries, C = jobs; dZ tile -> acc[128 x d] += dZ C, with C's
+//         transposed copy as the K-major B operand.
+//   kDj:  R = jobs, C = queries; the same with dZ^T, acc[128 x d] += dZ^T Q.
+// dZ enters the second product as two BF16 terms (hi + lo, near-FP32 accuracy).
+// Warps 0-3: epilogue (TMEM lane quarters); warp 4: TMA; warp 5: MMA issue.
+// Every wait is bounded; a timeout sets the status word.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "lr_internal.h"
+#include "ptx.h"
+
+namespace lr {
+namespace {
+
+constexpr int kRRows = 128;     // rows of the resident tile
+constexpr int kCRows = 64;      // rows of a streamed tile
+constexpr int kLossThreads = 192;
+constexpr uint32_t kLossTmemCols = 256;  // 2 score tiles of 64 columns + accumulator (<= 128)
+constexpr float kLog2e = 1.4426950408889634f;
+
+enum LossMode : int { kFwd = 0, kDq = 1, kDj = 2 };
+
+struct LossSmem {
+  size_t r, c, ct, dz, bars, holder, total;
+};
+
+__host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
+  LossSmem L;
+  size_t off = 0;
+  L.r = off;
+  off += (size_t)(dp / 64) * kRRows * 128;  // K-blocks of 128 rows x 128 bytes
+  L.c = off;
+  off += (size_t)2 * (dp / 64) * kCRows * 128;
+  L.ct = off;
+  off += mode == kFwd ? 0 : (size_t)2 * dp * 128;  // transposed C tile: dp rows x 64 values
+  L.dz = off;
+  off += mode == kFwd ? 0 : (size_t)2 * 2 * kRRows * 128;  // [buffer][hi, lo] 128 rows x 64 values
+  L.bars = off;
+  off += 16 * 8;
+  L.holder = off;
+  L.total = off + 16;
+  return L;
+}
+
+__device__ __forceinline__ bool wwait(uint64_t *bar, uint32_t parity, int lane) {
+  bool got = true;
+  if (lane == 0) got = mbar_wait(bar, parity);
+  return __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kLossThreads, 1)
+    k_loss(const LossArgs a, const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
+           const __grid_constant__ CUtensorMap tm_ct) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int dp = a.dp;
+  const LossSmem L = loss_smem(dp, MODE);
+  const int KB = dp / 64;  // 64-value K-blocks of the score product
+  unsigned char *sr = smem + L.r;
+  unsigned char *sc = smem + L.c;
+  unsigned char *sct = smem + L.ct;
+  unsigned char *sdz = smem + L.dz;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
+  uint64_t *bar_r = bars, *c_full = bars + 1, *c_empty = bars + 3, *s_full = bars + 5, *s_empty = bars + 7;
+  uint64_t *dz_full = bars + 9, *dz_empty = bars + 11, *acc_full = bars + 13;
+  uint32_t *holder = reinterpret_cast<uint32_t *>(smem + L.holder);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r0 = blockIdx.x * kRRows;
+  const int t0 = blockIdx.y * a.c_per_split;
+  const int T = min(a.c_per_split, a.n_ctiles - t0);  // streamed tiles of this CTA (>= 1 by construction)
+  const size_t c_bytes = (size_t)KB * kCRows * 128;
+  const size_t ct_bytes = (size_t)dp * 128;
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar_r, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&c_full[i], 1);
+      mbar_init(&c_empty[i], 1);
+      mbar_init(&s_full[i], 1);
+      mbar_init(&s_empty[i], 4);
+      mbar_init(&dz_full[i], 4);
+      mbar_init(&dz_empty[i], 1);
+    }
+    mbar_init(acc_full, 1);
+    fence_mbar_init();
+  }
+  if (warp == 5) {
+    tmem_alloc(holder, kLossTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *holder;
+  bool ok = true;
+
+  if (warp == 4) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      int issued = 0;
+      mbar_arrive_expect_tx(bar_r, (uint32_t)(KB * kRRows * 128));
+      for (int kb = 0; kb < KB; ++kb) tma_load_2d(sr + (size_t)kb * kRRows * 128, &tm_r, kb * 64, r0, bar_r);
+      for (int t = 0; t < T && ok; ++t) {
+        const int b = t & 1;
+        if (!mbar_wait(&c_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u)) {
+          ok = false;
+          break;
+        }
+        const int c0 = (t0 + t) * kCRows;
+        mbar_arrive_expect_tx(&c_full[b], (uint32_t)(c_bytes + (MODE == kFwd ? 0 : ct_bytes)));
+        for (int kb = 0; kb < KB; ++kb)
+          tma_load_2d(sc + (size_t)b * c_bytes + (size_t)kb * kCRows * 128, &tm_c, kb * 64, c0, &c_full[b]);
+        if (MODE != kFwd) tma_load_2d(sct + (size_t)b * ct_bytes, &tm_ct, c0, 0, &c_full[b]);
+        issued = t + 1;
+      }
+      if (!ok) {
+        atomicOr(a.status, kErrTimeout);
+        mbar_wait(bar_r, 0u);  // let issued loads land
+        for (int t = issued > 2 ? issued - 2 : 0; t < issued; ++t) mbar_wait(&c_full[t & 1], (uint32_t)((t >> 1) & 1));
+      }
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t id_s = idesc_bf16(kRRows, kCRows), id_g = idesc_bf16(kRRows, dp);
+      const uint32_t acc = tmem + 2u * kCRows;
+      bool issued = false;
+      auto issue_s = [&](int t) -> bool {
+        const int b = t & 1;
+        if (!mbar_wait(&c_full[b], (uint32_t)((t >> 1) & 1))) return false;
+        if (!mbar_wait(&s_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u)) return false;
+        tc_fence_after();
+        const uint32_t ra = smem_u32(sr), ca = smem_u32(sc + (size_t)b * c_bytes);
+        for (int k = 0; k < dp / 16; ++k) {
+          const uint32_t koff = (uint32_t)(k & 3) * 32u;
+          mma_bf16(tmem + (uint32_t)(b * kCRows), sw128_desc(ra + (uint32_t)(k >> 2) * (kRRows * 128) + koff),
+                   sw128_desc(ca + (uint32_t)(k >> 2) * (kCRows * 128) + koff), id_s, k > 0 ? 1u : 0u);
+        }
+        issued = true;
+        mma_commit(&s_full[b]);
+        if (MODE == kFwd) mma_commit(&c_empty[b]);
+        return true;
+      };
+      if (!mbar_wait(bar_r, 0u)) ok = false;
+      if (ok && T > 0) ok = issue_s(0);
+      for (int t = 0; t < T && ok; ++t) {
+        if (t + 1 < T && !issue_s(t + 1)) {
+          ok = false;
+          break;
+        }
+        if (MODE != kFwd) {
+          const int b = t & 1;
+          if (!mbar_wait(&dz_full[b], (uint32_t)((t >> 1) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dh = smem_u32(sdz + (size_t)(2 * b) * kRRows * 128);
+          const uint32_t dl = smem_u32(sdz + (size_t)(2 * b + 1) * kRRows * 128);
+          const uint32_t ct = smem_u32(sct + (size_t)b * ct_bytes);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {  // K = the tile's 64 streamed rows
+            mma_bf16(acc, sw128_desc(dh + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g,
+                     (t | k) != 0 ? 1u : 0u);
+            mma_bf16(acc, sw128_desc(dl + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g, 1u);
+          }
+          mma_commit(&dz_empty[b]);
+          mma_commit(&c_empty[b]);
+        }
+      }
+      if (issued) {  // every MMA has completed before the epilogue reads the accumulator / TMEM is freed
+        mma_commit(acc_full);
+        if (!mbar_wait(acc_full, 0u)) ok = false;
+      } else {
+        mbar_arrive(acc_full);
+      }
+      if (!ok) atomicOr(a.status, kErrTimeout);
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int r = warp * 32 + lane;
+    const int grow = r0 + r;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    // row identity: query (kFwd, kDq) or job (kDj)
+    const bool rvalid = MODE == kDj ? grow < a.M : grow < a.B;
+    int pos_row = -1;
+    float lse_row = 0.f;
+    if (MODE != kDj && rvalid) {
+      pos_row = a.pos[grow];
+      if (MODE == kDq) lse_row = a.lse[grow];
+    }
+    float m = -INFINITY, ssum = 0.f, zpos = 0.f;
+    bool have_pos = false;
+    for (int t = 0; t < T && ok; ++t) {
+      const int b = t & 1;
+      const int c0 = (t0 + t) * kCRows;
+      if (!wwait(&s_full[b], (uint32_t)((t >> 1) & 1), lane)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint32_t sv[64];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t (&part)[16] = *reinterpret_cast<uint32_t (*)[16]>(&sv[16 * q]);
+        tmem_ld16(trow + (uint32_t)(b * kCRows + 16 * q), part);
+      }
+      tmem_ld_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_empty[b]);
+      // allowed columns of this tile as a 64-bit mask
+      uint64_t allow = 0ull;
+      if (rvalid) {
+        if (MODE != kDj) {
+          uint64_t bits = ~0ull;
+          if (a.mask != nullptr && c0 < a.M) {
+            const uint32_t *mrow = a.mask + (size_t)grow * a.Mw + (c0 >> 5);
+            const uint32_t w0 = __ldg(mrow), w1 = (c0 >> 5) + 1 < a.Mw ? __ldg(mrow + 1) : 0u;
+            bits = ((uint64_t)w1 << 32) | w0;
+          }
+          const int lim = a.M - c0;  // columns past M do not exist
+          const uint64_t exist = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1ull) : 0ull);
+          if (pos_row >= c0 && pos_row < c0 + 64) bits |= 1ull << (pos_row - c0);
+          allow = bits & exist;
+        } else {
+          const int lim = a.B - c0;
+          for (int c = 0; c < 64 && c < lim; ++c) {
+            const int q = c0 + c;
+            bool al = a.mask == nullptr || ((__ldg(a.mask + (size_t)q * a.Mw + (grow >> 5)) >> (grow & 31)) & 1u);
+            al = al || __ldg(a.pos + q) == grow;
+            allow |= (uint64_t)(al ? 1u : 0u) << c;
+          }
+        }
+      }
+      if (MODE == kFwd) {
+        float tmax = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < 64; ++c)
+          if ((allow >> c) & 1ull) tmax = fmaxf(tmax, __uint_as_float(sv[c]) * a.inv_tau);
+        if (tmax > -INFINITY) {
+          const float mn = fmaxf(m, tmax);
+          float add = 0.f;
+#pragma unroll
+          for (int c = 0; c < 64; ++c)
+            if ((allow >> c) & 1ull) add += exp2f((__uint_as_float(sv[c]) * a.inv_tau - mn) * kLog2e);
+          ssum = ssum * exp2f((m - mn) * kLog2e) + add;
+          m = mn;
+        }
+        if (pos_row >= c0 && pos_row < c0 + 64) {
+          const int pc = pos_row - c0;
+#pragma unroll
+          for (int c = 0; c < 64; ++c)
+            if (c == pc) zpos = __uint_as_float(sv[c]) * a.inv_tau;
+          have_pos = true;
+        }
+      } else {
+        // dZ of this tile as two BF16 terms, written in the 128-byte-swizzled K-major layout
+        if (!wwait(&dz_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u, lane)) {
+          ok = false;
+          break;
+        }
+        unsigned char *dh = sdz + (size_t)(2 * b) * kRRows * 128 + (size_t)r * 128;
+        unsigned char *dl = sdz + (size_t)(2 * b + 1) * kRRows * 128 + (size_t)r * 128;
+        const float g = (a.dloss != nullptr ? __ldg(a.dloss) : 1.f) * a.inv_b;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float dz2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int c = ch * 8 + u * 2 + h;
+              float dz = 0.f;
+              if ((allow >> c) & 1ull) {
+                const float z = __uint_as_float(sv[c]) * a.inv_tau;
+                float lse, ispos;
+                if (MODE == kDq) {
+                  lse = lse_row;
+                  ispos = (c0 + c) == pos_row ? 1.f : 0.f;
+                } else {
+                  lse = __ldg(a.lse + c0 + c);
+                  ispos = __ldg(a.pos + c0 + c) == grow ? 1.f : 0.f;
+                }
+                dz = (exp2f((z - lse) * kLog2e) - ispos) * g;
+              }
+              dz2[h] = dz;
+            }
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(dz2[0]), h1 = __float2bfloat16_rn(dz2[1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(dz2[0] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(dz2[1] - __bfloat162float(h1));
+            hw[u] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[u] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          const int slot = ((ch ^ (r & 7)) & 7) << 4;
+          *reinterpret_cast<uint4 *>(dh + slot) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4 *>(dl + slot) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&dz_full[b]);
+      }
+    }
+    if (MODE == kFwd) {
+      if (rvalid) {
+        a.part_m[(size_t)blockIdx.y * a.rows_p + grow] = m;
+        a.part_s[(size_t)blockIdx.y * a.rows_p + grow] = ssum;
+        if (have_pos) a.zpos[grow] = zpos;
+      }
+    } else {
+      if (!wwait(acc_full, 0u, lane)) ok = false;
+      tc_fence_after();
+      const uint32_t acc = trow + 2u * kCRows;
+      float *orow = a.out + (size_t)blockIdx.y * a.out_split + (size_t)grow * a.out_ld;
+      const bool wr = ok && (MODE == kDq ? grow < a.rows_p : grow < a.M);
+      for (int c = 0; c < dp; c += 16) {
+        uint32_t v[16];
+        tmem_ld16(acc + (uint32_t)c, v);
+        tmem_ld_wait();
+        if (wr)
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c + i < a.out_cols) orow[c + i] = __uint_as_float(v[i]) * a.inv_tau;
+      }
+    }
+    if (!ok && lane == 0) atomicOr(a.status, kErrTimeout);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 5) tmem_dealloc(tmem, kLossTmemCols);
+}
+
+// X [rows][d] (BF16 or FP32) -> P [rows_p][dp] and PT [dp][rows_p], BF16, zero padded.
+__global__ void k_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, __nv_bfloat16 *P,
+                            __nv_bfloat16 *PT) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)rows_p * dp) return;
+  const int row = (int)(i / dp), k = (int)(i % dp);
+  __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+  if (row < rows && k < d) {
+    v = elem == kElemBF16 ? reinterpret_cast<const __nv_bfloat16 *>(X)[(size_t)row * d + k]
+                          : __float2bfloat16_rn(reinterpret_cast<const float *>(X)[(size_t)row * d + k]);
+  }
+  P[i] = v;
+  PT[(size_t)k * rows_p + row] = v;
+}
+
+// Per query: combine the split partials into lse and the loss term; one CTA sums the
+// terms in FP64 in a fixed order.  An out-of-range positive makes the loss NaN.
+__global__ void k_loss_combine(const LossArgs a, int splits, float *lse, float *loss) {
+  __shared__ double red[1024];
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
+    float mx = -INFINITY;
+    for (int s = 0; s < splits; ++s) mx = fmaxf(mx, a.part_m[(size_t)s * a.rows_p + q]);
+    float sum = 0.f;
+    for (int s = 0; s < splits; ++s) {
+      const float ms = a.part_m[(size_t)s * a.rows_p + q];
+      if (ms > -INFINITY) sum += a.part_s[(size_t)s * a.rows_p + q] * exp2f((ms - mx) * kLog2e);
+    }
+    const float l = mx + logf(sum);
+    lse[q] = l;
+    const int p = a.pos[q];
+    acc += (p >= 0 && p < a.M) ? (double)l - (double)a.zpos[q] : (double)NAN;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = (float)(red[0] / (double)a.B);
+}
+
+__global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)B * d) return;
+  const int q = (int)(i / d), k = (int)(i % d);
+  float s = 0.f;
+  for (int sp = 0; sp < splits; ++sp) s += part[(size_t)sp * split_stride + (size_t)q * dp + k];
+  dQ[i] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
+                             cudaStream_t s) {
+  const int64_t n = (int64_t)rows_p * dp;
+  k_loss_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, elem, rows, d, rows_p, dp, (__nv_bfloat16 *)P,
+                                                         (__nv_bfloat16 *)PT);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y, const void *tm_r, const void *tm_c,
+                             const void *tm_ct, cudaStream_t s) {
+  const LossSmem L = loss_smem(a.dp, mode);
+  const size_t smem = L.total + 1024;
+  const CUtensorMap &r = *static_cast<const CUtensorMap *>(tm_r);
+  const CUtensorMap &c = *static_cast<const CUtensorMap *>(tm_c);
+  const CUtensorMap &ct = *static_cast<const CUtensorMap *>(tm_ct ? tm_ct : tm_c);
+  dim3 grid(grid_x, grid_y);
+  cudaError_t e;
+  switch (mode) {
+    case kFwd:
+      e = cudaFuncSetAttribute(k_loss<kFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_loss<kFwd><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
+      break;
+    case kDq:
+      e = cudaFuncSetAttribute(k_loss<kDq>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_loss<kDq><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
+      break;
+    case kDj:
+      e = cudaFuncSetAttribute(k_loss<kDj>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_loss<kDj><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, float *loss, cudaStream_t s) {
+  k_loss_combine<<<1, 1024, 0, s>>>(a, splits, lse, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ,
+                                  cudaStream_t s) {
+  const int64_t n = (int64_t)B * d;
+  k_loss_dq_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, splits, split_stride, B, d, dp, dQ);
+  return cudaGetLastError();
+}
+
+}  // namespace lr

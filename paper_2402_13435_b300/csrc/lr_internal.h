@@ -158,6 +158,40 @@ struct RescoreArgs {
   uint32_t *err;
 };
 cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s);
+// Masked softmax loss passes (loss.cu).  Row tiles of 128 over R, streamed
+// 64-row tiles of C; see loss.cu for the three modes.
+struct LossArgs {
+  int32_t B, M;            // queries, jobs (true sizes)
+  int32_t dp;              // padded dimension (64 or 128)
+  int32_t rows_p;          // padded rows of the forward partials (= padded B)
+  int32_t n_ctiles;        // 64-row tiles of C
+  int32_t c_per_split;     // C tiles per CTA (grid.y splits the C range)
+  float inv_tau;
+  float inv_b;             // 1 / B
+  const float *dloss;      // device scalar dL (backward; null = 1)
+  const int32_t *pos;      // [B] positive column per query
+  const uint32_t *mask;    // [B][Mw] bit j of row i: job j allowed for query i (null = all allowed)
+  int32_t Mw;
+  const float *lse;        // [B] saved log-sum-exp (backward)
+  float *part_m, *part_s;  // forward partials [splits][rows_p]
+  float *zpos;             // [rows_p] z of each query's positive
+  float *out;              // backward output rows (dQ partials or dJ)
+  size_t out_split;        // elements between splits of out
+  int32_t out_ld, out_cols;
+  uint32_t *status;        // device status word (timeouts)
+};
+cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
+                             cudaStream_t s);
+cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y, const void *tm_r, const void *tm_c,
+                             const void *tm_ct, cudaStream_t s);
+cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, float *loss, cudaStream_t s);
+cudaError_t launch_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ,
+                                  cudaStream_t s);
+// 2-D tiled TMA descriptor (innermost dimension first); false when the driver
+// entry point is unavailable or the encoder rejects the description.
+bool encode_tmap_2d(void *tmap, int dtype_code, const void *base, uint64_t dim0, uint64_t dim1, uint64_t stride1,
+                    uint32_t box0, uint32_t box1, int swizzle_code);
+
 cudaError_t launch_quantize_rows(const float *X, int64_t n, int d_pad, int elem, void *Xq, float *scale,
                                  cudaStream_t s);
 cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,

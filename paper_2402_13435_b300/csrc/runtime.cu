@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "lr_internal.h"
+#include "ptx.h"
 
 namespace lr {
 
@@ -143,9 +144,9 @@ struct lr_index {
   int32_t gen = 0;
   size_t device_bytes = 0;
   // TMA descriptor of X for the tensor-core plan (128 rows x 32 floats, 128-byte swizzle)
-  alignas(64) CUtensorMap tmap_x;
+  CUtensorMap tmap_x;
   bool have_tmap = false;
-  alignas(64) CUtensorMap tmap_xq;  // low-precision rows (precision form)
+  CUtensorMap tmap_xq;  // low-precision rows (precision form)
   bool have_tmap_q = false;
 };
 
@@ -268,6 +269,21 @@ int32_t sample_rank(const SamplePlan &p, int K) {
 }
 
 }  // namespace
+
+namespace lr {
+bool encode_tmap_2d(void *tmap, int dtype_code, const void *base, uint64_t dim0, uint64_t dim1, uint64_t stride1,
+                    uint32_t box0, uint32_t box1, int swizzle_code) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride1};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(static_cast<CUtensorMap *>(tmap), (CUtensorMapDataType)dtype_code, 2, const_cast<void *>(base), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, (CUtensorMapSwizzle)swizzle_code,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace lr
 
 extern "C" {
 
@@ -1025,6 +1041,180 @@ lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64
 lr_status lr_index_sync(lr_index *index, void *stream) {
   if (!index) return fail(LR_ERR_INVALID, "index is null");
   return check_err_word(index, (cudaStream_t)stream, "lr_index_sync");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ loss
+namespace {
+
+// Geometry and workspace of the loss passes for B queries, M jobs, dimension d.
+struct LossPlan {
+  int Bp = 0, Mp = 0, dp = 0, n_ctiles = 0, c_per_split = 0, splits = 0;
+  size_t o_qp = 0, o_qt = 0, o_jp = 0, o_jt = 0, o_pm = 0, o_ps = 0, o_zp = 0, o_dq = 0, o_st = 0, total = 0;
+};
+
+LossPlan loss_plan(int B, int M, int d, int sms) {
+  LossPlan P;
+  P.Bp = (B + 127) / 128 * 128;
+  P.Mp = (M + 127) / 128 * 128;
+  P.dp = d <= 64 ? 64 : 128;
+  P.n_ctiles = P.Mp / 64;
+  const int rtiles = P.Bp / 128;
+  const int want = std::max(1, std::min((sms + rtiles - 1) / rtiles, P.n_ctiles));
+  P.c_per_split = (P.n_ctiles + want - 1) / want;
+  P.splits = (P.n_ctiles + P.c_per_split - 1) / P.c_per_split;
+  Carver cv;
+  P.o_qp = cv.take<uint16_t>((size_t)P.Bp * P.dp);
+  P.o_qt = cv.take<uint16_t>((size_t)P.Bp * P.dp);
+  P.o_jp = cv.take<uint16_t>((size_t)P.Mp * P.dp);
+  P.o_jt = cv.take<uint16_t>((size_t)P.Mp * P.dp);
+  P.o_pm = cv.take<float>((size_t)P.splits * P.Bp);
+  P.o_ps = cv.take<float>((size_t)P.splits * P.Bp);
+  P.o_zp = cv.take<float>(P.Bp);
+  P.o_dq = cv.take<float>((size_t)P.splits * P.Bp * P.dp);
+  P.o_st = cv.take<uint32_t>(4);
+  P.total = align_up(cv.off, 256);
+  return P;
+}
+
+int current_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+    cudaGetLastError();
+    return 148;
+  }
+  return sms;
+}
+
+lr_status loss_check(const void *Q, const void *J, int B, int M, int d, int dtype, const int32_t *pos,
+                     const uint32_t *mask, void *ws, size_t ws_bytes, const LossPlan &P) {
+  if (B < 1 || M < 1) return fail(LR_ERR_INVALID, "B and M must be >= 1");
+  if (d < 1 || d > 128) return fail(LR_ERR_UNSUPPORTED, "the loss kernels take d in [1, 128]");
+  if (dtype != LR_BF16 && dtype != LR_F32) return fail(LR_ERR_INVALID, "dtype must be LR_BF16 or LR_F32");
+  if (!is_device_ptr(Q) || !is_device_ptr(J) || !is_device_ptr(pos) || !is_device_ptr(ws) ||
+      (mask && !is_device_ptr(mask)))
+    return fail(LR_ERR_INVALID, "Q, J, pos, mask and workspace must be device memory");
+  if (ws_bytes < P.total) return fail(LR_ERR_WORKSPACE, "workspace smaller than lr_score_workspace_size()");
+  return LR_OK;
+}
+
+struct LossMaps {
+  CUtensorMap qr, qc, qt, jr, jc, jt;
+};
+
+lr_status loss_prepare(const void *Q, const void *J, int B, int M, int d, int dtype, char *w, const LossPlan &P,
+                       LossMaps &T, cudaStream_t s) {
+  const int elem = dtype == LR_BF16 ? kElemBF16 : kElemF32;
+  LR_CK(cudaMemsetAsync(w + P.o_st, 0, sizeof(uint32_t), s));
+  LR_CK(launch_loss_prep(Q, elem, B, d, P.Bp, P.dp, w + P.o_qp, w + P.o_qt, s));
+  LR_CK(launch_loss_prep(J, elem, M, d, P.Mp, P.dp, w + P.o_jp, w + P.o_jt, s));
+  const int bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, sw = CU_TENSOR_MAP_SWIZZLE_128B;
+  const uint64_t rs = (uint64_t)P.dp * 2;
+  bool ok = encode_tmap_2d(&T.qr, bf, w + P.o_qp, P.dp, P.Bp, rs, 64, 128, sw) &&
+            encode_tmap_2d(&T.qc, bf, w + P.o_qp, P.dp, P.Bp, rs, 64, 64, sw) &&
+            encode_tmap_2d(&T.qt, bf, w + P.o_qt, P.Bp, P.dp, (uint64_t)P.Bp * 2, 64, P.dp, sw) &&
+            encode_tmap_2d(&T.jr, bf, w + P.o_jp, P.dp, P.Mp, rs, 64, 128, sw) &&
+            encode_tmap_2d(&T.jc, bf, w + P.o_jp, P.dp, P.Mp, rs, 64, 64, sw) &&
+            encode_tmap_2d(&T.jt, bf, w + P.o_jt, P.Mp, P.dp, (uint64_t)P.Mp * 2, 64, P.dp, sw);
+  if (!ok) return fail(LR_ERR_CUDA, "cannot encode the TMA descriptors of the loss operands");
+  return LR_OK;
+}
+
+LossArgs loss_args(int B, int M, float inv_tau, const int32_t *pos, const uint32_t *mask, char *w,
+                   const LossPlan &P) {
+  LossArgs a{};
+  a.B = B;
+  a.M = M;
+  a.dp = P.dp;
+  a.rows_p = P.Bp;
+  a.n_ctiles = P.n_ctiles;
+  a.c_per_split = P.c_per_split;
+  a.inv_tau = inv_tau;
+  a.inv_b = 1.0f / (float)B;
+  a.pos = pos;
+  a.mask = mask;
+  a.Mw = (M + 31) / 32;
+  a.part_m = (float *)(w + P.o_pm);
+  a.part_s = (float *)(w + P.o_ps);
+  a.zpos = (float *)(w + P.o_zp);
+  a.status = (uint32_t *)(w + P.o_st);
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lr_score_workspace_size(int32_t B, int32_t M, int32_t d) {
+  if (B < 1 || M < 1 || d < 1 || d > 128) return 0;
+  return loss_plan(B, M, d, current_sms()).total;
+}
+
+lr_status lr_score_forward(const void *Q, const void *J, int32_t B, int32_t M, int32_t d, int32_t dtype,
+                           const int32_t *pos, const uint32_t *mask_bits, float inv_tau, float *loss, float *lse,
+                           void *workspace, size_t workspace_bytes, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const LossPlan P = loss_plan(B, M, d, current_sms());
+  lr_status st = loss_check(Q, J, B, M, d, dtype, pos, mask_bits, workspace, workspace_bytes, P);
+  if (st != LR_OK) return st;
+  if (!is_device_ptr(loss) || !is_device_ptr(lse)) return fail(LR_ERR_INVALID, "loss and lse must be device memory");
+  char *w = (char *)workspace;
+  LossMaps T;
+  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, s);
+  if (st != LR_OK) return st;
+  LossArgs a = loss_args(B, M, inv_tau, pos, mask_bits, w, P);
+  LR_CK(launch_loss_pass(0, a, P.Bp / 128, P.splits, &T.qr, &T.jc, nullptr, s));
+  LR_CK(launch_loss_combine(a, P.splits, lse, loss, s));
+  return LR_OK;
+}
+
+lr_status lr_score_backward(const void *Q, const void *J, int32_t B, int32_t M, int32_t d, int32_t dtype,
+                            const int32_t *pos, const uint32_t *mask_bits, float inv_tau, const float *lse,
+                            const float *dloss, float *dQ, float *dJ, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const LossPlan P = loss_plan(B, M, d, current_sms());
+  lr_status st = loss_check(Q, J, B, M, d, dtype, pos, mask_bits, workspace, workspace_bytes, P);
+  if (st != LR_OK) return st;
+  if (!is_device_ptr(lse) || !is_device_ptr(dQ) || !is_device_ptr(dJ) || (dloss && !is_device_ptr(dloss)))
+    return fail(LR_ERR_INVALID, "lse, dloss, dQ and dJ must be device memory");
+  char *w = (char *)workspace;
+  LossMaps T;
+  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, s);
+  if (st != LR_OK) return st;
+  // dQ: query tiles against job tiles, per-split partials, then their sum
+  LossArgs a = loss_args(B, M, inv_tau, pos, mask_bits, w, P);
+  a.lse = lse;
+  a.dloss = dloss;
+  a.out = (float *)(w + P.o_dq);
+  a.out_split = (size_t)P.Bp * P.dp;
+  a.out_ld = P.dp;
+  a.out_cols = P.dp;
+  LR_CK(launch_loss_pass(1, a, P.Bp / 128, P.splits, &T.qr, &T.jc, &T.jt, s));
+  LR_CK(launch_loss_dq_reduce((const float *)(w + P.o_dq), P.splits, (size_t)P.Bp * P.dp, B, d, P.dp, dQ, s));
+  // dJ: job tiles against every query tile, written straight to dJ
+  LossArgs b = a;
+  b.n_ctiles = P.Bp / 64;
+  b.c_per_split = P.Bp / 64;
+  b.out = dJ;
+  b.out_split = 0;
+  b.out_ld = d;
+  b.out_cols = d;
+  LR_CK(launch_loss_pass(2, b, P.Mp / 128, 1, &T.jr, &T.qc, &T.qt, s));
+  return LR_OK;
+}
+
+lr_status lr_score_status(void *workspace, int32_t B, int32_t M, int32_t d, void *stream) {
+  if (!workspace) return fail(LR_ERR_INVALID, "workspace is null");
+  const LossPlan P = loss_plan(B, M, d, current_sms());
+  uint32_t e = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  LR_CK(cudaMemcpyAsync(&e, (char *)workspace + P.o_st, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  LR_CK(cudaStreamSynchronize(s));
+  if (e & kErrTimeout) return fail(LR_ERR_TIMEOUT, "a bounded device wait of the loss kernels timed out");
+  return LR_OK;
 }
 
 }  // extern "C"
