@@ -281,6 +281,49 @@ lr_status lr_score_backward(const void *Q, const void *J, int32_t B, int32_t M, 
 /* Synchronise `stream` and report (then clear) a device wait timeout of the last loss call on `workspace`. */
 lr_status lr_score_status(void *workspace, int32_t B, int32_t M, int32_t d, void *stream);
 
+/*
+ * Serving (appendix "Batch Inference", "Memory Pre-Allocation"): continuous
+ * batching of independent requests over a resident index.  The server owns
+ * `slots` search contexts that share the index's rows and term storage, each
+ * with its own workspace for up to `max_queries` queries and its own CUDA
+ * stream, so batches of different slots run on the GPU at the same time.
+ * arena_bytes (0: no limit) caps the device memory of the slots: fewer slots
+ * than asked are created when they would not fit (memory-based admission).
+ * A scheduler thread forms each batch from the pending requests, first come
+ * first served, while it fits the slot; requests that arrive while every slot
+ * is busy join the next batch a slot forms.  Each request's result is the same
+ * as an lr_search of that request alone with the same plan.
+ *
+ * lr_server_submit copies the request (host q [B][dim] FP32, host filters,
+ * host k [B] or NULL with k_all) and returns at once with a ticket; a request
+ * with more queries or term occurrences than a slot holds is rejected with
+ * LR_ERR_WORKSPACE.  lr_server_wait blocks until the request is done (or
+ * timeout_ms passes: LR_ERR_TIMEOUT; negative = no limit), copies its rows into
+ * host outputs with row stride k_stride (-1 / -inf padded) and the latency from
+ * submit to completion, and releases the ticket.  lr_server_get_stats reports
+ * counts and latency percentiles since creation or the last reset.
+ * lr_server_destroy finishes pending work and frees the slots (the index stays).
+ */
+typedef struct lr_server lr_server;
+typedef struct lr_server_opts {
+  int32_t slots;        /* concurrent batches                          */
+  int32_t max_queries;  /* queries per batch (a slot's capacity)       */
+  int32_t plan;         /* lr_plan used for every batch                */
+} lr_server_opts;
+typedef struct lr_server_stats {
+  int64_t submitted, completed, batches, queries;
+  int32_t slots;
+  size_t slot_bytes;
+  double p50_ms, p99_ms, mean_ms, max_ms, elapsed_s;
+} lr_server_stats;
+lr_status lr_server_create(lr_index *index, const lr_server_opts *opts, size_t arena_bytes, lr_server **out);
+lr_status lr_server_submit(lr_server *server, const float *q, int32_t B, const lr_filters *f, const int32_t *k,
+                           int32_t k_all, uint64_t *ticket);
+lr_status lr_server_wait(lr_server *server, uint64_t ticket, int32_t timeout_ms, int32_t *out_ids, float *out_scores,
+                         int32_t *out_count, int32_t k_stride, double *latency_ms);
+lr_status lr_server_get_stats(lr_server *server, lr_server_stats *stats, int32_t reset);
+lr_status lr_server_destroy(lr_server *server);
+
 /* Human-readable description of the calling thread's last failure. */
 const char *lr_last_error_message(void);
 

@@ -441,3 +441,84 @@ def masked_softmax_loss(Q, J, pos, mask_bits=None, inv_tau: float = 20.0):
     except NameError:
         fn = _MSL = _autograd_function()
     return fn.apply(Q, J, pos, mask_bits, inv_tau)
+
+
+# ----------------------------------------------------------------------------- serving
+class lr_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_queries", ctypes.c_int32), ("plan", ctypes.c_int32)]
+
+
+class lr_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("queries", ctypes.c_int64), ("slots", ctypes.c_int32), ("slot_bytes", ctypes.c_size_t),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("elapsed_s", ctypes.c_double)]
+
+
+_lib.lr_server_create.argtypes = [_vp, ctypes.POINTER(lr_server_opts), ctypes.c_size_t, ctypes.POINTER(_vp)]
+_lib.lr_server_submit.argtypes = [_vp, _vp, _i32, ctypes.POINTER(lr_filters), _vp, _i32,
+                                  ctypes.POINTER(ctypes.c_uint64)]
+_lib.lr_server_wait.argtypes = [_vp, ctypes.c_uint64, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_double)]
+_lib.lr_server_get_stats.argtypes = [_vp, ctypes.POINTER(lr_server_stats), _i32]
+_lib.lr_server_destroy.argtypes = [_vp]
+for _n in ("lr_server_create", "lr_server_submit", "lr_server_wait", "lr_server_get_stats", "lr_server_destroy"):
+    getattr(_lib, _n).restype = ctypes.c_int
+
+
+class Server:
+    """Continuous-batching server over a resident index (see include/lr.h, lr_server_*).
+
+    submit() copies a request (host FP32 queries [B][dim], filters, K) and returns a ticket at once;
+    wait() blocks for its result.  Thread-safe: several client threads may submit and wait."""
+
+    def __init__(self, index: "Index", slots: int = 2, max_queries: int = 64, plan: str = "auto",
+                 arena_bytes: int = 0):
+        o = lr_server_opts(int(slots), int(max_queries), _PLAN[plan])
+        h = ctypes.c_void_p()
+        _check(_lib.lr_server_create(ctypes.c_void_p(index.handle), ctypes.byref(o), int(arena_bytes),
+                                     ctypes.byref(h)), "lr_server_create")
+        self.handle = h.value
+        self.index = index
+
+    def submit(self, q, filters, k) -> int:
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        f = Filters.of(filters)
+        B = int(q.shape[0])
+        if np.isscalar(k):
+            k_arr, k_all = None, int(k)
+        else:
+            k_arr = np.ascontiguousarray(k, dtype=np.int32)
+            k_all = int(k_arr.max())
+        fc = f.c()
+        t = ctypes.c_uint64()
+        _check(_lib.lr_server_submit(ctypes.c_void_p(self.handle), q.ctypes.data, B, ctypes.byref(fc),
+                                     None if k_arr is None else k_arr.ctypes.data, k_all, ctypes.byref(t)),
+               "lr_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, B: int, k_stride: int, timeout_ms: int = -1):
+        ids = np.empty((B, k_stride), dtype=np.int32)
+        sc = np.empty((B, k_stride), dtype=np.float32)
+        cnt = np.empty(B, dtype=np.int32)
+        lat = ctypes.c_double()
+        _check(_lib.lr_server_wait(ctypes.c_void_p(self.handle), int(ticket), int(timeout_ms), ids.ctypes.data,
+                                   sc.ctypes.data, cnt.ctypes.data, int(k_stride), ctypes.byref(lat)),
+               "lr_server_wait")
+        return ids, sc, cnt, float(lat.value)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = lr_server_stats()
+        _check(_lib.lr_server_get_stats(ctypes.c_void_p(self.handle), ctypes.byref(st), int(reset)),
+               "lr_server_get_stats")
+        return {n: getattr(st, n) for n, _ in lr_server_stats._fields_}
+
+    def close(self) -> None:
+        if self.handle:
+            _check(_lib.lr_server_destroy(ctypes.c_void_p(self.handle)), "lr_server_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -192,6 +192,15 @@ cudaError_t launch_loss_dq_reduce(const float *part, int splits, size_t split_st
 bool encode_tmap_2d(void *tmap, int dtype_code, const void *base, uint64_t dim0, uint64_t dim1, uint64_t stride1,
                     uint32_t box0, uint32_t box1, int swizzle_code);
 
+// Serving slots: search contexts sharing one resident index (runtime.cu).
+lr_status index_clone_slot(const lr_index *base, int max_batch, void *stream, lr_index **out);
+void index_destroy_slot(lr_index *ix);
+int index_max_k(const lr_index *ix);
+int index_max_batch_terms(const lr_index *ix);
+int index_dim(const lr_index *ix);
+int index_vocab(const lr_index *ix);
+int index_device(const lr_index *ix);
+
 cudaError_t launch_quantize_rows(const float *X, int64_t n, int d_pad, int elem, void *Xq, float *scale,
                                  cudaStream_t s);
 cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,

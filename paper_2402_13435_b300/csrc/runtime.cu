@@ -89,6 +89,7 @@ struct SubBatch {
 }  // namespace
 
 struct lr_index {
+  bool owns_data = true;  // false for a serving slot: rows and term storage belong to the base index
   int device = 0, num_sms = 0;
   int64_t n = 0;
   int dim = 0, d_pad = 0, metric = 0, vocab = 0;
@@ -154,12 +155,14 @@ namespace {
 
 void free_index(lr_index *ix) {
   if (!ix) return;
-  cudaFree(ix->X);
-  cudaFree(ix->Xq);
-  cudaFree(ix->xscale);
-  cudaFree(ix->dense_bm);
-  cudaFree(ix->post_off_d);
-  cudaFree(ix->post_ids_d);
+  if (ix->owns_data) {
+    cudaFree(ix->X);
+    cudaFree(ix->Xq);
+    cudaFree(ix->xscale);
+    cudaFree(ix->dense_bm);
+    cudaFree(ix->post_off_d);
+    cudaFree(ix->post_ids_d);
+  }
   cudaFree(ix->ws);
   for (int i = 0; i < 2; ++i) {
     if (ix->filt_h[i]) cudaFreeHost(ix->filt_h[i]);
@@ -283,6 +286,161 @@ bool encode_tmap_2d(void *tmap, int dtype_code, const void *base, uint64_t dim0,
              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, (CUtensorMapSwizzle)swizzle_code,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+}  // namespace lr
+
+namespace {
+// Search workspace of an index (sizes from max_batch, max_k, max_kq and the
+// sampling geometry), carved from one device allocation, plus the pinned
+// double-buffered filter staging and its events.
+lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
+  // ---- sampling geometry and candidate capacities
+  ix->auto_stride = ix->n_groups >= 256 ? (int)std::min<int64_t>(64, ix->n_groups / 16) : 0;
+  const SamplePlan sp = make_sample_plan(ix, ix->auto_stride);
+  int64_t samp_rows = sp.sampled_rows;
+  samp_rows = std::max<int64_t>(samp_rows, std::min<int64_t>(ix->n_groups * kGroupRows / 2 + kGroupRows, 1 << 16));
+  ix->samp_cap = samp_rows;
+  int64_t cap = 0;
+  if (sp.stride > 0) {
+    const double r = std::max(64.0, std::ceil(4.0 * ix->max_kq * sp.frac));
+    cap = pow2_ceil((int64_t)std::ceil(4.0 * r / sp.frac));
+  }
+  cap = std::max<int64_t>(cap, std::min<int64_t>(ix->n, 1 << 16));
+  cap = std::max<int64_t>(cap, ix->max_kq);
+  ix->cand_cap = cap;
+
+  // ---- workspace, one allocation
+  const int B = ix->max_batch;
+  const int nsp = (ix->has_postings && ix->n_dense < ix->vocab) ? ix->max_sparse : 0;
+  ix->filt_bytes = align_up((size_t)B * 16 + (size_t)ix->max_batch_terms * 32 + (size_t)nsp * 4 + 65536, 256);
+  Carver cv;
+  const size_t o_qraw = cv.take<float>((size_t)B * ix->dim);
+  const size_t o_qws = cv.take<float>((size_t)B * ix->d_pad);
+  const size_t o_sparse = cv.take<uint32_t>((size_t)nsp * ix->n_words);
+  // per-query state block (cleared by one memset per search)
+  const size_t o_state = cv.take<char>(0);
+  const size_t o_tau = cv.take<uint64_t>(B);
+  const size_t o_pre = cv.take<uint64_t>(B);
+  const size_t o_pass = cv.take<unsigned long long>(B);
+  const size_t o_cnt = cv.take<uint32_t>(B);
+  const size_t o_ovf = cv.take<uint32_t>(B);
+  const size_t o_scnt = cv.take<uint32_t>(B);
+  const size_t o_sovf = cv.take<uint32_t>(B);
+  const size_t o_flag = cv.take<uint32_t>(B);
+  const size_t o_krem = cv.take<int32_t>(B);
+  const size_t o_nflag = cv.take<uint32_t>(1);
+  const size_t o_state_end = cv.take<char>(0);
+  const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
+  const size_t o_err = cv.take<uint32_t>(1);
+  const size_t o_kq = cv.take<int32_t>(B);
+  const size_t o_rank = cv.take<int32_t>(B);
+  const size_t o_hist = cv.take<uint32_t>((size_t)B * kFbBins);
+  const size_t o_samp = cv.take<uint64_t>((size_t)B * ix->samp_cap);
+  const size_t o_cand = cv.take<uint64_t>((size_t)B * ix->cand_cap);
+  const size_t o_oids = cv.take<int32_t>((size_t)B * ix->max_k);
+  const size_t o_osc = cv.take<float>((size_t)B * ix->max_k);
+  const size_t o_ocnt = cv.take<int32_t>(B);
+  const size_t o_ocand = cv.take<int32_t>(B);
+  const size_t o_ofb = cv.take<int32_t>(B);
+  const bool lowp = ix->elem != kElemF32;
+  const size_t o_cids = cv.take<int32_t>(lowp ? (size_t)B * ix->max_kq : 0);
+  const size_t o_csc = cv.take<float>(lowp ? (size_t)B * ix->max_kq : 0);
+  const size_t o_ccnt = cv.take<int32_t>(lowp ? B : 0);
+  const size_t o_kfin = cv.take<int32_t>(lowp ? B : 0);
+  const size_t o_ties = cv.take<int32_t>(lowp ? B : 0);
+  const size_t o_filt = cv.take<char>(ix->filt_bytes);
+  ix->ws_bytes = align_up(cv.off, 256);
+  if (cudaMalloc(&ix->ws, ix->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LR_ERR_NOMEM, "cannot allocate the search workspace (" + std::to_string(ix->ws_bytes) +
+                                          " bytes); lower max_batch, max_k or max_sparse_terms");
+  }
+  ix->device_bytes += ix->ws_bytes;
+  char *w = ix->ws;
+  ix->q_raw = (float *)(w + o_qraw);
+  ix->q_ws = (float *)(w + o_qws);
+  ix->sparse_bm = nsp ? (uint32_t *)(w + o_sparse) : nullptr;
+  ix->state = w + o_state;
+  ix->state_bytes = o_state_end - o_state;
+  ix->tau = (uint64_t *)(w + o_tau);
+  ix->prefix = (uint64_t *)(w + o_pre);
+  ix->pass = (unsigned long long *)(w + o_pass);
+  ix->cnt = (uint32_t *)(w + o_cnt);
+  ix->ovf = (uint32_t *)(w + o_ovf);
+  ix->scnt = (uint32_t *)(w + o_scnt);
+  ix->sovf = (uint32_t *)(w + o_sovf);
+  ix->flag = (uint32_t *)(w + o_flag);
+  ix->krem = (int32_t *)(w + o_krem);
+  ix->n_flag = (uint32_t *)(w + o_nflag);
+  ix->done_ctr = (uint32_t *)(w + o_done);
+  ix->work_ctr = ix->done_ctr + 1;
+  ix->err = (uint32_t *)(w + o_err);
+  ix->kq = (int32_t *)(w + o_kq);
+  ix->rank = (int32_t *)(w + o_rank);
+  ix->hist = (uint32_t *)(w + o_hist);
+  ix->samp_buf = (uint64_t *)(w + o_samp);
+  ix->cand_buf = (uint64_t *)(w + o_cand);
+  ix->o_ids = (int32_t *)(w + o_oids);
+  ix->o_sc = (float *)(w + o_osc);
+  ix->o_cnt = (int32_t *)(w + o_ocnt);
+  ix->o_cand = (int32_t *)(w + o_ocand);
+  ix->o_fb = (int32_t *)(w + o_ofb);
+  if (lowp) {
+    ix->c_ids = (int32_t *)(w + o_cids);
+    ix->c_sc = (float *)(w + o_csc);
+    ix->c_cnt = (int32_t *)(w + o_ccnt);
+    ix->kfin = (int32_t *)(w + o_kfin);
+    ix->o_ties = (int32_t *)(w + o_ties);
+  }
+  ix->filt_d = w + o_filt;
+  LR_CK(cudaMemsetAsync(ix->done_ctr, 0, 2 * sizeof(uint32_t), s));
+  LR_CK(cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), s));
+  LR_CK(cudaMemsetAsync(ix->hist, 0, (size_t)B * kFbBins * sizeof(uint32_t), s));
+  for (int i = 0; i < 2; ++i) {
+    LR_CK(cudaHostAlloc((void **)&ix->filt_h[i], ix->filt_bytes, cudaHostAllocDefault));
+    LR_CK(cudaEventCreateWithFlags(&ix->filt_ev[i], cudaEventDisableTiming));
+  }
+  ix->sparse_stamp.assign(ix->vocab, 0);
+  ix->sparse_id.assign(ix->vocab, -1);
+  ix->local_stamp.assign(ix->vocab, 0);
+  ix->local_id.assign(ix->vocab, -1);
+  return LR_OK;
+}
+
+}  // namespace
+
+namespace lr {
+// A second search context over the same resident index: it shares the rows,
+// the term storage and the TMA descriptors, and owns a workspace sized for
+// max_batch queries (serving slots run their batches concurrently).
+lr_status index_clone_slot(const lr_index *base, int max_batch, void *stream, lr_index **out) {
+  if (!base || !out || max_batch < 1) return fail(LR_ERR_INVALID, "index_clone_slot: bad arguments");
+  lr_index *ix = new lr_index(*base);
+  ix->owns_data = false;
+  ix->device_bytes = 0;
+  ix->ws = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    ix->filt_h[i] = nullptr;
+    ix->filt_ev[i] = nullptr;
+    ix->filt_ev_live[i] = false;
+  }
+  ix->max_batch_terms = (int)((int64_t)base->max_batch_terms * max_batch / std::max(base->max_batch, 1)) + 64;
+  ix->max_batch = max_batch;
+  const lr_status st = alloc_search_workspace(ix, (cudaStream_t)stream);
+  if (st != LR_OK) {
+    free_index(ix);
+    return st;
+  }
+  *out = ix;
+  return LR_OK;
+}
+void index_destroy_slot(lr_index *ix) {
+  if (ix) free_index(ix);
+}
+int index_max_k(const lr_index *ix) { return ix->max_k; }
+int index_max_batch_terms(const lr_index *ix) { return ix->max_batch_terms; }
+int index_dim(const lr_index *ix) { return ix->dim; }
+int index_vocab(const lr_index *ix) { return ix->vocab; }
+int index_device(const lr_index *ix) { return ix->device; }
 }  // namespace lr
 
 extern "C" {
@@ -451,116 +609,10 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
     }
   }
 
-  // ---- sampling geometry and candidate capacities
-  ix->auto_stride = ix->n_groups >= 256 ? (int)std::min<int64_t>(64, ix->n_groups / 16) : 0;
-  const SamplePlan sp = make_sample_plan(ix, ix->auto_stride);
-  int64_t samp_rows = sp.sampled_rows;
-  samp_rows = std::max<int64_t>(samp_rows, std::min<int64_t>(ix->n_groups * kGroupRows / 2 + kGroupRows, 1 << 16));
-  ix->samp_cap = samp_rows;
-  int64_t cap = 0;
-  if (sp.stride > 0) {
-    const double r = std::max(64.0, std::ceil(4.0 * ix->max_kq * sp.frac));
-    cap = pow2_ceil((int64_t)std::ceil(4.0 * r / sp.frac));
+  {
+    const lr_status wst = alloc_search_workspace(ix, s);
+    if (wst != LR_OK) return cleanup(wst);
   }
-  cap = std::max<int64_t>(cap, std::min<int64_t>(ix->n, 1 << 16));
-  cap = std::max<int64_t>(cap, ix->max_kq);
-  ix->cand_cap = cap;
-
-  // ---- workspace, one allocation
-  const int B = ix->max_batch;
-  const int nsp = (ix->has_postings && ix->n_dense < ix->vocab) ? ix->max_sparse : 0;
-  ix->filt_bytes = align_up((size_t)B * 16 + (size_t)ix->max_batch_terms * 32 + (size_t)nsp * 4 + 65536, 256);
-  Carver cv;
-  const size_t o_qraw = cv.take<float>((size_t)B * ix->dim);
-  const size_t o_qws = cv.take<float>((size_t)B * ix->d_pad);
-  const size_t o_sparse = cv.take<uint32_t>((size_t)nsp * ix->n_words);
-  // per-query state block (cleared by one memset per search)
-  const size_t o_state = cv.take<char>(0);
-  const size_t o_tau = cv.take<uint64_t>(B);
-  const size_t o_pre = cv.take<uint64_t>(B);
-  const size_t o_pass = cv.take<unsigned long long>(B);
-  const size_t o_cnt = cv.take<uint32_t>(B);
-  const size_t o_ovf = cv.take<uint32_t>(B);
-  const size_t o_scnt = cv.take<uint32_t>(B);
-  const size_t o_sovf = cv.take<uint32_t>(B);
-  const size_t o_flag = cv.take<uint32_t>(B);
-  const size_t o_krem = cv.take<int32_t>(B);
-  const size_t o_nflag = cv.take<uint32_t>(1);
-  const size_t o_state_end = cv.take<char>(0);
-  const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
-  const size_t o_err = cv.take<uint32_t>(1);
-  const size_t o_kq = cv.take<int32_t>(B);
-  const size_t o_rank = cv.take<int32_t>(B);
-  const size_t o_hist = cv.take<uint32_t>((size_t)B * kFbBins);
-  const size_t o_samp = cv.take<uint64_t>((size_t)B * ix->samp_cap);
-  const size_t o_cand = cv.take<uint64_t>((size_t)B * ix->cand_cap);
-  const size_t o_oids = cv.take<int32_t>((size_t)B * ix->max_k);
-  const size_t o_osc = cv.take<float>((size_t)B * ix->max_k);
-  const size_t o_ocnt = cv.take<int32_t>(B);
-  const size_t o_ocand = cv.take<int32_t>(B);
-  const size_t o_ofb = cv.take<int32_t>(B);
-  const bool lowp = ix->elem != kElemF32;
-  const size_t o_cids = cv.take<int32_t>(lowp ? (size_t)B * ix->max_kq : 0);
-  const size_t o_csc = cv.take<float>(lowp ? (size_t)B * ix->max_kq : 0);
-  const size_t o_ccnt = cv.take<int32_t>(lowp ? B : 0);
-  const size_t o_kfin = cv.take<int32_t>(lowp ? B : 0);
-  const size_t o_ties = cv.take<int32_t>(lowp ? B : 0);
-  const size_t o_filt = cv.take<char>(ix->filt_bytes);
-  ix->ws_bytes = align_up(cv.off, 256);
-  if (cudaMalloc(&ix->ws, ix->ws_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return cleanup(fail(LR_ERR_NOMEM, "cannot allocate the search workspace (" + std::to_string(ix->ws_bytes) +
-                                          " bytes); lower max_batch, max_k or max_sparse_terms"));
-  }
-  ix->device_bytes += ix->ws_bytes;
-  char *w = ix->ws;
-  ix->q_raw = (float *)(w + o_qraw);
-  ix->q_ws = (float *)(w + o_qws);
-  ix->sparse_bm = nsp ? (uint32_t *)(w + o_sparse) : nullptr;
-  ix->state = w + o_state;
-  ix->state_bytes = o_state_end - o_state;
-  ix->tau = (uint64_t *)(w + o_tau);
-  ix->prefix = (uint64_t *)(w + o_pre);
-  ix->pass = (unsigned long long *)(w + o_pass);
-  ix->cnt = (uint32_t *)(w + o_cnt);
-  ix->ovf = (uint32_t *)(w + o_ovf);
-  ix->scnt = (uint32_t *)(w + o_scnt);
-  ix->sovf = (uint32_t *)(w + o_sovf);
-  ix->flag = (uint32_t *)(w + o_flag);
-  ix->krem = (int32_t *)(w + o_krem);
-  ix->n_flag = (uint32_t *)(w + o_nflag);
-  ix->done_ctr = (uint32_t *)(w + o_done);
-  ix->work_ctr = ix->done_ctr + 1;
-  ix->err = (uint32_t *)(w + o_err);
-  ix->kq = (int32_t *)(w + o_kq);
-  ix->rank = (int32_t *)(w + o_rank);
-  ix->hist = (uint32_t *)(w + o_hist);
-  ix->samp_buf = (uint64_t *)(w + o_samp);
-  ix->cand_buf = (uint64_t *)(w + o_cand);
-  ix->o_ids = (int32_t *)(w + o_oids);
-  ix->o_sc = (float *)(w + o_osc);
-  ix->o_cnt = (int32_t *)(w + o_ocnt);
-  ix->o_cand = (int32_t *)(w + o_ocand);
-  ix->o_fb = (int32_t *)(w + o_ofb);
-  if (lowp) {
-    ix->c_ids = (int32_t *)(w + o_cids);
-    ix->c_sc = (float *)(w + o_csc);
-    ix->c_cnt = (int32_t *)(w + o_ccnt);
-    ix->kfin = (int32_t *)(w + o_kfin);
-    ix->o_ties = (int32_t *)(w + o_ties);
-  }
-  ix->filt_d = w + o_filt;
-  CK2(cudaMemsetAsync(ix->done_ctr, 0, 2 * sizeof(uint32_t), s));
-  CK2(cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), s));
-  CK2(cudaMemsetAsync(ix->hist, 0, (size_t)B * kFbBins * sizeof(uint32_t), s));
-  for (int i = 0; i < 2; ++i) {
-    CK2(cudaHostAlloc((void **)&ix->filt_h[i], ix->filt_bytes, cudaHostAllocDefault));
-    CK2(cudaEventCreateWithFlags(&ix->filt_ev[i], cudaEventDisableTiming));
-  }
-  ix->sparse_stamp.assign(ix->vocab, 0);
-  ix->sparse_id.assign(ix->vocab, -1);
-  ix->local_stamp.assign(ix->vocab, 0);
-  ix->local_id.assign(ix->vocab, -1);
 
   // ---- input validity recorded by the build kernels
   uint32_t e = 0;

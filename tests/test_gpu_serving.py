@@ -1,0 +1,106 @@
+"""Serving: continuous batching over a resident index (needs a GPU).
+
+Each request's result must equal an lr_search of that request alone with the same plan (bit for bit),
+and agree with the oracle within the tolerance rule whatever plan its batch ends up using.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from oracle.compare import check_topk
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_13435_b300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def setup(lr):
+    c = datagen.corpus(9, 60_000, 64, 2048, 16.0, 1.1)
+    po, pid = c.postings()
+    idx = lr.lr_index_create(c.X, c.V, post_off=po, post_ids=pid, n_dense_terms=64, metric="cosine", max_batch=64,
+                             max_k=200)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(40):
+        B = int(rng.integers(1, 9))
+        K = int(rng.choice([10, 50, 200]))
+        reqs.append((datagen.query_embeddings(200 + i, B, 64), datagen.filters(100 + i, B, c.V, 1.1), K))
+    yield c, idx, reqs
+    lr.lr_index_destroy(idx)
+
+
+@pytest.mark.parametrize("plan", ["gemv", "tc"])
+def test_each_result_equals_the_request_alone(lr, setup, plan):
+    c, idx, reqs = setup
+    with lr.Server(idx, slots=3, max_queries=32, plan=plan) as srv:
+        tickets = [srv.submit(Q, f, K) for (Q, f, K) in reqs]  # all in flight at once
+        outs = [srv.wait(t, Q.shape[0], K) for t, (Q, f, K) in zip(tickets, reqs)]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["submitted"] == len(reqs)
+    assert st["batches"] < len(reqs)  # requests were batched together
+    assert st["queries"] == sum(Q.shape[0] for Q, _, _ in reqs)
+    assert 0.0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    for (Q, f, K), (ids, sc, cnt, lat) in zip(reqs, outs):
+        ia, sa, ca = lr.lr_search(idx, Q, f, K, plan=plan)
+        assert np.array_equal(cnt, ca) and np.array_equal(ids, ia) and np.array_equal(sc, sa)
+        assert lat > 0.0
+
+
+def test_auto_plan_results_match_the_oracle(lr, setup):
+    c, idx, reqs = setup
+    with lr.Server(idx, slots=2, max_queries=48, plan="auto") as srv:
+        tickets = [srv.submit(Q, f, K) for (Q, f, K) in reqs[:12]]
+        outs = [srv.wait(t, Q.shape[0], K) for t, (Q, f, K) in zip(tickets, reqs[:12])]
+    for (Q, f, K), (ids, sc, cnt, _) in zip(reqs[:12], outs):
+        ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+        check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f, metric="cosine")
+
+
+def test_concurrent_clients(lr, setup):
+    c, idx, reqs = setup
+    alone = [lr.lr_search(idx, Q, f, K, plan="gemv") for (Q, f, K) in reqs]
+    errors = []
+    with lr.Server(idx, slots=2, max_queries=24, plan="gemv") as srv:
+        def client(part):
+            try:
+                for i in part:
+                    Q, f, K = reqs[i]
+                    ids, sc, cnt, _ = srv.wait(srv.submit(Q, f, K), Q.shape[0], K)
+                    if not (np.array_equal(ids, alone[i][0]) and np.array_equal(sc, alone[i][1])):
+                        errors.append(i)
+            except Exception as e:  # noqa: BLE001 - reported below
+                errors.append(repr(e))
+
+        threads = [threading.Thread(target=client, args=(range(t, len(reqs), 4),)) for t in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+    assert not errors, errors
+
+
+def test_admission_limits(lr, setup):
+    c, idx, reqs = setup
+    with lr.Server(idx, slots=4, max_queries=8, plan="gemv", arena_bytes=1) as srv:
+        assert srv.stats()["slots"] == 1  # the arena holds one slot
+        Q = datagen.query_embeddings(1, 9, 64)
+        f = datagen.filters(1, 9, c.V, 1.1)
+        with pytest.raises(lr.LRError) as e:
+            srv.submit(Q, f, 10)
+        assert e.value.status == lr.LR_ERR_WORKSPACE
+        Q, f, K = reqs[0]
+        ids, sc, cnt, _ = srv.wait(srv.submit(Q, f, K), Q.shape[0], K)
+        ia, sa, ca = lr.lr_search(idx, Q, f, K, plan="gemv")
+        assert np.array_equal(ids, ia)
