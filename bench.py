@@ -52,6 +52,16 @@ def parse():
     p.add_argument("--lam", type=float, default=40.0)
     p.add_argument("--n-dense", type=int, default=256)
     p.add_argument("--bands", default="0.001,0.01,0.1,0.5")
+    # other forms of the method (one JSON line each):
+    #   --form loss   masked softmax loss fwd+bwd, B=4096 queries vs 4096 in-batch + 16384 sampled jobs, d=128
+    #   --form serve  continuous batching over a resident 20M x 128 BF16 index, Poisson request streams
+    p.add_argument("--form", choices=("search", "loss", "serve"), default="search")
+    p.add_argument("--loss-b", type=int, default=4096)
+    p.add_argument("--loss-m", type=int, default=4096 + 16384)
+    p.add_argument("--tau", type=float, default=0.05)
+    p.add_argument("--rates", default="100,300,5000,10000,20000,50000")
+    p.add_argument("--slots", type=int, default=3)
+    p.add_argument("--max-requests", type=int, default=2000)
     a = p.parse_args()
     a.band_list = tuple(float(x) for x in a.bands.split(","))
     return a
@@ -485,10 +495,148 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_loss(args):
+    """Masked softmax loss (forward + backward) at the two-tower training-step shape."""
+    import torch
+    import datagen
+    import paper_2402_13435_b300 as lr
+
+    B, M, d = args.loss_b, args.loss_m, args.dim
+    inv_tau = 1.0 / args.tau
+    c = datagen.corpus(args.seed, M, d, 4096, 20.0, 1.1)  # jobs: in-batch positives first, then sampled
+    Q = torch.from_numpy(datagen.query_embeddings(args.seed + 1, B, d)).to(torch.bfloat16).cuda()
+    J = torch.from_numpy(c.X).to(torch.bfloat16).cuda()
+    pos = torch.arange(B, dtype=torch.int32, device="cuda")
+    f = datagen.filters(args.seed + 2, B, c.V, 1.1)
+    idx = lr.lr_index_create(c.X, c.V, bitsets=c.bitsets(), metric="dot", max_batch=B, max_k=16,
+                             max_batch_terms=16 * B)
+    npass, mask = lr.lr_filter_count(idx, f, bitmap=True)  # the term constraint as the loss mask
+    torch.cuda.synchronize()
+    ws = lr.loss_workspace(B, M, d)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd, bwd = [], []
+    for i in range(args.warmup + args.steps):
+        ev[0].record()
+        loss, lse = lr.lr_score_forward(Q, J, pos, mask, inv_tau, ws)
+        ev[1].record()
+        dQ, dJ = lr.lr_score_backward(Q, J, pos, mask, inv_tau, lse, None, ws)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[1].elapsed_time(ev[2]))
+    lr.lr_score_status(ws, B, M, d)
+    fm, bm = float(np.median(fwd)), float(np.median(bwd))
+    flops = 4 * 2.0 * B * M * d  # forward logits, recomputed logits, dZ.J and dZ^T.Q: 86 GF at this shape
+    tf = flops / ((fm + bm) / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        peak, kind = float(pk["bf16_tflops"]), "measured (bf16 burst)"
+    except (OSError, KeyError, ValueError):
+        peak, kind = 1800.0, "fallback"
+    parity = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        allowed = np.unpackbits(mask.cpu().numpy().view(np.uint8), axis=1, bitorder="little")[:, :M].astype(bool)
+        t0 = time.perf_counter()
+        ref = oracle.softmax_loss(Q.double().cpu().numpy(), J.double().cpu().numpy(), np.arange(B), allowed, inv_tau)
+        cpu_s = time.perf_counter() - t0
+        g = lambda a, r: float(np.max(np.abs(a.cpu().numpy() - r)) / max(np.max(np.abs(r)), 1e-30))
+        parity = {"loss_rel_err": abs(float(loss.item()) - ref[0]) / abs(ref[0]), "dQ_rel_err": g(dQ, ref[2]),
+                  "dJ_rel_err": g(dJ, ref[3]), "oracle": "FP64 torch autograd on the BF16 inputs",
+                  "oracle_s": round(cpu_s, 2)}
+    out = {"metric": "masked softmax loss fwd+bwd ms @B=%d M=%d d=%d BF16" % (B, M, d), "value": fm + bm,
+           "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+           "dtype": "bf16", "data": "synthetic (seeded generator)", "fwd_ms": fm, "bwd_ms": bm,
+           "config": {"workload": "two-tower step: %d queries vs %d in-batch positives + %d sampled jobs, tau=%g, "
+                                  "term mask from the cfg-1 filter generator (%.1f%% allowed)"
+                                  % (B, B, M - B, args.tau, 100.0 * float(npass.sum()) / (B * M)),
+                      "B": B, "M": M, "d": d},
+           "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                        "traffic": None, "flops_per_step": flops, "peak_kind": kind},
+           "parity": parity}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Poisson request streams against the continuous-batching server over a resident BF16 index."""
+    import torch
+    import datagen
+    import paper_2402_13435_b300 as lr
+
+    rng = np.random.default_rng(args.seed)
+    t0 = time.time()
+    c = datagen.corpus(args.seed, args.n, args.dim, args.vocab, args.lam, 1.1)
+    bands = np.geomspace(0.0005, 0.5, 8)  # selectivity log-uniform over 0.05 % .. 50 %
+    pool = []
+    for i, sb in enumerate(bands):
+        fb = datagen.filters_in_band(args.seed + 7, 96, c.V, 1.1, c.df, c.n, float(sb),
+                                     stream_offset=(i + 1) * 100_000_000)
+        pool += [fb.clauses(j) for j in range(fb.n)]
+    Qpool = datagen.query_embeddings(args.seed + 3, 4096, args.dim)
+    gen_s = time.time() - t0
+    po, pid = c.postings()
+    idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), c.V, post_off=po, post_ids=pid, n_dense_terms=-1,
+                             metric="cosine", max_batch=256, max_k=2000, dtype=args.dtype,
+                             oversample=args.oversample)
+    torch.cuda.synchronize()
+    nreq = args.max_requests
+    reqs = []
+    for i in range(nreq):
+        Bq = int(rng.integers(1, 65))
+        K = int(rng.choice([100, 500, 1000, 2000]))
+        rows = rng.integers(0, len(Qpool), size=Bq)
+        fl = [pool[int(j)] for j in rng.integers(0, len(pool), size=Bq)]
+        reqs.append((Qpool[rows], datagen.Filters.from_lists(fl), K))
+    loads = []
+    with lr.Server(idx, slots=args.slots, max_queries=256, plan=args.plan) as srv:
+        srv.wait(srv.submit(*reqs[0]), reqs[0][0].shape[0], reqs[0][2])  # warm up
+        for rate in [float(r) for r in args.rates.split(",")]:
+            srv.stats(reset=True)
+            gaps = rng.exponential(1.0 / rate, size=nreq)
+            tickets = []
+            t_start = time.perf_counter()
+            due = t_start
+            for i, (Q, f, K) in enumerate(reqs):
+                due += gaps[i]
+                while True:
+                    now = time.perf_counter()
+                    if now >= due:
+                        break
+                    time.sleep(min(due - now, 0.001))
+                tickets.append(srv.submit(Q, f, K))
+            t_sub = time.perf_counter() - t_start
+            for t, (Q, f, K) in zip(tickets, reqs):
+                srv.wait(t, Q.shape[0], K)
+            t_all = time.perf_counter() - t_start
+            st = srv.stats()
+            loads.append({"offered_rps": rate, "submitted_rps": nreq / t_sub, "achieved_rps": nreq / t_all,
+                          "achieved_qps": st["queries"] / t_all, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                          "mean_batch_queries": st["queries"] / max(st["batches"], 1), "batches": st["batches"]})
+        slots = srv.stats()["slots"]
+    best = max(l["achieved_qps"] for l in loads)
+    out = {"metric": "serving QPS with p50/p99 latency per offered request rate", "value": best,
+           "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": args.dtype,
+           "data": "synthetic (seeded generator)",
+           "config": {"workload": "resident N=%d x d=%d %s index (oversample %d), Poisson requests of 1-64 queries, "
+                                  "K in {100,500,1000,2000}, selectivity log-uniform 0.05-50%%; %d requests per load "
+                                  "point, %d slots of 256 queries" % (args.n, args.dim, args.dtype, args.oversample,
+                                                                      nreq, slots),
+                      "n_jobs": args.n, "dim": args.dim, "slots": slots},
+           "loads": loads, "setup_s": {"generate": round(gen_s, 1)}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "loss":
+        run_loss(args)
+    elif args.form == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
