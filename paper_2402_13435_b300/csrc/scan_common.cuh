@@ -36,6 +36,68 @@ __device__ __forceinline__ void eval_cnf(const ScanArgs &a, int q, const uint32_
   eval_cnf_lists(a.qc_off, a.cl_off, a.cl_slot, q, sw, pw);
 }
 
+// A query's CNF held in registers: up to 16 slot ids (one byte each, in clause
+// order) and a mask of the terms that open a clause.  Evaluating it issues only
+// independent shared-memory loads, no dependent global ones.
+struct PackedCnf {
+  uint32_t slot[4];
+  uint32_t start;  // bit t: term t opens a new clause
+  int nt;          // terms
+  bool ok;         // false: the query does not fit (more than 16 terms)
+};
+
+__device__ __forceinline__ PackedCnf pack_cnf(const ScanArgs &a, int q) {
+  PackedCnf p;
+  p.slot[0] = p.slot[1] = p.slot[2] = p.slot[3] = 0u;
+  p.start = 0u;
+  p.nt = 0;
+  p.ok = true;
+  const int c0 = a.qc_off[q], c1 = a.qc_off[q + 1];
+  for (int c = c0; c < c1; ++c) {
+    const int t0 = a.cl_off[c], t1 = a.cl_off[c + 1];
+    for (int t = t0; t < t1; ++t) {
+      const int s = a.cl_slot[t];
+      if (p.nt >= 16 || s > 255) {
+        p.ok = false;
+        return p;
+      }
+      if (t == t0) p.start |= 1u << p.nt;
+      p.slot[p.nt >> 2] |= (uint32_t)s << ((p.nt & 3) * 8);
+      ++p.nt;
+    }
+  }
+  return p;
+}
+
+__device__ __forceinline__ void eval_packed(const PackedCnf &p, const uint32_t *sw, uint32_t (&pw)[8]) {
+  uint32_t cw[8];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    pw[w] = 0xFFFFFFFFu;
+    cw[w] = 0u;
+  }
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    if (t < p.nt) {
+      if (t > 0 && ((p.start >> t) & 1u)) {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          pw[w] &= cw[w];
+          cw[w] = 0u;
+        }
+      }
+      const uint32_t s = (p.slot[t >> 2] >> ((t & 3) * 8)) & 0xFFu;
+      const uint4 *src = reinterpret_cast<const uint4 *>(sw + s * 8);
+      const uint4 lo = src[0], hi = src[1];
+      cw[0] |= lo.x; cw[1] |= lo.y; cw[2] |= lo.z; cw[3] |= lo.w;
+      cw[4] |= hi.x; cw[5] |= hi.y; cw[6] |= hi.z; cw[7] |= hi.w;
+    }
+  }
+  if (p.nt > 0)
+#pragma unroll
+    for (int w = 0; w < 8; ++w) pw[w] &= cw[w];
+}
+
 // Digit step of the exact fallback: for every participating query find the
 // digit whose bin holds the krem-th largest key, fix it in the prefix and clear
 // the histogram.  Runs in the last CTA of a kHist launch.

@@ -11,13 +11,15 @@
 // where x_hi and q_hi are exact in TF32; the unit truncates x_lo and q_lo to
 // TF32 (11 significant bits of their 13), an error below 2^-22 |x q| per term.
 //
-// One CTA per SM, ten warps with fixed roles:
-//   warp 0     producer: takes 256-row groups from the work counter, prefetches
-//              the groups' term words (cp.async), evaluates every query's CNF,
-//              publishes per-tile row messages (the mask of the queries that
-//              pass each row) and issues 2-D TMA loads (128 rows x 32 floats,
-//              128-byte swizzle) of the tiles some query passes into a ring of
-//              raw stages; tiles nobody passes are not read ("skip rows").
+// One CTA per SM, eleven warps with fixed roles:
+//   warp 0     predicate: takes 256-row groups from the work counter (read one
+//              chunk ahead), prefetches the groups' term words (cp.async),
+//              evaluates every query's CNF (held in registers when it has at
+//              most 16 terms) and publishes per-tile row messages (the mask of
+//              the queries that pass each row); tiles nobody passes are not
+//              published and never read ("skip rows").
+//   warp 10    loader: issues the 2-D TMA loads (128 rows x 32 floats, 128-byte
+//              swizzle) of every published tile into a ring of raw stages.
 //   warp 1     owns the tensor memory and issues the MMAs from one thread.  The
 //              job operand comes from tensor memory: per 8-wide K step one MMA
 //              of width 2N with x_hi against [q_hi ; q_lo] and one of width N
@@ -33,7 +35,7 @@
 //              without branches, and record the few candidates in a per-warp
 //              shared-memory list flushed to the query buffers in bulk.
 // All waits are bounded; on a timeout the error word gets LR_ERR_TIMEOUT, the
-// producer lets issued copies land, the MMA warp waits for its MMAs, and the
+// loader lets issued copies land, the MMA warp waits for its MMAs, and the
 // tensor memory is freed before the CTA exits.
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -46,9 +48,9 @@
 namespace lr {
 namespace {
 
-constexpr int kTcThreads = 320;
-constexpr int kConvWarp0 = 2;
+constexpr int kTcThreads = 352;
 constexpr int kEpiWarp0 = 6;
+constexpr int kLoadWarp = 10;
 constexpr int kMetaDepth = 4;
 constexpr int kTileRows = 128;
 constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile of 128-byte rows
@@ -221,14 +223,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const bool live1 = q1 < a.nq && (a.active == nullptr || a.active[a.q_base + q1] != 0u);
     const int64_t n_items = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
     int64_t item = 0, item_end = 0;
+    // work counter read one chunk ahead: the atomic of the next chunk is in
+    // flight while the current one is processed
+    uint32_t pref = 0;
+    if (lane == 0) pref = atomicAdd(a.work_ctr, 1u);
     auto next_group = [&]() -> int64_t {
       if (item + 1 < item_end) return a.g_begin + (++item) * a.g_step;
-      uint32_t c = 0;
-      if (lane == 0) c = atomicAdd(a.work_ctr, 1u);
-      c = __shfl_sync(0xFFFFFFFFu, c, 0);
+      const uint32_t c = __shfl_sync(0xFFFFFFFFu, pref, 0);
       item = (int64_t)c * kTcGroupChunk;
       item_end = item + kTcGroupChunk < n_items ? item + kTcGroupChunk : n_items;
-      return item < n_items ? a.g_begin + item * a.g_step : -1;
+      if (item >= n_items) return -1;
+      if (lane == 0) pref = atomicAdd(a.work_ctr, 1u);
+      return a.g_begin + item * a.g_step;
     };
     auto prefetch = [&](int64_t g, int t) {
       uint32_t *dst = slot_tab + (size_t)t * a.n_slots * 8;
@@ -238,8 +244,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       cp_async_commit();
     };
+    // each lane's queries' CNFs in registers (queries with more than 16 terms use the lists)
+    const PackedCnf pk0 = live0 ? pack_cnf(a, q0) : PackedCnf{};
+    const PackedCnf pk1 = live1 ? pack_cnf(a, q1) : PackedCnf{};
     unsigned long long pass0 = 0, pass1 = 0;
-    uint64_t pm = 0, pr = 0;
+    uint64_t pm = 0;
     int t = 0;
     int64_t g = next_group();
     if (g >= 0) prefetch(g, 0);
@@ -251,11 +260,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       __syncwarp();
       uint32_t pw0[8], pw1[8];
       const uint32_t *tab = slot_tab + (size_t)t * a.n_slots * 8;
-      if (live0) eval_cnf(a, q0, tab, pw0);
+      if (live0 && pk0.ok) eval_packed(pk0, tab, pw0);
+      else if (live0) eval_cnf(a, q0, tab, pw0);
       else
 #pragma unroll
         for (int w = 0; w < 8; ++w) pw0[w] = 0u;
-      if (live1) eval_cnf(a, q1, tab, pw1);
+      if (live1 && pk1.ok) eval_packed(pk1, tab, pw1);
+      else if (live1) eval_cnf(a, q1, tab, pw1);
       else
 #pragma unroll
         for (int w = 0; w < 8; ++w) pw1[w] = 0u;
@@ -298,18 +309,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&meta_full[m]);
         ++pm;
-        for (int c = 0; c < C && ok; ++c) {
-          const int s = (int)(pr % (uint64_t)S);
-          if (!warp_wait(&raw_empty[s], (uint32_t)((pr / S) & 1u) ^ 1u, lane)) {
-            ok = false;
-            break;
-          }
-          if (lane == 0) {
-            mbar_arrive_expect_tx(&raw_full[s], (uint32_t)(kTileRows * tc_row_bytes(E)));
-            tma_load_2d(raw + (size_t)s * kChunkBytes, &tmap, c * tc_epc(E), (int)row0, &raw_full[s]);
-          }
-          ++pr;
-        }
       }
       g = gn;
       gn = gnn;
@@ -328,15 +327,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ok = false;
       }
     }
-    if (!ok && lane == 0) {
-      atomicOr(a.err, kErrTimeout);
-      const uint64_t first = pr > (uint64_t)S ? pr - S : 0;  // let issued loads land
-      for (uint64_t p = first; p < pr; ++p) mbar_wait(&raw_full[p % S], (uint32_t)((p / S) & 1u));
-    }
+    if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
     if (a.pass_cnt != nullptr) {
       if (live0) atomicAdd(&a.pass_cnt[a.q_base + q0], pass0);
       if (live1) atomicAdd(&a.pass_cnt[a.q_base + q1], pass1);
     }
+  } else if (warp == kLoadWarp) {
+    // ------------------------------------------------------------- loader
+    // issues the TMA loads of every published tile, in message order, into the
+    // ring of raw stages; decoupled from the predicate warp so that neither
+    // waits for the other's latencies
+    if (lane == 0) {
+      uint64_t pm = 0, pr = 0;
+      while (ok) {
+        const int m = (int)(pm % kMetaDepth);
+        if (!mbar_wait(&meta_full[m], (uint32_t)((pm / kMetaDepth) & 1u))) {
+          ok = false;
+          break;
+        }
+        if (meta[m].done) break;
+        const int row0 = (int)meta[m].row0;
+        for (int c = 0; c < C; ++c) {
+          const int s = (int)(pr % (uint64_t)S);
+          if (!mbar_wait(&raw_empty[s], (uint32_t)((pr / S) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&raw_full[s], (uint32_t)(kTileRows * tc_row_bytes(E)));
+          tma_load_2d(raw + (size_t)s * kChunkBytes, &tmap, c * tc_epc(E), row0, &raw_full[s]);
+          ++pr;
+        }
+        if (!ok) break;
+        ++pm;
+      }
+      if (!ok) {
+        atomicOr(a.err, kErrTimeout);
+        const uint64_t first = pr > (uint64_t)S ? pr - S : 0;  // let issued loads land
+        for (uint64_t p = first; p < pr; ++p) mbar_wait(&raw_full[p % S], (uint32_t)((p / S) & 1u));
+      }
+    }
+    __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issuer
     if (lane == 0) {
