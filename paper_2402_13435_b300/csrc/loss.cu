@@ -36,7 +36,15 @@ constexpr float kLog2e = 1.4426950408889634f;
 enum LossMode : int { kFwd = 0, kDq = 1, kDj = 2 };
 
 struct LossSmem {
-  size_t r, c, ct, dz, bars, holder, total;
+  size_t r, c, ct, dz, stage, bars, holder, total;
+};
+
+// kDj staging of one query tile for the epilogue: mask words of the CTA's 128
+// job rows (4 per query), positives and log-sum-exps of the tile's 64 queries
+struct DjStage {
+  uint32_t mask[kCRows * 4];
+  int32_t pos[kCRows];
+  float lse[kCRows];
 };
 
 __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
@@ -50,6 +58,8 @@ __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
   off += mode == kFwd ? 0 : (size_t)2 * dp * 128;  // transposed C tile: dp rows x 64 values
   L.dz = off;
   off += mode == kFwd ? 0 : (size_t)2 * 2 * kRRows * 128;  // [buffer][hi, lo] 128 rows x 64 values
+  L.stage = off;
+  off += mode == kDj ? 2 * sizeof(DjStage) : 0;
   L.bars = off;
   off += 16 * 8;
   L.holder = off;
@@ -76,6 +86,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   unsigned char *sc = smem + L.c;
   unsigned char *sct = smem + L.ct;
   unsigned char *sdz = smem + L.dz;
+  DjStage *stg = reinterpret_cast<DjStage *>(smem + L.stage);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
   uint64_t *bar_r = bars, *c_full = bars + 1, *c_empty = bars + 3, *s_full = bars + 5, *s_empty = bars + 7;
   uint64_t *dz_full = bars + 9, *dz_empty = bars + 11, *acc_full = bars + 13;
@@ -209,9 +220,67 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     }
     float m = -INFINITY, ssum = 0.f, zpos = 0.f;
     bool have_pos = false;
-    for (int t = 0; t < T && ok; ++t) {
+    // Mask words (and for kDj the query tile's positives and lse) are fetched
+    // one tile ahead.  kFwd/kDq: this row's two words, in registers.  kDj: the
+    // 128 epilogue threads stage the query tile in shared memory (double
+    // buffered; each iteration ends at one named barrier that every epilogue
+    // warp reaches, also after a failed wait, so no warp waits forever).
+    uint32_t nw0 = ~0u, nw1 = ~0u;  // kFwd/kDq: next tile's mask words
+    uint32_t sm0 = 0u, sm1 = 0u;    // kDj: this thread's share of the next stage
+    int spos = -1;
+    float slse = 0.f;
+    auto fetch_row_words = [&](int tt) {
+      const int cc0 = (t0 + tt) * kCRows;
+      nw0 = nw1 = ~0u;
+      if (rvalid && a.mask != nullptr && cc0 < a.M) {
+        const uint32_t *mrow = a.mask + (size_t)grow * a.Mw + (cc0 >> 5);
+        nw0 = __ldg(mrow);
+        nw1 = (cc0 >> 5) + 1 < a.Mw ? __ldg(mrow + 1) : 0u;
+      }
+    };
+    auto fetch_stage = [&](int tt) {
+      const int cc0 = (t0 + tt) * kCRows;
+      uint32_t v[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int i = r + k * kRRows;
+        const int q = cc0 + (i >> 2), w = (r0 >> 5) + (i & 3);
+        v[k] = (a.mask != nullptr && q < a.B && w < a.Mw) ? __ldg(a.mask + (size_t)q * a.Mw + w) : 0u;
+      }
+      sm0 = v[0];
+      sm1 = v[1];
+      const int q = cc0 + r;
+      spos = (r < kCRows && q < a.B) ? __ldg(a.pos + q) : -1;
+      slse = (r < kCRows && q < a.B) ? __ldg(a.lse + q) : 0.f;
+    };
+    auto store_stage = [&](int buf) {
+      DjStage &st = stg[buf];
+      st.mask[r] = sm0;
+      st.mask[r + kRRows] = sm1;
+      if (r < kCRows) {
+        st.pos[r] = spos;
+        st.lse[r] = slse;
+      }
+    };
+    if (MODE == kDj) {
+      if (T > 0) {
+        fetch_stage(0);
+        store_stage(0);
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    } else if (T > 0) {
+      fetch_row_words(0);
+    }
+    for (int t = 0; t < T; ++t) {
       const int b = t & 1;
       const int c0 = (t0 + t) * kCRows;
+      const uint32_t cw0 = nw0, cw1 = nw1;
+      if (t + 1 < T) {
+        if (MODE == kDj) fetch_stage(t + 1);
+        else fetch_row_words(t + 1);
+      }
+      do {
+      if (!ok) break;
       if (!wwait(&s_full[b], (uint32_t)((t >> 1) & 1), lane)) {
         ok = false;
         break;
@@ -228,26 +297,27 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&s_empty[b]);
       // allowed columns of this tile as a 64-bit mask
-      uint64_t allow = 0ull;
+      // allowed columns of this tile: bit c of al[c / 32]
+      uint32_t al[2] = {0u, 0u};
       if (rvalid) {
         if (MODE != kDj) {
-          uint64_t bits = ~0ull;
-          if (a.mask != nullptr && c0 < a.M) {
-            const uint32_t *mrow = a.mask + (size_t)grow * a.Mw + (c0 >> 5);
-            const uint32_t w0 = __ldg(mrow), w1 = (c0 >> 5) + 1 < a.Mw ? __ldg(mrow + 1) : 0u;
-            bits = ((uint64_t)w1 << 32) | w0;
-          }
+          uint32_t w0 = cw0, w1 = cw1;
           const int lim = a.M - c0;  // columns past M do not exist
-          const uint64_t exist = lim >= 64 ? ~0ull : (lim > 0 ? ((1ull << lim) - 1ull) : 0ull);
-          if (pos_row >= c0 && pos_row < c0 + 64) bits |= 1ull << (pos_row - c0);
-          allow = bits & exist;
+          w0 &= lim >= 32 ? ~0u : (lim > 0 ? ((1u << lim) - 1u) : 0u);
+          w1 &= lim >= 64 ? ~0u : (lim > 32 ? ((1u << (lim - 32)) - 1u) : 0u);
+          const int pc = pos_row - c0;
+          if (pc >= 0 && pc < 32) w0 |= 1u << pc;
+          if (pc >= 32 && pc < 64) w1 |= 1u << (pc - 32);
+          al[0] = w0;
+          al[1] = w1;
         } else {
+          const DjStage &st = stg[b];
           const int lim = a.B - c0;
-          for (int c = 0; c < 64 && c < lim; ++c) {
-            const int q = c0 + c;
-            bool al = a.mask == nullptr || ((__ldg(a.mask + (size_t)q * a.Mw + (grow >> 5)) >> (grow & 31)) & 1u);
-            al = al || __ldg(a.pos + q) == grow;
-            allow |= (uint64_t)(al ? 1u : 0u) << c;
+#pragma unroll
+          for (int c = 0; c < 64; ++c) {
+            const bool ok_c = c < lim && (a.mask == nullptr || ((st.mask[c * 4 + (r >> 5)] >> (r & 31)) & 1u) ||
+                                          st.pos[c] == grow);
+            al[c >> 5] |= (ok_c ? 1u : 0u) << (c & 31);
           }
         }
       }
@@ -255,14 +325,16 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         float tmax = -INFINITY;
 #pragma unroll
         for (int c = 0; c < 64; ++c)
-          if ((allow >> c) & 1ull) tmax = fmaxf(tmax, __uint_as_float(sv[c]) * a.inv_tau);
+          tmax = fmaxf(tmax, ((al[c >> 5] >> (c & 31)) & 1u) ? __uint_as_float(sv[c]) * a.inv_tau : -INFINITY);
         if (tmax > -INFINITY) {
           const float mn = fmaxf(m, tmax);
           float add = 0.f;
 #pragma unroll
-          for (int c = 0; c < 64; ++c)
-            if ((allow >> c) & 1ull) add += exp2f((__uint_as_float(sv[c]) * a.inv_tau - mn) * kLog2e);
-          ssum = ssum * exp2f((m - mn) * kLog2e) + add;
+          for (int c = 0; c < 64; ++c) {
+            const float e = __expf(__uint_as_float(sv[c]) * a.inv_tau - mn);
+            add += ((al[c >> 5] >> (c & 31)) & 1u) ? e : 0.f;
+          }
+          ssum = ssum * __expf(m - mn) + add;
           m = mn;
         }
         if (pos_row >= c0 && pos_row < c0 + 64) {
@@ -281,6 +353,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         unsigned char *dh = sdz + (size_t)(2 * b) * kRRows * 128 + (size_t)r * 128;
         unsigned char *dl = sdz + (size_t)(2 * b + 1) * kRRows * 128 + (size_t)r * 128;
         const float g = (a.dloss != nullptr ? __ldg(a.dloss) : 1.f) * a.inv_b;
+        const int pc = pos_row - c0;  // kDq: the positive's column in this tile
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t hw[4], lw[4];
@@ -290,26 +363,23 @@ __global__ void __launch_bounds__(kLossThreads, 1)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int c = ch * 8 + u * 2 + h;
-              float dz = 0.f;
-              if ((allow >> c) & 1ull) {
-                const float z = __uint_as_float(sv[c]) * a.inv_tau;
-                float lse, ispos;
-                if (MODE == kDq) {
-                  lse = lse_row;
-                  ispos = (c0 + c) == pos_row ? 1.f : 0.f;
-                } else {
-                  lse = __ldg(a.lse + c0 + c);
-                  ispos = __ldg(a.pos + c0 + c) == grow ? 1.f : 0.f;
-                }
-                dz = (exp2f((z - lse) * kLog2e) - ispos) * g;
+              const float z = __uint_as_float(sv[c]) * a.inv_tau;
+              float lse, ispos;
+              if (MODE == kDq) {
+                lse = lse_row;
+                ispos = c == pc ? 1.f : 0.f;
+              } else {
+                lse = stg[b].lse[c];
+                ispos = stg[b].pos[c] == grow ? 1.f : 0.f;
               }
-              dz2[h] = dz;
+              const float dz = (__expf(z - lse) - ispos) * g;
+              dz2[h] = ((al[c >> 5] >> (c & 31)) & 1u) ? dz : 0.f;
             }
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(dz2[0]), h1 = __float2bfloat16_rn(dz2[1]);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(dz2[0] - __bfloat162float(h0));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(dz2[1] - __bfloat162float(h1));
-            hw[u] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            lw[u] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            const __nv_bfloat162 hv = __float22bfloat162_rn(make_float2(dz2[0], dz2[1]));
+            const float2 hf = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __float22bfloat162_rn(make_float2(dz2[0] - hf.x, dz2[1] - hf.y));
+            hw[u] = *reinterpret_cast<const uint32_t *>(&hv);
+            lw[u] = *reinterpret_cast<const uint32_t *>(&lv);
           }
           const int slot = ((ch ^ (r & 7)) & 7) << 4;
           *reinterpret_cast<uint4 *>(dh + slot) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -318,6 +388,11 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&dz_full[b]);
+      }
+      } while (0);
+      if (MODE == kDj) {  // the next tile's stage, then this tile's barrier (every iteration, every warp)
+        if (t + 1 < T) store_stage((t + 1) & 1);
+        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
     }
     if (MODE == kFwd) {

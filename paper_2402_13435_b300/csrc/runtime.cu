@@ -1103,8 +1103,29 @@ namespace {
 // Geometry and workspace of the loss passes for B queries, M jobs, dimension d.
 struct LossPlan {
   int Bp = 0, Mp = 0, dp = 0, n_ctiles = 0, c_per_split = 0, splits = 0;
-  size_t o_qp = 0, o_qt = 0, o_jp = 0, o_jt = 0, o_pm = 0, o_ps = 0, o_zp = 0, o_dq = 0, o_st = 0, total = 0;
+  int nj_ctiles = 0, cj_per_split = 0, splits_j = 0;  // the dJ pass: job tiles against query tiles
+  size_t o_qp = 0, o_qt = 0, o_jp = 0, o_jt = 0, o_pm = 0, o_ps = 0, o_zp = 0, o_dq = 0, o_dj = 0, o_st = 0,
+         total = 0;
 };
+
+// Split of the streamed range over CTAs: the count (at most 16) that minimises
+// (waves of CTAs over the SMs) x (streamed tiles per CTA + a CTA's fixed cost,
+// about two tiles: tensor-memory allocation and the resident tile's load).
+void choose_split(int rtiles, int ctiles, int sms, int &splits, int &per) {
+  long best = -1;
+  splits = 1;
+  per = ctiles;
+  for (int s = 1; s <= std::min(ctiles, 16); ++s) {
+    const int p = (ctiles + s - 1) / s;
+    const int se = (ctiles + p - 1) / p;
+    const long cost = (long)((rtiles * se + sms - 1) / sms) * (p + 2);
+    if (best < 0 || cost < best) {
+      best = cost;
+      splits = se;
+      per = p;
+    }
+  }
+}
 
 LossPlan loss_plan(int B, int M, int d, int sms) {
   LossPlan P;
@@ -1112,10 +1133,9 @@ LossPlan loss_plan(int B, int M, int d, int sms) {
   P.Mp = (M + 127) / 128 * 128;
   P.dp = d <= 64 ? 64 : 128;
   P.n_ctiles = P.Mp / 64;
-  const int rtiles = P.Bp / 128;
-  const int want = std::max(1, std::min((sms + rtiles - 1) / rtiles, P.n_ctiles));
-  P.c_per_split = (P.n_ctiles + want - 1) / want;
-  P.splits = (P.n_ctiles + P.c_per_split - 1) / P.c_per_split;
+  choose_split(P.Bp / 128, P.n_ctiles, sms, P.splits, P.c_per_split);
+  P.nj_ctiles = P.Bp / 64;
+  choose_split(P.Mp / 128, P.nj_ctiles, sms, P.splits_j, P.cj_per_split);
   Carver cv;
   P.o_qp = cv.take<uint16_t>((size_t)P.Bp * P.dp);
   P.o_qt = cv.take<uint16_t>((size_t)P.Bp * P.dp);
@@ -1125,6 +1145,7 @@ LossPlan loss_plan(int B, int M, int d, int sms) {
   P.o_ps = cv.take<float>((size_t)P.splits * P.Bp);
   P.o_zp = cv.take<float>(P.Bp);
   P.o_dq = cv.take<float>((size_t)P.splits * P.Bp * P.dp);
+  P.o_dj = cv.take<float>((size_t)P.splits_j * P.Mp * P.dp);
   P.o_st = cv.take<uint32_t>(4);
   P.total = align_up(cv.off, 256);
   return P;
@@ -1246,15 +1267,16 @@ lr_status lr_score_backward(const void *Q, const void *J, int32_t B, int32_t M, 
   a.out_cols = P.dp;
   LR_CK(launch_loss_pass(1, a, P.Bp / 128, P.splits, &T.qr, &T.jc, &T.jt, s));
   LR_CK(launch_loss_dq_reduce((const float *)(w + P.o_dq), P.splits, (size_t)P.Bp * P.dp, B, d, P.dp, dQ, s));
-  // dJ: job tiles against every query tile, written straight to dJ
+  // dJ: job tiles against query tiles, per-split partials, then their sum
   LossArgs b = a;
-  b.n_ctiles = P.Bp / 64;
-  b.c_per_split = P.Bp / 64;
-  b.out = dJ;
-  b.out_split = 0;
-  b.out_ld = d;
-  b.out_cols = d;
-  LR_CK(launch_loss_pass(2, b, P.Mp / 128, 1, &T.jr, &T.qc, &T.qt, s));
+  b.n_ctiles = P.nj_ctiles;
+  b.c_per_split = P.cj_per_split;
+  b.out = (float *)(w + P.o_dj);
+  b.out_split = (size_t)P.Mp * P.dp;
+  b.out_ld = P.dp;
+  b.out_cols = P.dp;
+  LR_CK(launch_loss_pass(2, b, P.Mp / 128, P.splits_j, &T.jr, &T.qc, &T.qt, s));
+  LR_CK(launch_loss_dq_reduce((const float *)(w + P.o_dj), P.splits_j, (size_t)P.Mp * P.dp, M, d, P.dp, dJ, s));
   return LR_OK;
 }
 
