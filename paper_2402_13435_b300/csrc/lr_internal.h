@@ -106,6 +106,12 @@ struct ScanArgs {
   int32_t hist_pass;             // 0 .. kFbPasses-1
   int32_t batch;                 // B (for the last-CTA step)
   uint32_t *err;                 // device error word
+  // tile list of the tensor-core plan: written by the tile filter, read by the
+  // scan, whose last CTA resets the count
+  int32_t *tile_row;             // [tile_cap] first row of each listed 128-row tile
+  void *tile_msg;                // [tile_cap][128] row masks: bit q = query q passes (32-bit if nq <= 32, else 64-bit)
+  uint32_t *tile_cnt;            // tiles listed
+  int64_t tile_cap;
 };
 
 struct SelectArgs {
@@ -137,6 +143,9 @@ struct SelectArgs {
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s);
+// Tile filter (term predicate of the tensor-core plan) and the scan that reads
+// its list; launch them back to back on one stream.
+cudaError_t launch_tile_filter(const ScanArgs &a, int max_grid, cudaStream_t s);
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
 

@@ -8,6 +8,7 @@
 namespace lr {
 
 constexpr uint32_t kErrTimeout = 1u << 4;  // device error bit: a bounded wait gave up
+constexpr uint32_t kErrTileList = 1u << 6;  // device error bit: the tile list overflowed (internal)
 constexpr uint32_t kSpinLimit = 1u << 20;  // try_wait calls before giving up (about a second at most)
 // A waiting thread sleeps until the phase completes or this many nanoseconds
 // pass, instead of spinning and taking issue slots from the working warps.

@@ -127,6 +127,10 @@ struct lr_index {
   uint32_t *n_flag = nullptr, *done_ctr = nullptr, *work_ctr = nullptr, *err = nullptr;
   uint32_t *hist = nullptr;
   uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
+  int32_t *tile_row = nullptr;  // tile list of the tensor-core plan
+  uint64_t *tile_msg = nullptr;
+  uint32_t *tile_cnt = nullptr;
+  int64_t tile_cap = 0;
   int32_t *o_ids = nullptr, *o_cnt = nullptr, *o_cand = nullptr, *o_fb = nullptr;
   int32_t *c_ids = nullptr, *c_cnt = nullptr, *kfin = nullptr, *o_ties = nullptr;  // precision form
   float *c_sc = nullptr;
@@ -184,7 +188,11 @@ lr_status check_err_word(lr_index *ix, cudaStream_t s, const char *where) {
     if (e & 2u) m += "inconsistent exact-selection state; ";
     if (e & 16u) m += "a bounded device wait timed out; ";
     if (e & 32u) m += "more than 1024 candidates inside the FP64 near-tie band; ";
-    const lr_status st = (e & 16u) ? LR_ERR_TIMEOUT : (e & 2u) ? LR_ERR_CUDA : (e & 32u) ? LR_ERR_WORKSPACE : LR_ERR_INVALID;
+    if (e & 64u) m += "tile list overflow (internal); ";
+    const lr_status st = (e & 16u)          ? LR_ERR_TIMEOUT
+                         : (e & (2u | 64u)) ? LR_ERR_CUDA
+                         : (e & 32u)        ? LR_ERR_WORKSPACE
+                                            : LR_ERR_INVALID;
     return fail(st, m);
   }
   return LR_OK;
@@ -328,6 +336,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_flag = cv.take<uint32_t>(B);
   const size_t o_krem = cv.take<int32_t>(B);
   const size_t o_nflag = cv.take<uint32_t>(1);
+  const size_t o_tcnt = cv.take<uint32_t>(1);
   const size_t o_state_end = cv.take<char>(0);
   const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
   const size_t o_err = cv.take<uint32_t>(1);
@@ -336,6 +345,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_hist = cv.take<uint32_t>((size_t)B * kFbBins);
   const size_t o_samp = cv.take<uint64_t>((size_t)B * ix->samp_cap);
   const size_t o_cand = cv.take<uint64_t>((size_t)B * ix->cand_cap);
+  ix->tile_cap = 2 * ix->n_groups;  // every 128-row tile of the index
+  const size_t o_trow = cv.take<int32_t>((size_t)ix->tile_cap);
+  const size_t o_tmsg = cv.take<uint64_t>((size_t)ix->tile_cap * 128);
   const size_t o_oids = cv.take<int32_t>((size_t)B * ix->max_k);
   const size_t o_osc = cv.take<float>((size_t)B * ix->max_k);
   const size_t o_ocnt = cv.take<int32_t>(B);
@@ -379,6 +391,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->hist = (uint32_t *)(w + o_hist);
   ix->samp_buf = (uint64_t *)(w + o_samp);
   ix->cand_buf = (uint64_t *)(w + o_cand);
+  ix->tile_row = (int32_t *)(w + o_trow);
+  ix->tile_msg = (uint64_t *)(w + o_tmsg);
+  ix->tile_cnt = (uint32_t *)(w + o_tcnt);
   ix->o_ids = (int32_t *)(w + o_oids);
   ix->o_sc = (float *)(w + o_osc);
   ix->o_cnt = (int32_t *)(w + o_ocnt);
@@ -860,6 +875,10 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.done_ctr = ix->done_ctr;
     a.work_ctr = ix->work_ctr;
     a.batch = B;
+    a.tile_row = ix->tile_row;
+    a.tile_msg = ix->tile_msg;
+    a.tile_cnt = ix->tile_cnt;
+    a.tile_cap = ix->tile_cap;
     return a;
   };
   const int vec = ix->d_pad / 32;
@@ -869,8 +888,12 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ix->num_sms));
   };
   auto launch_scan = [&](const ScanArgs &a, int64_t groups) {
-    return plan == LR_PLAN_TC ? launch_scan_tc(a, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(groups), s)
-                              : launch_scan_gemv(a, nq_tmpl(a.nq), vec, grid_for(groups), s);
+    if (plan != LR_PLAN_TC) return launch_scan_gemv(a, nq_tmpl(a.nq), vec, grid_for(groups), s);
+    // the term predicate first (its tile list feeds the scan), then the scan
+    ++n_launch;
+    const cudaError_t e = launch_tile_filter(a, 2 * ix->num_sms, s);
+    if (e != cudaSuccess) return e;
+    return launch_scan_tc(a, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(2 * groups), s);
   };
 
   // 1. threshold sample

@@ -11,15 +11,13 @@
 // where x_hi and q_hi are exact in TF32; the unit truncates x_lo and q_lo to
 // TF32 (11 significant bits of their 13), an error below 2^-22 |x q| per term.
 //
-// One CTA per SM, eleven warps with fixed roles:
-//   warp 0     predicate: takes 256-row groups from the work counter (read one
-//              chunk ahead), prefetches the groups' term words (cp.async),
-//              evaluates every query's CNF (held in registers when it has at
-//              most 16 terms) and publishes per-tile row messages (the mask of
-//              the queries that pass each row); tiles nobody passes are not
-//              published and never read ("skip rows").
-//   warp 10    loader: issues the 2-D TMA loads (128 rows x 32 floats, 128-byte
-//              swizzle) of every published tile into a ring of raw stages.
+// The term predicate runs first, in the tile filter: it lists the 128-row
+// tiles that some query passes, each with its per-row query masks; tiles nobody
+// passes are never read ("skip rows").  CTA b of the scan takes list entries
+// b, b + grid, b + 2 grid, ..., so every role knows the tile sequence without
+// waiting for another.  One CTA per SM, ten warps with fixed roles:
+//   warp 0     loader: issues the 2-D TMA loads (128 rows x 32 floats, 128-byte
+//              swizzle) of its tiles into a ring of raw stages.
 //   warp 1     owns the tensor memory and issues the MMAs from one thread.  The
 //              job operand comes from tensor memory: per 8-wide K step one MMA
 //              of width 2N with x_hi against [q_hi ; q_lo] and one of width N
@@ -31,6 +29,7 @@
 //              stages therefore never wait on the tensor core, and shared
 //              memory holds little besides them.
 //   warps 6-9  epilogue: read the accumulator (warp w owns lanes 32*(w%4) ..),
+//              with the row masks of the tile read one tile ahead,
 //              test every passing (row, query) against the query's threshold
 //              without branches, and record the few candidates in a per-warp
 //              shared-memory list flushed to the query buffers in bulk.
@@ -41,6 +40,8 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "lr_internal.h"
 #include "ptx.h"
 #include "scan_common.cuh"
@@ -48,10 +49,9 @@
 namespace lr {
 namespace {
 
-constexpr int kTcThreads = 352;
+constexpr int kTcThreads = 320;
 constexpr int kEpiWarp0 = 6;
-constexpr int kLoadWarp = 10;
-constexpr int kMetaDepth = 4;
+constexpr int kLoadWarp = 0;
 constexpr int kTileRows = 128;
 constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile of 128-byte rows
 
@@ -60,28 +60,22 @@ constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile o
 // e4m3 in 64-value (64-byte) blocks.
 __host__ __device__ constexpr int tc_epc(int e) { return e == kElemF32 ? 32 : 64; }
 __host__ __device__ constexpr int tc_row_bytes(int e) { return e == kElemFP8 ? 64 : 128; }
-constexpr int kTcGroupChunk = 2;              // groups per work-counter grab
 constexpr int kWarpCand = 512;                // candidates staged per epilogue warp (flushed past 256)
 constexpr int kABufs = 4;                     // x_hi/x_lo chunk buffers in tensor memory
 constexpr uint32_t kTmemCols = 512;           // the whole tensor memory: one CTA per SM
 
-// Messenger of one 128-row tile: for each row, the mask of the launch's queries
-// that pass it (bit q).
-struct TileMeta {
-  int64_t row0;
-  uint32_t done;
-  uint32_t pad;
-  uint64_t qm[kTileRows];
-};
+// Row mask word of the tile list: bit q = launch query q passes the row.
+template <int N>
+using RowMask = typename std::conditional<(N <= 32), uint32_t, uint64_t>::type;
 
 struct TcLayout {
   int S, C, C32, N;
-  size_t raw, q, meta, slots, taus, cand, ccnt, cq, bars, holder, total;
+  size_t raw, q, taus, cand, ccnt, cq, bars, holder, total;
 };
 
 __host__ __device__ inline size_t tc_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int n_slots, int S) {
+__host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S) {
   TcLayout T;
   T.S = S;
   T.C = d_pad / epc;   // raw chunks per tile
@@ -92,10 +86,6 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int n_s
   off += (size_t)S * kChunkBytes;
   T.q = off;  // per chunk: 2N rows (N rows of q_hi, then N rows of q_lo), 128 bytes each
   off += (size_t)T.C32 * 2 * N * 128;
-  T.meta = tc_align(off, 16);
-  off = T.meta + (size_t)kMetaDepth * sizeof(TileMeta);
-  T.slots = tc_align(off, 16);
-  off = T.slots + (size_t)2 * (n_slots > 0 ? n_slots : 1) * 32;
   T.taus = tc_align(off, 16);
   off = T.taus + (size_t)N * 12;  // 64-bit thresholds, then their score words as floats
   T.cand = tc_align(off, 16);     // per epilogue warp: keys, then query indices (bytes)
@@ -105,25 +95,10 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int n_s
   T.cq = off;  // per epilogue warp: per-query counts, then reserved bases, of one flush
   off = T.cq + (size_t)4 * 2 * N * 4;
   T.bars = tc_align(off, 16);
-  off = T.bars + (size_t)(2 * S + 2 * kABufs + 4 + 2 * kMetaDepth + 1) * 8;
+  off = T.bars + (size_t)(2 * S + 2 * kABufs + 4 + 1) * 8;
   T.holder = tc_align(off, 16);
   T.total = T.holder + 16;
   return T;
-}
-
-// 32x32 bit-matrix transpose across the warp: lane i holds row i on entry
-// (bit c = column c) and column i on exit (bit r = row r).  Five stages swap
-// the off-diagonal blocks of size 16, 8, 4, 2, 1.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int j = 16 >> st;
-    const uint32_t m = masks[st];
-    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-    x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
-  }
-  return x;
 }
 
 // Leader-lane wait broadcast to the warp.
@@ -140,26 +115,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned for the swizzle atoms
-  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, a.n_slots, S);
+  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S);
   const int C = T.C;
   const int C32 = T.C32;
   unsigned char *raw = smem + T.raw;
   float *qop = reinterpret_cast<float *>(smem + T.q);
-  TileMeta *meta = reinterpret_cast<TileMeta *>(smem + T.meta);
-  uint32_t *slot_tab = reinterpret_cast<uint32_t *>(smem + T.slots);
   uint64_t *taus = reinterpret_cast<uint64_t *>(smem + T.taus);
   float *thr = reinterpret_cast<float *>(taus + N);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + T.bars);
   uint64_t *raw_full = bars, *raw_empty = bars + S;
   uint64_t *a_full = bars + 2 * S, *a_empty = a_full + kABufs;
   uint64_t *acc_full = a_empty + kABufs, *acc_empty = acc_full + 2;
-  uint64_t *meta_full = acc_empty + 2, *meta_empty = meta_full + kMetaDepth;
-  uint64_t *drain = meta_empty + kMetaDepth;
+  uint64_t *drain = acc_empty + 2;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + T.holder);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const uint32_t acol0 = 4u * (uint32_t)N;  // first tensor-memory column of the x_hi/x_lo buffers
   __shared__ bool s_last;
+  __shared__ uint32_t s_nlist;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
@@ -174,12 +147,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 4);
     }
-    for (int i = 0; i < kMetaDepth; ++i) {
-      mbar_init(&meta_full[i], 1);
-      mbar_init(&meta_empty[i], 4);
-    }
     mbar_init(drain, 1);
     fence_mbar_init();
+    // tiles listed by the tile filter (never more than the list holds)
+    const uint32_t nl = *reinterpret_cast<const volatile uint32_t *>(a.tile_cnt);
+    s_nlist = (int64_t)nl < a.tile_cap ? nl : (uint32_t)a.tile_cap;
   }
   // queries of the launch in the K-major 128-byte swizzle layout, split into hi/lo
   for (int i = threadIdx.x; i < C32 * N * 32; i += blockDim.x) {
@@ -216,170 +188,53 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t dmask = (1u << (top - shift)) - 1u;
   bool ok = true;
 
-  if (warp == 0) {
-    // ------------------------------------------------------------- producer
-    const int q0 = lane, q1 = lane + 32;
-    const bool live0 = q0 < a.nq && (a.active == nullptr || a.active[a.q_base + q0] != 0u);
-    const bool live1 = q1 < a.nq && (a.active == nullptr || a.active[a.q_base + q1] != 0u);
-    const int64_t n_items = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
-    int64_t item = 0, item_end = 0;
-    // work counter read one chunk ahead: the atomic of the next chunk is in
-    // flight while the current one is processed
-    uint32_t pref = 0;
-    if (lane == 0) pref = atomicAdd(a.work_ctr, 1u);
-    auto next_group = [&]() -> int64_t {
-      if (item + 1 < item_end) return a.g_begin + (++item) * a.g_step;
-      const uint32_t c = __shfl_sync(0xFFFFFFFFu, pref, 0);
-      item = (int64_t)c * kTcGroupChunk;
-      item_end = item + kTcGroupChunk < n_items ? item + kTcGroupChunk : n_items;
-      if (item >= n_items) return -1;
-      if (lane == 0) pref = atomicAdd(a.work_ctr, 1u);
-      return a.g_begin + item * a.g_step;
-    };
-    auto prefetch = [&](int64_t g, int t) {
-      uint32_t *dst = slot_tab + (size_t)t * a.n_slots * 8;
-      for (int i = lane; i < 2 * a.n_slots; i += 32) {
-        const int s = i >> 1, h = i & 1;
-        cp_async16(dst + s * 8 + h * 4, a.slot_bm[s] + g * kGroupWords + h * 4);
-      }
-      cp_async_commit();
-    };
-    // each lane's queries' CNFs in registers (queries with more than 16 terms use the lists)
-    const PackedCnf pk0 = live0 ? pack_cnf(a, q0) : PackedCnf{};
-    const PackedCnf pk1 = live1 ? pack_cnf(a, q1) : PackedCnf{};
-    unsigned long long pass0 = 0, pass1 = 0;
-    uint64_t pm = 0;
-    int t = 0;
-    int64_t g = next_group();
-    if (g >= 0) prefetch(g, 0);
-    int64_t gn = g >= 0 ? next_group() : -1;
-    if (gn >= 0) prefetch(gn, 1);
-    else cp_async_commit();
-    while (g >= 0 && ok) {
-      cp_async_wait_group<1>();
-      __syncwarp();
-      uint32_t pw0[8], pw1[8];
-      const uint32_t *tab = slot_tab + (size_t)t * a.n_slots * 8;
-      if (live0 && pk0.ok) eval_packed(pk0, tab, pw0);
-      else if (live0) eval_cnf(a, q0, tab, pw0);
-      else
-#pragma unroll
-        for (int w = 0; w < 8; ++w) pw0[w] = 0u;
-      if (live1 && pk1.ok) eval_packed(pk1, tab, pw1);
-      else if (live1) eval_cnf(a, q1, tab, pw1);
-      else
-#pragma unroll
-        for (int w = 0; w < 8; ++w) pw1[w] = 0u;
-      __syncwarp();
-      const int64_t gnn = gn >= 0 ? next_group() : -1;
-      if (gnn >= 0) prefetch(gnn, t);
-      else cp_async_commit();
-      const int64_t r0 = g * kGroupRows;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) {
-        const int64_t left = a.n - (r0 + w * 32);
-        const uint32_t valid = left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u);
-        pw0[w] &= valid;
-        pw1[w] &= valid;
-        pass0 += (unsigned long long)__popc(pw0[w]);
-        pass1 += (unsigned long long)__popc(pw1[w]);
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uint32_t any = 0;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) any |= pw0[4 * h + w] | pw1[4 * h + w];
-        if (__reduce_or_sync(0xFFFFFFFFu, any) == 0u || !ok) continue;
-        const int m = (int)(pm % kMetaDepth);
-        if (!warp_wait(&meta_empty[m], (uint32_t)((pm / kMetaDepth) & 1u) ^ 1u, lane)) {
-          ok = false;
-          break;
-        }
-        const int64_t row0 = r0 + h * kTileRows;
-        if (lane == 0) {
-          meta[m].row0 = row0;
-          meta[m].done = 0u;
-        }
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {  // lane r: queries passing row 32w + r of the tile
-          const uint32_t lo32 = transpose32(pw0[4 * h + w], lane);
-          const uint32_t hi32 = N > 32 ? transpose32(pw1[4 * h + w], lane) : 0u;
-          meta[m].qm[w * 32 + lane] = ((uint64_t)hi32 << 32) | lo32;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&meta_full[m]);
-        ++pm;
-      }
-      g = gn;
-      gn = gnn;
-      t ^= 1;
-    }
-    cp_async_wait_all();
-    if (ok) {  // end-of-work marker for the other roles
-      const int m = (int)(pm % kMetaDepth);
-      if (warp_wait(&meta_empty[m], (uint32_t)((pm / kMetaDepth) & 1u) ^ 1u, lane)) {
-        if (lane == 0) {
-          meta[m].done = 1u;
-          mbar_arrive(&meta_full[m]);
-        }
-        ++pm;
-      } else {
-        ok = false;
-      }
-    }
-    if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
-    if (a.pass_cnt != nullptr) {
-      if (live0) atomicAdd(&a.pass_cnt[a.q_base + q0], pass0);
-      if (live1) atomicAdd(&a.pass_cnt[a.q_base + q1], pass1);
-    }
-  } else if (warp == kLoadWarp) {
+  // this CTA's tiles: list entries blockIdx.x + k * gridDim.x, k < n_mine
+  const int64_t n_list = (int64_t)s_nlist;
+  const int64_t n_mine = n_list > (int64_t)blockIdx.x ? (n_list - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto entry = [&](int64_t k) -> int64_t { return (int64_t)blockIdx.x + k * (int64_t)gridDim.x; };
+
+  if (warp == kLoadWarp) {
     // ------------------------------------------------------------- loader
-    // issues the TMA loads of every published tile, in message order, into the
-    // ring of raw stages; decoupled from the predicate warp so that neither
-    // waits for the other's latencies
-    if (lane == 0) {
-      uint64_t pm = 0, pr = 0;
-      while (ok) {
-        const int m = (int)(pm % kMetaDepth);
-        if (!mbar_wait(&meta_full[m], (uint32_t)((pm / kMetaDepth) & 1u))) {
+    // the warp reads the first rows of 32 tiles at a time (the next 32 in
+    // flight meanwhile); lane 0 issues the TMA loads into the raw ring
+    auto rows_from = [&](int64_t k0) -> int32_t {
+      const int64_t k = k0 + lane;
+      return k < n_mine ? a.tile_row[entry(k)] : 0;
+    };
+    int32_t rcur = rows_from(0), rnext = rows_from(32);
+    uint64_t pr = 0;
+    for (int64_t k = 0; k < n_mine && ok; ++k) {
+      if (k > 0 && (k & 31) == 0) {
+        rcur = rnext;
+        rnext = rows_from(k + 32);
+      }
+      const int row0 = __shfl_sync(0xFFFFFFFFu, rcur, (int)(k & 31));
+      for (int c = 0; c < C; ++c) {
+        const int s = (int)(pr % (uint64_t)S);
+        if (!warp_wait(&raw_empty[s], (uint32_t)((pr / S) & 1u) ^ 1u, lane)) {
           ok = false;
           break;
         }
-        if (meta[m].done) break;
-        const int row0 = (int)meta[m].row0;
-        for (int c = 0; c < C; ++c) {
-          const int s = (int)(pr % (uint64_t)S);
-          if (!mbar_wait(&raw_empty[s], (uint32_t)((pr / S) & 1u) ^ 1u)) {
-            ok = false;
-            break;
-          }
+        if (lane == 0) {
           mbar_arrive_expect_tx(&raw_full[s], (uint32_t)(kTileRows * tc_row_bytes(E)));
           tma_load_2d(raw + (size_t)s * kChunkBytes, &tmap, c * tc_epc(E), row0, &raw_full[s]);
-          ++pr;
         }
-        if (!ok) break;
-        ++pm;
+        ++pr;
       }
-      if (!ok) {
-        atomicOr(a.err, kErrTimeout);
-        const uint64_t first = pr > (uint64_t)S ? pr - S : 0;  // let issued loads land
-        for (uint64_t p = first; p < pr; ++p) mbar_wait(&raw_full[p % S], (uint32_t)((p / S) & 1u));
-      }
+    }
+    if (!ok && lane == 0) {
+      atomicOr(a.err, kErrTimeout);
+      const uint64_t first = pr > (uint64_t)S ? pr - S : 0;  // let issued loads land
+      for (uint64_t p = first; p < pr; ++p) mbar_wait(&raw_full[p % S], (uint32_t)((p / S) & 1u));
     }
     __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t idesc2 = idesc_tf32(kTileRows, 2 * N), idesc1 = idesc_tf32(kTileRows, N);
-      uint64_t pm = 0, pr = 0, pa = 0;
+      uint64_t pr = 0, pa = 0;
       bool issued = false;
-      while (ok) {
-        const int m = (int)(pm % kMetaDepth);
-        if (!mbar_wait(&meta_full[m], (uint32_t)((pm / kMetaDepth) & 1u))) {
-          ok = false;
-          break;
-        }
-        if (meta[m].done) break;
+      for (int64_t k = 0; k < n_mine && ok; ++k) {
         const int ab = (int)(pa & 1u);
         if (!mbar_wait(&acc_empty[ab], (uint32_t)((pa >> 1) & 1u) ^ 1u)) {
           ok = false;
@@ -424,7 +279,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!ok) break;
         mma_commit(&acc_full[ab]);
         ++pa;
-        ++pm;
       }
       if (issued) {  // every MMA has finished before the tensor memory is freed
         mma_commit(drain);
@@ -437,14 +291,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ------------------------------------------------------------- converters
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;  // this thread's row of every tile
-    uint64_t pm = 0, pr = 0;
-    while (ok) {
-      const int m = (int)(pm % kMetaDepth);
-      if (!warp_wait(&meta_full[m], (uint32_t)((pm / kMetaDepth) & 1u), lane)) {
-        ok = false;
-        break;
-      }
-      if (meta[m].done) break;
+    uint64_t pr = 0;
+    for (int64_t k = 0; k < n_mine && ok; ++k) {
       for (int c = 0; c < C; ++c) {
         const int s = (int)(pr % (uint64_t)S), l = (int)(pr % (uint64_t)kABufs);
         if (!warp_wait(&raw_full[s], (uint32_t)((pr / S) & 1u), lane)) {
@@ -512,15 +360,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (lane == 0) mbar_arrive(&a_full[l]);
         ++pr;
       }
-      if (!ok) break;
-      ++pm;
     }
     if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
   } else {
     // ------------------------------------------------------------- epilogue
     const int quarter = warp & 3;
     const int ew = warp - kEpiWarp0;
-    uint64_t pm = 0, pa = 0;
+    uint64_t pa = 0;
     // Candidates are recorded in a per-warp shared-memory list by the lanes that
     // find them (a shared-memory atomic each).  A flush tests them exactly,
     // counts them per query, reserves each query's range of its buffer with one
@@ -571,13 +417,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) *ccnt = 0u;
       __syncwarp();
     };
-    while (ok) {
-      const int m = (int)(pm % kMetaDepth);
-      if (!warp_wait(&meta_full[m], (uint32_t)((pm / kMetaDepth) & 1u), lane)) {
-        ok = false;
-        break;
+    // this lane's row mask (and FP8 row scale) read one tile ahead, the tiles'
+    // first rows two ahead, so no global load latency sits on the tile's path
+    const int lr = quarter * 32 + lane;
+    const RowMask<N> *msg = static_cast<const RowMask<N> *>(a.tile_msg) + lr;
+    auto row_of = [&](int64_t k) -> int32_t { return k < n_mine ? a.tile_row[entry(k)] : 0; };
+    auto scale_of = [&](int32_t row0, int64_t k) -> float {  // FP8 rows: score = scale * <q, x8>
+      if constexpr (E == kElemFP8) {
+        const int64_t g = (int64_t)row0 + lr;
+        return k < n_mine && g < a.n ? __ldg(a.xscale + g) : 0.f;
+      } else {
+        return 1.f;
       }
-      if (meta[m].done) break;
+    };
+    RowMask<N> qm_next = n_mine > 0 ? msg[(size_t)entry(0) * kTileRows] : (RowMask<N>)0;
+    int32_t row_next = row_of(0), row_after = row_of(1);
+    float xs_next = scale_of(row_next, 0);
+    for (int64_t k = 0; k < n_mine && ok; ++k) {
+      const uint64_t qmask = (uint64_t)qm_next;
+      const uint32_t grow = (uint32_t)(row_next + lr);
+      const float xs = xs_next;
+      if (k + 1 < n_mine) qm_next = msg[(size_t)entry(k + 1) * kTileRows];
+      xs_next = scale_of(row_after, k + 1);
+      row_next = row_after;
+      row_after = row_of(k + 2);
       const int ab = (int)(pa & 1u);
       if (!warp_wait(&acc_full[ab], (uint32_t)((pa >> 1) & 1u), lane)) {
         ok = false;
@@ -585,10 +448,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 2 * N);
-      const uint64_t qmask = meta[m].qm[quarter * 32 + lane];
-      const uint32_t grow = (uint32_t)(meta[m].row0 + quarter * 32 + lane);
-      float xs = 1.f;  // FP8 rows: score = scale * <q, x8>
-      if constexpr (E == kElemFP8) xs = (int64_t)grow < a.n ? __ldg(a.xscale + grow) : 0.f;
 #pragma unroll 1
       for (int j = 0; j < N / 16; ++j) {
         const uint32_t bm = (uint32_t)(qmask >> (16 * j)) & 0xFFFFu;
@@ -651,12 +510,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&acc_empty[ab]);
-        mbar_arrive(&meta_empty[m]);
-      }
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
       ++pa;
-      ++pm;
     }
     flush();
     if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
@@ -679,7 +534,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (a.mode == kHist) hist_step(a, top, shift);
     __syncthreads();
     if (threadIdx.x == 0) {
-      *a.work_ctr = 0u;
+      *a.tile_cnt = 0u;  // the next tile filter starts an empty list
       *a.done_ctr = 0u;
     }
   }
@@ -691,8 +546,8 @@ cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cuda
   const size_t budget = 220u * 1024u;
   int S = 12;
   if (a.d_pad % tc_epc(E) != 0) return cudaErrorInvalidValue;
-  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, a.n_slots, S).total + 1024 > budget) --S;
-  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, a.n_slots, S);
+  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, S).total + 1024 > budget) --S;
+  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S);
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
   auto *fn = k_scan_tc<N, E>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(T.total + 1024));
