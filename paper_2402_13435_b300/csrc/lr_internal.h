@@ -108,8 +108,9 @@ struct ScanArgs {
   uint32_t *err;                 // device error word
   // tile list of the tensor-core plan: written by the tile filter, read by the
   // scan, whose last CTA resets the count
-  int32_t *tile_row;             // [tile_cap] first row of each listed 128-row tile
-  void *tile_msg;                // [tile_cap][128] row masks: bit q = query q passes (32-bit if nq <= 32, else 64-bit)
+  int32_t *tile_row;             // [tile_cap] ids t of the listed 128-row tiles (rows 128 t ..)
+  void *tile_msg;                // [tile_cap][128] row masks by tile id: bit q = query q passes the row
+                                 // (32-bit words if nq <= 32, else 64-bit)
   uint32_t *tile_cnt;            // tiles listed
   int64_t tile_cap;
 };

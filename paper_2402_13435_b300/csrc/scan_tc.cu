@@ -49,8 +49,9 @@
 namespace lr {
 namespace {
 
-constexpr int kTcThreads = 320;
-constexpr int kEpiWarp0 = 6;
+constexpr int kTcThreads = 448;
+constexpr int kEpiWarp0 = 6;    // epilogue warps 6-9
+constexpr int kConvWarp1 = 10;  // second converter set: warps 10-13 (the first is warps 2-5)
 constexpr int kLoadWarp = 0;
 constexpr int kTileRows = 128;
 constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile of 128-byte rows
@@ -192,23 +193,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int64_t n_list = (int64_t)s_nlist;
   const int64_t n_mine = n_list > (int64_t)blockIdx.x ? (n_list - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   auto entry = [&](int64_t k) -> int64_t { return (int64_t)blockIdx.x + k * (int64_t)gridDim.x; };
+  // id of the CTA's k-th tile; an id outside the index (which the tile filter
+  // never writes) is reported and read as -1: its rows are loaded from tile 0
+  // and no query tests them
+  auto tile_id = [&](int64_t k) -> int32_t {
+    const int32_t t = a.tile_row[entry(k)];
+    if ((int64_t)(uint32_t)t * kTileRows < a.n) return t;
+    atomicOr(a.err, kErrTileList);
+    return -1;
+  };
 
   if (warp == kLoadWarp) {
     // ------------------------------------------------------------- loader
-    // the warp reads the first rows of 32 tiles at a time (the next 32 in
-    // flight meanwhile); lane 0 issues the TMA loads into the raw ring
-    auto rows_from = [&](int64_t k0) -> int32_t {
+    // the warp reads the ids of 32 tiles at a time (the next 32 in flight
+    // meanwhile); lane 0 issues the TMA loads into the raw ring
+    auto ids_from = [&](int64_t k0) -> int32_t {
       const int64_t k = k0 + lane;
-      return k < n_mine ? a.tile_row[entry(k)] : 0;
+      return k < n_mine ? tile_id(k) : 0;
     };
-    int32_t rcur = rows_from(0), rnext = rows_from(32);
+    int32_t rcur = ids_from(0), rnext = ids_from(32);
     uint64_t pr = 0;
     for (int64_t k = 0; k < n_mine && ok; ++k) {
       if (k > 0 && (k & 31) == 0) {
         rcur = rnext;
-        rnext = rows_from(k + 32);
+        rnext = ids_from(k + 32);
       }
-      const int row0 = __shfl_sync(0xFFFFFFFFu, rcur, (int)(k & 31));
+      const int row0 = max(__shfl_sync(0xFFFFFFFFu, rcur, (int)(k & 31)), 0) * kTileRows;
       for (int c = 0; c < C; ++c) {
         const int s = (int)(pr % (uint64_t)S);
         if (!warp_wait(&raw_empty[s], (uint32_t)((pr / S) & 1u) ^ 1u, lane)) {
@@ -287,13 +297,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!ok) atomicOr(a.err, kErrTimeout);
     }
     __syncwarp();
-  } else if (warp < kEpiWarp0) {
+  } else if (warp < kEpiWarp0 || warp >= kConvWarp1) {
     // ------------------------------------------------------------- converters
+    // two sets of four warps take alternate chunks (set = chunk index & 1), so
+    // two chunks per lane quarter are in flight; S and kABufs are even, so a
+    // raw stage or an x_hi/x_lo buffer always belongs to the same set and its
+    // barrier phases are met in order
     const int quarter = warp & 3;
+    const uint64_t cset = warp >= kConvWarp1 ? 1u : 0u;
     const int r = quarter * 32 + lane;  // this thread's row of every tile
     uint64_t pr = 0;
     for (int64_t k = 0; k < n_mine && ok; ++k) {
-      for (int c = 0; c < C; ++c) {
+      for (int c = 0; c < C; ++c, ++pr) {
+        if ((pr & 1u) != cset) continue;
         const int s = (int)(pr % (uint64_t)S), l = (int)(pr % (uint64_t)kABufs);
         if (!warp_wait(&raw_full[s], (uint32_t)((pr / S) & 1u), lane)) {
           ok = false;
@@ -358,7 +374,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&a_full[l]);
-        ++pr;
       }
     }
     if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
@@ -417,30 +432,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) *ccnt = 0u;
       __syncwarp();
     };
-    // this lane's row mask (and FP8 row scale) read one tile ahead, the tiles'
-    // first rows two ahead, so no global load latency sits on the tile's path
+    // this lane's row mask (and FP8 row scale) read one tile ahead, the tile
+    // ids two ahead, so no global load latency sits on the tile's path
     const int lr = quarter * 32 + lane;
     const RowMask<N> *msg = static_cast<const RowMask<N> *>(a.tile_msg) + lr;
-    auto row_of = [&](int64_t k) -> int32_t { return k < n_mine ? a.tile_row[entry(k)] : 0; };
-    auto scale_of = [&](int32_t row0, int64_t k) -> float {  // FP8 rows: score = scale * <q, x8>
+    auto tile_of = [&](int64_t k) -> int32_t { return k < n_mine ? tile_id(k) : -1; };
+    auto mask_of = [&](int32_t t, int64_t k) -> RowMask<N> {
+      return k < n_mine && t >= 0 ? msg[(size_t)t * kTileRows] : (RowMask<N>)0;
+    };
+    auto scale_of = [&](int32_t t, int64_t k) -> float {  // FP8 rows: score = scale * <q, x8>
       if constexpr (E == kElemFP8) {
-        const int64_t g = (int64_t)row0 + lr;
-        return k < n_mine && g < a.n ? __ldg(a.xscale + g) : 0.f;
+        const int64_t g = (int64_t)t * kTileRows + lr;
+        return k < n_mine && t >= 0 && g < a.n ? __ldg(a.xscale + g) : 0.f;
       } else {
         return 1.f;
       }
     };
-    RowMask<N> qm_next = n_mine > 0 ? msg[(size_t)entry(0) * kTileRows] : (RowMask<N>)0;
-    int32_t row_next = row_of(0), row_after = row_of(1);
-    float xs_next = scale_of(row_next, 0);
+    int32_t t_next = tile_of(0), t_after = tile_of(1);
+    RowMask<N> qm_next = mask_of(t_next, 0);
+    float xs_next = scale_of(t_next, 0);
     for (int64_t k = 0; k < n_mine && ok; ++k) {
       const uint64_t qmask = (uint64_t)qm_next;
-      const uint32_t grow = (uint32_t)(row_next + lr);
+      const uint32_t grow = (uint32_t)(max(t_next, 0) * kTileRows + lr);
       const float xs = xs_next;
-      if (k + 1 < n_mine) qm_next = msg[(size_t)entry(k + 1) * kTileRows];
-      xs_next = scale_of(row_after, k + 1);
-      row_next = row_after;
-      row_after = row_of(k + 2);
+      qm_next = mask_of(t_after, k + 1);
+      xs_next = scale_of(t_after, k + 1);
+      t_next = t_after;
+      t_after = tile_of(k + 2);
       const int ab = (int)(pa & 1u);
       if (!warp_wait(&acc_full[ab], (uint32_t)((pa >> 1) & 1u), lane)) {
         ok = false;
@@ -543,10 +561,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 template <int N, int E>
 cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cudaStream_t s) {
   static_assert(4 * N + 64 * kABufs <= (int)kTmemCols, "tensor memory budget");
+  static_assert(kABufs % 2 == 0, "each converter set owns every other x_hi/x_lo buffer");
   const size_t budget = 220u * 1024u;
-  int S = 12;
+  int S = 12;  // raw stages: even (each converter set owns every other stage)
   if (a.d_pad % tc_epc(E) != 0) return cudaErrorInvalidValue;
-  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, S).total + 1024 > budget) --S;
+  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, S).total + 1024 > budget) S -= 2;
   const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S);
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
   auto *fn = k_scan_tc<N, E>;

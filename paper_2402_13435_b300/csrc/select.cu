@@ -86,7 +86,13 @@ constexpr int kPilot = 4096;  // keys of the strided pilot sample (kPilot <= kSm
 // passes run over global memory, so the result is exact either way.
 __device__ uint64_t kth_large(const uint64_t *g, int64_t n, uint32_t r, uint64_t *sbuf, SelShared &sh) {
   const int tid = threadIdx.x;
-  for (int i = tid; i < kPilot; i += blockDim.x) sbuf[i] = __ldcg(g + (int64_t)i * n / kPilot);
+  constexpr int kPu = kPilot / kSelThreads;  // pilot loads per thread, all in flight together
+  static_assert(kPilot % kSelThreads == 0, "pilot split");
+  uint64_t pv[kPu];
+#pragma unroll
+  for (int u = 0; u < kPu; ++u) pv[u] = __ldcg(g + (int64_t)(tid + u * kSelThreads) * n / kPilot);
+#pragma unroll
+  for (int u = 0; u < kPu; ++u) sbuf[tid + u * kSelThreads] = pv[u];
   __syncthreads();
   const double e = (double)r * (double)kPilot / (double)n;
   double want = ceil(e + 3.0 * sqrt(e) + 8.0);
@@ -94,7 +100,7 @@ __device__ uint64_t kth_large(const uint64_t *g, int64_t n, uint32_t r, uint64_t
   const uint64_t t0 = block_kth(sbuf, kPilot, rp, sh);
   if (tid == 0) sh.n_out = 0u;
   __syncthreads();
-  constexpr int kU = 4;  // loads in flight per thread
+  constexpr int kU = 16;  // loads in flight per thread (64 KB per CTA)
   for (int64_t b = tid; b < n; b += (int64_t)kU * blockDim.x) {
     uint64_t v[kU];
 #pragma unroll

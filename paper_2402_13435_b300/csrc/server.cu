@@ -53,6 +53,7 @@ struct Request {
   // result
   bool done = false;
   lr_status status = LR_OK;
+  std::string message;  // the failure's message, recorded on the scheduler thread
   std::vector<int32_t> ids, count;  // [B][k_max], [B]
   std::vector<float> scores;
   double latency_ms = 0.0;
@@ -72,6 +73,7 @@ struct Slot {
   int B = 0, k_all = 0;
   bool busy = false;
   lr_status launch_status = LR_OK;
+  std::string launch_message;
 };
 
 }  // namespace
@@ -159,6 +161,7 @@ void launch(lr_server *S, Slot &sl) {
   }
   if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = fail(LR_ERR_CUDA, "serving: event record failed");
   sl.launch_status = st;
+  sl.launch_message = st == LR_OK ? std::string() : std::string(lr_last_error_message());
 }
 
 // Hand each request of a finished slot its rows (called with the lock held).
@@ -167,6 +170,7 @@ void retire(lr_server *S, Slot &sl) {
   int row = 0;
   for (Request *r : sl.reqs) {
     r->status = sl.launch_status;
+    r->message = sl.launch_message;
     r->ids.assign((size_t)r->B * r->k_max, -1);
     r->scores.assign((size_t)r->B * r->k_max, -INFINITY);
     r->count.assign(r->B, 0);
@@ -369,9 +373,10 @@ lr_status lr_server_wait(lr_server *S, uint64_t ticket, int32_t timeout_ms, int3
   }
   if (latency_ms) *latency_ms = r->latency_ms;
   const lr_status st = r->status;
+  const std::string msg = r->message;
   S->live.erase(it);
   delete r;
-  return st;
+  return st == LR_OK ? LR_OK : fail(st, "request failed: " + msg);
 }
 
 lr_status lr_server_get_stats(lr_server *S, lr_server_stats *st, int32_t reset) {

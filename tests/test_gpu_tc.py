@@ -94,3 +94,21 @@ def test_tc_alone_and_in_a_batch_give_identical_rows(lr):
     for b in (0, 17, 31):
         alone = _run(lr, idx, Q[b:b + 1].copy(), f.subset([b]), K, plan="tc")
         assert np.array_equal(alone[0][0], batch[0][b]) and np.array_equal(alone[1][0], batch[1][b])
+
+
+@pytest.mark.parametrize("S", [1, 95, 96, 97, 256])
+def test_tc_distinct_term_counts(lr, S):
+    """Batches whose distinct terms put the tile filter's word tables on either side of the 48 KB
+    default shared-memory limit (94 to 96 terms was the gap), up to the 256-term maximum."""
+    n, d, V, B, K = 30_000, 64, 512, 32, 40
+    c = datagen.corpus(12, n, d, V, 10.0, 1.1)
+    qs = [[] for _ in range(B)]
+    for t in range(S):
+        qs[t % B].append(t)
+    f = Filters.from_lists([[q] if q else [] for q in qs])
+    assert len(set(int(t) for t in f.terms)) == S
+    Q = datagen.query_embeddings(12, B, d)
+    idx = lr.lr_index_create(c.X, V, bitsets=c.bitsets(), metric="cosine", max_batch=B, max_k=64)
+    ids, sc, cnt = _run(lr, idx, Q, f, K, plan="tc")
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
