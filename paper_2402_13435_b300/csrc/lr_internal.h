@@ -113,6 +113,7 @@ struct ScanArgs {
                                  // (32-bit words if nq <= 32, else 64-bit)
   uint32_t *tile_cnt;            // tiles listed
   int64_t tile_cap;
+  int32_t keep_list;             // 1: the scan leaves the list for later launches (else its last CTA empties it)
 };
 
 struct SelectArgs {
@@ -146,7 +147,7 @@ struct SelectArgs {
 cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s);
 // Tile filter (term predicate of the tensor-core plan) and the scan that reads
 // its list; launch them back to back on one stream.
-cudaError_t launch_tile_filter(const ScanArgs &a, int max_grid, cudaStream_t s);
+cudaError_t launch_tile_filter(const ScanArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
 

@@ -887,12 +887,19 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     const int64_t want = plan == LR_PLAN_TC ? groups : (groups + 3) / 4;
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ix->num_sms));
   };
-  auto launch_scan = [&](const ScanArgs &a, int64_t groups) {
+  // Tensor-core plan: the tile filter (term predicate) writes the list of
+  // tiles the scan reads.  With one sub-batch the main pass keeps its list and
+  // the exact fallback's scans reuse it (masked to the flagged queries) instead
+  // of filtering again.
+  const bool reuse_list = plan == LR_PLAN_TC && C.subs.size() == 1;
+  auto launch_scan = [&](ScanArgs a, int64_t groups, bool filter = true, bool keep = false) {
     if (plan != LR_PLAN_TC) return launch_scan_gemv(a, nq_tmpl(a.nq), vec, grid_for(groups), s);
-    // the term predicate first (its tile list feeds the scan), then the scan
-    ++n_launch;
-    const cudaError_t e = launch_tile_filter(a, 2 * ix->num_sms, s);
-    if (e != cudaSuccess) return e;
+    a.keep_list = keep ? 1 : 0;
+    if (filter) {
+      ++n_launch;
+      const cudaError_t e = launch_tile_filter(a, ix->num_sms, s);
+      if (e != cudaSuccess) return e;
+    }
     return launch_scan_tc(a, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(2 * groups), s);
   };
 
@@ -929,7 +936,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.buf_cnt = ix->cnt;
     a.overflow = ix->ovf;
     a.pass_cnt = ix->pass;
-    LR_LAUNCH(launch_scan(a, ix->n_groups));
+    LR_LAUNCH(launch_scan(a, ix->n_groups, true, reuse_list));
     ++n_scan;
   }
   if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
@@ -971,7 +978,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       a.hist = ix->hist;
       a.active = ix->flag;
       a.any_active = ix->n_flag;
-      LR_LAUNCH(launch_scan(a, ix->n_groups));
+      LR_LAUNCH(launch_scan(a, ix->n_groups, !reuse_list, reuse_list));
     }
   }
   LR_LAUNCH(launch_fallback_finish(ix->prefix, ix->flag, ix->tau, B, ix->n_flag, s));
@@ -984,7 +991,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.overflow = ix->ovf;
     a.active = ix->flag;
     a.any_active = ix->n_flag;
-    LR_LAUNCH(launch_scan(a, ix->n_groups));
+    LR_LAUNCH(launch_scan(a, ix->n_groups, !reuse_list, reuse_list));
   }
   SelectArgs fb = fa;
   fb.cap = ix->cand_cap;

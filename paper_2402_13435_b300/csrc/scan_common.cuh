@@ -46,17 +46,19 @@ struct PackedCnf {
   bool ok;         // false: the query does not fit (more than 16 terms)
 };
 
-__device__ __forceinline__ PackedCnf pack_cnf(const ScanArgs &a, int q) {
+// From clause lists qc (clause ranges per query), cl (slot ranges per clause)
+// and cs (slot ids), in shared or global memory.
+__device__ __forceinline__ PackedCnf pack_cnf_lists(const int32_t *qc, const int32_t *cl, const int32_t *cs, int q) {
   PackedCnf p;
   p.slot[0] = p.slot[1] = p.slot[2] = p.slot[3] = 0u;
   p.start = 0u;
   p.nt = 0;
   p.ok = true;
-  const int c0 = a.qc_off[q], c1 = a.qc_off[q + 1];
+  const int c0 = qc[q], c1 = qc[q + 1];
   for (int c = c0; c < c1; ++c) {
-    const int t0 = a.cl_off[c], t1 = a.cl_off[c + 1];
+    const int t0 = cl[c], t1 = cl[c + 1];
     for (int t = t0; t < t1; ++t) {
-      const int s = a.cl_slot[t];
+      const int s = cs[t];
       if (p.nt >= 16 || s > 255) {
         p.ok = false;
         return p;
@@ -67,6 +69,10 @@ __device__ __forceinline__ PackedCnf pack_cnf(const ScanArgs &a, int q) {
     }
   }
   return p;
+}
+
+__device__ __forceinline__ PackedCnf pack_cnf(const ScanArgs &a, int q) {
+  return pack_cnf_lists(a.qc_off, a.cl_off, a.cl_slot, q);
 }
 
 __device__ __forceinline__ void eval_packed(const PackedCnf &p, const uint32_t *sw, uint32_t (&pw)[8]) {

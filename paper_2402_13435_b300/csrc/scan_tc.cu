@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t acol0 = 4u * (uint32_t)N;  // first tensor-memory column of the x_hi/x_lo buffers
   __shared__ bool s_last;
   __shared__ uint32_t s_nlist;
+  __shared__ uint32_t s_live[2];  // bit q: query q takes part in this launch
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
@@ -154,25 +155,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t nl = *reinterpret_cast<const volatile uint32_t *>(a.tile_cnt);
     s_nlist = (int64_t)nl < a.tile_cap ? nl : (uint32_t)a.tile_cap;
   }
-  // queries of the launch in the K-major 128-byte swizzle layout, split into hi/lo
-  for (int i = threadIdx.x; i < C32 * N * 32; i += blockDim.x) {
-    const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
-    const float v = r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 32 + k] : 0.f;
-    const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-    const int rl = r + N;  // row of q_lo in the combined operand
-    const size_t base = (size_t)c * 2 * N * 128;
-    qop[(base + (size_t)r * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4) / 4] = h;
-    qop[(base + (size_t)rl * 128 + ((((k >> 2) ^ (rl & 7)) & 7) << 4) + (k & 3) * 4) / 4] = v - h;
+  // queries of the launch in the K-major 128-byte swizzle layout, split into
+  // hi/lo; each thread issues its loads of a round together, then stores
+  constexpr int kQu = 8;
+  for (int i0 = 0; i0 < C32 * N * 32; i0 += kQu * kTcThreads) {
+    float v[kQu];
+#pragma unroll
+    for (int u = 0; u < kQu; ++u) {
+      const int i = i0 + u * kTcThreads + threadIdx.x;
+      const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
+      v[u] = i < C32 * N * 32 && r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 32 + k] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kQu; ++u) {
+      const int i = i0 + u * kTcThreads + threadIdx.x;
+      if (i >= C32 * N * 32) break;
+      const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
+      const float h = __uint_as_float(__float_as_uint(v[u]) & 0xFFFFE000u);
+      const int rl = r + N;  // row of q_lo in the combined operand
+      const size_t base = (size_t)c * 2 * N * 128;
+      qop[(base + (size_t)r * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4) / 4] = h;
+      qop[(base + (size_t)rl * 128 + ((((k >> 2) ^ (rl & 7)) & 7) << 4) + (k & 3) * 4) / 4] = v[u] - h;
+    }
   }
-  for (int q = threadIdx.x; q < N; q += blockDim.x) {
-    const int g2 = a.q_base + q;
-    const bool live = q < a.nq && (a.active == nullptr || a.active[g2] != 0u);
-    taus[q] = !live ? 0ull : (a.mode == kCollect ? (a.tau ? a.tau[g2] : 0ull) : a.prefix[g2]);
-    // score_key(s) >= h  <=>  s >= thr[q] for every non-NaN score s
-    const uint32_t h = (uint32_t)(taus[q] >> 32);
-    thr[q] = h <= score_key(-INFINITY) ? -INFINITY
-             : h > score_key(INFINITY) ? __uint_as_float(0x7FFFFFFFu)  // NaN: no score passes
-                                       : key_score(h);
+  {  // thread q < N: query q's threshold; warps 0-1 record which queries take part
+    const int q = threadIdx.x;
+    bool live = false;
+    if (q < N) {
+      const int g2 = a.q_base + q;
+      live = q < a.nq && (a.active == nullptr || a.active[g2] != 0u);
+      taus[q] = !live ? 0ull : (a.mode == kCollect ? (a.tau ? a.tau[g2] : 0ull) : a.prefix[g2]);
+      // score_key(s) >= h  <=>  s >= thr[q] for every non-NaN score s
+      const uint32_t h = (uint32_t)(taus[q] >> 32);
+      thr[q] = h <= score_key(-INFINITY) ? -INFINITY
+               : h > score_key(INFINITY) ? __uint_as_float(0x7FFFFFFFu)  // NaN: no score passes
+                                         : key_score(h);
+    }
+    if (warp < 2) {
+      const uint32_t b = __ballot_sync(0xFFFFFFFFu, live);
+      if (lane == 0) s_live[warp] = b;
+    }
   }
   fence_proxy_async();
   if (warp == 1) {
@@ -448,11 +470,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         return 1.f;
       }
     };
+    // the list may be one written for a larger set of queries (the exact
+    // fallback reuses the main pass's list): only this launch's queries count
+    const uint64_t live_mask = ((uint64_t)s_live[1] << 32) | s_live[0];
     int32_t t_next = tile_of(0), t_after = tile_of(1);
     RowMask<N> qm_next = mask_of(t_next, 0);
     float xs_next = scale_of(t_next, 0);
     for (int64_t k = 0; k < n_mine && ok; ++k) {
-      const uint64_t qmask = (uint64_t)qm_next;
+      const uint64_t qmask = (uint64_t)qm_next & live_mask;
       const uint32_t grow = (uint32_t)(max(t_next, 0) * kTileRows + lr);
       const float xs = xs_next;
       qm_next = mask_of(t_after, k + 1);
@@ -552,7 +577,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (a.mode == kHist) hist_step(a, top, shift);
     __syncthreads();
     if (threadIdx.x == 0) {
-      *a.tile_cnt = 0u;  // the next tile filter starts an empty list
+      if (!a.keep_list) *a.tile_cnt = 0u;  // the next tile filter starts an empty list
       *a.done_ctr = 0u;
     }
   }
