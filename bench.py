@@ -239,21 +239,26 @@ def scan_plan(args):
 
 
 def measured_traffic(args):
-    """DRAM bytes per main-scan launch from the committed ncu record, or None when the record does
-    not cover this kernel source or this workload (10M x 128, batch 32, tensor-core plan)."""
+    """DRAM bytes per main pass (tile filter + scan) from the committed ncu record, or None when the
+    record does not cover the current kernel sources or this workload (10M x 128, batch 32, tensor-core
+    plan, FP32 rows)."""
     import hashlib
 
     kernel, _, _ = scan_plan(args)
+    if kernel != "k_scan_tc":
+        return None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            rec = json.load(fh)[kernel]
-        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
-            digest = hashlib.sha256(fh.read()).hexdigest()
+            rec = json.load(fh)["main_pass"]
+        for path, want in rec["sources"].items():
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != want:
+                    return None
     except (OSError, KeyError, ValueError):
         return None
-    if digest != rec["source_sha256"] or (args.n, args.dim, args.batch, args.dtype) != (10_000_000, 128, 32, "f32"):
+    if (args.n, args.dim, args.batch, args.dtype) != (10_000_000, 128, 32, "f32"):
         return None
-    return float(rec["traffic_per_launch_10M"])
+    return float(rec["traffic_per_pass_10M"])
 
 
 def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
@@ -426,7 +431,9 @@ def run_ours(args):
     achieved = (sum(per_launch) / 1e9) / (scan_ms / 1e3)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic(args),
-            "kernel": "%s (main scan, %d launches per step)" % (scan_plan(args)[0], n_scan),
+            "kernel": ("k_tile_filter + k_scan_tc (main pass: term filter, then scan; %d per step)" % n_scan
+                       if scan_plan(args)[0] == "k_scan_tc" else
+                       "%s (main scan, %d launches per step)" % (scan_plan(args)[0], n_scan)),
             "algorithmic_bytes_per_launch": float(np.mean(per_launch)), "launch_ms": scan_ms / max(n_scan, 1),
             "peak_kind": peak_kind}
 
