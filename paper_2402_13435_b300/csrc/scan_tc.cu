@@ -15,24 +15,27 @@
 // tiles that some query passes, each with its per-row query masks; tiles nobody
 // passes are never read ("skip rows").  CTA b of the scan takes list entries
 // b, b + grid, b + 2 grid, ..., so every role knows the tile sequence without
-// waiting for another.  One CTA per SM, ten warps with fixed roles:
+// waiting for another.  One CTA per SM, 14 warps with fixed roles (18 for
+// BF16/FP8 rows):
 //   warp 0     loader: issues the 2-D TMA loads (128 rows x 32 floats, 128-byte
 //              swizzle) of its tiles into a ring of raw stages.
 //   warp 1     owns the tensor memory and issues the MMAs from one thread.  The
 //              job operand comes from tensor memory: per 8-wide K step one MMA
 //              of width 2N with x_hi against [q_hi ; q_lo] and one of width N
 //              with x_lo against q_hi, so accumulator columns [0, N) and
-//              [N, 2N) add up to the 3xTF32 product.
-//   warps 2-5  converters, one per tensor-memory lane quarter: each thread
-//              reads its row of a landed chunk, releases the raw stage at once,
-//              and writes x_hi and x_lo into tensor memory (tcgen05.st).  Raw
-//              stages therefore never wait on the tensor core, and shared
-//              memory holds little besides them.
-//   warps 6-9  epilogue: read the accumulator (warp w owns lanes 32*(w%4) ..),
-//              with the row masks of the tile read one tile ahead,
-//              test every passing (row, query) against the query's threshold
-//              without branches, and record the few candidates in a per-warp
-//              shared-memory list flushed to the query buffers in bulk.
+//              [N, 2N) add up to the 3xTF32 product.  Four accumulator buffers
+//              when N <= 32 (two above), so the MMAs run ahead of the epilogue.
+//   warps 2-5, 10-13  converters, two sets of one warp per tensor-memory lane
+//              quarter, taking alternate chunks: each thread reads its row of a
+//              landed chunk, releases the raw stage at once, and writes x_hi
+//              and x_lo into tensor memory (tcgen05.st).  Raw stages therefore
+//              never wait on the tensor core.
+//   warps 6-9 (and 14-17)  epilogue: read the accumulator (warp w owns lanes
+//              32*(w%4) ..), with the row masks of the tile read one tile
+//              ahead, test every passing (row, query) against the query's
+//              threshold without branches, and record the few candidates in a
+//              per-warp shared-memory list flushed to the query buffers in
+//              bulk; a second set takes alternate tiles for BF16/FP8 rows.
 // All waits are bounded; on a timeout the error word gets LR_ERR_TIMEOUT, the
 // loader lets issued copies land, the MMA warp waits for its MMAs, and the
 // tensor memory is freed before the CTA exits.
@@ -49,9 +52,16 @@
 namespace lr {
 namespace {
 
-constexpr int kTcThreads = 448;
-constexpr int kEpiWarp0 = 6;    // epilogue warps 6-9
-constexpr int kConvWarp1 = 10;  // second converter set: warps 10-13 (the first is warps 2-5)
+// warp roles: 0 loader, 1 MMA issuer, 2-5 and 10-13 the two converter sets,
+// 6-9 the epilogue set, and for BF16/FP8 rows 14-17 a second epilogue set (the
+// narrow rows leave more tiles per microsecond to test; FP32 runs faster with
+// one set and the shared memory it saves)
+constexpr int kEpiWarp0 = 6;
+constexpr int kConvWarp1 = 10;
+constexpr int kEpiWarp1 = 14;
+__host__ __device__ constexpr int tc_epi_sets(int e) { return e == kElemF32 ? 1 : 2; }
+__host__ __device__ constexpr int tc_threads(int e) { return (kEpiWarp1 + 4 * (tc_epi_sets(e) - 1)) * 32; }
+__device__ __forceinline__ bool is_converter(int w) { return (w >= 2 && w < kEpiWarp0) || (w >= kConvWarp1 && w < kEpiWarp1); }
 constexpr int kLoadWarp = 0;
 constexpr int kTileRows = 128;
 constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile of 128-byte rows
@@ -64,6 +74,9 @@ __host__ __device__ constexpr int tc_row_bytes(int e) { return e == kElemFP8 ? 6
 constexpr int kWarpCand = 512;                // candidates staged per epilogue warp (flushed past 256)
 constexpr int kABufs = 4;                     // x_hi/x_lo chunk buffers in tensor memory
 constexpr uint32_t kTmemCols = 512;           // the whole tensor memory: one CTA per SM
+// Accumulator buffers (2N columns each): four when they fit beside the x_hi/x_lo
+// buffers, so the MMAs can run up to four tiles ahead of the epilogue.
+__host__ __device__ constexpr int tc_acc_bufs(int n) { return n <= 32 ? 4 : 2; }  // even: one per epilogue set
 
 // Row mask word of the tile list: bit q = launch query q passes the row.
 template <int N>
@@ -76,7 +89,7 @@ struct TcLayout {
 
 __host__ __device__ inline size_t tc_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S) {
+__host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S, int epi_warps) {
   TcLayout T;
   T.S = S;
   T.C = d_pad / epc;   // raw chunks per tile
@@ -90,13 +103,13 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S) 
   T.taus = tc_align(off, 16);
   off = T.taus + (size_t)N * 12;  // 64-bit thresholds, then their score words as floats
   T.cand = tc_align(off, 16);     // per epilogue warp: keys, then query indices (bytes)
-  off = T.cand + (size_t)4 * kWarpCand * 9;
+  off = T.cand + (size_t)epi_warps * kWarpCand * 9;
   T.ccnt = tc_align(off, 16);
-  off = T.ccnt + 16;
+  off = T.ccnt + (size_t)epi_warps * 4;
   T.cq = off;  // per epilogue warp: per-query counts, then reserved bases, of one flush
-  off = T.cq + (size_t)4 * 2 * N * 4;
+  off = T.cq + (size_t)epi_warps * 2 * N * 4;
   T.bars = tc_align(off, 16);
-  off = T.bars + (size_t)(2 * S + 2 * kABufs + 4 + 1) * 8;
+  off = T.bars + (size_t)(2 * S + 2 * kABufs + 2 * tc_acc_bufs(N) + 1) * 8;
   T.holder = tc_align(off, 16);
   T.total = T.holder + 16;
   return T;
@@ -110,13 +123,14 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
 }
 
 template <int N, int E>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(tc_threads(E), 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned for the swizzle atoms
-  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S);
+  constexpr int kSets = tc_epi_sets(E), kThreads = tc_threads(E);
+  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S, 4 * kSets);
   const int C = T.C;
   const int C32 = T.C32;
   unsigned char *raw = smem + T.raw;
@@ -126,12 +140,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + T.bars);
   uint64_t *raw_full = bars, *raw_empty = bars + S;
   uint64_t *a_full = bars + 2 * S, *a_empty = a_full + kABufs;
-  uint64_t *acc_full = a_empty + kABufs, *acc_empty = acc_full + 2;
-  uint64_t *drain = acc_empty + 2;
+  constexpr int kAcc = tc_acc_bufs(N);
+  uint64_t *acc_full = a_empty + kABufs, *acc_empty = acc_full + kAcc;
+  uint64_t *drain = acc_empty + kAcc;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + T.holder);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const uint32_t acol0 = 4u * (uint32_t)N;  // first tensor-memory column of the x_hi/x_lo buffers
+  const uint32_t acol0 = (uint32_t)(kAcc * 2 * N);  // first tensor-memory column of the x_hi/x_lo buffers
   __shared__ bool s_last;
   __shared__ uint32_t s_nlist;
   __shared__ uint32_t s_live[2];  // bit q: query q takes part in this launch
@@ -145,7 +160,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&a_full[i], 4);
       mbar_init(&a_empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kAcc; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 4);
     }
@@ -158,17 +173,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // queries of the launch in the K-major 128-byte swizzle layout, split into
   // hi/lo; each thread issues its loads of a round together, then stores
   constexpr int kQu = 8;
-  for (int i0 = 0; i0 < C32 * N * 32; i0 += kQu * kTcThreads) {
+  for (int i0 = 0; i0 < C32 * N * 32; i0 += kQu * kThreads) {
     float v[kQu];
 #pragma unroll
     for (int u = 0; u < kQu; ++u) {
-      const int i = i0 + u * kTcThreads + threadIdx.x;
+      const int i = i0 + u * kThreads + threadIdx.x;
       const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
       v[u] = i < C32 * N * 32 && r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 32 + k] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < kQu; ++u) {
-      const int i = i0 + u * kTcThreads + threadIdx.x;
+      const int i = i0 + u * kThreads + threadIdx.x;
       if (i >= C32 * N * 32) break;
       const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
       const float h = __uint_as_float(__float_as_uint(v[u]) & 0xFFFFE000u);
@@ -267,8 +282,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint64_t pr = 0, pa = 0;
       bool issued = false;
       for (int64_t k = 0; k < n_mine && ok; ++k) {
-        const int ab = (int)(pa & 1u);
-        if (!mbar_wait(&acc_empty[ab], (uint32_t)((pa >> 1) & 1u) ^ 1u)) {
+        const int ab = (int)(pa % (uint64_t)kAcc);
+        if (!mbar_wait(&acc_empty[ab], (uint32_t)((pa / kAcc) & 1u) ^ 1u)) {
           ok = false;
           break;
         }
@@ -319,7 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!ok) atomicOr(a.err, kErrTimeout);
     }
     __syncwarp();
-  } else if (warp < kEpiWarp0 || warp >= kConvWarp1) {
+  } else if (is_converter(warp)) {
     // ------------------------------------------------------------- converters
     // two sets of four warps take alternate chunks (set = chunk index & 1), so
     // two chunks per lane quarter are in flight; S and kABufs are even, so a
@@ -401,18 +416,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
   } else {
     // ------------------------------------------------------------- epilogue
+    // with two sets, sets of four warps take alternate tiles (set = tile index
+    // & 1); with an even number of accumulator buffers each buffer belongs to
+    // one set
     const int quarter = warp & 3;
-    const int ew = warp - kEpiWarp0;
-    uint64_t pa = 0;
+    const int eset = warp >= kEpiWarp1 ? 1 : 0;
+    const int ew = eset * 4 + (warp - (eset ? kEpiWarp1 : kEpiWarp0));  // 0..7: the warp's candidate list
     // Candidates are recorded in a per-warp shared-memory list by the lanes that
-    // find them (a shared-memory atomic each).  A flush tests them exactly,
+    // find them (a shared-memory atomic each; placing them by a prefix sum over
+    // the lanes was measured slower).  A flush tests them exactly,
     // counts them per query, reserves each query's range of its buffer with one
     // global atomic and scatters the keys, so a query with many candidates (a
     // broad filter in the threshold sample) does not serialise on its counter.
     // The flush stays inline: an out-of-line call in this loop, between the
     // warp-collective tensor-memory loads, has faulted.
     uint64_t *ckey = reinterpret_cast<uint64_t *>(smem + T.cand) + (size_t)ew * kWarpCand;
-    uint8_t *cqry = reinterpret_cast<uint8_t *>(smem + T.cand + (size_t)4 * kWarpCand * 8) + (size_t)ew * kWarpCand;
+    uint8_t *cqry = reinterpret_cast<uint8_t *>(smem + T.cand + (size_t)4 * kSets * kWarpCand * 8) + (size_t)ew * kWarpCand;
     uint32_t *ccnt = reinterpret_cast<uint32_t *>(smem + T.ccnt) + ew;
     uint32_t *cq = reinterpret_cast<uint32_t *>(smem + T.cq) + (size_t)ew * 2 * N;
     uint32_t *cb = cq + N;
@@ -473,33 +492,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // the list may be one written for a larger set of queries (the exact
     // fallback reuses the main pass's list): only this launch's queries count
     const uint64_t live_mask = ((uint64_t)s_live[1] << 32) | s_live[0];
-    int32_t t_next = tile_of(0), t_after = tile_of(1);
-    RowMask<N> qm_next = mask_of(t_next, 0);
-    float xs_next = scale_of(t_next, 0);
-    for (int64_t k = 0; k < n_mine && ok; ++k) {
+    int32_t t_next = tile_of(eset), t_after = tile_of(eset + kSets);
+    RowMask<N> qm_next = mask_of(t_next, eset);
+    float xs_next = scale_of(t_next, eset);
+    for (int64_t k = eset; k < n_mine && ok; k += kSets) {  // this set's tiles
       const uint64_t qmask = (uint64_t)qm_next & live_mask;
       const uint32_t grow = (uint32_t)(max(t_next, 0) * kTileRows + lr);
       const float xs = xs_next;
-      qm_next = mask_of(t_after, k + 1);
-      xs_next = scale_of(t_after, k + 1);
+      qm_next = mask_of(t_after, k + kSets);
+      xs_next = scale_of(t_after, k + kSets);
       t_next = t_after;
-      t_after = tile_of(k + 2);
-      const int ab = (int)(pa & 1u);
-      if (!warp_wait(&acc_full[ab], (uint32_t)((pa >> 1) & 1u), lane)) {
+      t_after = tile_of(k + 2 * kSets);
+      const uint64_t pa = (uint64_t)k;  // accumulator use = tile index
+      const int ab = (int)(pa % (uint64_t)kAcc);
+      if (!warp_wait(&acc_full[ab], (uint32_t)((pa / kAcc) & 1u), lane)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 2 * N);
-#pragma unroll 1
-      for (int j = 0; j < N / 16; ++j) {
+      // queries 16j .. 16j+15 of the lane's row: rh = x_hi.q_hi + x_lo.q_hi, rl = x_hi.q_lo
+      auto test_block = [&](int j, const uint32_t (&rh)[16], const uint32_t (&rl)[16]) {
         const uint32_t bm = (uint32_t)(qmask >> (16 * j)) & 0xFFFFu;
-        if (!__any_sync(0xFFFFFFFFu, bm != 0u)) continue;  // no lane needs this block of 16 queries
-        __syncwarp();
-        uint32_t rh[16], rl[16];
-        tmem_ld16(taddr + (uint32_t)(16 * j), rh);      // x_hi.q_hi + x_lo.q_hi
-        tmem_ld16(taddr + (uint32_t)(N + 16 * j), rl);  // x_hi.q_lo
-        tmem_ld_wait();
         if (a.mode == kCollect) {
           // A key can reach the threshold only if its score word does, i.e. the
           // score reaches the float threshold: a branch-free test builds the
@@ -550,11 +564,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               atomicAdd(&a.hist[(size_t)(a.q_base + q) * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
           }
         }
+      };
+      // one block of 16 queries at a time (loading all blocks before one wait
+      // was measured slower)
+#pragma unroll 1
+      for (int j = 0; j < N / 16; ++j) {
+        if (!__any_sync(0xFFFFFFFFu, ((qmask >> (16 * j)) & 0xFFFFu) != 0u)) continue;  // no lane needs it
+        __syncwarp();
+        uint32_t rh[16], rl[16];
+        tmem_ld16(taddr + (uint32_t)(16 * j), rh);
+        tmem_ld16(taddr + (uint32_t)(N + 16 * j), rl);
+        tmem_ld_wait();
+        test_block(j, rh, rl);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[ab]);
-      ++pa;
     }
     flush();
     if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
@@ -585,18 +610,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 template <int N, int E>
 cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cudaStream_t s) {
-  static_assert(4 * N + 64 * kABufs <= (int)kTmemCols, "tensor memory budget");
+  static_assert(tc_acc_bufs(N) * 2 * N + 64 * kABufs <= (int)kTmemCols, "tensor memory budget");
   static_assert(kABufs % 2 == 0, "each converter set owns every other x_hi/x_lo buffer");
   const size_t budget = 220u * 1024u;
   int S = 12;  // raw stages: even (each converter set owns every other stage)
   if (a.d_pad % tc_epc(E) != 0) return cudaErrorInvalidValue;
-  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, S).total + 1024 > budget) S -= 2;
-  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S);
+  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, S, 4 * tc_epi_sets(E)).total + 1024 > budget) S -= 2;
+  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S, 4 * tc_epi_sets(E));
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
   auto *fn = k_scan_tc<N, E>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(T.total + 1024));
   if (e != cudaSuccess) return e;
-  fn<<<grid, kTcThreads, T.total + 1024, s>>>(a, tmap, S);
+  fn<<<grid, tc_threads(E), T.total + 1024, s>>>(a, tmap, S);
   return cudaGetLastError();
 }
 
