@@ -239,17 +239,14 @@ def scan_plan(args):
 
 
 def measured_traffic(args):
-    """DRAM bytes per main pass (tile filter + scan) from the committed ncu record, or None when the
-    record does not cover the current kernel sources or this workload (10M x 128, batch 32, tensor-core
-    plan, FP32 rows)."""
+    """DRAM bytes per main-scan launch from the committed ncu record, or None when the record does not
+    cover the current kernel sources or this workload (10M x 128, batch 32, tensor-core plan, FP32)."""
     import hashlib
 
     kernel, _, _ = scan_plan(args)
-    if kernel != "k_scan_tc":
-        return None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            rec = json.load(fh)["main_pass"]
+            rec = json.load(fh)[kernel]
         for path, want in rec["sources"].items():
             with open(os.path.join(ROOT, path), "rb") as fh:
                 if hashlib.sha256(fh.read()).hexdigest() != want:
@@ -258,15 +255,18 @@ def measured_traffic(args):
         return None
     if (args.n, args.dim, args.batch, args.dtype) != (10_000_000, 128, 32, "f32"):
         return None
-    return float(rec["traffic_per_pass_10M"])
+    return float(rec["traffic_per_launch_10M"])
 
 
 def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
-    """Bytes the main scan must move per launch: rows that pass some query of the launch (each read
-    once at d_pad*4 bytes) plus, per distinct term, the cheaper of its bitmap and its posting list."""
+    """Bytes the main scan must move per launch.  GEMV scan (predicate inside): rows that pass some
+    query of the launch (each read once at d_pad*elem bytes) plus, per distinct term, the cheaper of
+    its bitmap and its posting list.  Tensor-core scan (the tile filter has run before, alongside the
+    threshold sample): the same rows plus the row masks of the listed tiles (128 rows x 4 bytes, 8 above
+    32 queries, per 128-row tile holding a passing row)."""
     import torch
 
-    _, per, d_pad = scan_plan(args)
+    kernel, per, d_pad = scan_plan(args)
     rb = row_bytes(args)
     n = corpus.n
     df = corpus.df
@@ -280,6 +280,12 @@ def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
             union |= bm[i]
         words = union.view(torch.int32).cpu().numpy().view(np.uint32)
         rows = int(np.unpackbits(words.view(np.uint8)).sum())
+        if kernel == "k_scan_tc":
+            tiles = int(np.count_nonzero(words[: len(words) // 4 * 4].reshape(-1, 4).any(axis=1)))
+            if len(words) % 4:
+                tiles += int(words[len(words) // 4 * 4:].any())
+            per_launch.append(rows * rb + tiles * 128 * (4 if sub.n <= 32 else 8))
+            continue
         terms = {int(t) for t in sub.terms}
         p = sum(min(n / 8.0, 4.0 * float(df[t])) for t in terms)
         per_launch.append(rows * rb + p)
@@ -431,9 +437,7 @@ def run_ours(args):
     achieved = (sum(per_launch) / 1e9) / (scan_ms / 1e3)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic(args),
-            "kernel": ("k_tile_filter + k_scan_tc (main pass: term filter, then scan; %d per step)" % n_scan
-                       if scan_plan(args)[0] == "k_scan_tc" else
-                       "%s (main scan, %d launches per step)" % (scan_plan(args)[0], n_scan)),
+            "kernel": "%s (main scan, %d launches per step)" % (scan_plan(args)[0], n_scan),
             "algorithmic_bytes_per_launch": float(np.mean(per_launch)), "launch_ms": scan_ms / max(n_scan, 1),
             "peak_kind": peak_kind}
 

@@ -120,6 +120,34 @@ __global__ void k_scatter_postings(const int64_t *post_off, const uint32_t *post
   }
 }
 
+// Dense expansion of sorted posting lists into term-major bitmaps (one block
+// per span of 2^span_log2 words of one term): the block ORs the span's
+// postings into shared memory and writes every word of the span once, so the
+// bitmaps need no clearing and no global atomics.  spans[t][j] is the offset
+// of term t's first posting at or after row 32 * 2^span_log2 * j.
+__global__ void k_expand_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *spans,
+                                  int n_spans, int span_log2, const int32_t *terms, uint32_t *bitmaps,
+                                  int64_t n_words, int64_t n) {
+  extern __shared__ uint32_t span_words[];
+  const int j = blockIdx.x;
+  const int32_t t = terms[blockIdx.y];
+  const int sw = 1 << span_log2;
+  const int64_t w0 = (int64_t)j << span_log2;
+  const int64_t base = post_off[t];
+  const int32_t *sp = spans + (size_t)t * (size_t)(n_spans + 1);
+  const int64_t lo = base + sp[j], hi = base + sp[j + 1];
+  for (int w = threadIdx.x; w < sw; w += blockDim.x) span_words[w] = 0u;
+  __syncthreads();
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+    const uint32_t id = post_ids[p];
+    const int64_t local = (int64_t)(id >> 5) - w0;
+    if ((int64_t)id < n && local >= 0 && local < sw) atomicOr(&span_words[local], 1u << (id & 31u));
+  }
+  __syncthreads();
+  uint32_t *bm = bitmaps + (size_t)blockIdx.y * (size_t)n_words;
+  for (int w = threadIdx.x; w < sw && w0 + w < n_words; w += blockDim.x) bm[w0 + w] = span_words[w];
+}
+
 // One warp per query: copy into [B][d_pad] (zero padded), FP32-normalised for cosine.
 __global__ void k_prep_queries(const float *in, float *out, int B, int dim, int d_pad, int cosine, uint32_t *err) {
   const int lane = threadIdx.x & 31;
@@ -223,6 +251,21 @@ cudaError_t launch_scatter_postings(const int64_t *post_off, const uint32_t *pos
     k_scatter_postings<<<grid, 256, 0, s>>>(post_off, post_ids, terms + t0, nt, bitmaps + (size_t)t0 * n_words,
                                             n_words, n, err);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_expand_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *spans,
+                                   int n_spans, int span_log2, const int32_t *terms, int n_terms, uint32_t *bitmaps,
+                                   int64_t n_words, int64_t n, cudaStream_t s) {
+  const size_t smem = (size_t)4 << span_log2;
+  if (smem > 48u * 1024u) return cudaErrorInvalidValue;
+  for (int t0 = 0; t0 < n_terms; t0 += 65535) {  // grid.y is limited to 65535
+    const int nt = n_terms - t0 < 65535 ? n_terms - t0 : 65535;
+    k_expand_postings<<<dim3((unsigned)n_spans, (unsigned)nt), 256, smem, s>>>(
+        post_off, post_ids, spans, n_spans, span_log2, terms + t0, bitmaps + (size_t)t0 * n_words, n_words, n);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

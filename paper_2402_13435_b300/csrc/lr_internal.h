@@ -108,7 +108,8 @@ struct ScanArgs {
   uint32_t *err;                 // device error word
   // tile list of the tensor-core plan: written by the tile filter, read by the
   // scan, whose last CTA resets the count
-  int32_t *tile_row;             // [tile_cap] ids t of the listed 128-row tiles (rows 128 t ..)
+  int32_t *tile_row;             // [tile_cap] ids e of the listed 128-row tiles: tile e & 1 of the
+                                 // (e >> 1)-th visited group (rows 128 e .. for a full pass)
   void *tile_msg;                // [tile_cap][128] row masks by tile id: bit q = query q passes the row
                                  // (32-bit words if nq <= 32, else 64-bit)
   uint32_t *tile_cnt;            // tiles listed
@@ -216,6 +217,11 @@ cudaError_t launch_quantize_rows(const float *X, int64_t n, int d_pad, int elem,
                                  cudaStream_t s);
 cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,
                                 uint32_t *err, cudaStream_t s);
+// Sorted posting lists -> term-major bitmaps, every word written (no clearing
+// needed); spans: [vocab][n_spans + 1] posting offsets at span boundaries.
+cudaError_t launch_expand_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *spans,
+                                   int n_spans, int span_log2, const int32_t *terms, int n_terms, uint32_t *bitmaps,
+                                   int64_t n_words, int64_t n, cudaStream_t s);
 cudaError_t launch_scatter_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *terms,
                                     int n_terms, uint32_t *bitmaps, int64_t n_words, int64_t n, uint32_t *err,
                                     cudaStream_t s);

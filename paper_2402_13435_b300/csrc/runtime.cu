@@ -109,6 +109,10 @@ struct lr_index {
   std::vector<int64_t> post_off_h;
   int64_t *post_off_d = nullptr;
   uint32_t *post_ids_d = nullptr;
+  // span table of the posting-list terms (sorted postings only): [vocab][n_spans + 1]
+  // offsets of each term's first posting at or after every span of 2^span_log2 words
+  int32_t *span_d = nullptr;
+  int n_spans = 0, span_log2 = 0;
   // limits
   int max_batch = 0, max_k = 0, max_batch_terms = 0, max_sparse = 0;
   int auto_stride = 0;
@@ -127,10 +131,18 @@ struct lr_index {
   uint32_t *n_flag = nullptr, *done_ctr = nullptr, *work_ctr = nullptr, *err = nullptr;
   uint32_t *hist = nullptr;
   uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
-  int32_t *tile_row = nullptr;  // tile list of the tensor-core plan
+  int32_t *tile_row = nullptr;  // tile list of the tensor-core plan: main pass
   uint64_t *tile_msg = nullptr;
   uint32_t *tile_cnt = nullptr;
   int64_t tile_cap = 0;
+  int32_t *tile_row_s = nullptr;  // and of the threshold sample (its own, so both filters can run at once)
+  uint64_t *tile_msg_s = nullptr;
+  uint32_t *tile_cnt_s = nullptr;
+  int64_t tile_cap_s = 0;
+  // second stream of the search: the main pass's tile filter runs there while
+  // the threshold sample runs on the caller's stream
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t *o_ids = nullptr, *o_cnt = nullptr, *o_cand = nullptr, *o_fb = nullptr;
   int32_t *c_ids = nullptr, *c_cnt = nullptr, *kfin = nullptr, *o_ties = nullptr;  // precision form
   float *c_sc = nullptr;
@@ -166,8 +178,12 @@ void free_index(lr_index *ix) {
     cudaFree(ix->dense_bm);
     cudaFree(ix->post_off_d);
     cudaFree(ix->post_ids_d);
+    cudaFree(ix->span_d);
   }
   cudaFree(ix->ws);
+  if (ix->ev_fork) cudaEventDestroy(ix->ev_fork);
+  if (ix->ev_join) cudaEventDestroy(ix->ev_join);
+  if (ix->aux) cudaStreamDestroy(ix->aux);
   for (int i = 0; i < 2; ++i) {
     if (ix->filt_h[i]) cudaFreeHost(ix->filt_h[i]);
     if (ix->filt_ev[i]) cudaEventDestroy(ix->filt_ev[i]);
@@ -337,6 +353,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_krem = cv.take<int32_t>(B);
   const size_t o_nflag = cv.take<uint32_t>(1);
   const size_t o_tcnt = cv.take<uint32_t>(1);
+  const size_t o_tcnt_s = cv.take<uint32_t>(1);
   const size_t o_state_end = cv.take<char>(0);
   const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
   const size_t o_err = cv.take<uint32_t>(1);
@@ -348,6 +365,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->tile_cap = 2 * ix->n_groups;  // every 128-row tile of the index
   const size_t o_trow = cv.take<int32_t>((size_t)ix->tile_cap);
   const size_t o_tmsg = cv.take<uint64_t>((size_t)ix->tile_cap * 128);
+  ix->tile_cap_s = 2 * (ix->samp_cap / kGroupRows + 2);  // the sampled groups' tiles (sample rows <= samp_cap)
+  const size_t o_trow_s = cv.take<int32_t>((size_t)ix->tile_cap_s);
+  const size_t o_tmsg_s = cv.take<uint64_t>((size_t)ix->tile_cap_s * 128);
   const size_t o_oids = cv.take<int32_t>((size_t)B * ix->max_k);
   const size_t o_osc = cv.take<float>((size_t)B * ix->max_k);
   const size_t o_ocnt = cv.take<int32_t>(B);
@@ -394,6 +414,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->tile_row = (int32_t *)(w + o_trow);
   ix->tile_msg = (uint64_t *)(w + o_tmsg);
   ix->tile_cnt = (uint32_t *)(w + o_tcnt);
+  ix->tile_row_s = (int32_t *)(w + o_trow_s);
+  ix->tile_msg_s = (uint64_t *)(w + o_tmsg_s);
+  ix->tile_cnt_s = (uint32_t *)(w + o_tcnt_s);
   ix->o_ids = (int32_t *)(w + o_oids);
   ix->o_sc = (float *)(w + o_osc);
   ix->o_cnt = (int32_t *)(w + o_ocnt);
@@ -414,6 +437,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
     LR_CK(cudaHostAlloc((void **)&ix->filt_h[i], ix->filt_bytes, cudaHostAllocDefault));
     LR_CK(cudaEventCreateWithFlags(&ix->filt_ev[i], cudaEventDisableTiming));
   }
+  LR_CK(cudaStreamCreateWithFlags(&ix->aux, cudaStreamNonBlocking));
+  LR_CK(cudaEventCreateWithFlags(&ix->ev_fork, cudaEventDisableTiming));
+  LR_CK(cudaEventCreateWithFlags(&ix->ev_join, cudaEventDisableTiming));
   ix->sparse_stamp.assign(ix->vocab, 0);
   ix->sparse_id.assign(ix->vocab, -1);
   ix->local_stamp.assign(ix->vocab, 0);
@@ -433,6 +459,9 @@ lr_status index_clone_slot(const lr_index *base, int max_batch, void *stream, lr
   ix->owns_data = false;
   ix->device_bytes = 0;
   ix->ws = nullptr;
+  ix->aux = nullptr;  // each context gets its own stream and events
+  ix->ev_fork = nullptr;
+  ix->ev_join = nullptr;
   for (int i = 0; i < 2; ++i) {
     ix->filt_h[i] = nullptr;
     ix->filt_ev[i] = nullptr;
@@ -622,6 +651,42 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
       CK2(cudaStreamSynchronize(s));
       cudaFree(terms_d);
     }
+    // Span table for the per-batch expansion of the posting-list terms: when
+    // every such list is sorted, a search writes each term's bitmap densely
+    // (k_expand_postings) instead of clearing it and scattering with atomics.
+    if (ix->n_dense < ix->vocab && nnz > 0 && !is_device_ptr(d->post_ids)) {
+      bool sorted = true;
+      for (int t = 0; t < ix->vocab && sorted; ++t) {
+        if (ix->term_dense[t] >= 0) continue;
+        for (int64_t p = po[t] + 1; p < po[t + 1]; ++p)
+          if (d->post_ids[p] < d->post_ids[p - 1]) {
+            sorted = false;
+            break;
+          }
+      }
+      int lg = 11;  // 2048 words (64K rows) per span, wider if the table would pass 256 MB
+      auto spans_for = [&](int l) { return (ix->n_words + (int64_t(1) << l) - 1) >> l; };
+      while (lg < 13 && (int64_t)ix->vocab * (spans_for(lg) + 1) * 4 > (int64_t(256) << 20)) ++lg;
+      const int64_t ns = spans_for(lg);
+      if (sorted && (int64_t)ix->vocab * (ns + 1) * 4 <= (int64_t(256) << 20)) {
+        std::vector<int32_t> tab((size_t)ix->vocab * (size_t)(ns + 1), 0);
+        for (int t = 0; t < ix->vocab; ++t) {
+          if (ix->term_dense[t] >= 0) continue;
+          const uint32_t *b = d->post_ids + po[t], *e = d->post_ids + po[t + 1];
+          int32_t *row = tab.data() + (size_t)t * (size_t)(ns + 1);
+          for (int64_t j = 0; j <= ns; ++j) {
+            const uint64_t first_row = (uint64_t)j << (lg + 5);
+            row[j] = (int32_t)(std::lower_bound(b, e, first_row, [](uint32_t x, uint64_t v) { return (uint64_t)x < v; }) - b);
+          }
+        }
+        CK2(cudaMalloc(&ix->span_d, tab.size() * sizeof(int32_t)));
+        ix->device_bytes += tab.size() * sizeof(int32_t);
+        CK2(cudaMemcpyAsync(ix->span_d, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK2(cudaStreamSynchronize(s));
+        ix->n_spans = (int)ns;
+        ix->span_log2 = lg;
+      }
+    }
   }
 
   {
@@ -653,6 +718,20 @@ struct Compiled {
   std::vector<int32_t> sparse_terms;  // distinct posting-list terms of the batch
   size_t off_k = 0, off_kfin = 0, off_rank = 0, off_sparse = 0, bytes = 0;
 };
+
+// The batch's posting-list terms -> workspace bitmaps (step A1): a dense write
+// of every word when the index has a span table, else clear + scatter.
+cudaError_t expand_sparse_terms(lr_index *ix, const Compiled &C, cudaStream_t s) {
+  const int32_t *terms = (const int32_t *)(ix->filt_d + C.off_sparse);
+  const int nt = (int)C.sparse_terms.size();
+  if (ix->span_d)
+    return launch_expand_postings(ix->post_off_d, ix->post_ids_d, ix->span_d, ix->n_spans, ix->span_log2, terms, nt,
+                                  ix->sparse_bm, ix->n_words, ix->n, s);
+  const cudaError_t e = cudaMemsetAsync(ix->sparse_bm, 0, (size_t)ix->n_words * nt * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  return launch_scatter_postings(ix->post_off_d, ix->post_ids_d, terms, nt, ix->sparse_bm, ix->n_words, ix->n, ix->err,
+                                 s);
+}
 
 // Validate the CNF batch and lay out, in the pinned staging buffer, the
 // per-launch slot tables and clause lists.  Slot pointers are device addresses
@@ -843,10 +922,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   }
   LR_LAUNCH(launch_prep_queries(qsrc, ix->q_ws, B, ix->dim, ix->d_pad, ix->metric == LR_COSINE, ix->err, s));
   if (!C.sparse_terms.empty()) {
-    const size_t words = (size_t)ix->n_words * C.sparse_terms.size();
-    LR_CK(cudaMemsetAsync(ix->sparse_bm, 0, words * sizeof(uint32_t), s));
-    LR_LAUNCH(launch_scatter_postings(ix->post_off_d, ix->post_ids_d, (const int32_t *)(ix->filt_d + C.off_sparse),
-                                  (int)C.sparse_terms.size(), ix->sparse_bm, ix->n_words, ix->n, ix->err, s));
+    ++n_launch;
+    LR_CK(expand_sparse_terms(ix, C, s));
   }
 
   auto scan_args = [&](const SubBatch &sb) {
@@ -903,12 +980,37 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     return launch_scan_tc(a, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(2 * groups), s);
   };
 
+  auto main_args = [&](const SubBatch &sb) {
+    ScanArgs a = scan_args(sb);
+    a.tau = ix->tau;
+    a.buf = ix->cand_buf;
+    a.buf_cap = cap;
+    a.buf_cnt = ix->cnt;
+    a.overflow = ix->ovf;
+    a.pass_cnt = ix->pass;
+    return a;
+  };
+  // With one sub-batch the main pass's tile filter does not depend on the
+  // threshold: it runs on the second stream while the threshold sample runs
+  // here, and the main scan waits for it.
+  const bool early_filter = reuse_list;
+  if (early_filter) {
+    LR_CK(cudaEventRecord(ix->ev_fork, s));
+    LR_CK(cudaStreamWaitEvent(ix->aux, ix->ev_fork, 0));
+    ++n_launch;
+    LR_CK(launch_tile_filter(main_args(C.subs[0]), ix->num_sms, ix->aux));
+    LR_CK(cudaEventRecord(ix->ev_join, ix->aux));
+  }
   // 1. threshold sample
   if (sp.stride > 0) {
     for (const SubBatch &sb : C.subs) {
       ScanArgs a = scan_args(sb);
       a.g_begin = sp.stride / 2;
       a.g_step = sp.stride;
+      a.tile_row = ix->tile_row_s;  // the sample's own tile list
+      a.tile_msg = ix->tile_msg_s;
+      a.tile_cnt = ix->tile_cnt_s;
+      a.tile_cap = ix->tile_cap_s;
       a.tau = nullptr;  // keep every passing key of the sampled groups
       a.buf = ix->samp_buf;
       a.buf_cap = ix->samp_cap;
@@ -927,16 +1029,10 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     LR_LAUNCH(launch_select(t, B, s));
   }
   // 2. main scan: candidates at or above the threshold, pass counts
+  if (early_filter) LR_CK(cudaStreamWaitEvent(s, ix->ev_join, 0));
   if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
   for (const SubBatch &sb : C.subs) {
-    ScanArgs a = scan_args(sb);
-    a.tau = ix->tau;
-    a.buf = ix->cand_buf;
-    a.buf_cap = cap;
-    a.buf_cnt = ix->cnt;
-    a.overflow = ix->ovf;
-    a.pass_cnt = ix->pass;
-    LR_LAUNCH(launch_scan(a, ix->n_groups, true, reuse_list));
+    LR_LAUNCH(launch_scan(main_args(sb), ix->n_groups, !early_filter, reuse_list));
     ++n_scan;
   }
   if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
@@ -1081,12 +1177,7 @@ lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64
   LR_CK(cudaEventRecord(ix->filt_ev[turn], s));
   ix->filt_ev_live[turn] = true;
   LR_CK(cudaMemsetAsync(ix->state, 0, ix->state_bytes, s));
-  if (!C.sparse_terms.empty()) {
-    const size_t words = (size_t)ix->n_words * C.sparse_terms.size();
-    LR_CK(cudaMemsetAsync(ix->sparse_bm, 0, words * sizeof(uint32_t), s));
-    LR_CK(launch_scatter_postings(ix->post_off_d, ix->post_ids_d, (const int32_t *)(ix->filt_d + C.off_sparse),
-                                  (int)C.sparse_terms.size(), ix->sparse_bm, ix->n_words, ix->n, ix->err, s));
-  }
+  if (!C.sparse_terms.empty()) LR_CK(expand_sparse_terms(ix, C, s));
   const int64_t out_words = (ix->n + 31) / 32;
   const bool bm_dev = out_bitmap && is_device_ptr(out_bitmap);
   uint32_t *bm = nullptr;

@@ -115,6 +115,12 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S, 
   return T;
 }
 
+// First row of list tile e: tile e & 1 of the (e >> 1)-th group the launch
+// visits (groups g_begin + i g_step).
+__device__ __forceinline__ int64_t tile_first_row(const ScanArgs &a, int32_t e) {
+  return (a.g_begin + (int64_t)(e >> 1) * a.g_step) * kGroupRows + (int64_t)(e & 1) * kTileRows;
+}
+
 // Leader-lane wait broadcast to the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int lane) {
   bool got = true;
@@ -230,12 +236,12 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   const int64_t n_list = (int64_t)s_nlist;
   const int64_t n_mine = n_list > (int64_t)blockIdx.x ? (n_list - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   auto entry = [&](int64_t k) -> int64_t { return (int64_t)blockIdx.x + k * (int64_t)gridDim.x; };
-  // id of the CTA's k-th tile; an id outside the index (which the tile filter
-  // never writes) is reported and read as -1: its rows are loaded from tile 0
-  // and no query tests them
+  // id of the CTA's k-th tile; an id outside the list's range or the index
+  // (which the tile filter never writes) is reported and read as -1: its rows
+  // are loaded from the first tile and no query tests them
   auto tile_id = [&](int64_t k) -> int32_t {
     const int32_t t = a.tile_row[entry(k)];
-    if ((int64_t)(uint32_t)t * kTileRows < a.n) return t;
+    if ((int64_t)(uint32_t)t < a.tile_cap && tile_first_row(a, t) < a.n) return t;
     atomicOr(a.err, kErrTileList);
     return -1;
   };
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         rcur = rnext;
         rnext = ids_from(k + 32);
       }
-      const int row0 = max(__shfl_sync(0xFFFFFFFFu, rcur, (int)(k & 31)), 0) * kTileRows;
+      const int row0 = (int)tile_first_row(a, max(__shfl_sync(0xFFFFFFFFu, rcur, (int)(k & 31)), 0));
       for (int c = 0; c < C; ++c) {
         const int s = (int)(pr % (uint64_t)S);
         if (!warp_wait(&raw_empty[s], (uint32_t)((pr / S) & 1u) ^ 1u, lane)) {
@@ -483,7 +489,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     };
     auto scale_of = [&](int32_t t, int64_t k) -> float {  // FP8 rows: score = scale * <q, x8>
       if constexpr (E == kElemFP8) {
-        const int64_t g = (int64_t)t * kTileRows + lr;
+        const int64_t g = tile_first_row(a, max(t, 0)) + lr;
         return k < n_mine && t >= 0 && g < a.n ? __ldg(a.xscale + g) : 0.f;
       } else {
         return 1.f;
@@ -497,7 +503,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     float xs_next = scale_of(t_next, eset);
     for (int64_t k = eset; k < n_mine && ok; k += kSets) {  // this set's tiles
       const uint64_t qmask = (uint64_t)qm_next & live_mask;
-      const uint32_t grow = (uint32_t)(max(t_next, 0) * kTileRows + lr);
+      const uint32_t grow = (uint32_t)(tile_first_row(a, max(t_next, 0)) + lr);
       const float xs = xs_next;
       qm_next = mask_of(t_after, k + kSets);
       xs_next = scale_of(t_after, k + kSets);

@@ -5,11 +5,13 @@
 // satisfy its CNF; Sec. 5.3 fuses that restriction with the embedding scan so
 // that rows no query accepts are never read.  Here the restriction runs as its
 // own wide kernel, one warp per group and one lane per two queries, and writes
-// for every 128-row tile t (rows 128 t ..) that some query passes
+// for every 128-row tile t that some query passes
 //     tile_msg[t][r]     the mask of the launch's queries that pass row r
 //                        (bit q; 32-bit words when the launch has at most 32
 //                        queries, else 64-bit), stored at the tile's own slot,
-// and appends t to the compact list tile_row[].  The scan then streams exactly
+// and appends t to the compact list tile_row[]; t = 2 i + h for tile h of the
+// i-th group the launch visits (groups g_begin + i g_step), so a full pass
+// numbers tiles by their rows and a sampled pass uses a compact range.  The scan then streams exactly
 // the listed tiles, and its pipeline carries no predicate latency.  A block
 // evaluates runs of eight consecutive groups, one per warp, with the next
 // run's term words (256 contiguous bytes per term at unit stride) in
@@ -147,7 +149,13 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (!((fl >> h) & 1u)) continue;
-        const uint32_t tile = (uint32_t)(g * 2 + h);  // tile id: rows 128 * id ..
+        if ((int64_t)(it * 2 + h) >= a.tile_cap) {  // the list buffers are smaller than the visit
+          if (lane == 0) atomicOr(a.err, kErrTileList);
+          continue;
+        }
+        // tile id: tile h of the it-th visited group (for a full pass, rows
+        // 128 id ..); ids stay below 2 x the groups visited <= tile_cap
+        const uint32_t tile = (uint32_t)(it * 2 + h);
         W *msg = static_cast<W *>(a.tile_msg) + (size_t)tile * 128;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {  // lane r: the queries that pass row 32w + r of the tile

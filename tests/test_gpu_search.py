@@ -231,3 +231,37 @@ def test_invalid_inputs_are_rejected(lr, small):
     with pytest.raises(lr.LRError) as e:
         lr.lr_index_create(Xbad, c.V, bitsets=c.bitsets(), max_batch=4, max_k=16)
     assert e.value.status == lr.LR_ERR_INVALID
+
+
+def test_unsorted_postings_give_identical_results(lr, small):
+    """Posting lists need not be sorted: an index over lists shuffled within each term expands them
+    by clearing and scattering (no span table) and must give the pass bitmaps and top-K of the sorted
+    lists, which the dense span expansion produces."""
+    c = small
+    B = 21
+    f = _mixed_filters(29, B, c.V, c.df, c.n)
+    po, pid = c.postings()
+    shuffled = np.array(pid, copy=True)
+    rng = np.random.default_rng(5)
+    for t in range(c.V):
+        seg = shuffled[po[t]:po[t + 1]]
+        rng.shuffle(seg)
+    Q = datagen.query_embeddings(29, B, c.d)
+
+    def _np(x):
+        return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+
+    outs = []
+    for ids in (pid, shuffled):
+        idx = lr.lr_index_create(c.X, c.V, post_off=po, post_ids=ids, n_dense_terms=32, metric="cosine",
+                                 max_batch=32, max_k=16)
+        cnt, bm = lr.lr_filter_count(idx, f, bitmap=True)
+        res = lr.lr_search(idx, Q, f, 16)
+        torch.cuda.synchronize()
+        lr.lr_index_sync(idx)
+        outs.append([_np(cnt), _np(bm)] + [_np(x) for x in res])
+        lr.lr_index_destroy(idx)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    ref_cnt, _ = oracle.filter(c.job_off, c.job_terms, c.n, f, want_matrix=True)
+    assert np.array_equal(outs[0][0], ref_cnt)
