@@ -429,8 +429,10 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     const int eset = warp >= kEpiWarp1 ? 1 : 0;
     const int ew = eset * 4 + (warp - (eset ? kEpiWarp1 : kEpiWarp0));  // 0..7: the warp's candidate list
     // Candidates are recorded in a per-warp shared-memory list by the lanes that
-    // find them (a shared-memory atomic each; placing them by a prefix sum over
-    // the lanes was measured slower).  A flush tests them exactly,
+    // find them: a shared-memory atomic each in the main scan, where hits are
+    // rare (a prefix sum over the lanes was measured slower there), and
+    // prefix-sum places in the threshold sample, where nearly every test hits.
+    // A flush tests them exactly,
     // counts them per query, reserves each query's range of its buffer with one
     // global atomic and scatters the keys, so a query with many candidates (a
     // broad filter in the threshold sample) does not serialise on its counter.
@@ -540,7 +542,38 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
             }
           }
           hit &= bm;
-          if (__any_sync(0xFFFFFFFFu, hit != 0u)) {
+          if (a.tau == nullptr) {
+            // Threshold sample: every passing pair is a candidate, so nearly
+            // every test hits; a prefix sum over the lanes' hit counts places
+            // them in the warp's list without atomics (flushed when full).
+            const uint32_t nh = (uint32_t)__popc(hit);
+            uint32_t incl = nh;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+              const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+              if (lane >= off) incl += t;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (total != 0u) {
+              uint32_t base = *ccnt;
+              if (base + total > (uint32_t)kWarpCand) {
+                flush();
+                base = 0u;
+              }
+              uint32_t e = base + incl - nh;
+#pragma unroll
+              for (int b = 0; b < 16; ++b) {
+                if ((hit >> b) & 1u) {
+                  ckey[e] = make_key(sc[b], grow);
+                  cqry[e] = (uint8_t)(16 * j + b);
+                  ++e;
+                }
+              }
+              __syncwarp();
+              if (lane == 0) *ccnt = base + total;
+              __syncwarp();
+            }
+          } else if (__any_sync(0xFFFFFFFFu, hit != 0u)) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {  // at most 256 entries are added between two checks
               const uint32_t hh = (hit >> (8 * h)) & 0xFFu;
