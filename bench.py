@@ -370,7 +370,8 @@ def run_ours(args):
     t0 = time.time()
     idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), c.V, post_off=wl["post_off"], post_ids=wl["post_ids"],
                              n_dense_terms=args.n_dense, metric="cosine", max_batch=max(args.batch, 32),
-                             max_k=args.k, dtype=args.dtype, oversample=args.oversample)
+                             max_k=args.k, dtype=args.dtype, oversample=args.oversample,
+                             max_sparse_terms=max(256, 4 * args.batch))
     torch.cuda.synchronize()
     build_s = time.time() - t0
     nb = len(wl["filters"])
