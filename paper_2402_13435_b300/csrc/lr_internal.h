@@ -152,6 +152,23 @@ cudaError_t launch_tile_filter(const ScanArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
 
+// Per-query threshold of the sample (the r-th largest sampled key, 0 when the
+// sample holds fewer than r keys or overflowed), split over up to 32 CTAs per
+// query for large samples.
+struct ThrArgs {
+  const uint64_t *buf;    // [B][cap] sample keys
+  int64_t cap;
+  const uint32_t *cnt;    // [B]
+  const uint32_t *overflow;
+  const int32_t *rank;    // [B] r
+  uint64_t *tau;          // [B] out
+  uint64_t *scratch;      // [B][8192] the slices' top keys
+  uint32_t *slice_n;      // [B][32] keys each slice kept
+  uint32_t *done;         // [B] slices finished (zero between launches)
+};
+constexpr int kThrScratchKeys = 8192;  // per query (the selection's shared-memory key capacity)
+cudaError_t launch_threshold(const ThrArgs &a, int B, cudaStream_t s);
+
 // FP32 rescore of the low-precision candidates with an FP64 re-rank of the
 // near ties at the K-th score (precision form).
 struct RescoreArgs {

@@ -135,6 +135,8 @@ struct lr_index {
   uint64_t *tile_msg = nullptr;
   uint32_t *tile_cnt = nullptr;
   int64_t tile_cap = 0;
+  uint64_t *thr_scratch = nullptr;  // split threshold selection: [B][8192] keys, [B][32] counts, [B] done
+  uint32_t *thr_slice_n = nullptr, *thr_done = nullptr;
   int32_t *tile_row_s = nullptr;  // and of the threshold sample (its own, so both filters can run at once)
   uint64_t *tile_msg_s = nullptr;
   uint32_t *tile_cnt_s = nullptr;
@@ -354,6 +356,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_nflag = cv.take<uint32_t>(1);
   const size_t o_tcnt = cv.take<uint32_t>(1);
   const size_t o_tcnt_s = cv.take<uint32_t>(1);
+  const size_t o_thr_done = cv.take<uint32_t>(B);
   const size_t o_state_end = cv.take<char>(0);
   const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
   const size_t o_err = cv.take<uint32_t>(1);
@@ -367,6 +370,8 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_tmsg = cv.take<uint64_t>((size_t)ix->tile_cap * 128);
   ix->tile_cap_s = 2 * (ix->samp_cap / kGroupRows + 2);  // the sampled groups' tiles (sample rows <= samp_cap)
   const size_t o_trow_s = cv.take<int32_t>((size_t)ix->tile_cap_s);
+  const size_t o_thr_scr = cv.take<uint64_t>((size_t)B * kThrScratchKeys);
+  const size_t o_thr_sn = cv.take<uint32_t>((size_t)B * 32);
   const size_t o_tmsg_s = cv.take<uint64_t>((size_t)ix->tile_cap_s * 128);
   const size_t o_oids = cv.take<int32_t>((size_t)B * ix->max_k);
   const size_t o_osc = cv.take<float>((size_t)B * ix->max_k);
@@ -417,6 +422,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->tile_row_s = (int32_t *)(w + o_trow_s);
   ix->tile_msg_s = (uint64_t *)(w + o_tmsg_s);
   ix->tile_cnt_s = (uint32_t *)(w + o_tcnt_s);
+  ix->thr_scratch = (uint64_t *)(w + o_thr_scr);
+  ix->thr_slice_n = (uint32_t *)(w + o_thr_sn);
+  ix->thr_done = (uint32_t *)(w + o_thr_done);
   ix->o_ids = (int32_t *)(w + o_oids);
   ix->o_sc = (float *)(w + o_osc);
   ix->o_cnt = (int32_t *)(w + o_ocnt);
@@ -1018,15 +1026,17 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       a.overflow = ix->sovf;
       LR_LAUNCH(launch_scan(a, sp.sampled_groups));
     }
-    SelectArgs t{};
-    t.mode = 0;
+    ThrArgs t{};
     t.buf = ix->samp_buf;
     t.cap = ix->samp_cap;
     t.cnt = ix->scnt;
     t.overflow = ix->sovf;
     t.rank = ix->rank;
     t.tau = ix->tau;
-    LR_LAUNCH(launch_select(t, B, s));
+    t.scratch = ix->thr_scratch;
+    t.slice_n = ix->thr_slice_n;
+    t.done = ix->thr_done;
+    LR_LAUNCH(launch_threshold(t, B, s));
   }
   // 2. main scan: candidates at or above the threshold, pass counts
   if (early_filter) LR_CK(cudaStreamWaitEvent(s, ix->ev_join, 0));

@@ -219,6 +219,104 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- threshold
+// Threshold of a query's sample (mode 0 of the selection, split over CTAs):
+// a large sample is cut into P <= kThrSlices slices of at most kSmemKeys keys;
+// CTA (q, p) finds the top r keys of its slice (the r-th largest key of the
+// whole sample is among the union of the slices' top r), and the last CTA of
+// the query selects the r-th largest of that union.  Samples that fit one
+// slice, or whose union would not fit shared memory, take one CTA.
+constexpr int kThrSlices = 32;
+static_assert(kSmemKeys == kThrScratchKeys, "scratch per query = shared-memory key capacity");
+
+__global__ void __launch_bounds__(kSelThreads) k_threshold(const ThrArgs a) {
+  extern __shared__ __align__(16) uint64_t sbuf[];  // [kSmemKeys] keys
+  __shared__ SelShared sh;
+  __shared__ bool s_last;
+  __shared__ uint32_t s_off[kThrSlices + 1];
+  const int q = blockIdx.x, p = blockIdx.y, tid = threadIdx.x;
+  const int64_t n = (int64_t)a.cnt[q] < a.cap ? (int64_t)a.cnt[q] : a.cap;
+  const int32_t r = a.rank[q];
+  if (r <= 0 || a.overflow[q] != 0u || n < r) {
+    if (p == 0 && tid == 0) a.tau[q] = 0ull;
+    return;
+  }
+  const uint64_t *g = a.buf + (size_t)q * (size_t)a.cap;
+  const int64_t P64 = (n + kSmemKeys - 1) / kSmemKeys;
+  const int P = (int)(P64 < kThrSlices ? P64 : kThrSlices);
+  if (P == 1 || (int64_t)P * r > kSmemKeys || P64 > kThrSlices) {  // one CTA takes the whole sample
+    if (p != 0) return;
+    uint64_t t;
+    if (n <= kSmemKeys) {
+      for (int64_t i = tid; i < n; i += blockDim.x) sbuf[i] = __ldcg(g + i);
+      __syncthreads();
+      t = block_kth(sbuf, n, (uint32_t)r, sh);
+    } else {
+      t = kth_large(g, n, (uint32_t)r, sbuf, sh);
+    }
+    if (tid == 0) a.tau[q] = t;
+    return;
+  }
+  if (p >= P) return;
+  const int64_t per = (n + P - 1) / P, lo = (int64_t)p * per, hi = lo + per < n ? lo + per : n;
+  const int64_t m = hi > lo ? hi - lo : 0;
+  constexpr int kU = 16;  // loads in flight per thread
+  for (int64_t b = tid; b < m; b += (int64_t)kU * blockDim.x) {
+    uint64_t v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = b + (int64_t)u * blockDim.x;
+      v[u] = i < m ? __ldcg(g + lo + i) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = b + (int64_t)u * blockDim.x;
+      if (i < m) sbuf[i] = v[u];
+    }
+  }
+  __syncthreads();
+  uint64_t *out = a.scratch + (size_t)q * kSmemKeys + (size_t)p * (size_t)r;  // r places for this slice
+  uint32_t kept;
+  if (m <= r) {
+    for (int64_t i = tid; i < m; i += blockDim.x) out[i] = sbuf[i];
+    kept = (uint32_t)m;
+  } else {
+    const uint64_t kth = block_kth(sbuf, m, (uint32_t)r, sh);
+    if (tid == 0) sh.n_out = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < m; i += blockDim.x)
+      if (sbuf[i] >= kth) out[atomicAdd(&sh.n_out, 1u)] = sbuf[i];  // exactly r keys (keys are distinct)
+    kept = (uint32_t)r;
+  }
+  if (tid == 0) a.slice_n[(size_t)q * kThrSlices + p] = kept;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&a.done[q], 1u) == (uint32_t)(P - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid == 0) {  // the union of the slices' top keys, gathered in slice order
+    uint32_t off = 0;
+    for (int pp = 0; pp < P; ++pp) {
+      s_off[pp] = off;
+      off += __ldcg(a.slice_n + (size_t)q * kThrSlices + pp);
+    }
+    s_off[P] = off;
+  }
+  __syncthreads();
+  const uint64_t *src = a.scratch + (size_t)q * kSmemKeys;
+  for (int pp = 0; pp < P; ++pp) {
+    const uint32_t kn = s_off[pp + 1] - s_off[pp];
+    for (uint32_t i = tid; i < kn; i += blockDim.x) sbuf[s_off[pp] + i] = __ldcg(src + (size_t)pp * r + i);
+  }
+  __syncthreads();
+  const uint64_t t = block_kth(sbuf, s_off[P], (uint32_t)r, sh);
+  if (tid == 0) {
+    a.tau[q] = t;
+    a.done[q] = 0u;  // ready for the next launch
+  }
+}
+
 // ---------------------------------------------------------------- rescore
 // Precision form: the low-precision scan has gathered each query's top c
 // candidates (c = oversample x K, by the scaled BF16/FP8 score).  Here every
@@ -391,6 +489,15 @@ __global__ void k_fallback_finish(const uint64_t *prefix, const uint32_t *flag, 
 }
 
 }  // namespace
+
+cudaError_t launch_threshold(const ThrArgs &a, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const size_t smem = (size_t)kSmemKeys * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(k_threshold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_threshold<<<dim3((unsigned)B, (unsigned)kThrSlices), kSelThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
