@@ -112,3 +112,30 @@ def test_tc_distinct_term_counts(lr, S):
     ids, sc, cnt = _run(lr, idx, Q, f, K, plan="tc")
     ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
     check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_tc_selective_batch_reads_compact_rows(lr, dtype):
+    """Every query of the batch passes few rows (rare terms), so most listed tiles hold a handful of
+    passing rows and most (row, query) pairs are masked out; FP32 and the BF16 precision form."""
+    n, d, V, B, K = 50_000, 128, 2048, 40, 30
+    c = datagen.corpus(14, n, d, V, 12.0, 1.1)
+    rare = [int(t) for t in np.argsort(c.df) if 20 <= c.df[t] <= 400][: 3 * B]
+    assert len(rare) == 3 * B
+    qs = [[[rare[3 * b]], [rare[3 * b + 1], rare[3 * b + 2]]] if b % 3 == 0 else [[rare[3 * b], rare[3 * b + 1]]]
+          for b in range(B)]
+    f = Filters.from_lists(qs)
+    Q = datagen.query_embeddings(14, B, d)
+    po, pid = c.postings()
+    idx = lr.lr_index_create(c.X, V, post_off=po, post_ids=pid, n_dense_terms=64, metric="cosine", max_batch=B,
+                             max_k=64, dtype=dtype)
+    ids, sc, cnt = _run(lr, idx, Q, f, K, plan="tc")
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    if dtype == "f32":
+        check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
+    else:  # the precision form: same rows, recall of the exact top K
+        assert np.array_equal(cnt, ref.count)
+        for b in range(B):
+            got, want = set(ids[b, :cnt[b]].tolist()), set(ref.ids[b, :ref.count[b]].tolist())
+            assert len(got & want) >= 0.999 * len(want) - 1e-9
+    lr.lr_index_destroy(idx)
