@@ -141,6 +141,7 @@ struct SelectArgs {
   int32_t *fallback_out;         // nullable stats
   int32_t fallback_round;        // 1 when this launch finishes fallback queries
   int32_t force_flag;            // 1: flag every query (exercise the exact fallback)
+  int32_t unsorted;              // 1: final mode writes the top K in any order (the caller re-ranks them)
   uint32_t *err;                 // device error word
 };
 
@@ -185,7 +186,11 @@ struct RescoreArgs {
   int32_t *out_count;      // nullable
   int32_t *tie_count;      // nullable [B]: candidates re-ranked in FP64
   uint32_t *err;
+  uint64_t *keys;          // [B][c_stride] FP32 keys of the candidates (written by the scoring launch)
+  uint32_t *gmax;          // [B] bits of max_j sum_k |q_k x_jk| (zero before the scoring launch)
 };
+// Two launches: the candidates' FP32 scores over several CTAs per query, then
+// per query the K-th key, the FP64 re-rank of the near-tie band and the output.
 cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s);
 // Masked softmax loss passes (loss.cu).  Row tiles of 128 over R, streamed
 // 64-row tiles of C; see loss.cu for the three modes.

@@ -147,6 +147,8 @@ struct lr_index {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t *o_ids = nullptr, *o_cnt = nullptr, *o_cand = nullptr, *o_fb = nullptr;
   int32_t *c_ids = nullptr, *c_cnt = nullptr, *kfin = nullptr, *o_ties = nullptr;  // precision form
+  uint64_t *rs_keys = nullptr;  // precision form: FP32 keys of the candidates [B][max_kq]
+  uint32_t *rs_gmax = nullptr;  // and the per-query FP32 rounding bound's magnitude [B]
   float *c_sc = nullptr;
   float *o_sc = nullptr;
   char *filt_d = nullptr;
@@ -357,6 +359,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_tcnt = cv.take<uint32_t>(1);
   const size_t o_tcnt_s = cv.take<uint32_t>(1);
   const size_t o_thr_done = cv.take<uint32_t>(B);
+  const size_t o_rs_gmax = cv.take<uint32_t>(ix->elem != kElemF32 ? B : 0);
   const size_t o_state_end = cv.take<char>(0);
   const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
   const size_t o_err = cv.take<uint32_t>(1);
@@ -384,6 +387,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_ccnt = cv.take<int32_t>(lowp ? B : 0);
   const size_t o_kfin = cv.take<int32_t>(lowp ? B : 0);
   const size_t o_ties = cv.take<int32_t>(lowp ? B : 0);
+  const size_t o_rs_keys = cv.take<uint64_t>(lowp ? (size_t)B * ix->max_kq : 0);
   const size_t o_filt = cv.take<char>(ix->filt_bytes);
   ix->ws_bytes = align_up(cv.off, 256);
   if (cudaMalloc(&ix->ws, ix->ws_bytes) != cudaSuccess) {
@@ -436,6 +440,8 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
     ix->c_cnt = (int32_t *)(w + o_ccnt);
     ix->kfin = (int32_t *)(w + o_kfin);
     ix->o_ties = (int32_t *)(w + o_ties);
+    ix->rs_keys = (uint64_t *)(w + o_rs_keys);
+    ix->rs_gmax = (uint32_t *)(w + o_rs_gmax);
   }
   ix->filt_d = w + o_filt;
   LR_CK(cudaMemsetAsync(ix->done_ctr, 0, 2 * sizeof(uint32_t), s));
@@ -1069,6 +1075,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.fallback_out = ix->o_fb;
   fa.fallback_round = 0;
   fa.force_flag = o.force_exact_fallback ? 1 : 0;
+  fa.unsorted = lowp ? 1 : 0;  // the precision form re-ranks the candidates in FP32
   fa.err = ix->err;
   LR_LAUNCH(launch_select(fa, B, s));
   // 4. exact fallback for flagged queries (each launch returns at once when none is flagged)
@@ -1123,6 +1130,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     ra.out_count = dev_out ? out_count : ix->o_cnt;
     ra.tie_count = ix->o_ties;
     ra.err = ix->err;
+    ra.keys = ix->rs_keys;
+    ra.gmax = ix->rs_gmax;
     LR_LAUNCH(launch_rescore(ra, B, s));
   }
 

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
       }
     }
     __syncthreads();
-    bitonic_desc(sort, P2);
+    if (!a.unsorted) bitonic_desc(sort, P2);
   }
   for (int i = tid; i < a.k_stride; i += blockDim.x) {
     if (i < kp) {
@@ -331,6 +331,56 @@ __global__ void __launch_bounds__(kSelThreads) k_threshold(const ThrArgs a) {
 // reported scores stay non-increasing).
 constexpr int kRsThreads = 512;
 constexpr int kMaxTie = 1024;
+constexpr int kRsSplit = 8;  // scoring CTAs per query
+constexpr int kRsRows = 4;   // candidates a warp scores at once (their rows in flight together)
+
+// FP32 dot product p = q.x and bound m = sum_k |q_k x_k| of every candidate:
+// CTA (q, s) takes candidates s * 16 + w (warp w) in steps of kRsSplit * 16
+// warps, kRsRows at a time; lane-strided partial sums, tree reductions.
+__global__ void __launch_bounds__(kRsThreads) k_rescore_scores(const RescoreArgs a) {
+  const int q = blockIdx.x, sl = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = a.ccnt[q] < a.c_stride ? a.ccnt[q] : a.c_stride;
+  const int32_t *cid = a.cid + (size_t)q * a.c_stride;
+  const float *qv = a.Q + (size_t)q * a.d_pad;
+  const int step = kRsSplit * nw * kRsRows;
+  uint32_t mx = 0u;
+  for (int i0 = (sl * nw + warp) * kRsRows; i0 < n; i0 += step) {
+    int32_t id[kRsRows];
+    float p[kRsRows], m[kRsRows];
+#pragma unroll
+    for (int u = 0; u < kRsRows; ++u) {
+      id[u] = i0 + u < n ? cid[i0 + u] : -1;
+      p[u] = 0.f;
+      m[u] = 0.f;
+    }
+    for (int k = lane; k < a.d_pad; k += 32) {
+      const float v = qv[k];
+      float xv[kRsRows];
+#pragma unroll
+      for (int u = 0; u < kRsRows; ++u) xv[u] = id[u] >= 0 ? a.X[(size_t)id[u] * a.d_pad + k] : 0.f;
+#pragma unroll
+      for (int u = 0; u < kRsRows; ++u) {
+        p[u] = fmaf(v, xv[u], p[u]);
+        m[u] = fmaf(fabsf(v), fabsf(xv[u]), m[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRsRows; ++u) {
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        p[u] += __shfl_xor_sync(0xFFFFFFFFu, p[u], off);
+        m[u] += __shfl_xor_sync(0xFFFFFFFFu, m[u], off);
+      }
+      if (id[u] >= 0) {
+        if (lane == 0) a.keys[(size_t)q * a.c_stride + i0 + u] = make_key(p[u], (uint32_t)id[u]);
+        mx = max(mx, __float_as_uint(m[u]));  // non-negative floats order as their bits
+      }
+    }
+  }
+  if (lane == 0 && mx != 0u) atomicMax(a.gmax + q, mx);
+}
+
 
 struct TieShared {
   double s[kMaxTie];
@@ -358,26 +408,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
     ts.gmax_bits = 0u;
   }
   __syncthreads();
-  // 1. FP32 scores, one warp per candidate (lane-strided partial sums, tree reduction)
-  for (int i = warp; i < n; i += nw) {
-    const int32_t id = cid[i];
-    const float *x = a.X + (size_t)id * a.d_pad;
-    float p = 0.f, m = 0.f;
-    for (int k = lane; k < a.d_pad; k += 32) {
-      const float v = qv[k], xv = x[k];
-      p = fmaf(v, xv, p);
-      m = fmaf(fabsf(v), fabsf(xv), m);
-    }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      p += __shfl_xor_sync(0xFFFFFFFFu, p, off);
-      m += __shfl_xor_sync(0xFFFFFFFFu, m, off);
-    }
-    if (lane == 0) {
-      keys[i] = make_key(p, (uint32_t)id);
-      atomicMax(&ts.gmax_bits, __float_as_uint(m));  // non-negative floats order as their bits
-    }
-  }
+  // 1. the candidates' FP32 keys, computed by the scoring launch
+  for (int i = tid; i < n; i += blockDim.x) keys[i] = __ldcg(a.keys + (size_t)q * a.c_stride + i);
+  if (tid == 0) ts.gmax_bits = __ldcg(a.gmax + q);
   __syncthreads();
   int n_tie = 0, n_above = 0;
   float s_above_last = INFINITY;
@@ -510,6 +543,9 @@ cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s) {
 
 cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
+  k_rescore_scores<<<dim3((unsigned)B, (unsigned)kRsSplit), kRsThreads, 0, s>>>(a);
+  const cudaError_t e0 = cudaGetLastError();
+  if (e0 != cudaSuccess) return e0;
   const size_t smem = (size_t)2 * kMaxK * sizeof(uint64_t);
   cudaError_t e = cudaFuncSetAttribute(k_rescore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
