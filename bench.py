@@ -226,11 +226,13 @@ def peaks():
 
 
 def scan_plan(args):
-    """The scan kernel the runtime picks for this batch and the queries one launch of it serves
-    (tensor-core tiles from 16 queries up, 64 per launch at d <= 128 and 32 above; SIMT
-    matrix-vector scan below that, 8 per launch)."""
+    """The scan kernel a search ran and the queries one launch of it serves (tensor-core tiles: 64 per
+    launch at d <= 128 and 32 above; SIMT matrix-vector scan: 8 per launch).  The plan is the one the
+    library reported for the timed steps (args.plan_used); before that, the requested plan, with "auto"
+    read as the batch-size rule."""
     d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
-    plan = args.plan if args.plan != "auto" else ("tc" if args.batch >= 16 else "gemv")
+    plan = getattr(args, "plan_used", None) or (args.plan if args.plan != "auto" else
+                                                 ("tc" if args.batch >= 16 else "gemv"))
     if plan == "tc" and args.dtype != "f32" and d_pad < 64:
         plan = "gemv"  # low-precision rows reach the tensor cores from 64 values up
     if plan == "tc":
@@ -412,6 +414,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
     ms = ev0.elapsed_time(ev1)
+    args.plan_used = probes[0].plan if probes[0].plan in ("gemv", "tc") else None
     step_ms = []
     lr.lr_index_sync(idx)
     ms = max_over_ranks(ms, world)

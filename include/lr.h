@@ -153,6 +153,8 @@ typedef struct lr_search_stats {
   void *scan_stop;       /* main scan launches, and right after them                */
   int32_t *n_scan_launches; /* host, 1 value: launches between scan_start/stop     */
   int32_t *rescore_ties; /* [B] precision form: candidates re-ranked in FP64         */
+  int32_t *plan_used;    /* host, 1 value: the scan plan the call ran (LR_PLAN_GEMV  */
+                         /* or LR_PLAN_TC; LR_PLAN_AUTO picks by the estimated bytes) */
 } lr_search_stats;
 
 /* Build an index (allocates every device buffer it will ever use: appendix

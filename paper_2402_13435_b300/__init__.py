@@ -58,7 +58,7 @@ class lr_search_opts(ctypes.Structure):
 class lr_search_stats(ctypes.Structure):
     _fields_ = [("pass_count", ctypes.c_void_p), ("cand_count", ctypes.c_void_p), ("fallback", ctypes.c_void_p),
                 ("n_launches", ctypes.c_void_p), ("scan_start", ctypes.c_void_p), ("scan_stop", ctypes.c_void_p),
-                ("n_scan_launches", ctypes.c_void_p), ("rescore_ties", ctypes.c_void_p)]
+                ("n_scan_launches", ctypes.c_void_p), ("rescore_ties", ctypes.c_void_p), ("plan_used", ctypes.c_void_p)]
 
 
 def _load():
@@ -220,6 +220,7 @@ class Probe:
         self.start, self.stop = start, stop
         self._n = np.zeros(1, dtype=np.int32)
         self._ns = np.zeros(1, dtype=np.int32)
+        self._plan = np.zeros(1, dtype=np.int32)
 
     @property
     def n_launches(self) -> int:
@@ -229,10 +230,16 @@ class Probe:
     def n_scan_launches(self) -> int:
         return int(self._ns[0])
 
+    @property
+    def plan(self) -> str:
+        """The scan plan the call ran: "gemv" or "tc"."""
+        return {v: k for k, v in _PLAN.items()}.get(int(self._plan[0]), "auto")
+
     def c(self) -> lr_search_stats:
         return lr_search_stats(None, None, None, self._n.ctypes.data,
                                self.start.cuda_event if self.start is not None else None,
-                               self.stop.cuda_event if self.stop is not None else None, self._ns.ctypes.data)
+                               self.stop.cuda_event if self.stop is not None else None, self._ns.ctypes.data,
+                               None, self._plan.ctypes.data)
 
 
 def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out_count=None, plan: str = "auto",

@@ -148,6 +148,22 @@ __global__ void k_expand_postings(const int64_t *post_off, const uint32_t *post_
   for (int w = threadIdx.x; w < sw && w0 + w < n_words; w += blockDim.x) bm[w0 + w] = span_words[w];
 }
 
+// Jobs holding each term (popcount of its term-major bitmap): one block per term.
+__global__ void k_term_counts(const uint32_t *bitmaps, int64_t n_words, int64_t *out) {
+  const uint32_t *bm = bitmaps + (size_t)blockIdx.x * (size_t)n_words;
+  unsigned long long c = 0;
+  for (int64_t w = threadIdx.x; w < n_words; w += blockDim.x) c += (unsigned long long)__popc(bm[w]);
+  for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+  __shared__ unsigned long long s_c[32];
+  if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_c[i];
+    out[blockIdx.x] = (int64_t)t;
+  }
+}
+
 // One warp per query: copy into [B][d_pad] (zero padded), FP32-normalised for cosine.
 __global__ void k_prep_queries(const float *in, float *out, int B, int dim, int d_pad, int cosine, uint32_t *err) {
   const int lane = threadIdx.x & 31;
@@ -269,6 +285,12 @@ cudaError_t launch_expand_postings(const int64_t *post_off, const uint32_t *post
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_term_counts(const uint32_t *bitmaps, int n_terms, int64_t n_words, int64_t *out, cudaStream_t s) {
+  if (n_terms <= 0) return cudaSuccess;
+  k_term_counts<<<n_terms, 256, 0, s>>>(bitmaps, n_words, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim, int d_pad, int cosine,

@@ -244,6 +244,8 @@ cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim,
 cudaError_t launch_expand_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *spans,
                                    int n_spans, int span_log2, const int32_t *terms, int n_terms, uint32_t *bitmaps,
                                    int64_t n_words, int64_t n, cudaStream_t s);
+// Jobs holding each of n_terms term-major bitmaps (popcount), int64 per term.
+cudaError_t launch_term_counts(const uint32_t *bitmaps, int n_terms, int64_t n_words, int64_t *out, cudaStream_t s);
 cudaError_t launch_scatter_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *terms,
                                     int n_terms, uint32_t *bitmaps, int64_t n_words, int64_t n, uint32_t *err,
                                     cudaStream_t s);

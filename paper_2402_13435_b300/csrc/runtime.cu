@@ -105,6 +105,7 @@ struct lr_index {
   uint32_t *dense_bm = nullptr;
   int n_dense = 0;
   std::vector<int32_t> term_dense;  // [vocab] dense bitmap index or -1
+  std::vector<double> term_frac;    // [vocab] fraction of the jobs holding each term (plan choice)
   bool has_postings = false;
   std::vector<int64_t> post_off_h;
   int64_t *post_off_d = nullptr;
@@ -627,10 +628,23 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
     CK2(launch_bitsets_to_termmajor(bits, ix->n, ix->vocab, ix->dense_bm, ix->n_words, s));
     CK2(cudaStreamSynchronize(s));
     if (tmpb) cudaFree(tmpb);
+    {  // document frequencies for the plan choice
+      int64_t *dfd = nullptr;
+      CK2(cudaMalloc(&dfd, sizeof(int64_t) * (size_t)ix->vocab));
+      std::vector<int64_t> df(ix->vocab);
+      CK2(launch_term_counts(ix->dense_bm, ix->vocab, ix->n_words, dfd, s));
+      CK2(cudaMemcpyAsync(df.data(), dfd, sizeof(int64_t) * (size_t)ix->vocab, cudaMemcpyDeviceToHost, s));
+      CK2(cudaStreamSynchronize(s));
+      cudaFree(dfd);
+      ix->term_frac.resize(ix->vocab);
+      for (int t = 0; t < ix->vocab; ++t) ix->term_frac[t] = (double)df[t] / (double)ix->n;
+    }
   } else {
     ix->has_postings = true;
     ix->post_off_h.assign(d->post_off, d->post_off + ix->vocab + 1);
     const std::vector<int64_t> &po = ix->post_off_h;
+    ix->term_frac.resize(ix->vocab);
+    for (int t = 0; t < ix->vocab; ++t) ix->term_frac[t] = (double)(po[t + 1] - po[t]) / (double)ix->n;
     if (po[0] != 0) return cleanup(fail(LR_ERR_INVALID, "post_off[0] must be 0"));
     for (int t = 0; t < ix->vocab; ++t)
       if (po[t + 1] < po[t]) return cleanup(fail(LR_ERR_INVALID, "post_off must be non-decreasing"));
@@ -732,6 +746,48 @@ struct Compiled {
   std::vector<int32_t> sparse_terms;  // distinct posting-list terms of the batch
   size_t off_k = 0, off_kfin = 0, off_rank = 0, off_sparse = 0, bytes = 0;
 };
+
+// Scan plan for LR_PLAN_AUTO.  Each filter's pass rate is estimated from its
+// terms' document frequencies as if terms were independent,
+//     s_q = prod_c (1 - prod_{t in c} (1 - df_t / n)),
+// and the union of a launch's queries as 1 - prod_q (1 - s_q).  The tensor-core
+// scan reads every 128-row tile holding a passing row of its (up to 64)
+// queries, the GEMV scan every passing row of its (up to 8), so the expected
+// bytes are  sum over 64-query launches of 1 - (1 - u)^128  and  sum over
+// 8-query launches of u; each is divided by the plan's measured fraction of
+// the HBM roofline (0.82 and 0.53 at 10M x 128) and the cheaper plan runs.
+// Without term statistics the batch size decides (>= 16 queries: tensor cores).
+int choose_plan(const lr_index *ix, const lr_filters *f, int B, bool tc_ok) {
+  if (!tc_ok) return LR_PLAN_GEMV;
+  const int by_size = B >= kTcMinBatch ? LR_PLAN_TC : LR_PLAN_GEMV;
+  // malformed filters are reported by the filter compiler; decide by size then
+  if (ix->term_frac.empty() || !f || !f->q_off || f->q_off[0] != 0) return by_size;
+  for (int b = 0; b < B; ++b)
+    if (f->q_off[b + 1] < f->q_off[b]) return by_size;
+  if (f->q_off[B] > 0 && (!f->c_off || !f->terms || f->c_off[0] != 0)) return by_size;
+  for (int c = 0; c < f->q_off[B]; ++c)
+    if (f->c_off[c + 1] <= f->c_off[c]) return by_size;
+  std::vector<double> s(B, 1.0);
+  for (int b = 0; b < B; ++b) {
+    for (int c = f->q_off[b]; c < f->q_off[b + 1]; ++c) {
+      double none = 1.0;
+      for (int i = f->c_off[c]; i < f->c_off[c + 1]; ++i) {
+        const uint32_t t = f->terms[i];
+        none *= 1.0 - (t < (uint32_t)ix->vocab ? ix->term_frac[t] : 0.0);
+      }
+      s[b] *= 1.0 - none;
+    }
+  }
+  auto union_of = [&](int b0, int b1) {
+    double none = 1.0;
+    for (int b = b0; b < b1; ++b) none *= 1.0 - s[b];
+    return 1.0 - none;
+  };
+  double tc = 0.0, gemv = 0.0;
+  for (int b0 = 0; b0 < B; b0 += kTcMaxQ) tc += 1.0 - std::pow(1.0 - union_of(b0, std::min(B, b0 + kTcMaxQ)), 128.0);
+  for (int b0 = 0; b0 < B; b0 += kGemvMaxQ) gemv += union_of(b0, std::min(B, b0 + kGemvMaxQ));
+  return tc / 0.82 < gemv / 0.53 ? LR_PLAN_TC : LR_PLAN_GEMV;
+}
 
 // The batch's posting-list terms -> workspace bitmaps (step A1): a dense write
 // of every word when the index has a span table, else clear + scatter.
@@ -889,7 +945,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   int plan = o.plan;
   const bool lowp = ix->elem != kElemF32;
   const bool tc_ok = lowp ? ix->have_tmap_q : ix->have_tmap;
-  if (plan == LR_PLAN_AUTO) plan = (B >= kTcMinBatch && tc_ok) ? LR_PLAN_TC : LR_PLAN_GEMV;
+  if (plan == LR_PLAN_AUTO) plan = choose_plan(ix, f, B, tc_ok);
   if (plan == LR_PLAN_TC && !tc_ok)
     return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable for this index (no TMA descriptor; "
                                     "low-precision rows need dim > 32)");
@@ -1146,6 +1202,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (stats) {
     if (stats->n_launches) *stats->n_launches = n_launch;
     if (stats->n_scan_launches) *stats->n_scan_launches = n_scan;
+    if (stats->plan_used) *stats->plan_used = plan;
     struct { void *dst; const void *src; size_t bytes; } cp[4] = {
         {stats->pass_count, ix->pass, sizeof(int64_t) * B},
         {stats->cand_count, ix->o_cand, sizeof(int32_t) * B},

@@ -30,7 +30,7 @@ def test_noalloc_matches_lr_search_on_two_calls_in_a_row():
         f = datagen.filters(seed, B, V, 1.1) if filtered else datagen.Filters.from_lists([[]] * B)
         Q = datagen.query_embeddings(seed, B, d)
         Qd = torch.from_numpy(Q).cuda()
-        ref_ids, ref_sc, ref_cnt = lr.lr_search(idx, Qd, f, K)
+        ref_ids, ref_sc, ref_cnt = lr.lr_search(idx, Qd, f, K, plan="gemv")  # the scan it shares
         bm = None
         if filtered:
             _, rows = lr.lr_filter_count(idx, f, bitmap=True)
