@@ -747,27 +747,18 @@ struct Compiled {
   size_t off_k = 0, off_kfin = 0, off_rank = 0, off_sparse = 0, bytes = 0;
 };
 
-// Scan plan for LR_PLAN_AUTO.  Each filter's pass rate is estimated from its
-// terms' document frequencies as if terms were independent,
-//     s_q = prod_c (1 - prod_{t in c} (1 - df_t / n)),
-// and the union of a launch's queries as 1 - prod_q (1 - s_q).  The tensor-core
-// scan reads every 128-row tile holding a passing row of its (up to 64)
-// queries, the GEMV scan every passing row of its (up to 8), so the expected
-// bytes are  sum over 64-query launches of 1 - (1 - u)^128  and  sum over
-// 8-query launches of u; each is divided by the plan's measured fraction of
-// the HBM roofline (0.82 and 0.53 at 10M x 128) and the cheaper plan runs.
-// Without term statistics the batch size decides (>= 16 queries: tensor cores).
-int choose_plan(const lr_index *ix, const lr_filters *f, int B, bool tc_ok) {
-  if (!tc_ok) return LR_PLAN_GEMV;
-  const int by_size = B >= kTcMinBatch ? LR_PLAN_TC : LR_PLAN_GEMV;
-  // malformed filters are reported by the filter compiler; decide by size then
-  if (ix->term_frac.empty() || !f || !f->q_off || f->q_off[0] != 0) return by_size;
+// Estimated pass rate of every filter of the batch (terms independent):
+//     s_q = prod_c (1 - prod_{t in c} (1 - df_t / n)).
+// false when the index has no term statistics or the filters are malformed
+// (which the filter compiler reports).
+bool estimate_pass_rates(const lr_index *ix, const lr_filters *f, int B, std::vector<double> &s) {
+  if (ix->term_frac.empty() || !f || !f->q_off || f->q_off[0] != 0) return false;
   for (int b = 0; b < B; ++b)
-    if (f->q_off[b + 1] < f->q_off[b]) return by_size;
-  if (f->q_off[B] > 0 && (!f->c_off || !f->terms || f->c_off[0] != 0)) return by_size;
+    if (f->q_off[b + 1] < f->q_off[b]) return false;
+  if (f->q_off[B] > 0 && (!f->c_off || !f->terms || f->c_off[0] != 0)) return false;
   for (int c = 0; c < f->q_off[B]; ++c)
-    if (f->c_off[c + 1] <= f->c_off[c]) return by_size;
-  std::vector<double> s(B, 1.0);
+    if (f->c_off[c + 1] <= f->c_off[c]) return false;
+  s.assign(B, 1.0);
   for (int b = 0; b < B; ++b) {
     for (int c = f->q_off[b]; c < f->q_off[b + 1]; ++c) {
       double none = 1.0;
@@ -778,6 +769,20 @@ int choose_plan(const lr_index *ix, const lr_filters *f, int B, bool tc_ok) {
       s[b] *= 1.0 - none;
     }
   }
+  return true;
+}
+
+// Scan plan for LR_PLAN_AUTO from the estimated pass rates s_q: the union of a
+// launch's queries is 1 - prod_q (1 - s_q).  The tensor-core scan reads every
+// 128-row tile holding a passing row of its (up to 64) queries, the GEMV scan
+// every passing row of its (up to 8), so the expected bytes are  sum over
+// 64-query launches of 1 - (1 - u)^128  and  sum over 8-query launches of u;
+// each is divided by the plan's measured fraction of the HBM roofline (0.82
+// and 0.53 at 10M x 128) and the cheaper plan runs.  Without estimates the
+// batch size decides (>= 16 queries: tensor cores).
+int choose_plan(int B, bool tc_ok, bool have_est, const std::vector<double> &s) {
+  if (!tc_ok) return LR_PLAN_GEMV;
+  if (!have_est) return B >= kTcMinBatch ? LR_PLAN_TC : LR_PLAN_GEMV;
   auto union_of = [&](int b0, int b1) {
     double none = 1.0;
     for (int b = b0; b < b1; ++b) none *= 1.0 - s[b];
@@ -945,7 +950,9 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   int plan = o.plan;
   const bool lowp = ix->elem != kElemF32;
   const bool tc_ok = lowp ? ix->have_tmap_q : ix->have_tmap;
-  if (plan == LR_PLAN_AUTO) plan = choose_plan(ix, f, B, tc_ok);
+  std::vector<double> est;  // estimated pass rate per filter
+  const bool have_est = estimate_pass_rates(ix, f, B, est);
+  if (plan == LR_PLAN_AUTO) plan = choose_plan(B, tc_ok, have_est, est);
   if (plan == LR_PLAN_TC && !tc_ok)
     return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable for this index (no TMA descriptor; "
                                     "low-precision rows need dim > 32)");
@@ -971,9 +978,21 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (sp.stride > 0 && sp.sampled_rows > ix->samp_cap)
     return fail(LR_ERR_WORKSPACE, "sample stride too small for the sample workspace");
   int32_t *rk = (int32_t *)(stage + C.off_rank);
-  for (int b = 0; b < B; ++b) rk[b] = sample_rank(sp, ks[b]);
+  // A filter expected to pass fewer than a quarter of what the final
+  // selection holds in shared memory (and of the candidate buffer) collects
+  // every passing key (rank 0: threshold 0) and needs no sample; when no filter
+  // needs one the sample is skipped.  A wrong estimate overflows the buffer
+  // and the exact fallback still gives the exact top K.  (Only with the
+  // automatic stride: an explicit one always runs the sample.)
   int64_t cap = ix->cand_cap;
   if (o.cand_cap > 0) cap = std::min<int64_t>(cap, std::max<int64_t>(o.cand_cap, 1));
+  const double direct = (double)std::min<int64_t>(cap, kThrScratchKeys);
+  bool need_sample = false;
+  for (int b = 0; b < B; ++b) {
+    const bool small = o.sample_stride == 0 && have_est && est[b] * (double)ix->n * 4.0 < direct;
+    rk[b] = small ? 0 : sample_rank(sp, ks[b]);
+    need_sample |= rk[b] > 0;
+  }
 
   // ---- device work
   int32_t n_launch = 0, n_scan = 0;
@@ -1072,7 +1091,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     LR_CK(cudaEventRecord(ix->ev_join, ix->aux));
   }
   // 1. threshold sample
-  if (sp.stride > 0) {
+  if (sp.stride > 0 && need_sample) {
     for (const SubBatch &sb : C.subs) {
       ScanArgs a = scan_args(sb);
       a.g_begin = sp.stride / 2;
