@@ -128,7 +128,7 @@ struct lr_index {
   uint64_t *tau = nullptr, *prefix = nullptr;
   unsigned long long *pass = nullptr;
   uint32_t *cnt = nullptr, *ovf = nullptr, *scnt = nullptr, *sovf = nullptr, *flag = nullptr;
-  int32_t *krem = nullptr, *kq = nullptr, *rank = nullptr;
+  int32_t *krem = nullptr;
   uint32_t *n_flag = nullptr, *done_ctr = nullptr, *work_ctr = nullptr, *err = nullptr;
   uint32_t *hist = nullptr;
   uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
@@ -147,7 +147,7 @@ struct lr_index {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t *o_ids = nullptr, *o_cnt = nullptr, *o_cand = nullptr, *o_fb = nullptr;
-  int32_t *c_ids = nullptr, *c_cnt = nullptr, *kfin = nullptr, *o_ties = nullptr;  // precision form
+  int32_t *c_ids = nullptr, *c_cnt = nullptr, *o_ties = nullptr;  // precision form
   uint64_t *rs_keys = nullptr;  // precision form: FP32 keys of the candidates [B][max_kq]
   uint32_t *rs_gmax = nullptr;  // and the per-query FP32 rounding bound's magnitude [B]
   float *c_sc = nullptr;
@@ -364,8 +364,6 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_state_end = cv.take<char>(0);
   const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
   const size_t o_err = cv.take<uint32_t>(1);
-  const size_t o_kq = cv.take<int32_t>(B);
-  const size_t o_rank = cv.take<int32_t>(B);
   const size_t o_hist = cv.take<uint32_t>((size_t)B * kFbBins);
   const size_t o_samp = cv.take<uint64_t>((size_t)B * ix->samp_cap);
   const size_t o_cand = cv.take<uint64_t>((size_t)B * ix->cand_cap);
@@ -386,7 +384,6 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_cids = cv.take<int32_t>(lowp ? (size_t)B * ix->max_kq : 0);
   const size_t o_csc = cv.take<float>(lowp ? (size_t)B * ix->max_kq : 0);
   const size_t o_ccnt = cv.take<int32_t>(lowp ? B : 0);
-  const size_t o_kfin = cv.take<int32_t>(lowp ? B : 0);
   const size_t o_ties = cv.take<int32_t>(lowp ? B : 0);
   const size_t o_rs_keys = cv.take<uint64_t>(lowp ? (size_t)B * ix->max_kq : 0);
   const size_t o_filt = cv.take<char>(ix->filt_bytes);
@@ -416,8 +413,6 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->done_ctr = (uint32_t *)(w + o_done);
   ix->work_ctr = ix->done_ctr + 1;
   ix->err = (uint32_t *)(w + o_err);
-  ix->kq = (int32_t *)(w + o_kq);
-  ix->rank = (int32_t *)(w + o_rank);
   ix->hist = (uint32_t *)(w + o_hist);
   ix->samp_buf = (uint64_t *)(w + o_samp);
   ix->cand_buf = (uint64_t *)(w + o_cand);
@@ -439,7 +434,6 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
     ix->c_ids = (int32_t *)(w + o_cids);
     ix->c_sc = (float *)(w + o_csc);
     ix->c_cnt = (int32_t *)(w + o_ccnt);
-    ix->kfin = (int32_t *)(w + o_kfin);
     ix->o_ties = (int32_t *)(w + o_ties);
     ix->rs_keys = (uint64_t *)(w + o_rs_keys);
     ix->rs_gmax = (uint32_t *)(w + o_rs_gmax);
@@ -1000,10 +994,11 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   LR_CK(cudaEventRecord(ix->filt_ev[turn], s));
   ix->filt_ev_live[turn] = true;
   LR_CK(cudaMemsetAsync(ix->state, 0, ix->state_bytes, s));
-  LR_CK(cudaMemcpyAsync(ix->kq, ix->filt_d + C.off_k, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
-  LR_CK(cudaMemcpyAsync(ix->rank, ix->filt_d + C.off_rank, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
-  if (lowp)
-    LR_CK(cudaMemcpyAsync(ix->kfin, ix->filt_d + C.off_kfin, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  // per-query K (scan and selection), final K and sample rank: read by the
+  // kernels where they were uploaded
+  const int32_t *kq_d = (const int32_t *)(ix->filt_d + C.off_k);
+  const int32_t *kfin_d = (const int32_t *)(ix->filt_d + C.off_kfin);
+  const int32_t *rank_d = (const int32_t *)(ix->filt_d + C.off_rank);
   const float *qsrc = q;
   if (!is_device_ptr(q)) {
     LR_CK(cudaMemcpyAsync(ix->q_raw, q, sizeof(float) * (size_t)B * ix->dim, cudaMemcpyHostToDevice, s));
@@ -1112,7 +1107,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     t.cap = ix->samp_cap;
     t.cnt = ix->scnt;
     t.overflow = ix->sovf;
-    t.rank = ix->rank;
+    t.rank = rank_d;
     t.tau = ix->tau;
     t.scratch = ix->thr_scratch;
     t.slice_n = ix->thr_slice_n;
@@ -1138,7 +1133,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.cap = cap;
   fa.cnt = ix->cnt;
   fa.overflow = ix->ovf;
-  fa.k = ix->kq;
+  fa.k = kq_d;
   fa.pass_cnt = ix->pass;
   fa.k_stride = lowp ? ix->max_kq : k_all;
   fa.out_ids = lowp ? ix->c_ids : dev_out ? out_ids : ix->o_ids;
@@ -1154,7 +1149,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.err = ix->err;
   LR_LAUNCH(launch_select(fa, B, s));
   // 4. exact fallback for flagged queries (each launch returns at once when none is flagged)
-  LR_LAUNCH(launch_fallback_prepare(ix->pass, ix->kq, ix->flag, ix->prefix, ix->krem, ix->cnt, ix->ovf, ix->hist, B,
+  LR_LAUNCH(launch_fallback_prepare(ix->pass, kq_d, ix->flag, ix->prefix, ix->krem, ix->cnt, ix->ovf, ix->hist, B,
                                 ix->n_flag, s));
   for (int p = 0; p < kFbPasses; ++p) {
     for (const SubBatch &sb : C.subs) {
@@ -1198,7 +1193,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     ra.cid = ix->c_ids;
     ra.ccnt = ix->c_cnt;
     ra.c_stride = ix->max_kq;
-    ra.k = ix->kfin;
+    ra.k = kfin_d;
     ra.k_stride = k_all;
     ra.out_ids = dev_out ? out_ids : ix->o_ids;
     ra.out_scores = dev_out ? out_scores : ix->o_sc;

@@ -21,14 +21,24 @@ namespace {
 constexpr int kSelThreads = 512;
 constexpr int kSmemKeys = 8192;  // candidate keys staged in shared memory when they fit
 
+constexpr uint32_t kFew = 32;  // a bin this small is finished by one warp
+
 struct SelShared {
   uint32_t hist[256];
   uint32_t digit;
   uint32_t krem;
+  uint32_t bin;  // keys in the chosen bin
   uint32_t n_out;
+  uint32_t n_few;
+  uint64_t result;
+  uint64_t few[kFew];
 };
 
 // r-th largest (1-based) of n distinct keys; keys may be in shared or global memory.
+// Radix select on 8-bit digits from the top; as soon as the bin that holds the
+// r-th largest key has at most kFew keys, those keys are gathered and one warp
+// finds the one with exactly krem - 1 of them above it, instead of running the
+// remaining digit passes.
 __device__ uint64_t block_kth(const uint64_t *keys, int64_t n, uint32_t r, SelShared &sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t prefix = 0;
@@ -55,25 +65,67 @@ __device__ uint64_t block_kth(const uint64_t *keys, int64_t n, uint32_t r, SelSh
       const uint32_t excl = incl - cs;
       const unsigned hit = __ballot_sync(0xFFFFFFFFu, excl < krem && krem <= incl);
       if (hit == 0u) {
-        if (lane == 0) { sh.digit = 0u; sh.krem = 1u; }  // unreachable for r <= n
+        if (lane == 0) { sh.digit = 0u; sh.krem = 1u; sh.bin = 0xFFFFFFFFu; }  // unreachable for r <= n
       } else if (lane == __ffs(hit) - 1) {
-        uint32_t cum = excl;
-        int d = 255 - 8 * lane;
+        uint32_t cum = excl, bin = c[7];
+        int d = 255 - 8 * lane - 7;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          if (cum + c[j] >= krem) { d = 255 - 8 * lane - j; break; }
+          if (cum + c[j] >= krem) { d = 255 - 8 * lane - j; bin = c[j]; break; }
           cum += c[j];
         }
         sh.digit = (uint32_t)d;
         sh.krem = krem - cum;
+        sh.bin = bin;
       }
     }
     __syncthreads();
     prefix |= (uint64_t)sh.digit << shift;
     krem = sh.krem;
+    const uint32_t bin = sh.bin;
     __syncthreads();
+    if (shift > 0 && bin <= kFew) {  // the rest is decided inside one small bin
+      if (tid == 0) {
+        sh.n_few = 0u;
+        sh.result = prefix;
+      }
+      __syncthreads();
+      for (int64_t i = tid; i < n; i += blockDim.x) {
+        const uint64_t key = keys[i];
+        if ((key >> shift) == (prefix >> shift)) {
+          const uint32_t pos = atomicAdd(&sh.n_few, 1u);
+          if (pos < kFew) sh.few[pos] = key;
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t m = sh.n_few < kFew ? sh.n_few : kFew;
+        const uint64_t v = (uint32_t)lane < m ? sh.few[lane] : 0ull;
+        uint32_t above = 0;
+        for (uint32_t j = 0; j < m; ++j) above += __shfl_sync(0xFFFFFFFFu, v, (int)j) > v ? 1u : 0u;
+        if ((uint32_t)lane < m && above == krem - 1u) sh.result = v;
+      }
+      __syncthreads();
+      return sh.result;
+    }
   }
   return prefix;
+}
+
+// Append `key` at dst[*cnt] (stored while below cap) when `take`: the taking
+// lanes of a warp claim their places with one shared atomic.  Called by whole,
+// converged warps.
+__device__ __forceinline__ void warp_append(bool take, uint64_t key, uint64_t *dst, uint32_t cap, uint32_t *cnt) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == lead) base = atomicAdd(cnt, (uint32_t)__popc(m));
+  base = __shfl_sync(0xFFFFFFFFu, base, lead);
+  if (take) {
+    const uint32_t pos = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+    if (pos < cap) dst[pos] = key;
+  }
 }
 
 constexpr int kPilot = 4096;  // keys of the strided pilot sample (kPilot <= kSmemKeys)
@@ -101,7 +153,8 @@ __device__ uint64_t kth_large(const uint64_t *g, int64_t n, uint32_t r, uint64_t
   if (tid == 0) sh.n_out = 0u;
   __syncthreads();
   constexpr int kU = 16;  // loads in flight per thread (64 KB per CTA)
-  for (int64_t b = tid; b < n; b += (int64_t)kU * blockDim.x) {
+  for (int64_t b0 = 0; b0 < n; b0 += (int64_t)kU * blockDim.x) {  // whole warps every trip
+    const int64_t b = b0 + tid;
     uint64_t v[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -109,12 +162,8 @@ __device__ uint64_t kth_large(const uint64_t *g, int64_t n, uint32_t r, uint64_t
       v[u] = i < n ? __ldcg(g + i) : 0ull;
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      if (b + (int64_t)u * blockDim.x < n && v[u] >= t0) {
-        const uint32_t pos = atomicAdd(&sh.n_out, 1u);
-        if (pos < (uint32_t)kSmemKeys) sbuf[pos] = v[u];
-      }
-    }
+    for (int u = 0; u < kU; ++u)
+      warp_append(b + (int64_t)u * blockDim.x < n && v[u] >= t0, v[u], sbuf, (uint32_t)kSmemKeys, &sh.n_out);
   }
   __syncthreads();
   const uint32_t c = sh.n_out;
@@ -135,6 +184,68 @@ __device__ void bitonic_desc(uint64_t *s, int P) {
       }
       __syncthreads();
     }
+  }
+}
+
+// Compare-exchange of the key at index i (this lane) with the one `st` lanes
+// away, inside bitonic merge step `size`; st < 32.
+__device__ __forceinline__ void cx_lanes(uint64_t &e, int i, int st, int size, int lane) {
+  const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, e, st);
+  const bool keep_max = ((lane & st) == 0) == ((i & size) == 0);
+  e = keep_max ? (e > y ? e : y) : (e < y ? e : y);
+}
+
+// Strides min(size/2, 32) .. 1 of bitonic merge step `size` on one 64-key chunk
+// held by a warp: lane l holds the keys at indices i0 = base + l and i0 + 32.
+__device__ __forceinline__ void merge_in_warp(uint64_t &e0, uint64_t &e1, int i0, int size, int lane) {
+  int st = size / 2;
+  if (size >= 64) {
+    const bool desc = (i0 & size) == 0;
+    const uint64_t hi = e0 > e1 ? e0 : e1, lo = e0 > e1 ? e1 : e0;
+    e0 = desc ? hi : lo;
+    e1 = desc ? lo : hi;
+    st = 16;
+  }
+  for (; st > 0; st >>= 1) {
+    cx_lanes(e0, i0, st, size, lane);
+    cx_lanes(e1, i0 + 32, st, size, lane);
+  }
+}
+
+// Descending bitonic sort of s[0, P), P a power of two of at least 64.  Merge
+// strides of 64 and more go through shared memory with one barrier each; the
+// strides below run in registers, one warp per 64-key chunk, so a sort of P
+// keys takes log2(P / 64) (log2(P / 64) + 1) / 2 + log2(P / 32) barriers.
+__device__ void bitonic_desc_chunks(uint64_t *s, int P) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int chunks = P / 64;
+  for (int ch = warp; ch < chunks; ch += nw) {
+    const int i0 = ch * 64 + lane;
+    uint64_t e0 = s[i0], e1 = s[i0 + 32];
+    for (int size = 2; size <= 64; size <<= 1) merge_in_warp(e0, e1, i0, size, lane);
+    s[i0] = e0;
+    s[i0 + 32] = e1;
+  }
+  __syncthreads();
+  for (int size = 128; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride >= 64; stride >>= 1) {
+      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+        const int pos = 2 * i - (i & (stride - 1));
+        const int par = pos + stride;
+        const bool desc = (pos & size) == 0;
+        const uint64_t x = s[pos], y = s[par];
+        if ((x < y) == desc) { s[pos] = y; s[par] = x; }
+      }
+      __syncthreads();
+    }
+    for (int ch = warp; ch < chunks; ch += nw) {
+      const int i0 = ch * 64 + lane;
+      uint64_t e0 = s[i0], e1 = s[i0 + 32];
+      merge_in_warp(e0, e1, i0, size, lane);
+      s[i0] = e0;
+      s[i0 + 32] = e1;
+    }
+    __syncthreads();
   }
 }
 
@@ -192,15 +303,18 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
     if (tid == 0) sh.n_out = 0u;
     for (int i = tid; i < P2; i += blockDim.x) sort[i] = 0ull;
     __syncthreads();
-    for (int64_t i = tid; i < n; i += blockDim.x) {
-      const uint64_t key = keys[i];
-      if (key >= kth) {
-        const uint32_t pos = atomicAdd(&sh.n_out, 1u);
-        if (pos < (uint32_t)P2) sort[pos] = key;
-      }
+    for (int64_t b = 0; b < n; b += blockDim.x) {  // whole warps every trip
+      const int64_t i = b + tid;
+      const uint64_t key = i < n ? keys[i] : 0ull;
+      warp_append(i < n && key >= kth, key, sort, (uint32_t)P2, &sh.n_out);
     }
     __syncthreads();
-    if (!a.unsorted) bitonic_desc(sort, P2);
+    if (!a.unsorted) {
+      if (P2 >= 64)
+        bitonic_desc_chunks(sort, P2);
+      else
+        bitonic_desc(sort, P2);
+    }
   }
   for (int i = tid; i < a.k_stride; i += blockDim.x) {
     if (i < kp) {
@@ -284,8 +398,11 @@ __global__ void __launch_bounds__(kSelThreads) k_threshold(const ThrArgs a) {
     const uint64_t kth = block_kth(sbuf, m, (uint32_t)r, sh);
     if (tid == 0) sh.n_out = 0u;
     __syncthreads();
-    for (int64_t i = tid; i < m; i += blockDim.x)
-      if (sbuf[i] >= kth) out[atomicAdd(&sh.n_out, 1u)] = sbuf[i];  // exactly r keys (keys are distinct)
+    for (int64_t b = 0; b < m; b += blockDim.x) {  // exactly r keys (keys are distinct)
+      const int64_t i = b + tid;
+      const uint64_t key = i < m ? sbuf[i] : 0ull;
+      warp_append(i < m && key >= kth, key, out, (uint32_t)r, &sh.n_out);
+    }
     kept = (uint32_t)r;
   }
   if (tid == 0) a.slice_n[(size_t)q * kThrSlices + p] = kept;
@@ -439,7 +556,12 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
     while (P2 < n_above) P2 <<= 1;
     for (int i = n_above + tid; i < P2; i += blockDim.x) sortb[i] = 0ull;
     __syncthreads();
-    if (n_above > 1) bitonic_desc(sortb, P2);
+    if (n_above > 1) {
+      if (P2 >= 64)
+        bitonic_desc_chunks(sortb, P2);
+      else
+        bitonic_desc(sortb, P2);
+    }
     for (int i = tid; i < n_above; i += blockDim.x) {
       ids[i] = (int32_t)key_id(sortb[i]);
       sc[i] = key_score((uint32_t)(sortb[i] >> 32));
