@@ -101,6 +101,7 @@ struct ScanArgs {
   uint64_t *prefix;              // [B] key bits fixed so far
   int32_t *krem;                 // [B] rank still to find below the prefix
   uint32_t *hist;                // [B][kFbBins]
+  uint64_t *tau_out;             // nullable: the last pass writes the selected key (the new tau)
   uint32_t *done_ctr;            // grid-completion counter (last CTA applies the digit step)
   uint32_t *work_ctr;            // dynamic work distribution (reset by the last CTA)
   int32_t hist_pass;             // 0 .. kFbPasses-1
@@ -121,8 +122,8 @@ struct SelectArgs {
   int32_t mode;                  // 0: threshold from a sample, 1: final top-K
   const uint64_t *buf;
   int64_t cap;
-  const uint32_t *cnt;
-  const uint32_t *overflow;
+  uint32_t *cnt;                 // reset with overflow for the queries a final launch flags
+  uint32_t *overflow;
   // threshold mode
   const int32_t *rank;           // [B] r: tau = r-th largest sample key (0 if fewer)
   uint64_t *tau;                 // [B]
@@ -135,6 +136,8 @@ struct SelectArgs {
   int32_t *out_count;            // nullable
   uint32_t *flag;                // [B] set when the candidate set cannot prove exactness
   uint32_t *n_flagged;
+  uint64_t *fb_prefix;           // [B] exact-fallback state, initialised for the queries flagged here
+  int32_t *fb_krem;              // [B]
   const uint32_t *only;          // nullable: process only queries with only[q] != 0
   const uint32_t *any;           // nullable: early exit when *any == 0
   int32_t *cand_count_out;       // nullable stats
@@ -255,11 +258,6 @@ cudaError_t launch_bitsets_to_termmajor(const uint64_t *bits, int64_t n, int voc
                                         cudaStream_t s);
 cudaError_t launch_filter_eval(const ScanArgs &a, unsigned long long *pass_cnt, uint32_t *out_bitmap,
                                int64_t out_words, int grid, cudaStream_t s);
-cudaError_t launch_fallback_prepare(const unsigned long long *pass_cnt, const int32_t *k, const uint32_t *flag,
-                                    uint64_t *prefix, int32_t *krem, uint32_t *cnt, uint32_t *overflow,
-                                    uint32_t *hist, int B, const uint32_t *any, cudaStream_t s);
-cudaError_t launch_fallback_finish(const uint64_t *prefix, const uint32_t *flag, uint64_t *tau, int B,
-                                   const uint32_t *any, cudaStream_t s);
 
 // ------------------------------------------------------------------ errors
 void set_error(const std::string &msg);

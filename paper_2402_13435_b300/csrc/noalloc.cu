@@ -239,10 +239,11 @@ extern "C" lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t d
   fa.out_count = out_count;
   fa.flag = flag;
   fa.n_flagged = nflag;
+  fa.fb_prefix = prefix;
+  fa.fb_krem = krem;
   fa.err = err;
   NA_CK(launch_select(fa, B, s));
   // exact fallback for queries whose candidate set cannot prove exactness
-  NA_CK(launch_fallback_prepare(pass, kq, flag, prefix, krem, cnt, ovf, hist, B, nflag, s));
   for (int p = 0; p < kFbPasses; ++p) {
     ScanArgs h = a;
     h.mode = kHist;
@@ -250,11 +251,11 @@ extern "C" lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t d
     h.prefix = prefix;
     h.krem = krem;
     h.hist = hist;
+    h.tau_out = tau;
     h.active = flag;
     h.any_active = nflag;
     NA_CK(launch_scan_gemv(h, nqt, vec, grid_for(n_groups), s));
   }
-  NA_CK(launch_fallback_finish(prefix, flag, tau, B, nflag, s));
   ScanArgs c = m;
   c.pass_cnt = nullptr;
   c.active = flag;

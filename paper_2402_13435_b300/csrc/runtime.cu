@@ -1141,6 +1141,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.out_count = lowp ? ix->c_cnt : dev_out ? out_count : ix->o_cnt;
   fa.flag = ix->flag;
   fa.n_flagged = ix->n_flag;
+  fa.fb_prefix = ix->prefix;
+  fa.fb_krem = ix->krem;
   fa.cand_count_out = ix->o_cand;
   fa.fallback_out = ix->o_fb;
   fa.fallback_round = 0;
@@ -1149,8 +1151,6 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.err = ix->err;
   LR_LAUNCH(launch_select(fa, B, s));
   // 4. exact fallback for flagged queries (each launch returns at once when none is flagged)
-  LR_LAUNCH(launch_fallback_prepare(ix->pass, kq_d, ix->flag, ix->prefix, ix->krem, ix->cnt, ix->ovf, ix->hist, B,
-                                ix->n_flag, s));
   for (int p = 0; p < kFbPasses; ++p) {
     for (const SubBatch &sb : C.subs) {
       ScanArgs a = scan_args(sb);
@@ -1159,12 +1159,12 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       a.prefix = ix->prefix;
       a.krem = ix->krem;
       a.hist = ix->hist;
+      a.tau_out = ix->tau;
       a.active = ix->flag;
       a.any_active = ix->n_flag;
       LR_LAUNCH(launch_scan(a, ix->n_groups, !reuse_list, reuse_list));
     }
   }
-  LR_LAUNCH(launch_fallback_finish(ix->prefix, ix->flag, ix->tau, B, ix->n_flag, s));
   for (const SubBatch &sb : C.subs) {
     ScanArgs a = scan_args(sb);
     a.tau = ix->tau;

@@ -106,7 +106,8 @@ __device__ __forceinline__ void eval_packed(const PackedCnf &p, const uint32_t *
 
 // Digit step of the exact fallback: for every participating query find the
 // digit whose bin holds the krem-th largest key, fix it in the prefix and clear
-// the histogram.  Runs in the last CTA of a kHist launch.
+// the histogram.  Runs in the last CTA of a kHist launch; after the last digit
+// (shift 0) the prefix is the selected key itself and becomes the query's tau.
 __device__ void hist_step(const ScanArgs &a, int top, int shift) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   const int nb = 1 << (top - shift);
@@ -117,6 +118,7 @@ __device__ void hist_step(const ScanArgs &a, int top, int shift) {
     uint32_t *h = a.hist + (size_t)gq * kFbBins;
     const uint32_t krem = (uint32_t)a.krem[gq];
     if (krem == 0u) {  // nothing passes this filter: no rank to find
+      if (shift == 0 && a.tau_out && lane == 0) a.tau_out[gq] = a.prefix[gq];
       for (int i = lane; i < nb; i += 32) h[i] = 0u;
       continue;
     }
@@ -143,6 +145,7 @@ __device__ void hist_step(const ScanArgs &a, int top, int shift) {
       }
       a.prefix[gq] |= (uint64_t)digit << shift;
       a.krem[gq] = (int32_t)(krem - cum);
+      if (shift == 0 && a.tau_out) a.tau_out[gq] = a.prefix[gq];
     }
     __syncwarp();
     for (int i = lane; i < nb; i += 32) h[i] = 0u;

@@ -284,8 +284,12 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   int32_t *ids = a.out_ids + (size_t)q * (size_t)a.k_stride;
   float *sc = a.out_scores + (size_t)q * (size_t)a.k_stride;
   if (a.fallback_round == 0 && (!exact || a.force_flag)) {
-    if (tid == 0) {
+    if (tid == 0) {  // hand the query to the exact fallback: no digit fixed, rank min(K, P), empty list
       a.flag[q] = 1u;
+      a.fb_prefix[q] = 0ull;
+      a.fb_krem[q] = kp;
+      a.cnt[q] = 0u;
+      a.overflow[q] = 0u;
       atomicAdd(a.n_flagged, 1u);
     }
     return;
@@ -622,27 +626,6 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
 
 // Fallback set-up: for flagged queries start the radix selection of the
 // min(K, #passing)-th key from an empty prefix and clear the candidate buffer.
-__global__ void k_fallback_prepare(const unsigned long long *pass_cnt, const int32_t *k, const uint32_t *flag,
-                                   uint64_t *prefix, int32_t *krem, uint32_t *cnt, uint32_t *overflow, int B,
-                                   const uint32_t *any) {
-  if (*reinterpret_cast<const volatile uint32_t *>(any) == 0u) return;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= B || flag[q] == 0u) return;
-  const unsigned long long P = pass_cnt[q];
-  prefix[q] = 0ull;
-  krem[q] = (int32_t)((unsigned long long)k[q] < P ? (unsigned long long)k[q] : P);
-  cnt[q] = 0u;
-  overflow[q] = 0u;
-}
-
-__global__ void k_fallback_finish(const uint64_t *prefix, const uint32_t *flag, uint64_t *tau, int B,
-                                  const uint32_t *any) {
-  if (*reinterpret_cast<const volatile uint32_t *>(any) == 0u) return;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= B || flag[q] == 0u) return;
-  tau[q] = prefix[q];
-}
-
 }  // namespace
 
 cudaError_t launch_threshold(const ThrArgs &a, int B, cudaStream_t s) {
@@ -672,19 +655,6 @@ cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_rescore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_rescore<<<B, kRsThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fallback_prepare(const unsigned long long *pass_cnt, const int32_t *k, const uint32_t *flag,
-                                    uint64_t *prefix, int32_t *krem, uint32_t *cnt, uint32_t *overflow,
-                                    uint32_t * /*hist*/, int B, const uint32_t *any, cudaStream_t s) {
-  k_fallback_prepare<<<(B + 127) / 128, 128, 0, s>>>(pass_cnt, k, flag, prefix, krem, cnt, overflow, B, any);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fallback_finish(const uint64_t *prefix, const uint32_t *flag, uint64_t *tau, int B,
-                                   const uint32_t *any, cudaStream_t s) {
-  k_fallback_finish<<<(B + 127) / 128, 128, 0, s>>>(prefix, flag, tau, B, any);
   return cudaGetLastError();
 }
 
