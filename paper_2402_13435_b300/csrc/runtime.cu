@@ -942,6 +942,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // scoring plan: SIMT matrix-vector scan for small batches, tensor-core tiles
   // (3xTF32) once a launch serves enough queries to be a real contraction
   int plan = o.plan;
+  if (plan != LR_PLAN_AUTO && plan != LR_PLAN_GEMV && plan != LR_PLAN_TC)
+    return fail(LR_ERR_INVALID, "plan must be LR_PLAN_AUTO, LR_PLAN_GEMV or LR_PLAN_TC");
   const bool lowp = ix->elem != kElemF32;
   const bool tc_ok = lowp ? ix->have_tmap_q : ix->have_tmap;
   std::vector<double> est;  // estimated pass rate per filter

@@ -275,3 +275,18 @@ def test_unsorted_postings_give_identical_results(lr, small):
         assert np.array_equal(a, b)
     ref_cnt, _ = oracle.filter(c.job_off, c.job_terms, c.n, f, want_matrix=True)
     assert np.array_equal(outs[0][0], ref_cnt)
+
+
+def test_unknown_plan_is_rejected(lr, small):
+    c = small
+    idx = lr.lr_index_create(c.X, c.V, bitsets=c.bitsets(), metric="cosine", max_batch=4, max_k=16)
+    qd = torch.from_numpy(datagen.query_embeddings(1, 2, c.d)).cuda()
+    out_i = torch.empty((2, 5), dtype=torch.int32, device="cuda")
+    out_s = torch.empty((2, 5), dtype=torch.float32, device="cuda")
+    fc = lr.Filters.of(Filters.from_lists([[], []])).c()
+    for plan in (3, -1):
+        opts = lr.lr_search_opts(plan=plan)
+        rc = lr._lib.lr_search_ex(lr.ctypes.c_void_p(idx.handle), lr._ptr(qd), 2, lr.ctypes.byref(fc), None, 5,
+                                  lr._ptr(out_i), lr._ptr(out_s), None, lr.ctypes.byref(opts), None, None)
+        assert rc == lr.LR_ERR_INVALID
+    lr.lr_index_destroy(idx)
