@@ -25,11 +25,16 @@
 //              with x_lo against q_hi, so accumulator columns [0, N) and
 //              [N, 2N) add up to the 3xTF32 product.  Four accumulator buffers
 //              when N <= 32 (two above), so the MMAs run ahead of the epilogue.
-//   warps 2-5, 10-13  converters, two sets of one warp per tensor-memory lane
-//              quarter, taking alternate chunks: each thread reads its row of a
-//              landed chunk, releases the raw stage at once, and writes x_hi
-//              and x_lo into tensor memory (tcgen05.st).  Raw stages therefore
-//              never wait on the tensor core.
+//              BF16 rows skip the converters: the MMA reads the landed stage
+//              from shared memory (kind::f16, 16-value K steps, x against the
+//              queries as a BF16 pair [q_hi ; q_lo]) and its commit frees the
+//              stage.
+//   warps 2-5, 10-13  converters (FP32 and FP8 rows), two sets of one warp per
+//              tensor-memory lane quarter, taking alternate chunks: each thread
+//              reads its row of a landed chunk, releases the raw stage at once,
+//              and writes x_hi and x_lo (FP8: the values, exact in TF32) into
+//              tensor memory (tcgen05.st).  Raw stages therefore never wait on
+//              the tensor core.
 //   warps 6-9 (and 14-17)  epilogue: read the accumulator (warp w owns lanes
 //              32*(w%4) ..), with the row masks of the tile read one tile
 //              ahead, test every passing (row, query) against the query's
@@ -40,6 +45,7 @@
 // loader lets issued copies land, the MMA warp waits for its MMAs, and the
 // tensor memory is freed before the CTA exits.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&raw_full[i], 1);
-      mbar_init(&raw_empty[i], 4);
+      mbar_init(&raw_empty[i], E == kElemBF16 ? 1 : 4);  // BF16: the MMAs' commit; else the converter warps
     }
     for (int i = 0; i < kABufs; ++i) {
       mbar_init(&a_full[i], 4);
@@ -177,8 +183,35 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     s_nlist = (int64_t)nl < a.tile_cap ? nl : (uint32_t)a.tile_cap;
   }
   // queries of the launch in the K-major 128-byte swizzle layout, split into
-  // hi/lo; each thread issues its loads of a round together, then stores
+  // hi/lo (TF32 for the TF32 MMA, BF16 for BF16 rows); each thread issues its
+  // loads of a round together, then stores
   constexpr int kQu = 8;
+  if constexpr (E == kElemBF16) {
+    // per 64-value chunk c: 2N rows of 128 bytes (q_hi rows 0..N-1, q_lo rows
+    // N..2N-1), 16-byte unit j of row r at unit j ^ (r % 8)
+    uint16_t *qb = reinterpret_cast<uint16_t *>(qop);
+    for (int i0 = 0; i0 < C * N * 64; i0 += kQu * kThreads) {
+      float v[kQu];
+#pragma unroll
+      for (int u = 0; u < kQu; ++u) {
+        const int i = i0 + u * kThreads + threadIdx.x;
+        const int c = i / (N * 64), rem = i % (N * 64), r = rem / 64, k = rem % 64;
+        v[u] = i < C * N * 64 && r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 64 + k] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kQu; ++u) {
+        const int i = i0 + u * kThreads + threadIdx.x;
+        if (i >= C * N * 64) break;
+        const int c = i / (N * 64), rem = i % (N * 64), r = rem / 64, k = rem % 64;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v[u]);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v[u] - __bfloat162float(h));
+        const int rl = r + N;
+        const size_t base = (size_t)c * 2 * N * 128;
+        qb[(base + (size_t)r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2) / 2] = __bfloat16_as_ushort(h);
+        qb[(base + (size_t)rl * 128 + ((((k >> 3) ^ (rl & 7)) & 7) << 4) + (k & 7) * 2) / 2] = __bfloat16_as_ushort(l);
+      }
+    }
+  } else
   for (int i0 = 0; i0 < C32 * N * 32; i0 += kQu * kThreads) {
     float v[kQu];
 #pragma unroll
@@ -296,6 +329,28 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(ab * 2 * N);
         for (int c = 0; c < C && ok; ++c) {
+          if constexpr (E == kElemBF16) {
+            // BF16 rows feed the tensor cores straight from the loaded stage:
+            // D[0,2N) += x . [q_hi ; q_lo]^T, four 16-value K steps per chunk;
+            // the commit frees the stage once the MMAs have read it
+            const int s = (int)(pr % (uint64_t)S);
+            if (!mbar_wait(&raw_full[s], (uint32_t)((pr / S) & 1u))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, 2 * N);
+            const uint32_t xa = smem_u32(raw + (size_t)s * kChunkBytes);
+            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_bf16(d, sw128_desc(xa + (uint32_t)ks * 32u), sw128_desc(qa + (uint32_t)ks * 32u), idesc_b,
+                       (c | ks) != 0 ? 1u : 0u);
+            issued = true;
+            mma_commit(&raw_empty[s]);
+            ++pr;
+            continue;
+          }
           const int l = (int)(pr % (uint64_t)kABufs);
           if (!mbar_wait(&a_full[l], (uint32_t)((pr / kABufs) & 1u))) {
             ok = false;
@@ -313,7 +368,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
               mma_tf32_tmem_a(d, al + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc1, 1u);
             }
           } else {
-            // BF16 / e4m3 values are exact in TF32: one MMA per 8-wide K step,
+            // e4m3 values are exact in TF32: one MMA per 8-wide K step,
             // D[0,2N) += x . [q_hi ; q_lo]^T over the chunk's 64 values (two
             // 32-value chunks of the query operand)
 #pragma unroll
@@ -342,6 +397,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     __syncwarp();
   } else if (is_converter(warp)) {
     // ------------------------------------------------------------- converters
+    // (idle for BF16 rows, which the MMAs read from the loaded stage)
     // two sets of four warps take alternate chunks (set = chunk index & 1), so
     // two chunks per lane quarter are in flight; S and kABufs are even, so a
     // raw stage or an x_hi/x_lo buffer always belongs to the same set and its
@@ -350,7 +406,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     const uint64_t cset = warp >= kConvWarp1 ? 1u : 0u;
     const int r = quarter * 32 + lane;  // this thread's row of every tile
     uint64_t pr = 0;
-    for (int64_t k = 0; k < n_mine && ok; ++k) {
+    for (int64_t k = 0; E != kElemBF16 && k < n_mine && ok; ++k) {
       for (int c = 0; c < C; ++c, ++pr) {
         if ((pr & 1u) != cset) continue;
         const int s = (int)(pr % (uint64_t)S), l = (int)(pr % (uint64_t)kABufs);
@@ -358,7 +414,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           ok = false;
           break;
         }
-        uint32_t hi[32], lo[32];  // FP32 rows: x_hi, x_lo; BF16/FP8 rows: values 0-31, 32-63
+        uint32_t hi[32], lo[32];  // FP32 rows: x_hi, x_lo; FP8 rows: values 0-31, 32-63
         const unsigned char *rowp = raw + (size_t)s * kChunkBytes + (size_t)r * tc_row_bytes(E);
         if constexpr (E == kElemF32) {
 #pragma unroll
@@ -370,18 +426,6 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
               const uint32_t hb = __float_as_uint(e[u]) & 0xFFFFE000u;
               hi[cc * 4 + u] = hb;
               lo[cc * 4 + u] = __float_as_uint(e[u] - __uint_as_float(hb));
-            }
-          }
-        } else if constexpr (E == kElemBF16) {
-#pragma unroll
-          for (int cc = 0; cc < 8; ++cc) {  // 128-byte swizzle: 8 values per 16-byte chunk
-            const uint4 v = *reinterpret_cast<const uint4 *>(rowp + (((cc ^ (r & 7)) & 7) << 4));
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-            uint32_t *dst = cc < 4 ? hi : lo;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              dst[(cc & 3) * 8 + 2 * u] = w[u] << 16;
-              dst[(cc & 3) * 8 + 2 * u + 1] = w[u] & 0xFFFF0000u;
             }
           }
         } else {
