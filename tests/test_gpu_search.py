@@ -290,3 +290,24 @@ def test_unknown_plan_is_rejected(lr, small):
                                   lr._ptr(out_i), lr._ptr(out_s), None, lr.ctypes.byref(opts), None, None)
         assert rc == lr.LR_ERR_INVALID
     lr.lr_index_destroy(idx)
+
+
+@pytest.mark.parametrize("plan", ["gemv", "tc"])
+@pytest.mark.parametrize("dup", [False, True])
+def test_k_sweep_across_select_and_sort_boundaries(lr, small, plan, dup):
+    """Per-query K on both sides of every boundary of the selection: the one-warp finish of the radix
+    select (bins of at most 32 keys), the register stages of the bitonic sort (64-key chunks) and its
+    shared-memory stages (128 .. 1024 keys).  With duplicated rows every score repeats ~300 times, so
+    the select must separate equal scores by their ids alone."""
+    c = small
+    ks = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1000, 1023, 1024]
+    B = len(ks)
+    X = np.ascontiguousarray(c.X[np.arange(c.n) % 97]) if dup else c.X
+    fm = _mixed_filters(31, B, c.V, c.df, c.n)
+    f = Filters.from_lists([fm.clauses(b) if b % 4 == 0 else [] for b in range(B)])
+    Q = datagen.query_embeddings(31, B, c.d)
+    idx = lr.lr_index_create(X, c.V, bitsets=c.bitsets(), metric="cosine", max_batch=32, max_k=1024)
+    ids, sc, cnt = _run(lr, idx, Q, f, ks, plan=plan)
+    ref = oracle.search(X, c.job_off, c.job_terms, Q, f, ks)
+    check_topk(ids, sc, cnt, ref, X, Q, c.job_off, c.job_terms, f)
+    lr.lr_index_destroy(idx)
