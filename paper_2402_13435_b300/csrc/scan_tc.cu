@@ -32,9 +32,10 @@
 //   warps 2-5, 10-13  converters (FP32 and FP8 rows), two sets of one warp per
 //              tensor-memory lane quarter, taking alternate chunks: each thread
 //              reads its row of a landed chunk, releases the raw stage at once,
-//              and writes x_hi and x_lo (FP8: the values, exact in TF32) into
-//              tensor memory (tcgen05.st).  Raw stages therefore never wait on
-//              the tensor core.
+//              and writes x_hi and x_lo (FP8: the values as BF16 pairs, exact,
+//              for kind::f16 MMAs against the BF16 query pair) into tensor
+//              memory (tcgen05.st).  Raw stages therefore never wait on the
+//              tensor core.
 //   warps 6-9 (and 14-17)  epilogue: read the accumulator (warp w owns lanes
 //              32*(w%4) ..), with the row masks of the tile read one tile
 //              ahead, test every passing (row, query) against the query's
@@ -183,10 +184,10 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     s_nlist = (int64_t)nl < a.tile_cap ? nl : (uint32_t)a.tile_cap;
   }
   // queries of the launch in the K-major 128-byte swizzle layout, split into
-  // hi/lo (TF32 for the TF32 MMA, BF16 for BF16 rows); each thread issues its
-  // loads of a round together, then stores
+  // hi/lo (a TF32 pair for FP32 rows, a BF16 pair for BF16 and FP8 rows); each
+  // thread issues its loads of a round together, then stores
   constexpr int kQu = 8;
-  if constexpr (E == kElemBF16) {
+  if constexpr (E != kElemF32) {
     // per 64-value chunk c: 2N rows of 128 bytes (q_hi rows 0..N-1, q_lo rows
     // N..2N-1), 16-byte unit j of row r at unit j ^ (r % 8)
     uint16_t *qb = reinterpret_cast<uint16_t *>(qop);
@@ -368,17 +369,18 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
               mma_tf32_tmem_a(d, al + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc1, 1u);
             }
           } else {
-            // e4m3 values are exact in TF32: one MMA per 8-wide K step,
-            // D[0,2N) += x . [q_hi ; q_lo]^T over the chunk's 64 values (two
-            // 32-value chunks of the query operand)
+            // e4m3 values are exact in BF16: the converters pack the chunk's 64
+            // values two per column, and four 16-value K steps of width 2N give
+            // D[0,2N) += x . [q_hi ; q_lo]^T with the BF16 query pair
+            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, 2 * N);
+            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
 #pragma unroll
-            for (int ks = 0; ks < 8; ++ks) {
-              const uint32_t qa = smem_u32(qop) + (uint32_t)((2 * c + (ks >> 2)) * 2 * N * 128) +
-                                  (uint32_t)(ks & 3) * 32u;
-              mma_tf32_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa), idesc2, (c | ks) != 0 ? 1u : 0u);
-            }
+            for (int ks = 0; ks < 4; ++ks)
+              mma_bf16_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc_b,
+                              (c | ks) != 0 ? 1u : 0u);
             (void)al;
             (void)idesc1;
+            (void)idesc2;
           }
           issued = true;
           mma_commit(&a_empty[l]);
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           ok = false;
           break;
         }
-        uint32_t hi[32], lo[32];  // FP32 rows: x_hi, x_lo; FP8 rows: values 0-31, 32-63
+        uint32_t hi[32], lo[32];  // FP32 rows: x_hi, x_lo; FP8 rows: hi holds the 64 values as BF16 pairs
         const unsigned char *rowp = raw + (size_t)s * kChunkBytes + (size_t)r * tc_row_bytes(E);
         if constexpr (E == kElemF32) {
 #pragma unroll
@@ -433,16 +435,15 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           for (int cc = 0; cc < 4; ++cc) {  // 64-byte swizzle: chunk cc of row r at slot cc ^ ((r / 2) % 4)
             const uint4 v = *reinterpret_cast<const uint4 *>(rowp + (((cc ^ (r >> 1)) & 3) << 4));
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-            uint32_t *dst = cc < 2 ? hi : lo;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
 #pragma unroll
-              for (int h = 0; h < 2; ++h) {
+              for (int h = 0; h < 2; ++h) {  // values 16cc + 4u + 2h and + 1: word 8cc + 2u + h, lower value low
                 const __half2_raw hr =
                     __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[u] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
                 const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
-                dst[(cc & 1) * 16 + 4 * u + 2 * h] = __float_as_uint(f.x);
-                dst[(cc & 1) * 16 + 4 * u + 2 * h + 1] = __float_as_uint(f.y);
+                const __nv_bfloat162 b = __floats2bfloat162_rn(f.x, f.y);  // exact: e4m3 fits BF16
+                hi[cc * 8 + 2 * u + h] = *reinterpret_cast<const uint32_t *>(&b);
               }
             }
           }
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         tc_fence_after();
         const uint32_t ta = tmem_base + ((uint32_t)(quarter * 32) << 16) + acol0 + (uint32_t)(l * 64);
         tmem_st32(ta, hi);
-        tmem_st32(ta + 32u, lo);
+        if constexpr (E == kElemF32) tmem_st32(ta + 32u, lo);
         tmem_st_wait();
         tc_fence_before();
         __syncwarp();
