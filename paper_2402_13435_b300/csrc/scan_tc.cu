@@ -24,16 +24,19 @@
 //              of width 2N with x_hi against [q_hi ; q_lo] and one of width N
 //              with x_lo against q_hi, so accumulator columns [0, N) and
 //              [N, 2N) add up to the 3xTF32 product.  Four accumulator buffers
-//              when N <= 32 (two above), so the MMAs run ahead of the epilogue.
+//              when N <= 32 (two above; always four for BF16 / FP8 rows, whose
+//              accumulators are N columns wide), so the MMAs run ahead of the
+//              epilogue.
 //              BF16 rows skip the converters: the MMA reads the landed stage
 //              from shared memory (kind::f16, 16-value K steps, x against the
-//              queries as a BF16 pair [q_hi ; q_lo]) and its commit frees the
-//              stage.
+//              queries rounded to BF16, one accumulator column per query: the
+//              low-precision scan only picks candidates for the FP32 rescore)
+//              and its commit frees the stage.
 //   warps 2-5, 10-13  converters (FP32 and FP8 rows), two sets of one warp per
 //              tensor-memory lane quarter, taking alternate chunks: each thread
 //              reads its row of a landed chunk, releases the raw stage at once,
 //              and writes x_hi and x_lo (FP8: the values as BF16 pairs, exact,
-//              for kind::f16 MMAs against the BF16 query pair) into tensor
+//              for kind::f16 MMAs against the BF16 queries) into tensor
 //              memory (tcgen05.st).  Raw stages therefore never wait on the
 //              tensor core.
 //   warps 6-9 (and 14-17)  epilogue: read the accumulator (warp w owns lanes
@@ -83,7 +86,13 @@ constexpr int kABufs = 4;                     // x_hi/x_lo chunk buffers in tens
 constexpr uint32_t kTmemCols = 512;           // the whole tensor memory: one CTA per SM
 // Accumulator buffers (2N columns each): four when they fit beside the x_hi/x_lo
 // buffers, so the MMAs can run up to four tiles ahead of the epilogue.
-__host__ __device__ constexpr int tc_acc_bufs(int n) { return n <= 32 ? 4 : 2; }  // even: one per epilogue set
+// accumulator buffers (even: each belongs to one epilogue set) and their
+// columns: FP32 rows accumulate x.q_hi and x.q_lo side by side (2N columns);
+// BF16 / FP8 rows, whose scan only picks candidates for the FP32 rescore,
+// score against the queries rounded to BF16 (N columns), so four buffers fit
+// up to N = 64
+__host__ __device__ constexpr int tc_acc_bufs(int e, int n) { return e != kElemF32 || n <= 32 ? 4 : 2; }
+__host__ __device__ constexpr int tc_acc_w(int e, int n) { return e == kElemF32 ? 2 * n : n; }
 
 // Row mask word of the tile list: bit q = launch query q passes the row.
 template <int N>
@@ -116,7 +125,7 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S, 
   T.cq = off;  // per epilogue warp: per-query counts, then reserved bases, of one flush
   off = T.cq + (size_t)epi_warps * 2 * N * 4;
   T.bars = tc_align(off, 16);
-  off = T.bars + (size_t)(2 * S + 2 * kABufs + 2 * tc_acc_bufs(N) + 1) * 8;
+  off = T.bars + (size_t)(2 * S + 2 * kABufs + 2 * 4 + 1) * 8;  // at most four accumulator buffers
   T.holder = tc_align(off, 16);
   T.total = T.holder + 16;
   return T;
@@ -153,13 +162,13 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + T.bars);
   uint64_t *raw_full = bars, *raw_empty = bars + S;
   uint64_t *a_full = bars + 2 * S, *a_empty = a_full + kABufs;
-  constexpr int kAcc = tc_acc_bufs(N);
+  constexpr int kAcc = tc_acc_bufs(E, N), kAccW = tc_acc_w(E, N);
   uint64_t *acc_full = a_empty + kABufs, *acc_empty = acc_full + kAcc;
   uint64_t *drain = acc_empty + kAcc;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + T.holder);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const uint32_t acol0 = (uint32_t)(kAcc * 2 * N);  // first tensor-memory column of the x_hi/x_lo buffers
+  const uint32_t acol0 = (uint32_t)(kAcc * kAccW);  // first tensor-memory column of the x_hi/x_lo buffers
   __shared__ bool s_last;
   __shared__ uint32_t s_nlist;
   __shared__ uint32_t s_live[2];  // bit q: query q takes part in this launch
@@ -183,13 +192,13 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     const uint32_t nl = *reinterpret_cast<const volatile uint32_t *>(a.tile_cnt);
     s_nlist = (int64_t)nl < a.tile_cap ? nl : (uint32_t)a.tile_cap;
   }
-  // queries of the launch in the K-major 128-byte swizzle layout, split into
-  // hi/lo (a TF32 pair for FP32 rows, a BF16 pair for BF16 and FP8 rows); each
-  // thread issues its loads of a round together, then stores
+  // queries of the launch in the K-major 128-byte swizzle layout: a TF32
+  // hi/lo pair for FP32 rows, the queries rounded to BF16 for BF16 and FP8
+  // rows; each thread issues its loads of a round together, then stores
   constexpr int kQu = 8;
   if constexpr (E != kElemF32) {
-    // per 64-value chunk c: 2N rows of 128 bytes (q_hi rows 0..N-1, q_lo rows
-    // N..2N-1), 16-byte unit j of row r at unit j ^ (r % 8)
+    // per 64-value chunk c: rows 0..N-1 of a 2N-row block of 128-byte rows,
+    // 16-byte unit j of row r at unit j ^ (r % 8)
     uint16_t *qb = reinterpret_cast<uint16_t *>(qop);
     for (int i0 = 0; i0 < C * N * 64; i0 += kQu * kThreads) {
       float v[kQu];
@@ -204,12 +213,9 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         const int i = i0 + u * kThreads + threadIdx.x;
         if (i >= C * N * 64) break;
         const int c = i / (N * 64), rem = i % (N * 64), r = rem / 64, k = rem % 64;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v[u]);
-        const __nv_bfloat16 l = __float2bfloat16_rn(v[u] - __bfloat162float(h));
-        const int rl = r + N;
         const size_t base = (size_t)c * 2 * N * 128;
-        qb[(base + (size_t)r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2) / 2] = __bfloat16_as_ushort(h);
-        qb[(base + (size_t)rl * 128 + ((((k >> 3) ^ (rl & 7)) & 7) << 4) + (k & 7) * 2) / 2] = __bfloat16_as_ushort(l);
+        qb[(base + (size_t)r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2) / 2] =
+            __bfloat16_as_ushort(__float2bfloat16_rn(v[u]));
       }
     }
   } else
@@ -328,19 +334,19 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(ab * 2 * N);
+        const uint32_t d = tmem_base + (uint32_t)(ab * kAccW);
         for (int c = 0; c < C && ok; ++c) {
           if constexpr (E == kElemBF16) {
             // BF16 rows feed the tensor cores straight from the loaded stage:
-            // D[0,2N) += x . [q_hi ; q_lo]^T, four 16-value K steps per chunk;
-            // the commit frees the stage once the MMAs have read it
+            // D[0,N) += x . bf16(q)^T, four 16-value K steps per chunk; the
+            // commit frees the stage once the MMAs have read it
             const int s = (int)(pr % (uint64_t)S);
             if (!mbar_wait(&raw_full[s], (uint32_t)((pr / S) & 1u))) {
               ok = false;
               break;
             }
             tc_fence_after();
-            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, 2 * N);
+            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, N);  // the q_hi rows
             const uint32_t xa = smem_u32(raw + (size_t)s * kChunkBytes);
             const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
 #pragma unroll
@@ -370,9 +376,9 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
             }
           } else {
             // e4m3 values are exact in BF16: the converters pack the chunk's 64
-            // values two per column, and four 16-value K steps of width 2N give
-            // D[0,2N) += x . [q_hi ; q_lo]^T with the BF16 query pair
-            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, 2 * N);
+            // values two per column, and four 16-value K steps of width N give
+            // D[0,N) += x . bf16(q)^T
+            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, N);  // the q_hi rows
             const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
@@ -563,7 +569,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         break;
       }
       tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 2 * N);
+      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kAccW);
       // queries 16j .. 16j+15 of the lane's row: rh = x_hi.q_hi + x_lo.q_hi, rl = x_hi.q_lo
       auto test_block = [&](int j, const uint32_t (&rh)[16], const uint32_t (&rl)[16]) {
         const uint32_t bm = (uint32_t)(qmask >> (16 * j)) & 0xFFFFu;
@@ -657,7 +663,12 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         __syncwarp();
         uint32_t rh[16], rl[16];
         tmem_ld16(taddr + (uint32_t)(16 * j), rh);
-        tmem_ld16(taddr + (uint32_t)(N + 16 * j), rl);
+        if constexpr (E == kElemF32) {
+          tmem_ld16(taddr + (uint32_t)(N + 16 * j), rl);
+        } else {
+#pragma unroll
+          for (int z = 0; z < 16; ++z) rl[z] = 0u;  // one accumulator column per query
+        }
         tmem_ld_wait();
         test_block(j, rh, rl);
       }
@@ -694,7 +705,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
 
 template <int N, int E>
 cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cudaStream_t s) {
-  static_assert(tc_acc_bufs(N) * 2 * N + 64 * kABufs <= (int)kTmemCols, "tensor memory budget");
+  static_assert(tc_acc_bufs(E, N) * tc_acc_w(E, N) + 64 * kABufs <= (int)kTmemCols, "tensor memory budget");
   static_assert(kABufs % 2 == 0, "each converter set owns every other x_hi/x_lo buffer");
   const size_t budget = 220u * 1024u;
   int S = 12;  // raw stages: even (each converter set owns every other stage)
