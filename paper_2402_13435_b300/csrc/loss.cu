@@ -21,6 +21,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "bits.cuh"
 #include "lr_internal.h"
 #include "ptx.h"
 
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       for (int k = 0; k < 2; ++k) {
         const int i = r + k * kRRows;
         const int q = cc0 + (i >> 2), w = (r0 >> 5) + (i & 3);
-        v[k] = (a.mask != nullptr && q < a.B && w < a.Mw) ? __ldg(a.mask + (size_t)q * a.Mw + w) : 0u;
+        v[k] = q < a.B && w < a.Mw ? (a.mask != nullptr ? __ldg(a.mask + (size_t)q * a.Mw + w) : ~0u) : 0u;
       }
       sm0 = v[0];
       sm1 = v[1];
@@ -296,30 +297,38 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&s_empty[b]);
-      // allowed columns of this tile as a 64-bit mask
-      // allowed columns of this tile: bit c of al[c / 32]
-      uint32_t al[2] = {0u, 0u};
-      if (rvalid) {
-        if (MODE != kDj) {
-          uint32_t w0 = cw0, w1 = cw1;
-          const int lim = a.M - c0;  // columns past M do not exist
-          w0 &= lim >= 32 ? ~0u : (lim > 0 ? ((1u << lim) - 1u) : 0u);
-          w1 &= lim >= 64 ? ~0u : (lim > 32 ? ((1u << (lim - 32)) - 1u) : 0u);
-          const int pc = pos_row - c0;
-          if (pc >= 0 && pc < 32) w0 |= 1u << pc;
-          if (pc >= 32 && pc < 64) w1 |= 1u << (pc - 32);
-          al[0] = w0;
-          al[1] = w1;
-        } else {
-          const DjStage &st = stg[b];
-          const int lim = a.B - c0;
+      // allowed columns of this tile: bit c of al[c / 32]; kDj also the
+      // columns whose positive is this row's job: bit c of pm[c / 32]
+      uint32_t al[2] = {0u, 0u}, pm[2] = {0u, 0u};
+      if (MODE == kDj) {
+        // the tile's 64 queries x this warp's 32 jobs as two 32 x 32 bit
+        // matrices, one query per lane (lane, lane + 32), transposed so that
+        // lane r holds its job's column
+        const DjStage &st = stg[b];
+        const int wj = (r0 >> 5) + warp;
+        uint32_t mw[2], pw[2];
 #pragma unroll
-          for (int c = 0; c < 64; ++c) {
-            const bool ok_c = c < lim && (a.mask == nullptr || ((st.mask[c * 4 + (r >> 5)] >> (r & 31)) & 1u) ||
-                                          st.pos[c] == grow);
-            al[c >> 5] |= (ok_c ? 1u : 0u) << (c & 31);
-          }
+        for (int h = 0; h < 2; ++h) {
+          const int p = st.pos[lane + 32 * h];
+          pw[h] = (p >= 0 && (p >> 5) == wj) ? 1u << (p & 31) : 0u;
+          mw[h] = st.mask[(lane + 32 * h) * 4 + warp] | pw[h];  // the positive is always allowed
         }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // every lane takes part in the transposes
+          pm[h] = bit_transpose32(pw[h], lane);
+          const uint32_t t = bit_transpose32(mw[h], lane);
+          al[h] = rvalid ? t : 0u;
+        }
+      } else if (rvalid) {
+        uint32_t w0 = cw0, w1 = cw1;
+        const int lim = a.M - c0;  // columns past M do not exist
+        w0 &= lim >= 32 ? ~0u : (lim > 0 ? ((1u << lim) - 1u) : 0u);
+        w1 &= lim >= 64 ? ~0u : (lim > 32 ? ((1u << (lim - 32)) - 1u) : 0u);
+        const int pc = pos_row - c0;
+        if (pc >= 0 && pc < 32) w0 |= 1u << pc;
+        if (pc >= 32 && pc < 64) w1 |= 1u << (pc - 32);
+        al[0] = w0;
+        al[1] = w1;
       }
       if (MODE == kFwd) {
         float tmax = -INFINITY;
@@ -370,7 +379,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
                 ispos = c == pc ? 1.f : 0.f;
               } else {
                 lse = stg[b].lse[c];
-                ispos = stg[b].pos[c] == grow ? 1.f : 0.f;
+                ispos = ((pm[c >> 5] >> (c & 31)) & 1u) ? 1.f : 0.f;
               }
               const float dz = (__expf(z - lse) - ispos) * g;
               dz2[h] = ((al[c >> 5] >> (c & 31)) & 1u) ? dz : 0.f;

@@ -21,6 +21,7 @@
 // counts of the launch are accumulated here as well.
 #include <algorithm>
 
+#include "bits.cuh"
 #include "lr_internal.h"
 #include "ptx.h"
 #include "scan_common.cuh"
@@ -32,22 +33,6 @@ constexpr int kTfThreads = 256;
 constexpr int kTfWarps = kTfThreads / 32;
 constexpr int kTfRun = kTfWarps;  // consecutive groups a block evaluates together (one per warp)
 constexpr int kTfAppend = 8;      // runs between a warp's list appends (16 tiles at most)
-
-// 32x32 bit-matrix transpose across the warp: lane i holds row i on entry
-// (bit c = column c) and column i on exit (bit r = row r).
-template <int J, uint32_t M>
-__device__ __forceinline__ uint32_t transpose_stage(uint32_t x, int lane) {
-  const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, J);
-  return (lane & J) ? (((y >> J) & M) | (x & ~M)) : ((x & M) | ((y & M) << J));
-}
-
-__device__ __forceinline__ uint32_t bit_transpose32(uint32_t x, int lane) {
-  x = transpose_stage<16, 0x0000FFFFu>(x, lane);
-  x = transpose_stage<8, 0x00FF00FFu>(x, lane);
-  x = transpose_stage<4, 0x0F0F0F0Fu>(x, lane);
-  x = transpose_stage<2, 0x33333333u>(x, lane);
-  return transpose_stage<1, 0x55555555u>(x, lane);
-}
 
 // W = uint32_t: at most 32 queries, one per lane; uint64_t: up to 64, two per lane.
 template <typename W>
