@@ -12,12 +12,13 @@
 // and appends t to the compact list tile_row[]; t = 2 i + h for tile h of the
 // i-th group the launch visits (groups g_begin + i g_step), so a full pass
 // numbers tiles by their rows and a sampled pass uses a compact range.  The scan then streams exactly
-// the listed tiles, and its pipeline carries no predicate latency.  A block
-// evaluates runs of eight consecutive groups, one per warp, with the next
-// run's term words (256 contiguous bytes per term at unit stride) in
-// flight while it evaluates the current one, and appends its tiles with one
-// atomic per eight runs, so the list order follows the warps' progress rather
-// than the row order; the scan does not depend on it.  The per-query pass
+// the listed tiles, and its pipeline carries no predicate latency.  Every
+// warp streams its own groups (global warp index, stride = all warps of the
+// grid) with the next group's term words (32 bytes per term) in flight while
+// it evaluates the current one, in its own double buffer, so no block-wide
+// barrier couples the warps; it appends its tiles with one atomic per eight
+// groups, so the list order follows the warps' progress rather than the row
+// order; the scan does not depend on it.  The per-query pass
 // counts of the launch are accumulated here as well.
 #include <algorithm>
 
@@ -31,8 +32,8 @@ namespace {
 
 constexpr int kTfThreads = 256;
 constexpr int kTfWarps = kTfThreads / 32;
-constexpr int kTfRun = kTfWarps;  // consecutive groups a block evaluates together (one per warp)
-constexpr int kTfAppend = 8;      // runs between a warp's list appends (16 tiles at most)
+constexpr int kTfRun = kTfWarps;  // groups a block has in flight (one per warp)
+constexpr int kTfAppend = 8;      // groups between a warp's list appends (16 tiles at most)
 
 // W = uint32_t: at most 32 queries, one per lane; uint64_t: up to 64, two per lane.
 template <typename W>
@@ -41,8 +42,8 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ uint4 tf_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // two buffers of one run's term words, [group of the run][slot][8] each;
-  // then the launch's clause lists (qc, cl, cs), staged once per block
+  // per warp two buffers of one group's term words, [slot][8] each; then the
+  // launch's clause lists (qc, cl, cs), staged once per block
   const size_t run_words = (size_t)kTfRun * a.n_slots * 8;
   uint32_t *tabs = reinterpret_cast<uint32_t *>(tf_smem);
   int32_t *s_qc = reinterpret_cast<int32_t *>(tf_smem) + 2 * run_words;
@@ -58,21 +59,20 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
   __syncthreads();
 
   const int64_t n_items = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
-  const int64_t n_runs = (n_items + kTfRun - 1) / kTfRun;
-  // the block loads a run's words together: per slot the run's groups are
-  // consecutive, so the copies of one slot cover kTfRun * 32 contiguous bytes
-  auto prefetch = [&](int64_t run, int buf) {
-    uint32_t *dst = tabs + (size_t)buf * run_words;
-    for (int i = threadIdx.x; i < a.n_slots * kTfRun * 2; i += blockDim.x) {
-      const int sl = i / (kTfRun * 2), p = i % (kTfRun * 2), gl = p >> 1, h = p & 1;
-      const int64_t it = run * kTfRun + gl;
-      if (it < n_items)
-        cp_async16(dst + ((size_t)gl * a.n_slots + sl) * 8 + h * 4,
-                   s_bm[sl] + (a.g_begin + it * a.g_step) * kGroupWords + h * 4);
+  // every warp streams its own groups (global warp index, stride = all
+  // warps), double buffering their term words in its own part of shared
+  // memory, so no block-wide barrier separates one group from the next
+  const int64_t gw = (int64_t)blockIdx.x * kTfWarps + warp, nw = (int64_t)gridDim.x * kTfWarps;
+  uint32_t *wtab = tabs + (size_t)warp * 2 * a.n_slots * 8;
+  auto prefetch = [&](int64_t it, int buf) {  // the group's 32 bytes of every slot
+    uint32_t *dst = wtab + (size_t)buf * a.n_slots * 8;
+    for (int i = lane; i < a.n_slots * 2; i += 32) {
+      const int sl = i >> 1, h = i & 1;
+      cp_async16(dst + sl * 8 + h * 4, s_bm[sl] + (a.g_begin + it * a.g_step) * kGroupWords + h * 4);
     }
     cp_async_commit();
   };
-  if ((int64_t)blockIdx.x < n_runs) prefetch(blockIdx.x, 0);  // in flight while the CNFs are packed
+  if (gw < n_items) prefetch(gw, 0);  // in flight while the CNFs are packed
 
   const int q0 = lane, q1 = lane + 32;
   const bool live0 = q0 < a.nq && (a.active == nullptr || a.active[a.q_base + q0] != 0u);
@@ -93,13 +93,16 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
   };
 
   int buf = 0, since = 0;
-  for (int64_t run = blockIdx.x; run < n_runs; run += gridDim.x) {
-    cp_async_wait_all();
-    __syncthreads();  // the run's words are visible, and every warp is done with the other buffer
-    if (run + gridDim.x < n_runs) prefetch(run + gridDim.x, buf ^ 1);
-    const int64_t it = run * kTfRun + warp;
-    if (it < n_items) {
-      const uint32_t *tab = tabs + (size_t)buf * run_words + (size_t)warp * a.n_slots * 8;
+  for (int64_t it = gw; it < n_items; it += nw) {
+    if (it + nw < n_items) {
+      prefetch(it + nw, buf ^ 1);  // every lane finished reading that buffer last group
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
+    __syncwarp();  // every lane's copies of this group have landed
+    {
+      const uint32_t *tab = wtab + (size_t)buf * a.n_slots * 8;
       const int64_t g = a.g_begin + it * a.g_step;
       uint32_t pw0[8], pw1[8];
 #pragma unroll
@@ -156,6 +159,7 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
         ++n_tiles;
       }
     }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
     buf ^= 1;
     if (++since == kTfAppend) {
       append();
