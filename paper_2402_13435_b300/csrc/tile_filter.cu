@@ -66,9 +66,10 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
   uint32_t *wtab = tabs + (size_t)warp * 2 * a.n_slots * 8;
   auto prefetch = [&](int64_t it, int buf) {  // the group's 32 bytes of every slot
     uint32_t *dst = wtab + (size_t)buf * a.n_slots * 8;
+    const size_t goff = (size_t)(a.g_begin + it * a.g_step) * kGroupWords;
     for (int i = lane; i < a.n_slots * 2; i += 32) {
       const int sl = i >> 1, h = i & 1;
-      cp_async16(dst + sl * 8 + h * 4, s_bm[sl] + (a.g_begin + it * a.g_step) * kGroupWords + h * 4);
+      cp_async16(dst + sl * 8 + h * 4, s_bm[sl] + goff + h * 4);
     }
     cp_async_commit();
   };
@@ -118,20 +119,25 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
         }
       }
       const int64_t r0 = g * kGroupRows;
-      uint32_t any0 = 0, any1 = 0;
+      if (r0 + kGroupRows > a.n) {  // the index's last group: rows past n do not exist
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const int64_t left = a.n - (r0 + w * 32);
+          const uint32_t valid = left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u);
+          pw0[w] &= valid;
+          pw1[w] &= valid;
+        }
+      }
+      uint32_t any0 = 0, any1 = 0, c0 = 0, c1 = 0;
 #pragma unroll
       for (int w = 0; w < 8; ++w) {
-        const int64_t left = a.n - (r0 + w * 32);
-        const uint32_t valid = left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u);
-        pw0[w] &= valid;
-        pass0 += (unsigned long long)__popc(pw0[w]);
-        if constexpr (kTwo) {
-          pw1[w] &= valid;
-          pass1 += (unsigned long long)__popc(pw1[w]);
-        }
+        c0 += (uint32_t)__popc(pw0[w]);
+        if constexpr (kTwo) c1 += (uint32_t)__popc(pw1[w]);
         if (w < 4) any0 |= pw0[w] | (kTwo ? pw1[w] : 0u);
         else any1 |= pw0[w] | (kTwo ? pw1[w] : 0u);
       }
+      pass0 += c0;
+      pass1 += c1;
       const uint32_t fl = (__reduce_or_sync(0xFFFFFFFFu, any0) != 0u ? 1u : 0u) |
                           (__reduce_or_sync(0xFFFFFFFFu, any1) != 0u ? 2u : 0u);
 #pragma unroll
