@@ -124,3 +124,25 @@ def test_precision_fewer_passing_than_candidates(lr, corpus):
         lr.lr_index_destroy(idx)
     ref = oracle.search(X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
     check_topk(ids, sc, cnt, ref, X, Q, c.job_off, c.job_terms, f, metric="cosine")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+@pytest.mark.parametrize("B", [24, 40, 64])
+def test_precision_tc_query_widths(lr, corpus, dtype, B):
+    """The tensor-core scan of low-precision rows at every query width it is built for (N = 32, 48, 64
+    accumulator columns): recall against the FP64 oracle and the plain path's score checks."""
+    c = corpus
+    po, pid = c.postings()
+    K = 100
+    f = datagen.filters(41 + B, B, c.V, 1.1)
+    Q = datagen.query_embeddings(42 + B, B, c.d)
+    idx = lr.lr_index_create(c.X, c.V, post_off=po, post_ids=pid, n_dense_terms=128, metric="cosine", max_batch=64,
+                             max_k=256, dtype=dtype, oversample=4)
+    try:
+        ids, sc, cnt = _run(lr, idx, Q, f, K, plan="tc")
+    finally:
+        lr.lr_index_destroy(idx)
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    rec = oracle.recall_at_k([ids[b, :cnt[b]] for b in range(B)], [ref.ids[b, :ref.count[b]] for b in range(B)])
+    assert rec >= 0.999, "recall@%d = %.5f" % (K, rec)
+    check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
