@@ -436,37 +436,53 @@ __global__ void __launch_bounds__(kLossThreads, 1)
 }
 
 // X [rows][d] (BF16 or FP32) -> P [rows_p][dp] and PT [dp][rows_p], BF16, zero padded.
+// A 32 x 32 tile per block goes through shared memory, so both copies are
+// written along their rows.
+constexpr int kPrepTile = 32;
 __global__ void k_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, __nv_bfloat16 *P,
                             __nv_bfloat16 *PT) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)rows_p * dp) return;
-  const int row = (int)(i / dp), k = (int)(i % dp);
-  __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-  if (row < rows && k < d) {
-    v = elem == kElemBF16 ? reinterpret_cast<const __nv_bfloat16 *>(X)[(size_t)row * d + k]
-                          : __float2bfloat16_rn(reinterpret_cast<const float *>(X)[(size_t)row * d + k]);
+  __shared__ __nv_bfloat16 tile[kPrepTile][kPrepTile + 1];
+  const int r0 = blockIdx.x * kPrepTile, k0 = blockIdx.y * kPrepTile;  // rows on x: no 65,535 limit
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads
+  for (int j = ty; j < kPrepTile; j += blockDim.y) {
+    const int row = r0 + j, k = k0 + tx;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+    if (row < rows && k < d) {
+      v = elem == kElemBF16 ? reinterpret_cast<const __nv_bfloat16 *>(X)[(size_t)row * d + k]
+                            : __float2bfloat16_rn(reinterpret_cast<const float *>(X)[(size_t)row * d + k]);
+    }
+    if (row < rows_p && k < dp) P[(size_t)row * dp + k] = v;
+    tile[j][tx] = v;
   }
-  P[i] = v;
-  PT[(size_t)k * rows_p + row] = v;
+  __syncthreads();
+  for (int j = ty; j < kPrepTile; j += blockDim.y) {
+    const int k = k0 + j, row = r0 + tx;
+    if (k < dp && row < rows_p) PT[(size_t)k * rows_p + row] = tile[tx][j];
+  }
 }
 
-// Per query: combine the split partials into lse and the loss term; one CTA sums the
-// terms in FP64 in a fixed order.  An out-of-range positive makes the loss NaN.
-__global__ void k_loss_combine(const LossArgs a, int splits, float *lse, float *loss) {
+// Per query (one thread each): combine the split partials into its log-sum-exp.
+__global__ void k_loss_lse(const LossArgs a, int splits, float *lse) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.B) return;
+  float mx = -INFINITY;
+  for (int s = 0; s < splits; ++s) mx = fmaxf(mx, a.part_m[(size_t)s * a.rows_p + q]);
+  float sum = 0.f;
+  for (int s = 0; s < splits; ++s) {
+    const float ms = a.part_m[(size_t)s * a.rows_p + q];
+    if (ms > -INFINITY) sum += a.part_s[(size_t)s * a.rows_p + q] * exp2f((ms - mx) * kLog2e);
+  }
+  lse[q] = mx + logf(sum);
+}
+
+// The loss: one CTA sums the queries' terms lse - z_pos in FP64 in a fixed
+// order.  An out-of-range positive makes the loss NaN.
+__global__ void k_loss_combine(const LossArgs a, const float *lse, float *loss) {
   __shared__ double red[1024];
   double acc = 0.0;
   for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
-    float mx = -INFINITY;
-    for (int s = 0; s < splits; ++s) mx = fmaxf(mx, a.part_m[(size_t)s * a.rows_p + q]);
-    float sum = 0.f;
-    for (int s = 0; s < splits; ++s) {
-      const float ms = a.part_m[(size_t)s * a.rows_p + q];
-      if (ms > -INFINITY) sum += a.part_s[(size_t)s * a.rows_p + q] * exp2f((ms - mx) * kLog2e);
-    }
-    const float l = mx + logf(sum);
-    lse[q] = l;
     const int p = a.pos[q];
-    acc += (p >= 0 && p < a.M) ? (double)l - (double)a.zpos[q] : (double)NAN;
+    acc += (p >= 0 && p < a.M) ? (double)lse[q] - (double)a.zpos[q] : (double)NAN;
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -490,9 +506,9 @@ __global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_str
 
 cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
                              cudaStream_t s) {
-  const int64_t n = (int64_t)rows_p * dp;
-  k_loss_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, elem, rows, d, rows_p, dp, (__nv_bfloat16 *)P,
-                                                         (__nv_bfloat16 *)PT);
+  const dim3 grid((unsigned)((rows_p + kPrepTile - 1) / kPrepTile), (unsigned)((dp + kPrepTile - 1) / kPrepTile));
+  k_loss_prep<<<grid, dim3(kPrepTile, 8), 0, s>>>(X, elem, rows, d, rows_p, dp, (__nv_bfloat16 *)P,
+                                                  (__nv_bfloat16 *)PT);
   return cudaGetLastError();
 }
 
@@ -528,7 +544,10 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
 }
 
 cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, float *loss, cudaStream_t s) {
-  k_loss_combine<<<1, 1024, 0, s>>>(a, splits, lse, loss);
+  if (a.B > 0) k_loss_lse<<<(unsigned)((a.B + 255) / 256), 256, 0, s>>>(a, splits, lse);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_loss_combine<<<1, 1024, 0, s>>>(a, lse, loss);
   return cudaGetLastError();
 }
 
