@@ -478,19 +478,23 @@ __global__ void k_loss_lse(const LossArgs a, int splits, float *lse) {
 // The loss: one CTA sums the queries' terms lse - z_pos in FP64 in a fixed
 // order.  An out-of-range positive makes the loss NaN.
 __global__ void k_loss_combine(const LossArgs a, const float *lse, float *loss) {
-  __shared__ double red[1024];
+  __shared__ double red[32];
   double acc = 0.0;
   for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
     const int p = a.pos[q];
     acc += (p >= 0 && p < a.M) ? (double)lse[q] - (double)a.zpos[q] : (double)NAN;
   }
-  red[threadIdx.x] = acc;
+  // fixed reduction tree: lanes by shuffles, then the warps' sums in warp order
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (int)threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+    if (threadIdx.x == 0) *loss = (float)(v / (double)a.B);
   }
-  if (threadIdx.x == 0) *loss = (float)(red[0] / (double)a.B);
 }
 
 __global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ) {
