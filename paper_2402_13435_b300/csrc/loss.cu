@@ -30,7 +30,9 @@ namespace {
 
 constexpr int kRRows = 128;     // rows of the resident tile
 constexpr int kCRows = 64;      // rows of a streamed tile
-constexpr int kLossThreads = 192;
+constexpr int kLossThreads = 320;  // warps 0-3 and 6-9: two epilogue sets; 4: TMA; 5: MMA
+constexpr int kLossFwdThreads = 192;  // the forward: one epilogue set
+constexpr int kCBufs = 3;          // streamed-tile buffers: a tile loads while the two before it are in use
 constexpr uint32_t kLossTmemCols = 256;  // 2 score tiles of 64 columns + accumulator (<= 128)
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -54,13 +56,13 @@ __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
   L.r = off;
   off += (size_t)(dp / 64) * kRRows * 128;  // K-blocks of 128 rows x 128 bytes
   L.c = off;
-  off += (size_t)2 * (dp / 64) * kCRows * 128;
+  off += (size_t)kCBufs * (dp / 64) * kCRows * 128;
   L.ct = off;
-  off += mode == kFwd ? 0 : (size_t)2 * dp * 128;  // transposed C tile: dp rows x 64 values
+  off += mode == kFwd ? 0 : (size_t)kCBufs * dp * 128;  // transposed C tile: dp rows x 64 values
   L.dz = off;
   off += mode == kFwd ? 0 : (size_t)2 * 2 * kRRows * 128;  // [buffer][hi, lo] 128 rows x 64 values
   L.stage = off;
-  off += mode == kDj ? 2 * sizeof(DjStage) : 0;
+  off += mode == kDj ? 4 * sizeof(DjStage) : 0;  // two per epilogue set
   L.bars = off;
   off += 16 * 8;
   L.holder = off;
@@ -89,8 +91,9 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   unsigned char *sdz = smem + L.dz;
   DjStage *stg = reinterpret_cast<DjStage *>(smem + L.stage);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
-  uint64_t *bar_r = bars, *c_full = bars + 1, *c_empty = bars + 3, *s_full = bars + 5, *s_empty = bars + 7;
-  uint64_t *dz_full = bars + 9, *dz_empty = bars + 11, *acc_full = bars + 13;
+  uint64_t *bar_r = bars, *c_full = bars + 1, *c_empty = bars + 1 + kCBufs;  // [kCBufs] each
+  uint64_t *s_full = bars + 1 + 2 * kCBufs, *s_empty = s_full + 2;               // [2]: one per epilogue set
+  uint64_t *dz_full = s_empty + 2, *dz_empty = dz_full + 2, *acc_full = dz_empty + 2;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + L.holder);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r0 = blockIdx.x * kRRows;
@@ -101,9 +104,11 @@ __global__ void __launch_bounds__(kLossThreads, 1)
 
   if (threadIdx.x == 0) {
     mbar_init(bar_r, 1);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kCBufs; ++i) {
       mbar_init(&c_full[i], 1);
       mbar_init(&c_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&s_full[i], 1);
       mbar_init(&s_empty[i], 4);
       mbar_init(&dz_full[i], 4);
@@ -129,8 +134,8 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       mbar_arrive_expect_tx(bar_r, (uint32_t)(KB * kRRows * 128));
       for (int kb = 0; kb < KB; ++kb) tma_load_2d(sr + (size_t)kb * kRRows * 128, &tm_r, kb * 64, r0, bar_r);
       for (int t = 0; t < T && ok; ++t) {
-        const int b = t & 1;
-        if (!mbar_wait(&c_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u)) {
+        const int b = t % kCBufs;
+        if (!mbar_wait(&c_empty[b], (uint32_t)((t / kCBufs) & 1) ^ 1u)) {
           ok = false;
           break;
         }
@@ -144,7 +149,8 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       if (!ok) {
         atomicOr(a.status, kErrTimeout);
         mbar_wait(bar_r, 0u);  // let issued loads land
-        for (int t = issued > 2 ? issued - 2 : 0; t < issued; ++t) mbar_wait(&c_full[t & 1], (uint32_t)((t >> 1) & 1));
+        for (int t = issued > kCBufs ? issued - kCBufs : 0; t < issued; ++t)
+          mbar_wait(&c_full[t % kCBufs], (uint32_t)((t / kCBufs) & 1));
       }
     }
     __syncwarp();
@@ -155,11 +161,11 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       const uint32_t acc = tmem + 2u * kCRows;
       bool issued = false;
       auto issue_s = [&](int t) -> bool {
-        const int b = t & 1;
-        if (!mbar_wait(&c_full[b], (uint32_t)((t >> 1) & 1))) return false;
+        const int b = t & 1, cb = t % kCBufs;  // score buffer (the epilogue set's), streamed-tile buffer
+        if (!mbar_wait(&c_full[cb], (uint32_t)((t / kCBufs) & 1))) return false;
         if (!mbar_wait(&s_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u)) return false;
         tc_fence_after();
-        const uint32_t ra = smem_u32(sr), ca = smem_u32(sc + (size_t)b * c_bytes);
+        const uint32_t ra = smem_u32(sr), ca = smem_u32(sc + (size_t)cb * c_bytes);
         for (int k = 0; k < dp / 16; ++k) {
           const uint32_t koff = (uint32_t)(k & 3) * 32u;
           mma_bf16(tmem + (uint32_t)(b * kCRows), sw128_desc(ra + (uint32_t)(k >> 2) * (kRRows * 128) + koff),
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         }
         issued = true;
         mma_commit(&s_full[b]);
-        if (MODE == kFwd) mma_commit(&c_empty[b]);
+        if (MODE == kFwd) mma_commit(&c_empty[cb]);
         return true;
       };
       if (!mbar_wait(bar_r, 0u)) ok = false;
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
           tc_fence_after();
           const uint32_t dh = smem_u32(sdz + (size_t)(2 * b) * kRRows * 128);
           const uint32_t dl = smem_u32(sdz + (size_t)(2 * b + 1) * kRRows * 128);
-          const uint32_t ct = smem_u32(sct + (size_t)b * ct_bytes);
+          const uint32_t ct = smem_u32(sct + (size_t)(t % kCBufs) * ct_bytes);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {  // K = the tile's 64 streamed rows
             mma_bf16(acc, sw128_desc(dh + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g,
@@ -194,7 +200,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
             mma_bf16(acc, sw128_desc(dl + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g, 1u);
           }
           mma_commit(&dz_empty[b]);
-          mma_commit(&c_empty[b]);
+          mma_commit(&c_empty[t % kCBufs]);
         }
       }
       if (issued) {  // every MMA has completed before the epilogue reads the accumulator / TMEM is freed
@@ -208,9 +214,18 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     __syncwarp();
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int r = warp * 32 + lane;
+    // two sets of four warps (0-3 and 6-9) take alternate streamed tiles: set e
+    // takes tiles e, e + 2, ..., so score buffer e and dZ buffer e are its own
+    // and their barrier phases come in order; warp w reads tensor-memory lanes
+    // 32 (w % 4) ..
+    // the forward epilogue is issue-bound with one set, and two CTAs of 192
+    // threads share an SM: it launches without warps 6-9
+    constexpr int kSets = MODE == kFwd ? 1 : 2;
+    const int eset = warp >= 6 ? 1 : 0, quarter = warp & 3;
+    const bool active = eset < kSets;
+    const int r = quarter * 32 + lane;
     const int grow = r0 + r;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
     // row identity: query (kFwd, kDq) or job (kDj)
     const bool rvalid = MODE == kDj ? grow < a.M : grow < a.B;
     int pos_row = -1;
@@ -222,10 +237,11 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     float m = -INFINITY, ssum = 0.f, zpos = 0.f;
     bool have_pos = false;
     // Mask words (and for kDj the query tile's positives and lse) are fetched
-    // one tile ahead.  kFwd/kDq: this row's two words, in registers.  kDj: the
-    // 128 epilogue threads stage the query tile in shared memory (double
-    // buffered; each iteration ends at one named barrier that every epilogue
-    // warp reaches, also after a failed wait, so no warp waits forever).
+    // one tile of the set ahead.  kFwd/kDq: this row's two words, in registers.
+    // kDj: the set's 128 threads stage the query tile in shared memory (double
+    // buffered per set; each iteration ends at the set's named barrier, which
+    // every warp of the set reaches, also after a failed wait, so no warp
+    // waits forever).
     uint32_t nw0 = ~0u, nw1 = ~0u;  // kFwd/kDq: next tile's mask words
     uint32_t sm0 = 0u, sm1 = 0u;    // kDj: this thread's share of the next stage
     int spos = -1;
@@ -263,22 +279,24 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         st.lse[r] = slse;
       }
     };
+    auto set_barrier = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + eset) : "memory"); };
     if (MODE == kDj) {
-      if (T > 0) {
-        fetch_stage(0);
-        store_stage(0);
+      if (eset < T) {
+        fetch_stage(eset);
+        store_stage(2 * eset);
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-    } else if (T > 0) {
-      fetch_row_words(0);
+      set_barrier();
+    } else if (active && eset < T) {
+      fetch_row_words(eset);
     }
-    for (int t = 0; t < T; ++t) {
-      const int b = t & 1;
+    for (int t = eset, it = 0; active && t < T; t += kSets, ++it) {
+      const int b = t & 1;                 // two sets: == eset
+      const int sb = 2 * eset + (it & 1);  // kDj: this tile's stage
       const int c0 = (t0 + t) * kCRows;
       const uint32_t cw0 = nw0, cw1 = nw1;
-      if (t + 1 < T) {
-        if (MODE == kDj) fetch_stage(t + 1);
-        else fetch_row_words(t + 1);
+      if (t + kSets < T) {
+        if (MODE == kDj) fetch_stage(t + kSets);
+        else fetch_row_words(t + kSets);
       }
       do {
       if (!ok) break;
@@ -304,14 +322,14 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         // the tile's 64 queries x this warp's 32 jobs as two 32 x 32 bit
         // matrices, one query per lane (lane, lane + 32), transposed so that
         // lane r holds its job's column
-        const DjStage &st = stg[b];
-        const int wj = (r0 >> 5) + warp;
+        const DjStage &st = stg[sb];
+        const int wj = (r0 >> 5) + quarter;
         uint32_t mw[2], pw[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int p = st.pos[lane + 32 * h];
           pw[h] = (p >= 0 && (p >> 5) == wj) ? 1u << (p & 31) : 0u;
-          mw[h] = st.mask[(lane + 32 * h) * 4 + warp] | pw[h];  // the positive is always allowed
+          mw[h] = st.mask[(lane + 32 * h) * 4 + quarter] | pw[h];  // the positive is always allowed
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // every lane takes part in the transposes
@@ -378,7 +396,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
                 lse = lse_row;
                 ispos = c == pc ? 1.f : 0.f;
               } else {
-                lse = stg[b].lse[c];
+                lse = stg[sb].lse[c];
                 ispos = ((pm[c >> 5] >> (c & 31)) & 1u) ? 1.f : 0.f;
               }
               const float dz = (__expf(z - lse) - ispos) * g;
@@ -399,18 +417,18 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         if (lane == 0) mbar_arrive(&dz_full[b]);
       }
       } while (0);
-      if (MODE == kDj) {  // the next tile's stage, then this tile's barrier (every iteration, every warp)
-        if (t + 1 < T) store_stage((t + 1) & 1);
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (MODE == kDj) {  // the set's next stage, then this tile's barrier (every iteration, every warp of the set)
+        if (t + 2 < T) store_stage(2 * eset + ((it + 1) & 1));
+        set_barrier();
       }
     }
-    if (MODE == kFwd) {
+    if (MODE == kFwd) {  // one set: the row's log-sum-exp partial of this split
       if (rvalid) {
         a.part_m[(size_t)blockIdx.y * a.rows_p + grow] = m;
         a.part_s[(size_t)blockIdx.y * a.rows_p + grow] = ssum;
         if (have_pos) a.zpos[grow] = zpos;
       }
-    } else {
+    } else if (eset == 0) {  // set 0 writes the accumulated rows
       if (!wwait(acc_full, 0u, lane)) ok = false;
       tc_fence_after();
       const uint32_t acc = trow + 2u * kCRows;
@@ -529,7 +547,7 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
     case kFwd:
       e = cudaFuncSetAttribute(k_loss<kFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_loss<kFwd><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
+      k_loss<kFwd><<<grid, kLossFwdThreads, smem, s>>>(a, r, c, ct);
       break;
     case kDq:
       e = cudaFuncSetAttribute(k_loss<kDq>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
