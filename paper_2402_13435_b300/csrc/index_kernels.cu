@@ -128,7 +128,7 @@ __global__ void k_scatter_postings(const int64_t *post_off, const uint32_t *post
 __global__ void k_expand_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *spans,
                                   int n_spans, int span_log2, const int32_t *terms, uint32_t *bitmaps,
                                   int64_t n_words, int64_t n) {
-  extern __shared__ uint32_t span_words[];
+  extern __shared__ __align__(16) uint32_t span_words[];
   const int j = blockIdx.x;
   const int32_t t = terms[blockIdx.y];
   const int sw = 1 << span_log2;
@@ -136,7 +136,8 @@ __global__ void k_expand_postings(const int64_t *post_off, const uint32_t *post_
   const int64_t base = post_off[t];
   const int32_t *sp = spans + (size_t)t * (size_t)(n_spans + 1);
   const int64_t lo = base + sp[j], hi = base + sp[j + 1];
-  for (int w = threadIdx.x; w < sw; w += blockDim.x) span_words[w] = 0u;
+  uint4 *span4 = reinterpret_cast<uint4 *>(span_words);  // spans are whole multiples of 4 words
+  for (int v = threadIdx.x; v < (sw >> 2); v += blockDim.x) span4[v] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
     const uint32_t id = post_ids[p];
@@ -144,8 +145,10 @@ __global__ void k_expand_postings(const int64_t *post_off, const uint32_t *post_
     if ((int64_t)id < n && local >= 0 && local < sw) atomicOr(&span_words[local], 1u << (id & 31u));
   }
   __syncthreads();
-  uint32_t *bm = bitmaps + (size_t)blockIdx.y * (size_t)n_words;
-  for (int w = threadIdx.x; w < sw && w0 + w < n_words; w += blockDim.x) bm[w0 + w] = span_words[w];
+  // n_words and w0 are multiples of 8 words: 16-byte stores stay aligned and
+  // a vector lies entirely inside or entirely past the bitmap
+  uint4 *bm4 = reinterpret_cast<uint4 *>(bitmaps + (size_t)blockIdx.y * (size_t)n_words + w0);
+  for (int v = threadIdx.x; v < (sw >> 2) && w0 + 4 * v < n_words; v += blockDim.x) bm4[v] = span4[v];
 }
 
 // Jobs holding each term (popcount of its term-major bitmap): one block per term.
