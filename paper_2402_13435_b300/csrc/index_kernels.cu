@@ -308,7 +308,7 @@ cudaError_t launch_filter_eval(const ScanArgs &a, unsigned long long *pass_cnt, 
                                int64_t out_words, int grid, cudaStream_t s) {
   const size_t smem = (size_t)(kScanThreads / 32) * (size_t)a.n_slots * 8 * sizeof(uint32_t);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_filter_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem((const void *)k_filter_eval, (size_t)smem);
     if (e != cudaSuccess) return e;
   }
   k_filter_eval<<<grid, kScanThreads, smem, s>>>(a, pass_cnt, out_bitmap, out_words);

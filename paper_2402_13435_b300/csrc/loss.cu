@@ -545,17 +545,17 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
   cudaError_t e;
   switch (mode) {
     case kFwd:
-      e = cudaFuncSetAttribute(k_loss<kFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = allow_dynamic_smem((const void *)k_loss<kFwd>, (size_t)smem);
       if (e != cudaSuccess) return e;
       k_loss<kFwd><<<grid, kLossFwdThreads, smem, s>>>(a, r, c, ct);
       break;
     case kDq:
-      e = cudaFuncSetAttribute(k_loss<kDq>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = allow_dynamic_smem((const void *)k_loss<kDq>, (size_t)smem);
       if (e != cudaSuccess) return e;
       k_loss<kDq><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
       break;
     case kDj:
-      e = cudaFuncSetAttribute(k_loss<kDj>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = allow_dynamic_smem((const void *)k_loss<kDj>, (size_t)smem);
       if (e != cudaSuccess) return e;
       k_loss<kDj><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
       break;

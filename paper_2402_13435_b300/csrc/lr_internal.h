@@ -4,7 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lr.h"
@@ -147,6 +150,25 @@ struct SelectArgs {
   int32_t unsorted;              // 1: final mode writes the top K in any order (the caller re-ranks them)
   uint32_t *err;                 // device error word
 };
+
+// Raise a kernel's dynamic shared-memory cap to at least `bytes` on the
+// current device.  The cap is a per-function attribute and setting it is a
+// costly driver call, so each (function, device) is raised only when a launch
+// needs more than it already allows; caps only grow, under a lock, so a
+// concurrent caller never lowers the cap another launch relies on.
+inline cudaError_t allow_dynamic_smem(const void *fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> allowed;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &cur = allowed[{fn, dev}];
+  if (cur >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, cudaStream_t s);

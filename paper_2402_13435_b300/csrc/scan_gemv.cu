@@ -353,7 +353,7 @@ cudaError_t launch_one(const ScanArgs &a, int grid, cudaStream_t s) {
   const WarpLayout L = warp_layout(DP, elem_bytes(E), NQ, a.n_slots, warps);
   if (L.total > budget) return cudaErrorInvalidValue;
   auto *fn = k_scan_gemv<DP, NQ, E>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)L.total);
   if (e != cudaSuccess) return e;
   fn<<<grid, warps * 32, L.total, s>>>(a);
   return cudaGetLastError();

@@ -714,7 +714,7 @@ cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cuda
   const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S, 4 * tc_epi_sets(E));
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
   auto *fn = k_scan_tc<N, E>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(T.total + 1024));
+  cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)(T.total + 1024));
   if (e != cudaSuccess) return e;
   fn<<<grid, tc_threads(E), T.total + 1024, s>>>(a, tmap, S);
   return cudaGetLastError();

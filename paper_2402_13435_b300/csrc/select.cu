@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
 cudaError_t launch_threshold(const ThrArgs &a, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   const size_t smem = (size_t)kSmemKeys * sizeof(uint64_t);
-  cudaError_t e = cudaFuncSetAttribute(k_threshold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void *)k_threshold, (size_t)smem);
   if (e != cudaSuccess) return e;
   k_threshold<<<dim3((unsigned)B, (unsigned)kThrSlices), kSelThreads, smem, s>>>(a);
   return cudaGetLastError();
@@ -640,7 +640,7 @@ cudaError_t launch_threshold(const ThrArgs &a, int B, cudaStream_t s) {
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   const size_t smem = (size_t)(kSmemKeys + kMaxK) * sizeof(uint64_t);
-  cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void *)k_select, (size_t)smem);
   if (e != cudaSuccess) return e;
   k_select<<<B, kSelThreads, smem, s>>>(a);
   return cudaGetLastError();
@@ -652,7 +652,7 @@ cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s) {
   const cudaError_t e0 = cudaGetLastError();
   if (e0 != cudaSuccess) return e0;
   const size_t smem = (size_t)2 * kMaxK * sizeof(uint64_t);
-  cudaError_t e = cudaFuncSetAttribute(k_rescore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void *)k_rescore, (size_t)smem);
   if (e != cudaSuccess) return e;
   k_rescore<<<B, kRsThreads, smem, s>>>(a);
   return cudaGetLastError();

@@ -239,7 +239,7 @@ cudaError_t launch_tile_filter(const ScanArgs &a, int num_sms, cudaStream_t s) {
   // the static shared memory (slot pointers, pass counts) counts against the
   // 48 KB default too: opt in well before the dynamic part alone reaches it
   if (smem > 32u * 1024u) {
-    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)smem);
     if (e != cudaSuccess) return e;
   }
   fn<<<grid, kTfThreads, smem, s>>>(a);
