@@ -318,3 +318,72 @@ def test_loss_gradient_rows_sum_to_zero_and_masked_columns_get_nothing():
     loss, _, dQ, dJ = oracle.softmax_loss(Q, J, pos, allowed, 3.0)
     assert np.max(np.abs(dQ[:, -1])) < 1e-15
     assert not np.any(dJ[never])
+
+
+# ------------------------------------------------------------------ per-pair predicate (the parity checker)
+def test_pair_pass_matches_paper_tbr_example(golden_dir):
+    """oracle.pair_pass rebuilds T_j per pair on its own path; it must give the appendix "TBR" example's
+    pass sets pair by pair, with the documents' term lists given unsorted and with repeats."""
+    g = json.load(open(os.path.join(golden_dir, "paper_tbr_example.json")))
+    sets = [set(a[o[0]:o[-1]]) for a, o in zip(g["attributes"], g["offsets"])]
+    lists = [sorted(s, reverse=True) + sorted(s)[:1] for s in sets]   # unsorted, one repeat
+    off = np.zeros(len(lists) + 1, dtype=np.int64)
+    for j, l in enumerate(lists):
+        off[j + 1] = off[j] + len(l)
+    terms = np.asarray([t for l in lists for t in l], dtype=np.int32)
+    f = Filters.from_lists([q["cnf"] for q in g["queries"]])
+    B, n = len(g["queries"]), len(sets)
+    qi, ji = np.repeat(np.arange(B), n), np.tile(np.arange(n), B)
+    got = oracle.pair_pass(off, terms, n, f, qi, ji).reshape(B, n)
+    for b, q in enumerate(g["queries"]):
+        assert sorted(np.nonzero(got[b])[0].tolist()) == q["pass"], q
+
+
+def test_pair_pass_truth_table_all_subsets_of_eight_terms():
+    """V = 8, jobs = all 256 term subsets (lists of different lengths, so a mis-indexed job offset
+    reads another job's terms), pairs visited in a shuffled order, against Python set expressions."""
+    sets = [{t for t in range(8) if (m >> t) & 1} for m in range(256)]
+    rng = np.random.default_rng(17)
+    lists = [list(rng.permutation(sorted(s))) for s in sets]          # T_j given in random order
+    off = np.zeros(257, dtype=np.int64)
+    for j, l in enumerate(lists):
+        off[j + 1] = off[j] + len(l)
+    terms = np.asarray([int(t) for l in lists for t in l], dtype=np.int32)
+    qs = []
+    for _ in range(60):
+        nc = int(rng.integers(0, 4))
+        qs.append([sorted(set(rng.choice(8, size=int(rng.integers(1, 5))).tolist())) for _ in range(nc)])
+    f = Filters.from_lists(qs)
+    qi, ji = np.repeat(np.arange(60), 256), np.tile(np.arange(256), 60)
+    perm = rng.permutation(qi.size)
+    got = np.empty(qi.size, dtype=bool)
+    got[perm] = oracle.pair_pass(off, terms, 256, f, qi[perm], ji[perm])
+    expect = np.asarray([all(sets[j] & set(c) for c in qs[b]) for b, j in zip(qi, ji)])
+    assert np.array_equal(got, expect)
+    # and the full-matrix predicate agrees with the per-pair one
+    _, mat = oracle.filter(off, terms, 256, f, want_matrix=True)
+    assert np.array_equal(mat.reshape(-1), expect)
+
+
+# ------------------------------------------------------------------ loss temperature (Sec. 5.1, Eq. 1)
+@pytest.mark.parametrize("inv_tau", [0.5, 20.0])
+def test_loss_temperature_closed_form_two_columns(inv_tau):
+    """B = 1 with two allowed columns, scores s+ (the positive) and s-: Eq. 1 and Eq. 2 give
+    L = log(1 + exp(inv_tau (s- - s+))), lse = log(e^{inv_tau s+} + e^{inv_tau s-}) and
+    dL/dq = inv_tau p- (j- - j+) with p- = 1 / (1 + exp(inv_tau (s+ - s-))).  Dropping or inverting
+    the temperature changes every one of them."""
+    Q = np.asarray([[0.75, -0.5, 0.25]])
+    J = np.asarray([[0.5, 0.25, -1.0],     # positive
+                    [0.25, -0.75, 0.5],    # allowed negative
+                    [2.0, 2.0, 2.0]])      # masked
+    s_pos, s_neg = float(Q[0] @ J[0]), float(Q[0] @ J[1])
+    allowed = np.asarray([[False, True, False]])
+    loss, lse, dQ, dJ = oracle.softmax_loss(Q, J, np.asarray([0]), allowed, inv_tau)
+    z = inv_tau * (s_neg - s_pos)
+    assert loss == pytest.approx(math.log1p(math.exp(z)), rel=1e-13)
+    assert lse[0] == pytest.approx(math.log(math.exp(inv_tau * s_pos) + math.exp(inv_tau * s_neg)), rel=1e-13)
+    p_neg = 1.0 / (1.0 + math.exp(-z))
+    assert np.allclose(dQ[0], inv_tau * p_neg * (J[1] - J[0]), rtol=1e-12, atol=1e-15)
+    assert np.allclose(dJ[1], inv_tau * p_neg * Q[0], rtol=1e-12, atol=1e-15)
+    assert np.allclose(dJ[0], -inv_tau * p_neg * Q[0], rtol=1e-12, atol=1e-15)
+    assert not np.any(dJ[2])
