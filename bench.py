@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--n-batches", type=int, default=4)
     p.add_argument("--plan", default="auto")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--cpu-queries", type=int, default=8)
+    p.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (0: one query per host core)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     # workload shape (defaults: the plain method at scale); the precision form of the same study is
@@ -55,7 +55,9 @@ def parse():
     # other forms of the method (one JSON line each):
     #   --form loss   masked softmax loss fwd+bwd, B=4096 queries vs 4096 in-batch + 16384 sampled jobs, d=128
     #   --form serve  continuous batching over a resident 20M x 128 BF16 index, Poisson request streams
-    p.add_argument("--form", choices=("search", "loss", "serve"), default="search")
+    #   --form sweep  selectivity sweep: each band alone at batch sizes --sweep-batches, per-point roofline
+    p.add_argument("--form", choices=("search", "loss", "serve", "sweep"), default="search")
+    p.add_argument("--sweep-batches", default="1,32,256,1024")
     p.add_argument("--loss-b", type=int, default=4096)
     p.add_argument("--loss-m", type=int, default=4096 + 16384)
     p.add_argument("--tau", type=float, default=0.05)
@@ -124,43 +126,62 @@ class ClockSampler:
                ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
                ("hw_power_brake_slowdown", "nvmlClocksEventReasonHwPowerBrakeSlowdown"))
 
-    def __init__(self, gpu: int, period_s: float = 0.005):
+    def __init__(self, gpu: int, period_s: float = 0.002):
         self.gpu = gpu
         self.period = period_s
         self.samples = []  # (sm_mhz, max_mhz, reasons bitmask, host time)
         self.window = (0.0, float("inf"))
+        self.load_end = None
         self.names = []
         self.stop = threading.Event()
         self.nv = None
         self.proc = None
+        self.source = "none"
+        self.errors = []
+
+    def _nvml_handle(self, nv):
+        """The NVML handle of this process's CUDA device: by UUID when CUDA_VISIBLE_DEVICES names one,
+        by its index there otherwise (NVML numbers every GPU of the machine)."""
+        vis = [x.strip() for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+        if vis and self.gpu < len(vis):
+            v = vis[self.gpu]
+            if v.isdigit():
+                return nv.nvmlDeviceGetHandleByIndex(int(v))
+            return nv.nvmlDeviceGetHandleByUUID(v)
+        return nv.nvmlDeviceGetHandleByIndex(self.gpu)
 
     def __enter__(self):
         try:
             import pynvml as nv
 
             nv.nvmlInit()
-            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-            ids = [x for x in vis.split(",") if x.strip() != ""]
-            phys = int(ids[self.gpu]) if ids and ids[self.gpu].strip().isdigit() else self.gpu
-            self.h = nv.nvmlDeviceGetHandleByIndex(phys)
+            self.h = self._nvml_handle(nv)
+            self.mx = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
+            self._reasons = (nv.nvmlDeviceGetCurrentClocksEventReasons
+                             if hasattr(nv, "nvmlDeviceGetCurrentClocksEventReasons")
+                             else nv.nvmlDeviceGetCurrentClocksThrottleReasons)
+            self._reasons(self.h)
             self.nv = nv
             self.names = [(nm, getattr(nv, attr)) for nm, attr in self.REASONS if hasattr(nv, attr)]
+            self.source = "nvml"
             self.t = threading.Thread(target=self._poll_nvml, daemon=True)
-        except Exception:
+        except Exception as e:  # no usable NVML: nvidia-smi's query loop instead
+            self.errors.append("nvml: %s" % e)
             self.nv = None
+            self.source = "nvidia-smi"
             self.t = threading.Thread(target=self._poll_smi, daemon=True)
         self.t.start()
         return self
 
     def _poll_nvml(self):
         nv, h = self.nv, self.h
-        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
         while not self.stop.is_set():
             try:
-                self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), mx,
-                                     nv.nvmlDeviceGetCurrentClocksEventReasons(h), time.perf_counter()))
-            except Exception:
-                pass
+                self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), self.mx, self._reasons(h),
+                                     time.perf_counter()))
+            except Exception as e:
+                if len(self.errors) < 3:
+                    self.errors.append("nvml sample: %s" % e)
             self.stop.wait(self.period)
 
     def _poll_smi(self):
@@ -168,8 +189,10 @@ class ClockSampler:
                   "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         self.names = [(nm, 1 << i) for i, (nm, _) in enumerate(self.REASONS[:4])]
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + fields,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+            vis = [x.strip() for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+            dev = vis[self.gpu] if vis and self.gpu < len(vis) else str(self.gpu)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, "--query-gpu=" + fields,
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             return
@@ -201,18 +224,27 @@ class ClockSampler:
             except Exception:
                 pass
 
-    def mark(self, t0: float, t1: float):
-        """Keep only the samples taken between host times t0 and t1 (the timed region)."""
+    def mark(self, t0: float, t1: float, t_load_end: float = None):
+        """The timed region ran between host times t0 and t1; when it is too short to hold a few samples,
+        the window extends to t_load_end, the end of the same workload's synchronised steps that follow
+        it (still under load), and the summary says so."""
         self.window = (t0, t1)
+        self.load_end = t_load_end
 
     def summary(self):
         got = [x for x in self.samples if self.window[0] <= x[3] <= self.window[1]]
+        window = "timed region"
+        if len(got) < 3 and self.load_end is not None:
+            got = [x for x in self.samples if self.window[0] <= x[3] <= self.load_end]
+            window = "timed region + the synchronised steps of the same workload that follow it"
         if not got:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source, "errors": self.errors[:3]}
         sm = [x[0] for x in got]
         reasons = sorted({nm for _, _, bits, _ in got for nm, b in self.names if bits & b})
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(x[1] for x in got)),
-                "sm_min_mhz": float(min(sm)), "reasons": reasons, "samples": len(sm)}
+                "sm_min_mhz": float(min(sm)), "reasons": reasons, "samples": len(sm), "source": self.source,
+                "window": window}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -282,15 +314,15 @@ def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
             union |= bm[i]
         words = union.view(torch.int32).cpu().numpy().view(np.uint32)
         rows = int(np.unpackbits(words.view(np.uint8)).sum())
+        terms = {int(t) for t in sub.terms} if sub.terms.size and int(sub.q_off[-1]) > 0 else set()
+        p = sum(min(n / 8.0, 4.0 * float(df[t])) for t in terms)
+        masks = 0
         if kernel == "k_scan_tc":
             tiles = int(np.count_nonzero(words[: len(words) // 4 * 4].reshape(-1, 4).any(axis=1)))
             if len(words) % 4:
                 tiles += int(words[len(words) // 4 * 4:].any())
-            per_launch.append(rows * rb + tiles * 128 * (4 if sub.n <= 32 else 8))
-            continue
-        terms = {int(t) for t in sub.terms}
-        p = sum(min(n / 8.0, 4.0 * float(df[t])) for t in terms)
-        per_launch.append(rows * rb + p)
+            masks = tiles * 128 * (4 if sub.n <= 32 else 8)
+        per_launch.append({"E": rows * rb, "P": p, "masks": masks})
     return per_launch
 
 
@@ -333,7 +365,8 @@ def run_reference(args):
     if rank != 0:
         return
     wl = make_workload(args)
-    per_step = max(1, args.cpu_queries // 2)
+    # the oracle runs OpenMP over queries: one query per host core uses them all
+    per_step = max(os.cpu_count() or 1, 1)
     times = []
     nq = 0
     for i in range(args.warmup + args.steps):
@@ -410,12 +443,22 @@ def run_ours(args):
             step(i, probes[i])
         ev1.record()
         torch.cuda.synchronize()
-        clk.mark(h0, time.perf_counter())
+        h1 = time.perf_counter()
         if world > 1:
             dist.barrier()
+        # ---- per-step latency distribution (separate, synchronised steps of the same workload)
+        lat = []
+        for i in range(min(args.steps, 20)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step(i)
+            e1.record()
+            torch.cuda.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        clk.mark(h0, h1, time.perf_counter())
+    step_ms = lat
     ms = ev0.elapsed_time(ev1)
     args.plan_used = probes[0].plan if probes[0].plan in ("gemv", "tc") else None
-    step_ms = []
     lr.lr_index_sync(idx)
     ms = max_over_ranks(ms, world)
     scan_ms = float(np.mean([p.start.elapsed_time(p.stop) for p in probes]))
@@ -423,26 +466,25 @@ def run_ours(args):
     launches = int(sum(p.n_launches for p in probes))
     value = whole_job_rate(B * args.steps, world, ms / 1e3)
 
-    # ---- per-step latency distribution (separate, synchronised steps)
-    lat = []
-    for i in range(min(args.steps, 20)):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        step(i)
-        e1.record()
-        torch.cuda.synchronize()
-        lat.append(e0.elapsed_time(e1))
-    step_ms = lat
-
     # ---- roofline of the dominant kernel (the main scan)
-    per_launch = algorithmic_scan_bytes(lr, idx, wl["filters"][0], c, args)
+    parts = algorithmic_scan_bytes(lr, idx, wl["filters"][0], c, args)
     peak, peak_kind = peaks()
-    # scan_ms covers n_scan launches of batch i % nb; use batch 0's bytes as the per-launch average
-    achieved = (sum(per_launch) / 1e9) / (scan_ms / 1e3)
+    # scan_ms covers n_scan launches of batch i % nb; batch 0's bytes stand for the per-launch average.
+    # E: rows some query of the launch must score x row bytes (the algorithmic bytes of the scan);
+    # masks: the tile filter's row masks the tensor-core scan reads; P: the batch's term words
+    E = sum(x["E"] for x in parts)
+    masks = sum(x["masks"] for x in parts)
+    P = sum(x["P"] for x in parts)
+    achieved = (E / 1e9) / (scan_ms / 1e3)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic(args),
             "kernel": "%s (main scan, %d launches per step)" % (scan_plan(args)[0], n_scan),
-            "algorithmic_bytes_per_launch": float(np.mean(per_launch)), "launch_ms": scan_ms / max(n_scan, 1),
+            "algorithmic_bytes_per_launch": E / len(parts), "launch_ms": scan_ms / max(n_scan, 1),
+            "frac_with_row_masks": ((E + masks) / 1e9) / (scan_ms / 1e3) / peak,
+            "frac_e_plus_p_over_step": ((E + P) / 1e9) / (ms / args.steps / 1e3) / peak,
+            "bytes_note": "achieved = E (rows passing some query of the launch x row bytes) / main-scan time; "
+                          "frac_with_row_masks adds the tile list's row masks the scan reads; "
+                          "frac_e_plus_p_over_step = (E + term bytes P) / whole step time",
             "peak_kind": peak_kind}
 
     # ---- end to end through the C ABI with host buffers
@@ -475,7 +517,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         from oracle.compare import check_topk
 
-        ref, sel, dt, cores = cpu_oracle_sample(wl, args, args.cpu_queries, 0)
+        ref, sel, dt, cores = cpu_oracle_sample(wl, args, args.cpu_queries or (os.cpu_count() or 8), 0)
         step(0)
         torch.cuda.synchronize()
         ids, sc, cnt = out_ids.cpu().numpy(), out_sc.cpu().numpy(), out_cnt.cpu().numpy()
@@ -501,7 +543,7 @@ def run_ours(args):
         p50, p99 = (float(np.percentile(step_ms, 50)), float(np.percentile(step_ms, 99))) if step_ms else (None, None)
         out = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, paper-shaped)",
+               "vs_baseline": None, "dtype": args.dtype, "data": "synthetic (seeded generator, paper-shaped)",
                "config": workload_config(args), "p50_ms": p50, "p99_ms": p99, "clocks": clk.summary(),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "parity": parity,
                "setup_s": {"generate": round(wl["gen_s"], 1), "index_build": round(build_s, 1)}}
@@ -644,6 +686,84 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sweep(args):
+    """Each selectivity band alone at each batch size (the scale configuration's sweep): per point the
+    achieved pass rates (exact, from the library's filter export), QPS, the main-scan time and two
+    roofline fractions -- per batch (rows some query of the batch passes, read once, plus term bytes P
+    and outputs O, over the step time) and per launch (each launch's union rows over its scan time)."""
+    import torch
+    import datagen
+    import paper_2402_13435_b300 as lr
+
+    t0 = time.time()
+    c = datagen.corpus(args.seed, args.n, args.dim, args.vocab, args.lam, 1.1)
+    po, pid = c.postings()
+    batches = [int(x) for x in args.sweep_batches.split(",")]
+    Bmax = max(batches)
+    idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), c.V, post_off=po, post_ids=pid,
+                             n_dense_terms=args.n_dense, metric="cosine", max_batch=max(Bmax, 32), max_k=args.k,
+                             dtype=args.dtype, oversample=args.oversample, max_sparse_terms=max(256, 4 * Bmax))
+    torch.cuda.synchronize()
+    peak, peak_kind = peaks()
+    rb = row_bytes(args)
+    points = []
+    for bi, band in enumerate(args.band_list):
+        fb = datagen.filters_in_band(args.seed + 5, Bmax, c.V, 1.1, c.df, c.n, band,
+                                     stream_offset=(bi + 1) * 100_000_000)
+        Qall = datagen.query_embeddings(args.seed + 6 + bi, Bmax, args.dim)
+        for B in batches:
+            f = fb.subset(range(B))
+            Qd = torch.from_numpy(np.ascontiguousarray(Qall[:B])).cuda()
+            oi = torch.empty((B, args.k), dtype=torch.int32, device="cuda")
+            osc = torch.empty((B, args.k), dtype=torch.float32, device="cuda")
+            oc = torch.empty(B, dtype=torch.int32, device="cuda")
+            steps = max(3, min(args.steps, 10 if B >= 256 else 30))
+            probes = [lr.Probe(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps)]
+            for _ in range(3):
+                lr.lr_search(idx, Qd, f, args.k, out_ids=oi, out_scores=osc, out_count=oc, plan=args.plan)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for i in range(steps):
+                lr.lr_search(idx, Qd, f, args.k, out_ids=oi, out_scores=osc, out_count=oc, plan=args.plan,
+                             probe=probes[i])
+            e1.record()
+            torch.cuda.synchronize()
+            lr.lr_index_sync(idx)
+            ms = e0.elapsed_time(e1) / steps
+            scan_ms = float(np.mean([p.start.elapsed_time(p.stop) for p in probes]))
+            plan = probes[0].plan
+            npass, bm = lr.lr_filter_count(idx, f, bitmap=True)
+            rates = npass.cpu().numpy() / c.n
+            words = bm.view(torch.int32)
+            union = words[0].clone()
+            for i in range(1, B):
+                union |= words[i]
+            urows = int(np.unpackbits(union.cpu().numpy().view(np.uint8)).sum())
+            terms = {int(t) for t in f.terms} if int(f.q_off[-1]) > 0 else set()
+            P = sum(min(c.n / 8.0, 4.0 * float(c.df[t])) for t in terms)
+            O = B * args.k * 8
+            per = 64 if plan == "tc" else 8
+            e_launch = 0
+            for q0 in range(0, B, per):
+                u = words[q0].clone()
+                for i in range(q0 + 1, min(B, q0 + per)):
+                    u |= words[i]
+                e_launch += int(np.unpackbits(u.cpu().numpy().view(np.uint8)).sum()) * rb
+            points.append({"band": band, "batch": B, "plan": plan, "qps": B / (ms / 1e3), "ms_per_step": ms,
+                           "scan_ms_per_step": scan_ms, "scan_launches": probes[0].n_scan_launches,
+                           "pass_rate_mean": float(rates.mean()), "pass_rate_min": float(rates.min()),
+                           "pass_rate_max": float(rates.max()), "union_rows": urows,
+                           "frac_per_batch": ((urows * rb + P + O) / 1e9) / (ms / 1e3) / peak,
+                           "frac_per_launch_scan": (e_launch / 1e9) / (scan_ms / 1e3) / peak})
+    out = {"metric": "selectivity sweep: QPS and roofline per band and batch", "unit": "queries/s",
+           "n_gpus": 1, "dtype": args.dtype, "data": "synthetic (seeded generator, paper-shaped)",
+           "config": workload_config(args), "peak": peak, "peak_kind": peak_kind, "points": points,
+           "setup_s": round(time.time() - t0, 1)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -652,6 +772,8 @@ def main():
         run_loss(args)
     elif args.form == "serve":
         run_serve(args)
+    elif args.form == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

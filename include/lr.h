@@ -98,6 +98,11 @@ typedef struct lr_index lr_index;
  *   max_sparse_terms distinct posting-list terms one batch may use (0: 256).
  *   oversample       precision form: candidates per query = oversample * K
  *                    (0: 4).  Ignored for LR_F32.
+ *   id_base          global id of row 0 (0 for a whole index).  An index over
+ *                    rows [id_base, id_base + n_jobs) of a larger job set -- one
+ *                    contiguous row shard -- returns global ids; ties still
+ *                    break by ascending id, so per-shard results merge exactly
+ *                    with lr_merge_topk.  id_base + n_jobs <= 2^31 - 1.
  */
 typedef struct lr_index_desc {
   int64_t n_jobs;
@@ -115,6 +120,7 @@ typedef struct lr_index_desc {
   int32_t max_batch_terms;
   int32_t max_sparse_terms;
   int32_t oversample;
+  int64_t id_base;
 } lr_index_desc;
 
 /*
@@ -212,10 +218,12 @@ lr_status lr_search_ex(lr_index *index, const float *q, int32_t B, const lr_filt
  * keeps until the process exits.  No cudaMalloc, cudaFree or allocating library
  * routine is called.
  *
- *   X            device [n_jobs][dim] FP32, dim in {32, 64, 128, 256}; the score
- *                is the plain inner product (normalise beforehand for cosine).
+ *   X            device [n_jobs][dim] FP32, contiguous rows, dim in {32, 64, 128,
+ *                256}, base 16-byte aligned (rows are copied in 16-byte pieces);
+ *                the score is the plain inner product (normalise beforehand for
+ *                cosine).
  *   n_jobs       1 .. 16,777,216.
- *   q            device [B][dim] FP32, 1 <= B <= 8.
+ *   q            device [B][dim] FP32, contiguous, 1 <= B <= 8.
  *   pass_bitmap  device, nullable (NULL = every job passes).  Row b starts at
  *                pass_bitmap + b * bitmap_stride_words; bit j%32 of word j/32 is
  *                set iff job j may be returned for query b.  The row stride must
@@ -226,15 +234,24 @@ lr_status lr_search_ex(lr_index *index, const float *q, int32_t B, const lr_filt
  *                out_count) and out_count [B] (nullable), device memory.
  * Results equal lr_search's for the same data and the LR_DOT metric.
  * Sizes beyond these limits return LR_ERR_WORKSPACE (LR_ERR_UNSUPPORTED for
- * dim).  The first call on a device looks up the array's device address with
- * that device current; make that first call before any stream capture.  All
- * calls share the array and keep the last call's contents (each call clears
- * what must start at zero), so calls that overlap on the GPU race: serialise
- * them.  Returns after enqueueing the work on `stream`.
+ * dim).  A pointer that is not device (or managed) memory, or that breaks the
+ * alignment above (outputs and q: 4 bytes), returns LR_ERR_INVALID before any
+ * work is enqueued.  Every call looks up the array's device address with the
+ * current device; the first call on a device also loads the library's device
+ * code there, so make that first call before any stream capture.  All calls
+ * share the array and keep the last call's contents (each call clears what must
+ * start at zero, the device error word included), so calls that overlap on the
+ * GPU race: serialise them.  Returns after enqueueing the work on `stream`.
  */
 lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t dim, const float *q, int32_t B,
                             const uint32_t *pass_bitmap, int64_t bitmap_stride_words, int32_t k, int32_t *out_ids,
                             float *out_scores, int32_t *out_count, void *stream);
+/* Wait for `stream` and report the device error word of the last
+ * lr_search_noalloc call on the current device (LR_ERR_TIMEOUT: a bounded
+ * device wait gave up; LR_ERR_CUDA: inconsistent selection state), then clear
+ * it.  Call it after the search and before the next one, whose start clears
+ * the word.  Allocates nothing. */
+lr_status lr_search_noalloc_status(void *stream);
 
 /*
  * Exact term filter only (F-TBR, Sec. 5.3 and appendix "TBR"): for each query the
@@ -249,6 +266,27 @@ lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64
 /* Wait for `stream` and report any error the library's kernels recorded on the
  * device for this index (LR_ERR_TIMEOUT for a bounded wait that gave up). */
 lr_status lr_index_sync(lr_index *index, void *stream);
+
+/*
+ * Exact merge of per-part top-K lists (Sec. 5.3, "Communication cost": the
+ * search splits by job rows; each part -- a row shard, on this GPU or another --
+ * returns its own top K' and one exchange brings the lists together).  The top
+ * K of a union of disjoint job sets is the top K of the union of each set's top
+ * K (K <= K'), so merging the lists under the same order (score desc, id asc)
+ * reproduces the unsharded result.
+ *
+ *   ids, scores  device [G][B][k_in] int32 / FP32: list g of query b, sorted by
+ *                (score desc, id asc), ids distinct across lists (global ids).
+ *   counts       device [G][B] int32: valid entries of each list (0 .. k_in).
+ *   k            1 .. 4096, k <= G * k_in; outputs device [B][k] int32 / FP32
+ *                (-1 / -inf past out_count) and out_count [B] (nullable):
+ *                min(k, sum_g counts).
+ * 1 <= G <= 64.  Lists that break the sort precondition give unspecified (but
+ * in-bounds) rows.  Stream-ordered; allocates nothing.
+ */
+lr_status lr_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int32_t G, int32_t B,
+                        int32_t k_in, int32_t k, int32_t *out_ids, float *out_scores, int32_t *out_count,
+                        void *stream);
 
 /*
  * Masked in-batch / sampled softmax loss of the two towers (Sec. 5.1, Eq. 1

@@ -6,7 +6,8 @@ binding raises -- there is no CPU fallback.
 
 Entry points mirror the C ABI names:
   lr_index_create, lr_index_destroy, lr_index_device_bytes, lr_search, lr_filter_count,
-  lr_index_sync, lr_last_error_message, lr_version.
+  lr_index_sync, lr_merge_topk, lr_search_noalloc, lr_search_noalloc_status, lr_last_error_message,
+  lr_version; the loss (lr_score_*) and serving (Server) calls.  Row shards: ``shard``.
 """
 from __future__ import annotations
 
@@ -28,7 +29,8 @@ _METRIC = {"dot": LR_DOT, "cosine": LR_COSINE}
 _PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC}
 
 SYMBOLS = ("lr_index_create", "lr_index_destroy", "lr_index_device_bytes", "lr_search", "lr_search_ex",
-           "lr_filter_count", "lr_index_sync", "lr_last_error_message", "lr_version")
+           "lr_filter_count", "lr_index_sync", "lr_last_error_message", "lr_version", "lr_merge_topk",
+           "lr_search_noalloc", "lr_search_noalloc_status")
 
 
 class LRError(RuntimeError):
@@ -43,7 +45,7 @@ class lr_index_desc(ctypes.Structure):
                 ("bitsets", ctypes.c_void_p), ("post_off", ctypes.c_void_p), ("post_ids", ctypes.c_void_p),
                 ("n_dense_terms", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_k", ctypes.c_int32),
                 ("max_batch_terms", ctypes.c_int32), ("max_sparse_terms", ctypes.c_int32),
-                ("oversample", ctypes.c_int32)]
+                ("oversample", ctypes.c_int32), ("id_base", ctypes.c_int64)]
 
 
 class lr_filters(ctypes.Structure):
@@ -171,11 +173,13 @@ class Index:
 
 def lr_index_create(emb, vocab: int, *, bitsets=None, post_off=None, post_ids=None, n_dense_terms: int = -1,
                     metric: str = "cosine", max_batch: int = 256, max_k: int = 1000, max_batch_terms: int = 0,
-                    max_sparse_terms: int = 0, dtype: str = "f32", oversample: int = 0, stream=None) -> Index:
+                    max_sparse_terms: int = 0, dtype: str = "f32", oversample: int = 0, id_base: int = 0,
+                    stream=None) -> Index:
     """Build an index over job embeddings ``emb`` [n][dim] FP32 (torch or numpy, host or device) and
     per-job terms given either as job-major ``bitsets`` [n][ceil(vocab/64)] uint64 or as posting lists
     (``post_off`` int64[vocab+1], ``post_ids`` uint32[nnz]).  ``dtype`` "bf16" or "fp8" selects the
-    precision form (low-precision scan of ``oversample`` x K candidates, FP32 rescore, FP64 near ties)."""
+    precision form (low-precision scan of ``oversample`` x K candidates, FP32 rescore, FP64 near ties).
+    ``id_base`` makes the index a row shard: row r is returned as job id_base + r."""
     n, dim = int(emb.shape[0]), int(emb.shape[1])
     keep = []
     if isinstance(emb, np.ndarray):
@@ -191,7 +195,7 @@ def lr_index_create(emb, vocab: int, *, bitsets=None, post_off=None, post_ids=No
                       bitsets=_ptr(bitsets), post_off=_ptr(post_off), post_ids=_ptr(post_ids),
                       n_dense_terms=int(n_dense_terms), max_batch=int(max_batch), max_k=int(max_k),
                       max_batch_terms=int(max_batch_terms), max_sparse_terms=int(max_sparse_terms),
-                      oversample=int(oversample))
+                      oversample=int(oversample), id_base=int(id_base))
     h = ctypes.c_void_p()
     _check(_lib.lr_index_create(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "lr_index_create")
     del keep
@@ -298,6 +302,29 @@ def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out
     return out_ids, out_scores, out_count
 
 
+_lib.lr_merge_topk.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 4
+_lib.lr_merge_topk.restype = ctypes.c_int
+
+
+def lr_merge_topk(ids, scores, counts, k: int, *, out_ids=None, out_scores=None, out_count=None, stream=None):
+    """Exact merge of G per-part top-K lists: ids / scores [G][B][k_in] (each list sorted by score desc,
+    id asc), counts [G][B] int32, all CUDA tensors.  Returns (ids [B][k], scores [B][k], count [B])."""
+    import torch
+
+    G, B, k_in = (int(x) for x in ids.shape)
+    if tuple(scores.shape) != (G, B, k_in) or tuple(counts.shape) != (G, B):
+        raise ValueError("ids/scores must be [G][B][k_in] and counts [G][B]")
+    if ids.dtype != torch.int32 or scores.dtype != torch.float32 or counts.dtype != torch.int32:
+        raise ValueError("ids and counts must be int32, scores float32")
+    if out_ids is None:
+        out_ids = torch.empty((B, k), dtype=torch.int32, device=ids.device)
+        out_scores = torch.empty((B, k), dtype=torch.float32, device=ids.device)
+        out_count = torch.empty(B, dtype=torch.int32, device=ids.device)
+    _check(_lib.lr_merge_topk(_ptr(ids), _ptr(scores), _ptr(counts), G, B, k_in, int(k), _ptr(out_ids),
+                              _ptr(out_scores), _ptr(out_count), _stream_ptr(stream)), "lr_merge_topk")
+    return out_ids, out_scores, out_count
+
+
 def lr_filter_count(index: Index, filters, *, bitmap: bool = False, device=None, stream=None):
     """Exact CNF filter: pass counts int64[B] and, with ``bitmap=True``, the [B][ceil(n/32)] pass bitmap."""
     import torch
@@ -319,18 +346,52 @@ _lib.lr_search_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
 _lib.lr_search_noalloc.restype = ctypes.c_int
 
 
+def _need(cond: bool, what: str):
+    if not cond:
+        raise ValueError("lr_search_noalloc: " + what)
+
+
 def lr_search_noalloc(X, q, k: int, *, pass_bitmap=None, out_ids, out_scores, out_count=None, stream=None) -> None:
     """Allocation-free top-K (see include/lr.h): every argument is a caller-owned CUDA tensor.
 
     X [n][dim] and q [B][dim] FP32 with dim in {32, 64, 128, 256}; pass_bitmap [B][stride] int32 with
     stride a multiple of 8 covering ceil(n/256)*8 words, or None; outputs [B][k] int32 / FP32 and [B]
     int32.  Scores are plain inner products.  Nothing is allocated by the library or by this wrapper.
+    Shapes, dtypes and devices are checked here (ValueError); pointer kinds and alignment again in
+    the library.  lr_search_noalloc_status() reports a device-side error of the call.
     """
+    import torch
+
+    for name, t in (("X", X), ("q", q), ("out_ids", out_ids), ("out_scores", out_scores)):
+        _need(isinstance(t, torch.Tensor) and t.is_cuda, "%s must be a CUDA tensor" % name)
+    _need(X.dim() == 2 and q.dim() == 2, "X and q must be 2-D")
     n, dim = int(X.shape[0]), int(X.shape[1])
     B = int(q.shape[0])
-    stride = int(pass_bitmap.shape[1]) if pass_bitmap is not None else 0
+    _need(X.dtype == torch.float32 and q.dtype == torch.float32, "X and q must be float32")
+    _need(int(q.shape[1]) == dim, "q has %d columns, X has %d" % (int(q.shape[1]), dim))
+    _need(out_ids.dtype == torch.int32 and out_scores.dtype == torch.float32, "outputs must be int32 / float32")
+    for name, t in (("out_ids", out_ids), ("out_scores", out_scores)):
+        _need(t.dim() == 2 and int(t.shape[0]) >= B and int(t.shape[1]) == int(k), "%s must be [B][k]" % name)
+    if out_count is not None:
+        _need(isinstance(out_count, torch.Tensor) and out_count.is_cuda and out_count.dtype == torch.int32
+              and out_count.numel() >= B, "out_count must be a CUDA int32 tensor of at least B elements")
+    stride = 0
+    if pass_bitmap is not None:
+        _need(isinstance(pass_bitmap, torch.Tensor) and pass_bitmap.is_cuda and pass_bitmap.dim() == 2
+              and pass_bitmap.element_size() == 4 and int(pass_bitmap.shape[0]) >= B,
+              "pass_bitmap must be a CUDA [B][stride] tensor of 32-bit words")
+        stride = int(pass_bitmap.shape[1])
     _check(_lib.lr_search_noalloc(_ptr(X), n, dim, _ptr(q), B, _ptr(pass_bitmap), stride, int(k), _ptr(out_ids),
                                   _ptr(out_scores), _ptr(out_count), _stream_ptr(stream)), "lr_search_noalloc")
+
+
+_lib.lr_search_noalloc_status.argtypes = [ctypes.c_void_p]
+_lib.lr_search_noalloc_status.restype = ctypes.c_int
+
+
+def lr_search_noalloc_status(stream=None) -> None:
+    """Wait for the stream and raise LRError if the last lr_search_noalloc call recorded a device error."""
+    _check(_lib.lr_search_noalloc_status(_stream_ptr(stream)), "lr_search_noalloc_status")
 
 
 # ----------------------------------------------------------------------------- loss (Sec. 5.1, Eq. 1-2)

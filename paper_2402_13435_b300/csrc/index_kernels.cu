@@ -188,9 +188,11 @@ __global__ void k_prep_queries(const float *in, float *out, int B, int dim, int 
 }
 
 // Exact filter export (lr_filter_count): per 256-row group and query, the 8
-// pass words; counts per query and optional bitmap rows.
+// pass words; counts per query and optional bitmap rows (query q's row at
+// out_bitmap + (q - out_row0) * out_words).
 __global__ void __launch_bounds__(kScanThreads) k_filter_eval(const ScanArgs a, unsigned long long *pass_cnt,
-                                                              uint32_t *out_bitmap, int64_t out_words) {
+                                                              uint32_t *out_bitmap, int64_t out_words,
+                                                              int out_row0) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   uint32_t *sw = smem + (size_t)warp * (size_t)a.n_slots * 8;
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kScanThreads) k_filter_eval(const ScanArgs a, 
         my += (unsigned long long)__popc(pw[w]);
         const int64_t word = g * kGroupWords + w;
         if (out_bitmap != nullptr && word < out_words)
-          out_bitmap[(size_t)(a.q_base + lane) * (size_t)out_words + word] = pw[w];
+          out_bitmap[(size_t)(a.q_base + lane - out_row0) * (size_t)out_words + word] = pw[w];
       }
     }
     __syncwarp();
@@ -305,13 +307,13 @@ cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim,
 }
 
 cudaError_t launch_filter_eval(const ScanArgs &a, unsigned long long *pass_cnt, uint32_t *out_bitmap,
-                               int64_t out_words, int grid, cudaStream_t s) {
+                               int64_t out_words, int out_row0, int grid, cudaStream_t s) {
   const size_t smem = (size_t)(kScanThreads / 32) * (size_t)a.n_slots * 8 * sizeof(uint32_t);
   if (smem > 48 * 1024) {
     cudaError_t e = allow_dynamic_smem((const void *)k_filter_eval, (size_t)smem);
     if (e != cudaSuccess) return e;
   }
-  k_filter_eval<<<grid, kScanThreads, smem, s>>>(a, pass_cnt, out_bitmap, out_words);
+  k_filter_eval<<<grid, kScanThreads, smem, s>>>(a, pass_cnt, out_bitmap, out_words, out_row0);
   return cudaGetLastError();
 }
 

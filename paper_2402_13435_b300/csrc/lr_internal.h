@@ -149,6 +149,7 @@ struct SelectArgs {
   int32_t force_flag;            // 1: flag every query (exercise the exact fallback)
   int32_t unsorted;              // 1: final mode writes the top K in any order (the caller re-ranks them)
   uint32_t *err;                 // device error word
+  int64_t id_base;               // added to every written job id (row shards of a larger index)
 };
 
 // Raise a kernel's dynamic shared-memory cap to at least `bytes` on the
@@ -213,10 +214,14 @@ struct RescoreArgs {
   uint32_t *err;
   uint64_t *keys;          // [B][c_stride] FP32 keys of the candidates (written by the scoring launch)
   uint32_t *gmax;          // [B] bits of max_j sum_k |q_k x_jk| (zero before the scoring launch)
+  int64_t id_base;         // added to every written job id (row shards of a larger index)
 };
 // Two launches: the candidates' FP32 scores over several CTAs per query, then
 // per query the K-th key, the FP64 re-rank of the near-tie band and the output.
 cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s);
+// Exact merge of G per-part top-K lists per query (merge.cu).
+cudaError_t launch_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int G, int B, int k_in,
+                              int k, int32_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t s);
 // Masked softmax loss passes (loss.cu).  Row tiles of 128 over R, streamed
 // 64-row tiles of C; see loss.cu for the three modes.
 struct LossArgs {
@@ -279,7 +284,7 @@ cudaError_t launch_rows_to_index(const float *in, float *out, int64_t n, int dim
 cudaError_t launch_bitsets_to_termmajor(const uint64_t *bits, int64_t n, int vocab, uint32_t *out, int64_t n_words,
                                         cudaStream_t s);
 cudaError_t launch_filter_eval(const ScanArgs &a, unsigned long long *pass_cnt, uint32_t *out_bitmap,
-                               int64_t out_words, int grid, cudaStream_t s);
+                               int64_t out_words, int out_row0, int grid, cudaStream_t s);
 
 // ------------------------------------------------------------------ errors
 void set_error(const std::string &msg);

@@ -1,0 +1,126 @@
+// Exact merge of per-part top-K lists (Sec. 5.3, "Communication cost"): the
+// search is split by contiguous job-row ranges, each part returns its own top
+// K' rows per query, and one exchange brings the G lists of every query
+// together.  Because the parts hold disjoint jobs and every list is sorted by
+// the same total order (score desc, id asc), the merged top K is the unsharded
+// top K.
+//
+// Merge by rank: entry i of list g has exactly i entries of its own list above
+// it, and in every other list h the number of entries above it is found by a
+// binary search.  Its rank in the union is the sum, so each entry that ranks
+// below k writes itself straight to its output position -- no sort and no
+// block-wide barrier beyond staging.  Keys are the library's 64-bit (ordered
+// score, ~id) keys, so equal scores order by ascending id.
+#include "lr_internal.h"
+
+namespace lr {
+namespace {
+
+constexpr int kMergeThreads = 256;
+constexpr int kMergeMaxG = 64;
+
+__device__ __forceinline__ uint64_t list_key(const int32_t *ids, const float *sc, int i) {
+  return make_key(sc[i], (uint32_t)ids[i]);
+}
+
+// Entries of list (ids, sc, n) whose key is larger than `key` (the list is
+// sorted by descending key).
+__device__ __forceinline__ int count_above(const int32_t *ids, const float *sc, int n, uint64_t key) {
+  int lo = 0, hi = n;  // answer in [lo, hi]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (list_key(ids, sc, mid) > key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge_topk(const int32_t *ids, const float *scores,
+                                                              const int32_t *counts, int G, int B, int k_in, int k,
+                                                              int32_t *out_ids, float *out_scores,
+                                                              int32_t *out_count) {
+  const int b = blockIdx.x;
+  __shared__ int cnt[kMergeMaxG];
+  __shared__ int total;
+  if (threadIdx.x == 0) total = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    int c = counts[(size_t)g * B + b];
+    c = c < 0 ? 0 : (c > k_in ? k_in : c);
+    cnt[g] = c;
+    atomicAdd(&total, c);
+  }
+  __syncthreads();
+  const int kout = total < k ? total : k;
+  int32_t *oi = out_ids + (size_t)b * k;
+  float *os = out_scores + (size_t)b * k;
+  for (int i = kout + threadIdx.x; i < k; i += blockDim.x) {
+    oi[i] = -1;
+    os[i] = -INFINITY;
+  }
+  // every valid entry of every list: its rank in the union
+  for (int g = 0; g < G; ++g) {
+    const int32_t *gi = ids + ((size_t)g * B + b) * k_in;
+    const float *gs = scores + ((size_t)g * B + b) * k_in;
+    const int n = cnt[g] < k ? cnt[g] : k;  // entries past k of one list rank past k
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t key = list_key(gi, gs, i);
+      int rank = i;
+      for (int h = 0; h < G && rank < k; ++h) {
+        if (h == g) continue;
+        const int32_t *hi = ids + ((size_t)h * B + b) * k_in;
+        const float *hs = scores + ((size_t)h * B + b) * k_in;
+        const int nh = cnt[h] < k ? cnt[h] : k;
+        rank += count_above(hi, hs, nh, key);
+      }
+      if (rank < kout) {
+        oi[rank] = gi[i];
+        os[rank] = gs[i];
+      }
+    }
+  }
+  if (threadIdx.x == 0 && out_count) out_count[b] = kout;
+}
+
+}  // namespace
+
+cudaError_t launch_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int G, int B, int k_in,
+                              int k, int32_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_merge_topk<<<B, kMergeThreads, 0, s>>>(ids, scores, counts, G, B, k_in, k, out_ids, out_scores, out_count);
+  return cudaGetLastError();
+}
+
+}  // namespace lr
+
+using namespace lr;
+
+namespace {
+bool merge_dev_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" lr_status lr_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int32_t G,
+                                   int32_t B, int32_t k_in, int32_t k, int32_t *out_ids, float *out_scores,
+                                   int32_t *out_count, void *stream) {
+  if (!ids || !scores || !counts || !out_ids || !out_scores) return fail(LR_ERR_INVALID, "lr_merge_topk: null pointer");
+  if (G < 1 || G > kMergeMaxG) return fail(LR_ERR_INVALID, "lr_merge_topk: G must be in [1, 64]");
+  if (B < 1 || k_in < 1) return fail(LR_ERR_INVALID, "lr_merge_topk: B and k_in must be >= 1");
+  if (k < 1 || k > kMaxK || (int64_t)k > (int64_t)G * k_in)
+    return fail(LR_ERR_INVALID, "lr_merge_topk: k must be in [1, min(4096, G * k_in)]");
+  if (!merge_dev_ptr(ids) || !merge_dev_ptr(scores) || !merge_dev_ptr(counts) || !merge_dev_ptr(out_ids) ||
+      !merge_dev_ptr(out_scores) || (out_count && !merge_dev_ptr(out_count)))
+    return fail(LR_ERR_INVALID, "lr_merge_topk: every array must be device memory");
+  const cudaError_t e =
+      launch_merge_topk(ids, scores, counts, G, B, k_in, k, out_ids, out_scores, out_count, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lr_merge_topk");
+  return LR_OK;
+}

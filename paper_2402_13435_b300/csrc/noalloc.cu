@@ -13,10 +13,11 @@
 // the library holds it (about 10 MiB) until the process exits.  All calls share
 // it, so two calls that overlap on the GPU (different streams, or different
 // host threads) race on it and must be serialised by the caller.  Each call
-// clears what has to start at zero before its first kernel.
-#include <mutex>
+// clears what has to start at zero before its first kernel, the device error
+// word included: lr_search_noalloc_status reads that word for the last call.
 
 #include "lr_internal.h"
+#include "ptx.h"
 
 namespace lr {
 namespace {
@@ -56,10 +57,28 @@ constexpr size_t kScratchBytes = al(kOffCand + (size_t)kNaMaxB * kNaCandCap * 8)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Per-device address of the scratch array, taken once with that device current.
-std::mutex g_mu;
-unsigned char *g_addr[128] = {};
-int g_sms[128] = {};
+// Device address of the scratch array on the current device.  Looked up on
+// every call (no work is enqueued), so a module reloaded after a device reset
+// never leaves a stale address behind.
+lr_status scratch_address(unsigned char **base) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(lr_search_noalloc scratch)");
+  *base = static_cast<unsigned char *>(p);
+  return LR_OK;
+}
+
+// Device (or managed) memory?  cudaPointerGetAttributes allocates nothing.
+bool na_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool aligned(const void *p, uintptr_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
 // Filter tables for B one-term queries whose "terms" are the caller's bitmaps,
 // plus per-query K and threshold rank.
@@ -104,27 +123,26 @@ extern "C" lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t d
   if (pass_bitmap && (bitmap_stride_words < n_groups * kGroupWords || bitmap_stride_words % kGroupWords != 0))
     return fail(LR_ERR_INVALID, "lr_search_noalloc: bitmap row stride must be a multiple of 8 words and cover "
                                 "ceil(n_jobs/256)*8 words");
-  if (pass_bitmap && (reinterpret_cast<uintptr_t>(pass_bitmap) % 32 != 0))
+  if (pass_bitmap && !aligned(pass_bitmap, 32))
     return fail(LR_ERR_INVALID, "lr_search_noalloc: pass_bitmap must be 32-byte aligned");
+  // the scan copies rows in 16-byte pieces; queries and outputs are 4-byte words
+  if (!aligned(X, 16)) return fail(LR_ERR_INVALID, "lr_search_noalloc: X must be 16-byte aligned");
+  if (!aligned(q, 4) || !aligned(out_ids, 4) || !aligned(out_scores, 4) || (out_count && !aligned(out_count, 4)))
+    return fail(LR_ERR_INVALID, "lr_search_noalloc: q and the outputs must be 4-byte aligned");
+  // every array is read or written by kernels: a host pointer would fault the device
+  if (!na_device_ptr(X) || !na_device_ptr(q) || !na_device_ptr(out_ids) || !na_device_ptr(out_scores) ||
+      (out_count && !na_device_ptr(out_count)) || (pass_bitmap && !na_device_ptr(pass_bitmap)))
+    return fail(LR_ERR_INVALID, "lr_search_noalloc: X, q, pass_bitmap and the outputs must be device memory");
 
-  int dev = 0;
+  int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= 128) return fail(LR_ERR_UNSUPPORTED, "lr_search_noalloc: device ordinal >= 128");
-  unsigned char *base;
-  int sms;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  unsigned char *base = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      void *p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(lr_search_noalloc scratch)");
-      e = cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-      g_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    base = g_addr[dev];
-    sms = g_sms[dev];
+    const lr_status st = scratch_address(&base);
+    if (st != LR_OK) return st;
   }
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -268,4 +286,22 @@ extern "C" lr_status lr_search_noalloc(const float *X, int64_t n_jobs, int32_t d
   NA_CK(launch_select(fb, B, s));
 #undef NA_CK
   return LR_OK;
+}
+
+extern "C" lr_status lr_search_noalloc_status(void *stream) {
+  unsigned char *base = nullptr;
+  const lr_status st = scratch_address(&base);
+  if (st != LR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t e = 0;
+  cudaError_t ce = cudaMemcpyAsync(&e, base + kOffErr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_fail(ce, "lr_search_noalloc_status");
+  if (e == 0u) return LR_OK;
+  ce = cudaMemsetAsync(base + kOffErr, 0, sizeof(uint32_t), s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_fail(ce, "lr_search_noalloc_status");
+  if (e & kErrTimeout) return fail(LR_ERR_TIMEOUT, "lr_search_noalloc: a bounded device wait timed out");
+  return fail(LR_ERR_CUDA, "lr_search_noalloc: the selection state was inconsistent (device error word " +
+                               std::to_string(e) + ")");
 }

@@ -92,6 +92,7 @@ struct lr_index {
   bool owns_data = true;  // false for a serving slot: rows and term storage belong to the base index
   int device = 0, num_sms = 0;
   int64_t n = 0;
+  int64_t id_base = 0;  // global id of row 0 (row shards of a larger index)
   int dim = 0, d_pad = 0, metric = 0, vocab = 0;
   int64_t n_groups = 0, n_words = 0;
   float *X = nullptr;
@@ -498,7 +499,7 @@ int index_device(const lr_index *ix) { return ix->device; }
 
 extern "C" {
 
-int32_t lr_version(void) { return 100; }
+int32_t lr_version(void) { return 200; }
 
 const char *lr_last_error_message(void) { return g_last_error.c_str(); }
 
@@ -528,12 +529,15 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   if (d->max_batch < 1) return fail(LR_ERR_INVALID, "max_batch must be >= 1");
   if (d->max_k < 1 || d->max_k > kMaxK) return fail(LR_ERR_INVALID, "max_k must be in [1, 4096]");
   if ((int64_t)oversample * d->max_k > kMaxK) return fail(LR_ERR_INVALID, "oversample * max_k must be <= 4096");
+  if (d->id_base < 0 || d->id_base + d->n_jobs > 0x7FFFFFFFll)
+    return fail(LR_ERR_INVALID, "id_base must be >= 0 and id_base + n_jobs <= 2^31 - 1 (int32 job ids)");
 
   cudaStream_t s = (cudaStream_t)stream;
   lr_index *ix = new lr_index();
   LR_CK(cudaGetDevice(&ix->device));
   LR_CK(cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, ix->device));
   ix->n = d->n_jobs;
+  ix->id_base = d->id_base;
   ix->dim = d->dim;
   ix->d_pad = d->dim <= 32 ? 32 : d->dim <= 64 ? 64 : d->dim <= 128 ? 128 : 256;
   ix->metric = d->metric;
@@ -1151,6 +1155,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.force_flag = o.force_exact_fallback ? 1 : 0;
   fa.unsorted = lowp ? 1 : 0;  // the precision form re-ranks the candidates in FP32
   fa.err = ix->err;
+  fa.id_base = lowp ? 0 : ix->id_base;  // the precision form's rescore reads rows by local id
   LR_LAUNCH(launch_select(fa, B, s));
   // 4. exact fallback for flagged queries (each launch returns at once when none is flagged)
   for (int p = 0; p < kFbPasses; ++p) {
@@ -1204,6 +1209,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     ra.err = ix->err;
     ra.keys = ix->rs_keys;
     ra.gmax = ix->rs_gmax;
+    ra.id_base = ix->id_base;
     LR_LAUNCH(launch_rescore(ra, B, s));
   }
 
@@ -1272,14 +1278,10 @@ lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64
   if (!C.sparse_terms.empty()) LR_CK(expand_sparse_terms(ix, C, s));
   const int64_t out_words = (ix->n + 31) / 32;
   const bool bm_dev = out_bitmap && is_device_ptr(out_bitmap);
-  uint32_t *bm = nullptr;
-  if (out_bitmap) {
-    if (bm_dev) {
-      bm = out_bitmap;
-    } else {
-      LR_CK(cudaMallocAsync((void **)&bm, sizeof(uint32_t) * (size_t)B * out_words, s));
-    }
-  }
+  // A host bitmap is staged, one sub-batch of at most 32 rows at a time, in the
+  // index's tile-mask region (2 n_groups x 128 x 8 bytes >= 32 rows of n/8
+  // bytes), so the call allocates nothing (appendix "Memory Pre-Allocation").
+  uint32_t *stage_bm = reinterpret_cast<uint32_t *>(ix->tile_msg);
   for (const SubBatch &sb : C.subs) {
     ScanArgs a{};
     a.n = ix->n;
@@ -1292,13 +1294,18 @@ lr_status lr_filter_count(lr_index *index, const lr_filters *f, int32_t B, int64
     a.cl_slot = (const int32_t *)(ix->filt_d + sb.off_cs);
     a.n_groups = ix->n_groups;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ix->n_groups + 7) / 8, (int64_t)ix->num_sms * 4));
-    LR_CK(launch_filter_eval(a, ix->pass, bm, out_words, grid, s));
+    if (!out_bitmap || bm_dev) {
+      LR_CK(launch_filter_eval(a, ix->pass, out_bitmap, out_words, 0, grid, s));
+      continue;
+    }
+    if ((size_t)sb.nq * (size_t)out_words * 4 > (size_t)ix->tile_cap * 128 * sizeof(uint64_t))
+      return fail(LR_ERR_WORKSPACE, "lr_filter_count: bitmap staging area too small");
+    LR_CK(launch_filter_eval(a, ix->pass, stage_bm, out_words, sb.q_base, grid, s));
+    LR_CK(cudaMemcpyAsync(out_bitmap + (size_t)sb.q_base * out_words, stage_bm,
+                          sizeof(uint32_t) * (size_t)sb.nq * out_words, cudaMemcpyDeviceToHost, s));
+    LR_CK(cudaStreamSynchronize(s));  // the next sub-batch reuses the staging rows
   }
   LR_CK(cudaMemcpyAsync(out_pass, ix->pass, sizeof(int64_t) * B, cudaMemcpyDefault, s));
-  if (out_bitmap && !bm_dev) {
-    LR_CK(cudaMemcpyAsync(out_bitmap, bm, sizeof(uint32_t) * (size_t)B * out_words, cudaMemcpyDeviceToHost, s));
-    LR_CK(cudaFreeAsync(bm, s));
-  }
   if (!is_device_ptr(out_pass) || (out_bitmap && !bm_dev)) LR_CK(cudaStreamSynchronize(s));
   return LR_OK;
 }

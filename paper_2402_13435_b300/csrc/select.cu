@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
   for (int i = tid; i < a.k_stride; i += blockDim.x) {
     if (i < kp) {
       const uint64_t key = sort[i];
-      ids[i] = (int32_t)key_id(key);
+      ids[i] = (int32_t)((int64_t)key_id(key) + a.id_base);
       sc[i] = key_score((uint32_t)(key >> 32));
     } else {
       ids[i] = -1;
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
         bitonic_desc(sortb, P2);
     }
     for (int i = tid; i < n_above; i += blockDim.x) {
-      ids[i] = (int32_t)key_id(sortb[i]);
+      ids[i] = (int32_t)((int64_t)key_id(sortb[i]) + a.id_base);
       sc[i] = key_score((uint32_t)(sortb[i] >> 32));
     }
     if (n_above > 0) s_above_last = key_score((uint32_t)(sortb[n_above - 1] >> 32));
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
     const int need = K - n_above;
     for (int i = tid; i < need; i += blockDim.x) {
       const bool have = i < n_tie;
-      ids[n_above + i] = have ? ts.id[i] : -1;
+      ids[n_above + i] = have ? (int32_t)((int64_t)ts.id[i] + a.id_base) : -1;
       sc[n_above + i] = have ? fminf((float)ts.s[i], s_above_last) : -INFINITY;
     }
   }

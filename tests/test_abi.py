@@ -14,8 +14,12 @@ HEADER = os.path.join(ROOT, "include", "lr.h")
 
 @pytest.fixture(scope="module")
 def lib_path():
-    from paper_2402_13435_b300 import build
+    import importlib.util
 
+    spec = importlib.util.spec_from_file_location("_lr_cuda_build",
+                                                  os.path.join(ROOT, "paper_2402_13435_b300", "build.py"))
+    build = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(build)  # by path: the package itself loads the library being built
     return build.build()
 
 
@@ -45,7 +49,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_binding_loads_and_reports_version(lib_path):
     import paper_2402_13435_b300 as lr
 
-    assert lr.lr_version() == 100
+    assert lr.lr_version() == 200
     assert set(lr.SYMBOLS) <= set(declared_functions())
 
 
@@ -88,3 +92,28 @@ def test_key_encoding_host_logic(tmp_path):
                            os.path.join(ROOT, "tests", "cpp", "keys_host_test.cu"), "-o", str(exe)])
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0 and "OK" in r.stdout, r.stdout
+
+
+def test_noalloc_rejects_misaligned_and_host_pointers_before_any_device_work(lib_path):
+    """lr_search_noalloc checks alignment (pure arithmetic) and then pointer kinds (no GPU here, or on
+    a GPU machine plain host addresses): both must fail with LR_ERR_INVALID before any kernel is enqueued."""
+    import paper_2402_13435_b300 as lr
+
+    L = lr._lib
+    n, d, B, K = 1000, 64, 2, 10
+    host = np.zeros((n, d), dtype=np.float32)
+    qh = np.zeros((B, d), dtype=np.float32)
+    ids = np.zeros((B, K), dtype=np.int32)
+    sc = np.zeros((B, K), dtype=np.float32)
+    base = host.ctypes.data
+    rc = L.lr_search_noalloc(base + 4, n, d, qh.ctypes.data, B, None, 0, K, ids.ctypes.data, sc.ctypes.data, None,
+                             None)
+    assert rc == lr.LR_ERR_INVALID and "16-byte" in lr.lr_last_error_message()
+    rc = L.lr_search_noalloc(base - base % 16, n, d, qh.ctypes.data + 2, B, None, 0, K, ids.ctypes.data,
+                             sc.ctypes.data, None, None)
+    assert rc == lr.LR_ERR_INVALID and "4-byte" in lr.lr_last_error_message()
+    rc = L.lr_search_noalloc(base - base % 16, n, d, qh.ctypes.data, B, None, 0, K, ids.ctypes.data,
+                             sc.ctypes.data, None, None)
+    assert rc == lr.LR_ERR_INVALID and "device memory" in lr.lr_last_error_message()
+    with pytest.raises(ValueError):  # the binding refuses numpy arrays outright
+        lr.lr_search_noalloc(host, qh, K, out_ids=ids, out_scores=sc)

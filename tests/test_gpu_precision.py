@@ -146,3 +146,28 @@ def test_precision_tc_query_widths(lr, corpus, dtype, B):
     rec = oracle.recall_at_k([ids[b, :cnt[b]] for b in range(B)], [ref.ids[b, :ref.count[b]] for b in range(B)])
     assert rec >= 0.999, "recall@%d = %.5f" % (K, rec)
     check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+@pytest.mark.parametrize("plan", ["gemv", "tc"])
+def test_precision_k1000_oversample4(lr, corpus, dtype, plan):
+    """The measured configuration's shape at reduced N: K = 1000 with 4x oversampling, so the
+    low-precision selection sorts K' = 4,000 candidates (the 4096-key bitonic stage)."""
+    c = corpus
+    dim = 64
+    X = np.ascontiguousarray(c.X[:, :dim])
+    po, pid = c.postings()
+    B, K = 6, 1000
+    fg = datagen.filters(41, B, c.V, 1.1)
+    f = Filters.from_lists([fg.clauses(b) if b % 2 else [] for b in range(B)])
+    Q = datagen.query_embeddings(42, B, dim)
+    idx = lr.lr_index_create(X, c.V, post_off=po, post_ids=pid, n_dense_terms=256, metric="cosine", max_batch=8,
+                             max_k=1024, dtype=dtype, oversample=4)
+    try:
+        ids, sc, cnt = _run(lr, idx, Q, f, K, plan=plan)
+    finally:
+        lr.lr_index_destroy(idx)
+    ref = oracle.search(X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    rec = oracle.recall_at_k([ids[b, :cnt[b]] for b in range(B)], [ref.ids[b, :ref.count[b]] for b in range(B)])
+    assert rec >= 0.999, "recall@%d = %.5f" % (K, rec)
+    check_topk(ids, sc, cnt, ref, X, Q, c.job_off, c.job_terms, f, metric="cosine")

@@ -311,3 +311,48 @@ def test_k_sweep_across_select_and_sort_boundaries(lr, small, plan, dup):
     ref = oracle.search(X, c.job_off, c.job_terms, Q, f, ks)
     check_topk(ids, sc, cnt, ref, X, Q, c.job_off, c.job_terms, f)
     lr.lr_index_destroy(idx)
+
+
+@pytest.mark.parametrize("plan", ["gemv", "tc"])
+@pytest.mark.parametrize("dup", [False, True])
+def test_k_above_1024_up_to_the_cap(lr, small, plan, dup):
+    """K from 1025 to the 4096 cap: the bitonic stages for 2048 and 4096 keys and the radix select on
+    both sides of those sizes, with and without repeated scores (every score ~300 times)."""
+    c = small
+    ks = [1025, 2000, 2048, 2049, 4096, 3000]
+    B = len(ks)
+    X = np.ascontiguousarray(c.X[np.arange(c.n) % 97]) if dup else c.X
+    fm = _mixed_filters(37, B, c.V, c.df, c.n)
+    f = Filters.from_lists([fm.clauses(0)] + [[] for _ in range(B - 1)])
+    Q = datagen.query_embeddings(37, B, c.d)
+    idx = lr.lr_index_create(X, c.V, bitsets=c.bitsets(), metric="cosine", max_batch=8, max_k=4096)
+    ids, sc, cnt = _run(lr, idx, Q, f, ks, plan=plan)
+    ref = oracle.search(X, c.job_off, c.job_terms, Q, f, ks)
+    check_topk(ids, sc, cnt, ref, X, Q, c.job_off, c.job_terms, f)
+    lr.lr_index_destroy(idx)
+
+
+def test_filter_count_host_bitmap_matches_device_bitmap(lr, small):
+    """A host output bitmap is staged through the index's own memory, 32 rows at a time (no allocation):
+    40 filters take two sub-batches and must give the device rows and the oracle's pass matrix."""
+    c = small
+    B = 40
+    f = _mixed_filters(41, B, c.V, c.df, c.n)
+    po, pid = c.postings()
+    idx = lr.lr_index_create(c.X, c.V, post_off=po, post_ids=pid, n_dense_terms=32, metric="cosine", max_batch=64,
+                             max_k=16)
+    cnt_d, bm_d = lr.lr_filter_count(idx, f, bitmap=True)
+    torch.cuda.synchronize()
+    words = (c.n + 31) // 32
+    host_bm = np.zeros((B, words), dtype=np.uint32)
+    host_cnt = np.zeros(B, dtype=np.int64)
+    fc = lr.Filters.of(f).c()
+    rc = lr._lib.lr_filter_count(lr.ctypes.c_void_p(idx.handle), lr.ctypes.byref(fc), B, host_cnt.ctypes.data,
+                                 host_bm.ctypes.data, None)
+    assert rc == lr.LR_OK, lr.lr_last_error_message()
+    assert np.array_equal(host_bm, bm_d.cpu().numpy().view(np.uint32))
+    assert np.array_equal(host_cnt, cnt_d.cpu().numpy())
+    ref_cnt, ref_mat = oracle.filter(c.job_off, c.job_terms, c.n, f, want_matrix=True)
+    bits = ((host_bm[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(B, -1)[:, :c.n].astype(bool)
+    assert np.array_equal(bits, ref_mat) and np.array_equal(host_cnt, ref_cnt)
+    lr.lr_index_destroy(idx)

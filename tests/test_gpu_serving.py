@@ -104,3 +104,39 @@ def test_admission_limits(lr, setup):
         ids, sc, cnt, _ = srv.wait(srv.submit(Q, f, K), Q.shape[0], K)
         ia, sa, ca = lr.lr_search(idx, Q, f, K, plan="gemv")
         assert np.array_equal(ids, ia)
+
+
+def test_wait_with_zero_timeout_on_a_pending_request(lr, setup):
+    """lr_server_wait with a 0 ms limit on a request still queued behind others returns LR_ERR_TIMEOUT and
+    keeps the ticket: a later wait without a limit returns its result."""
+    c, idx, reqs = setup
+    big = [(datagen.query_embeddings(300 + i, 32, 64), datagen.filters(300 + i, 32, c.V, 1.1), 200)
+           for i in range(12)]
+    with lr.Server(idx, slots=1, max_queries=32, plan="tc") as srv:
+        tickets = [srv.submit(Q, f, K) for (Q, f, K) in big]
+        with pytest.raises(lr.LRError) as e:
+            srv.wait(tickets[-1], 32, 200, timeout_ms=0)
+        assert e.value.status == lr.LR_ERR_TIMEOUT
+        outs = [srv.wait(t, 32, 200) for t in tickets]
+    Q, f, K = big[-1]
+    ids, sc, cnt, _ = outs[-1]
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
+
+
+def test_serving_k2000(lr):
+    """Requests with K = 2000 (above the 1024-key sort stage) through the server, each equal to its
+    lr_search alone and within the oracle's tolerance."""
+    c = datagen.corpus(19, 40_000, 64, 1024, 12.0, 1.1)
+    idx = lr.lr_index_create(c.X, c.V, bitsets=c.bitsets(), metric="cosine", max_batch=16, max_k=2048)
+    reqs = [(datagen.query_embeddings(400 + i, B, 64), datagen.Filters.from_lists([[]] * B) if i % 2 else
+             datagen.filters(400 + i, B, c.V, 1.1), 2000) for i, B in enumerate((1, 3, 5, 2))]
+    with lr.Server(idx, slots=2, max_queries=8, plan="gemv") as srv:
+        tickets = [srv.submit(Q, f, K) for (Q, f, K) in reqs]
+        outs = [srv.wait(t, Q.shape[0], K) for t, (Q, f, K) in zip(tickets, reqs)]
+    for (Q, f, K), (ids, sc, cnt, _) in zip(reqs, outs):
+        alone = lr.lr_search(idx, Q, f, K, plan="gemv")
+        assert np.array_equal(ids, alone[0]) and np.array_equal(sc, alone[1])
+        ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+        check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
+    lr.lr_index_destroy(idx)
