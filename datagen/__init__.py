@@ -243,3 +243,19 @@ SMALL = dict(n=100_000, d=64, V=4096, lam=20.0, zipf_s=1.1, n_queries=256, k=100
              term_layout="bitsets")
 SCALE = dict(n=10_000_000, d=128, V=16384, lam=40.0, zipf_s=1.1, batches=(1, 32, 256, 1024),
              bands=(0.001, 0.01, 0.10, 0.50), k=1000, metric="cosine", term_layout="postings", n_dense=256)
+
+
+# ----------------------------------------------------------------------------- sign-bit projection
+def sign_projection(seed: int, d: int, nbits: int = 512, bin_size: int = 8):
+    """The random draws of the sign-bit quantisation (appendix "Quantization"): coordinates permuted,
+    cut into bins of ``bin_size``, one random sign per entry -- repeated with fresh permutations until
+    ``nbits`` bins exist (the rows have fewer coordinates than bits).  Returns idx int32 and sgn int8
+    (+1 / -1), each [nbits * bin_size], bin b holding entries b * bin_size .. (b + 1) * bin_size - 1."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x5167]))
+    total = nbits * bin_size
+    perms = []
+    while sum(p.size for p in perms) < total:
+        perms.append(rng.permutation(d))
+    idx = np.concatenate(perms)[:total].astype(np.int32)
+    sgn = np.where(rng.integers(0, 2, size=total) == 1, 1, -1).astype(np.int8)
+    return idx, sgn

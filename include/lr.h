@@ -289,6 +289,33 @@ lr_status lr_merge_topk(const int32_t *ids, const float *scores, const int32_t *
                         void *stream);
 
 /*
+ * Top K of dense score rows (appendix "Fast Top K Selection").  For each row b
+ * of scores the k largest (score desc, index asc), written as (index, score).
+ *
+ *   LR_TOPK_BUCKET  the appendix's selection: bucketised score = (int)(t * G) + G
+ *                   with t the score mapped from [lo, hi] onto [-1, 1] (scores
+ *                   outside go to the end buckets), buckets counted, the first
+ *                   bucket l from the top at which k scores are gathered, and
+ *                   only the scores in buckets >= l selected and sorted.
+ *   LR_TOPK_RADIX   no bounds: the library's radix select over every score.
+ * Both return the exact top k (the bucket pass only narrows the candidates).
+ *
+ *   scores      device [B][row_stride] FP32, finite; the first n of each row.
+ *   k           1 .. 4096; out_ids [B][k] int32 (index in the row, -1 past n)
+ *               and out_scores [B][k] FP32 (-inf past n), device.
+ *   lo, hi, granularity   bucket method: score bounds and G (1 .. 2048; the
+ *               paper uses 100 on cosine scores, lo = -1, hi = 1).
+ *   out_threshold_bucket  nullable device [B]: the bucket l of each row.
+ *   workspace   device, lr_topk_workspace_size(B, n) bytes, caller-owned.
+ * Stream-ordered; allocates nothing.
+ */
+typedef enum lr_topk_method { LR_TOPK_BUCKET = 0, LR_TOPK_RADIX = 1 } lr_topk_method;
+size_t lr_topk_workspace_size(int32_t B, int64_t n);
+lr_status lr_topk(const float *scores, int32_t B, int64_t n, int64_t row_stride, int32_t k, int32_t method, float lo,
+                  float hi, int32_t granularity, int32_t *out_ids, float *out_scores, int32_t *out_threshold_bucket,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * Masked in-batch / sampled softmax loss of the two towers (Sec. 5.1, Eq. 1
  * and Eq. 2) and its gradients, on the tensor cores (BF16 operands, FP32
  * accumulation), recomputing the B x M logits instead of storing them.

@@ -10,6 +10,11 @@ Contents, each written from the paper's definitions:
   * ``filter``      -- pass counts / pass matrix of the CNF predicate.
   * ``messenger``   -- the (rowId, batchId) list of a batch (appendix "Message Passing between Layers",
                        "Batch Inference"), ordered by rowId then batchId.
+  * ``topk_scores`` -- top-k of dense score rows by (score desc, index asc) (appendix "Fast Top K
+                       Selection" defines the goal; the oracle sorts instead of bucketing).
+  * ``sign_codes``, ``sign_search`` -- the sign-bit pre-selection of the appendix "Quantization"
+                       (Eq. 4 agreement count, whole score levels kept down to quantK jobs) followed by the
+                       exact FP64 rescoring of the kept jobs.
   * ``recall_at_k`` -- Eq. (recall@k) of Sec. 6.2: mean over queries of |R_i ∩ A_i| / |A_i|.
   * ``softmax_loss`` -- the in-batch / sampled softmax loss of Sec. 5.1 (P(J_j|S_i) = e^{z_ij}/sum_k e^{z_ik},
                        L = -(1/N) sum_i log P(J_pos(i) | S_i)) with the term mask setting failing jobs to
@@ -34,7 +39,8 @@ def build(force: bool = False) -> str:
     """Compile lr_oracle.c (plain C, OpenMP over queries) into liblr_oracle.so."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", tmp,
+                               "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -55,6 +61,11 @@ def _load():
         L.oracle_pair_scores.restype = ctypes.c_int
         L.oracle_pair_pass.argtypes = [i64, vp, vp, i32, vp, vp, vp, i64, vp, vp, vp]
         L.oracle_pair_pass.restype = ctypes.c_int
+        L.oracle_sign_codes.argtypes = [i64, i32, vp, i32, i32, vp, vp, vp]
+        L.oracle_sign_codes.restype = ctypes.c_int
+        L.oracle_sign_search.argtypes = [i64, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32, i32, vp, vp, i32, vp,
+                                         i64, vp, vp, vp, vp]
+        L.oracle_sign_search.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
@@ -152,6 +163,68 @@ def pair_pass(job_off, job_terms, n: int, f, qi, ji) -> np.ndarray:
     if rc:
         raise RuntimeError("oracle_pair_pass: index out of range")
     return out.astype(bool)
+
+
+def topk_scores(scores, k: int):
+    """Top k of each row of a dense score matrix by (score desc, index asc) -- the plain definition that
+    the appendix "Fast Top K Selection" reaches with buckets: a full stable order of the row
+    (numpy lexsort), first min(k, n).  Returns (ids int64 [B][k], scores float64 [B][k]) padded with
+    (-1, -inf)."""
+    S = np.asarray(scores)
+    B, n = S.shape
+    ids = np.full((B, k), -1, dtype=np.int64)
+    out = np.full((B, k), -np.inf, dtype=np.float64)
+    idx = np.arange(n)
+    for b in range(B):
+        order = np.lexsort((idx, -S[b].astype(np.float64)))[:k]
+        ids[b, :order.size] = order
+        out[b, :order.size] = S[b][order]
+    return ids, out
+
+
+def sign_codes(X, idx, sgn, bin_size: int) -> np.ndarray:
+    """Sign codes of the rows of X (appendix "Quantization"): uint64 [n][nbits/64], bit b set iff
+    sum_m sgn[b,m] * x[idx[b,m]] (FP32, m in order) > 0; idx / sgn are [nbits * bin_size]."""
+    X = _c(X, np.float32)
+    idx, sgn = _c(idx, np.int32), _c(sgn, np.int8)
+    nbits = idx.size // int(bin_size)
+    if nbits % 64 or idx.size != sgn.size:
+        raise ValueError("projection must describe a multiple of 64 bits")
+    out = np.zeros((X.shape[0], nbits // 64), dtype=np.uint64)
+    if _load().oracle_sign_codes(X.shape[0], X.shape[1], _p(X), nbits, int(bin_size), _p(idx), _p(sgn), _p(out)):
+        raise ValueError("projection index out of range")
+    return out
+
+
+def sign_agree(a, b) -> np.ndarray:
+    """Eq. 4 for code rows a [m][W] against b [W] (or [m][W]): matching bit positions."""
+    a = np.asarray(a, dtype=np.uint64)
+    x = np.bitwise_not(np.bitwise_xor(a, np.asarray(b, dtype=np.uint64)))
+    return np.unpackbits(x.view(np.uint8), axis=-1).reshape(x.shape[:-1] + (-1,)).sum(axis=-1)
+
+
+def sign_search(X, job_off, job_terms, Q, f, k, codes, qcodes, quant_k, cap: int, metric: str = "cosine"):
+    """Filtered top-K with sign-bit pre-selection (see lr_oracle.c).  quant_k: int or [B] candidates wanted
+    per query.  Returns (SearchResult, ncand int64 [B])."""
+    X, Q = _c(X, np.float32), _c(Q, np.float32)
+    n, d = X.shape
+    B = Q.shape[0]
+    ks = np.full(B, int(k), dtype=np.int32) if np.isscalar(k) else _c(k, np.int32)
+    kmax = int(max(int(ks.max()), 1))
+    qk = np.full(B, int(quant_k), dtype=np.int64) if np.isscalar(quant_k) else _c(quant_k, np.int64)
+    codes, qcodes = _c(codes, np.uint64), _c(qcodes, np.uint64)
+    job_off, job_terms = _c(job_off, np.int64), _c(job_terms, np.int32)
+    q_off, c_off, terms = _c(f.q_off, np.int32), _c(f.c_off, np.int32), _c(f.terms, np.uint32)
+    ids = np.empty((B, kmax), dtype=np.int64)
+    sc = np.empty((B, kmax), dtype=np.float64)
+    cnt = np.empty(B, dtype=np.int64)
+    ncand = np.empty(B, dtype=np.int64)
+    rc = _load().oracle_sign_search(n, d, _p(X), _p(job_off), _p(job_terms), B, _p(Q), _p(q_off), _p(c_off),
+                                    _p(terms), _p(ks), kmax, METRICS[metric], _p(codes), _p(qcodes),
+                                    codes.shape[1] * 64, _p(qk), int(cap), _p(ids), _p(sc), _p(cnt), _p(ncand))
+    if rc:
+        raise RuntimeError("oracle_sign_search failed")
+    return SearchResult(ids, sc, cnt, ncand), ncand
 
 
 def recall_at_k(retrieved: Sequence[Sequence[int]], relevant: Sequence[Sequence[int]]) -> float:

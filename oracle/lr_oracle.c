@@ -286,3 +286,123 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------ sign-bit pre-selection -- */
+/*
+ * Sign codes (appendix "Quantization", Sec. 5.3: a quantisation akin to
+ * OP+ORP).  The caller gives the random projection: sample b of a row is
+ *     s_b = sum_{m < bin} sgn[b * bin + m] * x[idx[b * bin + m]],
+ * added in FP32 in the order m = 0, 1, ..., and bit b of the code is 1 iff
+ * s_b > 0 (bit b % 64 of word b / 64).  The projection is the appendix's:
+ * coordinates permuted, cut into bins, each entry multiplied by a random sign
+ * and the bin summed (several permutations when the row has fewer coordinates
+ * than bits).
+ */
+int oracle_sign_codes(int64_t n, int32_t d, const float *X, int32_t nbits, int32_t bin, const int32_t *idx,
+                      const int8_t *sgn, uint64_t *codes) {
+  const int32_t W = nbits / 64;
+  for (int64_t i = 0; i < (int64_t)nbits * bin; ++i)
+    if (idx[i] < 0 || idx[i] >= d) return 1;
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < n; ++j) {
+    const float *x = X + (size_t)j * (size_t)d;
+    uint64_t *c = codes + (size_t)j * (size_t)W;
+    for (int32_t w = 0; w < W; ++w) c[w] = 0;
+    for (int32_t b = 0; b < nbits; ++b) {
+      float s = 0.0f;
+      for (int32_t m = 0; m < bin; ++m) {
+        const float v = x[idx[(size_t)b * bin + m]];
+        const float t = sgn[(size_t)b * bin + m] > 0 ? v : -v;
+        s = s + t;
+      }
+      if (s > 0.0f) c[b / 64] |= (uint64_t)1 << (b % 64);
+    }
+  }
+  return 0;
+}
+
+/* Eq. 4: the number of positions at which two codes hold the same bit. */
+static int32_t sign_agree(const uint64_t *a, const uint64_t *b, int32_t W) {
+  int32_t s = 0;
+  for (int32_t w = 0; w < W; ++w) s += __builtin_popcountll(~(a[w] ^ b[w]));
+  return s;
+}
+
+/*
+ * Filtered search with sign-bit pre-selection: for each query the passing jobs
+ * are scored by Eq. 4 against the query's code; the pre-selection keeps whole
+ * score levels from the top, down to the highest level t at which at least
+ * Q = min(quant_k[b], #passing) jobs are kept (one level higher when that set
+ * would exceed `cap` jobs); the kept jobs are scored exactly (FP64 dot or
+ * cosine, as oracle_search) and the top k[b] by (score desc, id asc) returned.
+ * out_ncand[b] = the number of jobs kept by the pre-selection.
+ */
+int oracle_sign_search(int64_t n, int32_t d, const float *X, const int64_t *job_off, const int32_t *job_terms,
+                       int32_t B, const float *Q, const int32_t *q_off, const int32_t *c_off, const uint32_t *terms,
+                       const int32_t *k, int32_t kmax, int32_t metric, const uint64_t *codes,
+                       const uint64_t *qcodes, int32_t nbits, const int64_t *quant_k, int64_t cap,
+                       int64_t *out_ids, double *out_scores, int64_t *out_count, int64_t *out_ncand) {
+  termsets_t S;
+  if (termsets_build(&S, n, job_off, job_terms)) return 1;
+  const int32_t W = nbits / 64;
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t b = 0; b < B; ++b) {
+    cnf_t C;
+    int32_t *level = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *hist = (int64_t *)calloc((size_t)nbits + 2, sizeof(int64_t));
+    scored_t *all = (scored_t *)malloc(sizeof(scored_t) * (size_t)(n > 0 ? n : 1));
+    if (!level || !hist || !all || cnf_build(&C, b, q_off, c_off, terms)) {
+      err = 1;
+      free(level); free(hist); free(all);
+      continue;
+    }
+    int64_t P = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      level[j] = -1;
+      if (!cnf_pass(&C, &S, j)) continue;
+      level[j] = sign_agree(codes + (size_t)j * W, qcodes + (size_t)b * W, W);
+      hist[level[j]] += 1;
+      ++P;
+    }
+    const int64_t want = quant_k[b] < P ? quant_k[b] : P;
+    int32_t t = nbits + 1;  /* keep nothing when want == 0 */
+    int64_t kept = 0;
+    if (want > 0) {
+      int64_t cum = 0;
+      for (t = nbits; t >= 0; --t) {
+        cum += hist[t];
+        if (cum >= want) break;
+      }
+      kept = cum;
+      if (kept > cap) { kept -= hist[t]; t += 1; }
+    }
+    const float *q = Q + (size_t)b * (size_t)d;
+    const double qn = (metric == 1) ? sqrt(dot64(q, q, d)) : 1.0;
+    int64_t m = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (level[j] < t) continue;
+      const float *x = X + (size_t)j * (size_t)d;
+      double s = dot64(q, x, d);
+      if (metric == 1) {
+        const double xn = sqrt(dot64(x, x, d));
+        s = (qn > 0.0 && xn > 0.0) ? s / (qn * xn) : 0.0;
+      }
+      all[m].s = s;
+      all[m].id = j;
+      ++m;
+    }
+    qsort(all, (size_t)m, sizeof(scored_t), cmp_scored);
+    const int64_t kk = k[b] < m ? k[b] : m;
+    for (int64_t i = 0; i < kmax; ++i) {
+      out_ids[(size_t)b * (size_t)kmax + (size_t)i] = (i < kk) ? all[i].id : -1;
+      out_scores[(size_t)b * (size_t)kmax + (size_t)i] = (i < kk) ? all[i].s : -INFINITY;
+    }
+    out_count[b] = kk;
+    out_ncand[b] = m;
+    cnf_free(&C);
+    free(level); free(hist); free(all);
+  }
+  termsets_free(&S);
+  return err;
+}

@@ -30,7 +30,7 @@ _PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC}
 
 SYMBOLS = ("lr_index_create", "lr_index_destroy", "lr_index_device_bytes", "lr_search", "lr_search_ex",
            "lr_filter_count", "lr_index_sync", "lr_last_error_message", "lr_version", "lr_merge_topk",
-           "lr_search_noalloc", "lr_search_noalloc_status")
+           "lr_search_noalloc", "lr_search_noalloc_status", "lr_topk", "lr_topk_workspace_size")
 
 
 class LRError(RuntimeError):
@@ -323,6 +323,42 @@ def lr_merge_topk(ids, scores, counts, k: int, *, out_ids=None, out_scores=None,
     _check(_lib.lr_merge_topk(_ptr(ids), _ptr(scores), _ptr(counts), G, B, k_in, int(k), _ptr(out_ids),
                               _ptr(out_scores), _ptr(out_count), _stream_ptr(stream)), "lr_merge_topk")
     return out_ids, out_scores, out_count
+
+
+LR_TOPK_BUCKET, LR_TOPK_RADIX = 0, 1
+_TOPK = {"bucket": LR_TOPK_BUCKET, "radix": LR_TOPK_RADIX}
+_lib.lr_topk_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int64]
+_lib.lr_topk_workspace_size.restype = ctypes.c_size_t
+_lib.lr_topk.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                         ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_void_p,
+                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+_lib.lr_topk.restype = ctypes.c_int
+
+
+def topk_workspace(B: int, n: int, device=None):
+    import torch
+
+    return torch.empty(int(_lib.lr_topk_workspace_size(int(B), int(n))), dtype=torch.uint8,
+                       device=device if device is not None else "cuda")
+
+
+def lr_topk(scores, k: int, *, method: str = "bucket", lo: float = -1.0, hi: float = 1.0, granularity: int = 100,
+            workspace=None, out_ids=None, out_scores=None, threshold_bucket=None, stream=None):
+    """Exact top k of each row of ``scores`` [B][n] (CUDA FP32): the appendix's bucket selection or the
+    library's radix selection.  Returns (ids [B][k] int32, scores [B][k] FP32)."""
+    import torch
+
+    if scores.dim() != 2 or scores.dtype != torch.float32 or not scores.is_cuda or scores.stride(1) != 1:
+        raise ValueError("scores must be a CUDA float32 [B][n] tensor with unit column stride")
+    B, n = int(scores.shape[0]), int(scores.shape[1])
+    ws = workspace if workspace is not None else topk_workspace(B, n, scores.device)
+    if out_ids is None:
+        out_ids = torch.empty((B, k), dtype=torch.int32, device=scores.device)
+        out_scores = torch.empty((B, k), dtype=torch.float32, device=scores.device)
+    _check(_lib.lr_topk(scores.data_ptr(), B, n, int(scores.stride(0)), int(k), _TOPK[method], float(lo), float(hi),
+                        int(granularity), _ptr(out_ids), _ptr(out_scores), _ptr(threshold_bucket), _ptr(ws),
+                        ws.numel(), _stream_ptr(stream)), "lr_topk")
+    return out_ids, out_scores
 
 
 def lr_filter_count(index: Index, filters, *, bitmap: bool = False, device=None, stream=None):

@@ -387,3 +387,106 @@ def test_loss_temperature_closed_form_two_columns(inv_tau):
     assert np.allclose(dJ[1], inv_tau * p_neg * Q[0], rtol=1e-12, atol=1e-15)
     assert np.allclose(dJ[0], -inv_tau * p_neg * Q[0], rtol=1e-12, atol=1e-15)
     assert not np.any(dJ[2])
+
+
+# ------------------------------------------------------------------ top-k of dense score rows
+def test_topk_scores_hand_case_and_against_the_search_oracle():
+    """oracle.topk_scores (numpy lexsort) on a hand case with ties, and against oracle.search (C qsort) on
+    an unfiltered index scored by a basis query, whose scores are one column of the rows."""
+    ids, sc = oracle.topk_scores(np.asarray([[0.5, -1.0, 0.5, 2.0, 0.25]], dtype=np.float32), 4)
+    assert ids.tolist() == [[3, 0, 2, 4]] and sc.tolist() == [[2.0, 0.5, 0.5, 0.25]]
+    ids, sc = oracle.topk_scores(np.asarray([[1.0, 3.0]], dtype=np.float32), 4)
+    assert ids.tolist() == [[1, 0, -1, -1]] and np.isneginf(sc[0, 2:]).all()
+    rng = np.random.default_rng(21)
+    n, d = 3000, 6
+    X = (rng.integers(-8, 9, size=(n, d)) / 8.0).astype(np.float32)   # many equal values
+    off, terms, _ = _corpus_from_sets([set() for _ in range(n)])
+    Q = np.eye(d, dtype=np.float32)[:3]
+    res = oracle.search(X, off, terms, Q, Filters.from_lists([[]] * 3), 250, metric="dot")
+    ids, sc = oracle.topk_scores(X[:, :3].T.copy(), 250)
+    assert np.array_equal(ids, res.ids) and np.array_equal(sc, res.scores)
+
+
+# ------------------------------------------------------------------ sign-bit pre-selection (appendix "Quantization")
+def test_sign_codes_single_coordinate_bins_read_the_signs():
+    """Bins of one entry with sign +1: bit b is just x[idx[b]] > 0 (and with sign -1, x[idx[b]] < 0)."""
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((50, 16)).astype(np.float32)
+    X[3, :] = 0.0                                       # zero sums give 0 bits
+    idx = np.tile(np.arange(16, dtype=np.int32), 8)     # 128 bits
+    for s in (1, -1):
+        sgn = np.full(128, s, dtype=np.int8)
+        codes = oracle.sign_codes(X, idx, sgn, 1)
+        bits = np.unpackbits(codes.view(np.uint8), axis=1, bitorder="little").astype(bool)
+        assert np.array_equal(bits, (s * X[:, idx]) > 0)
+
+
+def test_sign_codes_exact_on_dyadic_rows():
+    """Dyadic entries make every FP32 partial sum exact: each bit equals the sign of the integer sum."""
+    rng = np.random.default_rng(32)
+    d, nbits, b = 24, 192, 5
+    Xi = rng.integers(-4, 5, size=(80, d))
+    X = (Xi / 8.0).astype(np.float32)
+    idx = rng.integers(0, d, size=nbits * b).astype(np.int32)
+    sgn = np.where(rng.integers(0, 2, nbits * b) == 1, 1, -1).astype(np.int8)
+    codes = oracle.sign_codes(X, idx, sgn, b)
+    sums = (Xi[:, idx] * sgn).reshape(80, nbits, b).sum(axis=2)
+    bits = np.unpackbits(codes.view(np.uint8), axis=1, bitorder="little").astype(bool)
+    assert np.array_equal(bits, sums > 0)
+
+
+def test_sign_agreement_count_eq4():
+    a = np.asarray([[0b1011, 0]], dtype=np.uint64)
+    b = np.asarray([0b0110, 0], dtype=np.uint64)
+    # positions 0 and 3 differ (1 vs 0), positions 1 and 2: equal and different -> 128 - 3 agreements
+    assert oracle.sign_agree(a, b).tolist() == [125]
+    rng = np.random.default_rng(33)
+    c = rng.integers(0, 2 ** 63, size=(10, 8), dtype=np.int64).astype(np.uint64)
+    assert np.all(oracle.sign_agree(c, c[0])[:1] == 512)
+    assert oracle.sign_agree(c[:1], np.bitwise_not(c[0])).tolist() == [0]
+    ham = [sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(r, c[0])) for r in c]
+    assert oracle.sign_agree(c, c[0]).tolist() == [512 - h for h in ham]
+
+
+def _sign_case(seed, n=4000, d=32, V=256, B=6):
+    c = datagen.corpus(seed, n, d, V, 10.0, 1.1)
+    f = datagen.filters(seed + 1, B, V, 1.1)
+    Q = datagen.query_embeddings(seed + 2, B, d)
+    idx, sgn = datagen.sign_projection(seed, d, 512, 8)
+    return c, f, Q, oracle.sign_codes(c.X, idx, sgn, 8), oracle.sign_codes(Q, idx, sgn, 8)
+
+
+def test_sign_search_without_pruning_is_the_plain_search():
+    """quantK at least the corpus size keeps every passing job: the result is oracle.search's."""
+    c, f, Q, cx, cq = _sign_case(34)
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, 40)
+    got, ncand = oracle.sign_search(c.X, c.job_off, c.job_terms, Q, f, 40, cx, cq, c.n, 10 * c.n)
+    assert np.array_equal(got.ids, ref.ids) and np.array_equal(got.scores, ref.scores)
+    assert np.array_equal(ncand, ref.pass_count)
+
+
+def test_sign_search_levels_by_brute_force():
+    """The kept set is every passing job whose Eq. 4 score reaches the highest level t with at least
+    min(quantK, #passing) jobs at or above it (one level up when that set would pass the cap), and the
+    result is the exact top K of the kept set."""
+    c, f, Q, cx, cq = _sign_case(35)
+    _, mat = oracle.filter(c.job_off, c.job_terms, c.n, f, want_matrix=True)
+    for qk, cap in ((50, 10 ** 9), (300, 10 ** 9), (300, 320), (1, 10 ** 9)):
+        got, ncand = oracle.sign_search(c.X, c.job_off, c.job_terms, Q, f, 20, cx, cq, qk, cap, metric="dot")
+        for b in range(Q.shape[0]):
+            lev = oracle.sign_agree(cx, cq[b])
+            passing = np.nonzero(mat[b])[0]
+            want = min(qk, passing.size)
+            kept = np.zeros(0, dtype=np.int64)
+            if want:
+                t = max(t for t in range(513) if (lev[passing] >= t).sum() >= want)
+                if (lev[passing] >= t).sum() > cap:
+                    t += 1
+                kept = passing[lev[passing] >= t]
+            assert ncand[b] == kept.size
+            s = (Q[b].astype(np.float64) * c.X[kept].astype(np.float64)).sum(axis=1)
+            order = np.lexsort((kept, -s))[:20]
+            m = order.size
+            assert got.ids[b, :m].tolist() == kept[order].tolist()
+            assert np.all(got.ids[b, m:] == -1)
+            assert ncand[b] <= max(cap, 0) or want == 0
