@@ -57,10 +57,12 @@ def parse():
     #   --form serve  continuous batching over a resident 20M x 128 BF16 index, Poisson request streams
     #   --form sweep  selectivity sweep: each band alone at batch sizes --sweep-batches, per-point roofline
     #   --form topk   appendix "Fast Top K Selection": top 2,000 of 1,000,000 scores, bucket vs radix vs sort
-    p.add_argument("--form", choices=("search", "loss", "serve", "sweep", "topk"), default="search")
+    p.add_argument("--form", choices=("search", "loss", "serve", "sweep", "topk", "sign"), default="search")
     p.add_argument("--topk-n", type=int, default=1_000_000)
     p.add_argument("--topk-k", type=int, default=2000)
     p.add_argument("--topk-rows", type=int, default=1)
+    #   --form sign   sign-bit pre-selection (512-bit codes, quantK = quant-mult x K) vs the plain search
+    p.add_argument("--quant-mult", type=int, default=200)
     p.add_argument("--sweep-batches", default="1,32,256,1024")
     p.add_argument("--loss-b", type=int, default=4096)
     p.add_argument("--loss-m", type=int, default=4096 + 16384)
@@ -196,7 +198,7 @@ class ClockSampler:
             vis = [x.strip() for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
             dev = vis[self.gpu] if vis and self.gpu < len(vis) else str(self.gpu)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, "--query-gpu=" + fields,
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             return
@@ -240,7 +242,7 @@ class ClockSampler:
         window = "timed region"
         if len(got) < 3 and self.load_end is not None:
             got = [x for x in self.samples if self.window[0] <= x[3] <= self.load_end]
-            window = "timed region + the synchronised steps of the same workload that follow it"
+            window = "timed region + the same workload's steps that follow it (latency and end-to-end steps)"
         if not got:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
                     "source": self.source, "errors": self.errors[:3]}
@@ -392,6 +394,36 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_e2e(lr, idx, wl, args, world):
+    """The same metric end to end through lr_search with pinned host query and output buffers: every
+    step copies its queries and filters to the device and its rows back inside the timed region."""
+    import torch
+    import torch.distributed as dist
+
+    nb = len(wl["filters"])
+    B, K = args.batch, args.k
+    hq = [torch.from_numpy(np.ascontiguousarray(wl["Q"][j])).pin_memory() for j in range(nb)]
+    h_ids = torch.empty((B, K), dtype=torch.int32).pin_memory()
+    h_sc = torch.empty((B, K), dtype=torch.float32).pin_memory()
+    h_cnt = torch.empty(B, dtype=torch.int32).pin_memory()
+    for i in range(args.warmup):
+        lr.lr_search(idx, hq[i % nb], wl["filters"][i % nb], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        j = i % nb
+        lr.lr_search(idx, hq[j], wl["filters"][j], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    f0 = wl["filters"][0]
+    h2d = B * args.dim * 4 + f0.q_off.nbytes + f0.c_off.nbytes + f0.terms.nbytes
+    d2h = B * K * 8 + B * 4
+    return {"value": whole_job_rate(B * args.steps, world, dt), "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -460,6 +492,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             lat.append(e0.elapsed_time(e1))
         clk.mark(h0, h1, time.perf_counter())
+        e2e = None if args.no_e2e else run_e2e(lr, idx, wl, args, world)
+        clk.mark(h0, h1, time.perf_counter())
     step_ms = lat
     ms = ev0.elapsed_time(ev1)
     args.plan_used = probes[0].plan if probes[0].plan in ("gemv", "tc") else None
@@ -491,29 +525,6 @@ def run_ours(args):
                           "frac_e_plus_p_over_step = (E + term bytes P) / whole step time",
             "peak_kind": peak_kind}
 
-    # ---- end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        hq = [torch.from_numpy(np.ascontiguousarray(wl["Q"][j])).pin_memory() for j in range(nb)]
-        h_ids = torch.empty((B, K), dtype=torch.int32).pin_memory()
-        h_sc = torch.empty((B, K), dtype=torch.float32).pin_memory()
-        h_cnt = torch.empty(B, dtype=torch.int32).pin_memory()
-        for i in range(args.warmup):
-            lr.lr_search(idx, hq[i % nb], wl["filters"][i % nb], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            j = i % nb
-            lr.lr_search(idx, hq[j], wl["filters"][j], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
-        torch.cuda.synchronize()
-        dt = max_over_ranks(time.perf_counter() - t0, world)
-        f0 = wl["filters"][0]
-        h2d = B * args.dim * 4 + f0.q_off.nbytes + f0.c_off.nbytes + f0.terms.nbytes
-        d2h = B * K * 8 + B * 4
-        e2e = {"value": whole_job_rate(B * args.steps, world, dt), "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
 
     # ---- CPU oracle baseline and parity of the sampled queries
     cpu = None
@@ -724,6 +735,9 @@ def run_sweep(args):
             steps = max(3, min(args.steps, 10 if B >= 256 else 30))
             probes = [lr.Probe(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                       for _ in range(steps)]
+            for p in probes:  # materialise the event handles the library records
+                p.start.record()
+                p.stop.record()
             for _ in range(3):
                 lr.lr_search(idx, Qd, f, args.k, out_ids=oi, out_scores=osc, out_count=oc, plan=args.plan)
             torch.cuda.synchronize()
@@ -842,6 +856,87 @@ def run_topk(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sign(args):
+    """Sign-bit pre-selection (appendix "Quantization"): 512-bit codes of the rows (bins of 8 permuted,
+    randomly signed coordinates), Eq. 4 agreement levels, about quant_mult x K jobs kept per query and
+    scored exactly -- against the plain exact search of the same batches on the same index.  Reports
+    QPS of both, the main-pass time (filter export + two code scans), the kept counts, and recall@K of
+    the pre-selection against the plain oracle on a sample of queries (CPU baseline leg)."""
+    import torch
+    import datagen
+    import paper_2402_13435_b300 as lr
+
+    wl = make_workload(args)
+    c = wl["corpus"]
+    idx_p, sgn_p = datagen.sign_projection(args.seed + 9, args.dim, 512, 8)
+    t0 = time.time()
+    idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), c.V, post_off=wl["post_off"], post_ids=wl["post_ids"],
+                             n_dense_terms=args.n_dense, metric="cosine", max_batch=max(args.batch, 32),
+                             max_k=args.k, max_sparse_terms=max(256, 4 * args.batch),
+                             sign_projection=(idx_p, sgn_p, 8), max_quant_k=args.quant_mult * args.k)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    nb = len(wl["filters"])
+    Qd = [torch.from_numpy(np.ascontiguousarray(wl["Q"][j])).cuda() for j in range(nb)]
+    B, K = args.batch, args.k
+    oi = torch.empty((B, K), dtype=torch.int32, device="cuda")
+    osc = torch.empty((B, K), dtype=torch.float32, device="cuda")
+    oc = torch.empty(B, dtype=torch.int32, device="cuda")
+    res = {}
+    for name, qm in (("sign", args.quant_mult), ("plain", 0)):
+        probes = [lr.Probe(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        for p in probes:
+            p.start.record()
+            p.stop.record()
+        for i in range(args.warmup):
+            lr.lr_search(idx, Qd[i % nb], wl["filters"][i % nb], K, out_ids=oi, out_scores=osc, out_count=oc,
+                         quant_mult=qm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.steps):
+            lr.lr_search(idx, Qd[i % nb], wl["filters"][i % nb], K, out_ids=oi, out_scores=osc, out_count=oc,
+                         quant_mult=qm, probe=probes[i])
+        e1.record()
+        torch.cuda.synchronize()
+        lr.lr_index_sync(idx)
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"qps": B / (ms / 1e3), "ms_per_step": ms,
+                     "main_pass_ms": float(np.mean([p.start.elapsed_time(p.stop) for p in probes])),
+                     "launches_per_step": probes[0].n_launches}
+    _, _, _, st = lr.lr_search(idx, Qd[0], wl["filters"][0], K, quant_mult=args.quant_mult, stats=True)
+    cand = st["cand_count"]
+    # code scans: the codes (64 B per row) twice plus the pass bitmaps; kept rows: 512 B each
+    code_bytes = 2 * c.n * 64 + 2 * B * c.n / 8
+    peak, kind = peaks()
+    out = {"metric": "sign-bit pre-selection QPS vs plain exact search", "value": res["sign"]["qps"],
+           "unit": "queries/s", "higher_is_better": True, "n_gpus": 1, "dtype": "u64 codes + f32 rescore",
+           "data": "synthetic (seeded generator, paper-shaped)", "config": workload_config(args),
+           "quant_mult": args.quant_mult, "sign_bits": 512, "sign_bin": 8, "forms": res,
+           "kept_per_query": {"mean": float(cand.mean()), "min": int(cand.min()), "max": int(cand.max())},
+           "roofline": {"bound": "hbm", "kernel": "k_sign_scan (histogram + collect passes)",
+                        "algorithmic_bytes_per_step": code_bytes, "peak": peak, "unit": "GB/s",
+                        "achieved": code_bytes / 1e9 / (res["sign"]["main_pass_ms"] / 1e3),
+                        "frac": code_bytes / 1e9 / (res["sign"]["main_pass_ms"] / 1e3) / peak, "peak_kind": kind},
+           "setup_s": {"index_build": round(build_s, 1)}}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        sel = list(range(min(args.cpu_queries or 8, B)))
+        fs = wl["filters"][0].subset(sel)
+        Q0 = wl["Q"][0][sel]
+        t1 = time.perf_counter()
+        ref = oracle.search(c.X, c.job_off, c.job_terms, Q0, fs, K, metric="cosine")
+        dt = time.perf_counter() - t1
+        ids = lr.lr_search(idx, Qd[0], wl["filters"][0], K, quant_mult=args.quant_mult)[0].cpu().numpy()
+        out["recall_at_k_vs_exact"] = oracle.recall_at_k([ids[b] for b in sel],
+                                                         [ref.ids[i, :ref.count[i]] for i in range(len(sel))])
+        out["cpu_baseline"] = {"value": len(sel) / dt, "unit": "queries/s", "cores": min(oracle.num_threads(),
+                               len(sel)), "kind": "oracle", "sample": "first %d queries of batch 0" % len(sel)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -854,6 +949,8 @@ def main():
         run_sweep(args)
     elif args.form == "topk":
         run_topk(args)
+    elif args.form == "sign":
+        run_sign(args)
     else:
         run_ours(args)
 

@@ -103,6 +103,19 @@ typedef struct lr_index lr_index;
  *                    contiguous row shard -- returns global ids; ties still
  *                    break by ascending id, so per-shard results merge exactly
  *                    with lr_merge_topk.  id_base + n_jobs <= 2^31 - 1.
+ *   sign_bits,       optional sign-bit codes for the pre-selection of the
+ *   sign_bin,        appendix "Quantization" (Sec. 5.3: akin to OP+ORP):
+ *   sign_idx,        sign_bits in {128, 256, 512, 1024} (0: none; the paper
+ *   sign_sgn         uses 512).  Bit b of a row's code is 1 iff
+ *                        sum_{m < sign_bin} sign_sgn[b*sign_bin+m] * x[sign_idx[b*sign_bin+m]] > 0,
+ *                    summed in FP32 in m order over the row as given in emb
+ *                    (before any normalisation).  sign_idx (int32, in [0, dim))
+ *                    and sign_sgn (int8, +1 / -1), host, [sign_bits * sign_bin]
+ *                    (sign_bits * sign_bin <= 32768), hold the random draws:
+ *                    coordinates permuted and cut into bins, a random sign per
+ *                    entry, several permutations when dim < sign_bits.
+ *   max_quant_k      largest pre-selection size quant_mult * K a search may ask
+ *                    for (0: 200 * max_k); sizes the candidate lists (twice this).
  */
 typedef struct lr_index_desc {
   int64_t n_jobs;
@@ -121,6 +134,11 @@ typedef struct lr_index_desc {
   int32_t max_sparse_terms;
   int32_t oversample;
   int64_t id_base;
+  int32_t sign_bits;
+  int32_t sign_bin;
+  const int32_t *sign_idx;
+  const int8_t *sign_sgn;
+  int64_t max_quant_k;
 } lr_index_desc;
 
 /*
@@ -146,6 +164,15 @@ typedef struct lr_search_opts {
                              -1 = no sample: every passing job is a candidate)        */
   int32_t cand_cap;       /* candidate slots per query (0 = auto; capped by workspace) */
   int32_t force_exact_fallback; /* 1: also run the exact radix fallback for every query */
+  int32_t quant_mult;     /* > 0 (index with sign codes): sign-bit pre-selection of
+                             about quant_mult * K jobs per query (the paper: 200),
+                             then exact FP32 scoring of those only; 0: off.  The
+                             pre-selection keeps whole Eq. 4 agreement levels from
+                             the top down to the highest level with at least
+                             min(quant_mult * K, #passing) jobs at or above it (one
+                             level higher if that would exceed 2 * max_quant_k);
+                             the result is the exact top K of the kept jobs.  F32
+                             indexes only.                                        */
 } lr_search_opts;
 
 /* Per-call statistics and instrumentation (every field optional).  Arrays may be
@@ -287,6 +314,21 @@ lr_status lr_index_sync(lr_index *index, void *stream);
 lr_status lr_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int32_t G, int32_t B,
                         int32_t k_in, int32_t k, int32_t *out_ids, float *out_scores, int32_t *out_count,
                         void *stream);
+
+/*
+ * Sign codes of rows (appendix "Quantization"), the encoding an index with
+ * sign_bits builds for its rows and every search for its queries: bit b of row
+ * j is 1 iff sum_{m < bin} sgn[b*bin+m] * x[j][idx[b*bin+m]] > 0, summed in FP32
+ * in m order; bit b is bit b % 64 of word b / 64 of the row's code.
+ *   x      device [n][dim] FP32 (dim <= 256); idx device int32 [nbits * bin] in
+ *          [0, dim) (an entry outside reads coordinate 0: wrong codes, never an
+ *          out-of-bounds read); sgn device int8 [nbits * bin] (+1 / -1; entries
+ *          > 0 count as +1); codes device [n][nbits / 64] uint64, 16-byte aligned.
+ *   nbits  128, 256, 512 or 1024; nbits * bin <= 32768.
+ * Stream-ordered; allocates nothing.
+ */
+lr_status lr_sign_encode(const float *x, int64_t n, int32_t dim, int32_t nbits, int32_t bin, const int32_t *idx,
+                         const int8_t *sgn, uint64_t *codes, void *stream);
 
 /*
  * Top K of dense score rows (appendix "Fast Top K Selection").  For each row b

@@ -30,7 +30,7 @@ _PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC}
 
 SYMBOLS = ("lr_index_create", "lr_index_destroy", "lr_index_device_bytes", "lr_search", "lr_search_ex",
            "lr_filter_count", "lr_index_sync", "lr_last_error_message", "lr_version", "lr_merge_topk",
-           "lr_search_noalloc", "lr_search_noalloc_status", "lr_topk", "lr_topk_workspace_size")
+           "lr_search_noalloc", "lr_search_noalloc_status", "lr_topk", "lr_topk_workspace_size", "lr_sign_encode")
 
 
 class LRError(RuntimeError):
@@ -45,7 +45,9 @@ class lr_index_desc(ctypes.Structure):
                 ("bitsets", ctypes.c_void_p), ("post_off", ctypes.c_void_p), ("post_ids", ctypes.c_void_p),
                 ("n_dense_terms", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_k", ctypes.c_int32),
                 ("max_batch_terms", ctypes.c_int32), ("max_sparse_terms", ctypes.c_int32),
-                ("oversample", ctypes.c_int32), ("id_base", ctypes.c_int64)]
+                ("oversample", ctypes.c_int32), ("id_base", ctypes.c_int64), ("sign_bits", ctypes.c_int32),
+                ("sign_bin", ctypes.c_int32), ("sign_idx", ctypes.c_void_p), ("sign_sgn", ctypes.c_void_p),
+                ("max_quant_k", ctypes.c_int64)]
 
 
 class lr_filters(ctypes.Structure):
@@ -54,7 +56,7 @@ class lr_filters(ctypes.Structure):
 
 class lr_search_opts(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_int32), ("sample_stride", ctypes.c_int32), ("cand_cap", ctypes.c_int32),
-                ("force_exact_fallback", ctypes.c_int32)]
+                ("force_exact_fallback", ctypes.c_int32), ("quant_mult", ctypes.c_int32)]
 
 
 class lr_search_stats(ctypes.Structure):
@@ -174,12 +176,14 @@ class Index:
 def lr_index_create(emb, vocab: int, *, bitsets=None, post_off=None, post_ids=None, n_dense_terms: int = -1,
                     metric: str = "cosine", max_batch: int = 256, max_k: int = 1000, max_batch_terms: int = 0,
                     max_sparse_terms: int = 0, dtype: str = "f32", oversample: int = 0, id_base: int = 0,
-                    stream=None) -> Index:
+                    sign_projection=None, max_quant_k: int = 0, stream=None) -> Index:
     """Build an index over job embeddings ``emb`` [n][dim] FP32 (torch or numpy, host or device) and
     per-job terms given either as job-major ``bitsets`` [n][ceil(vocab/64)] uint64 or as posting lists
     (``post_off`` int64[vocab+1], ``post_ids`` uint32[nnz]).  ``dtype`` "bf16" or "fp8" selects the
     precision form (low-precision scan of ``oversample`` x K candidates, FP32 rescore, FP64 near ties).
-    ``id_base`` makes the index a row shard: row r is returned as job id_base + r."""
+    ``id_base`` makes the index a row shard: row r is returned as job id_base + r.
+    ``sign_projection`` = (idx int32, sgn int8, bin) builds sign-bit codes of len(idx) / bin bits for the
+    pre-selection of the appendix "Quantization" (searches with ``quant_mult``)."""
     n, dim = int(emb.shape[0]), int(emb.shape[1])
     keep = []
     if isinstance(emb, np.ndarray):
@@ -191,11 +195,20 @@ def lr_index_create(emb, vocab: int, *, bitsets=None, post_off=None, post_ids=No
         post_ids = np.ascontiguousarray(np.asarray(post_ids), dtype=np.uint32) if isinstance(post_ids, np.ndarray) \
             or not hasattr(post_ids, "data_ptr") else post_ids
     keep += [emb, bitsets, post_off, post_ids]
+    sign_bits = sign_bin = 0
+    s_idx = s_sgn = None
+    if sign_projection is not None:
+        s_idx = np.ascontiguousarray(sign_projection[0], dtype=np.int32)
+        s_sgn = np.ascontiguousarray(sign_projection[1], dtype=np.int8)
+        sign_bin = int(sign_projection[2])
+        sign_bits = s_idx.size // sign_bin
+        keep += [s_idx, s_sgn]
     d = lr_index_desc(n_jobs=n, dim=dim, dtype=_DTYPE[dtype], metric=_METRIC[metric], vocab=int(vocab), emb=_ptr(emb),
                       bitsets=_ptr(bitsets), post_off=_ptr(post_off), post_ids=_ptr(post_ids),
                       n_dense_terms=int(n_dense_terms), max_batch=int(max_batch), max_k=int(max_k),
                       max_batch_terms=int(max_batch_terms), max_sparse_terms=int(max_sparse_terms),
-                      oversample=int(oversample), id_base=int(id_base))
+                      oversample=int(oversample), id_base=int(id_base), sign_bits=sign_bits, sign_bin=sign_bin,
+                      sign_idx=_ptr(s_idx), sign_sgn=_ptr(s_sgn), max_quant_k=int(max_quant_k))
     h = ctypes.c_void_p()
     _check(_lib.lr_index_create(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "lr_index_create")
     del keep
@@ -247,8 +260,8 @@ class Probe:
 
 
 def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out_count=None, plan: str = "auto",
-              sample_stride: int = 0, cand_cap: int = 0, force_exact_fallback: bool = False, stats: bool = False,
-              probe: Optional[Probe] = None, stream=None):
+              sample_stride: int = 0, cand_cap: int = 0, force_exact_fallback: bool = False, quant_mult: int = 0,
+              stats: bool = False, probe: Optional[Probe] = None, stream=None):
     """Filtered top-K for the query batch ``q`` [B][dim] FP32 (torch tensor or numpy array, host or device).
 
     ``k`` is an int or a per-query sequence.  Outputs default to new device tensors on q's device
@@ -280,7 +293,7 @@ def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out
             out_scores = torch.empty((B, k_all), dtype=torch.float32, device=q.device)
             out_count = torch.empty(B, dtype=torch.int32, device=q.device)
     opts = lr_search_opts(plan=_PLAN[plan], sample_stride=int(sample_stride), cand_cap=int(cand_cap),
-                          force_exact_fallback=int(bool(force_exact_fallback)))
+                          force_exact_fallback=int(bool(force_exact_fallback)), quant_mult=int(quant_mult))
     st = None
     st_arrays = None
     if stats:
@@ -323,6 +336,26 @@ def lr_merge_topk(ids, scores, counts, k: int, *, out_ids=None, out_scores=None,
     _check(_lib.lr_merge_topk(_ptr(ids), _ptr(scores), _ptr(counts), G, B, k_in, int(k), _ptr(out_ids),
                               _ptr(out_scores), _ptr(out_count), _stream_ptr(stream)), "lr_merge_topk")
     return out_ids, out_scores, out_count
+
+
+_lib.lr_sign_encode.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+_lib.lr_sign_encode.restype = ctypes.c_int
+
+
+def lr_sign_encode(x, idx, sgn, bin_size: int, stream=None):
+    """Sign codes of the rows of x [n][dim] (CUDA FP32) under the projection idx / sgn (CUDA int32 / int8,
+    [nbits * bin_size]): returns uint64 codes [n][nbits/64] as an int64 CUDA tensor."""
+    import torch
+
+    n, dim = int(x.shape[0]), int(x.shape[1])
+    nbits = int(idx.numel()) // int(bin_size)
+    if x.dtype != torch.float32 or idx.dtype != torch.int32 or sgn.dtype != torch.int8 or not x.is_cuda:
+        raise ValueError("x float32, idx int32 and sgn int8 CUDA tensors expected")
+    codes = torch.empty((n, nbits // 64), dtype=torch.int64, device=x.device)
+    _check(_lib.lr_sign_encode(_ptr(x), n, dim, nbits, int(bin_size), _ptr(idx), _ptr(sgn), _ptr(codes),
+                               _stream_ptr(stream)), "lr_sign_encode")
+    return codes
 
 
 LR_TOPK_BUCKET, LR_TOPK_RADIX = 0, 1

@@ -219,6 +219,32 @@ struct RescoreArgs {
 // Two launches: the candidates' FP32 scores over several CTAs per query, then
 // per query the K-th key, the FP64 re-rank of the near-tie band and the output.
 cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s);
+// Sign-bit pre-selection (sign.cu).
+struct SignScanArgs {
+  const uint64_t *codes;      // [n][nbits/64] job codes
+  int64_t n;
+  int32_t nbits;
+  const uint64_t *qcodes;     // [B][nbits/64] query codes
+  const uint32_t *pass;       // [B][pass_words] pass bitmaps (bit j of row b: job j passes filter b)
+  int64_t pass_words;
+  int32_t q_base, nq;         // queries of this launch (nq <= 32)
+  int32_t mode;               // 0: histogram of agreement levels, 1: collect jobs at or above level[q]
+  uint32_t *hist;             // [B][hist_stride]
+  int32_t hist_stride;
+  const int32_t *level;       // [B]
+  uint64_t *buf;              // [B][cap] job ids
+  int64_t cap;
+  uint32_t *cnt;              // [B]
+};
+size_t sign_encode_smem(int nbits, int bin, int dim);
+cudaError_t launch_sign_encode(const float *x, int64_t n, int dim, int64_t ld, int nbits, int bin, const int32_t *idx,
+                               const int8_t *sgn, uint64_t *codes, int num_sms, cudaStream_t s);
+cudaError_t launch_sign_scan(const SignScanArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_sign_levels(const uint32_t *hist, int hist_stride, int nbits, int B, const int64_t *quant_k,
+                               const unsigned long long *pass_cnt, int64_t cap, int32_t *level,
+                               unsigned long long *ncand, cudaStream_t s);
+cudaError_t launch_sign_rescore(const float *X, int d_pad, const float *Q, uint64_t *buf, int64_t cap,
+                                const uint32_t *cnt, int B, int num_sms, cudaStream_t s);
 // Exact merge of G per-part top-K lists per query (merge.cu).
 cudaError_t launch_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int G, int B, int k_in,
                               int k, int32_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t s);

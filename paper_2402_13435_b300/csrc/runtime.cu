@@ -171,6 +171,17 @@ struct lr_index {
   bool have_tmap = false;
   CUtensorMap tmap_xq;  // low-precision rows (precision form)
   bool have_tmap_q = false;
+  // sign-bit pre-selection: codes of the rows, the projection, candidate lists
+  int sign_bits = 0, sign_bin = 0, sign_W = 0;
+  uint64_t *sign_codes = nullptr;  // [n][sign_W]
+  int32_t *sign_idx_d = nullptr;   // [sign_bits * sign_bin]
+  int8_t *sign_sgn_d = nullptr;
+  int64_t sign_max_qk = 0, sign_cap = 0;
+  uint32_t *sign_pass = nullptr;   // workspace: [max_batch][n_words] pass bitmaps
+  uint64_t *sign_qcodes = nullptr; // [max_batch][sign_W]
+  uint64_t *sign_buf = nullptr;    // [max_batch][sign_cap] kept ids, then keys
+  int32_t *sign_level = nullptr;   // state block: [max_batch]
+  unsigned long long *sign_ncand = nullptr;
 };
 
 namespace {
@@ -185,6 +196,9 @@ void free_index(lr_index *ix) {
     cudaFree(ix->post_off_d);
     cudaFree(ix->post_ids_d);
     cudaFree(ix->span_d);
+    cudaFree(ix->sign_codes);
+    cudaFree(ix->sign_idx_d);
+    cudaFree(ix->sign_sgn_d);
   }
   cudaFree(ix->ws);
   if (ix->ev_fork) cudaEventDestroy(ix->ev_fork);
@@ -341,7 +355,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   // ---- workspace, one allocation
   const int B = ix->max_batch;
   const int nsp = (ix->has_postings && ix->n_dense < ix->vocab) ? ix->max_sparse : 0;
-  ix->filt_bytes = align_up((size_t)B * 16 + (size_t)ix->max_batch_terms * 32 + (size_t)nsp * 4 + 65536, 256);
+  ix->filt_bytes = align_up((size_t)B * 24 + (size_t)ix->max_batch_terms * 32 + (size_t)nsp * 4 + 65536, 256);
   Carver cv;
   const size_t o_qraw = cv.take<float>((size_t)B * ix->dim);
   const size_t o_qws = cv.take<float>((size_t)B * ix->d_pad);
@@ -362,6 +376,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_tcnt_s = cv.take<uint32_t>(1);
   const size_t o_thr_done = cv.take<uint32_t>(B);
   const size_t o_rs_gmax = cv.take<uint32_t>(ix->elem != kElemF32 ? B : 0);
+  const bool sign = ix->sign_codes != nullptr;
+  const size_t o_sg_level = cv.take<int32_t>(sign ? B : 0);
+  const size_t o_sg_ncand = cv.take<unsigned long long>(sign ? B : 0);
   const size_t o_state_end = cv.take<char>(0);
   const size_t o_done = cv.take<uint32_t>(2);  // completion counter, work counter
   const size_t o_err = cv.take<uint32_t>(1);
@@ -387,6 +404,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_ccnt = cv.take<int32_t>(lowp ? B : 0);
   const size_t o_ties = cv.take<int32_t>(lowp ? B : 0);
   const size_t o_rs_keys = cv.take<uint64_t>(lowp ? (size_t)B * ix->max_kq : 0);
+  const size_t o_sg_pass = cv.take<uint32_t>(sign ? (size_t)B * ix->n_words : 0);
+  const size_t o_sg_qc = cv.take<uint64_t>(sign ? (size_t)B * ix->sign_W : 0);
+  const size_t o_sg_buf = cv.take<uint64_t>(sign ? (size_t)B * ix->sign_cap : 0);
   const size_t o_filt = cv.take<char>(ix->filt_bytes);
   ix->ws_bytes = align_up(cv.off, 256);
   if (cudaMalloc(&ix->ws, ix->ws_bytes) != cudaSuccess) {
@@ -440,6 +460,13 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
     ix->rs_gmax = (uint32_t *)(w + o_rs_gmax);
   }
   ix->filt_d = w + o_filt;
+  if (sign) {
+    ix->sign_level = (int32_t *)(w + o_sg_level);
+    ix->sign_ncand = (unsigned long long *)(w + o_sg_ncand);
+    ix->sign_pass = (uint32_t *)(w + o_sg_pass);
+    ix->sign_qcodes = (uint64_t *)(w + o_sg_qc);
+    ix->sign_buf = (uint64_t *)(w + o_sg_buf);
+  }
   LR_CK(cudaMemsetAsync(ix->done_ctr, 0, 2 * sizeof(uint32_t), s));
   LR_CK(cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), s));
   LR_CK(cudaMemsetAsync(ix->hist, 0, (size_t)B * kFbBins * sizeof(uint32_t), s));
@@ -531,6 +558,21 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
   if ((int64_t)oversample * d->max_k > kMaxK) return fail(LR_ERR_INVALID, "oversample * max_k must be <= 4096");
   if (d->id_base < 0 || d->id_base + d->n_jobs > 0x7FFFFFFFll)
     return fail(LR_ERR_INVALID, "id_base must be >= 0 and id_base + n_jobs <= 2^31 - 1 (int32 job ids)");
+  if (d->sign_bits != 0) {
+    const int sb = d->sign_bits;
+    if (sb != 128 && sb != 256 && sb != 512 && sb != 1024)
+      return fail(LR_ERR_INVALID, "sign_bits must be 0, 128, 256, 512 or 1024");
+    if (d->sign_bin < 1 || (int64_t)sb * d->sign_bin > 32768)
+      return fail(LR_ERR_INVALID, "sign_bin must be >= 1 with sign_bits * sign_bin <= 32768");
+    if (!d->sign_idx || !d->sign_sgn) return fail(LR_ERR_INVALID, "sign_idx and sign_sgn are required");
+    if (is_device_ptr(d->sign_idx) || is_device_ptr(d->sign_sgn))
+      return fail(LR_ERR_INVALID, "sign_idx and sign_sgn must be host memory");
+    for (int64_t i = 0; i < (int64_t)sb * d->sign_bin; ++i) {
+      if (d->sign_idx[i] < 0 || d->sign_idx[i] >= d->dim) return fail(LR_ERR_INVALID, "sign_idx entry outside [0, dim)");
+      if (d->sign_sgn[i] != 1 && d->sign_sgn[i] != -1) return fail(LR_ERR_INVALID, "sign_sgn entries must be +1 or -1");
+    }
+    if (d->max_quant_k < 0) return fail(LR_ERR_INVALID, "max_quant_k must be >= 0");
+  }
 
   cudaStream_t s = (cudaStream_t)stream;
   lr_index *ix = new lr_index();
@@ -587,6 +629,42 @@ lr_status lr_index_create(const lr_index_desc *d, void *stream, lr_index **out) 
       CK2(cudaStreamSynchronize(s));
     }
     cudaFree(tmp);
+  }
+  if (d->sign_bits != 0) {  // sign codes of the rows as given (before normalisation)
+    ix->sign_bits = d->sign_bits;
+    ix->sign_bin = d->sign_bin;
+    ix->sign_W = d->sign_bits / 64;
+    ix->sign_max_qk = d->max_quant_k > 0 ? d->max_quant_k : 200ll * d->max_k;
+    ix->sign_cap = 2 * ix->sign_max_qk;
+    const size_t np = (size_t)d->sign_bits * d->sign_bin;
+    const size_t cbytes = (size_t)ix->n * ix->sign_W * sizeof(uint64_t);
+    if (cudaMalloc(&ix->sign_codes, cbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(fail(LR_ERR_NOMEM, "cannot allocate the sign codes"));
+    }
+    ix->device_bytes += cbytes;
+    CK2(cudaMalloc(&ix->sign_idx_d, np * sizeof(int32_t)));
+    CK2(cudaMalloc(&ix->sign_sgn_d, np));
+    ix->device_bytes += np * 5;
+    CK2(cudaMemcpyAsync(ix->sign_idx_d, d->sign_idx, np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK2(cudaMemcpyAsync(ix->sign_sgn_d, d->sign_sgn, np, cudaMemcpyHostToDevice, s));
+    if (is_device_ptr(d->emb)) {
+      CK2(launch_sign_encode(d->emb, ix->n, ix->dim, ix->dim, ix->sign_bits, ix->sign_bin, ix->sign_idx_d,
+                             ix->sign_sgn_d, ix->sign_codes, ix->num_sms, s));
+    } else {
+      const int64_t chunk = std::max<int64_t>(1, (64ll << 20) / ((int64_t)ix->dim * 4));
+      float *tmp = nullptr;
+      CK2(cudaMalloc(&tmp, (size_t)std::min<int64_t>(chunk, ix->n) * ix->dim * sizeof(float)));
+      for (int64_t r = 0; r < ix->n; r += chunk) {
+        const int64_t m = std::min<int64_t>(chunk, ix->n - r);
+        CK2(cudaMemcpyAsync(tmp, d->emb + (size_t)r * ix->dim, (size_t)m * ix->dim * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+        CK2(launch_sign_encode(tmp, m, ix->dim, ix->dim, ix->sign_bits, ix->sign_bin, ix->sign_idx_d,
+                               ix->sign_sgn_d, ix->sign_codes + (size_t)r * ix->sign_W, ix->num_sms, s));
+        CK2(cudaStreamSynchronize(s));
+      }
+      cudaFree(tmp);
+    }
   }
   if (ix->elem != kElemF32) {  // low-precision copy read by the scan (precision form)
     const size_t qbytes = (size_t)ix->n * ix->d_pad * (ix->elem == kElemBF16 ? 2 : 1);
@@ -926,6 +1004,158 @@ lr_status compile_filters(lr_index *ix, const lr_filters *f, int B, int max_q_pe
 // ------------------------------------------------------------------ search
 namespace {
 
+// Search with the sign-bit pre-selection (appendix "Quantization"): the CNF
+// filter gives pass bitmaps, the Eq. 4 agreement of the passing jobs with the
+// query's code is histogrammed, whole agreement levels from the top are kept
+// down to about quant_mult * K jobs, and only those are scored exactly (FP32)
+// and selected.  TBR -> Quant -> EBR, as the appendix chains them.
+lr_status run_sign_search(lr_index *ix, const float *q, int B, const lr_filters *f, const int32_t *k, int k_all,
+                          int32_t *out_ids, float *out_scores, int32_t *out_count, const lr_search_opts &o,
+                          const lr_search_stats *stats, cudaStream_t s) {
+  if (o.quant_mult < 0) return fail(LR_ERR_INVALID, "quant_mult must be >= 0");
+  if (!ix->sign_codes) return fail(LR_ERR_UNSUPPORTED, "the index has no sign codes (sign_bits = 0)");
+  if (ix->elem != kElemF32) return fail(LR_ERR_UNSUPPORTED, "sign-bit pre-selection needs an LR_F32 index");
+  const int turn = ix->filt_turn;
+  ix->filt_turn ^= 1;
+  if (ix->filt_ev_live[turn]) LR_CK(cudaEventSynchronize(ix->filt_ev[turn]));
+  char *stage = ix->filt_h[turn];
+  Compiled C;
+  lr_status st = compile_filters(ix, f, B, 32, stage, C);
+  if (st != LR_OK) return st;
+  int32_t *kf = (int32_t *)(stage + C.off_kfin);
+  const size_t off_qk = align_up(C.bytes, 16);
+  if (off_qk + sizeof(int64_t) * B > ix->filt_bytes) return fail(LR_ERR_WORKSPACE, "filters: staging area too small");
+  int64_t *qk = (int64_t *)(stage + off_qk);
+  for (int b = 0; b < B; ++b) {
+    const int kb = k ? k[b] : k_all;
+    if (kb < 1 || kb > ix->max_k || kb > k_all) return fail(LR_ERR_INVALID, "K must be in [1, min(max_k, k_all)]");
+    kf[b] = kb;
+    qk[b] = (int64_t)o.quant_mult * kb;
+    if (qk[b] > ix->sign_max_qk) return fail(LR_ERR_WORKSPACE, "quant_mult * K exceeds the index's max_quant_k");
+  }
+  const size_t bytes = off_qk + sizeof(int64_t) * B;
+  int32_t n_launch = 0;
+  LR_CK(cudaMemcpyAsync(ix->filt_d, stage, bytes, cudaMemcpyHostToDevice, s));
+  LR_CK(cudaEventRecord(ix->filt_ev[turn], s));
+  ix->filt_ev_live[turn] = true;
+  LR_CK(cudaMemsetAsync(ix->state, 0, ix->state_bytes, s));
+  LR_CK(cudaMemsetAsync(ix->hist, 0, (size_t)B * kFbBins * sizeof(uint32_t), s));
+  const int32_t *kfin_d = (const int32_t *)(ix->filt_d + C.off_kfin);
+  const int64_t *qk_d = (const int64_t *)(ix->filt_d + off_qk);
+  const float *qsrc = q;
+  if (!is_device_ptr(q)) {
+    LR_CK(cudaMemcpyAsync(ix->q_raw, q, sizeof(float) * (size_t)B * ix->dim, cudaMemcpyHostToDevice, s));
+    qsrc = ix->q_raw;
+  }
+  LR_LAUNCH(launch_prep_queries(qsrc, ix->q_ws, B, ix->dim, ix->d_pad, ix->metric == LR_COSINE, ix->err, s));
+  // the query codes come from the queries as given, like the rows' codes
+  LR_LAUNCH(launch_sign_encode(qsrc, B, ix->dim, ix->dim, ix->sign_bits, ix->sign_bin, ix->sign_idx_d,
+                               ix->sign_sgn_d, ix->sign_qcodes, ix->num_sms, s));
+  if (!C.sparse_terms.empty()) {
+    ++n_launch;
+    LR_CK(expand_sparse_terms(ix, C, s));
+  }
+  // TBR: pass bitmaps and counts of every filter
+  for (const SubBatch &sb : C.subs) {
+    ScanArgs a{};
+    a.n = ix->n;
+    a.q_base = sb.q_base;
+    a.nq = sb.nq;
+    a.slot_bm = (const uint32_t *const *)(ix->filt_d + sb.off_slots);
+    a.n_slots = sb.n_slots;
+    a.qc_off = (const int32_t *)(ix->filt_d + sb.off_qc);
+    a.cl_off = (const int32_t *)(ix->filt_d + sb.off_cl);
+    a.cl_slot = (const int32_t *)(ix->filt_d + sb.off_cs);
+    a.n_groups = ix->n_groups;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ix->n_groups + 7) / 8, (int64_t)ix->num_sms * 4));
+    LR_LAUNCH(launch_filter_eval(a, ix->pass, ix->sign_pass, ix->n_words, 0, grid, s));
+  }
+  // Quant: agreement levels, the level of each query, the kept jobs
+  SignScanArgs g{};
+  g.codes = ix->sign_codes;
+  g.n = ix->n;
+  g.nbits = ix->sign_bits;
+  g.qcodes = ix->sign_qcodes;
+  g.pass = ix->sign_pass;
+  g.pass_words = ix->n_words;
+  g.hist = ix->hist;
+  g.hist_stride = kFbBins;
+  g.level = ix->sign_level;
+  g.buf = ix->sign_buf;
+  g.cap = ix->sign_cap;
+  g.cnt = ix->cnt;
+  if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
+  int32_t n_scan = 0;
+  for (const SubBatch &sb : C.subs) {
+    g.q_base = sb.q_base;
+    g.nq = sb.nq;
+    g.mode = 0;
+    LR_LAUNCH(launch_sign_scan(g, ix->num_sms, s));
+    ++n_scan;
+  }
+  LR_LAUNCH(launch_sign_levels(ix->hist, kFbBins, ix->sign_bits, B, qk_d, ix->pass, ix->sign_cap, ix->sign_level,
+                               ix->sign_ncand, s));
+  for (const SubBatch &sb : C.subs) {
+    g.q_base = sb.q_base;
+    g.nq = sb.nq;
+    g.mode = 1;
+    LR_LAUNCH(launch_sign_scan(g, ix->num_sms, s));
+    ++n_scan;
+  }
+  if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
+  // EBR: exact FP32 scores of the kept jobs, then the exact top K among them
+  LR_LAUNCH(launch_sign_rescore(ix->X, ix->d_pad, ix->q_ws, ix->sign_buf, ix->sign_cap, ix->cnt, B, ix->num_sms, s));
+  const bool dev_out = is_device_ptr(out_ids) && is_device_ptr(out_scores) &&
+                       (out_count == nullptr || is_device_ptr(out_count));
+  if (!dev_out && k_all > ix->max_k) return fail(LR_ERR_INVALID, "host outputs need k_all <= max_k");
+  SelectArgs fa{};
+  fa.mode = 1;
+  fa.buf = ix->sign_buf;
+  fa.cap = ix->sign_cap;
+  fa.cnt = ix->cnt;
+  fa.overflow = ix->ovf;
+  fa.k = kfin_d;
+  fa.pass_cnt = ix->sign_ncand;
+  fa.k_stride = k_all;
+  fa.out_ids = dev_out ? out_ids : ix->o_ids;
+  fa.out_scores = dev_out ? out_scores : ix->o_sc;
+  fa.out_count = dev_out ? out_count : ix->o_cnt;
+  fa.flag = ix->flag;
+  fa.n_flagged = ix->n_flag;
+  fa.fb_prefix = ix->prefix;
+  fa.fb_krem = ix->krem;
+  fa.cand_count_out = ix->o_cand;
+  fa.fallback_out = ix->o_fb;
+  fa.err = ix->err;
+  fa.id_base = ix->id_base;
+  LR_LAUNCH(launch_select(fa, B, s));
+  // the exact fallback of the plain search expects a clear histogram
+  LR_CK(cudaMemsetAsync(ix->hist, 0, (size_t)B * kFbBins * sizeof(uint32_t), s));
+  bool need_sync = false;
+  if (!dev_out) {
+    LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
+    LR_CK(cudaMemcpyAsync(out_scores, ix->o_sc, sizeof(float) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
+    if (out_count) LR_CK(cudaMemcpyAsync(out_count, ix->o_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
+    need_sync = true;
+  }
+  if (stats) {
+    if (stats->n_launches) *stats->n_launches = n_launch;
+    if (stats->n_scan_launches) *stats->n_scan_launches = n_scan;
+    if (stats->plan_used) *stats->plan_used = LR_PLAN_GEMV;
+    struct { void *dst; const void *src; size_t bytes; } cp[3] = {
+        {stats->pass_count, ix->pass, sizeof(int64_t) * B},
+        {stats->cand_count, ix->o_cand, sizeof(int32_t) * B},
+        {stats->fallback, ix->o_fb, sizeof(int32_t) * B}};
+    for (auto &c : cp) {
+      if (!c.dst) continue;
+      LR_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, s));
+      need_sync |= !is_device_ptr(c.dst);
+    }
+  }
+  if (need_sync) LR_CK(cudaStreamSynchronize(s));
+  return LR_OK;
+}
+
 lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, const int32_t *k, int k_all,
                      int32_t *out_ids, float *out_scores, int32_t *out_count, const lr_search_opts *opts,
                      const lr_search_stats *stats, cudaStream_t s) {
@@ -936,6 +1166,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (k_all > ix->max_k && k == nullptr) return fail(LR_ERR_INVALID, "K exceeds max_k");
   lr_search_opts o{};
   if (opts) o = *opts;
+  if (o.quant_mult != 0) return run_sign_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, o, stats, s);
 
   // pick and wait for a staging buffer
   const int turn = ix->filt_turn;
