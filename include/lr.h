@@ -51,11 +51,23 @@ typedef enum lr_dtype { LR_F32 = 0, LR_BF16 = 1, LR_FP8_E4M3 = 2 } lr_dtype;
  * search); a zero vector scores 0.  (Sec. 5.2 uses cosine similarity.) */
 typedef enum lr_metric { LR_DOT = 0, LR_COSINE = 1 } lr_metric;
 
-/* Scoring plan.  AUTO picks by batch size. */
+/* Scoring plan (Sec. 5.3, "EBR first or TBR first").  AUTO picks the plan with
+ * the smallest estimated cost from the batch size and the terms' document
+ * frequencies. */
 typedef enum lr_plan {
   LR_PLAN_AUTO = 0,
-  LR_PLAN_GEMV = 1,  /* SIMT FP32 matrix-vector scan, HBM-bound at small batches */
-  LR_PLAN_TC = 2     /* tcgen05 tensor-core tiles (3xTF32 split), large batches  */
+  LR_PLAN_GEMV = 1,  /* F-TBR + F-EBR fused: SIMT FP32 matrix-vector scan that
+                        tests the CNF per 256-row group and scores passing rows */
+  LR_PLAN_TC = 2,    /* F-TBR + F-EBR: tile filter, then tcgen05 tensor-core
+                        scoring (3xTF32 split) of the tiles some query passes  */
+  LR_PLAN_TBR = 3    /* TBR first (H-TBR): per query the clause with the
+                        shortest posting lists gives the candidate rows, the
+                        whole CNF is tested on them, only the passing rows are
+                        scored (FP32).  Needs an index built from posting lists
+                        (each list naming a job at most once), at least one
+                        clause per query and at most the candidate capacity
+                        (65,536 per query from 65,536 rows up) postings in the
+                        chosen clause; LR_ERR_UNSUPPORTED otherwise.           */
 } lr_plan;
 
 typedef struct lr_index lr_index;

@@ -24,9 +24,9 @@ LR_OK, LR_ERR_INVALID, LR_ERR_NOMEM, LR_ERR_WORKSPACE, LR_ERR_CUDA, LR_ERR_TIMEO
 LR_F32, LR_BF16, LR_FP8_E4M3 = 0, 1, 2
 _DTYPE = {"f32": LR_F32, "bf16": LR_BF16, "fp8": LR_FP8_E4M3}
 LR_DOT, LR_COSINE = 0, 1
-LR_PLAN_AUTO, LR_PLAN_GEMV, LR_PLAN_TC = 0, 1, 2
+LR_PLAN_AUTO, LR_PLAN_GEMV, LR_PLAN_TC, LR_PLAN_TBR = 0, 1, 2, 3
 _METRIC = {"dot": LR_DOT, "cosine": LR_COSINE}
-_PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC}
+_PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC, "tbr": LR_PLAN_TBR}
 
 SYMBOLS = ("lr_index_create", "lr_index_destroy", "lr_index_device_bytes", "lr_search", "lr_search_ex",
            "lr_filter_count", "lr_index_sync", "lr_last_error_message", "lr_version", "lr_merge_topk",
@@ -249,7 +249,7 @@ class Probe:
 
     @property
     def plan(self) -> str:
-        """The scan plan the call ran: "gemv" or "tc"."""
+        """The plan the call ran: "gemv", "tc" or "tbr"."""
         return {v: k for k, v in _PLAN.items()}.get(int(self._plan[0]), "auto")
 
     def c(self) -> lr_search_stats:

@@ -245,6 +245,26 @@ cudaError_t launch_sign_levels(const uint32_t *hist, int hist_stride, int nbits,
                                unsigned long long *ncand, cudaStream_t s);
 cudaError_t launch_sign_rescore(const float *X, int d_pad, const float *Q, uint64_t *buf, int64_t cap,
                                 const uint32_t *cnt, int B, int num_sms, cudaStream_t s);
+// TBR-first plan (tbr.cu): candidate rows from the postings of one clause per query.
+struct TbrRange {
+  int64_t begin, end;     // posting-list offsets of one term of the chosen clause
+  const uint32_t *bm;     // that term's bitmap (to drop rows an earlier term already produced)
+};
+struct TbrArgs {
+  int64_t n;
+  int32_t q_base, nq;                // this launch's queries (CNF tables are launch-local)
+  const uint32_t *const *slot_bm;
+  const int32_t *qc_off, *cl_off, *cl_slot;
+  const int32_t *r_off;              // [B+1] ranges of each (batch-global) query
+  const TbrRange *ranges;
+  const uint32_t *post_ids;
+  uint64_t *buf;                     // [B][cap] kept row ids (the messenger list), scored in place later
+  int64_t cap;
+  uint32_t *cnt;                     // [B]
+  unsigned long long *pass_cnt;      // [B] rows passing the CNF
+  uint32_t *err;
+};
+cudaError_t launch_tbr_collect(const TbrArgs &a, int num_sms, int64_t max_postings, cudaStream_t s);
 // Exact merge of G per-part top-K lists per query (merge.cu).
 cudaError_t launch_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int G, int B, int k_in,
                               int k, int32_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t s);

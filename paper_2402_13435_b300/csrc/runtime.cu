@@ -355,7 +355,9 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   // ---- workspace, one allocation
   const int B = ix->max_batch;
   const int nsp = (ix->has_postings && ix->n_dense < ix->vocab) ? ix->max_sparse : 0;
-  ix->filt_bytes = align_up((size_t)B * 24 + (size_t)ix->max_batch_terms * 32 + (size_t)nsp * 4 + 65536, 256);
+  // per query: K, final K, sample rank, quantK (24 B); TBR-first: up to 16 posting ranges (24 B) and an offset
+  ix->filt_bytes =
+      align_up((size_t)B * (24 + 16 * 24 + 8) + (size_t)ix->max_batch_terms * 32 + (size_t)nsp * 4 + 65536, 256);
   Carver cv;
   const size_t o_qraw = cv.take<float>((size_t)B * ix->dim);
   const size_t o_qws = cv.take<float>((size_t)B * ix->d_pad);
@@ -870,6 +872,80 @@ int choose_plan(int B, bool tc_ok, bool have_est, const std::vector<double> &s) 
   return tc / 0.82 < gemv / 0.53 ? LR_PLAN_TC : LR_PLAN_GEMV;
 }
 
+// TBR-first choice per query: the clause whose distinct terms have the fewest
+// postings (the smaller set of the paper's intersection argument).  ok is
+// false when the index has no posting lists, a query has no clause, or a
+// chosen clause has more postings than `cap`.
+struct TbrPlan {
+  bool ok = false;
+  std::vector<int32_t> clause;     // [B] chosen clause (global clause index)
+  std::vector<int64_t> postings;   // [B] postings of that clause
+  int64_t max_postings = 0;
+};
+
+TbrPlan plan_tbr(const lr_index *ix, const lr_filters *f, int B, int64_t cap) {
+  TbrPlan P;
+  if (!ix->has_postings || !f || !f->q_off || !f->c_off || !f->terms) return P;
+  P.clause.assign(B, -1);
+  P.postings.assign(B, 0);
+  const std::vector<int64_t> &po = ix->post_off_h;
+  for (int b = 0; b < B; ++b) {
+    const int c0 = f->q_off[b], c1 = f->q_off[b + 1];
+    if (c1 <= c0) return P;
+    int64_t best = -1;
+    for (int c = c0; c < c1; ++c) {
+      int64_t tot = 0;
+      for (int i = f->c_off[c]; i < f->c_off[c + 1]; ++i) {
+        const uint32_t t = f->terms[i];
+        if (t >= (uint32_t)ix->vocab) return P;
+        bool seen = false;  // a repeated term adds no rows
+        for (int i2 = f->c_off[c]; i2 < i; ++i2) seen |= f->terms[i2] == t;
+        if (!seen) tot += po[t + 1] - po[t];
+      }
+      if (best < 0 || tot < best) {
+        best = tot;
+        P.clause[b] = c;
+      }
+    }
+    if (best > cap) return P;
+    int distinct = 0;  // the collect kernel holds up to 16 ranges per query
+    const int c = P.clause[b];
+    for (int i = f->c_off[c]; i < f->c_off[c + 1]; ++i) {
+      bool seen = false;
+      for (int i2 = f->c_off[c]; i2 < i; ++i2) seen |= f->terms[i2] == f->terms[i];
+      distinct += seen ? 0 : 1;
+    }
+    if (distinct > 16) return P;
+    P.postings[b] = best;
+    P.max_postings = std::max(P.max_postings, best);
+  }
+  P.ok = true;
+  return P;
+}
+
+// Estimated cost of the TBR-first plan against the scan plans, in bytes of
+// HBM-equivalent traffic: the postings and their bit tests (term words mostly
+// L2 hits: ~16 B per posting), the passing rows gathered at about half the
+// streaming rate; the scans read the rows they must (as choose_plan) plus the
+// predicate's pass over every 256-row group, which measured as ~64 B per row
+// for the SIMT scan and ~32 B per row for the tile filter at 10M rows.
+bool tbr_cheaper(const lr_index *ix, int B, const TbrPlan &T, const std::vector<double> &est, bool tc_ok) {
+  const double rb = 4.0 * ix->d_pad, n = (double)ix->n;
+  double tbr = 0.0;
+  for (int b = 0; b < B; ++b) tbr += 16.0 * (double)T.postings[b] + 2.0 * est[b] * n * rb;
+  auto union_of = [&](int b0, int b1) {
+    double none = 1.0;
+    for (int b = b0; b < b1; ++b) none *= 1.0 - est[b];
+    return 1.0 - none;
+  };
+  double gemv = 0.0, tc = 0.0;
+  for (int b0 = 0; b0 < B; b0 += kGemvMaxQ) gemv += union_of(b0, std::min(B, b0 + kGemvMaxQ)) * n * rb / 0.53 + 64.0 * n;
+  for (int b0 = 0; b0 < B; b0 += kTcMaxQ)
+    tc += (1.0 - std::pow(1.0 - union_of(b0, std::min(B, b0 + kTcMaxQ)), 128.0)) * n * rb / 0.82 + 32.0 * n;
+  const double scan = tc_ok ? std::min(gemv, tc) : gemv;
+  return tbr < 0.5 * scan;
+}
+
 // The batch's posting-list terms -> workspace bitmaps (step A1): a dense write
 // of every word when the index has a span table, else clear + scatter.
 cudaError_t expand_sparse_terms(lr_index *ix, const Compiled &C, cudaStream_t s) {
@@ -1156,6 +1232,143 @@ lr_status run_sign_search(lr_index *ix, const float *q, int B, const lr_filters 
   return LR_OK;
 }
 
+// TBR-first search (Sec. 5.3, "EBR first or TBR first"): the postings of each
+// query's chosen clause are the candidates; rows passing the whole CNF form the
+// query's messenger list; only those rows are scored (FP32) and selected.
+lr_status run_tbr_search(lr_index *ix, const float *q, int B, const lr_filters *f, const int32_t *k, int k_all,
+                         int32_t *out_ids, float *out_scores, int32_t *out_count, const lr_search_stats *stats,
+                         cudaStream_t s, const TbrPlan &T, int64_t cap) {
+  const int turn = ix->filt_turn;
+  ix->filt_turn ^= 1;
+  if (ix->filt_ev_live[turn]) LR_CK(cudaEventSynchronize(ix->filt_ev[turn]));
+  char *stage = ix->filt_h[turn];
+  Compiled C;
+  lr_status st = compile_filters(ix, f, B, kTcMaxQ, stage, C);
+  if (st != LR_OK) return st;
+  int32_t *kf = (int32_t *)(stage + C.off_kfin);
+  for (int b = 0; b < B; ++b) {
+    const int kb = k ? k[b] : k_all;
+    if (kb < 1 || kb > ix->max_k || kb > k_all) return fail(LR_ERR_INVALID, "K must be in [1, min(max_k, k_all)]");
+    kf[b] = kb;
+  }
+  // posting ranges of every query's chosen clause, with each term's bitmap
+  const size_t off_roff = align_up(C.bytes, 16);
+  const size_t off_rng = align_up(off_roff + sizeof(int32_t) * (B + 1), 16);
+  int32_t *roff = (int32_t *)(stage + off_roff);
+  TbrRange *rng = (TbrRange *)(stage + off_rng);
+  const size_t bm_words = (size_t)ix->n_words;
+  int R = 0;
+  roff[0] = 0;
+  for (int b = 0; b < B; ++b) {
+    const int c = T.clause[b];
+    for (int i = f->c_off[c]; i < f->c_off[c + 1]; ++i) {
+      const int32_t t = (int32_t)f->terms[i];
+      bool seen = false;
+      for (int i2 = f->c_off[c]; i2 < i; ++i2) seen |= (int32_t)f->terms[i2] == t;
+      if (seen) continue;
+      if (off_rng + sizeof(TbrRange) * (R + 1) > ix->filt_bytes)
+        return fail(LR_ERR_WORKSPACE, "filters: staging area too small");
+      TbrRange r;
+      r.begin = ix->post_off_h[t];
+      r.end = ix->post_off_h[t + 1];
+      r.bm = ix->term_dense[t] >= 0 ? ix->dense_bm + (size_t)ix->term_dense[t] * bm_words
+                                    : ix->sparse_bm + (size_t)ix->sparse_id[t] * bm_words;
+      std::memcpy(rng + R, &r, sizeof(TbrRange));
+      ++R;
+    }
+    roff[b + 1] = R;
+  }
+  const size_t bytes = off_rng + sizeof(TbrRange) * std::max(R, 1);
+  int32_t n_launch = 0;
+  LR_CK(cudaMemcpyAsync(ix->filt_d, stage, bytes, cudaMemcpyHostToDevice, s));
+  LR_CK(cudaEventRecord(ix->filt_ev[turn], s));
+  ix->filt_ev_live[turn] = true;
+  LR_CK(cudaMemsetAsync(ix->state, 0, ix->state_bytes, s));
+  const int32_t *kfin_d = (const int32_t *)(ix->filt_d + C.off_kfin);
+  const float *qsrc = q;
+  if (!is_device_ptr(q)) {
+    LR_CK(cudaMemcpyAsync(ix->q_raw, q, sizeof(float) * (size_t)B * ix->dim, cudaMemcpyHostToDevice, s));
+    qsrc = ix->q_raw;
+  }
+  LR_LAUNCH(launch_prep_queries(qsrc, ix->q_ws, B, ix->dim, ix->d_pad, ix->metric == LR_COSINE, ix->err, s));
+  if (!C.sparse_terms.empty()) {
+    ++n_launch;
+    LR_CK(expand_sparse_terms(ix, C, s));
+  }
+  if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
+  int32_t n_scan = 0;
+  for (const SubBatch &sb : C.subs) {
+    TbrArgs a{};
+    a.n = ix->n;
+    a.q_base = sb.q_base;
+    a.nq = sb.nq;
+    a.slot_bm = (const uint32_t *const *)(ix->filt_d + sb.off_slots);
+    a.qc_off = (const int32_t *)(ix->filt_d + sb.off_qc);
+    a.cl_off = (const int32_t *)(ix->filt_d + sb.off_cl);
+    a.cl_slot = (const int32_t *)(ix->filt_d + sb.off_cs);
+    a.r_off = (const int32_t *)(ix->filt_d + off_roff);
+    a.ranges = (const TbrRange *)(ix->filt_d + off_rng);
+    a.post_ids = ix->post_ids_d;
+    a.buf = ix->cand_buf;
+    a.cap = cap;
+    a.cnt = ix->cnt;
+    a.pass_cnt = ix->pass;
+    a.err = ix->err;
+    LR_LAUNCH(launch_tbr_collect(a, ix->num_sms, T.max_postings, s));
+    ++n_scan;
+  }
+  LR_LAUNCH(launch_sign_rescore(ix->X, ix->d_pad, ix->q_ws, ix->cand_buf, cap, ix->cnt, B, ix->num_sms, s));
+  ++n_scan;
+  if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
+  const bool dev_out = is_device_ptr(out_ids) && is_device_ptr(out_scores) &&
+                       (out_count == nullptr || is_device_ptr(out_count));
+  if (!dev_out && k_all > ix->max_k) return fail(LR_ERR_INVALID, "host outputs need k_all <= max_k");
+  SelectArgs fa{};
+  fa.mode = 1;
+  fa.buf = ix->cand_buf;
+  fa.cap = cap;
+  fa.cnt = ix->cnt;
+  fa.overflow = ix->ovf;
+  fa.k = kfin_d;
+  fa.pass_cnt = ix->pass;
+  fa.k_stride = k_all;
+  fa.out_ids = dev_out ? out_ids : ix->o_ids;
+  fa.out_scores = dev_out ? out_scores : ix->o_sc;
+  fa.out_count = dev_out ? out_count : ix->o_cnt;
+  fa.flag = ix->flag;
+  fa.n_flagged = ix->n_flag;
+  fa.fb_prefix = ix->prefix;
+  fa.fb_krem = ix->krem;
+  fa.cand_count_out = ix->o_cand;
+  fa.fallback_out = ix->o_fb;
+  fa.err = ix->err;
+  fa.id_base = ix->id_base;
+  LR_LAUNCH(launch_select(fa, B, s));
+  bool need_sync = false;
+  if (!dev_out) {
+    LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
+    LR_CK(cudaMemcpyAsync(out_scores, ix->o_sc, sizeof(float) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
+    if (out_count) LR_CK(cudaMemcpyAsync(out_count, ix->o_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
+    need_sync = true;
+  }
+  if (stats) {
+    if (stats->n_launches) *stats->n_launches = n_launch;
+    if (stats->n_scan_launches) *stats->n_scan_launches = n_scan;
+    if (stats->plan_used) *stats->plan_used = LR_PLAN_TBR;
+    struct { void *dst; const void *src; size_t bytes; } cp[3] = {
+        {stats->pass_count, ix->pass, sizeof(int64_t) * B},
+        {stats->cand_count, ix->o_cand, sizeof(int32_t) * B},
+        {stats->fallback, ix->o_fb, sizeof(int32_t) * B}};
+    for (auto &c : cp) {
+      if (!c.dst) continue;
+      LR_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, s));
+      need_sync |= !is_device_ptr(c.dst);
+    }
+  }
+  if (need_sync) LR_CK(cudaStreamSynchronize(s));
+  return LR_OK;
+}
+
 lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, const int32_t *k, int k_all,
                      int32_t *out_ids, float *out_scores, int32_t *out_count, const lr_search_opts *opts,
                      const lr_search_stats *stats, cudaStream_t s) {
@@ -1177,12 +1390,24 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // scoring plan: SIMT matrix-vector scan for small batches, tensor-core tiles
   // (3xTF32) once a launch serves enough queries to be a real contraction
   int plan = o.plan;
-  if (plan != LR_PLAN_AUTO && plan != LR_PLAN_GEMV && plan != LR_PLAN_TC)
-    return fail(LR_ERR_INVALID, "plan must be LR_PLAN_AUTO, LR_PLAN_GEMV or LR_PLAN_TC");
+  if (plan != LR_PLAN_AUTO && plan != LR_PLAN_GEMV && plan != LR_PLAN_TC && plan != LR_PLAN_TBR)
+    return fail(LR_ERR_INVALID, "plan must be LR_PLAN_AUTO, LR_PLAN_GEMV, LR_PLAN_TC or LR_PLAN_TBR");
   const bool lowp = ix->elem != kElemF32;
   const bool tc_ok = lowp ? ix->have_tmap_q : ix->have_tmap;
   std::vector<double> est;  // estimated pass rate per filter
   const bool have_est = estimate_pass_rates(ix, f, B, est);
+  // the automatic plan considers TBR first only when no scan option is forced
+  const bool scan_opts = o.sample_stride != 0 || o.cand_cap != 0 || o.force_exact_fallback != 0;
+  if (plan == LR_PLAN_TBR || (plan == LR_PLAN_AUTO && have_est && !scan_opts)) {
+    int64_t tcap = ix->cand_cap;
+    if (o.cand_cap > 0) tcap = std::min<int64_t>(tcap, o.cand_cap);
+    const TbrPlan T = plan_tbr(ix, f, B, tcap);
+    if (plan == LR_PLAN_TBR && !T.ok)
+      return fail(LR_ERR_UNSUPPORTED, "TBR-first plan needs posting lists, a clause per query and a chosen clause "
+                                      "with at most the candidate capacity of postings and 16 distinct terms");
+    if (plan == LR_PLAN_TBR || (T.ok && tbr_cheaper(ix, B, T, est, tc_ok)))
+      return run_tbr_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, stats, s, T, tcap);
+  }
   if (plan == LR_PLAN_AUTO) plan = choose_plan(B, tc_ok, have_est, est);
   if (plan == LR_PLAN_TC && !tc_ok)
     return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable for this index (no TMA descriptor; "

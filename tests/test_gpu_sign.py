@@ -42,7 +42,7 @@ def corpus():
     return datagen.corpus(41, 70_001, 64, 1024, 16.0, 1.1)
 
 
-@pytest.mark.parametrize("quant_mult,max_qk", [(4, 0), (20, 0), (50, 600)])
+@pytest.mark.parametrize("quant_mult,max_qk", [(4, 0), (20, 0), (1, 40)])
 @pytest.mark.parametrize("metric", ["cosine", "dot"])
 def test_sign_search_matches_the_oracle(lr, corpus, quant_mult, max_qk, metric):
     c = corpus
