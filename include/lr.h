@@ -399,6 +399,25 @@ lr_status lr_score_backward(const void *Q, const void *J, int32_t B, int32_t M, 
                             const int32_t *pos, const uint32_t *mask_bits, float inv_tau, const float *lse,
                             const float *dloss, float *dQ, float *dJ, void *workspace, size_t workspace_bytes,
                             void *stream);
+/*
+ * Online hard-negative mining (Sec. 5.1, "Online Hard Negative Sampling"; Sec.
+ * 5.2, the second curriculum stage): for every query i the n_neg allowed
+ * columns j != pos[i] with the highest score <Q_i, J_j> (BF16 operands, FP32
+ * accumulation, the loss kernels' tensor-core product), ordered by (score desc,
+ * column asc).  "Allowed" is the loss's mask (bit j of row i of mask_bits, or
+ * every column when NULL).  out_ids / out_scores [B][n_neg] device (-1 / -inf
+ * past out_count), out_count [B] (nullable unless out_mask is given):
+ * min(n_neg, allowed negatives).  out_mask (nullable) [B][ceil(M/32)] device:
+ * the mined columns as a loss mask, so lr_score_forward / lr_score_backward with
+ * it compute the loss over each query's positive and its hard negatives only
+ * (the m x k training matrix of Sec. 5.1).  1 <= n_neg <= min(4096, M); other
+ * arguments as lr_score_forward; workspace: lr_hard_negatives_workspace_size.
+ */
+size_t lr_hard_negatives_workspace_size(int32_t B, int32_t M, int32_t d);
+lr_status lr_hard_negatives(const void *Q, const void *J, int32_t B, int32_t M, int32_t d, int32_t dtype,
+                            const int32_t *pos, const uint32_t *mask_bits, int32_t n_neg, int32_t *out_ids,
+                            float *out_scores, int32_t *out_count, uint32_t *out_mask, void *workspace,
+                            size_t workspace_bytes, void *stream);
 /* Synchronise `stream` and report (then clear) a device wait timeout of the last loss call on `workspace`. */
 lr_status lr_score_status(void *workspace, int32_t B, int32_t M, int32_t d, void *stream);
 

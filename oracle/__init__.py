@@ -15,6 +15,8 @@ Contents, each written from the paper's definitions:
   * ``sign_codes``, ``sign_search`` -- the sign-bit pre-selection of the appendix "Quantization"
                        (Eq. 4 agreement count, whole score levels kept down to quantK jobs) followed by the
                        exact FP64 rescoring of the kept jobs.
+  * ``hard_negatives`` -- the online hard negatives of Sec. 5.1: per query the top allowed columns
+                       other than its positive by the tower score.
   * ``recall_at_k`` -- Eq. (recall@k) of Sec. 6.2: mean over queries of |R_i ∩ A_i| / |A_i|.
   * ``softmax_loss`` -- the in-batch / sampled softmax loss of Sec. 5.1 (P(J_j|S_i) = e^{z_ij}/sum_k e^{z_ik},
                        L = -(1/N) sum_i log P(J_pos(i) | S_i)) with the term mask setting failing jobs to
@@ -225,6 +227,30 @@ def sign_search(X, job_off, job_terms, Q, f, k, codes, qcodes, quant_k, cap: int
     if rc:
         raise RuntimeError("oracle_sign_search failed")
     return SearchResult(ids, sc, cnt, ncand), ncand
+
+
+def hard_negatives(Q, J, pos, allowed, n_neg: int):
+    """Online hard negatives of Sec. 5.1: per query i, the n_neg columns j != pos[i] allowed for i with the
+    highest <Q_i, J_j> (FP64 of the given values), ordered by (score desc, j asc).  allowed: bool [B][M] or
+    None (every column).  Returns (ids int64 [B][n_neg], scores float64 [B][n_neg], count int64 [B]) padded
+    with (-1, -inf)."""
+    Qd = np.asarray(Q, dtype=np.float64)
+    Jd = np.asarray(J, dtype=np.float64)
+    B, M = Qd.shape[0], Jd.shape[0]
+    S = Qd @ Jd.T
+    ids = np.full((B, n_neg), -1, dtype=np.int64)
+    sc = np.full((B, n_neg), -np.inf, dtype=np.float64)
+    cnt = np.zeros(B, dtype=np.int64)
+    cols = np.arange(M)
+    for i in range(B):
+        ok = np.ones(M, dtype=bool) if allowed is None else np.asarray(allowed[i], dtype=bool).copy()
+        ok[int(pos[i])] = False
+        cand = cols[ok]
+        order = np.lexsort((cand, -S[i, cand]))[:n_neg]
+        cnt[i] = order.size
+        ids[i, :order.size] = cand[order]
+        sc[i, :order.size] = S[i, cand[order]]
+    return ids, sc, cnt
 
 
 def recall_at_k(retrieved: Sequence[Sequence[int]], relevant: Sequence[Sequence[int]]) -> float:

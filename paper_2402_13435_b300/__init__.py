@@ -30,7 +30,8 @@ _PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC, "tbr": LR
 
 SYMBOLS = ("lr_index_create", "lr_index_destroy", "lr_index_device_bytes", "lr_search", "lr_search_ex",
            "lr_filter_count", "lr_index_sync", "lr_last_error_message", "lr_version", "lr_merge_topk",
-           "lr_search_noalloc", "lr_search_noalloc_status", "lr_topk", "lr_topk_workspace_size", "lr_sign_encode")
+           "lr_search_noalloc", "lr_search_noalloc_status", "lr_topk", "lr_topk_workspace_size", "lr_sign_encode", "lr_hard_negatives",
+           "lr_hard_negatives_workspace_size")
 
 
 class LRError(RuntimeError):
@@ -540,6 +541,34 @@ def lr_score_backward(Q, J, pos, mask_bits, inv_tau: float, lse, dloss=None, wor
                                   _ptr(lse), _ptr(dloss), _ptr(dQ), _ptr(dJ), _ptr(ws), ws.numel(),
                                   _stream_ptr(stream)), "lr_score_backward")
     return dQ, dJ
+
+
+_lib.lr_hard_negatives_workspace_size.argtypes = [_i32, _i32, _i32]
+_lib.lr_hard_negatives_workspace_size.restype = ctypes.c_size_t
+_lib.lr_hard_negatives.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
+                                   ctypes.c_size_t, _vp]
+_lib.lr_hard_negatives.restype = ctypes.c_int
+
+
+def lr_hard_negatives(Q, J, pos, n_neg: int, mask_bits=None, want_mask: bool = True, workspace=None, stream=None):
+    """Online hard negatives (Sec. 5.1): per query the n_neg allowed columns (not its positive) with the
+    highest <Q_i, J_j>.  Returns (ids [B][n_neg] int32, scores [B][n_neg] FP32, count [B] int32, mask
+    [B][ceil(M/32)] int32 or None) -- the mask feeds lr_score_forward / masked_softmax_loss."""
+    import torch
+
+    B, M, d, dt = _loss_shapes(Q, J, pos, mask_bits)
+    n = int(_lib.lr_hard_negatives_workspace_size(B, M, d))
+    if n == 0:
+        raise ValueError("unsupported shape (d must be in [1, 128])")
+    ws = workspace if workspace is not None else torch.empty(n, dtype=torch.uint8, device=Q.device)
+    ids = torch.empty((B, n_neg), dtype=torch.int32, device=Q.device)
+    sc = torch.empty((B, n_neg), dtype=torch.float32, device=Q.device)
+    cnt = torch.empty(B, dtype=torch.int32, device=Q.device)
+    mask = torch.empty((B, (M + 31) // 32), dtype=torch.int32, device=Q.device) if want_mask else None
+    _check(_lib.lr_hard_negatives(_ptr(Q), _ptr(J), B, M, d, dt, _ptr(pos), _ptr(mask_bits), int(n_neg), _ptr(ids),
+                                  _ptr(sc), _ptr(cnt), _ptr(mask), _ptr(ws), ws.numel(), _stream_ptr(stream)),
+           "lr_hard_negatives")
+    return ids, sc, cnt, mask
 
 
 def lr_score_status(workspace, B: int, M: int, d: int, stream=None) -> None:

@@ -15,6 +15,10 @@
 //   kDq:  R = queries, C = jobs; dZ tile -> acc[128 x d] += dZ C, with C's
 //         transposed copy as the K-major B operand.
 //   kDj:  R = jobs, C = queries; the same with dZ^T, acc[128 x d] += dZ^T Q.
+//   kKeys: R = queries, C = jobs; the raw scores <q_i, j_j> of every allowed
+//         negative (allowed column, not the positive) as selection keys
+//         (ordered score, ~column), 0 for the others, plus per-query counts --
+//         the in-batch hard-negative mining of Sec. 5.1 ranks them.
 // dZ enters the second product as two BF16 terms (hi + lo, near-FP32 accuracy).
 // Warps 0-3: epilogue (TMEM lane quarters); warp 4: TMA; warp 5: MMA issue.
 // Every wait is bounded; a timeout sets the status word.
@@ -36,7 +40,7 @@ constexpr int kCBufs = 3;          // streamed-tile buffers: a tile loads while 
 constexpr uint32_t kLossTmemCols = 256;  // 2 score tiles of 64 columns + accumulator (<= 128)
 constexpr float kLog2e = 1.4426950408889634f;
 
-enum LossMode : int { kFwd = 0, kDq = 1, kDj = 2 };
+enum LossMode : int { kFwd = 0, kDq = 1, kDj = 2, kKeys = 3 };
 
 struct LossSmem {
   size_t r, c, ct, dz, stage, bars, holder, total;
@@ -58,9 +62,10 @@ __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
   L.c = off;
   off += (size_t)kCBufs * (dp / 64) * kCRows * 128;
   L.ct = off;
-  off += mode == kFwd ? 0 : (size_t)kCBufs * dp * 128;  // transposed C tile: dp rows x 64 values
+  const bool one_product = mode == kFwd || mode == kKeys;
+  off += one_product ? 0 : (size_t)kCBufs * dp * 128;  // transposed C tile: dp rows x 64 values
   L.dz = off;
-  off += mode == kFwd ? 0 : (size_t)2 * 2 * kRRows * 128;  // [buffer][hi, lo] 128 rows x 64 values
+  off += one_product ? 0 : (size_t)2 * 2 * kRRows * 128;  // [buffer][hi, lo] 128 rows x 64 values
   L.stage = off;
   off += mode == kDj ? 4 * sizeof(DjStage) : 0;  // two per epilogue set
   L.bars = off;
@@ -82,6 +87,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
            const __grid_constant__ CUtensorMap tm_ct) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  constexpr bool kOne = MODE == kFwd || MODE == kKeys;  // the score product only
   const int dp = a.dp;
   const LossSmem L = loss_smem(dp, MODE);
   const int KB = dp / 64;  // 64-value K-blocks of the score product
@@ -140,10 +146,10 @@ __global__ void __launch_bounds__(kLossThreads, 1)
           break;
         }
         const int c0 = (t0 + t) * kCRows;
-        mbar_arrive_expect_tx(&c_full[b], (uint32_t)(c_bytes + (MODE == kFwd ? 0 : ct_bytes)));
+        mbar_arrive_expect_tx(&c_full[b], (uint32_t)(c_bytes + (kOne ? 0 : ct_bytes)));
         for (int kb = 0; kb < KB; ++kb)
           tma_load_2d(sc + (size_t)b * c_bytes + (size_t)kb * kCRows * 128, &tm_c, kb * 64, c0, &c_full[b]);
-        if (MODE != kFwd) tma_load_2d(sct + (size_t)b * ct_bytes, &tm_ct, c0, 0, &c_full[b]);
+        if (!kOne) tma_load_2d(sct + (size_t)b * ct_bytes, &tm_ct, c0, 0, &c_full[b]);
         issued = t + 1;
       }
       if (!ok) {
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         }
         issued = true;
         mma_commit(&s_full[b]);
-        if (MODE == kFwd) mma_commit(&c_empty[cb]);
+        if (kOne) mma_commit(&c_empty[cb]);
         return true;
       };
       if (!mbar_wait(bar_r, 0u)) ok = false;
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
           ok = false;
           break;
         }
-        if (MODE != kFwd) {
+        if (!kOne) {
           const int b = t & 1;
           if (!mbar_wait(&dz_full[b], (uint32_t)((t >> 1) & 1))) {
             ok = false;
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     // 32 (w % 4) ..
     // the forward epilogue is issue-bound with one set, and two CTAs of 192
     // threads share an SM: it launches without warps 6-9
-    constexpr int kSets = MODE == kFwd ? 1 : 2;
+    constexpr int kSets = kOne ? 1 : 2;
     const int eset = warp >= 6 ? 1 : 0, quarter = warp & 3;
     const bool active = eset < kSets;
     const int r = quarter * 32 + lane;
@@ -236,6 +242,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     }
     float m = -INFINITY, ssum = 0.f, zpos = 0.f;
     bool have_pos = false;
+    unsigned long long negc = 0;  // kKeys: allowed negatives of the row
     // Mask words (and for kDj the query tile's positives and lse) are fetched
     // one tile of the set ahead.  kFwd/kDq: this row's two words, in registers.
     // kDj: the set's 128 threads stage the query tile in shared memory (double
@@ -371,6 +378,28 @@ __global__ void __launch_bounds__(kLossThreads, 1)
             if (c == pc) zpos = __uint_as_float(sv[c]) * a.inv_tau;
           have_pos = true;
         }
+      } else if (MODE == kKeys) {
+        if (rvalid) {
+          uint32_t nb[2] = {al[0], al[1]};  // allowed columns without the positive
+          const int pc = pos_row - c0;
+          if (pc >= 0 && pc < 32) nb[0] &= ~(1u << pc);
+          if (pc >= 32 && pc < 64) nb[1] &= ~(1u << (pc - 32));
+          negc += (unsigned long long)(__popc(nb[0]) + __popc(nb[1]));
+          uint64_t *krow = a.keys + (size_t)grow * (size_t)a.keys_ld + c0;
+          const int lim = a.M - c0 < 64 ? a.M - c0 : 64;
+#pragma unroll
+          for (int c = 0; c < 64; c += 2) {
+            const uint64_t k0 =
+                ((nb[c >> 5] >> (c & 31)) & 1u) ? make_key(__uint_as_float(sv[c]), (uint32_t)(c0 + c)) : 0ull;
+            const uint64_t k1 = ((nb[(c + 1) >> 5] >> ((c + 1) & 31)) & 1u)
+                                    ? make_key(__uint_as_float(sv[c + 1]), (uint32_t)(c0 + c + 1))
+                                    : 0ull;
+            if (c + 1 < lim)
+              *reinterpret_cast<ulonglong2 *>(krow + c) = make_ulonglong2(k0, k1);
+            else if (c < lim)
+              krow[c] = k0;
+          }
+        }
       } else {
         // dZ of this tile as two BF16 terms, written in the 128-byte-swizzled K-major layout
         if (!wwait(&dz_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u, lane)) {
@@ -428,6 +457,8 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         a.part_s[(size_t)blockIdx.y * a.rows_p + grow] = ssum;
         if (have_pos) a.zpos[grow] = zpos;
       }
+    } else if (MODE == kKeys) {
+      if (rvalid && negc) atomicAdd(&a.neg_cnt[grow], negc);
     } else if (eset == 0) {  // set 0 writes the accumulated rows
       if (!wwait(acc_full, 0u, lane)) ok = false;
       tc_fence_after();
@@ -524,7 +555,39 @@ __global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_str
   dQ[i] = s;
 }
 
+// Per query: the selection's K and the key row's length.
+__global__ void k_hn_setup(int B, int n_neg, int M, int32_t *kq, uint32_t *cnt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B) return;
+  kq[q] = n_neg;
+  cnt[q] = (uint32_t)M;
+}
+
+// The mined negatives as loss mask bits (bit j of row q: job j is one of q's hard
+// negatives); the rows were cleared before.
+__global__ void k_hn_mask(const int32_t *ids, const int32_t *count, int B, int n_neg, int Mw, uint32_t *mask) {
+  const int q = blockIdx.y;
+  const int n = count[q];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n && i < n_neg; i += gridDim.x * blockDim.x) {
+    const int j = ids[(size_t)q * n_neg + i];
+    if (j >= 0 && (j >> 5) < Mw) atomicOr(&mask[(size_t)q * Mw + (j >> 5)], 1u << (j & 31));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_hn_setup(int B, int n_neg, int M, int32_t *kq, uint32_t *cnt, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_hn_setup<<<(B + 255) / 256, 256, 0, s>>>(B, n_neg, M, kq, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hn_mask(const int32_t *ids, const int32_t *count, int B, int n_neg, int Mw, uint32_t *mask,
+                           cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_hn_mask<<<dim3((unsigned)((n_neg + 255) / 256), (unsigned)B), 256, 0, s>>>(ids, count, B, n_neg, Mw, mask);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
                              cudaStream_t s) {
@@ -558,6 +621,11 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
       e = allow_dynamic_smem((const void *)k_loss<kDj>, (size_t)smem);
       if (e != cudaSuccess) return e;
       k_loss<kDj><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
+      break;
+    case kKeys:
+      e = allow_dynamic_smem((const void *)k_loss<kKeys>, (size_t)smem);
+      if (e != cudaSuccess) return e;
+      k_loss<kKeys><<<grid, kLossFwdThreads, smem, s>>>(a, r, c, ct);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -289,7 +289,13 @@ struct LossArgs {
   size_t out_split;        // elements between splits of out
   int32_t out_ld, out_cols;
   uint32_t *status;        // device status word (timeouts)
+  uint64_t *keys;          // hard negatives: [rows_p][keys_ld] selection keys of the allowed negatives
+  int64_t keys_ld;
+  unsigned long long *neg_cnt;  // [B] allowed negatives per query
 };
+cudaError_t launch_hn_setup(int B, int n_neg, int M, int32_t *kq, uint32_t *cnt, cudaStream_t s);
+cudaError_t launch_hn_mask(const int32_t *ids, const int32_t *count, int B, int n_neg, int Mw, uint32_t *mask,
+                           cudaStream_t s);
 cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
                              cudaStream_t s);
 cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y, const void *tm_r, const void *tm_c,

@@ -1956,6 +1956,89 @@ lr_status lr_score_backward(const void *Q, const void *J, int32_t B, int32_t M, 
   return LR_OK;
 }
 
+// ---------------------------------------------------------------- hard negatives
+// Workspace of lr_hard_negatives: the loss passes' operand copies, then the
+// selection keys [Bp][Mp] and the per-query selection state.
+struct HnLayout {
+  size_t keys, negc, cnt, kq, ovf, flag, nflag, err, prefix, krem, zero_end, total;
+};
+
+HnLayout hn_layout(const LossPlan &P, int B) {
+  HnLayout H{};
+  Carver cv;
+  cv.off = P.total;
+  H.keys = cv.take<uint64_t>((size_t)P.Bp * P.Mp);
+  H.negc = cv.take<unsigned long long>(B);
+  H.cnt = cv.take<uint32_t>(B);
+  H.ovf = cv.take<uint32_t>(B);
+  H.flag = cv.take<uint32_t>(B);
+  H.nflag = cv.take<uint32_t>(1);
+  H.err = cv.take<uint32_t>(1);
+  H.prefix = cv.take<uint64_t>(B);
+  H.krem = cv.take<int32_t>(B);
+  H.zero_end = cv.take<char>(0);
+  H.kq = cv.take<int32_t>(B);
+  H.total = align_up(cv.off, 256);
+  return H;
+}
+
+size_t lr_hard_negatives_workspace_size(int32_t B, int32_t M, int32_t d) {
+  if (B < 1 || M < 1 || d < 1 || d > 128) return 0;
+  return hn_layout(loss_plan(B, M, d, current_sms()), B).total;
+}
+
+lr_status lr_hard_negatives(const void *Q, const void *J, int32_t B, int32_t M, int32_t d, int32_t dtype,
+                            const int32_t *pos, const uint32_t *mask_bits, int32_t n_neg, int32_t *out_ids,
+                            float *out_scores, int32_t *out_count, uint32_t *out_mask, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const LossPlan P = loss_plan(B, M, d, current_sms());
+  lr_status st = loss_check(Q, J, B, M, d, dtype, pos, mask_bits, workspace, P.total, P);
+  if (st != LR_OK) return st;
+  const HnLayout H = hn_layout(P, B);
+  if (workspace_bytes < H.total) return fail(LR_ERR_WORKSPACE, "workspace smaller than lr_hard_negatives_workspace_size()");
+  if (n_neg < 1 || n_neg > kMaxK || n_neg > M) return fail(LR_ERR_INVALID, "n_neg must be in [1, min(4096, M)]");
+  if (!out_ids || !out_scores || !is_device_ptr(out_ids) || !is_device_ptr(out_scores) ||
+      (out_count && !is_device_ptr(out_count)) || (out_mask && !is_device_ptr(out_mask)))
+    return fail(LR_ERR_INVALID, "outputs must be device memory");
+  if (out_mask && !out_count) return fail(LR_ERR_INVALID, "out_mask needs out_count");
+  char *w = (char *)workspace;
+  LossMaps T;
+  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, s);
+  if (st != LR_OK) return st;
+  LR_CK(cudaMemsetAsync(w + H.negc, 0, H.zero_end - H.negc, s));
+  LossArgs a = loss_args(B, M, 1.0f, pos, mask_bits, w, P);
+  a.keys = (uint64_t *)(w + H.keys);
+  a.keys_ld = P.Mp;
+  a.neg_cnt = (unsigned long long *)(w + H.negc);
+  LR_CK(launch_loss_pass(3, a, P.Bp / 128, P.splits, &T.qr, &T.jc, nullptr, s));
+  LR_CK(launch_hn_setup(B, n_neg, M, (int32_t *)(w + H.kq), (uint32_t *)(w + H.cnt), s));
+  SelectArgs fa{};
+  fa.mode = 1;
+  fa.buf = a.keys;
+  fa.cap = P.Mp;
+  fa.cnt = (uint32_t *)(w + H.cnt);
+  fa.overflow = (uint32_t *)(w + H.ovf);
+  fa.k = (const int32_t *)(w + H.kq);
+  fa.pass_cnt = a.neg_cnt;
+  fa.k_stride = n_neg;
+  fa.out_ids = out_ids;
+  fa.out_scores = out_scores;
+  fa.out_count = out_count;
+  fa.flag = (uint32_t *)(w + H.flag);
+  fa.n_flagged = (uint32_t *)(w + H.nflag);
+  fa.fb_prefix = (uint64_t *)(w + H.prefix);
+  fa.fb_krem = (int32_t *)(w + H.krem);
+  fa.err = (uint32_t *)(w + H.err);
+  LR_CK(launch_select(fa, B, s));
+  if (out_mask) {
+    const int Mw = (M + 31) / 32;
+    LR_CK(cudaMemsetAsync(out_mask, 0, sizeof(uint32_t) * (size_t)B * Mw, s));
+    LR_CK(launch_hn_mask(out_ids, out_count, B, n_neg, Mw, out_mask, s));
+  }
+  return LR_OK;
+}
+
 lr_status lr_score_status(void *workspace, int32_t B, int32_t M, int32_t d, void *stream) {
   if (!workspace) return fail(LR_ERR_INVALID, "workspace is null");
   const LossPlan P = loss_plan(B, M, d, current_sms());

@@ -284,7 +284,7 @@ def test_unknown_plan_is_rejected(lr, small):
     out_i = torch.empty((2, 5), dtype=torch.int32, device="cuda")
     out_s = torch.empty((2, 5), dtype=torch.float32, device="cuda")
     fc = lr.Filters.of(Filters.from_lists([[], []])).c()
-    for plan in (3, -1):
+    for plan in (4, -1):
         opts = lr.lr_search_opts(plan=plan)
         rc = lr._lib.lr_search_ex(lr.ctypes.c_void_p(idx.handle), lr._ptr(qd), 2, lr.ctypes.byref(fc), None, 5,
                                   lr._ptr(out_i), lr._ptr(out_s), None, lr.ctypes.byref(opts), None, None)

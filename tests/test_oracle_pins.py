@@ -490,3 +490,33 @@ def test_sign_search_levels_by_brute_force():
             assert got.ids[b, :m].tolist() == kept[order].tolist()
             assert np.all(got.ids[b, m:] == -1)
             assert ncand[b] <= max(cap, 0) or want == 0
+
+
+# ------------------------------------------------------------------ hard negatives (Sec. 5.1)
+def test_hard_negatives_brute_force_and_special_cases():
+    """Brute force over tiny inputs (the unique best subset), the positive and masked columns never
+    chosen, every column when n_neg = M - 1, fewer than n_neg allowed pads."""
+    rng = np.random.default_rng(51)
+    for trial in range(40):
+        B, M = 2, int(rng.integers(2, 9))
+        Q = (rng.integers(-2, 3, size=(B, 3)) / 2.0)
+        J = (rng.integers(-2, 3, size=(M, 3)) / 2.0)
+        pos = rng.integers(0, M, size=B)
+        allowed = rng.random((B, M)) < 0.7
+        n_neg = int(rng.integers(1, M + 1))
+        ids, sc, cnt = oracle.hard_negatives(Q, J, pos, allowed, n_neg)
+        for i in range(B):
+            cand = [j for j in range(M) if allowed[i, j] and j != pos[i]]
+            s = {j: float(Q[i] @ J[j]) for j in cand}
+            kk = min(n_neg, len(cand))
+            better = lambda a, b: s[a] > s[b] or (s[a] == s[b] and a < b)
+            best = [set(S) for S in itertools.combinations(cand, kk)
+                    if all(better(a, b) for a in S for b in cand if b not in S)]
+            assert len(best) == 1 and set(ids[i, :kk].tolist()) == best[0] and cnt[i] == kk
+            assert all(better(ids[i, t], ids[i, t + 1]) for t in range(kk - 1))
+            assert np.all(ids[i, kk:] == -1) and np.all(np.isneginf(sc[i, kk:]))
+    Q = rng.standard_normal((3, 4))
+    J = rng.standard_normal((10, 4))
+    ids, _, cnt = oracle.hard_negatives(Q, J, [0, 5, 9], None, 9)
+    for i, p in enumerate([0, 5, 9]):
+        assert cnt[i] == 9 and sorted(ids[i].tolist()) == [j for j in range(10) if j != p]
