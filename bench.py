@@ -57,7 +57,10 @@ def parse():
     #   --form serve  continuous batching over a resident 20M x 128 BF16 index, Poisson request streams
     #   --form sweep  selectivity sweep: each band alone at batch sizes --sweep-batches, per-point roofline
     #   --form topk   appendix "Fast Top K Selection": top 2,000 of 1,000,000 scores, bucket vs radix vs sort
-    p.add_argument("--form", choices=("search", "loss", "serve", "sweep", "topk", "sign"), default="search")
+    #   --form hardneg  in-batch hard-negative mining (top --n-neg per query) + the loss over the mined set
+    p.add_argument("--form", choices=("search", "loss", "serve", "sweep", "topk", "sign", "hardneg"),
+                   default="search")
+    p.add_argument("--n-neg", type=int, default=1024)
     p.add_argument("--topk-n", type=int, default=1_000_000)
     p.add_argument("--topk-k", type=int, default=2000)
     p.add_argument("--topk-rows", type=int, default=1)
@@ -937,6 +940,66 @@ def run_sign(args):
     print(json.dumps(out), flush=True)
 
 
+def run_hardneg(args):
+    """Second-stage training step of Sec. 5.2: mine each query's top n_neg negatives among the in-batch
+    positives and sampled jobs (allowed by the term mask), then the loss forward and backward over the
+    positive and the mined negatives only.  Times mining and loss separately (CUDA events)."""
+    import torch
+    import datagen
+    import paper_2402_13435_b300 as lr
+
+    B, M, d = args.loss_b, args.loss_m, args.dim
+    inv_tau = 1.0 / args.tau
+    c = datagen.corpus(args.seed, M, d, 4096, 20.0, 1.1)
+    Q = torch.from_numpy(datagen.query_embeddings(args.seed + 1, B, d)).to(torch.bfloat16).cuda()
+    J = torch.from_numpy(c.X).to(torch.bfloat16).cuda()
+    pos = torch.arange(B, dtype=torch.int32, device="cuda")
+    f = datagen.filters(args.seed + 2, B, c.V, 1.1)
+    idx = lr.lr_index_create(c.X, c.V, bitsets=c.bitsets(), metric="dot", max_batch=B, max_k=16,
+                             max_batch_terms=16 * B)
+    npass, mask = lr.lr_filter_count(idx, f, bitmap=True)
+    torch.cuda.synchronize()
+    ws = torch.empty(int(lr._lib.lr_hard_negatives_workspace_size(B, M, d)), dtype=torch.uint8, device="cuda")
+    lws = lr.loss_workspace(B, M, d)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    mine, fwd, bwd = [], [], []
+    for i in range(args.warmup + args.steps):
+        ev[0].record()
+        ids, sc, cnt, mined = lr.lr_hard_negatives(Q, J, pos, args.n_neg, mask_bits=mask, workspace=ws)
+        ev[1].record()
+        loss, lse = lr.lr_score_forward(Q, J, pos, mined, inv_tau, lws)
+        ev[2].record()
+        dQ, dJ = lr.lr_score_backward(Q, J, pos, mined, inv_tau, lse, None, lws)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            mine.append(ev[0].elapsed_time(ev[1]))
+            fwd.append(ev[1].elapsed_time(ev[2]))
+            bwd.append(ev[2].elapsed_time(ev[3]))
+    lr.lr_score_status(lws, B, M, d)
+    mm, fm, bm = (float(np.median(x)) for x in (mine, fwd, bwd))
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        peak, kind = float(pk["bf16_tflops"]), "measured (bf16 burst)"
+    except (OSError, KeyError, ValueError):
+        peak, kind = 1800.0, "fallback"
+    flops = 2.0 * B * M * d
+    out = {"metric": "hard-negative mining ms @B=%d M=%d d=%d top-%d BF16" % (B, M, d, args.n_neg), "value": mm,
+           "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "bf16", "data": "synthetic (seeded generator)",
+           "mine_ms": mm, "loss_fwd_ms_on_mined": fm, "loss_bwd_ms_on_mined": bm,
+           "config": {"workload": "%d queries vs %d in-batch positives + %d sampled jobs, term mask from the cfg-1 "
+                                  "filter generator (%.1f%% allowed), top %d negatives per query"
+                                  % (B, B, M - B, 100.0 * float(npass.sum()) / (B * M), args.n_neg),
+                      "B": B, "M": M, "d": d, "n_neg": args.n_neg},
+           "mined_mean": float(cnt.float().mean().item()),
+           "roofline": {"bound": "hbm", "note": "score product on the tensor cores (%.1f GFLOP) plus B x M 8-byte "
+                                                "keys written and read by the selection" % (flops / 1e9),
+                        "keys_bytes": 2 * 8.0 * B * M, "peak_tflops": peak, "peak_kind": kind,
+                        "tensor_tflops_achieved": flops / (mm / 1e3) / 1e12}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -951,6 +1014,8 @@ def main():
         run_topk(args)
     elif args.form == "sign":
         run_sign(args)
+    elif args.form == "hardneg":
+        run_hardneg(args)
     else:
         run_ours(args)
 
