@@ -58,7 +58,8 @@ def parse():
     #   --form sweep  selectivity sweep: each band alone at batch sizes --sweep-batches, per-point roofline
     #   --form topk   appendix "Fast Top K Selection": top 2,000 of 1,000,000 scores, bucket vs radix vs sort
     #   --form hardneg  in-batch hard-negative mining (top --n-neg per query) + the loss over the mined set
-    p.add_argument("--form", choices=("search", "loss", "serve", "sweep", "topk", "sign", "hardneg"),
+    #   --form peaks    device facts and library GEMM rates (cuBLAS via torch) for the roofline denominators
+    p.add_argument("--form", choices=("search", "loss", "serve", "sweep", "topk", "sign", "hardneg", "peaks"),
                    default="search")
     p.add_argument("--n-neg", type=int, default=1024)
     p.add_argument("--topk-n", type=int, default=1_000_000)
@@ -1000,6 +1001,57 @@ def run_hardneg(args):
     print(json.dumps(out), flush=True)
 
 
+def run_peaks(args):
+    """Device facts (SM count, L2 size, clocks) and the throughput of library dense products per type:
+    torch.matmul (cuBLAS) in BF16, TF32, FP32 without TF32 (SIMT), FP64, and torch._scaled_mm in FP8 e4m3,
+    each the best of 10 CUDA-event-timed calls after warm-up.  These are the denominators a fraction of
+    peak for those types would use; the HBM copy and BF16 peaks come from the driver's measurement."""
+    import torch
+
+    dev = torch.cuda.get_device_properties(0)
+    out = {"metric": "device peaks (library dense products)", "n_gpus": 1, "name": dev.name,
+           "sm_count": dev.multi_processor_count, "l2_bytes": int(getattr(dev, "L2_cache_size", 0)),
+           "total_mem_bytes": int(dev.total_memory), "rates_tflops": {}}
+
+    def timeit(fn, flops):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return flops / (best / 1e3) / 1e12
+
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    ab, bb = a.to(torch.bfloat16), b.to(torch.bfloat16)
+    out["rates_tflops"]["bf16"] = timeit(lambda: ab @ bb, 2.0 * n ** 3)
+    torch.backends.cuda.matmul.allow_tf32 = True
+    out["rates_tflops"]["tf32"] = timeit(lambda: a @ b, 2.0 * n ** 3)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["rates_tflops"]["fp32_no_tf32"] = timeit(lambda: a @ b, 2.0 * n ** 3)
+    m = 4096
+    a64, b64 = torch.randn(m, m, device="cuda", dtype=torch.float64), torch.randn(m, m, device="cuda",
+                                                                                   dtype=torch.float64)
+    out["rates_tflops"]["fp64"] = timeit(lambda: a64 @ b64, 2.0 * m ** 3)
+    try:
+        a8 = a.to(torch.float8_e4m3fn)
+        b8 = b.to(torch.float8_e4m3fn).t().contiguous().t()
+        one = torch.ones((), device="cuda")
+        out["rates_tflops"]["fp8_e4m3"] = timeit(
+            lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16), 2.0 * n ** 3)
+    except Exception as e:  # the scaled product may be missing from a build
+        out["rates_tflops"]["fp8_e4m3"] = None
+        out["fp8_error"] = str(e)[:200]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1016,6 +1068,8 @@ def main():
         run_sign(args)
     elif args.form == "hardneg":
         run_hardneg(args)
+    elif args.form == "peaks":
+        run_peaks(args)
     else:
         run_ours(args)
 

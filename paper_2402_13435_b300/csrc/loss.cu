@@ -16,9 +16,9 @@
 //         transposed copy as the K-major B operand.
 //   kDj:  R = jobs, C = queries; the same with dZ^T, acc[128 x d] += dZ^T Q.
 //   kKeys: R = queries, C = jobs; the raw scores <q_i, j_j> of every allowed
-//         negative (allowed column, not the positive) as selection keys
-//         (ordered score, ~column), 0 for the others, plus per-query counts --
-//         the in-batch hard-negative mining of Sec. 5.1 ranks them.
+//         negative (allowed column, not the positive) appended to the query's
+//         key list as selection keys (ordered score, ~column) -- the in-batch
+//         hard-negative mining of Sec. 5.1 ranks them.
 // dZ enters the second product as two BF16 terms (hi + lo, near-FP32 accuracy).
 // Warps 0-3: epilogue (TMEM lane quarters); warp 4: TMA; warp 5: MMA issue.
 // Every wait is bounded; a timeout sets the status word.
@@ -39,6 +39,16 @@ constexpr int kLossFwdThreads = 192;  // the forward: one epilogue set
 constexpr int kCBufs = 3;          // streamed-tile buffers: a tile loads while the two before it are in use
 constexpr uint32_t kLossTmemCols = 256;  // 2 score tiles of 64 columns + accumulator (<= 128)
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// 2^x on the special-function unit (ex2.approx: relative error ~2^-22; 2^-inf = 0).
+// The epilogues work in log2 units -- z2 = s * inv_tau * log2(e) by one
+// multiply(-add) -- so each exponential is this one instruction.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 enum LossMode : int { kFwd = 0, kDq = 1, kDj = 2, kKeys = 3 };
 
@@ -238,11 +248,10 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     float lse_row = 0.f;
     if (MODE != kDj && rvalid) {
       pos_row = a.pos[grow];
-      if (MODE == kDq) lse_row = a.lse[grow];
+      if (MODE == kDq) lse_row = a.lse[grow] * kLog2e;  // log2 units
     }
     float m = -INFINITY, ssum = 0.f, zpos = 0.f;
     bool have_pos = false;
-    unsigned long long negc = 0;  // kKeys: allowed negatives of the row
     // Mask words (and for kDj the query tile's positives and lse) are fetched
     // one tile of the set ahead.  kFwd/kDq: this row's two words, in registers.
     // kDj: the set's 128 threads stage the query tile in shared memory (double
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       sm1 = v[1];
       const int q = cc0 + r;
       spos = (r < kCRows && q < a.B) ? __ldg(a.pos + q) : -1;
-      slse = (r < kCRows && q < a.B) ? __ldg(a.lse + q) : 0.f;
+      slse = (r < kCRows && q < a.B) ? __ldg(a.lse + q) * kLog2e : 0.f;  // log2 units
     };
     auto store_stage = [&](int buf) {
       DjStage &st = stg[buf];
@@ -356,21 +365,6 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         al[1] = w1;
       }
       if (MODE == kFwd) {
-        float tmax = -INFINITY;
-#pragma unroll
-        for (int c = 0; c < 64; ++c)
-          tmax = fmaxf(tmax, ((al[c >> 5] >> (c & 31)) & 1u) ? __uint_as_float(sv[c]) * a.inv_tau : -INFINITY);
-        if (tmax > -INFINITY) {
-          const float mn = fmaxf(m, tmax);
-          float add = 0.f;
-#pragma unroll
-          for (int c = 0; c < 64; ++c) {
-            const float e = __expf(__uint_as_float(sv[c]) * a.inv_tau - mn);
-            add += ((al[c >> 5] >> (c & 31)) & 1u) ? e : 0.f;
-          }
-          ssum = ssum * __expf(m - mn) + add;
-          m = mn;
-        }
         if (pos_row >= c0 && pos_row < c0 + 64) {
           const int pc = pos_row - c0;
 #pragma unroll
@@ -378,26 +372,39 @@ __global__ void __launch_bounds__(kLossThreads, 1)
             if (c == pc) zpos = __uint_as_float(sv[c]) * a.inv_tau;
           have_pos = true;
         }
+        // the running maximum m is in log2 units; failing columns become -inf,
+        // whose exponential is 0
+        const float c2 = a.inv_tau * kLog2e;
+        float tmax = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          const float z2 = ((al[c >> 5] >> (c & 31)) & 1u) ? __uint_as_float(sv[c]) * c2 : -INFINITY;
+          sv[c] = __float_as_uint(z2);
+          tmax = fmaxf(tmax, z2);
+        }
+        if (tmax > -INFINITY) {
+          const float mn = fmaxf(m, tmax);
+          float add = 0.f;
+#pragma unroll
+          for (int c = 0; c < 64; ++c) add += ex2_approx(__uint_as_float(sv[c]) - mn);
+          ssum = ssum * ex2_approx(m - mn) + add;
+          m = mn;
+        }
       } else if (MODE == kKeys) {
         if (rvalid) {
-          uint32_t nb[2] = {al[0], al[1]};  // allowed columns without the positive
+          // allowed columns without the positive (al has no column past M),
+          // appended to the row's key list in place of the tile's range
+          uint32_t nb[2] = {al[0], al[1]};
           const int pc = pos_row - c0;
           if (pc >= 0 && pc < 32) nb[0] &= ~(1u << pc);
           if (pc >= 32 && pc < 64) nb[1] &= ~(1u << (pc - 32));
-          negc += (unsigned long long)(__popc(nb[0]) + __popc(nb[1]));
-          uint64_t *krow = a.keys + (size_t)grow * (size_t)a.keys_ld + c0;
-          const int lim = a.M - c0 < 64 ? a.M - c0 : 64;
+          const uint32_t cntk = (uint32_t)(__popc(nb[0]) + __popc(nb[1]));
+          if (cntk) {
+            uint32_t o = atomicAdd(&a.key_cnt[grow], cntk);
+            uint64_t *krow = a.keys + (size_t)grow * (size_t)a.keys_ld;
 #pragma unroll
-          for (int c = 0; c < 64; c += 2) {
-            const uint64_t k0 =
-                ((nb[c >> 5] >> (c & 31)) & 1u) ? make_key(__uint_as_float(sv[c]), (uint32_t)(c0 + c)) : 0ull;
-            const uint64_t k1 = ((nb[(c + 1) >> 5] >> ((c + 1) & 31)) & 1u)
-                                    ? make_key(__uint_as_float(sv[c + 1]), (uint32_t)(c0 + c + 1))
-                                    : 0ull;
-            if (c + 1 < lim)
-              *reinterpret_cast<ulonglong2 *>(krow + c) = make_ulonglong2(k0, k1);
-            else if (c < lim)
-              krow[c] = k0;
+            for (int c = 0; c < 64; ++c)
+              if ((nb[c >> 5] >> (c & 31)) & 1u) krow[o++] = make_key(__uint_as_float(sv[c]), (uint32_t)(c0 + c));
           }
         }
       } else {
@@ -409,6 +416,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         unsigned char *dh = sdz + (size_t)(2 * b) * kRRows * 128 + (size_t)r * 128;
         unsigned char *dl = sdz + (size_t)(2 * b + 1) * kRRows * 128 + (size_t)r * 128;
         const float g = (a.dloss != nullptr ? __ldg(a.dloss) : 1.f) * a.inv_b;
+        const float c2 = a.inv_tau * kLog2e;
         const int pc = pos_row - c0;  // kDq: the positive's column in this tile
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
@@ -419,8 +427,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int c = ch * 8 + u * 2 + h;
-              const float z = __uint_as_float(sv[c]) * a.inv_tau;
-              float lse, ispos;
+              float lse, ispos;  // lse in log2 units
               if (MODE == kDq) {
                 lse = lse_row;
                 ispos = c == pc ? 1.f : 0.f;
@@ -428,7 +435,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
                 lse = stg[sb].lse[c];
                 ispos = ((pm[c >> 5] >> (c & 31)) & 1u) ? 1.f : 0.f;
               }
-              const float dz = (__expf(z - lse) - ispos) * g;
+              const float dz = (ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -lse)) - ispos) * g;
               dz2[h] = ((al[c >> 5] >> (c & 31)) & 1u) ? dz : 0.f;
             }
             const __nv_bfloat162 hv = __float22bfloat162_rn(make_float2(dz2[0], dz2[1]));
@@ -453,12 +460,11 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     }
     if (MODE == kFwd) {  // one set: the row's log-sum-exp partial of this split
       if (rvalid) {
-        a.part_m[(size_t)blockIdx.y * a.rows_p + grow] = m;
+        a.part_m[(size_t)blockIdx.y * a.rows_p + grow] = m * kLn2;  // natural units for the combine
         a.part_s[(size_t)blockIdx.y * a.rows_p + grow] = ssum;
         if (have_pos) a.zpos[grow] = zpos;
       }
     } else if (MODE == kKeys) {
-      if (rvalid && negc) atomicAdd(&a.neg_cnt[grow], negc);
     } else if (eset == 0) {  // set 0 writes the accumulated rows
       if (!wwait(acc_full, 0u, lane)) ok = false;
       tc_fence_after();
@@ -555,12 +561,12 @@ __global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_str
   dQ[i] = s;
 }
 
-// Per query: the selection's K and the key row's length.
-__global__ void k_hn_setup(int B, int n_neg, int M, int32_t *kq, uint32_t *cnt) {
+// Per query: the selection's K, and its pass count = the keys listed.
+__global__ void k_hn_setup(int B, int n_neg, const uint32_t *key_cnt, int32_t *kq, unsigned long long *npass) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= B) return;
   kq[q] = n_neg;
-  cnt[q] = (uint32_t)M;
+  npass[q] = key_cnt[q];
 }
 
 // The mined negatives as loss mask bits (bit j of row q: job j is one of q's hard
@@ -576,9 +582,10 @@ __global__ void k_hn_mask(const int32_t *ids, const int32_t *count, int B, int n
 
 }  // namespace
 
-cudaError_t launch_hn_setup(int B, int n_neg, int M, int32_t *kq, uint32_t *cnt, cudaStream_t s) {
+cudaError_t launch_hn_setup(int B, int n_neg, const uint32_t *key_cnt, int32_t *kq, unsigned long long *npass,
+                            cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  k_hn_setup<<<(B + 255) / 256, 256, 0, s>>>(B, n_neg, M, kq, cnt);
+  k_hn_setup<<<(B + 255) / 256, 256, 0, s>>>(B, n_neg, key_cnt, kq, npass);
   return cudaGetLastError();
 }
 

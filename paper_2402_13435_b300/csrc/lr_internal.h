@@ -291,9 +291,10 @@ struct LossArgs {
   uint32_t *status;        // device status word (timeouts)
   uint64_t *keys;          // hard negatives: [rows_p][keys_ld] selection keys of the allowed negatives
   int64_t keys_ld;
-  unsigned long long *neg_cnt;  // [B] allowed negatives per query
+  uint32_t *key_cnt;       // [B] keys listed per query (zero before the pass)
 };
-cudaError_t launch_hn_setup(int B, int n_neg, int M, int32_t *kq, uint32_t *cnt, cudaStream_t s);
+cudaError_t launch_hn_setup(int B, int n_neg, const uint32_t *key_cnt, int32_t *kq, unsigned long long *npass,
+                            cudaStream_t s);
 cudaError_t launch_hn_mask(const int32_t *ids, const int32_t *count, int B, int n_neg, int Mw, uint32_t *mask,
                            cudaStream_t s);
 cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,

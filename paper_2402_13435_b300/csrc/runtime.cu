@@ -2010,9 +2010,9 @@ lr_status lr_hard_negatives(const void *Q, const void *J, int32_t B, int32_t M, 
   LossArgs a = loss_args(B, M, 1.0f, pos, mask_bits, w, P);
   a.keys = (uint64_t *)(w + H.keys);
   a.keys_ld = P.Mp;
-  a.neg_cnt = (unsigned long long *)(w + H.negc);
+  a.key_cnt = (uint32_t *)(w + H.cnt);
   LR_CK(launch_loss_pass(3, a, P.Bp / 128, P.splits, &T.qr, &T.jc, nullptr, s));
-  LR_CK(launch_hn_setup(B, n_neg, M, (int32_t *)(w + H.kq), (uint32_t *)(w + H.cnt), s));
+  LR_CK(launch_hn_setup(B, n_neg, a.key_cnt, (int32_t *)(w + H.kq), (unsigned long long *)(w + H.negc), s));
   SelectArgs fa{};
   fa.mode = 1;
   fa.buf = a.keys;
@@ -2020,7 +2020,7 @@ lr_status lr_hard_negatives(const void *Q, const void *J, int32_t B, int32_t M, 
   fa.cnt = (uint32_t *)(w + H.cnt);
   fa.overflow = (uint32_t *)(w + H.ovf);
   fa.k = (const int32_t *)(w + H.kq);
-  fa.pass_cnt = a.neg_cnt;
+  fa.pass_cnt = (const unsigned long long *)(w + H.negc);
   fa.k_stride = n_neg;
   fa.out_ids = out_ids;
   fa.out_scores = out_scores;
