@@ -851,25 +851,44 @@ bool estimate_pass_rates(const lr_index *ix, const lr_filters *f, int B, std::ve
 }
 
 // Scan plan for LR_PLAN_AUTO from the estimated pass rates s_q: the union of a
-// launch's queries is 1 - prod_q (1 - s_q).  The tensor-core scan reads every
-// 128-row tile holding a passing row of its (up to 64) queries, the GEMV scan
-// every passing row of its (up to 8), so the expected bytes are  sum over
-// 64-query launches of 1 - (1 - u)^128  and  sum over 8-query launches of u;
-// each is divided by the plan's measured fraction of the HBM roofline (0.82
-// and 0.53 at 10M x 128) and the cheaper plan runs.  Without estimates the
-// batch size decides (>= 16 queries: tensor cores).
-int choose_plan(int B, bool tc_ok, bool have_est, const std::vector<double> &s) {
+// launch's queries is u = 1 - prod_q (1 - s_q).  Estimated times, calibrated
+// on the 10M x 128 FP32 selectivity sweep and scaled by the rows:
+//   SIMT scan, per launch of up to 8 queries: a floor for the predicate over
+//     every 256-row group (0.115 ms per 10M rows) plus the union's rows
+//     gathered at an effective 2.0 TB/s when they are scattered (u <= 10 %),
+//     rising to 5.8 TB/s as they become contiguous (u = 50 %);
+//   tensor-core scan: the tile filter (60 us per 10M rows) plus, per launch of
+//     up to 64 queries, the listed tiles (a tile is listed when one of its 128
+//     rows passes: 1 - (1 - u)^128 of them) streamed at 5.2 TB/s.
+// Without estimates the batch size decides (>= 16 queries: tensor cores).
+double gemv_time_s(int64_t n, double rb, int B, const std::vector<double> &s) {
+  double t = 0.0;
+  for (int b0 = 0; b0 < B; b0 += kGemvMaxQ) {
+    double none = 1.0;
+    for (int b = b0; b < std::min(B, b0 + kGemvMaxQ); ++b) none *= 1.0 - s[b];
+    const double u = 1.0 - none;
+    const double bw = u <= 0.1 ? 2.0e12 : u >= 0.5 ? 5.8e12 : 2.0e12 + (u - 0.1) / 0.4 * 3.8e12;
+    t += 0.115e-3 * (double)n / 1e7 + u * (double)n * rb / bw;
+  }
+  return t;
+}
+
+double tc_time_s(int64_t n, double rb, int B, const std::vector<double> &s) {
+  double t = 60e-6 * (double)n / 1e7;
+  for (int b0 = 0; b0 < B; b0 += kTcMaxQ) {
+    double none = 1.0;
+    for (int b = b0; b < std::min(B, b0 + kTcMaxQ); ++b) none *= 1.0 - s[b];
+    const double u = 1.0 - none;
+    t += (1.0 - std::pow(1.0 - u, 128.0)) * (double)n * rb / 5.2e12 + 10e-6;
+  }
+  return t;
+}
+
+int choose_plan(const lr_index *ix, int B, bool tc_ok, bool have_est, const std::vector<double> &s) {
   if (!tc_ok) return LR_PLAN_GEMV;
   if (!have_est) return B >= kTcMinBatch ? LR_PLAN_TC : LR_PLAN_GEMV;
-  auto union_of = [&](int b0, int b1) {
-    double none = 1.0;
-    for (int b = b0; b < b1; ++b) none *= 1.0 - s[b];
-    return 1.0 - none;
-  };
-  double tc = 0.0, gemv = 0.0;
-  for (int b0 = 0; b0 < B; b0 += kTcMaxQ) tc += 1.0 - std::pow(1.0 - union_of(b0, std::min(B, b0 + kTcMaxQ)), 128.0);
-  for (int b0 = 0; b0 < B; b0 += kGemvMaxQ) gemv += union_of(b0, std::min(B, b0 + kGemvMaxQ));
-  return tc / 0.82 < gemv / 0.53 ? LR_PLAN_TC : LR_PLAN_GEMV;
+  const double rb = 4.0 * ix->d_pad * (ix->elem == kElemF32 ? 1.0 : ix->elem == kElemBF16 ? 0.5 : 0.25);
+  return tc_time_s(ix->n, rb, B, s) < gemv_time_s(ix->n, rb, B, s) ? LR_PLAN_TC : LR_PLAN_GEMV;
 }
 
 // TBR-first choice per query: the clause whose distinct terms have the fewest
@@ -923,26 +942,18 @@ TbrPlan plan_tbr(const lr_index *ix, const lr_filters *f, int B, int64_t cap) {
   return P;
 }
 
-// Estimated cost of the TBR-first plan against the scan plans, in bytes of
-// HBM-equivalent traffic: the postings and their bit tests (term words mostly
-// L2 hits: ~16 B per posting), the passing rows gathered at about half the
-// streaming rate; the scans read the rows they must (as choose_plan) plus the
-// predicate's pass over every 256-row group, which measured as ~64 B per row
-// for the SIMT scan and ~32 B per row for the tile filter at 10M rows.
+// Estimated time of the TBR-first plan against the scans' (choose_plan): the
+// postings and their bit tests (term words mostly L2 hits: ~16 B of traffic
+// per posting at 3.2 TB/s), the passing rows gathered in FP32 at 2 TB/s, and a
+// fixed 30 us (launches, selection).  TBR first is taken when it is estimated
+// at less than half the cheaper scan.
 bool tbr_cheaper(const lr_index *ix, int B, const TbrPlan &T, const std::vector<double> &est, bool tc_ok) {
   const double rb = 4.0 * ix->d_pad, n = (double)ix->n;
-  double tbr = 0.0;
-  for (int b = 0; b < B; ++b) tbr += 16.0 * (double)T.postings[b] + 2.0 * est[b] * n * rb;
-  auto union_of = [&](int b0, int b1) {
-    double none = 1.0;
-    for (int b = b0; b < b1; ++b) none *= 1.0 - est[b];
-    return 1.0 - none;
-  };
-  double gemv = 0.0, tc = 0.0;
-  for (int b0 = 0; b0 < B; b0 += kGemvMaxQ) gemv += union_of(b0, std::min(B, b0 + kGemvMaxQ)) * n * rb / 0.53 + 64.0 * n;
-  for (int b0 = 0; b0 < B; b0 += kTcMaxQ)
-    tc += (1.0 - std::pow(1.0 - union_of(b0, std::min(B, b0 + kTcMaxQ)), 128.0)) * n * rb / 0.82 + 32.0 * n;
-  const double scan = tc_ok ? std::min(gemv, tc) : gemv;
+  double tbr = 30e-6;
+  for (int b = 0; b < B; ++b) tbr += 16.0 * (double)T.postings[b] / 3.2e12 + est[b] * n * 4.0 * ix->d_pad / 2.0e12;
+  const double rbs = rb * (ix->elem == kElemF32 ? 1.0 : ix->elem == kElemBF16 ? 0.5 : 0.25);
+  const double gemv = gemv_time_s(ix->n, rbs, B, est);
+  const double scan = tc_ok ? std::min(gemv, tc_time_s(ix->n, rbs, B, est)) : gemv;
   return tbr < 0.5 * scan;
 }
 
@@ -1408,7 +1419,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     if (plan == LR_PLAN_TBR || (T.ok && tbr_cheaper(ix, B, T, est, tc_ok)))
       return run_tbr_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, stats, s, T, tcap);
   }
-  if (plan == LR_PLAN_AUTO) plan = choose_plan(B, tc_ok, have_est, est);
+  if (plan == LR_PLAN_AUTO) plan = choose_plan(ix, B, tc_ok, have_est, est);
   if (plan == LR_PLAN_TC && !tc_ok)
     return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable for this index (no TMA descriptor; "
                                     "low-precision rows need dim > 32)");
