@@ -27,18 +27,18 @@
 //              when N <= 32 (two above; always four for BF16 / FP8 rows, whose
 //              accumulators are N columns wide), so the MMAs run ahead of the
 //              epilogue.
-//              BF16 rows skip the converters: the MMA reads the landed stage
-//              from shared memory (kind::f16, 16-value K steps, x against the
-//              queries rounded to BF16, one accumulator column per query: the
-//              low-precision scan only picks candidates for the FP32 rescore)
-//              and its commit frees the stage.
-//   warps 2-5, 10-13  converters (FP32 and FP8 rows), two sets of one warp per
+//              BF16 and e4m3 rows skip the converters: the MMA reads the
+//              landed stage from shared memory (BF16: kind::f16, 16-value K
+//              steps, against the queries rounded to BF16; e4m3: kind::f8f6f4,
+//              32-value K steps, against the queries rounded to e4m3 under one
+//              power-of-two scale per launch; one accumulator column per
+//              query: the low-precision scan only picks candidates for the
+//              FP32 rescore) and its commit frees the stage.
+//   warps 2-5, 10-13  converters (FP32 rows), two sets of one warp per
 //              tensor-memory lane quarter, taking alternate chunks: each thread
 //              reads its row of a landed chunk, releases the raw stage at once,
-//              and writes x_hi and x_lo (FP8: the values as BF16 pairs, exact,
-//              for kind::f16 MMAs against the BF16 queries) into tensor
-//              memory (tcgen05.st).  Raw stages therefore never wait on the
-//              tensor core.
+//              and writes x_hi and x_lo into tensor memory (tcgen05.st).  Raw
+//              stages therefore never wait on the tensor core.
 //   warps 6-9 (and 14-17)  epilogue: read the accumulator (warp w owns lanes
 //              32*(w%4) ..), with the row masks of the tile read one tile
 //              ahead, test every passing (row, query) against the query's
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&raw_full[i], 1);
-      mbar_init(&raw_empty[i], E == kElemBF16 ? 1 : 4);  // BF16: the MMAs' commit; else the converter warps
+      mbar_init(&raw_empty[i], E == kElemF32 ? 4 : 1);  // FP32: the converter warps; else the MMAs' commit
     }
     for (int i = 0; i < kABufs; ++i) {
       mbar_init(&a_full[i], 4);
@@ -196,7 +196,44 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   // hi/lo pair for FP32 rows, the queries rounded to BF16 for BF16 and FP8
   // rows; each thread issues its loads of a round together, then stores
   constexpr int kQu = 8;
-  if constexpr (E != kElemF32) {
+  __shared__ float s_qinv;  // FP8 rows: 1 / the launch's power-of-two query scale
+  if constexpr (E == kElemFP8) {
+    // e4m3 queries for kind::f8f6f4 MMAs against the e4m3 rows: one
+    // power-of-two scale for the whole launch maps the largest |q| into the
+    // e4m3 range (the scale is exact; the epilogue divides it out with the row
+    // scale).  Per 64-value chunk c: rows 0..N-1 of 64 bytes, 64-byte swizzle
+    // (16-byte unit j of row r at unit j ^ ((r / 2) % 4)).
+    __shared__ float s_qmax[32];
+    float mx = 0.f;
+    for (int i = threadIdx.x; i < a.nq * a.d_pad; i += kThreads)
+      mx = fmaxf(mx, fabsf(a.Q[(size_t)a.q_base * a.d_pad + i]));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    if (lane == 0) s_qmax[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.f;
+      for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, s_qmax[w]);
+      // 2^e with 2^e * m <= 256 (below the e4m3 maximum 448); m = 0: scale 1
+      int e = 0;
+      if (m > 0.f) {
+        e = (int)floorf(log2f(256.f / m));
+        while (ldexpf(m, e) > 256.f) --e;
+        e = e > 100 ? 100 : (e < -100 ? -100 : e);
+      }
+      s_qinv = ldexpf(1.f, -e);
+      s_qmax[0] = ldexpf(1.f, e);
+    }
+    __syncthreads();
+    const float qs = s_qmax[0];
+    unsigned char *q8 = reinterpret_cast<unsigned char *>(qop);
+    for (int i = threadIdx.x; i < C * N * 64; i += kThreads) {
+      const int c = i / (N * 64), rem = i % (N * 64), r = rem / 64, k = rem % 64;
+      const float v = r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 64 + k] * qs : 0.f;
+      q8[(size_t)c * N * 64 + (size_t)r * 64 + ((((k >> 4) ^ (r >> 1)) & 3) << 4) + (k & 15)] =
+          (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+  } else if constexpr (E == kElemBF16) {
     // per 64-value chunk c: rows 0..N-1 of a 2N-row block of 128-byte rows,
     // 16-byte unit j of row r at unit j ^ (r % 8)
     uint16_t *qb = reinterpret_cast<uint16_t *>(qop);
@@ -336,6 +373,28 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(ab * kAccW);
         for (int c = 0; c < C && ok; ++c) {
+          if constexpr (E == kElemFP8) {
+            // e4m3 rows feed the tensor cores straight from the loaded stage:
+            // D[0,N) += x8 . e4m3(q s)^T, two 32-value K steps per 64-value
+            // chunk; the commit frees the stage once the MMAs have read it
+            const int s = (int)(pr % (uint64_t)S);
+            if (!mbar_wait(&raw_full[s], (uint32_t)((pr / S) & 1u))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            constexpr uint32_t idesc8 = idesc_e4m3(kTileRows, N);
+            const uint32_t xa = smem_u32(raw + (size_t)s * kChunkBytes);
+            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * N * 64);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)
+              mma_e4m3(d, sw64_desc(xa + (uint32_t)ks * 32u), sw64_desc(qa + (uint32_t)ks * 32u), idesc8,
+                       (c | ks) != 0 ? 1u : 0u);
+            issued = true;
+            mma_commit(&raw_empty[s]);
+            ++pr;
+            continue;
+          }
           if constexpr (E == kElemBF16) {
             // BF16 rows feed the tensor cores straight from the loaded stage:
             // D[0,N) += x . bf16(q)^T, four 16-value K steps per chunk; the
@@ -365,28 +424,13 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           }
           tc_fence_after();
           const uint32_t ah = tmem_base + acol0 + (uint32_t)(l * 64), al = ah + 32u;
-          if constexpr (E == kElemF32) {
-            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
+          const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              // D[0,2N) += x_hi . [q_hi ; q_lo]^T, then D[0,N) += x_lo . q_hi^T
-              mma_tf32_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc2,
-                              (c | ks) != 0 ? 1u : 0u);
-              mma_tf32_tmem_a(d, al + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc1, 1u);
-            }
-          } else {
-            // e4m3 values are exact in BF16: the converters pack the chunk's 64
-            // values two per column, and four 16-value K steps of width N give
-            // D[0,N) += x . bf16(q)^T
-            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, N);  // the q_hi rows
-            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              mma_bf16_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc_b,
-                              (c | ks) != 0 ? 1u : 0u);
-            (void)al;
-            (void)idesc1;
-            (void)idesc2;
+          for (int ks = 0; ks < 4; ++ks) {
+            // D[0,2N) += x_hi . [q_hi ; q_lo]^T, then D[0,N) += x_lo . q_hi^T
+            mma_tf32_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc2,
+                            (c | ks) != 0 ? 1u : 0u);
+            mma_tf32_tmem_a(d, al + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc1, 1u);
           }
           issued = true;
           mma_commit(&a_empty[l]);
@@ -405,7 +449,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     __syncwarp();
   } else if (is_converter(warp)) {
     // ------------------------------------------------------------- converters
-    // (idle for BF16 rows, which the MMAs read from the loaded stage)
+    // (FP32 rows only: the MMAs read BF16 and e4m3 rows from the loaded stage)
     // two sets of four warps take alternate chunks (set = chunk index & 1), so
     // two chunks per lane quarter are in flight; S and kABufs are even, so a
     // raw stage or an x_hi/x_lo buffer always belongs to the same set and its
@@ -414,7 +458,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     const uint64_t cset = warp >= kConvWarp1 ? 1u : 0u;
     const int r = quarter * 32 + lane;  // this thread's row of every tile
     uint64_t pr = 0;
-    for (int64_t k = 0; E != kElemBF16 && k < n_mine && ok; ++k) {
+    for (int64_t k = 0; E == kElemF32 && k < n_mine && ok; ++k) {
       for (int c = 0; c < C; ++c, ++pr) {
         if ((pr & 1u) != cset) continue;
         const int s = (int)(pr % (uint64_t)S), l = (int)(pr % (uint64_t)kABufs);
@@ -422,36 +466,17 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           ok = false;
           break;
         }
-        uint32_t hi[32], lo[32];  // FP32 rows: x_hi, x_lo; FP8 rows: hi holds the 64 values as BF16 pairs
+        uint32_t hi[32], lo[32];  // x_hi, x_lo of the row's 32 values
         const unsigned char *rowp = raw + (size_t)s * kChunkBytes + (size_t)r * tc_row_bytes(E);
-        if constexpr (E == kElemF32) {
 #pragma unroll
-          for (int cc = 0; cc < 8; ++cc) {  // 16-byte chunk cc of the row sits at slot cc ^ (r % 8)
-            const float4 v = *reinterpret_cast<const float4 *>(rowp + (((cc ^ (r & 7)) & 7) << 4));
-            const float e[4] = {v.x, v.y, v.z, v.w};
+        for (int cc = 0; cc < 8; ++cc) {  // 16-byte chunk cc of the row sits at slot cc ^ (r % 8)
+          const float4 v = *reinterpret_cast<const float4 *>(rowp + (((cc ^ (r & 7)) & 7) << 4));
+          const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t hb = __float_as_uint(e[u]) & 0xFFFFE000u;
-              hi[cc * 4 + u] = hb;
-              lo[cc * 4 + u] = __float_as_uint(e[u] - __uint_as_float(hb));
-            }
-          }
-        } else {
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {  // 64-byte swizzle: chunk cc of row r at slot cc ^ ((r / 2) % 4)
-            const uint4 v = *reinterpret_cast<const uint4 *>(rowp + (((cc ^ (r >> 1)) & 3) << 4));
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {  // values 16cc + 4u + 2h and + 1: word 8cc + 2u + h, lower value low
-                const __half2_raw hr =
-                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[u] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
-                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
-                const __nv_bfloat162 b = __floats2bfloat162_rn(f.x, f.y);  // exact: e4m3 fits BF16
-                hi[cc * 8 + 2 * u + h] = *reinterpret_cast<const uint32_t *>(&b);
-              }
-            }
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t hb = __float_as_uint(e[u]) & 0xFFFFE000u;
+            hi[cc * 4 + u] = hb;
+            lo[cc * 4 + u] = __float_as_uint(e[u] - __uint_as_float(hb));
           }
         }
         __syncwarp();
@@ -463,7 +488,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         tc_fence_after();
         const uint32_t ta = tmem_base + ((uint32_t)(quarter * 32) << 16) + acol0 + (uint32_t)(l * 64);
         tmem_st32(ta, hi);
-        if constexpr (E == kElemF32) tmem_st32(ta + 32u, lo);
+        tmem_st32(ta + 32u, lo);
         tmem_st_wait();
         tc_fence_before();
         __syncwarp();
@@ -543,7 +568,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     auto scale_of = [&](int32_t t, int64_t k) -> float {  // FP8 rows: score = scale * <q, x8>
       if constexpr (E == kElemFP8) {
         const int64_t g = tile_first_row(a, max(t, 0)) + lr;
-        return k < n_mine && t >= 0 && g < a.n ? __ldg(a.xscale + g) : 0.f;
+        return k < n_mine && t >= 0 && g < a.n ? __ldg(a.xscale + g) * s_qinv : 0.f;  // exact: 2^-e
       } else {
         return 1.f;
       }
