@@ -74,6 +74,7 @@ def parse():
     p.add_argument("--rates", default="100,300,5000,10000,20000,50000")
     p.add_argument("--slots", type=int, default=3)
     p.add_argument("--max-requests", type=int, default=2000)
+    p.add_argument("--clients", type=int, default=4, help="serve form: client threads submitting the stream")
     a = p.parse_args()
     a.band_list = tuple(float(x) for x in a.bands.split(","))
     return a
@@ -671,19 +672,33 @@ def run_serve(args):
         srv.wait(srv.submit(*reqs[0]), reqs[0][0].shape[0], reqs[0][2])  # warm up
         for rate in [float(r) for r in args.rates.split(",")]:
             srv.stats(reset=True)
-            gaps = rng.exponential(1.0 / rate, size=nreq)
-            tickets = []
+            # arrival times of one Poisson stream, submitted by several client threads (each takes every
+            # n-th request at its due time; the library call releases the interpreter lock), so a single
+            # Python thread's submit cost does not cap the offered rate
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+            tickets = [None] * nreq
+            n_cli = args.clients
             t_start = time.perf_counter()
-            due = t_start
-            for i, (Q, f, K) in enumerate(reqs):
-                due += gaps[i]
-                while True:
-                    now = time.perf_counter()
-                    if now >= due:
-                        break
-                    time.sleep(min(due - now, 0.001))
-                tickets.append(srv.submit(Q, f, K))
-            t_sub = time.perf_counter() - t_start
+            sub_end = [t_start] * n_cli
+
+            def client(c):
+                for i in range(c, nreq, n_cli):
+                    due = t_start + arrivals[i]
+                    while True:
+                        now = time.perf_counter()
+                        if now >= due:
+                            break
+                        time.sleep(min(due - now, 0.001))
+                    Q, f, K = reqs[i]
+                    tickets[i] = srv.submit(Q, f, K)
+                sub_end[c] = time.perf_counter()
+
+            threads = [threading.Thread(target=client, args=(c,)) for c in range(n_cli)]
+            for th in threads:
+                th.start()
+            for th in threads:
+                th.join()
+            t_sub = max(sub_end) - t_start
             for t, (Q, f, K) in zip(tickets, reqs):
                 srv.wait(t, Q.shape[0], K)
             t_all = time.perf_counter() - t_start
@@ -698,8 +713,8 @@ def run_serve(args):
            "data": "synthetic (seeded generator)",
            "config": {"workload": "resident N=%d x d=%d %s index (oversample %d), Poisson requests of 1-64 queries, "
                                   "K in {100,500,1000,2000}, selectivity log-uniform 0.05-50%%; %d requests per load "
-                                  "point, %d slots of 256 queries" % (args.n, args.dim, args.dtype, args.oversample,
-                                                                      nreq, slots),
+                                  "point from %d client threads, %d slots of 256 queries"
+                                  % (args.n, args.dim, args.dtype, args.oversample, nreq, args.clients, slots),
                       "n_jobs": args.n, "dim": args.dim, "slots": slots},
            "loads": loads, "setup_s": {"generate": round(gen_s, 1)}}
     print(json.dumps(out), flush=True)
