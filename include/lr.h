@@ -65,8 +65,9 @@ typedef enum lr_plan {
                         whole CNF is tested on them, only the passing rows are
                         scored (FP32).  Needs an index built from posting lists
                         (each list naming a job at most once), at least one
-                        clause per query and at most the candidate capacity
-                        (65,536 per query from 65,536 rows up) postings in the
+                        clause per query and at most the query's share of the
+                        candidate buffer (max_batch x 65,536 keys from 65,536
+                        rows up, split evenly over the batch) postings in the
                         chosen clause; LR_ERR_UNSUPPORTED otherwise.           */
 } lr_plan;
 

@@ -859,10 +859,12 @@ bool estimate_pass_rates(const lr_index *ix, const lr_filters *f, int B, std::ve
 //     rising to 5.8 TB/s as they become contiguous (u = 50 %);
 //   tensor-core scan: the tile filter (60 us per 10M rows) plus, per launch of
 //     up to 64 queries, the listed tiles (a tile is listed when one of its 128
-//     rows passes: 1 - (1 - u)^128 of them) streamed at 5.2 TB/s.
+//     rows passes: 1 - (1 - u)^128 of them) streamed at 5.2 TB/s;
+//   and each plan's fixed launches (prep, expansion, sample, selection and the
+//     exact fallback's early-exit launches): ~30 us for the scans.
 // Without estimates the batch size decides (>= 16 queries: tensor cores).
 double gemv_time_s(int64_t n, double rb, int B, const std::vector<double> &s) {
-  double t = 0.0;
+  double t = 30e-6;
   for (int b0 = 0; b0 < B; b0 += kGemvMaxQ) {
     double none = 1.0;
     for (int b = b0; b < std::min(B, b0 + kGemvMaxQ); ++b) none *= 1.0 - s[b];
@@ -874,7 +876,7 @@ double gemv_time_s(int64_t n, double rb, int B, const std::vector<double> &s) {
 }
 
 double tc_time_s(int64_t n, double rb, int B, const std::vector<double> &s) {
-  double t = 60e-6 * (double)n / 1e7;
+  double t = 30e-6 + 60e-6 * (double)n / 1e7;
   for (int b0 = 0; b0 < B; b0 += kTcMaxQ) {
     double none = 1.0;
     for (int b = b0; b < std::min(B, b0 + kTcMaxQ); ++b) none *= 1.0 - s[b];
@@ -945,11 +947,11 @@ TbrPlan plan_tbr(const lr_index *ix, const lr_filters *f, int B, int64_t cap) {
 // Estimated time of the TBR-first plan against the scans' (choose_plan): the
 // postings and their bit tests (term words mostly L2 hits: ~16 B of traffic
 // per posting at 3.2 TB/s), the passing rows gathered in FP32 at 2 TB/s, and a
-// fixed 30 us (launches, selection).  TBR first is taken when it is estimated
-// at less than half the cheaper scan.
+// fixed 12 us (five launches, against the scans' dozen).  TBR first is taken
+// when it is estimated at less than half the cheaper scan.
 bool tbr_cheaper(const lr_index *ix, int B, const TbrPlan &T, const std::vector<double> &est, bool tc_ok) {
   const double rb = 4.0 * ix->d_pad, n = (double)ix->n;
-  double tbr = 30e-6;
+  double tbr = 12e-6;
   for (int b = 0; b < B; ++b) tbr += 16.0 * (double)T.postings[b] / 3.2e12 + est[b] * n * 4.0 * ix->d_pad / 2.0e12;
   const double rbs = rb * (ix->elem == kElemF32 ? 1.0 : ix->elem == kElemBF16 ? 0.5 : 0.25);
   const double gemv = gemv_time_s(ix->n, rbs, B, est);
@@ -1410,7 +1412,9 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // the automatic plan considers TBR first only when no scan option is forced
   const bool scan_opts = o.sample_stride != 0 || o.cand_cap != 0 || o.force_exact_fallback != 0;
   if (plan == LR_PLAN_TBR || (plan == LR_PLAN_AUTO && have_est && !scan_opts)) {
-    int64_t tcap = ix->cand_cap;
+    // the candidate buffer holds max_batch x cand_cap keys: a batch of B
+    // queries gives each query an equal share of it for its messenger list
+    int64_t tcap = ix->cand_cap * (int64_t)ix->max_batch / B;
     if (o.cand_cap > 0) tcap = std::min<int64_t>(tcap, o.cand_cap);
     const TbrPlan T = plan_tbr(ix, f, B, tcap);
     if (plan == LR_PLAN_TBR && !T.ok)

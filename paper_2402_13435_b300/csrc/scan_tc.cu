@@ -69,9 +69,14 @@ namespace {
 constexpr int kEpiWarp0 = 6;
 constexpr int kConvWarp1 = 10;
 constexpr int kEpiWarp1 = 14;
-__host__ __device__ constexpr int tc_epi_sets(int e) { return e == kElemF32 ? 1 : 2; }
-__host__ __device__ constexpr int tc_threads(int e) { return (kEpiWarp1 + 4 * (tc_epi_sets(e) - 1)) * 32; }
+// BF16 and e4m3 rows need no converters (their MMAs read the loaded stage):
+// warps 2-5 and 10-13 become epilogue sets 2 and 3 there, so four sets of four
+// warps test alternate tiles
+__host__ __device__ constexpr int tc_epi_sets(int e) { return e == kElemF32 ? 1 : 4; }
+__host__ __device__ constexpr int tc_threads(int e) { return (e == kElemF32 ? kEpiWarp1 : kEpiWarp1 + 4) * 32; }
 __device__ __forceinline__ bool is_converter(int w) { return (w >= 2 && w < kEpiWarp0) || (w >= kConvWarp1 && w < kEpiWarp1); }
+// epilogue set of an epilogue warp: 6-9 -> 0, 14-17 -> 1, 2-5 -> 2, 10-13 -> 3
+__device__ __forceinline__ int epi_set(int w) { return w >= kEpiWarp1 ? 1 : w >= kConvWarp1 ? 3 : w >= kEpiWarp0 ? 0 : 2; }
 constexpr int kLoadWarp = 0;
 constexpr int kTileRows = 128;
 constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile of 128-byte rows
@@ -91,7 +96,9 @@ constexpr uint32_t kTmemCols = 512;           // the whole tensor memory: one CT
 // BF16 / FP8 rows, whose scan only picks candidates for the FP32 rescore,
 // score against the queries rounded to BF16 (N columns), so four buffers fit
 // up to N = 64
-__host__ __device__ constexpr int tc_acc_bufs(int e, int n) { return e != kElemF32 || n <= 32 ? 4 : 2; }
+// (BF16 / e4m3 rows: eight N-column buffers, two per epilogue set, in the
+// tensor memory the x_hi/x_lo buffers of FP32 rows would take)
+__host__ __device__ constexpr int tc_acc_bufs(int e, int n) { return e != kElemF32 ? 8 : n <= 32 ? 4 : 2; }
 __host__ __device__ constexpr int tc_acc_w(int e, int n) { return e == kElemF32 ? 2 * n : n; }
 
 // Row mask word of the tile list: bit q = launch query q passes the row.
@@ -105,8 +112,9 @@ struct TcLayout {
 
 __host__ __device__ inline size_t tc_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S, int epi_warps) {
+__host__ __device__ inline TcLayout tc_layout(int d_pad, int e, int N, int S, int epi_warps) {
   TcLayout T;
+  const int epc = tc_epc(e);
   T.S = S;
   T.C = d_pad / epc;   // raw chunks per tile
   T.C32 = d_pad / 32;  // 32-value chunks of the query operand
@@ -114,8 +122,11 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int epc, int N, int S, 
   size_t off = 0;
   T.raw = off;
   off += (size_t)S * kChunkBytes;
-  T.q = off;  // per chunk: 2N rows (N rows of q_hi, then N rows of q_lo), 128 bytes each
-  off += (size_t)T.C32 * 2 * N * 128;
+  // the query operand: FP32 rows, per 32-value chunk 2N rows (q_hi, then q_lo)
+  // of 128 bytes; BF16, per 64-value chunk a 2N-row block of 128-byte rows (N
+  // used); e4m3, per 64-value chunk N rows of 64 bytes
+  T.q = off;
+  off += e == kElemF32 ? (size_t)T.C32 * 2 * N * 128 : e == kElemBF16 ? (size_t)T.C * 2 * N * 128 : (size_t)T.C * N * 64;
   T.taus = tc_align(off, 16);
   off = T.taus + (size_t)N * 12;  // 64-bit thresholds, then their score words as floats
   T.cand = tc_align(off, 16);     // per epilogue warp: keys, then query indices (bytes)
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   unsigned char *smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned for the swizzle atoms
   constexpr int kSets = tc_epi_sets(E), kThreads = tc_threads(E);
-  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S, 4 * kSets);
+  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * kSets);
   const int C = T.C;
   const int C32 = T.C32;
   unsigned char *raw = smem + T.raw;
@@ -447,7 +458,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
       if (!ok) atomicOr(a.err, kErrTimeout);
     }
     __syncwarp();
-  } else if (is_converter(warp)) {
+  } else if (E == kElemF32 && is_converter(warp)) {
     // ------------------------------------------------------------- converters
     // (FP32 rows only: the MMAs read BF16 and e4m3 rows from the loaded stage)
     // two sets of four warps take alternate chunks (set = chunk index & 1), so
@@ -502,8 +513,8 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     // & 1); with an even number of accumulator buffers each buffer belongs to
     // one set
     const int quarter = warp & 3;
-    const int eset = warp >= kEpiWarp1 ? 1 : 0;
-    const int ew = eset * 4 + (warp - (eset ? kEpiWarp1 : kEpiWarp0));  // 0..7: the warp's candidate list
+    const int eset = epi_set(warp);
+    const int ew = eset * 4 + ((warp - 2) & 3);  // the warp's candidate list (each set's warps start at 2 mod 4)
     // Candidates are recorded in a per-warp shared-memory list by the lanes that
     // find them: a shared-memory atomic each in the main scan, where hits are
     // rare (a prefix sum over the lanes was measured slower there), and
@@ -730,13 +741,15 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
 
 template <int N, int E>
 cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cudaStream_t s) {
-  static_assert(tc_acc_bufs(E, N) * tc_acc_w(E, N) + 64 * kABufs <= (int)kTmemCols, "tensor memory budget");
+  static_assert(tc_acc_bufs(E, N) * tc_acc_w(E, N) + (E == kElemF32 ? 64 * kABufs : 0) <= (int)kTmemCols,
+                "tensor memory budget");
+  static_assert(tc_acc_bufs(E, N) % tc_epi_sets(E) == 0, "each accumulator buffer belongs to one epilogue set");
   static_assert(kABufs % 2 == 0, "each converter set owns every other x_hi/x_lo buffer");
   const size_t budget = 220u * 1024u;
   int S = 12;  // raw stages: even (each converter set owns every other stage)
   if (a.d_pad % tc_epc(E) != 0) return cudaErrorInvalidValue;
-  while (S > 2 && tc_layout(a.d_pad, tc_epc(E), N, S, 4 * tc_epi_sets(E)).total + 1024 > budget) S -= 2;
-  const TcLayout T = tc_layout(a.d_pad, tc_epc(E), N, S, 4 * tc_epi_sets(E));
+  while (S > 2 && tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E)).total + 1024 > budget) S -= 2;
+  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E));
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
   auto *fn = k_scan_tc<N, E>;
   cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)(T.total + 1024));

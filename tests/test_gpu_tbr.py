@@ -93,13 +93,31 @@ def test_tbr_plan_rejections(lr, setup):
     c, idx = setup
     Q = torch.from_numpy(datagen.query_embeddings(91, 2, c.d)).cuda()
     common = int(np.argmax(c.df))
-    for f in (Filters.from_lists([[], [[5]]]),                         # a query without a clause
-              Filters.from_lists([[[common]], [[common]]])):           # more postings than the capacity
-        with pytest.raises(lr.LRError) as e:
-            lr.lr_search(idx, Q, f, 10, plan="tbr")
-        assert e.value.status == lr.LR_ERR_UNSUPPORTED
+    with pytest.raises(lr.LRError) as e:                                # a query without a clause
+        lr.lr_search(idx, Q, Filters.from_lists([[], [[5]]]), 10, plan="tbr")
+    assert e.value.status == lr.LR_ERR_UNSUPPORTED
+    # 32 queries share the candidate buffer (32 x 65,536 keys): a clause with more postings than a
+    # query's share cannot run TBR first
+    Q32 = torch.from_numpy(datagen.query_embeddings(92, 32, c.d)).cuda()
+    with pytest.raises(lr.LRError) as e:
+        lr.lr_search(idx, Q32, Filters.from_lists([[[common]]] * 32), 10, plan="tbr")
+    assert e.value.status == lr.LR_ERR_UNSUPPORTED
     bits = lr.lr_index_create(c.X[:5000], c.V, bitsets=c.bitsets()[:5000], max_batch=4, max_k=16)
     with pytest.raises(lr.LRError) as e:                                # no posting lists
         lr.lr_search(bits, Q, Filters.from_lists([[[5]], [[6]]]), 10, plan="tbr")
     assert e.value.status == lr.LR_ERR_UNSUPPORTED
     lr.lr_index_destroy(bits)
+
+
+def test_tbr_plan_single_query_with_a_broad_clause(lr, setup):
+    """A single query's share of the candidate buffer is the whole buffer: a clause with ~100k postings
+    (half the index) still runs TBR first, with exact pass counts and the oracle's rows."""
+    c, idx = setup
+    order = np.argsort(-c.df)
+    t = int(order[np.searchsorted(-c.df[order], -c.n // 2)])   # a term held by about half the jobs
+    f = Filters.from_lists([[[t]]])
+    Q = datagen.query_embeddings(93, 1, c.d)
+    ids, sc, cnt, st = lr.lr_search(idx, torch.from_numpy(Q).cuda(), f, 300, plan="tbr", stats=True)
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, 300)
+    assert np.array_equal(st["pass_count"], ref.pass_count)
+    check_topk(ids.cpu().numpy(), sc.cpu().numpy(), cnt.cpu().numpy(), ref, c.X, Q, c.job_off, c.job_terms, f)
