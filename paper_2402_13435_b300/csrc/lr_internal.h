@@ -119,6 +119,12 @@ struct ScanArgs {
   uint32_t *tile_cnt;            // tiles listed
   int64_t tile_cap;
   int32_t keep_list;             // 1: the scan leaves the list for later launches (else its last CTA empties it)
+  // two-block scans (128 queries per tensor-core launch): the tile filter of
+  // each 64-query block writes the masks of EVERY visited tile (zero when no
+  // query passes) and no list; the scan visits every tile in order and reads
+  // block 1's masks from tile_msg2
+  int32_t dense_tiles;
+  void *tile_msg2;
 };
 
 struct SelectArgs {
@@ -177,6 +183,9 @@ cudaError_t launch_scan_gemv(const ScanArgs &a, int nq_tmpl, int vec, int grid, 
 // its list; launch them back to back on one stream.
 cudaError_t launch_tile_filter(const ScanArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
+// The same scan for two 64-query blocks per converted tile (FP32 rows, d <= 128,
+// dense tile masks in tile_msg / tile_msg2): the index is read once per 128 queries.
+cudaError_t launch_scan_tc2(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
 
 // Per-query threshold of the sample (the r-th largest sampled key, 0 when the

@@ -135,6 +135,7 @@ struct lr_index {
   uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
   int32_t *tile_row = nullptr;  // tile list of the tensor-core plan: main pass
   uint64_t *tile_msg = nullptr;
+  uint64_t *tile_msg2 = nullptr;  // FP32 rows, d <= 128, batches above 64: the second query block's masks
   uint32_t *tile_cnt = nullptr;
   int64_t tile_cap = 0;
   uint64_t *thr_scratch = nullptr;  // split threshold selection: [B][8192] keys, [B][32] counts, [B] done
@@ -390,6 +391,10 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->tile_cap = 2 * ix->n_groups;  // every 128-row tile of the index
   const size_t o_trow = cv.take<int32_t>((size_t)ix->tile_cap);
   const size_t o_tmsg = cv.take<uint64_t>((size_t)ix->tile_cap * 128);
+  // two-block scans read the index once per 128 queries (FP32 rows only: the
+  // low-precision scans already reach their bound with 64)
+  const bool two_block = ix->elem == kElemF32 && ix->d_pad <= 128 && B > kTcMaxQ;
+  const size_t o_tmsg2 = cv.take<uint64_t>(two_block ? (size_t)ix->tile_cap * 128 : 0);
   ix->tile_cap_s = 2 * (ix->samp_cap / kGroupRows + 2);  // the sampled groups' tiles (sample rows <= samp_cap)
   const size_t o_trow_s = cv.take<int32_t>((size_t)ix->tile_cap_s);
   const size_t o_thr_scr = cv.take<uint64_t>((size_t)B * kThrScratchKeys);
@@ -441,6 +446,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->cand_buf = (uint64_t *)(w + o_cand);
   ix->tile_row = (int32_t *)(w + o_trow);
   ix->tile_msg = (uint64_t *)(w + o_tmsg);
+  ix->tile_msg2 = two_block ? (uint64_t *)(w + o_tmsg2) : nullptr;
   ix->tile_cnt = (uint32_t *)(w + o_tcnt);
   ix->tile_row_s = (int32_t *)(w + o_trow_s);
   ix->tile_msg_s = (uint64_t *)(w + o_tmsg_s);
@@ -1594,7 +1600,27 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // 2. main scan: candidates at or above the threshold, pass counts
   if (early_filter) LR_CK(cudaStreamWaitEvent(s, ix->ev_join, 0));
   if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
-  for (const SubBatch &sb : C.subs) {
+  // FP32 rows: two consecutive sub-batches (a full one of 64 queries and the
+  // next) share one scan that converts each tile once and scores it against
+  // both; their tile filters write every tile's masks (no list)
+  const bool pairs = plan == LR_PLAN_TC && !lowp && ix->tile_msg2 != nullptr && !early_filter;
+  for (size_t i = 0; i < C.subs.size(); ++i) {
+    const SubBatch &sb = C.subs[i];
+    if (pairs && i + 1 < C.subs.size() && sb.nq == kTcMaxQ && C.subs[i + 1].q_base == sb.q_base + kTcMaxQ) {
+      const SubBatch &sb2 = C.subs[i + 1];
+      ScanArgs a0 = main_args(sb), a1 = main_args(sb2);
+      a0.dense_tiles = a1.dense_tiles = 1;
+      a1.tile_msg = ix->tile_msg2;
+      LR_LAUNCH(launch_tile_filter(a0, ix->num_sms, s));
+      LR_LAUNCH(launch_tile_filter(a1, ix->num_sms, s));
+      ScanArgs a2 = a0;
+      a2.nq = sb.nq + sb2.nq;
+      a2.tile_msg2 = ix->tile_msg2;
+      LR_LAUNCH(launch_scan_tc2(a2, &ix->tmap_x, grid_for(2 * ix->n_groups), s));
+      ++n_scan;
+      ++i;
+      continue;
+    }
     LR_LAUNCH(launch_scan(main_args(sb), ix->n_groups, !early_filter, reuse_list));
     ++n_scan;
   }

@@ -72,8 +72,8 @@ constexpr int kEpiWarp1 = 14;
 // BF16 and e4m3 rows need no converters (their MMAs read the loaded stage):
 // warps 2-5 and 10-13 become epilogue sets 2 and 3 there, so four sets of four
 // warps test alternate tiles
-__host__ __device__ constexpr int tc_epi_sets(int e) { return e == kElemF32 ? 1 : 4; }
-__host__ __device__ constexpr int tc_threads(int e) { return (e == kElemF32 ? kEpiWarp1 : kEpiWarp1 + 4) * 32; }
+__host__ __device__ constexpr int tc_epi_sets(int e) { return e == kElemF32 ? 2 : 4; }
+__host__ __device__ constexpr int tc_threads(int e) { return (e == kElemF32 ? kEpiWarp1 + 4 : kEpiWarp1 + 4) * 32; }
 __device__ __forceinline__ bool is_converter(int w) { return (w >= 2 && w < kEpiWarp0) || (w >= kConvWarp1 && w < kEpiWarp1); }
 // epilogue set of an epilogue warp: 6-9 -> 0, 14-17 -> 1, 2-5 -> 2, 10-13 -> 3
 __device__ __forceinline__ int epi_set(int w) { return w >= kEpiWarp1 ? 1 : w >= kConvWarp1 ? 3 : w >= kEpiWarp0 ? 0 : 2; }
@@ -86,8 +86,10 @@ constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile o
 // e4m3 in 64-value (64-byte) blocks.
 __host__ __device__ constexpr int tc_epc(int e) { return e == kElemF32 ? 32 : 64; }
 __host__ __device__ constexpr int tc_row_bytes(int e) { return e == kElemFP8 ? 64 : 128; }
-constexpr int kWarpCand = 512;                // candidates staged per epilogue warp (flushed past 256)
-constexpr int kABufs = 4;                     // x_hi/x_lo chunk buffers in tensor memory
+// candidates staged per epilogue warp (half with two query blocks, whose
+// query operands leave less shared memory)
+__host__ __device__ constexpr int tc_warp_cand(int nb) { return nb > 1 ? 256 : 512; }
+constexpr int kMaxABufs = 4;                  // x_hi/x_lo chunk buffers in tensor memory, at most
 constexpr uint32_t kTmemCols = 512;           // the whole tensor memory: one CTA per SM
 // Accumulator buffers (2N columns each): four when they fit beside the x_hi/x_lo
 // buffers, so the MMAs can run up to four tiles ahead of the epilogue.
@@ -100,6 +102,14 @@ constexpr uint32_t kTmemCols = 512;           // the whole tensor memory: one CT
 // tensor memory the x_hi/x_lo buffers of FP32 rows would take)
 __host__ __device__ constexpr int tc_acc_bufs(int e, int n) { return e != kElemF32 ? 8 : n <= 32 ? 4 : 2; }
 __host__ __device__ constexpr int tc_acc_w(int e, int n) { return e == kElemF32 ? 2 * n : n; }
+// FP32 rows: x_hi/x_lo buffers (64 columns each) in the tensor memory the
+// accumulators leave, at most four (six for narrow blocks, with two
+// accumulators instead of four, measured slower)
+__host__ __device__ constexpr int tc_abufs(int e, int n) {
+  return e != kElemF32 ? 0 : ((512 - tc_acc_bufs(e, n) * tc_acc_w(e, n)) / 64 & ~1) > kMaxABufs
+                                 ? kMaxABufs
+                                 : ((512 - tc_acc_bufs(e, n) * tc_acc_w(e, n)) / 64 & ~1);  // even: two converter sets
+}
 
 // Row mask word of the tile list: bit q = launch query q passes the row.
 template <int N>
@@ -112,7 +122,7 @@ struct TcLayout {
 
 __host__ __device__ inline size_t tc_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int d_pad, int e, int N, int S, int epi_warps) {
+__host__ __device__ inline TcLayout tc_layout(int d_pad, int e, int N, int S, int epi_warps, int NB = 1) {
   TcLayout T;
   const int epc = tc_epc(e);
   T.S = S;
@@ -126,17 +136,18 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int e, int N, int S, in
   // of 128 bytes; BF16, per 64-value chunk a 2N-row block of 128-byte rows (N
   // used); e4m3, per 64-value chunk N rows of 64 bytes
   T.q = off;
-  off += e == kElemF32 ? (size_t)T.C32 * 2 * N * 128 : e == kElemBF16 ? (size_t)T.C * 2 * N * 128 : (size_t)T.C * N * 64;
+  off += (size_t)NB * (e == kElemF32 ? (size_t)T.C32 * 2 * N * 128
+                                      : e == kElemBF16 ? (size_t)T.C * 2 * N * 128 : (size_t)T.C * N * 64);
   T.taus = tc_align(off, 16);
-  off = T.taus + (size_t)N * 12;  // 64-bit thresholds, then their score words as floats
+  off = T.taus + (size_t)NB * N * 12;  // 64-bit thresholds, then their score words as floats
   T.cand = tc_align(off, 16);     // per epilogue warp: keys, then query indices (bytes)
-  off = T.cand + (size_t)epi_warps * kWarpCand * 9;
+  off = T.cand + (size_t)epi_warps * tc_warp_cand(NB) * 9;
   T.ccnt = tc_align(off, 16);
   off = T.ccnt + (size_t)epi_warps * 4;
   T.cq = off;  // per epilogue warp: per-query counts, then reserved bases, of one flush
   off = T.cq + (size_t)epi_warps * 2 * N * 4;
   T.bars = tc_align(off, 16);
-  off = T.bars + (size_t)(2 * S + 2 * kABufs + 2 * 4 + 1) * 8;  // at most four accumulator buffers
+  off = T.bars + (size_t)(2 * S + 2 * kMaxABufs + 2 * 8 + 1) * 8;  // at most eight accumulator buffers
   T.holder = tc_align(off, 16);
   T.total = T.holder + 16;
   return T;
@@ -155,25 +166,33 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
   return __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
 }
 
-template <int N, int E>
+// NB = 2: each converted tile is scored against two 64-query blocks, each into
+// its own accumulator (FP32 rows only; 128 queries per launch).
+template <int N, int E, int NB>
 __global__ void __launch_bounds__(tc_threads(E), 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
+  static_assert(NB == 1 || (NB == 2 && E == kElemF32 && N == 64), "two query blocks: FP32 rows, 64 queries each");
+  static_assert(NB == 1 || NB == tc_epi_sets(E), "with several query blocks each epilogue set takes one");
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned for the swizzle atoms
   constexpr int kSets = tc_epi_sets(E), kThreads = tc_threads(E);
-  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * kSets);
+  constexpr int kABufs = E == kElemF32 ? tc_abufs(E, N) : 2;  // (unused for BF16 / e4m3 rows)
+  constexpr int kWarpCand = tc_warp_cand(NB), kLaneCand = kWarpCand / 32;
+  static_assert(kLaneCand >= 8, "a lane records up to eight hits between two room checks");
+  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * kSets, NB);
   const int C = T.C;
   const int C32 = T.C32;
   unsigned char *raw = smem + T.raw;
   float *qop = reinterpret_cast<float *>(smem + T.q);
   uint64_t *taus = reinterpret_cast<uint64_t *>(smem + T.taus);
-  float *thr = reinterpret_cast<float *>(taus + N);
+  float *thr = reinterpret_cast<float *>(taus + NB * N);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + T.bars);
   uint64_t *raw_full = bars, *raw_empty = bars + S;
   uint64_t *a_full = bars + 2 * S, *a_empty = a_full + kABufs;
-  constexpr int kAcc = tc_acc_bufs(E, N), kAccW = tc_acc_w(E, N);
+  // several query blocks share one accumulator of 2 NB N columns (both epilogue sets read it)
+  constexpr int kAcc = NB > 1 ? 1 : tc_acc_bufs(E, N), kAccW = NB > 1 ? 2 * NB * N : tc_acc_w(E, N);
   uint64_t *acc_full = a_empty + kABufs, *acc_empty = acc_full + kAcc;
   uint64_t *drain = acc_empty + kAcc;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + T.holder);
@@ -182,7 +201,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   const uint32_t acol0 = (uint32_t)(kAcc * kAccW);  // first tensor-memory column of the x_hi/x_lo buffers
   __shared__ bool s_last;
   __shared__ uint32_t s_nlist;
-  __shared__ uint32_t s_live[2];  // bit q: query q takes part in this launch
+  __shared__ uint32_t s_live[2 * NB];  // bit q: query q takes part in this launch
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
@@ -195,13 +214,21 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     }
     for (int i = 0; i < kAcc; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4);
+      mbar_init(&acc_empty[i], NB > 1 ? 4 * kSets : 4);  // with several blocks every set releases it
     }
     mbar_init(drain, 1);
     fence_mbar_init();
-    // tiles listed by the tile filter (never more than the list holds)
-    const uint32_t nl = *reinterpret_cast<const volatile uint32_t *>(a.tile_cnt);
-    s_nlist = (int64_t)nl < a.tile_cap ? nl : (uint32_t)a.tile_cap;
+    // tiles listed by the tile filter (never more than the list holds), or
+    // with dense tile masks every tile of the visited groups, in order
+    if (a.dense_tiles) {
+      const int64_t ng = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
+      int64_t nt = 2 * ng;
+      if (nt > 0 && tile_first_row(a, (int32_t)(nt - 1)) >= a.n) --nt;  // a last group of <= 128 rows
+      s_nlist = (uint32_t)(nt < a.tile_cap ? nt : a.tile_cap);
+    } else {
+      const uint32_t nl = *reinterpret_cast<const volatile uint32_t *>(a.tile_cnt);
+      s_nlist = (int64_t)nl < a.tile_cap ? nl : (uint32_t)a.tile_cap;
+    }
   }
   // queries of the launch in the K-major 128-byte swizzle layout: a TF32
   // hi/lo pair for FP32 rows, the queries rounded to BF16 for BF16 and FP8
@@ -267,30 +294,36 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
       }
     }
   } else
-  for (int i0 = 0; i0 < C32 * N * 32; i0 += kQu * kThreads) {
+  for (int i0 = 0; i0 < NB * C32 * N * 32; i0 += kQu * kThreads) {
+    // block bq holds queries bq N .. bq N + N - 1 in its own operand region
     float v[kQu];
 #pragma unroll
     for (int u = 0; u < kQu; ++u) {
       const int i = i0 + u * kThreads + threadIdx.x;
-      const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
-      v[u] = i < C32 * N * 32 && r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 32 + k] : 0.f;
+      const int bq = i / (C32 * N * 32), ii = i % (C32 * N * 32);
+      const int c = ii / (N * 32), rem = ii % (N * 32), r = rem / 32, k = rem % 32;
+      const int qi = bq * N + r;
+      v[u] = i < NB * C32 * N * 32 && qi < a.nq ? a.Q[(size_t)(a.q_base + qi) * a.d_pad + c * 32 + k] : 0.f;
+      (void)qi;
     }
 #pragma unroll
     for (int u = 0; u < kQu; ++u) {
       const int i = i0 + u * kThreads + threadIdx.x;
-      if (i >= C32 * N * 32) break;
-      const int c = i / (N * 32), rem = i % (N * 32), r = rem / 32, k = rem % 32;
+      if (i >= NB * C32 * N * 32) break;
+      const int bq = i / (C32 * N * 32), ii = i % (C32 * N * 32);
+      const int c = ii / (N * 32), rem = ii % (N * 32), r = rem / 32, k = rem % 32;
       const float h = __uint_as_float(__float_as_uint(v[u]) & 0xFFFFE000u);
-      const int rl = r + N;  // row of q_lo in the combined operand
-      const size_t base = (size_t)c * 2 * N * 128;
-      qop[(base + (size_t)r * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4) / 4] = h;
+      const int rh = bq * N + r;  // rows of q_hi (all blocks), then of q_lo
+      const int rl = NB * N + rh;
+      const size_t base = (size_t)c * 2 * NB * N * 128;
+      qop[(base + (size_t)rh * 128 + ((((k >> 2) ^ (rh & 7)) & 7) << 4) + (k & 3) * 4) / 4] = h;
       qop[(base + (size_t)rl * 128 + ((((k >> 2) ^ (rl & 7)) & 7) << 4) + (k & 3) * 4) / 4] = v[u] - h;
     }
   }
-  {  // thread q < N: query q's threshold; warps 0-1 record which queries take part
+  {  // thread q < NB N: query q's threshold; warps 0 .. 2 NB - 1 record which queries take part
     const int q = threadIdx.x;
     bool live = false;
-    if (q < N) {
+    if (q < NB * N) {
       const int g2 = a.q_base + q;
       live = q < a.nq && (a.active == nullptr || a.active[g2] != 0u);
       taus[q] = !live ? 0ull : (a.mode == kCollect ? (a.tau ? a.tau[g2] : 0ull) : a.prefix[g2]);
@@ -300,7 +333,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
                : h > score_key(INFINITY) ? __uint_as_float(0x7FFFFFFFu)  // NaN: no score passes
                                          : key_score(h);
     }
-    if (warp < 2) {
+    if (warp < 2 * NB) {
       const uint32_t b = __ballot_sync(0xFFFFFFFFu, live);
       if (lane == 0) s_live[warp] = b;
     }
@@ -328,7 +361,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   // (which the tile filter never writes) is reported and read as -1: its rows
   // are loaded from the first tile and no query tests them
   auto tile_id = [&](int64_t k) -> int32_t {
-    const int32_t t = a.tile_row[entry(k)];
+    const int32_t t = a.dense_tiles ? (int32_t)entry(k) : a.tile_row[entry(k)];
     if ((int64_t)(uint32_t)t < a.tile_cap && tile_first_row(a, t) < a.n) return t;
     atomicOr(a.err, kErrTileList);
     return -1;
@@ -372,7 +405,9 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc2 = idesc_tf32(kTileRows, 2 * N), idesc1 = idesc_tf32(kTileRows, N);
+      // every query block at once: x_hi against all 2 NB N operand rows, x_lo
+      // against the NB N q_hi rows (one accumulator of 2 NB N columns)
+      const uint32_t idesc2 = idesc_tf32(kTileRows, 2 * NB * N), idesc1 = idesc_tf32(kTileRows, NB * N);
       uint64_t pr = 0, pa = 0;
       bool issued = false;
       for (int64_t k = 0; k < n_mine && ok; ++k) {
@@ -435,10 +470,10 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           }
           tc_fence_after();
           const uint32_t ah = tmem_base + acol0 + (uint32_t)(l * 64), al = ah + 32u;
-          const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
+          const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * NB * N * 128);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
-            // D[0,2N) += x_hi . [q_hi ; q_lo]^T, then D[0,N) += x_lo . q_hi^T
+            // D[0,2NB N) += x_hi . [q_hi ; q_lo]^T, then D[0,NB N) += x_lo . q_hi^T
             mma_tf32_tmem_a(d, ah + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc2,
                             (c | ks) != 0 ? 1u : 0u);
             mma_tf32_tmem_a(d, al + (uint32_t)(ks * 8), sw128_desc(qa + (uint32_t)ks * 32u), idesc1, 1u);
@@ -515,10 +550,15 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     const int quarter = warp & 3;
     const int eset = epi_set(warp);
     const int ew = eset * 4 + ((warp - 2) & 3);  // the warp's candidate list (each set's warps start at 2 mod 4)
+    const int bq = NB > 1 ? eset : 0;  // the set's query block (one per set with several blocks)
+    const int qoff = bq * N;           // its first query within the launch
     // Candidates are recorded in a per-warp shared-memory list by the lanes that
-    // find them: a shared-memory atomic each in the main scan, where hits are
-    // rare (a prefix sum over the lanes was measured slower there), and
-    // prefix-sum places in the threshold sample, where nearly every test hits.
+    // find them.  In the main scan, where hits are rare, each lane owns every
+    // 32nd entry (entry 32 i + lane, i < kLaneCand) and counts its own in a
+    // register: no shared atomic or cross-lane exchange sits on the hit path
+    // (a shared-memory atomic per hit measured three times the cost of the
+    // score tests).  In the threshold sample, where nearly every test hits, a
+    // prefix sum over the lanes' hit counts packs the list.
     // A flush tests them exactly,
     // counts them per query, reserves each query's range of its buffer with one
     // global atomic and scatters the keys, so a query with many candidates (a
@@ -528,10 +568,12 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     uint64_t *ckey = reinterpret_cast<uint64_t *>(smem + T.cand) + (size_t)ew * kWarpCand;
     uint8_t *cqry = reinterpret_cast<uint8_t *>(smem + T.cand + (size_t)4 * kSets * kWarpCand * 8) + (size_t)ew * kWarpCand;
     uint32_t *ccnt = reinterpret_cast<uint32_t *>(smem + T.ccnt) + ew;
-    uint32_t *cq = reinterpret_cast<uint32_t *>(smem + T.cq) + (size_t)ew * 2 * N;
+    uint32_t *cq = reinterpret_cast<uint32_t *>(smem + T.cq) + (size_t)ew * 2 * N;  // the set's block
     uint32_t *cb = cq + N;
     if (lane == 0) *ccnt = 0u;
     __syncwarp();
+    const bool lane_slots = a.tau != nullptr;  // main scan: per-lane entries
+    uint32_t lcnt = 0;                         // this lane's entries (lane_slots)
     auto flush = [&]() {
       __syncwarp();
       const uint32_t n = *ccnt < (uint32_t)kWarpCand ? *ccnt : (uint32_t)kWarpCand;
@@ -542,15 +584,15 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
       for (int u = 0; u < kWarpCand / 32; ++u) {
         const uint32_t e = (uint32_t)lane + 32u * (uint32_t)u;
         rk[u] = 0xFFFFFFFFu;
-        if (e < n) {
+        if (lane_slots ? (uint32_t)u < lcnt : e < n) {
           const int q = cqry[e];
-          if (ckey[e] >= taus[q]) rk[u] = atomicAdd(&cq[q], 1u);
+          if (ckey[e] >= taus[q]) rk[u] = atomicAdd(&cq[q - qoff], 1u);
         }
       }
       __syncwarp();
       for (int i = lane; i < N; i += 32) {
         const uint32_t c = cq[i];
-        cb[i] = c != 0u ? atomicAdd(&a.buf_cnt[a.q_base + i], c) : 0u;
+        cb[i] = c != 0u ? atomicAdd(&a.buf_cnt[a.q_base + qoff + i], c) : 0u;
       }
       __syncwarp();
 #pragma unroll
@@ -558,7 +600,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         if (rk[u] == 0xFFFFFFFFu) continue;
         const uint32_t e = (uint32_t)lane + 32u * (uint32_t)u;
         const int q = cqry[e];
-        const uint32_t pos = cb[q] + rk[u];
+        const uint32_t pos = cb[q - qoff] + rk[u];
         if ((int64_t)pos < a.buf_cap)
           a.buf[(size_t)(a.q_base + q) * (size_t)a.buf_cap + pos] = ckey[e];
         else
@@ -566,15 +608,18 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
       }
       __syncwarp();
       if (lane == 0) *ccnt = 0u;
+      lcnt = 0u;
       __syncwarp();
     };
     // this lane's row mask (and FP8 row scale) read one tile ahead, the tile
     // ids two ahead, so no global load latency sits on the tile's path
     const int lr = quarter * 32 + lane;
     const RowMask<N> *msg = static_cast<const RowMask<N> *>(a.tile_msg) + lr;
+    // two query blocks: the second block's row masks come from their own array
+    const RowMask<N> *msg2 = NB > 1 ? static_cast<const RowMask<N> *>(a.tile_msg2) + lr : msg;
     auto tile_of = [&](int64_t k) -> int32_t { return k < n_mine ? tile_id(k) : -1; };
-    auto mask_of = [&](int32_t t, int64_t k) -> RowMask<N> {
-      return k < n_mine && t >= 0 ? msg[(size_t)t * kTileRows] : (RowMask<N>)0;
+    auto mask_of = [&](int32_t t, int64_t k, int bq) -> RowMask<N> {
+      return k < n_mine && t >= 0 ? (bq == 0 ? msg : msg2)[(size_t)t * kTileRows] : (RowMask<N>)0;
     };
     auto scale_of = [&](int32_t t, int64_t k) -> float {  // FP8 rows: score = scale * <q, x8>
       if constexpr (E == kElemFP8) {
@@ -586,18 +631,23 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     };
     // the list may be one written for a larger set of queries (the exact
     // fallback reuses the main pass's list): only this launch's queries count
-    const uint64_t live_mask = ((uint64_t)s_live[1] << 32) | s_live[0];
-    int32_t t_next = tile_of(eset), t_after = tile_of(eset + kSets);
-    RowMask<N> qm_next = mask_of(t_next, eset);
-    float xs_next = scale_of(t_next, eset);
-    for (int64_t k = eset; k < n_mine && ok; k += kSets) {  // this set's tiles
+    // Units of work: accumulator use pa = tile k x NB + query block; this set
+    // takes pa = eset, eset + kSets, ..: alternate tiles with one block, block
+    // eset of every tile with two (NB = kSets)
+    const uint64_t live_mask = ((uint64_t)s_live[2 * bq + 1] << 32) | s_live[2 * bq];
+    constexpr int kStep = NB > 1 ? 1 : kSets;  // tiles between two of the set's units
+    const int64_t k0 = NB > 1 ? 0 : eset;
+    int32_t t_next = tile_of(k0), t_after = tile_of(k0 + kStep);
+    RowMask<N> qm_next = mask_of(t_next, k0, bq);
+    float xs_next = scale_of(t_next, k0);
+    for (int64_t k = k0; k < n_mine && ok; k += kStep) {  // this set's tiles
       const uint64_t qmask = (uint64_t)qm_next & live_mask;
+      qm_next = mask_of(t_after, k + kStep, bq);
       const uint32_t grow = (uint32_t)(tile_first_row(a, max(t_next, 0)) + lr);
       const float xs = xs_next;
-      qm_next = mask_of(t_after, k + kSets);
-      xs_next = scale_of(t_after, k + kSets);
+      xs_next = scale_of(t_after, k + kStep);
       t_next = t_after;
-      t_after = tile_of(k + 2 * kSets);
+      t_after = tile_of(k + 2 * kStep);
       const uint64_t pa = (uint64_t)k;  // accumulator use = tile index
       const int ab = (int)(pa % (uint64_t)kAcc);
       if (!warp_wait(&acc_full[ab], (uint32_t)((pa / kAcc) & 1u), lane)) {
@@ -616,7 +666,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
           // exact key tests run at the flush).
           float sc[16];
           uint32_t hit = 0;
-          const float4 *tv = reinterpret_cast<const float4 *>(thr + 16 * j);
+          const float4 *tv = reinterpret_cast<const float4 *>(thr + qoff + 16 * j);
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const float4 t = tv[v];
@@ -624,12 +674,12 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int b = 4 * v + u;
-              sc[b] = (__uint_as_float(rh[b]) + __uint_as_float(rl[b])) * xs;
+              sc[b] = (E == kElemF32 ? __uint_as_float(rh[b]) + __uint_as_float(rl[b]) : __uint_as_float(rh[b])) * xs;
               hit |= (sc[b] >= tt[u] ? 1u : 0u) << b;
             }
           }
           hit &= bm;
-          if (a.tau == nullptr) {
+          if (NB == 1 && a.tau == nullptr) {
             // Threshold sample: every passing pair is a candidate, so nearly
             // every test hits; a prefix sum over the lanes' hit counts places
             // them in the warp's list without atomics (flushed when full).
@@ -652,7 +702,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
               for (int b = 0; b < 16; ++b) {
                 if ((hit >> b) & 1u) {
                   ckey[e] = make_key(sc[b], grow);
-                  cqry[e] = (uint8_t)(16 * j + b);
+                  cqry[e] = (uint8_t)(qoff + 16 * j + b);
                   ++e;
                 }
               }
@@ -662,30 +712,31 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
             }
           } else if (__any_sync(0xFFFFFFFFu, hit != 0u)) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {  // at most 256 entries are added between two checks
+            for (int h = 0; h < 2; ++h) {  // eight queries at a time: room for all of every lane's hits, else flush first
               const uint32_t hh = (hit >> (8 * h)) & 0xFFu;
-              if (!__any_sync(0xFFFFFFFFu, hh != 0u)) continue;
+              if (__any_sync(0xFFFFFFFFu, lcnt + (uint32_t)__popc(hh) > (uint32_t)kLaneCand)) flush();
+              if (hh != 0u) {
 #pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                if ((hh >> u) & 1u) {
-                  const int b = 8 * h + u;
-                  const uint32_t e = atomicAdd(ccnt, 1u);
-                  if (e < (uint32_t)kWarpCand) {
+                for (int u = 0; u < 8; ++u) {
+                  if ((hh >> u) & 1u) {
+                    const int b = 8 * h + u;
+                    const uint32_t e = lcnt * 32u + (uint32_t)lane;
                     ckey[e] = make_key(sc[b], grow);
-                    cqry[e] = (uint8_t)(16 * j + b);
+                    cqry[e] = (uint8_t)(qoff + 16 * j + b);
+                    ++lcnt;
                   }
                 }
               }
-              __syncwarp();
-              if (*ccnt > (uint32_t)(kWarpCand / 2)) flush();
             }
           }
         } else {
 #pragma unroll
           for (int b = 0; b < 16; ++b) {
             if (!((bm >> b) & 1u)) continue;
-            const int q = 16 * j + b;
-            const uint64_t key = make_key((__uint_as_float(rh[b]) + __uint_as_float(rl[b])) * xs, grow);
+            const int q = qoff + 16 * j + b;
+            const uint64_t key =
+                make_key((E == kElemF32 ? __uint_as_float(rh[b]) + __uint_as_float(rl[b]) : __uint_as_float(rh[b])) * xs,
+                         grow);
             if (top >= 64 || (key >> top) == (taus[q] >> top))
               atomicAdd(&a.hist[(size_t)(a.q_base + q) * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
           }
@@ -698,12 +749,12 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
         if (!__any_sync(0xFFFFFFFFu, ((qmask >> (16 * j)) & 0xFFFFu) != 0u)) continue;  // no lane needs it
         __syncwarp();
         uint32_t rh[16], rl[16];
-        tmem_ld16(taddr + (uint32_t)(16 * j), rh);
+        tmem_ld16(taddr + (uint32_t)(qoff + 16 * j), rh);
         if constexpr (E == kElemF32) {
-          tmem_ld16(taddr + (uint32_t)(N + 16 * j), rl);
+          tmem_ld16(taddr + (uint32_t)(NB * N + qoff + 16 * j), rl);
         } else {
 #pragma unroll
-          for (int z = 0; z < 16; ++z) rl[z] = 0u;  // one accumulator column per query
+          for (int z = 0; z < 16; ++z) rl[z] = 0u;  // one accumulator column per query (rl unused)
         }
         tmem_ld_wait();
         test_block(j, rh, rl);
@@ -739,19 +790,20 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   }
 }
 
-template <int N, int E>
+template <int N, int E, int NB = 1>
 cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cudaStream_t s) {
-  static_assert(tc_acc_bufs(E, N) * tc_acc_w(E, N) + (E == kElemF32 ? 64 * kABufs : 0) <= (int)kTmemCols,
+  static_assert(tc_acc_bufs(E, N) * tc_acc_w(E, N) + (E == kElemF32 ? 64 * tc_abufs(E, N) : 0) <= (int)kTmemCols,
                 "tensor memory budget");
   static_assert(tc_acc_bufs(E, N) % tc_epi_sets(E) == 0, "each accumulator buffer belongs to one epilogue set");
-  static_assert(kABufs % 2 == 0, "each converter set owns every other x_hi/x_lo buffer");
+  static_assert(E != kElemF32 || (tc_abufs(E, N) % 2 == 0 && tc_abufs(E, N) >= 4),
+                "each converter set owns every other x_hi/x_lo buffer");
   const size_t budget = 220u * 1024u;
   int S = 12;  // raw stages: even (each converter set owns every other stage)
   if (a.d_pad % tc_epc(E) != 0) return cudaErrorInvalidValue;
-  while (S > 2 && tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E)).total + 1024 > budget) S -= 2;
-  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E));
+  while (S > 2 && tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E), NB).total + 1024 > budget) S -= 2;
+  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E), NB);
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
-  auto *fn = k_scan_tc<N, E>;
+  auto *fn = k_scan_tc<N, E, NB>;
   cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)(T.total + 1024));
   if (e != cudaSuccess) return e;
   fn<<<grid, tc_threads(E), T.total + 1024, s>>>(a, tmap, S);
@@ -778,6 +830,15 @@ cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cuda
     case kElemFP8 * 4 + 3: return launch_tc<64, kElemFP8>(a, tm, grid, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_scan_tc2(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s) {
+  // FP32 rows, 65..128 queries as two 64-query blocks; a tile's chunks must all
+  // fit the x_hi/x_lo buffers, which stay until the second block has read them
+  if (a.elem != kElemF32 || a.d_pad > 32 * tc_abufs(kElemF32, 64) || a.nq <= 64 || a.nq > 128 || !a.dense_tiles ||
+      a.tile_msg2 == nullptr || a.mode != kCollect || a.tau == nullptr)  // the main scan only
+    return cudaErrorInvalidValue;
+  return launch_tc<64, kElemF32, 2>(a, *static_cast<const CUtensorMap *>(tmap_x), grid, s);
 }
 
 }  // namespace lr

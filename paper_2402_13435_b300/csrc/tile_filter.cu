@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
                         (__reduce_or_sync(0xFFFFFFFFu, any1) != 0u ? 2u : 0u);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      if (!((fl >> h) & 1u)) continue;
+      if (!a.dense_tiles && !((fl >> h) & 1u)) continue;  // dense: every tile's masks, zero or not
       if ((int64_t)(it * 2 + h) >= a.tile_cap) {  // the list buffers are smaller than the visit
         if (lane == 0) atomicOr(a.err, kErrTileList);
         continue;
@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_fil
           msg[w * 32 + lane] = lo32;
         }
       }
+      if (a.dense_tiles) continue;  // no list: the scan visits every tile
       if ((uint32_t)lane == n_tiles) my_tile = tile;
       ++n_tiles;
     }
@@ -235,7 +236,8 @@ cudaError_t launch_tile_filter(const ScanArgs &a, int num_sms, cudaStream_t s) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(runs, (int64_t)num_sms * per_sm));
   const size_t smem = (size_t)2 * kTfRun * (a.n_slots > 0 ? a.n_slots : 1) * 32 +
                       (size_t)(a.nq + 1 + a.n_cl + 1 + a.n_tm) * sizeof(int32_t);
-  auto *fn = a.nq <= 32 ? k_tile_filter<uint32_t> : k_tile_filter<uint64_t>;
+  // dense masks feed a two-block scan, which reads 64-bit masks whatever the block's size
+  auto *fn = a.nq <= 32 && !a.dense_tiles ? k_tile_filter<uint32_t> : k_tile_filter<uint64_t>;
   // the static shared memory (slot pointers, pass counts) counts against the
   // 48 KB default too: opt in well before the dynamic part alone reaches it
   if (smem > 32u * 1024u) {
