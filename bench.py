@@ -270,8 +270,8 @@ def peaks():
 
 def scan_plan(args):
     """The scan kernel a search ran and the queries one launch of it serves (tensor-core tiles: 64 per
-    launch at d <= 128 and 32 above, 128 for FP32 rows at d <= 128 in batches above 64, whose
-    launches score each tile against two 64-query blocks; SIMT matrix-vector scan: 8 per launch).  The plan is the one the
+    launch at d <= 128 and 32 above; FP32 rows at d <= 128 in batches above 64: 128 (two 64-query
+    blocks per launch), 96 above 128 queries (two 48-query blocks); SIMT matrix-vector scan: 8 per launch).  The plan is the one the
     library reported for the timed steps (args.plan_used); before that, the requested plan, with "auto"
     read as the batch-size rule."""
     d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
@@ -281,7 +281,7 @@ def scan_plan(args):
         plan = "gemv"  # low-precision rows reach the tensor cores from 64 values up
     if plan == "tc":
         if args.dtype == "f32" and d_pad <= 128 and args.batch > 64:
-            return "k_scan_tc", 128, d_pad
+            return "k_scan_tc", (96 if args.batch > 128 else 128), d_pad
         return "k_scan_tc", (64 if d_pad <= 128 else 32), d_pad
     return "k_scan_gemv", 8, d_pad
 
@@ -311,7 +311,7 @@ def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
     query of the launch (each read once at d_pad*elem bytes) plus, per distinct term, the cheaper of
     its bitmap and its posting list.  Tensor-core scan (the tile filter has run before, alongside the
     threshold sample): the same rows plus the row masks of the listed tiles (128 rows x 4 bytes, 8 above
-    32 queries, per 128-row tile holding a passing row); a two-block launch (128 queries) reads two
+    32 queries, per 128-row tile holding a passing row); a two-block launch (96 or 128 queries) reads two
     8-byte masks per row of every tile."""
     import torch
 
@@ -332,7 +332,7 @@ def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
         terms = {int(t) for t in sub.terms} if sub.terms.size and int(sub.q_off[-1]) > 0 else set()
         p = sum(min(n / 8.0, 4.0 * float(df[t])) for t in terms)
         masks = 0
-        if kernel == "k_scan_tc" and per == 128 and sub.n > 64:
+        if kernel == "k_scan_tc" and per in (96, 128) and sub.n > per // 2:
             masks = (n + 127) // 128 * 128 * 16
         elif kernel == "k_scan_tc":
             tiles = int(np.count_nonzero(words[: len(words) // 4 * 4].reshape(-1, 4).any(axis=1)))

@@ -1433,7 +1433,12 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (plan == LR_PLAN_TC && !tc_ok)
     return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable for this index (no TMA descriptor; "
                                     "low-precision rows need dim > 32)");
-  const int max_q = plan == LR_PLAN_TC ? (ix->d_pad <= 128 ? kTcMaxQ : kTcMaxQ / 2) : kGemvMaxQ;
+  // FP32 rows above 64 queries: pairs of sub-batches share two-block scans,
+  // of 64 up to 128 queries, of 48 above (two accumulators: fewer launches
+  // than blocks of 64 from there on)
+  const bool pairs = plan == LR_PLAN_TC && !lowp && ix->tile_msg2 != nullptr && B > kTcMaxQ;
+  const int block_q = B > kTc2MinBatch ? kTc2BlockQ : kTcMaxQ;
+  const int max_q = plan == LR_PLAN_TC ? (pairs ? block_q : ix->d_pad <= 128 ? kTcMaxQ : kTcMaxQ / 2) : kGemvMaxQ;
   lr_status st = compile_filters(ix, f, B, max_q, stage, C);
   if (st != LR_OK) return st;
   // ks: the K the scan and the selection work with (oversample x K for the
@@ -1600,13 +1605,13 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // 2. main scan: candidates at or above the threshold, pass counts
   if (early_filter) LR_CK(cudaStreamWaitEvent(s, ix->ev_join, 0));
   if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
-  // FP32 rows: two consecutive sub-batches (a full one of 64 queries and the
-  // next) share one scan that converts each tile once and scores it against
-  // both; their tile filters write every tile's masks (no list)
-  const bool pairs = plan == LR_PLAN_TC && !lowp && ix->tile_msg2 != nullptr && !early_filter;
+  // FP32 rows: two consecutive sub-batches (a full one of block_q queries and
+  // the next) share one scan that converts each tile once and scores it
+  // against both; their tile filters write every tile's masks (no list)
   for (size_t i = 0; i < C.subs.size(); ++i) {
     const SubBatch &sb = C.subs[i];
-    if (pairs && i + 1 < C.subs.size() && sb.nq == kTcMaxQ && C.subs[i + 1].q_base == sb.q_base + kTcMaxQ) {
+    if (pairs && !early_filter && i + 1 < C.subs.size() && sb.nq == block_q &&
+        C.subs[i + 1].q_base == sb.q_base + block_q) {
       const SubBatch &sb2 = C.subs[i + 1];
       ScanArgs a0 = main_args(sb), a1 = main_args(sb2);
       a0.dense_tiles = a1.dense_tiles = 1;
@@ -1616,6 +1621,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       ScanArgs a2 = a0;
       a2.nq = sb.nq + sb2.nq;
       a2.tile_msg2 = ix->tile_msg2;
+      a2.block_q = block_q;
       LR_LAUNCH(launch_scan_tc2(a2, &ix->tmap_x, grid_for(2 * ix->n_groups), s));
       ++n_scan;
       ++i;

@@ -171,14 +171,14 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
 template <int N, int E, int NB>
 __global__ void __launch_bounds__(tc_threads(E), 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
-  static_assert(NB == 1 || (NB == 2 && E == kElemF32 && N == 64), "two query blocks: FP32 rows, 64 queries each");
+  static_assert(NB == 1 || (NB == 2 && E == kElemF32 && (N == kTc2BlockQ || N == 64)),
+                "two query blocks: FP32 rows, 48 or 64 queries each");
   static_assert(NB == 1 || NB == tc_epi_sets(E), "with several query blocks each epilogue set takes one");
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned for the swizzle atoms
   constexpr int kSets = tc_epi_sets(E), kThreads = tc_threads(E);
-  constexpr int kABufs = E == kElemF32 ? tc_abufs(E, N) : 2;  // (unused for BF16 / e4m3 rows)
   constexpr int kWarpCand = tc_warp_cand(NB), kLaneCand = kWarpCand / 32;
   static_assert(kLaneCand >= 8, "a lane records up to eight hits between two room checks");
   const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * kSets, NB);
@@ -190,9 +190,16 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   float *thr = reinterpret_cast<float *>(taus + NB * N);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + T.bars);
   uint64_t *raw_full = bars, *raw_empty = bars + S;
+  // several query blocks share each accumulator of 2 NB N columns (both
+  // epilogue sets read it), as many as fit next to two x_hi/x_lo buffers:
+  // two of 192 columns for 48-query blocks (the MMAs of a tile overlap the
+  // tests of the one before), one of 256 for 64-query blocks
+  constexpr int kAccW = NB > 1 ? 2 * NB * N : tc_acc_w(E, N);
+  constexpr int kAcc = NB > 1 ? (512 - 2 * 64) / kAccW : tc_acc_bufs(E, N);
+  constexpr int kABufs = E != kElemF32 ? 2 : NB > 1 ? (512 - kAcc * kAccW) / 64 : tc_abufs(E, N);  // (unused for BF16 / e4m3)
+  static_assert(E != kElemF32 || (kAcc * kAccW + 64 * kABufs <= 512 && kABufs >= 2 && kABufs % 2 == 0),
+                "tensor memory: accumulators and an even number of x_hi/x_lo buffers");
   uint64_t *a_full = bars + 2 * S, *a_empty = a_full + kABufs;
-  // several query blocks share one accumulator of 2 NB N columns (both epilogue sets read it)
-  constexpr int kAcc = NB > 1 ? 1 : tc_acc_bufs(E, N), kAccW = NB > 1 ? 2 * NB * N : tc_acc_w(E, N);
   uint64_t *acc_full = a_empty + kABufs, *acc_empty = acc_full + kAcc;
   uint64_t *drain = acc_empty + kAcc;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + T.holder);
@@ -634,7 +641,14 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     // Units of work: accumulator use pa = tile k x NB + query block; this set
     // takes pa = eset, eset + kSets, ..: alternate tiles with one block, block
     // eset of every tile with two (NB = kSets)
-    const uint64_t live_mask = ((uint64_t)s_live[2 * bq + 1] << 32) | s_live[2 * bq];
+    uint64_t live_mask;  // bits of the launch's queries qoff .. qoff + N - 1
+    {
+      const int w = qoff >> 5, sh = qoff & 31;
+      const uint64_t lo = (uint64_t)s_live[w] | ((uint64_t)(w + 1 < 2 * NB ? s_live[w + 1] : 0u) << 32);
+      const uint64_t hi = w + 2 < 2 * NB ? s_live[w + 2] : 0u;
+      live_mask = sh != 0 ? (lo >> sh) | (hi << (64 - sh)) : lo;
+      if (N < 64) live_mask &= (1ull << N) - 1ull;
+    }
     constexpr int kStep = NB > 1 ? 1 : kSets;  // tiles between two of the set's units
     const int64_t k0 = NB > 1 ? 0 : eset;
     int32_t t_next = tile_of(k0), t_after = tile_of(k0 + kStep);
@@ -795,7 +809,7 @@ cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cuda
   static_assert(tc_acc_bufs(E, N) * tc_acc_w(E, N) + (E == kElemF32 ? 64 * tc_abufs(E, N) : 0) <= (int)kTmemCols,
                 "tensor memory budget");
   static_assert(tc_acc_bufs(E, N) % tc_epi_sets(E) == 0, "each accumulator buffer belongs to one epilogue set");
-  static_assert(E != kElemF32 || (tc_abufs(E, N) % 2 == 0 && tc_abufs(E, N) >= 4),
+  static_assert(E != kElemF32 || NB > 1 || (tc_abufs(E, N) % 2 == 0 && tc_abufs(E, N) >= 4),
                 "each converter set owns every other x_hi/x_lo buffer");
   const size_t budget = 220u * 1024u;
   int S = 12;  // raw stages: even (each converter set owns every other stage)
@@ -833,12 +847,15 @@ cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cuda
 }
 
 cudaError_t launch_scan_tc2(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s) {
-  // FP32 rows, 65..128 queries as two 64-query blocks; a tile's chunks must all
-  // fit the x_hi/x_lo buffers, which stay until the second block has read them
-  if (a.elem != kElemF32 || a.d_pad > 32 * tc_abufs(kElemF32, 64) || a.nq <= 64 || a.nq > 128 || !a.dense_tiles ||
-      a.tile_msg2 == nullptr || a.mode != kCollect || a.tau == nullptr)  // the main scan only
+  // FP32 rows, d <= 128 (the query operand of both blocks fills 96 or 128 KB),
+  // block_q + 1 .. 2 block_q queries as two blocks of block_q (48 or 64), the
+  // main scan only
+  const int bq = a.block_q;
+  if (a.elem != kElemF32 || a.d_pad > 128 || (bq != kTc2BlockQ && bq != 64) || a.nq <= bq || a.nq > 2 * bq ||
+      !a.dense_tiles || a.tile_msg2 == nullptr || a.mode != kCollect || a.tau == nullptr)
     return cudaErrorInvalidValue;
-  return launch_tc<64, kElemF32, 2>(a, *static_cast<const CUtensorMap *>(tmap_x), grid, s);
+  const CUtensorMap &tm = *static_cast<const CUtensorMap *>(tmap_x);
+  return bq == 64 ? launch_tc<64, kElemF32, 2>(a, tm, grid, s) : launch_tc<kTc2BlockQ, kElemF32, 2>(a, tm, grid, s);
 }
 
 }  // namespace lr

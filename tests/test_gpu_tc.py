@@ -141,19 +141,20 @@ def test_tc_selective_batch_reads_compact_rows(lr, dtype):
     lr.lr_index_destroy(idx)
 
 
-@pytest.mark.parametrize("B,n", [(128, 30_820), (150, 41_003), (200, 25_700)])
+@pytest.mark.parametrize("B,n", [(100, 25_700), (129, 30_820), (150, 41_003), (200, 25_700)])
 def test_tc_two_query_blocks_match_oracle(lr, B, n):
-    """FP32 batches above 64 queries: a full 64-query sub-batch and the next share one scan launch that
-    scores each converted tile against both blocks (dense row masks, every tile visited).  Index sizes
-    end in a last 256-row group of 100, 32 and 100 rows (a last group of at most 128 rows has no
-    second tile); the exact fallback and the threshold sample keep one block per launch."""
+    """FP32 batches above 64 queries: a full sub-batch and the next share one scan launch that scores
+    each converted tile against both blocks (dense row masks, every tile visited): sub-batches of 64
+    up to 128 queries (one accumulator of 256 columns), of 48 above (two of 192).  Index sizes end in
+    a last 256-row group of 100, 32 and 100 rows (a last group of at most 128 rows has no second
+    tile); the exact fallback and the threshold sample keep one block per launch."""
     d, V, K = 128, 1024, 50
     c = datagen.corpus(41 + B, n, d, V, 14.0, 1.1)
     f = datagen.filters(300 + B, B, V, 1.1)
     qs = [f.clauses(b) for b in range(B)]
     qs[1] = []                       # unfiltered query in block 0
     qs[70] = []                      # and in block 1
-    qs[100] = [[V - 1]]              # a rare term: few passing rows
+    qs[B - 5] = [[V - 1]]            # a rare term: few passing rows
     f = Filters.from_lists(qs)
     Q = datagen.query_embeddings(300 + B, B, d)
     idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), V, bitsets=c.bitsets(), metric="cosine",
@@ -161,17 +162,23 @@ def test_tc_two_query_blocks_match_oracle(lr, B, n):
     got = _run(lr, idx, Q, f, K, plan="tc")
     ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
     check_topk(*got, ref, c.X, Q, c.job_off, c.job_terms, f)
+    # every passing job of these small indexes is a candidate: no query may need the exact
+    # fallback (a block that skipped some of its queries would, and still return exact rows)
+    _, _, _, st = lr.lr_search(idx, torch.from_numpy(Q).cuda(), f, K, plan="tc", stats=True)
+    torch.cuda.synchronize()
+    assert not np.asarray(st["fallback"]).any(), np.flatnonzero(np.asarray(st["fallback"]))
     for kw in (dict(force_exact_fallback=True), dict(cand_cap=60), dict(sample_stride=-1)):
         other = _run(lr, idx, Q, f, K, plan="tc", **kw)
         assert np.array_equal(other[0], got[0]) and np.array_equal(other[1], got[1]), kw
-    for b in (0, 63, 64, 65, B - 1):  # the same rows as the query searched alone (one block)
+    for b in (0, 47, 48, 95, 96, B - 1):  # the same rows as the query searched alone (one block)
         alone = _run(lr, idx, Q[b:b + 1].copy(), f.subset([b]), K, plan="tc")
         assert np.array_equal(alone[0][0], got[0][b]) and np.array_equal(alone[1][0], got[1][b]), b
 
 
 def test_tc_two_query_blocks_with_uneven_sub_batches(lr):
     """Sub-batches end early when a run of queries would exceed 256 distinct terms: only a full
-    64-query sub-batch pairs with the next one, the others scan alone."""
+    48-query sub-batch pairs with the next one (here the first two); the runs of 42 six-term queries
+    after them scan alone."""
     n, d, V, B, K = 33_000, 64, 2048, 180, 40
     c = datagen.corpus(43, n, d, V, 14.0, 1.1)
     qs = []
@@ -179,7 +186,7 @@ def test_tc_two_query_blocks_with_uneven_sub_batches(lr):
         if b < 64:
             qs.append([[b % 50]])                                   # 50 distinct terms: one full sub-batch
         else:
-            qs.append([[50 + 5 * b + j for j in range(5)]])         # 5 fresh terms each: runs of 51
+            qs.append([[50 + 6 * b + j for j in range(6)]])         # 6 fresh terms each: runs of 42
     f = Filters.from_lists(qs)
     Q = datagen.query_embeddings(43, B, d)
     idx = lr.lr_index_create(c.X, V, bitsets=c.bitsets(), metric="dot", max_batch=B, max_k=64)
