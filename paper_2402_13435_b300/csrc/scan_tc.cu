@@ -72,8 +72,15 @@ constexpr int kEpiWarp1 = 14;
 // BF16 and e4m3 rows need no converters (their MMAs read the loaded stage):
 // warps 2-5 and 10-13 become epilogue sets 2 and 3 there, so four sets of four
 // warps test alternate tiles
-__host__ __device__ constexpr int tc_epi_sets(int e) { return e == kElemF32 ? 2 : 4; }
-__host__ __device__ constexpr int tc_threads(int e) { return (e == kElemF32 ? kEpiWarp1 + 4 : kEpiWarp1 + 4) * 32; }
+// FP32 rows: one set up to 32 queries (a second measured 1.5 % slower there:
+// its shared memory comes out of the raw stages), two for wider blocks and for
+// two-block launches (one set per block)
+__host__ __device__ constexpr int tc_epi_sets(int e, int n, int nb) {
+  return e != kElemF32 ? 4 : (nb > 1 || n > 32) ? 2 : 1;
+}
+__host__ __device__ constexpr int tc_threads(int e, int n, int nb) {
+  return (tc_epi_sets(e, n, nb) == 1 ? kEpiWarp1 : kEpiWarp1 + 4) * 32;
+}
 __device__ __forceinline__ bool is_converter(int w) { return (w >= 2 && w < kEpiWarp0) || (w >= kConvWarp1 && w < kEpiWarp1); }
 // epilogue set of an epilogue warp: 6-9 -> 0, 14-17 -> 1, 2-5 -> 2, 10-13 -> 3
 __device__ __forceinline__ int epi_set(int w) { return w >= kEpiWarp1 ? 1 : w >= kConvWarp1 ? 3 : w >= kEpiWarp0 ? 0 : 2; }
@@ -169,16 +176,16 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
 // NB = 2: each converted tile is scored against two 64-query blocks, each into
 // its own accumulator (FP32 rows only; 128 queries per launch).
 template <int N, int E, int NB>
-__global__ void __launch_bounds__(tc_threads(E), 1)
+__global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
   static_assert(NB == 1 || (NB == 2 && E == kElemF32 && (N == kTc2BlockQ || N == 64)),
                 "two query blocks: FP32 rows, 48 or 64 queries each");
-  static_assert(NB == 1 || NB == tc_epi_sets(E), "with several query blocks each epilogue set takes one");
+  static_assert(NB == 1 || NB == tc_epi_sets(E, N, NB), "with several query blocks each epilogue set takes one");
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned for the swizzle atoms
-  constexpr int kSets = tc_epi_sets(E), kThreads = tc_threads(E);
+  constexpr int kSets = tc_epi_sets(E, N, NB), kThreads = tc_threads(E, N, NB);
   constexpr int kWarpCand = tc_warp_cand(NB), kLaneCand = kWarpCand / 32;
   static_assert(kLaneCand >= 8, "a lane records up to eight hits between two room checks");
   const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * kSets, NB);
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     fence_mbar_init();
     // tiles listed by the tile filter (never more than the list holds), or
     // with dense tile masks every tile of the visited groups, in order
-    if (a.dense_tiles) {
+    if (NB > 1 && a.dense_tiles) {
       const int64_t ng = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
       int64_t nt = 2 * ng;
       if (nt > 0 && tile_first_row(a, (int32_t)(nt - 1)) >= a.n) --nt;  // a last group of <= 128 rows
@@ -307,7 +314,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
 #pragma unroll
     for (int u = 0; u < kQu; ++u) {
       const int i = i0 + u * kThreads + threadIdx.x;
-      const int bq = i / (C32 * N * 32), ii = i % (C32 * N * 32);
+      const int bq = NB > 1 ? i / (C32 * N * 32) : 0, ii = NB > 1 ? i % (C32 * N * 32) : i;
       const int c = ii / (N * 32), rem = ii % (N * 32), r = rem / 32, k = rem % 32;
       const int qi = bq * N + r;
       v[u] = i < NB * C32 * N * 32 && qi < a.nq ? a.Q[(size_t)(a.q_base + qi) * a.d_pad + c * 32 + k] : 0.f;
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
     for (int u = 0; u < kQu; ++u) {
       const int i = i0 + u * kThreads + threadIdx.x;
       if (i >= NB * C32 * N * 32) break;
-      const int bq = i / (C32 * N * 32), ii = i % (C32 * N * 32);
+      const int bq = NB > 1 ? i / (C32 * N * 32) : 0, ii = NB > 1 ? i % (C32 * N * 32) : i;
       const int c = ii / (N * 32), rem = ii % (N * 32), r = rem / 32, k = rem % 32;
       const float h = __uint_as_float(__float_as_uint(v[u]) & 0xFFFFE000u);
       const int rh = bq * N + r;  // rows of q_hi (all blocks), then of q_lo
@@ -368,7 +375,9 @@ __global__ void __launch_bounds__(tc_threads(E), 1)
   // (which the tile filter never writes) is reported and read as -1: its rows
   // are loaded from the first tile and no query tests them
   auto tile_id = [&](int64_t k) -> int32_t {
-    const int32_t t = a.dense_tiles ? (int32_t)entry(k) : a.tile_row[entry(k)];
+    // dense tile masks come with two-block launches only: a compile-time test
+    // (a runtime one here, on every tile id, measured 6 % slower)
+    const int32_t t = (NB > 1 && a.dense_tiles) ? (int32_t)entry(k) : a.tile_row[entry(k)];
     if ((int64_t)(uint32_t)t < a.tile_cap && tile_first_row(a, t) < a.n) return t;
     atomicOr(a.err, kErrTileList);
     return -1;
@@ -808,25 +817,27 @@ template <int N, int E, int NB = 1>
 cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cudaStream_t s) {
   static_assert(tc_acc_bufs(E, N) * tc_acc_w(E, N) + (E == kElemF32 ? 64 * tc_abufs(E, N) : 0) <= (int)kTmemCols,
                 "tensor memory budget");
-  static_assert(tc_acc_bufs(E, N) % tc_epi_sets(E) == 0, "each accumulator buffer belongs to one epilogue set");
+  static_assert(NB > 1 || tc_acc_bufs(E, N) % tc_epi_sets(E, N, NB) == 0,
+                "each accumulator buffer belongs to one epilogue set");
   static_assert(E != kElemF32 || NB > 1 || (tc_abufs(E, N) % 2 == 0 && tc_abufs(E, N) >= 4),
                 "each converter set owns every other x_hi/x_lo buffer");
   const size_t budget = 220u * 1024u;
   int S = 12;  // raw stages: even (each converter set owns every other stage)
   if (a.d_pad % tc_epc(E) != 0) return cudaErrorInvalidValue;
-  while (S > 2 && tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E), NB).total + 1024 > budget) S -= 2;
-  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E), NB);
+  while (S > 2 && tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E, N, NB), NB).total + 1024 > budget) S -= 2;
+  const TcLayout T = tc_layout(a.d_pad, E, N, S, 4 * tc_epi_sets(E, N, NB), NB);
   if (T.total + 1024 > budget) return cudaErrorInvalidValue;
   auto *fn = k_scan_tc<N, E, NB>;
   cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)(T.total + 1024));
   if (e != cudaSuccess) return e;
-  fn<<<grid, tc_threads(E), T.total + 1024, s>>>(a, tmap, S);
+  fn<<<grid, tc_threads(E, N, NB), T.total + 1024, s>>>(a, tmap, S);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s) {
+  if (a.dense_tiles) return cudaErrorInvalidValue;  // dense tile masks feed two-block launches only
   const CUtensorMap &tm = *static_cast<const CUtensorMap *>(tmap_x);
   const int n16 = (a.nq + 15) / 16 * 16;
   switch (a.elem * 4 + n16 / 16 - 1) {
