@@ -517,7 +517,6 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int n = a.ccnt[q] < a.c_stride ? a.ccnt[q] : a.c_stride;
   const int K = a.k[q] < n ? a.k[q] : n;
-  const int32_t *cid = a.cid + (size_t)q * a.c_stride;
   const float *qv = a.Q + (size_t)q * a.d_pad;
   uint64_t *keys = sbuf;
   uint64_t *sortb = sbuf + kMaxK;
