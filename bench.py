@@ -271,7 +271,8 @@ def peaks():
 def scan_plan(args):
     """The scan kernel a search ran and the queries one launch of it serves (tensor-core tiles: 64 per
     launch at d <= 128 and 32 above; FP32 rows at d <= 128 in batches above 64: 128 (two 64-query
-    blocks per launch), 96 above 128 queries (two 48-query blocks); SIMT matrix-vector scan: 8 per launch).  The plan is the one the
+    blocks per launch), 96 above 128 queries (two 48-query blocks); BF16 rows above 64 queries: 256 (four
+    64-query blocks in one N = 256 MMA); SIMT matrix-vector scan: 8 per launch).  The plan is the one the
     library reported for the timed steps (args.plan_used); before that, the requested plan, with "auto"
     read as the batch-size rule."""
     d_pad = 32 if args.dim <= 32 else 64 if args.dim <= 64 else 128 if args.dim <= 128 else 256
@@ -282,6 +283,8 @@ def scan_plan(args):
     if plan == "tc":
         if args.dtype == "f32" and d_pad <= 128 and args.batch > 64:
             return "k_scan_tc", (96 if args.batch > 128 else 128), d_pad
+        if args.dtype == "bf16" and d_pad <= 128 and args.batch > 64:
+            return "k_scan_tc", 256, d_pad
         return "k_scan_tc", (64 if d_pad <= 128 else 32), d_pad
     return "k_scan_gemv", 8, d_pad
 
@@ -332,8 +335,9 @@ def algorithmic_scan_bytes(lr, idx, filters, corpus, args):
         terms = {int(t) for t in sub.terms} if sub.terms.size and int(sub.q_off[-1]) > 0 else set()
         p = sum(min(n / 8.0, 4.0 * float(df[t])) for t in terms)
         masks = 0
-        if kernel == "k_scan_tc" and per in (96, 128) and sub.n > per // 2:
-            masks = (n + 127) // 128 * 128 * 16
+        block = {96: 48, 128: 64, 256: 64}.get(per) if kernel == "k_scan_tc" else None
+        if block is not None and sub.n > block:  # several blocks: every tile, one 8-byte mask per row and block
+            masks = (n + 127) // 128 * 128 * 8 * -(-sub.n // block)
         elif kernel == "k_scan_tc":
             tiles = int(np.count_nonzero(words[: len(words) // 4 * 4].reshape(-1, 4).any(axis=1)))
             if len(words) % 4:

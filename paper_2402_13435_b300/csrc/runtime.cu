@@ -135,7 +135,7 @@ struct lr_index {
   uint64_t *samp_buf = nullptr, *cand_buf = nullptr;
   int32_t *tile_row = nullptr;  // tile list of the tensor-core plan: main pass
   uint64_t *tile_msg = nullptr;
-  uint64_t *tile_msg2 = nullptr;  // FP32 rows, d <= 128, batches above 64: the second query block's masks
+  uint64_t *tile_msg2 = nullptr;  // d <= 128, batches above 64: the row masks of query blocks 1, 2, ..
   uint32_t *tile_cnt = nullptr;
   int64_t tile_cap = 0;
   uint64_t *thr_scratch = nullptr;  // split threshold selection: [B][8192] keys, [B][32] counts, [B] done
@@ -393,8 +393,13 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   const size_t o_tmsg = cv.take<uint64_t>((size_t)ix->tile_cap * 128);
   // two-block scans read the index once per 128 queries (FP32 rows only: the
   // low-precision scans already reach their bound with 64)
-  const bool two_block = ix->elem == kElemF32 && ix->d_pad <= 128 && B > kTcMaxQ;
-  const size_t o_tmsg2 = cv.take<uint64_t>(two_block ? (size_t)ix->tile_cap * 128 : 0);
+  // several-block scans: FP32 rows two blocks, BF16 rows four (one array of
+  // row masks per block after the first)
+  const int extra_blocks = ix->d_pad > 128 || B <= kTcMaxQ ? 0
+                           : ix->elem == kElemF32    ? 1
+                           : ix->elem == kElemBF16   ? kBf16Blocks - 1
+                                                     : 0;
+  const size_t o_tmsg2 = cv.take<uint64_t>((size_t)extra_blocks * ix->tile_cap * 128);
   ix->tile_cap_s = 2 * (ix->samp_cap / kGroupRows + 2);  // the sampled groups' tiles (sample rows <= samp_cap)
   const size_t o_trow_s = cv.take<int32_t>((size_t)ix->tile_cap_s);
   const size_t o_thr_scr = cv.take<uint64_t>((size_t)B * kThrScratchKeys);
@@ -446,7 +451,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   ix->cand_buf = (uint64_t *)(w + o_cand);
   ix->tile_row = (int32_t *)(w + o_trow);
   ix->tile_msg = (uint64_t *)(w + o_tmsg);
-  ix->tile_msg2 = two_block ? (uint64_t *)(w + o_tmsg2) : nullptr;
+  ix->tile_msg2 = extra_blocks > 0 ? (uint64_t *)(w + o_tmsg2) : nullptr;
   ix->tile_cnt = (uint32_t *)(w + o_tcnt);
   ix->tile_row_s = (int32_t *)(w + o_trow_s);
   ix->tile_msg_s = (uint64_t *)(w + o_tmsg_s);
@@ -1433,11 +1438,14 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (plan == LR_PLAN_TC && !tc_ok)
     return fail(LR_ERR_UNSUPPORTED, "tensor-core plan unavailable for this index (no TMA descriptor; "
                                     "low-precision rows need dim > 32)");
-  // FP32 rows above 64 queries: pairs of sub-batches share two-block scans,
-  // of 64 up to 128 queries, of 48 above (two accumulators: fewer launches
-  // than blocks of 64 from there on)
-  const bool pairs = plan == LR_PLAN_TC && !lowp && ix->tile_msg2 != nullptr && B > kTcMaxQ;
-  const int block_q = B > kTc2MinBatch ? kTc2BlockQ : kTcMaxQ;
+  // Above 64 queries consecutive sub-batches share several-block scans: FP32
+  // rows two blocks, of 64 up to 128 queries and of 48 above (two
+  // accumulators: fewer launches than blocks of 64 from there on); BF16 rows
+  // up to four blocks of 64
+  const bool pairs = plan == LR_PLAN_TC && ix->tile_msg2 != nullptr && B > kTcMaxQ &&
+                     (ix->elem == kElemF32 || ix->elem == kElemBF16);
+  const int block_q = ix->elem == kElemF32 && B > kTc2MinBatch ? kTc2BlockQ : kTcMaxQ;
+  const int group_max = ix->elem == kElemBF16 ? kBf16Blocks : 2;
   const int max_q = plan == LR_PLAN_TC ? (pairs ? block_q : ix->d_pad <= 128 ? kTcMaxQ : kTcMaxQ / 2) : kGemvMaxQ;
   lr_status st = compile_filters(ix, f, B, max_q, stage, C);
   if (st != LR_OK) return st;
@@ -1605,26 +1613,35 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   // 2. main scan: candidates at or above the threshold, pass counts
   if (early_filter) LR_CK(cudaStreamWaitEvent(s, ix->ev_join, 0));
   if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
-  // FP32 rows: two consecutive sub-batches (a full one of block_q queries and
-  // the next) share one scan that converts each tile once and scores it
-  // against both; their tile filters write every tile's masks (no list)
+  // Consecutive sub-batches (full ones of block_q queries, then one more)
+  // share one scan that reads (and for FP32 converts) each tile once and
+  // scores it against every block; their tile filters write every tile's
+  // masks (no list), block b's into tile_msg2 + (b - 1) msg_block_stride
+  const int64_t msg_stride = ix->tile_cap * 128;
   for (size_t i = 0; i < C.subs.size(); ++i) {
     const SubBatch &sb = C.subs[i];
-    if (pairs && !early_filter && i + 1 < C.subs.size() && sb.nq == block_q &&
-        C.subs[i + 1].q_base == sb.q_base + block_q) {
-      const SubBatch &sb2 = C.subs[i + 1];
-      ScanArgs a0 = main_args(sb), a1 = main_args(sb2);
-      a0.dense_tiles = a1.dense_tiles = 1;
-      a1.tile_msg = ix->tile_msg2;
-      LR_LAUNCH(launch_tile_filter(a0, ix->num_sms, s));
-      LR_LAUNCH(launch_tile_filter(a1, ix->num_sms, s));
-      ScanArgs a2 = a0;
-      a2.nq = sb.nq + sb2.nq;
-      a2.tile_msg2 = ix->tile_msg2;
-      a2.block_q = block_q;
-      LR_LAUNCH(launch_scan_tc2(a2, &ix->tmap_x, grid_for(2 * ix->n_groups), s));
+    size_t g = 1;  // sub-batches in this launch
+    while (pairs && !early_filter && g < (size_t)group_max && i + g < C.subs.size() &&
+           C.subs[i + g - 1].nq == block_q && C.subs[i + g].q_base == C.subs[i + g - 1].q_base + block_q)
+      ++g;
+    if (g > 1) {
+      ScanArgs a0 = main_args(sb);
+      int nq = 0;
+      for (size_t b = 0; b < g; ++b) {
+        ScanArgs ab = main_args(C.subs[i + b]);
+        ab.dense_tiles = 1;
+        if (b > 0) ab.tile_msg = ix->tile_msg2 + (size_t)(b - 1) * (size_t)msg_stride;
+        LR_LAUNCH(launch_tile_filter(ab, ix->num_sms, s));
+        nq += C.subs[i + b].nq;
+      }
+      a0.dense_tiles = 1;
+      a0.nq = nq;
+      a0.tile_msg2 = ix->tile_msg2;
+      a0.msg_block_stride = msg_stride;
+      a0.block_q = block_q;
+      LR_LAUNCH(launch_scan_tc2(a0, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(2 * ix->n_groups), s));
       ++n_scan;
-      ++i;
+      i += g - 1;
       continue;
     }
     LR_LAUNCH(launch_scan(main_args(sb), ix->n_groups, !early_filter, reuse_list));

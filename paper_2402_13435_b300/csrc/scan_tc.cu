@@ -143,8 +143,9 @@ __host__ __device__ inline TcLayout tc_layout(int d_pad, int e, int N, int S, in
   // of 128 bytes; BF16, per 64-value chunk a 2N-row block of 128-byte rows (N
   // used); e4m3, per 64-value chunk N rows of 64 bytes
   T.q = off;
-  off += (size_t)NB * (e == kElemF32 ? (size_t)T.C32 * 2 * N * 128
-                                      : e == kElemBF16 ? (size_t)T.C * 2 * N * 128 : (size_t)T.C * N * 64);
+  off += e == kElemF32    ? (size_t)NB * T.C32 * 2 * N * 128
+         : e == kElemBF16 ? (size_t)T.C * (NB > 1 ? NB * N : 2 * N) * 128
+                          : (size_t)NB * T.C * N * 64;
   T.taus = tc_align(off, 16);
   off = T.taus + (size_t)NB * N * 12;  // 64-bit thresholds, then their score words as floats
   T.cand = tc_align(off, 16);     // per epilogue warp: keys, then query indices (bytes)
@@ -178,8 +179,9 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
 template <int N, int E, int NB>
 __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
-  static_assert(NB == 1 || (NB == 2 && E == kElemF32 && (N == kTc2BlockQ || N == 64)),
-                "two query blocks: FP32 rows, 48 or 64 queries each");
+  static_assert(NB == 1 || (NB == 2 && E == kElemF32 && (N == kTc2BlockQ || N == 64)) ||
+                    (NB == kBf16Blocks && E == kElemBF16 && N == 64),
+                "several query blocks: FP32 rows, two of 48 or 64 queries; BF16 rows, four of 64");
   static_assert(NB == 1 || NB == tc_epi_sets(E, N, NB), "with several query blocks each epilogue set takes one");
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ unsigned char smem_raw[];
@@ -201,8 +203,8 @@ __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
   // epilogue sets read it), as many as fit next to two x_hi/x_lo buffers:
   // two of 192 columns for 48-query blocks (the MMAs of a tile overlap the
   // tests of the one before), one of 256 for 64-query blocks
-  constexpr int kAccW = NB > 1 ? 2 * NB * N : tc_acc_w(E, N);
-  constexpr int kAcc = NB > 1 ? (512 - 2 * 64) / kAccW : tc_acc_bufs(E, N);
+  constexpr int kAccW = NB > 1 ? (E == kElemF32 ? 2 : 1) * NB * N : tc_acc_w(E, N);
+  constexpr int kAcc = NB > 1 ? (E == kElemF32 ? 512 - 2 * 64 : 512) / kAccW : tc_acc_bufs(E, N);
   constexpr int kABufs = E != kElemF32 ? 2 : NB > 1 ? (512 - kAcc * kAccW) / 64 : tc_abufs(E, N);  // (unused for BF16 / e4m3)
   static_assert(E != kElemF32 || (kAcc * kAccW + 64 * kABufs <= 512 && kABufs >= 2 && kABufs % 2 == 0),
                 "tensor memory: accumulators and an even number of x_hi/x_lo buffers");
@@ -286,23 +288,25 @@ __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
           (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
     }
   } else if constexpr (E == kElemBF16) {
-    // per 64-value chunk c: rows 0..N-1 of a 2N-row block of 128-byte rows,
-    // 16-byte unit j of row r at unit j ^ (r % 8)
+    // per 64-value chunk c: rows 0..NB N - 1 (every block's queries) of a
+    // block of 128-byte rows (2N rows for one block), 16-byte unit j of row r
+    // at unit j ^ (r % 8)
+    constexpr int kQRows = NB * N;
     uint16_t *qb = reinterpret_cast<uint16_t *>(qop);
-    for (int i0 = 0; i0 < C * N * 64; i0 += kQu * kThreads) {
+    for (int i0 = 0; i0 < C * kQRows * 64; i0 += kQu * kThreads) {
       float v[kQu];
 #pragma unroll
       for (int u = 0; u < kQu; ++u) {
         const int i = i0 + u * kThreads + threadIdx.x;
-        const int c = i / (N * 64), rem = i % (N * 64), r = rem / 64, k = rem % 64;
-        v[u] = i < C * N * 64 && r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 64 + k] : 0.f;
+        const int c = i / (kQRows * 64), rem = i % (kQRows * 64), r = rem / 64, k = rem % 64;
+        v[u] = i < C * kQRows * 64 && r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 64 + k] : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < kQu; ++u) {
         const int i = i0 + u * kThreads + threadIdx.x;
-        if (i >= C * N * 64) break;
-        const int c = i / (N * 64), rem = i % (N * 64), r = rem / 64, k = rem % 64;
-        const size_t base = (size_t)c * 2 * N * 128;
+        if (i >= C * kQRows * 64) break;
+        const int c = i / (kQRows * 64), rem = i % (kQRows * 64), r = rem / 64, k = rem % 64;
+        const size_t base = (size_t)c * (NB > 1 ? kQRows : 2 * N) * 128;
         qb[(base + (size_t)r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2) / 2] =
             __bfloat16_as_ushort(__float2bfloat16_rn(v[u]));
       }
@@ -467,9 +471,10 @@ __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
               break;
             }
             tc_fence_after();
-            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, N);  // the q_hi rows
+            // every block's queries in one MMA (N = NB N: 256 columns with four blocks)
+            constexpr uint32_t idesc_b = idesc_bf16(kTileRows, NB * N);
             const uint32_t xa = smem_u32(raw + (size_t)s * kChunkBytes);
-            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * 2 * N * 128);
+            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * (NB > 1 ? NB * N : 2 * N) * 128);
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
               mma_bf16(d, sw128_desc(xa + (uint32_t)ks * 32u), sw128_desc(qa + (uint32_t)ks * 32u), idesc_b,
@@ -631,8 +636,10 @@ __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
     // ids two ahead, so no global load latency sits on the tile's path
     const int lr = quarter * 32 + lane;
     const RowMask<N> *msg = static_cast<const RowMask<N> *>(a.tile_msg) + lr;
-    // two query blocks: the second block's row masks come from their own array
-    const RowMask<N> *msg2 = NB > 1 ? static_cast<const RowMask<N> *>(a.tile_msg2) + lr : msg;
+    // blocks 1 .. NB - 1: their row masks in tile_msg2, msg_block_stride words apart
+    const RowMask<N> *msg2 =
+        NB > 1 ? static_cast<const RowMask<N> *>(a.tile_msg2) + (size_t)(bq > 0 ? bq - 1 : 0) * a.msg_block_stride + lr
+               : msg;
     auto tile_of = [&](int64_t k) -> int32_t { return k < n_mine ? tile_id(k) : -1; };
     auto mask_of = [&](int32_t t, int64_t k, int bq) -> RowMask<N> {
       return k < n_mine && t >= 0 ? (bq == 0 ? msg : msg2)[(size_t)t * kTileRows] : (RowMask<N>)0;
@@ -858,14 +865,17 @@ cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cuda
 }
 
 cudaError_t launch_scan_tc2(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s) {
-  // FP32 rows, d <= 128 (the query operand of both blocks fills 96 or 128 KB),
-  // block_q + 1 .. 2 block_q queries as two blocks of block_q (48 or 64), the
-  // main scan only
+  // the main scan only, d <= 128 (the query operand of every block in shared
+  // memory): FP32 rows, block_q + 1 .. 2 block_q queries as two blocks of
+  // block_q (48 or 64); BF16 rows, 65 .. 256 queries as four blocks of 64
   const int bq = a.block_q;
-  if (a.elem != kElemF32 || a.d_pad > 128 || (bq != kTc2BlockQ && bq != 64) || a.nq <= bq || a.nq > 2 * bq ||
-      !a.dense_tiles || a.tile_msg2 == nullptr || a.mode != kCollect || a.tau == nullptr)
+  const int nb = a.elem == kElemF32 ? 2 : kBf16Blocks;
+  if ((a.elem != kElemF32 && a.elem != kElemBF16) || a.d_pad > 128 || a.nq <= bq || a.nq > nb * bq ||
+      (a.elem == kElemF32 && bq != kTc2BlockQ && bq != 64) || (a.elem == kElemBF16 && bq != 64) || !a.dense_tiles ||
+      a.tile_msg2 == nullptr || a.mode != kCollect || a.tau == nullptr)
     return cudaErrorInvalidValue;
   const CUtensorMap &tm = *static_cast<const CUtensorMap *>(tmap_x);
+  if (a.elem == kElemBF16) return launch_tc<64, kElemBF16, kBf16Blocks>(a, tm, grid, s);
   return bq == 64 ? launch_tc<64, kElemF32, 2>(a, tm, grid, s) : launch_tc<kTc2BlockQ, kElemF32, 2>(a, tm, grid, s);
 }
 

@@ -171,3 +171,37 @@ def test_precision_k1000_oversample4(lr, corpus, dtype, plan):
     rec = oracle.recall_at_k([ids[b, :cnt[b]] for b in range(B)], [ref.ids[b, :ref.count[b]] for b in range(B)])
     assert rec >= 0.999, "recall@%d = %.5f" % (K, rec)
     check_topk(ids, sc, cnt, ref, X, Q, c.job_off, c.job_terms, f, metric="cosine")
+
+
+@pytest.mark.parametrize("B", [100, 200, 256, 300])
+def test_precision_bf16_four_block_launches(lr, corpus, B):
+    """BF16 rows above 64 queries: up to four consecutive 64-query sub-batches share one scan launch
+    whose MMA covers all of them (N = 256; dense row masks, every tile visited); 100 and 200 queries
+    make partial groups (2 and 4 sub-batches, the last partial), 300 a group of four and a single
+    sub-batch.  Recall against the FP64 oracle, the plain path's score checks, no exact fallback for
+    any query, and rows identical to the same queries searched alone."""
+    c = corpus
+    po, pid = c.postings()
+    K = 100
+    f = datagen.filters(61 + B, B, c.V, 1.1)
+    qs = [f.clauses(b) for b in range(B)]
+    qs[3] = []            # unfiltered queries in blocks 0 and 2
+    qs[130 % B] = []
+    f = Filters.from_lists(qs)
+    Q = datagen.query_embeddings(62 + B, B, c.d)
+    idx = lr.lr_index_create(c.X, c.V, post_off=po, post_ids=pid, n_dense_terms=128, metric="cosine",
+                             max_batch=320, max_k=128, dtype="bf16", oversample=4, max_sparse_terms=2048)
+    try:
+        ids, sc, cnt, st = _run(lr, idx, Q, f, K, plan="tc", stats=True)
+        assert not np.asarray(st["fallback"]).any(), np.flatnonzero(np.asarray(st["fallback"]))
+        for b in (0, 63, 64, 127, 128, 191, 192, B - 1):
+            if b >= B:
+                continue
+            a_ids, a_sc, a_cnt = _run(lr, idx, Q[b:b + 1], f.subset([b]), K, plan="tc")
+            assert a_cnt[0] == cnt[b] and np.array_equal(a_ids[0], ids[b]) and np.array_equal(a_sc[0], sc[b]), b
+    finally:
+        lr.lr_index_destroy(idx)
+    ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
+    rec = oracle.recall_at_k([ids[b, :cnt[b]] for b in range(B)], [ref.ids[b, :ref.count[b]] for b in range(B)])
+    assert rec >= 0.999, "recall@%d = %.5f" % (K, rec)
+    check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
