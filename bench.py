@@ -271,7 +271,7 @@ def peaks():
 def scan_plan(args):
     """The scan kernel a search ran and the queries one launch of it serves (tensor-core tiles: 64 per
     launch at d <= 128 and 32 above; FP32 rows at d <= 128 in batches above 64: 128 (two 64-query
-    blocks per launch), 96 above 128 queries (two 48-query blocks); BF16 rows above 64 queries: 256 (four
+    blocks per launch), 96 above 128 queries (two 48-query blocks); BF16 / e4m3 rows above 64 queries: 256 (four
     64-query blocks in one N = 256 MMA); SIMT matrix-vector scan: 8 per launch).  The plan is the one the
     library reported for the timed steps (args.plan_used); before that, the requested plan, with "auto"
     read as the batch-size rule."""
@@ -283,7 +283,7 @@ def scan_plan(args):
     if plan == "tc":
         if args.dtype == "f32" and d_pad <= 128 and args.batch > 64:
             return "k_scan_tc", (96 if args.batch > 128 else 128), d_pad
-        if args.dtype == "bf16" and d_pad <= 128 and args.batch > 64:
+        if args.dtype in ("bf16", "fp8") and d_pad <= 128 and args.batch > 64:
             return "k_scan_tc", 256, d_pad
         return "k_scan_tc", (64 if d_pad <= 128 else 32), d_pad
     return "k_scan_gemv", 8, d_pad

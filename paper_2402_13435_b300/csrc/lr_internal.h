@@ -24,7 +24,7 @@ constexpr int kGemvMaxSlots = 256;  // distinct terms per scan launch (shared-me
 constexpr int kTcMaxQ = 64;         // queries per tensor-core launch (MMA N <= 64)
 constexpr int kTc2BlockQ = 48;      // FP32 rows, batches above kTc2MinBatch: queries per block of a two-block launch
 constexpr int kTc2MinBatch = 128;   // up to it (and above 64) the two blocks hold 64 queries each
-constexpr int kBf16Blocks = 4;      // BF16 rows above 64 queries: 64-query blocks per launch (one N = 256 MMA)
+constexpr int kBf16Blocks = 4;      // BF16 / e4m3 rows above 64 queries: 64-query blocks per launch (one N = 256 MMA)
 constexpr int kTcMinBatch = 16;     // batches from this size use the tensor-core plan by default
 constexpr int kFbBits = 11;         // radix digit of the exact fallback selection
 constexpr int kFbBins = 1 << kFbBits;
@@ -190,8 +190,9 @@ cudaError_t launch_tile_filter(const ScanArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 // The same scan for several query blocks per tile (d <= 128, dense tile masks
 // in tile_msg for block 0 and tile_msg2 + (b - 1) msg_block_stride for block b):
-// FP32 rows, two blocks of a.block_q (48 or 64) per converted tile; BF16 rows,
-// four blocks of 64 in one N = 256 MMA.  The index is read once per launch.
+// FP32 rows, two blocks of a.block_q (48 or 64) per converted tile; BF16 and
+// e4m3 rows, four blocks of 64 in one N = 256 MMA.  The index is read once per
+// launch.
 cudaError_t launch_scan_tc2(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s);
 

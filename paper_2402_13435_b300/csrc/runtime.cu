@@ -397,8 +397,7 @@ lr_status alloc_search_workspace(lr_index *ix, cudaStream_t s) {
   // row masks per block after the first)
   const int extra_blocks = ix->d_pad > 128 || B <= kTcMaxQ ? 0
                            : ix->elem == kElemF32    ? 1
-                           : ix->elem == kElemBF16   ? kBf16Blocks - 1
-                                                     : 0;
+                                                     : kBf16Blocks - 1;
   const size_t o_tmsg2 = cv.take<uint64_t>((size_t)extra_blocks * ix->tile_cap * 128);
   ix->tile_cap_s = 2 * (ix->samp_cap / kGroupRows + 2);  // the sampled groups' tiles (sample rows <= samp_cap)
   const size_t o_trow_s = cv.take<int32_t>((size_t)ix->tile_cap_s);
@@ -1440,12 +1439,11 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
                                     "low-precision rows need dim > 32)");
   // Above 64 queries consecutive sub-batches share several-block scans: FP32
   // rows two blocks, of 64 up to 128 queries and of 48 above (two
-  // accumulators: fewer launches than blocks of 64 from there on); BF16 rows
-  // up to four blocks of 64
-  const bool pairs = plan == LR_PLAN_TC && ix->tile_msg2 != nullptr && B > kTcMaxQ &&
-                     (ix->elem == kElemF32 || ix->elem == kElemBF16);
+  // accumulators: fewer launches than blocks of 64 from there on); BF16 and
+  // e4m3 rows up to four blocks of 64
+  const bool pairs = plan == LR_PLAN_TC && ix->tile_msg2 != nullptr && B > kTcMaxQ;
   const int block_q = ix->elem == kElemF32 && B > kTc2MinBatch ? kTc2BlockQ : kTcMaxQ;
-  const int group_max = ix->elem == kElemBF16 ? kBf16Blocks : 2;
+  const int group_max = ix->elem == kElemF32 ? 2 : kBf16Blocks;
   const int max_q = plan == LR_PLAN_TC ? (pairs ? block_q : ix->d_pad <= 128 ? kTcMaxQ : kTcMaxQ / 2) : kGemvMaxQ;
   lr_status st = compile_filters(ix, f, B, max_q, stage, C);
   if (st != LR_OK) return st;

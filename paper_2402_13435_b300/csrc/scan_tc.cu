@@ -180,8 +180,8 @@ template <int N, int E, int NB>
 __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
   static_assert(NB == 1 || (NB == 2 && E == kElemF32 && (N == kTc2BlockQ || N == 64)) ||
-                    (NB == kBf16Blocks && E == kElemBF16 && N == 64),
-                "several query blocks: FP32 rows, two of 48 or 64 queries; BF16 rows, four of 64");
+                    (NB == kBf16Blocks && E != kElemF32 && N == 64),
+                "several query blocks: FP32 rows, two of 48 or 64 queries; BF16 / e4m3 rows, four of 64");
   static_assert(NB == 1 || NB == tc_epi_sets(E, N, NB), "with several query blocks each epilogue set takes one");
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ unsigned char smem_raw[];
@@ -281,10 +281,11 @@ __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
     __syncthreads();
     const float qs = s_qmax[0];
     unsigned char *q8 = reinterpret_cast<unsigned char *>(qop);
-    for (int i = threadIdx.x; i < C * N * 64; i += kThreads) {
-      const int c = i / (N * 64), rem = i % (N * 64), r = rem / 64, k = rem % 64;
+    constexpr int kQRows = NB * N;  // every block's queries
+    for (int i = threadIdx.x; i < C * kQRows * 64; i += kThreads) {
+      const int c = i / (kQRows * 64), rem = i % (kQRows * 64), r = rem / 64, k = rem % 64;
       const float v = r < a.nq ? a.Q[(size_t)(a.q_base + r) * a.d_pad + c * 64 + k] * qs : 0.f;
-      q8[(size_t)c * N * 64 + (size_t)r * 64 + ((((k >> 4) ^ (r >> 1)) & 3) << 4) + (k & 15)] =
+      q8[(size_t)c * kQRows * 64 + (size_t)r * 64 + ((((k >> 4) ^ (r >> 1)) & 3) << 4) + (k & 15)] =
           (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
     }
   } else if constexpr (E == kElemBF16) {
@@ -449,9 +450,9 @@ __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
               break;
             }
             tc_fence_after();
-            constexpr uint32_t idesc8 = idesc_e4m3(kTileRows, N);
+            constexpr uint32_t idesc8 = idesc_e4m3(kTileRows, NB * N);  // every block's queries
             const uint32_t xa = smem_u32(raw + (size_t)s * kChunkBytes);
-            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * N * 64);
+            const uint32_t qa = smem_u32(qop) + (uint32_t)(c * NB * N * 64);
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks)
               mma_e4m3(d, sw64_desc(xa + (uint32_t)ks * 32u), sw64_desc(qa + (uint32_t)ks * 32u), idesc8,
@@ -867,15 +868,16 @@ cudaError_t launch_scan_tc(const ScanArgs &a, const void *tmap_x, int grid, cuda
 cudaError_t launch_scan_tc2(const ScanArgs &a, const void *tmap_x, int grid, cudaStream_t s) {
   // the main scan only, d <= 128 (the query operand of every block in shared
   // memory): FP32 rows, block_q + 1 .. 2 block_q queries as two blocks of
-  // block_q (48 or 64); BF16 rows, 65 .. 256 queries as four blocks of 64
+  // block_q (48 or 64); BF16 and e4m3 rows, 65 .. 256 queries as four blocks of 64
   const int bq = a.block_q;
   const int nb = a.elem == kElemF32 ? 2 : kBf16Blocks;
-  if ((a.elem != kElemF32 && a.elem != kElemBF16) || a.d_pad > 128 || a.nq <= bq || a.nq > nb * bq ||
-      (a.elem == kElemF32 && bq != kTc2BlockQ && bq != 64) || (a.elem == kElemBF16 && bq != 64) || !a.dense_tiles ||
-      a.tile_msg2 == nullptr || a.mode != kCollect || a.tau == nullptr)
+  if (a.d_pad > 128 || a.nq <= bq || a.nq > nb * bq || (a.elem == kElemF32 && bq != kTc2BlockQ && bq != 64) ||
+      (a.elem != kElemF32 && bq != 64) || !a.dense_tiles || a.tile_msg2 == nullptr || a.mode != kCollect ||
+      a.tau == nullptr)
     return cudaErrorInvalidValue;
   const CUtensorMap &tm = *static_cast<const CUtensorMap *>(tmap_x);
   if (a.elem == kElemBF16) return launch_tc<64, kElemBF16, kBf16Blocks>(a, tm, grid, s);
+  if (a.elem == kElemFP8) return launch_tc<64, kElemFP8, kBf16Blocks>(a, tm, grid, s);
   return bq == 64 ? launch_tc<64, kElemF32, 2>(a, tm, grid, s) : launch_tc<kTc2BlockQ, kElemF32, 2>(a, tm, grid, s);
 }
 

@@ -173,12 +173,13 @@ def test_precision_k1000_oversample4(lr, corpus, dtype, plan):
     check_topk(ids, sc, cnt, ref, X, Q, c.job_off, c.job_terms, f, metric="cosine")
 
 
-@pytest.mark.parametrize("B", [100, 200, 256, 300])
-def test_precision_bf16_four_block_launches(lr, corpus, B):
-    """BF16 rows above 64 queries: up to four consecutive 64-query sub-batches share one scan launch
+@pytest.mark.parametrize("dtype,B", [("bf16", 100), ("bf16", 200), ("bf16", 256), ("bf16", 300), ("fp8", 150),
+                                     ("fp8", 256)])
+def test_precision_four_block_launches(lr, corpus, dtype, B):
+    """BF16 / e4m3 rows above 64 queries: up to four consecutive 64-query sub-batches share one scan launch
     whose MMA covers all of them (N = 256; dense row masks, every tile visited); 100 and 200 queries
     make partial groups (2 and 4 sub-batches, the last partial), 300 a group of four and a single
-    sub-batch.  Recall against the FP64 oracle, the plain path's score checks, no exact fallback for
+    sub-batch (e4m3: one power-of-two query scale for the whole launch).  Recall against the FP64 oracle, the plain path's score checks, no exact fallback for
     any query, and rows identical to the same queries searched alone."""
     c = corpus
     po, pid = c.postings()
@@ -190,7 +191,7 @@ def test_precision_bf16_four_block_launches(lr, corpus, B):
     f = Filters.from_lists(qs)
     Q = datagen.query_embeddings(62 + B, B, c.d)
     idx = lr.lr_index_create(c.X, c.V, post_off=po, post_ids=pid, n_dense_terms=128, metric="cosine",
-                             max_batch=320, max_k=128, dtype="bf16", oversample=4, max_sparse_terms=2048)
+                             max_batch=320, max_k=128, dtype=dtype, oversample=4, max_sparse_terms=2048)
     try:
         ids, sc, cnt, st = _run(lr, idx, Q, f, K, plan="tc", stats=True)
         assert not np.asarray(st["fallback"]).any(), np.flatnonzero(np.asarray(st["fallback"]))
