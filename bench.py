@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--tau", type=float, default=0.05)
     p.add_argument("--rates", default="100,300,5000,10000,20000,50000")
     p.add_argument("--slots", type=int, default=3)
+    p.add_argument("--chunks", type=int, default=0, help="serve form: >= 2 runs the rotating scan over that many "
+                                                          "row chunks (one slot of 256 lanes)")
     p.add_argument("--max-requests", type=int, default=2000)
     p.add_argument("--clients", type=int, default=4, help="serve form: client threads submitting the stream")
     a = p.parse_args()
@@ -678,7 +680,7 @@ def run_serve(args):
         fl = [pool[int(j)] for j in rng.integers(0, len(pool), size=Bq)]
         reqs.append((Qpool[rows], datagen.Filters.from_lists(fl), K))
     loads = []
-    with lr.Server(idx, slots=args.slots, max_queries=256, plan=args.plan) as srv:
+    with lr.Server(idx, slots=args.slots, max_queries=256, plan=args.plan, chunks=args.chunks) as srv:
         srv.wait(srv.submit(*reqs[0]), reqs[0][0].shape[0], reqs[0][2])  # warm up
         for rate in [float(r) for r in args.rates.split(",")]:
             srv.stats(reset=True)
@@ -716,6 +718,8 @@ def run_serve(args):
             loads.append({"offered_rps": rate, "submitted_rps": nreq / t_sub, "achieved_rps": nreq / t_all,
                           "achieved_qps": st["queries"] / t_all, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                           "mean_batch_queries": st["queries"] / max(st["batches"], 1), "batches": st["batches"]})
+            if args.chunks >= 2:  # batches are scan steps: queries per step = active lanes
+                loads[-1]["mean_batch_queries"] = st["queries"] * args.chunks / max(st["batches"], 1)
         slots = srv.stats()["slots"]
     best = max(l["achieved_qps"] for l in loads)
     out = {"metric": "serving QPS with p50/p99 latency per offered request rate", "value": best,
@@ -723,9 +727,11 @@ def run_serve(args):
            "data": "synthetic (seeded generator)",
            "config": {"workload": "resident N=%d x d=%d %s index (oversample %d), Poisson requests of 1-64 queries, "
                                   "K in {100,500,1000,2000}, selectivity log-uniform 0.05-50%%; %d requests per load "
-                                  "point from %d client threads, %d slots of 256 queries"
-                                  % (args.n, args.dim, args.dtype, args.oversample, nreq, args.clients, slots),
-                      "n_jobs": args.n, "dim": args.dim, "slots": slots},
+                                  "point from %d client threads, %s"
+                                  % (args.n, args.dim, args.dtype, args.oversample, nreq, args.clients,
+                                     "%d slots of 256 queries" % slots if args.chunks < 2 else
+                                     "rotating scan over %d row chunks, 256 lanes" % args.chunks),
+                      "n_jobs": args.n, "dim": args.dim, "slots": slots, "chunks": max(args.chunks, 1)},
            "loads": loads, "setup_s": {"generate": round(gen_s, 1)}}
     print(json.dumps(out), flush=True)
 

@@ -186,6 +186,15 @@ typedef struct lr_search_opts {
                              level higher if that would exceed 2 * max_quant_k);
                              the result is the exact top K of the kept jobs.  F32
                              indexes only.                                        */
+  int32_t reserved;       /* 0                                                        */
+  int64_t row_begin;      /* search only job rows [row_begin, row_end) (both 0: every */
+  int64_t row_end;        /* row); row_begin a multiple of 256, row_end a multiple of
+                             256 or n; ids stay the index's row ids (+ id_base).  The
+                             exact top K of the range: its rows are a chunk of the
+                             index for a scan that covers the index in steps (the
+                             rotating scan of the serving loop).  Not with
+                             quant_mult or the TBR-first plan (LR_PLAN_AUTO then
+                             chooses a scan).  Invalid ranges: LR_ERR_INVALID.      */
 } lr_search_opts;
 
 /* Per-call statistics and instrumentation (every field optional).  Arrays may be
@@ -450,6 +459,13 @@ typedef struct lr_server_opts {
   int32_t slots;        /* concurrent batches                          */
   int32_t max_queries;  /* queries per batch (a slot's capacity)       */
   int32_t plan;         /* lr_plan used for every batch                */
+  int32_t chunks;       /* <= 1: slots, each batch one whole search;   */
+                        /* C >= 2: the rotating scan -- the index in C */
+                        /* row chunks, each step scans one chunk for   */
+                        /* every active query (one slot of max_queries */
+                        /* lanes); a request joins at the next chunk   */
+                        /* boundary and is done after C steps, its     */
+                        /* chunks' top K merged exactly on the device  */
 } lr_server_opts;
 typedef struct lr_server_stats {
   int64_t submitted, completed, batches, queries;

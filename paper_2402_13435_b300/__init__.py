@@ -57,7 +57,8 @@ class lr_filters(ctypes.Structure):
 
 class lr_search_opts(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_int32), ("sample_stride", ctypes.c_int32), ("cand_cap", ctypes.c_int32),
-                ("force_exact_fallback", ctypes.c_int32), ("quant_mult", ctypes.c_int32)]
+                ("force_exact_fallback", ctypes.c_int32), ("quant_mult", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64)]
 
 
 class lr_search_stats(ctypes.Structure):
@@ -262,13 +263,14 @@ class Probe:
 
 def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out_count=None, plan: str = "auto",
               sample_stride: int = 0, cand_cap: int = 0, force_exact_fallback: bool = False, quant_mult: int = 0,
-              stats: bool = False, probe: Optional[Probe] = None, stream=None):
+              stats: bool = False, probe: Optional[Probe] = None, stream=None, row_range=None):
     """Filtered top-K for the query batch ``q`` [B][dim] FP32 (torch tensor or numpy array, host or device).
 
     ``k`` is an int or a per-query sequence.  Outputs default to new device tensors on q's device
     (host numpy arrays when q is a numpy array).  Returns (ids [B][kmax] int32, scores [B][kmax] FP32,
     count [B] int32) and, with ``stats=True``, a dict of per-query statistics.  ``probe`` collects
-    launch counts and scan-phase CUDA events without a synchronisation.
+    launch counts and scan-phase CUDA events without a synchronisation.  ``row_range`` = (begin, end)
+    restricts the search to job rows [begin, end) (begin a multiple of 256, end a multiple of 256 or n).
     """
     import torch
 
@@ -294,7 +296,8 @@ def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out
             out_scores = torch.empty((B, k_all), dtype=torch.float32, device=q.device)
             out_count = torch.empty(B, dtype=torch.int32, device=q.device)
     opts = lr_search_opts(plan=_PLAN[plan], sample_stride=int(sample_stride), cand_cap=int(cand_cap),
-                          force_exact_fallback=int(bool(force_exact_fallback)), quant_mult=int(quant_mult))
+                          force_exact_fallback=int(bool(force_exact_fallback)), quant_mult=int(quant_mult),
+                          row_begin=int(row_range[0]) if row_range else 0, row_end=int(row_range[1]) if row_range else 0)
     st = None
     st_arrays = None
     if stats:
@@ -611,7 +614,8 @@ def masked_softmax_loss(Q, J, pos, mask_bits=None, inv_tau: float = 20.0):
 
 # ----------------------------------------------------------------------------- serving
 class lr_server_opts(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_int32), ("max_queries", ctypes.c_int32), ("plan", ctypes.c_int32)]
+    _fields_ = [("slots", ctypes.c_int32), ("max_queries", ctypes.c_int32), ("plan", ctypes.c_int32),
+                ("chunks", ctypes.c_int32)]
 
 
 class lr_server_stats(ctypes.Structure):
@@ -638,8 +642,8 @@ class Server:
     wait() blocks for its result.  Thread-safe: several client threads may submit and wait."""
 
     def __init__(self, index: "Index", slots: int = 2, max_queries: int = 64, plan: str = "auto",
-                 arena_bytes: int = 0):
-        o = lr_server_opts(int(slots), int(max_queries), _PLAN[plan])
+                 arena_bytes: int = 0, chunks: int = 0):
+        o = lr_server_opts(int(slots), int(max_queries), _PLAN[plan], int(chunks))
         h = ctypes.c_void_p()
         _check(_lib.lr_server_create(ctypes.c_void_p(index.handle), ctypes.byref(o), int(arena_bytes),
                                      ctypes.byref(h)), "lr_server_create")

@@ -285,6 +285,16 @@ cudaError_t launch_tbr_collect(const TbrArgs &a, int num_sms, int64_t max_postin
 // Exact merge of G per-part top-K lists per query (merge.cu).
 cudaError_t launch_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int G, int B, int k_in,
                               int k, int32_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t s);
+// Rotating scan of the serving loop: merge each batch row's chunk result into
+// the running top-K of its lane (lane_of[b], k_of[b]); reset lanes; gather the
+// rows of finished lanes into a compact block.
+cudaError_t launch_lane_merge(const int32_t *c_ids, const float *c_sc, const int32_t *c_cnt, int B, int c_stride,
+                              const int32_t *lane_of, const int32_t *k_of, int32_t *run_ids, float *run_sc,
+                              int32_t *run_cnt, int run_stride, cudaStream_t s);
+cudaError_t launch_lane_reset(const int32_t *lanes, int n, int32_t *run_cnt, cudaStream_t s);
+cudaError_t launch_lane_gather(const int32_t *lanes, int n, const int32_t *run_ids, const float *run_sc,
+                               const int32_t *run_cnt, int run_stride, int k_stride, int32_t *out_ids, float *out_sc,
+                               int32_t *out_cnt, cudaStream_t s);
 // Masked softmax loss passes (loss.cu).  Row tiles of 128 over R, streamed
 // 64-row tiles of C; see loss.cu for the three modes.
 struct LossArgs {
@@ -334,6 +344,7 @@ int index_max_batch_terms(const lr_index *ix);
 int index_dim(const lr_index *ix);
 int index_vocab(const lr_index *ix);
 int index_device(const lr_index *ix);
+int64_t index_rows(const lr_index *ix);
 
 cudaError_t launch_quantize_rows(const float *X, int64_t n, int d_pad, int elem, void *Xq, float *scale,
                                  cudaStream_t s);

@@ -93,6 +93,104 @@ cudaError_t launch_merge_topk(const int32_t *ids, const float *scores, const int
   return cudaGetLastError();
 }
 
+namespace {
+
+// Rotating scan: batch row b of a chunk's result (c_cnt[b] entries, sorted)
+// merged into the running top-K of its query's lane (run_cnt entries, sorted,
+// from the chunks before; the two hold disjoint rows).  Each entry's rank in
+// the union is its index plus the entries of the other list above it; the
+// first k_of[b] are staged in shared memory and written back to the lane.
+__global__ void __launch_bounds__(kMergeThreads) k_lane_merge(const int32_t *c_ids, const float *c_sc,
+                                                              const int32_t *c_cnt, int c_stride,
+                                                              const int32_t *lane_of, const int32_t *k_of,
+                                                              int32_t *run_ids, float *run_sc, int32_t *run_cnt,
+                                                              int run_stride) {
+  extern __shared__ __align__(16) unsigned char lm_smem[];
+  const int b = blockIdx.x;
+  const int lane = lane_of[b];
+  const int k = k_of[b];
+  int32_t *oi = reinterpret_cast<int32_t *>(lm_smem);
+  float *os = reinterpret_cast<float *>(lm_smem) + run_stride;
+  const int32_t *ci = c_ids + (size_t)b * c_stride;
+  const float *cs = c_sc + (size_t)b * c_stride;
+  int32_t *ri = run_ids + (size_t)lane * run_stride;
+  float *rs = run_sc + (size_t)lane * run_stride;
+  const int nc = min(min(c_cnt[b], c_stride), k), nr = min(run_cnt[lane], k);
+  const int kout = min(nc + nr, k);
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    const int rank = i + count_above(ci, cs, nc, list_key(ri, rs, i));
+    if (rank < kout) {
+      oi[rank] = ri[i];
+      os[rank] = rs[i];
+    }
+  }
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const int rank = i + count_above(ri, rs, nr, list_key(ci, cs, i));
+    if (rank < kout) {
+      oi[rank] = ci[i];
+      os[rank] = cs[i];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kout; i += blockDim.x) {
+    ri[i] = oi[i];
+    rs[i] = os[i];
+  }
+  if (threadIdx.x == 0) run_cnt[lane] = kout;
+}
+
+__global__ void k_lane_reset(const int32_t *lanes, int n, int32_t *run_cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) run_cnt[lanes[i]] = 0;
+}
+
+// Rows of finished lanes into a compact [n][k_stride] result block (-1 / -inf
+// past each lane's count).
+__global__ void __launch_bounds__(kMergeThreads) k_lane_gather(const int32_t *lanes, const int32_t *run_ids,
+                                                               const float *run_sc, const int32_t *run_cnt,
+                                                               int run_stride, int k_stride, int32_t *out_ids,
+                                                               float *out_sc, int32_t *out_cnt) {
+  const int j = blockIdx.x;
+  const int lane = lanes[j];
+  const int c = min(run_cnt[lane], k_stride);
+  for (int i = threadIdx.x; i < k_stride; i += blockDim.x) {
+    out_ids[(size_t)j * k_stride + i] = i < c ? run_ids[(size_t)lane * run_stride + i] : -1;
+    out_sc[(size_t)j * k_stride + i] = i < c ? run_sc[(size_t)lane * run_stride + i] : -INFINITY;
+  }
+  if (threadIdx.x == 0) out_cnt[j] = c;
+}
+
+}  // namespace
+
+cudaError_t launch_lane_merge(const int32_t *c_ids, const float *c_sc, const int32_t *c_cnt, int B, int c_stride,
+                              const int32_t *lane_of, const int32_t *k_of, int32_t *run_ids, float *run_sc,
+                              int32_t *run_cnt, int run_stride, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const size_t smem = (size_t)run_stride * 8;
+  if (smem > 48u * 1024u) {
+    const cudaError_t e = allow_dynamic_smem((const void *)k_lane_merge, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_lane_merge<<<B, kMergeThreads, smem, s>>>(c_ids, c_sc, c_cnt, c_stride, lane_of, k_of, run_ids, run_sc, run_cnt,
+                                              run_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lane_reset(const int32_t *lanes, int n, int32_t *run_cnt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_lane_reset<<<(n + 255) / 256, 256, 0, s>>>(lanes, n, run_cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lane_gather(const int32_t *lanes, int n, const int32_t *run_ids, const float *run_sc,
+                               const int32_t *run_cnt, int run_stride, int k_stride, int32_t *out_ids, float *out_sc,
+                               int32_t *out_cnt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_lane_gather<<<n, kMergeThreads, 0, s>>>(lanes, run_ids, run_sc, run_cnt, run_stride, k_stride, out_ids, out_sc,
+                                            out_cnt);
+  return cudaGetLastError();
+}
+
 }  // namespace lr
 
 using namespace lr;

@@ -290,12 +290,14 @@ struct SamplePlan {
   double frac = 1.0;
 };
 
-SamplePlan make_sample_plan(const lr_index *ix, int stride) {
+// Groups [g0, g1) of the index (a search of a row range samples that range).
+SamplePlan make_sample_plan(const lr_index *ix, int stride, int64_t g0 = 0, int64_t g1 = -1) {
   SamplePlan p;
+  if (g1 < 0) g1 = ix->n_groups;
   if (stride <= 0) return p;
   p.stride = stride;
-  const int64_t begin = stride / 2;
-  p.sampled_groups = ix->n_groups > begin ? (ix->n_groups - begin + stride - 1) / stride : 0;
+  const int64_t begin = g0 + stride / 2;
+  p.sampled_groups = g1 > begin ? (g1 - begin + stride - 1) / stride : 0;
   int64_t rows = 0;
   if (p.sampled_groups > 0) {
     // every sampled group is full except possibly the last group of the index
@@ -303,7 +305,8 @@ SamplePlan make_sample_plan(const lr_index *ix, int stride) {
     rows = (p.sampled_groups - 1) * kGroupRows + std::min<int64_t>(kGroupRows, ix->n - last * kGroupRows);
   }
   p.sampled_rows = rows;
-  p.frac = ix->n > 0 ? (double)rows / (double)ix->n : 1.0;
+  const int64_t range_rows = std::min<int64_t>(ix->n, g1 * kGroupRows) - g0 * kGroupRows;
+  p.frac = range_rows > 0 ? (double)rows / (double)range_rows : 1.0;
   return p;
 }
 
@@ -534,11 +537,12 @@ int index_max_batch_terms(const lr_index *ix) { return ix->max_batch_terms; }
 int index_dim(const lr_index *ix) { return ix->dim; }
 int index_vocab(const lr_index *ix) { return ix->vocab; }
 int index_device(const lr_index *ix) { return ix->device; }
+int64_t index_rows(const lr_index *ix) { return ix->n; }
 }  // namespace lr
 
 extern "C" {
 
-int32_t lr_version(void) { return 200; }
+int32_t lr_version(void) { return 201; }
 
 const char *lr_last_error_message(void) { return g_last_error.c_str(); }
 
@@ -1402,6 +1406,21 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (k_all > ix->max_k && k == nullptr) return fail(LR_ERR_INVALID, "K exceeds max_k");
   lr_search_opts o{};
   if (opts) o = *opts;
+  // row range: groups [g0, g1) of the index
+  const bool ranged = o.row_begin != 0 || o.row_end != 0;
+  int64_t g0 = 0, g1 = ix->n_groups, range_rows = ix->n;
+  if (ranged) {
+    if (o.row_begin < 0 || o.row_end > ix->n || o.row_begin >= o.row_end || o.row_begin % kGroupRows != 0 ||
+        (o.row_end % kGroupRows != 0 && o.row_end != ix->n))
+      return fail(LR_ERR_INVALID, "row range: need 0 <= row_begin < row_end <= n, row_begin a multiple of 256 and "
+                                  "row_end a multiple of 256 or n");
+    if (o.quant_mult != 0 || o.plan == LR_PLAN_TBR)
+      return fail(LR_ERR_UNSUPPORTED, "row range: not with sign pre-selection or the TBR-first plan");
+    g0 = o.row_begin / kGroupRows;
+    g1 = (o.row_end + kGroupRows - 1) / kGroupRows;
+    range_rows = o.row_end - o.row_begin;
+  }
+  const int64_t range_groups = g1 - g0;
   if (o.quant_mult != 0) return run_sign_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, o, stats, s);
 
   // pick and wait for a staging buffer
@@ -1421,7 +1440,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   const bool have_est = estimate_pass_rates(ix, f, B, est);
   // the automatic plan considers TBR first only when no scan option is forced
   const bool scan_opts = o.sample_stride != 0 || o.cand_cap != 0 || o.force_exact_fallback != 0;
-  if (plan == LR_PLAN_TBR || (plan == LR_PLAN_AUTO && have_est && !scan_opts)) {
+  if (plan == LR_PLAN_TBR || (plan == LR_PLAN_AUTO && have_est && !scan_opts && !ranged)) {
     // the candidate buffer holds max_batch x cand_cap keys: a batch of B
     // queries gives each query an equal share of it for its messenger list
     int64_t tcap = ix->cand_cap * (int64_t)ix->max_batch / B;
@@ -1462,7 +1481,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   int stride = ix->auto_stride;
   if (o.sample_stride > 0) stride = o.sample_stride;
   if (o.sample_stride < 0) stride = 0;
-  const SamplePlan sp = make_sample_plan(ix, stride);
+  const SamplePlan sp = make_sample_plan(ix, stride, g0, g1);
   if (sp.stride > 0 && sp.sampled_rows > ix->samp_cap)
     return fail(LR_ERR_WORKSPACE, "sample stride too small for the sample workspace");
   int32_t *rk = (int32_t *)(stage + C.off_rank);
@@ -1477,7 +1496,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   const double direct = (double)std::min<int64_t>(cap, kThrScratchKeys);
   bool need_sample = false;
   for (int b = 0; b < B; ++b) {
-    const bool small = o.sample_stride == 0 && have_est && est[b] * (double)ix->n * 4.0 < direct;
+    const bool small = o.sample_stride == 0 && have_est && est[b] * (double)range_rows * 4.0 < direct;
     rk[b] = small ? 0 : sample_rank(sp, ks[b]);
     need_sample |= rk[b] > 0;
   }
@@ -1522,8 +1541,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.cl_slot = (const int32_t *)(ix->filt_d + sb.off_cs);
     a.n_cl = sb.n_cl;
     a.n_tm = sb.n_tm;
-    a.n_groups = ix->n_groups;
-    a.g_begin = 0;
+    a.n_groups = g1;
+    a.g_begin = g0;
     a.g_step = 1;
     a.mode = kCollect;
     a.err = ix->err;
@@ -1583,7 +1602,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   if (sp.stride > 0 && need_sample) {
     for (const SubBatch &sb : C.subs) {
       ScanArgs a = scan_args(sb);
-      a.g_begin = sp.stride / 2;
+      a.g_begin = g0 + sp.stride / 2;
       a.g_step = sp.stride;
       a.tile_row = ix->tile_row_s;  // the sample's own tile list
       a.tile_msg = ix->tile_msg_s;
@@ -1637,12 +1656,12 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       a0.tile_msg2 = ix->tile_msg2;
       a0.msg_block_stride = msg_stride;
       a0.block_q = block_q;
-      LR_LAUNCH(launch_scan_tc2(a0, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(2 * ix->n_groups), s));
+      LR_LAUNCH(launch_scan_tc2(a0, lowp ? &ix->tmap_xq : &ix->tmap_x, grid_for(2 * range_groups), s));
       ++n_scan;
       i += g - 1;
       continue;
     }
-    LR_LAUNCH(launch_scan(main_args(sb), ix->n_groups, !early_filter, reuse_list));
+    LR_LAUNCH(launch_scan(main_args(sb), range_groups, !early_filter, reuse_list));
     ++n_scan;
   }
   if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
@@ -1687,7 +1706,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
       a.tau_out = ix->tau;
       a.active = ix->flag;
       a.any_active = ix->n_flag;
-      LR_LAUNCH(launch_scan(a, ix->n_groups, !reuse_list, reuse_list));
+      LR_LAUNCH(launch_scan(a, range_groups, !reuse_list, reuse_list));
     }
   }
   for (const SubBatch &sb : C.subs) {
@@ -1699,7 +1718,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     a.overflow = ix->ovf;
     a.active = ix->flag;
     a.any_active = ix->n_flag;
-    LR_LAUNCH(launch_scan(a, ix->n_groups, !reuse_list, reuse_list));
+    LR_LAUNCH(launch_scan(a, range_groups, !reuse_list, reuse_list));
   }
   SelectArgs fb = fa;
   fb.cap = ix->cand_cap;

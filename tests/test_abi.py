@@ -49,7 +49,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_binding_loads_and_reports_version(lib_path):
     import paper_2402_13435_b300 as lr
 
-    assert lr.lr_version() == 200
+    assert lr.lr_version() == 201
     assert set(lr.SYMBOLS) <= set(declared_functions())
 
 

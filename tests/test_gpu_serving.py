@@ -140,3 +140,52 @@ def test_serving_k2000(lr):
         ref = oracle.search(c.X, c.job_off, c.job_terms, Q, f, K, metric="cosine")
         check_topk(ids, sc, cnt, ref, c.X, Q, c.job_off, c.job_terms, f)
     lr.lr_index_destroy(idx)
+
+
+@pytest.mark.parametrize("plan,chunks", [("gemv", 3), ("tc", 7)])
+def test_rotating_scan_results_equal_the_request_alone(lr, setup, plan, chunks):
+    """The rotating scan: the index in row chunks, each step one chunk for every active query; 40
+    requests in flight against 32 lanes, so later requests join while earlier ones are mid-rotation
+    and start at whichever chunk comes next.  Every result equals the request searched alone over the
+    whole index with the same plan, bit for bit (the chunks' top K merged exactly)."""
+    c, idx, reqs = setup
+    with lr.Server(idx, max_queries=32, plan=plan, chunks=chunks) as srv:
+        tickets = [srv.submit(Q, f, K) for (Q, f, K) in reqs]
+        outs = [srv.wait(t, Q.shape[0], K) for t, (Q, f, K) in zip(tickets, reqs)]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["queries"] == sum(Q.shape[0] for Q, _, _ in reqs)
+    assert st["slots"] == 1 and st["batches"] >= chunks
+    for (Q, f, K), (ids, sc, cnt, lat) in zip(reqs, outs):
+        ia, sa, ca = lr.lr_search(idx, Q, f, K, plan=plan)
+        assert np.array_equal(cnt, ca) and np.array_equal(ids, ia) and np.array_equal(sc, sa)
+        assert lat > 0.0
+
+
+@pytest.mark.parametrize("plan", ["gemv", "tc"])
+def test_row_range_searches_merge_to_the_full_search(lr, setup, plan):
+    """lr_search_opts row range: each range's rows only (ids inside the range), and the exact merge of
+    a partition of the index into ranges (one ending at n, not a multiple of 256) equals the search
+    of the whole index bit for bit; invalid ranges are rejected."""
+    c, idx, reqs = setup
+    Q, f, _ = reqs[5]
+    K = 50
+    n = c.X.shape[0]
+    bounds = [0, 256 * 40, 256 * 41, 256 * 150, n]
+    parts = []
+    for r0, r1 in zip(bounds[:-1], bounds[1:]):
+        ids, sc, cnt = lr.lr_search(idx, Q, f, K, plan=plan, row_range=(r0, r1))
+        for b in range(Q.shape[0]):
+            assert np.all((ids[b, :cnt[b]] >= r0) & (ids[b, :cnt[b]] < r1))
+        parts.append((ids, sc, cnt))
+    G, B = len(parts), Q.shape[0]
+    ids_d = torch.from_numpy(np.stack([p[0] for p in parts])).cuda()
+    sc_d = torch.from_numpy(np.stack([p[1] for p in parts])).cuda()
+    cnt_d = torch.from_numpy(np.stack([p[2] for p in parts])).cuda()
+    mi, ms, mc = lr.lr_merge_topk(ids_d, sc_d, cnt_d, K)
+    ia, sa, ca = lr.lr_search(idx, Q, f, K, plan=plan)
+    assert np.array_equal(mc.cpu().numpy(), ca) and np.array_equal(mi.cpu().numpy(), ia)
+    assert np.array_equal(ms.cpu().numpy(), sa)
+    for bad in ((100, 1000), (0, n + 1), (512, 512), (1024, 300)):
+        with pytest.raises(lr.LRError) as e:
+            lr.lr_search(idx, Q, f, K, plan=plan, row_range=bad)
+        assert e.value.status == lr.LR_ERR_INVALID
