@@ -93,9 +93,9 @@ constexpr int kChunkBytes = kTileRows * 128;  // one raw stage: a 128-row tile o
 // e4m3 in 64-value (64-byte) blocks.
 __host__ __device__ constexpr int tc_epc(int e) { return e == kElemF32 ? 32 : 64; }
 __host__ __device__ constexpr int tc_row_bytes(int e) { return e == kElemFP8 ? 64 : 128; }
-// candidates staged per epilogue warp (half with two query blocks, whose
+// candidates staged per epilogue warp (half for FP32 two-block launches, whose
 // query operands leave less shared memory)
-__host__ __device__ constexpr int tc_warp_cand(int nb) { return nb > 1 ? 256 : 512; }
+__host__ __device__ constexpr int tc_warp_cand(int nb) { return nb == 2 ? 256 : 512; }
 constexpr int kMaxABufs = 4;                  // x_hi/x_lo chunk buffers in tensor memory, at most
 constexpr uint32_t kTmemCols = 512;           // the whole tensor memory: one CTA per SM
 // Accumulator buffers (2N columns each): four when they fit beside the x_hi/x_lo
@@ -742,19 +742,43 @@ __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
               __syncwarp();
             }
           } else if (__any_sync(0xFFFFFFFFu, hit != 0u)) {
+            if constexpr (NB > 1) {
+              // several-block launches (many candidates per tile): a lane
+              // visits only its own hits (usually one or two), the score of
+              // hit b picked by a branch-free select chain (measured 4-8 %
+              // faster there, 0.7 % slower for one block)
+              constexpr int kPart = kLaneCand >= 16 ? 16 : 8;  // queries per room check
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {  // eight queries at a time: room for all of every lane's hits, else flush first
-              const uint32_t hh = (hit >> (8 * h)) & 0xFFu;
-              if (__any_sync(0xFFFFFFFFu, lcnt + (uint32_t)__popc(hh) > (uint32_t)kLaneCand)) flush();
-              if (hh != 0u) {
+              for (int h = 0; h < 16 / kPart; ++h) {
+                uint32_t hh = kPart == 16 ? hit : (hit >> (8 * h)) & 0xFFu;
+                if (__any_sync(0xFFFFFFFFu, lcnt + (uint32_t)__popc(hh) > (uint32_t)kLaneCand)) flush();
+                while (hh != 0u) {
+                  const int b = kPart * h + __ffs(hh) - 1;
+                  hh &= hh - 1u;
+                  float v = sc[0];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                  if ((hh >> u) & 1u) {
-                    const int b = 8 * h + u;
-                    const uint32_t e = lcnt * 32u + (uint32_t)lane;
-                    ckey[e] = make_key(sc[b], grow);
-                    cqry[e] = (uint8_t)(qoff + 16 * j + b);
-                    ++lcnt;
+                  for (int u = 1; u < 16; ++u) v = b == u ? sc[u] : v;
+                  const uint32_t e = lcnt * 32u + (uint32_t)lane;
+                  ckey[e] = make_key(v, grow);
+                  cqry[e] = (uint8_t)(qoff + 16 * j + b);
+                  ++lcnt;
+                }
+              }
+            } else {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {  // eight queries at a time: room for all of every lane's hits, else flush first
+                const uint32_t hh = (hit >> (8 * h)) & 0xFFu;
+                if (__any_sync(0xFFFFFFFFu, lcnt + (uint32_t)__popc(hh) > (uint32_t)kLaneCand)) flush();
+                if (hh != 0u) {
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) {
+                    if ((hh >> u) & 1u) {
+                      const int b = 8 * h + u;
+                      const uint32_t e = lcnt * 32u + (uint32_t)lane;
+                      ckey[e] = make_key(sc[b], grow);
+                      cqry[e] = (uint8_t)(qoff + 16 * j + b);
+                      ++lcnt;
+                    }
                   }
                 }
               }
