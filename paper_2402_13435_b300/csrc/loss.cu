@@ -38,6 +38,9 @@ constexpr int kLossThreads = 320;  // warps 0-3 and 6-9: two epilogue sets; 4: T
 constexpr int kLossFwdThreads = 192;  // the forward: one epilogue set
 constexpr int kCBufs = 3;          // streamed-tile buffers: a tile loads while the two before it are in use
 constexpr uint32_t kLossTmemCols = 256;  // 2 score tiles of 64 columns + accumulator (<= 128)
+// backward passes at dp = 128: the second product runs transposed (the
+// accumulator is [dp lanes][hi rows | lo rows], 256 columns), so 512 columns
+constexpr uint32_t kLossTmemColsT = 512;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -117,6 +120,14 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   const int T = min(a.c_per_split, a.n_ctiles - t0);  // streamed tiles of this CTA (>= 1 by construction)
   const size_t c_bytes = (size_t)KB * kCRows * 128;
   const size_t ct_bytes = (size_t)dp * 128;
+  // Backward passes with dp = 128: acc^T[k][r | 128 + r] += C^T[k][c] .
+  // [dZ_hi ; dZ_lo][r][c] as ONE MMA of N = 256 per 16-value K step (the
+  // transposed C tile as A, the stacked hi / lo dZ rows as B) instead of two
+  // MMAs of N = 128 with dZ_hi and dZ_lo as A: an MMA costs about the same
+  // whatever its width up to 128 columns, so the product issues half the
+  // instructions.  The write-out adds the two halves.
+  const bool swap = !kOne && dp == 128;
+  const uint32_t tmem_cols = swap ? kLossTmemColsT : kLossTmemCols;
 
   if (threadIdx.x == 0) {
     mbar_init(bar_r, 1);
@@ -134,7 +145,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     fence_mbar_init();
   }
   if (warp == 5) {
-    tmem_alloc(holder, kLossTmemCols);
+    tmem_alloc(holder, tmem_cols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -174,6 +185,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     // ---------------------------------------------------------------- MMA
     if (lane == 0) {
       const uint32_t id_s = idesc_bf16(kRRows, kCRows), id_g = idesc_bf16(kRRows, dp);
+      const uint32_t id_t = idesc_bf16(128, 2 * kRRows);  // the transposed product: M = dp = 128, N = 256
       const uint32_t acc = tmem + 2u * kCRows;
       bool issued = false;
       auto issue_s = [&](int t) -> bool {
@@ -209,11 +221,18 @@ __global__ void __launch_bounds__(kLossThreads, 1)
           const uint32_t dh = smem_u32(sdz + (size_t)(2 * b) * kRRows * 128);
           const uint32_t dl = smem_u32(sdz + (size_t)(2 * b + 1) * kRRows * 128);
           const uint32_t ct = smem_u32(sct + (size_t)(t % kCBufs) * ct_bytes);
+          if (swap) {  // dh and dl are adjacent: 256 rows of one K-major operand
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {  // K = the tile's 64 streamed rows
-            mma_bf16(acc, sw128_desc(dh + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g,
-                     (t | k) != 0 ? 1u : 0u);
-            mma_bf16(acc, sw128_desc(dl + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g, 1u);
+            for (int k = 0; k < 4; ++k)  // K = the tile's 64 streamed rows
+              mma_bf16(acc, sw128_desc(ct + (uint32_t)k * 32u), sw128_desc(dh + (uint32_t)k * 32u), id_t,
+                       (t | k) != 0 ? 1u : 0u);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // K = the tile's 64 streamed rows
+              mma_bf16(acc, sw128_desc(dh + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g,
+                       (t | k) != 0 ? 1u : 0u);
+              mma_bf16(acc, sw128_desc(dl + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g, 1u);
+            }
           }
           mma_commit(&dz_empty[b]);
           mma_commit(&c_empty[t % kCBufs]);
@@ -469,16 +488,36 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       if (!wwait(acc_full, 0u, lane)) ok = false;
       tc_fence_after();
       const uint32_t acc = trow + 2u * kCRows;
-      float *orow = a.out + (size_t)blockIdx.y * a.out_split + (size_t)grow * a.out_ld;
-      const bool wr = ok && (MODE == kDq ? grow < a.rows_p : grow < a.M);
-      for (int c = 0; c < dp; c += 16) {
-        uint32_t v[16];
-        tmem_ld16(acc + (uint32_t)c, v);
-        tmem_ld_wait();
-        if (wr)
+      if (swap) {
+        // lane k (= this thread's TMEM lane) holds column k of every row: rows
+        // r and 128 + r are the hi and lo halves; a warp's 32 lanes write 32
+        // consecutive columns of a row
+        const int k = quarter * 32 + lane;
+        float *ocol = a.out + (size_t)blockIdx.y * a.out_split + k;
+        const int rows_ok = MODE == kDq ? a.rows_p : a.M;
+        for (int rr = 0; rr < kRRows; rr += 16) {
+          uint32_t vh[16], vl[16];
+          tmem_ld16(acc + (uint32_t)rr, vh);
+          tmem_ld16(acc + (uint32_t)(kRRows + rr), vl);
+          tmem_ld_wait();
+          if (ok && k < a.out_cols)
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c + i < a.out_cols) orow[c + i] = __uint_as_float(v[i]) * a.inv_tau;
+            for (int i = 0; i < 16; ++i)
+              if (r0 + rr + i < rows_ok)
+                ocol[(size_t)(r0 + rr + i) * a.out_ld] = (__uint_as_float(vh[i]) + __uint_as_float(vl[i])) * a.inv_tau;
+        }
+      } else {
+        float *orow = a.out + (size_t)blockIdx.y * a.out_split + (size_t)grow * a.out_ld;
+        const bool wr = ok && (MODE == kDq ? grow < a.rows_p : grow < a.M);
+        for (int c = 0; c < dp; c += 16) {
+          uint32_t v[16];
+          tmem_ld16(acc + (uint32_t)c, v);
+          tmem_ld_wait();
+          if (wr)
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (c + i < a.out_cols) orow[c + i] = __uint_as_float(v[i]) * a.inv_tau;
+        }
       }
     }
     if (!ok && lane == 0) atomicOr(a.status, kErrTimeout);
@@ -487,7 +526,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 5) tmem_dealloc(tmem, kLossTmemCols);
+  if (warp == 5) tmem_dealloc(tmem, tmem_cols);
 }
 
 // X [rows][d] (BF16 or FP32) -> P [rows_p][dp] and PT [dp][rows_p], BF16, zero padded.
