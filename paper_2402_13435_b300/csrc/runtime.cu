@@ -1694,31 +1694,34 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.err = ix->err;
   fa.id_base = lowp ? 0 : ix->id_base;  // the precision form's rescore reads rows by local id
   LR_LAUNCH(launch_select(fa, B, s));
-  // 4. exact fallback for flagged queries (each launch returns at once when none is flagged)
-  for (int p = 0; p < kFbPasses; ++p) {
-    for (const SubBatch &sb : C.subs) {
+  // 4. exact fallback for flagged queries (each launch returns at once when none
+  //    is flagged): kFbPasses histogram passes, then the collect, per
+  //    sub-batch; the sub-batch's first pass filters its tiles and the list
+  //    serves the other passes (the collect's scan clears it for the next
+  //    sub-batch; with one sub-batch the main pass's list serves all of them)
+  for (const SubBatch &sb : C.subs) {
+    for (int p = 0; p <= kFbPasses; ++p) {
       ScanArgs a = scan_args(sb);
-      a.mode = kHist;
-      a.hist_pass = p;
-      a.prefix = ix->prefix;
-      a.krem = ix->krem;
-      a.hist = ix->hist;
-      a.tau_out = ix->tau;
       a.active = ix->flag;
       a.any_active = ix->n_flag;
-      LR_LAUNCH(launch_scan(a, range_groups, !reuse_list, reuse_list));
+      if (p < kFbPasses) {
+        a.mode = kHist;
+        a.hist_pass = p;
+        a.prefix = ix->prefix;
+        a.krem = ix->krem;
+        a.hist = ix->hist;
+        a.tau_out = ix->tau;
+      } else {
+        a.tau = ix->tau;
+        a.buf = ix->cand_buf;
+        a.buf_cap = ix->cand_cap;
+        a.buf_cnt = ix->cnt;
+        a.overflow = ix->ovf;
+      }
+      const bool filter = !reuse_list && p == 0;
+      const bool keep = reuse_list || p < kFbPasses;
+      LR_LAUNCH(launch_scan(a, range_groups, filter, keep));
     }
-  }
-  for (const SubBatch &sb : C.subs) {
-    ScanArgs a = scan_args(sb);
-    a.tau = ix->tau;
-    a.buf = ix->cand_buf;
-    a.buf_cap = ix->cand_cap;
-    a.buf_cnt = ix->cnt;
-    a.overflow = ix->ovf;
-    a.active = ix->flag;
-    a.any_active = ix->n_flag;
-    LR_LAUNCH(launch_scan(a, range_groups, !reuse_list, reuse_list));
   }
   SelectArgs fb = fa;
   fb.cap = ix->cand_cap;
