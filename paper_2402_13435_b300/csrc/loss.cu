@@ -20,7 +20,16 @@
 //         key list as selection keys (ordered score, ~column) -- the in-batch
 //         hard-negative mining of Sec. 5.1 ranks them.
 // dZ enters the second product as two BF16 terms (hi + lo, near-FP32 accuracy).
-// Warps 0-3: epilogue (TMEM lane quarters); warp 4: TMA; warp 5: MMA issue.
+// Two epilogue sets (warps 0-3 and 6-9, TMEM lane quarters) take alternate
+// streamed tiles; warp 4 issues the TMA loads, warp 5 the MMAs.  The streamed
+// tiles come in pairs: one N = 128 MMA per K step scores both tiles of a pair
+// (an MMA costs about the same at N = 64 as at N = 128), into the two sets'
+// score buffers.  Tensor memory holds the scores of two pairs, so the MMAs of
+// pair p + 2 are queued behind the second products of pair p and the sets
+// find pair p + 1 scored when they finish pair p.
+// The streamed operand and its transposed copy (the second product's
+// operand) sit in separate rings: a pair's stage is free once it is scored, a
+// transposed tile's once its product is done.
 // Every wait is bounded; a timeout sets the status word.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -33,14 +42,17 @@ namespace lr {
 namespace {
 
 constexpr int kRRows = 128;     // rows of the resident tile
-constexpr int kCRows = 64;      // rows of a streamed tile
+constexpr int kCRows = 64;      // rows of a streamed tile (one epilogue set's score columns)
+constexpr int kPairRows = 2 * kCRows;  // a pair of streamed tiles: the score MMAs' N
 constexpr int kLossThreads = 320;  // warps 0-3 and 6-9: two epilogue sets; 4: TMA; 5: MMA
-constexpr int kLossFwdThreads = 192;  // the forward: one epilogue set
-constexpr int kCBufs = 3;          // streamed-tile buffers: a tile loads while the two before it are in use
-constexpr uint32_t kLossTmemCols = 256;  // 2 score tiles of 64 columns + accumulator (<= 128)
-// backward passes at dp = 128: the second product runs transposed (the
-// accumulator is [dp lanes][hi rows | lo rows], 256 columns), so 512 columns
-constexpr uint32_t kLossTmemColsT = 512;
+constexpr int kPBufsOne = 6;       // pair stages of the score-only passes (TMA latency under load is ~2 us)
+constexpr int kPBufs = 2;          // pair stages of the backward passes
+constexpr int kTBufs = 3;          // transposed-tile stages of the backward passes
+// tensor memory: two pair slots of 128 score columns, then (backward) the
+// accumulator at column 256: [128 rows][dp], or at dp = 128 the transposed
+// product's [dp lanes][hi rows | lo rows], 256 columns
+constexpr uint32_t kLossTmemColsOne = 256;
+constexpr uint32_t kLossTmemCols = 512;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -73,16 +85,16 @@ __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
   L.r = off;
   off += (size_t)(dp / 64) * kRRows * 128;  // K-blocks of 128 rows x 128 bytes
   L.c = off;
-  off += (size_t)kCBufs * (dp / 64) * kCRows * 128;
-  L.ct = off;
   const bool one_product = mode == kFwd || mode == kKeys;
-  off += one_product ? 0 : (size_t)kCBufs * dp * 128;  // transposed C tile: dp rows x 64 values
+  off += (size_t)(one_product ? kPBufsOne : kPBufs) * (dp / 64) * kPairRows * 128;  // [stage][K-block][128 rows]
+  L.ct = off;
+  off += one_product ? 0 : (size_t)kTBufs * dp * 128;  // transposed C tile: dp rows x 64 values
   L.dz = off;
   off += one_product ? 0 : (size_t)2 * 2 * kRRows * 128;  // [buffer][hi, lo] 128 rows x 64 values
   L.stage = off;
   off += mode == kDj ? 4 * sizeof(DjStage) : 0;  // two per epilogue set
   L.bars = off;
-  off += 16 * 8;
+  off += 40 * 8;
   L.holder = off;
   L.total = off + 16;
   return L;
@@ -110,15 +122,18 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   unsigned char *sdz = smem + L.dz;
   DjStage *stg = reinterpret_cast<DjStage *>(smem + L.stage);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
-  uint64_t *bar_r = bars, *c_full = bars + 1, *c_empty = bars + 1 + kCBufs;  // [kCBufs] each
-  uint64_t *s_full = bars + 1 + 2 * kCBufs, *s_empty = s_full + 2;               // [2]: one per epilogue set
-  uint64_t *dz_full = s_empty + 2, *dz_empty = dz_full + 2, *acc_full = dz_empty + 2;
+  constexpr int nP = kOne ? kPBufsOne : kPBufs;  // pair stages
+  uint64_t *bar_r = bars, *c_full = bars + 1, *c_empty = c_full + nP;  // [nP] each
+  uint64_t *t_full = c_empty + nP, *t_empty = t_full + kTBufs;       // [kTBufs] each
+  uint64_t *s_full = t_empty + kTBufs, *s_empty = s_full + 4;        // [pair slot][epilogue set]
+  uint64_t *dz_full = s_empty + 4, *dz_empty = dz_full + 2, *acc_full = dz_empty + 2;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + L.holder);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r0 = blockIdx.x * kRRows;
   const int t0 = blockIdx.y * a.c_per_split;
   const int T = min(a.c_per_split, a.n_ctiles - t0);  // streamed tiles of this CTA (>= 1 by construction)
-  const size_t c_bytes = (size_t)KB * kCRows * 128;
+  const int NP = (T + 1) / 2;                          // pairs (the last one may hold one tile)
+  const size_t p_bytes = (size_t)KB * kPairRows * 128;
   const size_t ct_bytes = (size_t)dp * 128;
   // Backward passes with dp = 128: acc^T[k][r | 128 + r] += C^T[k][c] .
   // [dZ_hi ; dZ_lo][r][c] as ONE MMA of N = 256 per 16-value K step (the
@@ -127,17 +142,23 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   // whatever its width up to 128 columns, so the product issues half the
   // instructions.  The write-out adds the two halves.
   const bool swap = !kOne && dp == 128;
-  const uint32_t tmem_cols = swap ? kLossTmemColsT : kLossTmemCols;
+  const uint32_t tmem_cols = kOne ? kLossTmemColsOne : kLossTmemCols;
 
   if (threadIdx.x == 0) {
     mbar_init(bar_r, 1);
-    for (int i = 0; i < kCBufs; ++i) {
+    for (int i = 0; i < nP; ++i) {
       mbar_init(&c_full[i], 1);
       mbar_init(&c_empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kTBufs; ++i) {
+      mbar_init(&t_full[i], 1);
+      mbar_init(&t_empty[i], 1);
+    }
+    for (int i = 0; i < 4; ++i) {
       mbar_init(&s_full[i], 1);
       mbar_init(&s_empty[i], 4);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&dz_full[i], 4);
       mbar_init(&dz_empty[i], 1);
     }
@@ -157,70 +178,92 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   if (warp == 4) {
     // ---------------------------------------------------------------- TMA
     if (lane == 0) {
-      int issued = 0;
+      int np = 0, nc = 0;  // pairs and transposed tiles issued
       mbar_arrive_expect_tx(bar_r, (uint32_t)(KB * kRRows * 128));
       for (int kb = 0; kb < KB; ++kb) tma_load_2d(sr + (size_t)kb * kRRows * 128, &tm_r, kb * 64, r0, bar_r);
-      for (int t = 0; t < T && ok; ++t) {
-        const int b = t % kCBufs;
-        if (!mbar_wait(&c_empty[b], (uint32_t)((t / kCBufs) & 1) ^ 1u)) {
-          ok = false;
-          break;
+      auto load_pair = [&](int p) -> bool {
+        const int st = p % nP, nt = min(2, T - 2 * p);
+        if (!mbar_wait(&c_empty[st], (uint32_t)((p / nP) & 1) ^ 1u)) return false;
+        mbar_arrive_expect_tx(&c_full[st], (uint32_t)(nt * KB * kCRows * 128));
+        for (int h = 0; h < nt; ++h) {
+          const int c0 = (t0 + 2 * p + h) * kCRows;
+          for (int kb = 0; kb < KB; ++kb)
+            tma_load_2d(sc + (size_t)st * p_bytes + (size_t)kb * kPairRows * 128 + (size_t)h * kCRows * 128, &tm_c,
+                        kb * 64, c0, &c_full[st]);
         }
-        const int c0 = (t0 + t) * kCRows;
-        mbar_arrive_expect_tx(&c_full[b], (uint32_t)(c_bytes + (kOne ? 0 : ct_bytes)));
-        for (int kb = 0; kb < KB; ++kb)
-          tma_load_2d(sc + (size_t)b * c_bytes + (size_t)kb * kCRows * 128, &tm_c, kb * 64, c0, &c_full[b]);
-        if (!kOne) tma_load_2d(sct + (size_t)b * ct_bytes, &tm_ct, c0, 0, &c_full[b]);
-        issued = t + 1;
+        return true;
+      };
+      auto load_ct = [&](int t) -> bool {
+        const int st = t % kTBufs;
+        if (!mbar_wait(&t_empty[st], (uint32_t)((t / kTBufs) & 1) ^ 1u)) return false;
+        mbar_arrive_expect_tx(&t_full[st], (uint32_t)ct_bytes);
+        tma_load_2d(sct + (size_t)st * ct_bytes, &tm_ct, (t0 + t) * kCRows, 0, &t_full[st]);
+        return true;
+      };
+      // Issue order = the order in which the MMA thread frees stages: pair p
+      // is scored before the products of tiles 2p - 2 and 2p - 1, so a pair
+      // is loaded once the transposed tiles two pairs before it are queued.
+      while (ok && (np < NP || (!kOne && nc < T))) {
+        if (np < NP && (kOne || np <= nc / 2 + 2)) {
+          ok = load_pair(np);
+          np += ok ? 1 : 0;
+        } else {
+          ok = load_ct(nc);
+          nc += ok ? 1 : 0;
+        }
       }
       if (!ok) {
         atomicOr(a.status, kErrTimeout);
         mbar_wait(bar_r, 0u);  // let issued loads land
-        for (int t = issued > kCBufs ? issued - kCBufs : 0; t < issued; ++t)
-          mbar_wait(&c_full[t % kCBufs], (uint32_t)((t / kCBufs) & 1));
+        for (int p = np > nP ? np - nP : 0; p < np; ++p) mbar_wait(&c_full[p % nP], (uint32_t)((p / nP) & 1));
+        for (int t = nc > kTBufs ? nc - kTBufs : 0; t < nc; ++t)
+          mbar_wait(&t_full[t % kTBufs], (uint32_t)((t / kTBufs) & 1));
       }
     }
     __syncwarp();
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA
     if (lane == 0) {
-      const uint32_t id_s = idesc_bf16(kRRows, kCRows), id_g = idesc_bf16(kRRows, dp);
+      const uint32_t id_s2 = idesc_bf16(kRRows, kPairRows), id_s1 = idesc_bf16(kRRows, kCRows);
+      const uint32_t id_g = idesc_bf16(kRRows, dp);
       const uint32_t id_t = idesc_bf16(128, 2 * kRRows);  // the transposed product: M = dp = 128, N = 256
-      const uint32_t acc = tmem + 2u * kCRows;
+      const uint32_t acc = tmem + 2u * kPairRows;
       bool issued = false;
-      auto issue_s = [&](int t) -> bool {
-        const int b = t & 1, cb = t % kCBufs;  // score buffer (the epilogue set's), streamed-tile buffer
-        if (!mbar_wait(&c_full[cb], (uint32_t)((t / kCBufs) & 1))) return false;
-        if (!mbar_wait(&s_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u)) return false;
+      // scores of pair p into slot j = p & 1: tile 2p into columns
+      // [128 j, 128 j + 64) (set 0), tile 2p + 1 into the next 64 (set 1),
+      // once both sets have read pair p - 2's
+      auto issue_pair = [&](int p) -> bool {
+        const int st = p % nP, nt = min(2, T - 2 * p), j = p & 1;
+        if (!mbar_wait(&c_full[st], (uint32_t)((p / nP) & 1))) return false;
+        for (int h = 0; h < nt; ++h)
+          if (!mbar_wait(&s_empty[2 * j + h], (uint32_t)((p >> 1) & 1) ^ 1u)) return false;
         tc_fence_after();
-        const uint32_t ra = smem_u32(sr), ca = smem_u32(sc + (size_t)cb * c_bytes);
+        const uint32_t ra = smem_u32(sr), ca = smem_u32(sc + (size_t)st * p_bytes);
         for (int k = 0; k < dp / 16; ++k) {
           const uint32_t koff = (uint32_t)(k & 3) * 32u;
-          mma_bf16(tmem + (uint32_t)(b * kCRows), sw128_desc(ra + (uint32_t)(k >> 2) * (kRRows * 128) + koff),
-                   sw128_desc(ca + (uint32_t)(k >> 2) * (kCRows * 128) + koff), id_s, k > 0 ? 1u : 0u);
+          mma_bf16(tmem + (uint32_t)(j * kPairRows), sw128_desc(ra + (uint32_t)(k >> 2) * (kRRows * 128) + koff),
+                   sw128_desc(ca + (uint32_t)(k >> 2) * (kPairRows * 128) + koff), nt == 2 ? id_s2 : id_s1,
+                   k > 0 ? 1u : 0u);
         }
         issued = true;
-        mma_commit(&s_full[b]);
-        if (kOne) mma_commit(&c_empty[cb]);
+        mma_commit(&s_full[2 * j]);
+        if (nt == 2) mma_commit(&s_full[2 * j + 1]);
+        mma_commit(&c_empty[st]);
         return true;
       };
       if (!mbar_wait(bar_r, 0u)) ok = false;
-      if (ok && T > 0) ok = issue_s(0);
-      for (int t = 0; t < T && ok; ++t) {
-        if (t + 1 < T && !issue_s(t + 1)) {
-          ok = false;
-          break;
-        }
-        if (!kOne) {
-          const int b = t & 1;
-          if (!mbar_wait(&dz_full[b], (uint32_t)((t >> 1) & 1))) {
+      for (int p = 0; p < 2 && p < NP && ok; ++p) ok = issue_pair(p);
+      for (int p = 0; p < NP && ok; ++p) {
+        for (int h = 0; h < 2 && 2 * p + h < T && !kOne; ++h) {
+          const int t = 2 * p + h, st = t % kTBufs;
+          if (!mbar_wait(&dz_full[h], (uint32_t)(p & 1)) || !mbar_wait(&t_full[st], (uint32_t)((t / kTBufs) & 1))) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t dh = smem_u32(sdz + (size_t)(2 * b) * kRRows * 128);
-          const uint32_t dl = smem_u32(sdz + (size_t)(2 * b + 1) * kRRows * 128);
-          const uint32_t ct = smem_u32(sct + (size_t)(t % kCBufs) * ct_bytes);
+          const uint32_t dh = smem_u32(sdz + (size_t)(2 * h) * kRRows * 128);
+          const uint32_t dl = smem_u32(sdz + (size_t)(2 * h + 1) * kRRows * 128);
+          const uint32_t ct = smem_u32(sct + (size_t)st * ct_bytes);
           if (swap) {  // dh and dl are adjacent: 256 rows of one K-major operand
 #pragma unroll
             for (int k = 0; k < 4; ++k)  // K = the tile's 64 streamed rows
@@ -234,9 +277,10 @@ __global__ void __launch_bounds__(kLossThreads, 1)
               mma_bf16(acc, sw128_desc(dl + (uint32_t)k * 32u), sw128_desc(ct + (uint32_t)k * 32u), id_g, 1u);
             }
           }
-          mma_commit(&dz_empty[b]);
-          mma_commit(&c_empty[t % kCBufs]);
+          mma_commit(&dz_empty[h]);
+          mma_commit(&t_empty[st]);
         }
+        if (ok && p + 2 < NP && !issue_pair(p + 2)) ok = false;
       }
       if (issued) {  // every MMA has completed before the epilogue reads the accumulator / TMEM is freed
         mma_commit(acc_full);
@@ -253,11 +297,8 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     // takes tiles e, e + 2, ..., so score buffer e and dZ buffer e are its own
     // and their barrier phases come in order; warp w reads tensor-memory lanes
     // 32 (w % 4) ..
-    // the forward epilogue is issue-bound with one set, and two CTAs of 192
-    // threads share an SM: it launches without warps 6-9
-    constexpr int kSets = kOne ? 1 : 2;
+    constexpr int kSets = 2;
     const int eset = warp >= 6 ? 1 : 0, quarter = warp & 3;
-    const bool active = eset < kSets;
     const int r = quarter * 32 + lane;
     const int grow = r0 + r;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -321,10 +362,10 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         store_stage(2 * eset);
       }
       set_barrier();
-    } else if (active && eset < T) {
+    } else if (eset < T) {
       fetch_row_words(eset);
     }
-    for (int t = eset, it = 0; active && t < T; t += kSets, ++it) {
+    for (int t = eset, it = 0; t < T; t += kSets, ++it) {
       const int b = t & 1;                 // two sets: == eset
       const int sb = 2 * eset + (it & 1);  // kDj: this tile's stage
       const int c0 = (t0 + t) * kCRows;
@@ -335,7 +376,8 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       }
       do {
       if (!ok) break;
-      if (!wwait(&s_full[b], (uint32_t)((t >> 1) & 1), lane)) {
+      const int slot = (t >> 1) & 1;  // pair slot of this tile's scores
+      if (!wwait(&s_full[2 * slot + b], (uint32_t)((t >> 2) & 1), lane)) {
         ok = false;
         break;
       }
@@ -344,12 +386,12 @@ __global__ void __launch_bounds__(kLossThreads, 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         uint32_t (&part)[16] = *reinterpret_cast<uint32_t (*)[16]>(&sv[16 * q]);
-        tmem_ld16(trow + (uint32_t)(b * kCRows + 16 * q), part);
+        tmem_ld16(trow + (uint32_t)(slot * kPairRows + b * kCRows + 16 * q), part);
       }
       tmem_ld_wait();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&s_empty[b]);
+      if (lane == 0) mbar_arrive(&s_empty[2 * slot + b]);
       // allowed columns of this tile: bit c of al[c / 32]; kDj also the
       // columns whose positive is this row's job: bit c of pm[c / 32]
       uint32_t al[2] = {0u, 0u}, pm[2] = {0u, 0u};
@@ -393,21 +435,36 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         }
         // the running maximum m is in log2 units; failing columns become -inf,
         // whose exponential is 0
+        // ssum = sum of 2^(z2 - m) over the allowed columns seen, z2 = s inv_tau
+        // log2(e).  The offset m is the maximum of the row's first tile with
+        // an allowed column and stays fixed (one FMA, one exponential per
+        // column) unless a later tile's terms would overflow: that tile is
+        // redone with its own maximum as the new offset.
         const float c2 = a.inv_tau * kLog2e;
-        float tmax = -INFINITY;
+        auto tile_max = [&]() {
+          float tmax = -INFINITY;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
-          const float z2 = ((al[c >> 5] >> (c & 31)) & 1u) ? __uint_as_float(sv[c]) * c2 : -INFINITY;
-          sv[c] = __float_as_uint(z2);
-          tmax = fmaxf(tmax, z2);
-        }
-        if (tmax > -INFINITY) {
-          const float mn = fmaxf(m, tmax);
+          for (int c = 0; c < 64; ++c)
+            if ((al[c >> 5] >> (c & 31)) & 1u) tmax = fmaxf(tmax, __uint_as_float(sv[c]) * c2);
+          return tmax;
+        };
+        if (m == -INFINITY) m = tile_max();
+        if (m > -INFINITY) {
           float add = 0.f;
 #pragma unroll
-          for (int c = 0; c < 64; ++c) add += ex2_approx(__uint_as_float(sv[c]) - mn);
-          ssum = ssum * ex2_approx(m - mn) + add;
-          m = mn;
+          for (int c = 0; c < 64; ++c)
+            add += ((al[c >> 5] >> (c & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -m)) : 0.f;
+          if (add < 0x1p100f) {
+            ssum += add;
+          } else {  // overflow or near it: rescale to this tile's maximum
+            const float mn = fmaxf(m, tile_max());
+            add = 0.f;
+#pragma unroll
+            for (int c = 0; c < 64; ++c)
+              add += ((al[c >> 5] >> (c & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -mn)) : 0.f;
+            ssum = ssum * ex2_approx(m - mn) + add;
+            m = mn;
+          }
         }
       } else if (MODE == kKeys) {
         if (rvalid) {
@@ -434,38 +491,56 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         }
         unsigned char *dh = sdz + (size_t)(2 * b) * kRRows * 128 + (size_t)r * 128;
         unsigned char *dl = sdz + (size_t)(2 * b + 1) * kRRows * 128 + (size_t)r * 128;
-        const float g = (a.dloss != nullptr ? __ldg(a.dloss) : 1.f) * a.inv_b;
         const float c2 = a.inv_tau * kLog2e;
-        const int pc = pos_row - c0;  // kDq: the positive's column in this tile
+        // dZ / g = softmax - [positive] on allowed columns (the factor g =
+        // dL / B is applied to the accumulated product); here the softmax
+        // term, the positives' -1 after the tile is written
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t hw[4], lw[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            float dz2[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int c = ch * 8 + u * 2 + h;
-              float lse, ispos;  // lse in log2 units
-              if (MODE == kDq) {
-                lse = lse_row;
-                ispos = c == pc ? 1.f : 0.f;
-              } else {
-                lse = stg[sb].lse[c];
-                ispos = ((pm[c >> 5] >> (c & 31)) & 1u) ? 1.f : 0.f;
-              }
-              const float dz = (ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -lse)) - ispos) * g;
-              dz2[h] = ((al[c >> 5] >> (c & 31)) & 1u) ? dz : 0.f;
-            }
-            const __nv_bfloat162 hv = __float22bfloat162_rn(make_float2(dz2[0], dz2[1]));
-            const float2 hf = __bfloat1622float2(hv);
-            const __nv_bfloat162 lv = __float22bfloat162_rn(make_float2(dz2[0] - hf.x, dz2[1] - hf.y));
-            hw[u] = *reinterpret_cast<const uint32_t *>(&hv);
+            const int c = ch * 8 + u * 2;  // columns c, c + 1
+            const float l0 = MODE == kDq ? lse_row : stg[sb].lse[c];  // log2 units
+            const float l1 = MODE == kDq ? lse_row : stg[sb].lse[c + 1];
+            const float p0 = ((al[c >> 5] >> (c & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -l0)) : 0.f;
+            const float p1 =
+                ((al[c >> 5] >> ((c + 1) & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c + 1]), c2, -l1)) : 0.f;
+            // hi = p truncated to BF16 (its upper 16 bits), lo = p - hi (exact)
+            // rounded to nearest: p = hi + lo within 2^-15 p
+            const uint32_t u0 = __float_as_uint(p0), u1 = __float_as_uint(p1);
+            const __nv_bfloat162 lv =
+                __floats2bfloat162_rn(p0 - __uint_as_float(u0 & 0xFFFF0000u), p1 - __uint_as_float(u1 & 0xFFFF0000u));
+            hw[u] = __byte_perm(u0, u1, 0x7632);
             lw[u] = *reinterpret_cast<const uint32_t *>(&lv);
           }
           const int slot = ((ch ^ (r & 7)) & 7) << 4;
           *reinterpret_cast<uint4 *>(dh + slot) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           *reinterpret_cast<uint4 *>(dl + slot) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        // column c of this row is a positive (an allowed column: the positive
+        // always is): its entry becomes p - 1, computed in FP32 from the
+        // column's score so that it keeps its relative accuracy when p is near 1
+        auto patch = [&](int c, float lse2) {
+          float sc = 0.f;
+#pragma unroll
+          for (int k = 0; k < 64; ++k) sc = k == c ? __uint_as_float(sv[k]) : sc;
+          const float v = ex2_approx(fmaf(sc, c2, -lse2)) - 1.f;
+          const __nv_bfloat16 nh = __float2bfloat16_rn(v);
+          const int so = ((((c >> 3) ^ (r & 7)) & 7) << 4) | ((c & 7) << 1);
+          *reinterpret_cast<__nv_bfloat16 *>(dh + so) = nh;
+          *reinterpret_cast<__nv_bfloat16 *>(dl + so) = __float2bfloat16_rn(v - __bfloat162float(nh));
+        };
+        if (MODE == kDq) {
+          const int pc = pos_row - c0;
+          if (pc >= 0 && pc < kCRows) patch(pc, lse_row);
+        } else {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            for (uint32_t w = pm[h] & al[h]; w != 0u; w &= w - 1u) {
+              const int c = 32 * h + __ffs(w) - 1;
+              patch(c, stg[sb].lse[c]);
+            }
         }
         fence_proxy_async();
         __syncwarp();
@@ -477,46 +552,55 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         set_barrier();
       }
     }
-    if (MODE == kFwd) {  // one set: the row's log-sum-exp partial of this split
+    if (MODE == kFwd) {  // the row's log-sum-exp partial of this split and set
       if (rvalid) {
-        a.part_m[(size_t)blockIdx.y * a.rows_p + grow] = m * kLn2;  // natural units for the combine
-        a.part_s[(size_t)blockIdx.y * a.rows_p + grow] = ssum;
+        const size_t part = (size_t)(2 * blockIdx.y + eset) * a.rows_p + grow;
+        a.part_m[part] = m * kLn2;  // natural units for the combine
+        a.part_s[part] = ssum;
         if (have_pos) a.zpos[grow] = zpos;
       }
     } else if (MODE == kKeys) {
-    } else if (eset == 0) {  // set 0 writes the accumulated rows
+    } else {  // both sets write the accumulated rows, set e its half
       if (!wwait(acc_full, 0u, lane)) ok = false;
       tc_fence_after();
-      const uint32_t acc = trow + 2u * kCRows;
+      const uint32_t acc = trow + 2u * kPairRows;
+      const float scale = a.inv_tau * (a.dloss != nullptr ? __ldg(a.dloss) : 1.f) * a.inv_b;  // inv_tau g
       if (swap) {
         // lane k (= this thread's TMEM lane) holds column k of every row: rows
         // r and 128 + r are the hi and lo halves; a warp's 32 lanes write 32
-        // consecutive columns of a row
+        // consecutive columns of a row.  Set e takes rows [64 e, 64 e + 64),
+        // 32 at a time (four loads in flight per wait).
         const int k = quarter * 32 + lane;
         float *ocol = a.out + (size_t)blockIdx.y * a.out_split + k;
         const int rows_ok = MODE == kDq ? a.rows_p : a.M;
-        for (int rr = 0; rr < kRRows; rr += 16) {
-          uint32_t vh[16], vl[16];
-          tmem_ld16(acc + (uint32_t)rr, vh);
-          tmem_ld16(acc + (uint32_t)(kRRows + rr), vl);
+        for (int rr = 64 * eset; rr < 64 * eset + 64; rr += 32) {
+          uint32_t vh[32], vl[32];
+          tmem_ld16(acc + (uint32_t)rr, *reinterpret_cast<uint32_t (*)[16]>(&vh[0]));
+          tmem_ld16(acc + (uint32_t)(rr + 16), *reinterpret_cast<uint32_t (*)[16]>(&vh[16]));
+          tmem_ld16(acc + (uint32_t)(kRRows + rr), *reinterpret_cast<uint32_t (*)[16]>(&vl[0]));
+          tmem_ld16(acc + (uint32_t)(kRRows + rr + 16), *reinterpret_cast<uint32_t (*)[16]>(&vl[16]));
           tmem_ld_wait();
           if (ok && k < a.out_cols)
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
+            for (int i = 0; i < 32; ++i)
               if (r0 + rr + i < rows_ok)
-                ocol[(size_t)(r0 + rr + i) * a.out_ld] = (__uint_as_float(vh[i]) + __uint_as_float(vl[i])) * a.inv_tau;
+                ocol[(size_t)(r0 + rr + i) * a.out_ld] = (__uint_as_float(vh[i]) + __uint_as_float(vl[i])) * scale;
         }
       } else {
+        // thread r holds row r: set e writes columns [e dp / 2, (e + 1) dp / 2)
         float *orow = a.out + (size_t)blockIdx.y * a.out_split + (size_t)grow * a.out_ld;
         const bool wr = ok && (MODE == kDq ? grow < a.rows_p : grow < a.M);
-        for (int c = 0; c < dp; c += 16) {
-          uint32_t v[16];
-          tmem_ld16(acc + (uint32_t)c, v);
+        for (int c = eset * (dp / 2); c < (eset + 1) * (dp / 2); c += 32) {
+          uint32_t v[32];
+          tmem_ld16(acc + (uint32_t)c, *reinterpret_cast<uint32_t (*)[16]>(&v[0]));
+          tmem_ld16(acc + (uint32_t)(c + 16), *reinterpret_cast<uint32_t (*)[16]>(&v[16]));
           tmem_ld_wait();
           if (wr)
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (c + i < a.out_cols) orow[c + i] = __uint_as_float(v[i]) * a.inv_tau;
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4 *>(orow + c + i) =
+                  make_float4(__uint_as_float(v[i]) * scale, __uint_as_float(v[i + 1]) * scale,
+                              __uint_as_float(v[i + 2]) * scale, __uint_as_float(v[i + 3]) * scale);
         }
       }
     }
@@ -529,75 +613,130 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   if (warp == 5) tmem_dealloc(tmem, tmem_cols);
 }
 
-// X [rows][d] (BF16 or FP32) -> P [rows_p][dp] and PT [dp][rows_p], BF16, zero padded.
-// A 32 x 32 tile per block goes through shared memory, so both copies are
-// written along their rows.
-constexpr int kPrepTile = 32;
-__global__ void k_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, __nv_bfloat16 *P,
-                            __nv_bfloat16 *PT) {
-  __shared__ __nv_bfloat16 tile[kPrepTile][kPrepTile + 1];
+// X [rows][d] (BF16 or FP32) -> P [rows_p][dp] and/or PT [dp][rows_p], BF16,
+// zero padded (either output may be null).  A 64 x 64 tile per block goes
+// through shared memory; a thread moves two adjacent values, so both copies
+// are written along their rows in 4-byte words.
+constexpr int kPrepTile = 64;
+
+__global__ void __launch_bounds__(256) k_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp,
+                                                   __nv_bfloat16 *P, __nv_bfloat16 *PT) {
+  __shared__ __nv_bfloat16 tile[kPrepTile][kPrepTile + 2];
   const int r0 = blockIdx.x * kPrepTile, k0 = blockIdx.y * kPrepTile;  // rows on x: no 65,535 limit
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads
-  for (int j = ty; j < kPrepTile; j += blockDim.y) {
-    const int row = r0 + j, k = k0 + tx;
-    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-    if (row < rows && k < d) {
-      v = elem == kElemBF16 ? reinterpret_cast<const __nv_bfloat16 *>(X)[(size_t)row * d + k]
-                            : __float2bfloat16_rn(reinterpret_cast<const float *>(X)[(size_t)row * d + k]);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;              // 32 x 8 threads
+  const int k = k0 + 2 * tx;
+  for (int j = ty; j < kPrepTile; j += 8) {
+    const int row = r0 + j;
+    float v0 = 0.f, v1 = 0.f;
+    if (row < rows) {
+      if (elem == kElemBF16) {
+        const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(X) + (size_t)row * d;
+        if (k < d) v0 = __bfloat162float(x[k]);
+        if (k + 1 < d) v1 = __bfloat162float(x[k + 1]);
+      } else {
+        const float *x = reinterpret_cast<const float *>(X) + (size_t)row * d;
+        if (k < d) v0 = x[k];
+        if (k + 1 < d) v1 = x[k + 1];
+      }
     }
-    if (row < rows_p && k < dp) P[(size_t)row * dp + k] = v;
-    tile[j][tx] = v;
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    if (P != nullptr && row < rows_p && k < dp) *reinterpret_cast<__nv_bfloat162 *>(P + (size_t)row * dp + k) = h;
+    tile[j][2 * tx] = h.x;
+    tile[j][2 * tx + 1] = h.y;
   }
+  if (PT == nullptr) return;
   __syncthreads();
-  for (int j = ty; j < kPrepTile; j += blockDim.y) {
-    const int k = k0 + j, row = r0 + tx;
-    if (k < dp && row < rows_p) PT[(size_t)k * rows_p + row] = tile[tx][j];
+  const int row = r0 + 2 * tx;  // PT columns (rows of X) of this thread
+  for (int j = ty; j < kPrepTile; j += 8) {
+    const int kk = k0 + j;
+    if (kk < dp && row < rows_p) {
+      __nv_bfloat162 h;
+      h.x = tile[2 * tx][j];
+      h.y = tile[2 * tx + 1][j];
+      *reinterpret_cast<__nv_bfloat162 *>(PT + (size_t)kk * rows_p + row) = h;
+    }
   }
 }
 
-// Per query (one thread each): combine the split partials into its log-sum-exp.
-__global__ void k_loss_lse(const LossArgs a, int splits, float *lse) {
+// Per query (one thread each): combine the split partials into its
+// log-sum-exp; each block sums its queries' terms lse - z_pos in FP64 in a
+// fixed order, and the last block to finish adds the blocks' sums in block
+// order (the loss does not depend on the blocks' timing).  An out-of-range
+// positive makes the loss NaN.  done[0] counts finished blocks (zero before
+// the launch; the last block resets it).
+constexpr int kLseThreads = 256;
+
+__global__ void __launch_bounds__(kLseThreads) k_loss_lse(const LossArgs a, int splits, float *lse, double *bsum,
+                                                          uint32_t *done, float *loss) {
+  __shared__ double red[kLseThreads / 32];
+  __shared__ bool last;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= a.B) return;
-  float mx = -INFINITY;
-  for (int s = 0; s < splits; ++s) mx = fmaxf(mx, a.part_m[(size_t)s * a.rows_p + q]);
-  float sum = 0.f;
-  for (int s = 0; s < splits; ++s) {
-    const float ms = a.part_m[(size_t)s * a.rows_p + q];
-    if (ms > -INFINITY) sum += a.part_s[(size_t)s * a.rows_p + q] * exp2f((ms - mx) * kLog2e);
-  }
-  lse[q] = mx + logf(sum);
-}
-
-// The loss: one CTA sums the queries' terms lse - z_pos in FP64 in a fixed
-// order.  An out-of-range positive makes the loss NaN.
-__global__ void k_loss_combine(const LossArgs a, const float *lse, float *loss) {
-  __shared__ double red[32];
-  double acc = 0.0;
-  for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
+  double term = 0.0;
+  if (q < a.B) {
+    float mx = -INFINITY;
+    for (int s = 0; s < splits; ++s) mx = fmaxf(mx, a.part_m[(size_t)s * a.rows_p + q]);
+    float sum = 0.f;
+    for (int s = 0; s < splits; ++s) {
+      const float ms = a.part_m[(size_t)s * a.rows_p + q];
+      if (ms > -INFINITY) sum += a.part_s[(size_t)s * a.rows_p + q] * exp2f((ms - mx) * kLog2e);
+    }
+    const float l = mx + logf(sum);
+    lse[q] = l;
     const int p = a.pos[q];
-    acc += (p >= 0 && p < a.M) ? (double)lse[q] - (double)a.zpos[q] : (double)NAN;
+    term = (p >= 0 && p < a.M) ? (double)l - (double)a.zpos[q] : (double)NAN;
   }
   // fixed reduction tree: lanes by shuffles, then the warps' sums in warp order
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int off = 16; off > 0; off >>= 1) term += __shfl_down_sync(0xFFFFFFFFu, term, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = (int)threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kLseThreads / 32; ++w) v += red[w];
+    bsum[blockIdx.x] = v;
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(bsum + i);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
-    if (threadIdx.x == 0) *loss = (float)(v / (double)a.B);
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kLseThreads / 32; ++w) t += red[w];
+    *loss = (float)(t / (double)a.B);
+    *done = 0u;
   }
 }
 
+// dQ / dJ = the sum of the split partials; four values of a row per thread.
 __global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ) {
+  const int dq4 = (d + 3) / 4;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)B * d) return;
-  const int q = (int)(i / d), k = (int)(i % d);
-  float s = 0.f;
-  for (int sp = 0; sp < splits; ++sp) s += part[(size_t)sp * split_stride + (size_t)q * dp + k];
-  dQ[i] = s;
+  if (i >= (int64_t)B * dq4) return;
+  const int q = (int)(i / dq4), k = 4 * (int)(i % dq4);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int sp = 0; sp < splits; ++sp) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(part + (size_t)sp * split_stride + (size_t)q * dp + k));
+    s.x += v.x;
+    s.y += v.y;
+    s.z += v.z;
+    s.w += v.w;
+  }
+  float *o = dQ + (size_t)q * d + k;
+  if ((d & 3) == 0) {
+    *reinterpret_cast<float4 *>(o) = s;
+  } else {
+    o[0] = s.x;
+    if (k + 1 < d) o[1] = s.y;
+    if (k + 2 < d) o[2] = s.z;
+    if (k + 3 < d) o[3] = s.w;
+  }
 }
 
 // Per query: the selection's K, and its pass count = the keys listed.
@@ -638,8 +777,7 @@ cudaError_t launch_hn_mask(const int32_t *ids, const int32_t *count, int B, int 
 cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
                              cudaStream_t s) {
   const dim3 grid((unsigned)((rows_p + kPrepTile - 1) / kPrepTile), (unsigned)((dp + kPrepTile - 1) / kPrepTile));
-  k_loss_prep<<<grid, dim3(kPrepTile, 8), 0, s>>>(X, elem, rows, d, rows_p, dp, (__nv_bfloat16 *)P,
-                                                  (__nv_bfloat16 *)PT);
+  k_loss_prep<<<grid, 256, 0, s>>>(X, elem, rows, d, rows_p, dp, (__nv_bfloat16 *)P, (__nv_bfloat16 *)PT);
   return cudaGetLastError();
 }
 
@@ -656,7 +794,7 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
     case kFwd:
       e = allow_dynamic_smem((const void *)k_loss<kFwd>, (size_t)smem);
       if (e != cudaSuccess) return e;
-      k_loss<kFwd><<<grid, kLossFwdThreads, smem, s>>>(a, r, c, ct);
+      k_loss<kFwd><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
       break;
     case kDq:
       e = allow_dynamic_smem((const void *)k_loss<kDq>, (size_t)smem);
@@ -671,7 +809,7 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
     case kKeys:
       e = allow_dynamic_smem((const void *)k_loss<kKeys>, (size_t)smem);
       if (e != cudaSuccess) return e;
-      k_loss<kKeys><<<grid, kLossFwdThreads, smem, s>>>(a, r, c, ct);
+      k_loss<kKeys><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -679,17 +817,18 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
   return cudaGetLastError();
 }
 
-cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, float *loss, cudaStream_t s) {
-  if (a.B > 0) k_loss_lse<<<(unsigned)((a.B + 255) / 256), 256, 0, s>>>(a, splits, lse);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_loss_combine<<<1, 1024, 0, s>>>(a, lse, loss);
+cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, double *bsum, uint32_t *done, float *loss,
+                                cudaStream_t s) {
+  k_loss_lse<<<(unsigned)((a.B + kLseThreads - 1) / kLseThreads), kLseThreads, 0, s>>>(a, splits, lse, bsum, done,
+                                                                                       loss);
   return cudaGetLastError();
 }
 
+int loss_combine_blocks(int B) { return (B + kLseThreads - 1) / kLseThreads; }
+
 cudaError_t launch_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ,
                                   cudaStream_t s) {
-  const int64_t n = (int64_t)B * d;
+  const int64_t n = (int64_t)B * ((d + 3) / 4);
   k_loss_dq_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, splits, split_stride, B, d, dp, dQ);
   return cudaGetLastError();
 }

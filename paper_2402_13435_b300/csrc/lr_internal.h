@@ -328,7 +328,9 @@ cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_
                              cudaStream_t s);
 cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y, const void *tm_r, const void *tm_c,
                              const void *tm_ct, cudaStream_t s);
-cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, float *loss, cudaStream_t s);
+cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, double *bsum, uint32_t *done, float *loss,
+                                cudaStream_t s);
+int loss_combine_blocks(int B);  // blocks of launch_loss_combine (one FP64 partial each)
 cudaError_t launch_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ,
                                   cudaStream_t s);
 // 2-D tiled TMA descriptor (innermost dimension first); false when the driver

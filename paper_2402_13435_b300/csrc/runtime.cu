@@ -1865,18 +1865,20 @@ struct LossPlan {
   int Bp = 0, Mp = 0, dp = 0, n_ctiles = 0, c_per_split = 0, splits = 0;
   int nj_ctiles = 0, cj_per_split = 0, splits_j = 0;  // the dJ pass: job tiles against query tiles
   size_t o_qp = 0, o_qt = 0, o_jp = 0, o_jt = 0, o_pm = 0, o_ps = 0, o_zp = 0, o_dq = 0, o_dj = 0, o_st = 0,
-         total = 0;
+         o_bs = 0, total = 0;
 };
 
 // Split of the streamed range over CTAs: the count (at most 16) that minimises
 // (waves of CTAs over the SMs) x (streamed tiles per CTA + a CTA's fixed cost,
 // about two tiles: tensor-memory allocation and the resident tile's load).
+// A CTA's range is a whole number of tile pairs where it can be (the score
+// MMAs take the streamed tiles two at a time).
 void choose_split(int rtiles, int ctiles, int sms, int &splits, int &per) {
   long best = -1;
   splits = 1;
   per = ctiles;
   for (int s = 1; s <= std::min(ctiles, 16); ++s) {
-    const int p = (ctiles + s - 1) / s;
+    const int p = ctiles >= 2 ? (ctiles + 2 * s - 1) / (2 * s) * 2 : ctiles;
     const int se = (ctiles + p - 1) / p;
     const long cost = (long)((rtiles * se + sms - 1) / sms) * (p + 2);
     if (best < 0 || cost < best) {
@@ -1901,12 +1903,13 @@ LossPlan loss_plan(int B, int M, int d, int sms) {
   P.o_qt = cv.take<uint16_t>((size_t)P.Bp * P.dp);
   P.o_jp = cv.take<uint16_t>((size_t)P.Mp * P.dp);
   P.o_jt = cv.take<uint16_t>((size_t)P.Mp * P.dp);
-  P.o_pm = cv.take<float>((size_t)P.splits * P.Bp);
-  P.o_ps = cv.take<float>((size_t)P.splits * P.Bp);
+  P.o_pm = cv.take<float>((size_t)2 * P.splits * P.Bp);  // one partial per split and epilogue set
+  P.o_ps = cv.take<float>((size_t)2 * P.splits * P.Bp);
   P.o_zp = cv.take<float>(P.Bp);
   P.o_dq = cv.take<float>((size_t)P.splits * P.Bp * P.dp);
   P.o_dj = cv.take<float>((size_t)P.splits_j * P.Mp * P.dp);
-  P.o_st = cv.take<uint32_t>(4);
+  P.o_st = cv.take<uint32_t>(4);  // status word, finished-block counter of the loss sum
+  P.o_bs = cv.take<double>((size_t)loss_combine_blocks(P.Bp));
   P.total = align_up(cv.off, 256);
   return P;
 }
@@ -1937,20 +1940,31 @@ struct LossMaps {
   CUtensorMap qr, qc, qt, jr, jc, jt;
 };
 
+// Operand copies and TMA descriptors of the loss passes.  BF16 inputs whose
+// rows are whole 16-byte words (d % 8 == 0, 16-byte aligned) are read in place
+// (the descriptors' zero fill pads rows past B or M and columns past d);
+// otherwise a BF16 copy padded to [rows_p][dp] is written.  The backward
+// passes also read the transposed copies [dp][rows_p] (need_t).
 lr_status loss_prepare(const void *Q, const void *J, int B, int M, int d, int dtype, char *w, const LossPlan &P,
-                       LossMaps &T, cudaStream_t s) {
+                       LossMaps &T, bool need_t, cudaStream_t s) {
   const int elem = dtype == LR_BF16 ? kElemBF16 : kElemF32;
-  LR_CK(cudaMemsetAsync(w + P.o_st, 0, sizeof(uint32_t), s));
-  LR_CK(launch_loss_prep(Q, elem, B, d, P.Bp, P.dp, w + P.o_qp, w + P.o_qt, s));
-  LR_CK(launch_loss_prep(J, elem, M, d, P.Mp, P.dp, w + P.o_jp, w + P.o_jt, s));
+  const bool direct = dtype == LR_BF16 && d % 8 == 0 && ((uintptr_t)Q & 15u) == 0 && ((uintptr_t)J & 15u) == 0;
+  LR_CK(cudaMemsetAsync(w + P.o_st, 0, 2 * sizeof(uint32_t), s));
+  if (!direct || need_t) {
+    LR_CK(launch_loss_prep(Q, elem, B, d, P.Bp, P.dp, direct ? nullptr : w + P.o_qp, need_t ? w + P.o_qt : nullptr, s));
+    LR_CK(launch_loss_prep(J, elem, M, d, P.Mp, P.dp, direct ? nullptr : w + P.o_jp, need_t ? w + P.o_jt : nullptr, s));
+  }
   const int bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, sw = CU_TENSOR_MAP_SWIZZLE_128B;
-  const uint64_t rs = (uint64_t)P.dp * 2;
-  bool ok = encode_tmap_2d(&T.qr, bf, w + P.o_qp, P.dp, P.Bp, rs, 64, 128, sw) &&
-            encode_tmap_2d(&T.qc, bf, w + P.o_qp, P.dp, P.Bp, rs, 64, 64, sw) &&
-            encode_tmap_2d(&T.qt, bf, w + P.o_qt, P.Bp, P.dp, (uint64_t)P.Bp * 2, 64, P.dp, sw) &&
-            encode_tmap_2d(&T.jr, bf, w + P.o_jp, P.dp, P.Mp, rs, 64, 128, sw) &&
-            encode_tmap_2d(&T.jc, bf, w + P.o_jp, P.dp, P.Mp, rs, 64, 64, sw) &&
-            encode_tmap_2d(&T.jt, bf, w + P.o_jt, P.Mp, P.dp, (uint64_t)P.Mp * 2, 64, P.dp, sw);
+  const void *qs = direct ? Q : (const void *)(w + P.o_qp), *js = direct ? J : (const void *)(w + P.o_jp);
+  const uint64_t inner = direct ? (uint64_t)d : (uint64_t)P.dp, rs = inner * 2;
+  const uint64_t qrows = direct ? (uint64_t)B : (uint64_t)P.Bp, jrows = direct ? (uint64_t)M : (uint64_t)P.Mp;
+  bool ok = encode_tmap_2d(&T.qr, bf, qs, inner, qrows, rs, 64, 128, sw) &&
+            encode_tmap_2d(&T.qc, bf, qs, inner, qrows, rs, 64, 64, sw) &&
+            encode_tmap_2d(&T.jr, bf, js, inner, jrows, rs, 64, 128, sw) &&
+            encode_tmap_2d(&T.jc, bf, js, inner, jrows, rs, 64, 64, sw);
+  if (ok && need_t)
+    ok = encode_tmap_2d(&T.qt, bf, w + P.o_qt, P.Bp, P.dp, (uint64_t)P.Bp * 2, 64, P.dp, sw) &&
+         encode_tmap_2d(&T.jt, bf, w + P.o_jt, P.Mp, P.dp, (uint64_t)P.Mp * 2, 64, P.dp, sw);
   if (!ok) return fail(LR_ERR_CUDA, "cannot encode the TMA descriptors of the loss operands");
   return LR_OK;
 }
@@ -1995,11 +2009,11 @@ lr_status lr_score_forward(const void *Q, const void *J, int32_t B, int32_t M, i
   if (!is_device_ptr(loss) || !is_device_ptr(lse)) return fail(LR_ERR_INVALID, "loss and lse must be device memory");
   char *w = (char *)workspace;
   LossMaps T;
-  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, s);
+  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, false, s);
   if (st != LR_OK) return st;
   LossArgs a = loss_args(B, M, inv_tau, pos, mask_bits, w, P);
   LR_CK(launch_loss_pass(0, a, P.Bp / 128, P.splits, &T.qr, &T.jc, nullptr, s));
-  LR_CK(launch_loss_combine(a, P.splits, lse, loss, s));
+  LR_CK(launch_loss_combine(a, 2 * P.splits, lse, (double *)(w + P.o_bs), (uint32_t *)(w + P.o_st) + 1, loss, s));
   return LR_OK;
 }
 
@@ -2015,7 +2029,7 @@ lr_status lr_score_backward(const void *Q, const void *J, int32_t B, int32_t M, 
     return fail(LR_ERR_INVALID, "lse, dloss, dQ and dJ must be device memory");
   char *w = (char *)workspace;
   LossMaps T;
-  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, s);
+  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, true, s);
   if (st != LR_OK) return st;
   // dQ: query tiles against job tiles, per-split partials, then their sum
   LossArgs a = loss_args(B, M, inv_tau, pos, mask_bits, w, P);
@@ -2088,7 +2102,7 @@ lr_status lr_hard_negatives(const void *Q, const void *J, int32_t B, int32_t M, 
   if (out_mask && !out_count) return fail(LR_ERR_INVALID, "out_mask needs out_count");
   char *w = (char *)workspace;
   LossMaps T;
-  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, s);
+  st = loss_prepare(Q, J, B, M, d, dtype, w, P, T, false, s);
   if (st != LR_OK) return st;
   LR_CK(cudaMemsetAsync(w + H.negc, 0, H.zero_end - H.negc, s));
   LossArgs a = loss_args(B, M, 1.0f, pos, mask_bits, w, P);

@@ -105,3 +105,18 @@ def test_loss_two_tower_step_size(lr):
     B, M, d = 4096, 4096 + 16384, 128
     Qb, Jb, pos, allowed = _inputs(3, B, M, d, 0.8, True)
     _check(lr, Qb, Jb, pos, allowed, 1.0 / 0.05)
+
+
+@pytest.mark.parametrize("in_batch", [True, False])
+def test_loss_confident_rows(lr, in_batch):
+    """Each query's positive is its own embedding, so the softmax puts ~0.998 on it and dZ at the positive,
+    p - 1, is ~-0.002: that entry must be formed in FP32 before its BF16 split (rebuilding it from the
+    split of p would leave ~2^-15 absolute, 1e-2 of the entry).  The FP32 exponent s inv_tau - lse of a
+    confident positive is itself a difference of two numbers near 17, so the entry keeps ~1e-3 of its
+    relative accuracy: the bound here is 1e-3 of the largest gradient."""
+    B, M, d = 96, 700, 64
+    Qb, Jb, pos, allowed = _inputs(13, B, M, d, 0.5, in_batch)
+    J = Jb.clone()
+    J[torch.from_numpy(pos).long()] = Qb  # s(q, positive) = |q|^2 = 1, the negatives' scores ~ N(0, 1/8)
+    allowed[np.arange(B), pos] = True
+    _check(lr, Qb, J, pos, allowed, 12.0, tol=1e-3)
