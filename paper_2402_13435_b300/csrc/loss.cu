@@ -614,15 +614,27 @@ __global__ void __launch_bounds__(kLossThreads, 1)
 }
 
 // X [rows][d] (BF16 or FP32) -> P [rows_p][dp] and/or PT [dp][rows_p], BF16,
-// zero padded (either output may be null).  A 64 x 64 tile per block goes
-// through shared memory; a thread moves two adjacent values, so both copies
-// are written along their rows in 4-byte words.
+// zero padded (either output may be null), for two operands in one launch
+// (blocks [0, nb0) take job 0).  A 64 x 64 tile per block goes through shared
+// memory; a thread moves two adjacent values, so both copies are written
+// along their rows in 4-byte words.
 constexpr int kPrepTile = 64;
 
-__global__ void __launch_bounds__(256) k_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp,
-                                                   __nv_bfloat16 *P, __nv_bfloat16 *PT) {
+struct PrepJob {
+  const void *X;
+  int rows, rows_p;
+  __nv_bfloat16 *P, *PT;
+};
+
+__global__ void __launch_bounds__(256) k_loss_prep(const PrepJob j0, const PrepJob j1, int nb0, int elem, int d,
+                                                   int dp) {
   __shared__ __nv_bfloat16 tile[kPrepTile][kPrepTile + 2];
-  const int r0 = blockIdx.x * kPrepTile, k0 = blockIdx.y * kPrepTile;  // rows on x: no 65,535 limit
+  const bool second = (int)blockIdx.x >= nb0;
+  const PrepJob &J = second ? j1 : j0;
+  const void *X = J.X;
+  const int rows = J.rows, rows_p = J.rows_p;
+  __nv_bfloat16 *P = J.P, *PT = J.PT;
+  const int r0 = ((int)blockIdx.x - (second ? nb0 : 0)) * kPrepTile, k0 = blockIdx.y * kPrepTile;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;              // 32 x 8 threads
   const int k = k0 + 2 * tx;
   for (int j = ty; j < kPrepTile; j += 8) {
@@ -658,41 +670,44 @@ __global__ void __launch_bounds__(256) k_loss_prep(const void *X, int elem, int 
   }
 }
 
-// Per query (one thread each): combine the split partials into its
-// log-sum-exp; each block sums its queries' terms lse - z_pos in FP64 in a
-// fixed order, and the last block to finish adds the blocks' sums in block
-// order (the loss does not depend on the blocks' timing).  An out-of-range
-// positive makes the loss NaN.  done[0] counts finished blocks (zero before
-// the launch; the last block resets it).
+// Per query (one warp each, lane s reads partial s, so the partials load in
+// one round): combine the split partials into its log-sum-exp; each block
+// sums its queries' terms lse - z_pos in FP64 in a fixed order, and the last
+// block to finish adds the blocks' sums in block order (the loss does not
+// depend on the blocks' timing).  An out-of-range positive makes the loss
+// NaN.  done[0] counts finished blocks (zero before the launch; the last block
+// resets it).  At most 32 partials per query.
 constexpr int kLseThreads = 256;
+constexpr int kLseQueries = kLseThreads / 32;
 
 __global__ void __launch_bounds__(kLseThreads) k_loss_lse(const LossArgs a, int splits, float *lse, double *bsum,
                                                           uint32_t *done, float *loss) {
-  __shared__ double red[kLseThreads / 32];
+  __shared__ double red[kLseQueries];
   __shared__ bool last;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int q = blockIdx.x * kLseQueries + w;
   double term = 0.0;
   if (q < a.B) {
-    float mx = -INFINITY;
-    for (int s = 0; s < splits; ++s) mx = fmaxf(mx, a.part_m[(size_t)s * a.rows_p + q]);
-    float sum = 0.f;
-    for (int s = 0; s < splits; ++s) {
-      const float ms = a.part_m[(size_t)s * a.rows_p + q];
-      if (ms > -INFINITY) sum += a.part_s[(size_t)s * a.rows_p + q] * exp2f((ms - mx) * kLog2e);
-    }
-    const float l = mx + logf(sum);
-    lse[q] = l;
-    const int p = a.pos[q];
-    term = (p >= 0 && p < a.M) ? (double)l - (double)a.zpos[q] : (double)NAN;
-  }
-  // fixed reduction tree: lanes by shuffles, then the warps' sums in warp order
+    const float ms = lane < splits ? a.part_m[(size_t)lane * a.rows_p + q] : -INFINITY;
+    const float ss = lane < splits ? a.part_s[(size_t)lane * a.rows_p + q] : 0.f;
+    float mx = ms;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) term += __shfl_down_sync(0xFFFFFFFFu, term, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    float sum = ms > -INFINITY ? ss * exp2f((ms - mx) * kLog2e) : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
+    const float l = mx + logf(sum);
+    if (lane == 0) {
+      lse[q] = l;
+      const int p = a.pos[q];
+      term = (p >= 0 && p < a.M) ? (double)l - (double)a.zpos[q] : (double)NAN;
+    }
+  }
+  if (lane == 0) red[w] = term;
   __syncthreads();
   if (threadIdx.x == 0) {
     double v = 0.0;
-    for (int w = 0; w < kLseThreads / 32; ++w) v += red[w];
+    for (int i = 0; i < kLseQueries; ++i) v += red[i];
     bsum[blockIdx.x] = v;
     __threadfence();
     last = atomicAdd(done, 1u) == gridDim.x - 1;
@@ -700,17 +715,15 @@ __global__ void __launch_bounds__(kLseThreads) k_loss_lse(const LossArgs a, int 
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double v = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(bsum + i);
+  if (w == 0) {  // the blocks' sums in block order: lane-strided partials, then a fixed shuffle tree
+    double v = 0.0;
+    for (int i = lane; i < (int)gridDim.x; i += 32) v += __ldcg(bsum + i);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kLseThreads / 32; ++w) t += red[w];
-    *loss = (float)(t / (double)a.B);
-    *done = 0u;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+    if (lane == 0) {
+      *loss = (float)(v / (double)a.B);
+      *done = 0u;
+    }
   }
 }
 
@@ -774,10 +787,13 @@ cudaError_t launch_hn_mask(const int32_t *ids, const int32_t *count, int B, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
-                             cudaStream_t s) {
-  const dim3 grid((unsigned)((rows_p + kPrepTile - 1) / kPrepTile), (unsigned)((dp + kPrepTile - 1) / kPrepTile));
-  k_loss_prep<<<grid, 256, 0, s>>>(X, elem, rows, d, rows_p, dp, (__nv_bfloat16 *)P, (__nv_bfloat16 *)PT);
+cudaError_t launch_loss_prep(int elem, int d, int dp, const void *X0, int rows0, int rows_p0, void *P0, void *PT0,
+                             const void *X1, int rows1, int rows_p1, void *P1, void *PT1, cudaStream_t s) {
+  const PrepJob j0{X0, rows0, rows_p0, (__nv_bfloat16 *)P0, (__nv_bfloat16 *)PT0};
+  const PrepJob j1{X1, rows1, rows_p1, (__nv_bfloat16 *)P1, (__nv_bfloat16 *)PT1};
+  const int nb0 = (rows_p0 + kPrepTile - 1) / kPrepTile, nb1 = (rows_p1 + kPrepTile - 1) / kPrepTile;
+  const dim3 grid((unsigned)(nb0 + nb1), (unsigned)((dp + kPrepTile - 1) / kPrepTile));
+  k_loss_prep<<<grid, 256, 0, s>>>(j0, j1, nb0, elem, d, dp);
   return cudaGetLastError();
 }
 
@@ -819,12 +835,12 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
 
 cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, double *bsum, uint32_t *done, float *loss,
                                 cudaStream_t s) {
-  k_loss_lse<<<(unsigned)((a.B + kLseThreads - 1) / kLseThreads), kLseThreads, 0, s>>>(a, splits, lse, bsum, done,
-                                                                                       loss);
+  if (splits > 32) return cudaErrorInvalidValue;
+  k_loss_lse<<<(unsigned)loss_combine_blocks(a.B), kLseThreads, 0, s>>>(a, splits, lse, bsum, done, loss);
   return cudaGetLastError();
 }
 
-int loss_combine_blocks(int B) { return (B + kLseThreads - 1) / kLseThreads; }
+int loss_combine_blocks(int B) { return (B + kLseQueries - 1) / kLseQueries; }
 
 cudaError_t launch_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ,
                                   cudaStream_t s) {

@@ -324,8 +324,10 @@ cudaError_t launch_hn_setup(int B, int n_neg, const uint32_t *key_cnt, int32_t *
                             cudaStream_t s);
 cudaError_t launch_hn_mask(const int32_t *ids, const int32_t *count, int B, int n_neg, int Mw, uint32_t *mask,
                            cudaStream_t s);
-cudaError_t launch_loss_prep(const void *X, int elem, int rows, int d, int rows_p, int dp, void *P, void *PT,
-                             cudaStream_t s);
+// Operand copies of two row-major matrices X0, X1 ([rows][d], BF16 or FP32) in one launch: P [rows_p][dp]
+// and/or PT [dp][rows_p] BF16, zero padded (null outputs are skipped).
+cudaError_t launch_loss_prep(int elem, int d, int dp, const void *X0, int rows0, int rows_p0, void *P0, void *PT0,
+                             const void *X1, int rows1, int rows_p1, void *P1, void *PT1, cudaStream_t s);
 cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y, const void *tm_r, const void *tm_c,
                              const void *tm_ct, cudaStream_t s);
 cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, double *bsum, uint32_t *done, float *loss,

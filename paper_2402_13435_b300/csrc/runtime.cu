@@ -1951,8 +1951,8 @@ lr_status loss_prepare(const void *Q, const void *J, int B, int M, int d, int dt
   const bool direct = dtype == LR_BF16 && d % 8 == 0 && ((uintptr_t)Q & 15u) == 0 && ((uintptr_t)J & 15u) == 0;
   LR_CK(cudaMemsetAsync(w + P.o_st, 0, 2 * sizeof(uint32_t), s));
   if (!direct || need_t) {
-    LR_CK(launch_loss_prep(Q, elem, B, d, P.Bp, P.dp, direct ? nullptr : w + P.o_qp, need_t ? w + P.o_qt : nullptr, s));
-    LR_CK(launch_loss_prep(J, elem, M, d, P.Mp, P.dp, direct ? nullptr : w + P.o_jp, need_t ? w + P.o_jt : nullptr, s));
+    LR_CK(launch_loss_prep(elem, d, P.dp, Q, B, P.Bp, direct ? nullptr : w + P.o_qp, need_t ? w + P.o_qt : nullptr, J, M,
+                           P.Mp, direct ? nullptr : w + P.o_jp, need_t ? w + P.o_jt : nullptr, s));
   }
   const int bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, sw = CU_TENSOR_MAP_SWIZZLE_128B;
   const void *qs = direct ? Q : (const void *)(w + P.o_qp), *js = direct ? J : (const void *)(w + P.o_jp);
