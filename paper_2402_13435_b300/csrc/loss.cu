@@ -20,8 +20,9 @@
 //         key list as selection keys (ordered score, ~column) -- the in-batch
 //         hard-negative mining of Sec. 5.1 ranks them.
 // dZ enters the second product as two BF16 terms (hi + lo, near-FP32 accuracy).
-// Two epilogue sets (warps 0-3 and 6-9, TMEM lane quarters) take alternate
-// streamed tiles; warp 4 issues the TMA loads, warp 5 the MMAs.  The streamed
+// Four epilogue sets of four warps (TMEM lane quarters) take the two tiles of
+// a pair, two sets per tile with 32 columns each; warp 4 issues the TMA
+// loads, warp 5 the MMAs.  The streamed
 // tiles come in pairs: one N = 128 MMA per K step scores both tiles of a pair
 // (an MMA costs about the same at N = 64 as at N = 128), into the two sets'
 // score buffers.  Tensor memory holds the scores of two pairs, so the MMAs of
@@ -44,7 +45,7 @@ namespace {
 constexpr int kRRows = 128;     // rows of the resident tile
 constexpr int kCRows = 64;      // rows of a streamed tile (one epilogue set's score columns)
 constexpr int kPairRows = 2 * kCRows;  // a pair of streamed tiles: the score MMAs' N
-constexpr int kLossThreads = 320;  // warps 0-3 and 6-9: two epilogue sets; 4: TMA; 5: MMA
+constexpr int kLossThreads = 576;  // warps 0-3, 6-9, 10-13, 14-17: four epilogue sets; 4: TMA; 5: MMA
 constexpr int kPBufsOne = 6;       // pair stages of the score-only passes (TMA latency under load is ~2 us)
 constexpr int kPBufs = 2;          // pair stages of the backward passes
 constexpr int kTBufs = 3;          // transposed-tile stages of the backward passes
@@ -71,12 +72,12 @@ struct LossSmem {
   size_t r, c, ct, dz, stage, bars, holder, total;
 };
 
-// kDj staging of one query tile for the epilogue: mask words of the CTA's 128
-// job rows (4 per query), positives and log-sum-exps of the tile's 64 queries
+// kDj staging of one epilogue set's 32 queries of a tile: mask words of the
+// CTA's 128 job rows (4 per query), positives and log-sum-exps
 struct DjStage {
-  uint32_t mask[kCRows * 4];
-  int32_t pos[kCRows];
-  float lse[kCRows];
+  uint32_t mask[32 * 4];
+  int32_t pos[32];
+  float lse[32];
 };
 
 __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
@@ -92,7 +93,7 @@ __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
   L.dz = off;
   off += one_product ? 0 : (size_t)2 * 2 * kRRows * 128;  // [buffer][hi, lo] 128 rows x 64 values
   L.stage = off;
-  off += mode == kDj ? 4 * sizeof(DjStage) : 0;  // two per epilogue set
+  off += mode == kDj ? 8 * sizeof(DjStage) : 0;  // two per epilogue set
   L.bars = off;
   off += 40 * 8;
   L.holder = off;
@@ -156,10 +157,10 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     }
     for (int i = 0; i < 4; ++i) {
       mbar_init(&s_full[i], 1);
-      mbar_init(&s_empty[i], 4);
+      mbar_init(&s_empty[i], 8);  // the two sets of the tile, four warps each
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&dz_full[i], 4);
+      mbar_init(&dz_full[i], 8);
       mbar_init(&dz_empty[i], 1);
     }
     mbar_init(acc_full, 1);
@@ -293,12 +294,14 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     __syncwarp();
   } else {
     // ---------------------------------------------------------------- epilogue
-    // two sets of four warps (0-3 and 6-9) take alternate streamed tiles: set e
-    // takes tiles e, e + 2, ..., so score buffer e and dZ buffer e are its own
-    // and their barrier phases come in order; warp w reads tensor-memory lanes
-    // 32 (w % 4) ..
-    constexpr int kSets = 2;
-    const int eset = warp >= 6 ? 1 : 0, quarter = warp & 3;
+    // four sets of four warps (0-3, 6-9, 10-13, 14-17): set e takes column
+    // half e >> 1 of the pair's tile e & 1 (tiles e & 1, e & 1 + 2, ...), so
+    // score buffer b = e & 1 and dZ buffer b are shared by two sets, each with
+    // its own 32 columns, and their barrier phases come in order; warp w reads
+    // tensor-memory lanes 32 (w % 4) ..
+    constexpr int kSets = 4;
+    const int eset = warp < 4 ? 0 : (warp - 2) >> 2, quarter = warp & 3;
+    const int b = eset & 1, half = eset >> 1;
     const int r = quarter * 32 + lane;
     const int grow = r0 + r;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -312,67 +315,54 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     }
     float m = -INFINITY, ssum = 0.f, zpos = 0.f;
     bool have_pos = false;
-    // Mask words (and for kDj the query tile's positives and lse) are fetched
-    // one tile of the set ahead.  kFwd/kDq: this row's two words, in registers.
-    // kDj: the set's 128 threads stage the query tile in shared memory (double
-    // buffered per set; each iteration ends at the set's named barrier, which
-    // every warp of the set reaches, also after a failed wait, so no warp
-    // waits forever).
-    uint32_t nw0 = ~0u, nw1 = ~0u;  // kFwd/kDq: next tile's mask words
-    uint32_t sm0 = 0u, sm1 = 0u;    // kDj: this thread's share of the next stage
+    // Mask words (and for kDj the set's 32 queries' positives and lse) are
+    // fetched one tile of the set ahead.  kFwd/kDq: this row's word of the
+    // set's 32 columns, in a register.  kDj: the set's 128 threads stage its
+    // queries in shared memory (double buffered per set; each iteration ends
+    // at the set's named barrier, which every warp of the set reaches, also
+    // after a failed wait, so no warp waits forever).
+    uint32_t nw = ~0u;  // kFwd/kDq: next tile's mask word
+    uint32_t smw = 0u;  // kDj: this thread's share of the next stage
     int spos = -1;
     float slse = 0.f;
-    auto fetch_row_words = [&](int tt) {
-      const int cc0 = (t0 + tt) * kCRows;
-      nw0 = nw1 = ~0u;
-      if (rvalid && a.mask != nullptr && cc0 < a.M) {
-        const uint32_t *mrow = a.mask + (size_t)grow * a.Mw + (cc0 >> 5);
-        nw0 = __ldg(mrow);
-        nw1 = (cc0 >> 5) + 1 < a.Mw ? __ldg(mrow + 1) : 0u;
-      }
+    auto fetch_row_word = [&](int tt) {
+      const int cc0 = (t0 + tt) * kCRows + 32 * half;
+      nw = ~0u;
+      if (rvalid && a.mask != nullptr && cc0 < a.M) nw = __ldg(a.mask + (size_t)grow * a.Mw + (cc0 >> 5));
     };
     auto fetch_stage = [&](int tt) {
-      const int cc0 = (t0 + tt) * kCRows;
-      uint32_t v[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int i = r + k * kRRows;
-        const int q = cc0 + (i >> 2), w = (r0 >> 5) + (i & 3);
-        v[k] = q < a.B && w < a.Mw ? (a.mask != nullptr ? __ldg(a.mask + (size_t)q * a.Mw + w) : ~0u) : 0u;
-      }
-      sm0 = v[0];
-      sm1 = v[1];
-      const int q = cc0 + r;
-      spos = (r < kCRows && q < a.B) ? __ldg(a.pos + q) : -1;
-      slse = (r < kCRows && q < a.B) ? __ldg(a.lse + q) * kLog2e : 0.f;  // log2 units
+      const int cq0 = (t0 + tt) * kCRows + 32 * half;
+      const int q = cq0 + (r >> 2), w = (r0 >> 5) + (r & 3);
+      smw = q < a.B && w < a.Mw ? (a.mask != nullptr ? __ldg(a.mask + (size_t)q * a.Mw + w) : ~0u) : 0u;
+      const int qq = cq0 + r;
+      spos = (r < 32 && qq < a.B) ? __ldg(a.pos + qq) : -1;
+      slse = (r < 32 && qq < a.B) ? __ldg(a.lse + qq) * kLog2e : 0.f;  // log2 units
     };
     auto store_stage = [&](int buf) {
       DjStage &st = stg[buf];
-      st.mask[r] = sm0;
-      st.mask[r + kRRows] = sm1;
-      if (r < kCRows) {
+      st.mask[r] = smw;
+      if (r < 32) {
         st.pos[r] = spos;
         st.lse[r] = slse;
       }
     };
     auto set_barrier = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + eset) : "memory"); };
     if (MODE == kDj) {
-      if (eset < T) {
-        fetch_stage(eset);
+      if (b < T) {
+        fetch_stage(b);
         store_stage(2 * eset);
       }
       set_barrier();
-    } else if (eset < T) {
-      fetch_row_words(eset);
+    } else if (b < T) {
+      fetch_row_word(b);
     }
-    for (int t = eset, it = 0; t < T; t += kSets, ++it) {
-      const int b = t & 1;                 // two sets: == eset
+    for (int t = b, it = 0; t < T; t += 2, ++it) {
       const int sb = 2 * eset + (it & 1);  // kDj: this tile's stage
-      const int c0 = (t0 + t) * kCRows;
-      const uint32_t cw0 = nw0, cw1 = nw1;
-      if (t + kSets < T) {
-        if (MODE == kDj) fetch_stage(t + kSets);
-        else fetch_row_words(t + kSets);
+      const int c0 = (t0 + t) * kCRows + 32 * half;  // first column of the set's 32
+      const uint32_t cw = nw;
+      if (t + 2 < T) {
+        if (MODE == kDj) fetch_stage(t + 2);
+        else fetch_row_word(t + 2);
       }
       do {
       if (!ok) break;
@@ -382,86 +372,74 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         break;
       }
       tc_fence_after();
-      uint32_t sv[64];
+      uint32_t sv[32];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 2; ++q) {
         uint32_t (&part)[16] = *reinterpret_cast<uint32_t (*)[16]>(&sv[16 * q]);
-        tmem_ld16(trow + (uint32_t)(slot * kPairRows + b * kCRows + 16 * q), part);
+        tmem_ld16(trow + (uint32_t)(slot * kPairRows + b * kCRows + 32 * half + 16 * q), part);
       }
       tmem_ld_wait();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&s_empty[2 * slot + b]);
-      // allowed columns of this tile: bit c of al[c / 32]; kDj also the
-      // columns whose positive is this row's job: bit c of pm[c / 32]
-      uint32_t al[2] = {0u, 0u}, pm[2] = {0u, 0u};
+      // allowed columns of the set's 32: bit c of al; kDj also the columns
+      // whose positive is this row's job: bit c of pm
+      uint32_t al = 0u, pm = 0u;
       if (MODE == kDj) {
-        // the tile's 64 queries x this warp's 32 jobs as two 32 x 32 bit
-        // matrices, one query per lane (lane, lane + 32), transposed so that
-        // lane r holds its job's column
+        // the set's 32 queries x this warp's 32 jobs as a 32 x 32 bit matrix,
+        // one query per lane, transposed so that lane r holds its job's row
         const DjStage &st = stg[sb];
         const int wj = (r0 >> 5) + quarter;
-        uint32_t mw[2], pw[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int p = st.pos[lane + 32 * h];
-          pw[h] = (p >= 0 && (p >> 5) == wj) ? 1u << (p & 31) : 0u;
-          mw[h] = st.mask[(lane + 32 * h) * 4 + quarter] | pw[h];  // the positive is always allowed
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {  // every lane takes part in the transposes
-          pm[h] = bit_transpose32(pw[h], lane);
-          const uint32_t t = bit_transpose32(mw[h], lane);
-          al[h] = rvalid ? t : 0u;
-        }
+        const int p = st.pos[lane];
+        const uint32_t pw = (p >= 0 && (p >> 5) == wj) ? 1u << (p & 31) : 0u;
+        const uint32_t mw = st.mask[lane * 4 + quarter] | pw;  // the positive is always allowed
+        pm = bit_transpose32(pw, lane);  // every lane takes part in the transposes
+        const uint32_t tr = bit_transpose32(mw, lane);
+        al = rvalid ? tr : 0u;
       } else if (rvalid) {
-        uint32_t w0 = cw0, w1 = cw1;
+        uint32_t w0 = cw;
         const int lim = a.M - c0;  // columns past M do not exist
         w0 &= lim >= 32 ? ~0u : (lim > 0 ? ((1u << lim) - 1u) : 0u);
-        w1 &= lim >= 64 ? ~0u : (lim > 32 ? ((1u << (lim - 32)) - 1u) : 0u);
         const int pc = pos_row - c0;
         if (pc >= 0 && pc < 32) w0 |= 1u << pc;
-        if (pc >= 32 && pc < 64) w1 |= 1u << (pc - 32);
-        al[0] = w0;
-        al[1] = w1;
+        al = w0;
       }
       if (MODE == kFwd) {
-        if (pos_row >= c0 && pos_row < c0 + 64) {
+        if (pos_row >= c0 && pos_row < c0 + 32) {
           const int pc = pos_row - c0;
 #pragma unroll
-          for (int c = 0; c < 64; ++c)
+          for (int c = 0; c < 32; ++c)
             if (c == pc) zpos = __uint_as_float(sv[c]) * a.inv_tau;
           have_pos = true;
         }
-        // the running maximum m is in log2 units; failing columns become -inf,
-        // whose exponential is 0
         // ssum = sum of 2^(z2 - m) over the allowed columns seen, z2 = s inv_tau
-        // log2(e).  The offset m is the maximum of the row's first tile with
-        // an allowed column and stays fixed (one FMA, one exponential per
-        // column) unless a later tile's terms would overflow: that tile is
-        // redone with its own maximum as the new offset.
+        // log2(e) (log2 units; failing columns add 0).  The offset m is the
+        // maximum of the set's first tile of the row with an allowed column
+        // and stays fixed (one FMA, one exponential per column) unless a
+        // later tile's terms would overflow: that tile is redone with its own
+        // maximum as the new offset.
         const float c2 = a.inv_tau * kLog2e;
         auto tile_max = [&]() {
           float tmax = -INFINITY;
 #pragma unroll
-          for (int c = 0; c < 64; ++c)
-            if ((al[c >> 5] >> (c & 31)) & 1u) tmax = fmaxf(tmax, __uint_as_float(sv[c]) * c2);
+          for (int c = 0; c < 32; ++c)
+            if ((al >> c) & 1u) tmax = fmaxf(tmax, __uint_as_float(sv[c]) * c2);
           return tmax;
         };
         if (m == -INFINITY) m = tile_max();
         if (m > -INFINITY) {
           float add = 0.f;
 #pragma unroll
-          for (int c = 0; c < 64; ++c)
-            add += ((al[c >> 5] >> (c & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -m)) : 0.f;
+          for (int c = 0; c < 32; ++c)
+            add += ((al >> c) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -m)) : 0.f;
           if (add < 0x1p100f) {
             ssum += add;
           } else {  // overflow or near it: rescale to this tile's maximum
             const float mn = fmaxf(m, tile_max());
             add = 0.f;
 #pragma unroll
-            for (int c = 0; c < 64; ++c)
-              add += ((al[c >> 5] >> (c & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -mn)) : 0.f;
+            for (int c = 0; c < 32; ++c)
+              add += ((al >> c) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -mn)) : 0.f;
             ssum = ssum * ex2_approx(m - mn) + add;
             m = mn;
           }
@@ -470,21 +448,21 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         if (rvalid) {
           // allowed columns without the positive (al has no column past M),
           // appended to the row's key list in place of the tile's range
-          uint32_t nb[2] = {al[0], al[1]};
+          uint32_t nb = al;
           const int pc = pos_row - c0;
-          if (pc >= 0 && pc < 32) nb[0] &= ~(1u << pc);
-          if (pc >= 32 && pc < 64) nb[1] &= ~(1u << (pc - 32));
-          const uint32_t cntk = (uint32_t)(__popc(nb[0]) + __popc(nb[1]));
+          if (pc >= 0 && pc < 32) nb &= ~(1u << pc);
+          const uint32_t cntk = (uint32_t)__popc(nb);
           if (cntk) {
             uint32_t o = atomicAdd(&a.key_cnt[grow], cntk);
             uint64_t *krow = a.keys + (size_t)grow * (size_t)a.keys_ld;
 #pragma unroll
-            for (int c = 0; c < 64; ++c)
-              if ((nb[c >> 5] >> (c & 31)) & 1u) krow[o++] = make_key(__uint_as_float(sv[c]), (uint32_t)(c0 + c));
+            for (int c = 0; c < 32; ++c)
+              if ((nb >> c) & 1u) krow[o++] = make_key(__uint_as_float(sv[c]), (uint32_t)(c0 + c));
           }
         }
       } else {
-        // dZ of this tile as two BF16 terms, written in the 128-byte-swizzled K-major layout
+        // dZ of the set's 32 columns as two BF16 terms, written in the
+        // 128-byte-swizzled K-major layout of the tile (chunks 4 half .. 4 half + 3)
         if (!wwait(&dz_empty[b], (uint32_t)((t >> 1) & 1) ^ 1u, lane)) {
           ok = false;
           break;
@@ -496,16 +474,15 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         // dL / B is applied to the accumulated product); here the softmax
         // term, the positives' -1 after the tile is written
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
+        for (int ch = 0; ch < 4; ++ch) {
           uint32_t hw[4], lw[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int c = ch * 8 + u * 2;  // columns c, c + 1
+            const int c = ch * 8 + u * 2;  // columns c, c + 1 of the set's 32
             const float l0 = MODE == kDq ? lse_row : stg[sb].lse[c];  // log2 units
             const float l1 = MODE == kDq ? lse_row : stg[sb].lse[c + 1];
-            const float p0 = ((al[c >> 5] >> (c & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -l0)) : 0.f;
-            const float p1 =
-                ((al[c >> 5] >> ((c + 1) & 31)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c + 1]), c2, -l1)) : 0.f;
+            const float p0 = ((al >> c) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c]), c2, -l0)) : 0.f;
+            const float p1 = ((al >> (c + 1)) & 1u) ? ex2_approx(fmaf(__uint_as_float(sv[c + 1]), c2, -l1)) : 0.f;
             // hi = p truncated to BF16 (its upper 16 bits), lo = p - hi (exact)
             // rounded to nearest: p = hi + lo within 2^-15 p
             const uint32_t u0 = __float_as_uint(p0), u1 = __float_as_uint(p1);
@@ -514,9 +491,9 @@ __global__ void __launch_bounds__(kLossThreads, 1)
             hw[u] = __byte_perm(u0, u1, 0x7632);
             lw[u] = *reinterpret_cast<const uint32_t *>(&lv);
           }
-          const int slot = ((ch ^ (r & 7)) & 7) << 4;
-          *reinterpret_cast<uint4 *>(dh + slot) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4 *>(dl + slot) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          const int so = (((4 * half + ch) ^ (r & 7)) & 7) << 4;
+          *reinterpret_cast<uint4 *>(dh + so) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4 *>(dl + so) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         // column c of this row is a positive (an allowed column: the positive
         // always is): its entry becomes p - 1, computed in FP32 from the
@@ -524,23 +501,22 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         auto patch = [&](int c, float lse2) {
           float sc = 0.f;
 #pragma unroll
-          for (int k = 0; k < 64; ++k) sc = k == c ? __uint_as_float(sv[k]) : sc;
+          for (int k = 0; k < 32; ++k) sc = k == c ? __uint_as_float(sv[k]) : sc;
           const float v = ex2_approx(fmaf(sc, c2, -lse2)) - 1.f;
           const __nv_bfloat16 nh = __float2bfloat16_rn(v);
-          const int so = ((((c >> 3) ^ (r & 7)) & 7) << 4) | ((c & 7) << 1);
+          const int gc = 32 * half + c;
+          const int so = ((((gc >> 3) ^ (r & 7)) & 7) << 4) | ((gc & 7) << 1);
           *reinterpret_cast<__nv_bfloat16 *>(dh + so) = nh;
           *reinterpret_cast<__nv_bfloat16 *>(dl + so) = __float2bfloat16_rn(v - __bfloat162float(nh));
         };
         if (MODE == kDq) {
           const int pc = pos_row - c0;
-          if (pc >= 0 && pc < kCRows) patch(pc, lse_row);
+          if (pc >= 0 && pc < 32) patch(pc, lse_row);
         } else {
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-            for (uint32_t w = pm[h] & al[h]; w != 0u; w &= w - 1u) {
-              const int c = 32 * h + __ffs(w) - 1;
-              patch(c, stg[sb].lse[c]);
-            }
+          for (uint32_t w = pm & al; w != 0u; w &= w - 1u) {
+            const int c = __ffs(w) - 1;
+            patch(c, stg[sb].lse[c]);
+          }
         }
         fence_proxy_async();
         __syncwarp();
@@ -554,13 +530,13 @@ __global__ void __launch_bounds__(kLossThreads, 1)
     }
     if (MODE == kFwd) {  // the row's log-sum-exp partial of this split and set
       if (rvalid) {
-        const size_t part = (size_t)(2 * blockIdx.y + eset) * a.rows_p + grow;
+        const size_t part = (size_t)(kSets * blockIdx.y + eset) * a.rows_p + grow;
         a.part_m[part] = m * kLn2;  // natural units for the combine
         a.part_s[part] = ssum;
         if (have_pos) a.zpos[grow] = zpos;
       }
     } else if (MODE == kKeys) {
-    } else {  // both sets write the accumulated rows, set e its half
+    } else {  // the four sets write the accumulated rows, set e its quarter
       if (!wwait(acc_full, 0u, lane)) ok = false;
       tc_fence_after();
       const uint32_t acc = trow + 2u * kPairRows;
@@ -568,36 +544,34 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       if (swap) {
         // lane k (= this thread's TMEM lane) holds column k of every row: rows
         // r and 128 + r are the hi and lo halves; a warp's 32 lanes write 32
-        // consecutive columns of a row.  Set e takes rows [64 e, 64 e + 64),
-        // 32 at a time (four loads in flight per wait).
+        // consecutive columns of a row.  Set e takes rows [32 e, 32 e + 32)
+        // (four loads in flight per wait).
         const int k = quarter * 32 + lane;
         float *ocol = a.out + (size_t)blockIdx.y * a.out_split + k;
         const int rows_ok = MODE == kDq ? a.rows_p : a.M;
-        for (int rr = 64 * eset; rr < 64 * eset + 64; rr += 32) {
-          uint32_t vh[32], vl[32];
-          tmem_ld16(acc + (uint32_t)rr, *reinterpret_cast<uint32_t (*)[16]>(&vh[0]));
-          tmem_ld16(acc + (uint32_t)(rr + 16), *reinterpret_cast<uint32_t (*)[16]>(&vh[16]));
-          tmem_ld16(acc + (uint32_t)(kRRows + rr), *reinterpret_cast<uint32_t (*)[16]>(&vl[0]));
-          tmem_ld16(acc + (uint32_t)(kRRows + rr + 16), *reinterpret_cast<uint32_t (*)[16]>(&vl[16]));
-          tmem_ld_wait();
-          if (ok && k < a.out_cols)
+        const int rr = 32 * eset;
+        uint32_t vh[32], vl[32];
+        tmem_ld16(acc + (uint32_t)rr, *reinterpret_cast<uint32_t (*)[16]>(&vh[0]));
+        tmem_ld16(acc + (uint32_t)(rr + 16), *reinterpret_cast<uint32_t (*)[16]>(&vh[16]));
+        tmem_ld16(acc + (uint32_t)(kRRows + rr), *reinterpret_cast<uint32_t (*)[16]>(&vl[0]));
+        tmem_ld16(acc + (uint32_t)(kRRows + rr + 16), *reinterpret_cast<uint32_t (*)[16]>(&vl[16]));
+        tmem_ld_wait();
+        if (ok && k < a.out_cols)
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (r0 + rr + i < rows_ok)
-                ocol[(size_t)(r0 + rr + i) * a.out_ld] = (__uint_as_float(vh[i]) + __uint_as_float(vl[i])) * scale;
-        }
+          for (int i = 0; i < 32; ++i)
+            if (r0 + rr + i < rows_ok)
+              ocol[(size_t)(r0 + rr + i) * a.out_ld] = (__uint_as_float(vh[i]) + __uint_as_float(vl[i])) * scale;
       } else {
-        // thread r holds row r: set e writes columns [e dp / 2, (e + 1) dp / 2)
+        // thread r holds row r: set e writes columns [e dp / 4, (e + 1) dp / 4)
         float *orow = a.out + (size_t)blockIdx.y * a.out_split + (size_t)grow * a.out_ld;
         const bool wr = ok && (MODE == kDq ? grow < a.rows_p : grow < a.M);
-        for (int c = eset * (dp / 2); c < (eset + 1) * (dp / 2); c += 32) {
-          uint32_t v[32];
-          tmem_ld16(acc + (uint32_t)c, *reinterpret_cast<uint32_t (*)[16]>(&v[0]));
-          tmem_ld16(acc + (uint32_t)(c + 16), *reinterpret_cast<uint32_t (*)[16]>(&v[16]));
+        for (int c = eset * (dp / 4); c < (eset + 1) * (dp / 4); c += 16) {
+          uint32_t v[16];
+          tmem_ld16(acc + (uint32_t)c, v);
           tmem_ld_wait();
           if (wr)
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
+            for (int i = 0; i < 16; i += 4)
               *reinterpret_cast<float4 *>(orow + c + i) =
                   make_float4(__uint_as_float(v[i]) * scale, __uint_as_float(v[i + 1]) * scale,
                               __uint_as_float(v[i + 2]) * scale, __uint_as_float(v[i + 3]) * scale);
@@ -670,13 +644,13 @@ __global__ void __launch_bounds__(256) k_loss_prep(const PrepJob j0, const PrepJ
   }
 }
 
-// Per query (one warp each, lane s reads partial s, so the partials load in
-// one round): combine the split partials into its log-sum-exp; each block
+// Per query (one warp each, lane s reads partials s and s + 32, so the
+// partials load in one round): combine the split partials into its log-sum-exp; each block
 // sums its queries' terms lse - z_pos in FP64 in a fixed order, and the last
 // block to finish adds the blocks' sums in block order (the loss does not
 // depend on the blocks' timing).  An out-of-range positive makes the loss
 // NaN.  done[0] counts finished blocks (zero before the launch; the last block
-// resets it).  At most 32 partials per query.
+// resets it).  At most 64 partials per query.
 constexpr int kLseThreads = 256;
 constexpr int kLseQueries = kLseThreads / 32;
 
@@ -688,12 +662,16 @@ __global__ void __launch_bounds__(kLseThreads) k_loss_lse(const LossArgs a, int 
   const int q = blockIdx.x * kLseQueries + w;
   double term = 0.0;
   if (q < a.B) {
+    const int s1 = lane + 32;
     const float ms = lane < splits ? a.part_m[(size_t)lane * a.rows_p + q] : -INFINITY;
     const float ss = lane < splits ? a.part_s[(size_t)lane * a.rows_p + q] : 0.f;
-    float mx = ms;
+    const float ms1 = s1 < splits ? a.part_m[(size_t)s1 * a.rows_p + q] : -INFINITY;
+    const float ss1 = s1 < splits ? a.part_s[(size_t)s1 * a.rows_p + q] : 0.f;
+    float mx = fmaxf(ms, ms1);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
-    float sum = ms > -INFINITY ? ss * exp2f((ms - mx) * kLog2e) : 0.f;
+    float sum = (ms > -INFINITY ? ss * exp2f((ms - mx) * kLog2e) : 0.f) +
+                (ms1 > -INFINITY ? ss1 * exp2f((ms1 - mx) * kLog2e) : 0.f);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
     const float l = mx + logf(sum);
@@ -835,7 +813,7 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
 
 cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, double *bsum, uint32_t *done, float *loss,
                                 cudaStream_t s) {
-  if (splits > 32) return cudaErrorInvalidValue;
+  if (splits > 64) return cudaErrorInvalidValue;
   k_loss_lse<<<(unsigned)loss_combine_blocks(a.B), kLseThreads, 0, s>>>(a, splits, lse, bsum, done, loss);
   return cudaGetLastError();
 }

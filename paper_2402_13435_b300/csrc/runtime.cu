@@ -1903,8 +1903,8 @@ LossPlan loss_plan(int B, int M, int d, int sms) {
   P.o_qt = cv.take<uint16_t>((size_t)P.Bp * P.dp);
   P.o_jp = cv.take<uint16_t>((size_t)P.Mp * P.dp);
   P.o_jt = cv.take<uint16_t>((size_t)P.Mp * P.dp);
-  P.o_pm = cv.take<float>((size_t)2 * P.splits * P.Bp);  // one partial per split and epilogue set
-  P.o_ps = cv.take<float>((size_t)2 * P.splits * P.Bp);
+  P.o_pm = cv.take<float>((size_t)4 * P.splits * P.Bp);  // one partial per split and epilogue set
+  P.o_ps = cv.take<float>((size_t)4 * P.splits * P.Bp);
   P.o_zp = cv.take<float>(P.Bp);
   P.o_dq = cv.take<float>((size_t)P.splits * P.Bp * P.dp);
   P.o_dj = cv.take<float>((size_t)P.splits_j * P.Mp * P.dp);
@@ -2013,7 +2013,7 @@ lr_status lr_score_forward(const void *Q, const void *J, int32_t B, int32_t M, i
   if (st != LR_OK) return st;
   LossArgs a = loss_args(B, M, inv_tau, pos, mask_bits, w, P);
   LR_CK(launch_loss_pass(0, a, P.Bp / 128, P.splits, &T.qr, &T.jc, nullptr, s));
-  LR_CK(launch_loss_combine(a, 2 * P.splits, lse, (double *)(w + P.o_bs), (uint32_t *)(w + P.o_st) + 1, loss, s));
+  LR_CK(launch_loss_combine(a, 4 * P.splits, lse, (double *)(w + P.o_bs), (uint32_t *)(w + P.o_st) + 1, loss, s));
   return LR_OK;
 }
 
