@@ -25,9 +25,10 @@
 // loads, warp 5 the MMAs.  The streamed
 // tiles come in pairs: one N = 128 MMA per K step scores both tiles of a pair
 // (an MMA costs about the same at N = 64 as at N = 128), into the two sets'
-// score buffers.  Tensor memory holds the scores of two pairs, so the MMAs of
-// pair p + 2 are queued behind the second products of pair p and the sets
-// find pair p + 1 scored when they finish pair p.
+// score buffers.  Tensor memory holds the scores of two pairs (four in the
+// score-only passes, which have no accumulator), so the MMAs of pair p + 2 are
+// queued behind the second products of pair p and the sets find pair p + 1
+// scored when they finish pair p.
 // The streamed operand and its transposed copy (the second product's
 // operand) sit in separate rings: a pair's stage is free once it is scored, a
 // transposed tile's once its product is done.
@@ -52,7 +53,7 @@ constexpr int kTBufs = 3;          // transposed-tile stages of the backward pas
 // tensor memory: two pair slots of 128 score columns, then (backward) the
 // accumulator at column 256: [128 rows][dp], or at dp = 128 the transposed
 // product's [dp lanes][hi rows | lo rows], 256 columns
-constexpr uint32_t kLossTmemColsOne = 256;
+constexpr uint32_t kLossTmemColsOne = 512;  // score-only passes: four pair slots
 constexpr uint32_t kLossTmemCols = 512;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -95,7 +96,7 @@ __host__ __device__ inline LossSmem loss_smem(int dp, int mode) {
   L.stage = off;
   off += mode == kDj ? 8 * sizeof(DjStage) : 0;  // two per epilogue set
   L.bars = off;
-  off += 40 * 8;
+  off += 48 * 8;
   L.holder = off;
   L.total = off + 16;
   return L;
@@ -126,8 +127,11 @@ __global__ void __launch_bounds__(kLossThreads, 1)
   constexpr int nP = kOne ? kPBufsOne : kPBufs;  // pair stages
   uint64_t *bar_r = bars, *c_full = bars + 1, *c_empty = c_full + nP;  // [nP] each
   uint64_t *t_full = c_empty + nP, *t_empty = t_full + kTBufs;       // [kTBufs] each
-  uint64_t *s_full = t_empty + kTBufs, *s_empty = s_full + 4;        // [pair slot][epilogue set]
-  uint64_t *dz_full = s_empty + 4, *dz_empty = dz_full + 2, *acc_full = dz_empty + 2;
+  // pair slots of scores in tensor memory: four in the score-only passes (no
+  // accumulator), two in the backward passes
+  constexpr int kSlots = kOne ? 4 : 2;
+  uint64_t *s_full = t_empty + kTBufs, *s_empty = s_full + 2 * kSlots;  // [pair slot][tile of the pair]
+  uint64_t *dz_full = s_empty + 2 * kSlots, *dz_empty = dz_full + 2, *acc_full = dz_empty + 2;
   uint32_t *holder = reinterpret_cast<uint32_t *>(smem + L.holder);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r0 = blockIdx.x * kRRows;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       mbar_init(&t_full[i], 1);
       mbar_init(&t_empty[i], 1);
     }
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2 * kSlots; ++i) {
       mbar_init(&s_full[i], 1);
       mbar_init(&s_empty[i], 8);  // the two sets of the tile, four warps each
     }
@@ -230,14 +234,14 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       const uint32_t id_t = idesc_bf16(128, 2 * kRRows);  // the transposed product: M = dp = 128, N = 256
       const uint32_t acc = tmem + 2u * kPairRows;
       bool issued = false;
-      // scores of pair p into slot j = p & 1: tile 2p into columns
-      // [128 j, 128 j + 64) (set 0), tile 2p + 1 into the next 64 (set 1),
-      // once both sets have read pair p - 2's
+      // scores of pair p into slot j = p % kSlots: tile 2p into columns
+      // [128 j, 128 j + 64), tile 2p + 1 into the next 64, once the sets have
+      // read pair p - kSlots's
       auto issue_pair = [&](int p) -> bool {
-        const int st = p % nP, nt = min(2, T - 2 * p), j = p & 1;
+        const int st = p % nP, nt = min(2, T - 2 * p), j = p % kSlots;
         if (!mbar_wait(&c_full[st], (uint32_t)((p / nP) & 1))) return false;
         for (int h = 0; h < nt; ++h)
-          if (!mbar_wait(&s_empty[2 * j + h], (uint32_t)((p >> 1) & 1) ^ 1u)) return false;
+          if (!mbar_wait(&s_empty[2 * j + h], (uint32_t)((p / kSlots) & 1) ^ 1u)) return false;
         tc_fence_after();
         const uint32_t ra = smem_u32(sr), ca = smem_u32(sc + (size_t)st * p_bytes);
         for (int k = 0; k < dp / 16; ++k) {
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
         return true;
       };
       if (!mbar_wait(bar_r, 0u)) ok = false;
-      for (int p = 0; p < 2 && p < NP && ok; ++p) ok = issue_pair(p);
+      for (int p = 0; p < kSlots && p < NP && ok; ++p) ok = issue_pair(p);
       for (int p = 0; p < NP && ok; ++p) {
         for (int h = 0; h < 2 && 2 * p + h < T && !kOne; ++h) {
           const int t = 2 * p + h, st = t % kTBufs;
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(kLossThreads, 1)
           mma_commit(&dz_empty[h]);
           mma_commit(&t_empty[st]);
         }
-        if (ok && p + 2 < NP && !issue_pair(p + 2)) ok = false;
+        if (ok && p + kSlots < NP && !issue_pair(p + kSlots)) ok = false;
       }
       if (issued) {  // every MMA has completed before the epilogue reads the accumulator / TMEM is freed
         mma_commit(acc_full);
@@ -366,8 +370,8 @@ __global__ void __launch_bounds__(kLossThreads, 1)
       }
       do {
       if (!ok) break;
-      const int slot = (t >> 1) & 1;  // pair slot of this tile's scores
-      if (!wwait(&s_full[2 * slot + b], (uint32_t)((t >> 2) & 1), lane)) {
+      const int slot = (t >> 1) % kSlots;  // pair slot of this tile's scores
+      if (!wwait(&s_full[2 * slot + b], (uint32_t)(((t >> 1) / kSlots) & 1), lane)) {
         ok = false;
         break;
       }
