@@ -865,37 +865,54 @@ bool estimate_pass_rates(const lr_index *ix, const lr_filters *f, int B, std::ve
 }
 
 // Scan plan for LR_PLAN_AUTO from the estimated pass rates s_q: the union of a
-// launch's queries is u = 1 - prod_q (1 - s_q).  Estimated times, calibrated
-// on the 10M x 128 FP32 selectivity sweep and scaled by the rows:
-//   SIMT scan, per launch of up to 8 queries: a floor for the predicate over
-//     every 256-row group (0.115 ms per 10M rows) plus the union's rows
-//     gathered at an effective 2.0 TB/s when they are scattered (u <= 10 %),
-//     rising to 5.8 TB/s as they become contiguous (u = 50 %);
+// launch's queries is u = 1 - prod_q (1 - s_q).  Estimated times, fitted to
+// the 10M x 128 FP32 selectivity sweep (each plan forced, batches 1 to 1,024)
+// and scaled by the rows:
+//   SIMT scan, per launch of up to 8 queries: ~55 us of threshold sample and
+//     selections, the predicate's visit of every 256-row group (50 us + 2 us
+//     per query per 10M rows), and the union's rows at 6.9 TB/s (up to four
+//     queries) or 5.3 TB/s (more: the FMAs per row count), down to 60 % of
+//     that when the rows are scattered (u -> 0), each passing row costing
+//     ~18 ps more in the sample and the selections; a row costs at least the
+//     FMAs of its d values per query, as an FP32 row of d values would;
 //   tensor-core scan: the tile filter (60 us per 10M rows) plus, per launch of
 //     up to 64 queries, the listed tiles (a tile is listed when one of its 128
-//     rows passes: 1 - (1 - u)^128 of them) streamed at 5.2 TB/s;
+//     rows passes: 1 - (1 - u)^128 of them) streamed at 5.2 TB/s; FP32 rows
+//     above 64 queries run one 128-query launch at 2.0 TB/s of rows (up to
+//     128 queries) or 96-query launches at 3.5 TB/s of rows, each with
+//     ~0.25 ms per 10M rows of filters and selections;
 //   and each plan's fixed launches (prep, expansion, sample, selection and the
-//     exact fallback's early-exit launches): ~30 us for the scans.
+//     exact fallback's early-exit launches): ~30 us.
 // Without estimates the batch size decides (>= 16 queries: tensor cores).
-double gemv_time_s(int64_t n, double rb, int B, const std::vector<double> &s) {
+double gemv_time_s(int64_t n, double rb, int dp, int B, const std::vector<double> &s) {
+  const double scale = (double)n / 1e7;
   double t = 30e-6;
   for (int b0 = 0; b0 < B; b0 += kGemvMaxQ) {
+    const int nq = std::min(B, b0 + kGemvMaxQ) - b0;
     double none = 1.0;
-    for (int b = b0; b < std::min(B, b0 + kGemvMaxQ); ++b) none *= 1.0 - s[b];
+    for (int b = b0; b < b0 + nq; ++b) none *= 1.0 - s[b];
     const double u = 1.0 - none;
-    const double bw = u <= 0.1 ? 2.0e12 : u >= 0.5 ? 5.8e12 : 2.0e12 + (u - 0.1) / 0.4 * 3.8e12;
-    t += 0.115e-3 * (double)n / 1e7 + u * (double)n * rb / bw;
+    const double bw = (nq <= 4 ? 6.9e12 : 5.3e12) * (u < 0.1 ? 0.6 + 4.0 * u : 1.0);
+    const double row_bytes = std::max(rb, 0.5 * dp * nq);  // FMA floor: an FP32 row at eight queries
+    t += 55e-6 + (50e-6 + 2e-6 * nq) * scale + u * (double)n * (row_bytes / bw + 1.8e-11);
   }
   return t;
 }
 
-double tc_time_s(int64_t n, double rb, int B, const std::vector<double> &s) {
-  double t = 30e-6 + 60e-6 * (double)n / 1e7;
-  for (int b0 = 0; b0 < B; b0 += kTcMaxQ) {
+double tc_time_s(int64_t n, double rb, bool fp32, int B, const std::vector<double> &s) {
+  const double scale = (double)n / 1e7;
+  double t = 30e-6 + 60e-6 * scale;
+  const bool blocks = fp32 && B > kTcMaxQ;
+  const int per = !blocks ? kTcMaxQ : B <= 2 * kTcMaxQ ? 2 * kTcMaxQ : 96;
+  for (int b0 = 0; b0 < B; b0 += per) {
     double none = 1.0;
-    for (int b = b0; b < std::min(B, b0 + kTcMaxQ); ++b) none *= 1.0 - s[b];
+    for (int b = b0; b < std::min(B, b0 + per); ++b) none *= 1.0 - s[b];
     const double u = 1.0 - none;
-    t += (1.0 - std::pow(1.0 - u, 128.0)) * (double)n * rb / 5.2e12 + 10e-6;
+    const double tiles = (1.0 - std::pow(1.0 - u, 128.0)) * (double)n * rb;
+    if (!blocks)
+      t += tiles / 5.2e12 + 10e-6;
+    else
+      t += tiles / (per == 96 ? 3.5e12 : 2.0e12) + 0.25e-3 * scale;
   }
   return t;
 }
@@ -904,7 +921,8 @@ int choose_plan(const lr_index *ix, int B, bool tc_ok, bool have_est, const std:
   if (!tc_ok) return LR_PLAN_GEMV;
   if (!have_est) return B >= kTcMinBatch ? LR_PLAN_TC : LR_PLAN_GEMV;
   const double rb = 4.0 * ix->d_pad * (ix->elem == kElemF32 ? 1.0 : ix->elem == kElemBF16 ? 0.5 : 0.25);
-  return tc_time_s(ix->n, rb, B, s) < gemv_time_s(ix->n, rb, B, s) ? LR_PLAN_TC : LR_PLAN_GEMV;
+  const bool fp32 = ix->elem == kElemF32;
+  return tc_time_s(ix->n, rb, fp32, B, s) < gemv_time_s(ix->n, rb, ix->d_pad, B, s) ? LR_PLAN_TC : LR_PLAN_GEMV;
 }
 
 // TBR-first choice per query: the clause whose distinct terms have the fewest
@@ -960,16 +978,22 @@ TbrPlan plan_tbr(const lr_index *ix, const lr_filters *f, int B, int64_t cap) {
 
 // Estimated time of the TBR-first plan against the scans' (choose_plan): the
 // postings and their bit tests (term words mostly L2 hits: ~16 B of traffic
-// per posting at 3.2 TB/s), the passing rows gathered in FP32 at 2 TB/s, and a
-// fixed 12 us (five launches, against the scans' dozen).  TBR first is taken
-// when it is estimated at less than half the cheaper scan.
+// per posting at 3.2 TB/s), the passing rows gathered in FP32 at 2 TB/s, the
+// selection of every passing row as a candidate (one CTA per query, ~1.1 ns
+// per candidate of the largest list: 0.14 ms for a 1 % filter over 10M rows),
+// and a fixed 12 us (five launches, against the scans' dozen).  TBR first is
+// taken when it is estimated at less than half the cheaper scan.
 bool tbr_cheaper(const lr_index *ix, int B, const TbrPlan &T, const std::vector<double> &est, bool tc_ok) {
   const double rb = 4.0 * ix->d_pad, n = (double)ix->n;
-  double tbr = 12e-6;
-  for (int b = 0; b < B; ++b) tbr += 16.0 * (double)T.postings[b] / 3.2e12 + est[b] * n * 4.0 * ix->d_pad / 2.0e12;
+  double tbr = 12e-6, cand_max = 0.0;
+  for (int b = 0; b < B; ++b) {
+    tbr += 16.0 * (double)T.postings[b] / 3.2e12 + est[b] * n * 4.0 * ix->d_pad / 2.0e12;
+    cand_max = std::max(cand_max, est[b] * n);
+  }
+  tbr += 1.1e-9 * cand_max;
   const double rbs = rb * (ix->elem == kElemF32 ? 1.0 : ix->elem == kElemBF16 ? 0.5 : 0.25);
-  const double gemv = gemv_time_s(ix->n, rbs, B, est);
-  const double scan = tc_ok ? std::min(gemv, tc_time_s(ix->n, rbs, B, est)) : gemv;
+  const double gemv = gemv_time_s(ix->n, rbs, ix->d_pad, B, est);
+  const double scan = tc_ok ? std::min(gemv, tc_time_s(ix->n, rbs, ix->elem == kElemF32, B, est)) : gemv;
   return tbr < 0.5 * scan;
 }
 

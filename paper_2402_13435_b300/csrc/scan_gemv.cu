@@ -12,22 +12,27 @@
 //     memory, and lane q evaluates query q's CNF (AND over clauses of OR over
 //     terms) word-wise.
 //   * Rows nobody passes are never read from HBM ("skip rows").  Passing rows
-//     are compacted into 32-row batches (the messenger: job id + mask of the
-//     queries that pass it) and fetched asynchronously.
-//   * Lane i scores row i of a batch against every query of the launch: a
-//     sequential FP32 FMA chain over the dimensions, row data from shared
-//     memory (rows sit 16 bytes apart beyond their length, so the 32 lanes'
-//     16-byte loads hit distinct banks) and query values broadcast from shared
-//     memory.  A score is therefore computed the same way whatever other
-//     queries share the launch.
+//     are compacted into 32-row lists (the messenger: job id + mask of the
+//     queries that pass it) in shared memory.
+//   * Rows go straight from HBM into registers: lane l holds dimensions
+//     [l d/32, (l + 1) d/32) of every row and of every query, so one row is one
+//     coalesced warp-wide load (d x element bytes).  A round takes R rows
+//     (R x NQ <= 32 row-query pairs); each lane forms its partial dot product of
+//     every pair (a sequential FP32 FMA chain over its d/32 values), and a
+//     butterfly over the lanes (offsets 16, 8, 4, 2, 1, each step halving the
+//     pairs a lane carries) leaves every pair's full sum in one lane.  The
+//     butterfly always combines lanes in the same order, so a pair's score does
+//     not depend on which other queries or rows share the launch or the round.
+//     The next round's rows are loaded while the current one is reduced.
+//   * No row data sits in shared memory (only the 32-row list and the term
+//     words), so many warps fit on an SM and keep rows in flight.
 //   * Candidates (mode kCollect): the 64-bit key (score, ~id) of each passing
 //     pair is compared with the query's threshold and appended to the query's
 //     buffer when it is not below it.  Mode kHist instead histograms one 11-bit
 //     digit of the keys that match the query's prefix (exact radix selection);
 //     the last CTA to finish fixes the digit for every query.
-//
-// Every mbarrier wait is bounded (ptx.h); a wait that gives up records
-// LR_ERR_TIMEOUT in the error word.
+#include <atomic>
+
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -39,176 +44,172 @@ namespace lr {
 namespace {
 
 constexpr int kChunkGroups = 2;  // groups handed out per work-counter grab
-
-// Per-warp pipeline (every warp of the CTA runs one independently):
-//   * take 256-row groups from the global work counter (chunks of kChunkGroups);
-//   * term words of the next group are prefetched with cp.async while the
-//     current group is processed (one commit group per prefetch);
-//   * lane q evaluates query q's CNF over the group's 8 words;
-//   * passing rows are packed into 32-row batches -- the paper's messenger: a
-//     slot holds the job id and the bit mask of the queries that pass it -- and
-//     each row is fetched by one warp-wide cp.async (16 bytes per lane, one
-//     coalesced request per row) into a padded shared-memory slot;
-//   * completion of a batch's copies is counted on the batch buffer's mbarrier
-//     (cp.async.mbarrier.arrive.noinc from every lane), and the previous batch is
-//     scored while the current one is in flight (double buffering).
-struct WarpLayout {
-  size_t row_stride, buf_bytes, per_warp, bars, meta, slots, rows, queries, total;
-};
-
-__host__ __device__ inline size_t w_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr int kWarps = 8;        // warps per CTA (each runs its own pipeline)
 
 __host__ __device__ constexpr int elem_bytes(int e) { return e == kElemF32 ? 4 : e == kElemBF16 ? 2 : 1; }
 
-__host__ __device__ inline WarpLayout warp_layout(int d_pad, int esz, int nq_tmpl, int n_slots, int warps) {
-  WarpLayout L;
-  L.row_stride = (size_t)d_pad * esz + 16;  // +16 bytes: the 32 lanes' 16-byte loads hit distinct banks
-  L.buf_bytes = 32 * L.row_stride;
-  // per-warp region: 2 barriers | meta (row, qmask) x 2 buffers | 2 term tables | 2 row buffers
-  L.bars = 0;
-  L.meta = 16;
-  L.slots = w_align(L.meta + 2 * 32 * 8, 16);
-  L.rows = w_align(L.slots + (size_t)2 * (n_slots > 0 ? n_slots : 1) * 32, 16);
-  L.per_warp = w_align(L.rows + 2 * L.buf_bytes, 128);
-  L.queries = (size_t)warps * L.per_warp;
-  L.total = L.queries + (size_t)nq_tmpl * d_pad * 4;
-  return L;
+// Rows per round: R x NQ row-query pairs per lane before the butterfly.
+template <int NQ>
+__host__ __device__ constexpr int rows_per_round() {
+  return NQ >= 8 ? 4 : 8;
 }
 
-// Row element (E) values of one 16-byte chunk as FP32 (exact: BF16 and e4m3
-// values are FP32 values).
-template <int E>
-__device__ __forceinline__ void chunk_to_f32(const uint4 &r, float (&x)[16 / elem_bytes(E)]) {
-  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+// Per-warp shared memory: the 32-row list (job ids, then query masks) and two
+// term-word tables of n_slots x 8 words (the group being evaluated and the next).
+__host__ __device__ inline size_t warp_bytes(int n_slots) {
+  const size_t b = 256 + (size_t)2 * (n_slots > 0 ? n_slots : 1) * 32;
+  return (b + 127) / 128 * 128;
+}
+
+// V consecutive row values (E) at p as FP32 (exact: BF16 and e4m3 values are
+// FP32 values); p is aligned to V x element bytes.
+template <int E, int V>
+__device__ __forceinline__ void load_vals(const unsigned char *p, float (&x)[V]) {
   if constexpr (E == kElemF32) {
+    if constexpr (V == 1) {
+      x[0] = __ldg(reinterpret_cast<const float *>(p));
+    } else if constexpr (V == 2) {
+      const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+      x[0] = v.x;
+      x[1] = v.y;
+    } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) x[i] = __uint_as_float(w[i]);
+      for (int i = 0; i < V; i += 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + i / 4);
+        x[i] = v.x;
+        x[i + 1] = v.y;
+        x[i + 2] = v.z;
+        x[i + 3] = v.w;
+      }
+    }
   } else if constexpr (E == kElemBF16) {
+    if constexpr (V == 1) {
+      x[0] = __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p)) << 16);
+    } else {
+      uint32_t w[V / 2];
+      if constexpr (V == 2) {
+        w[0] = __ldg(reinterpret_cast<const uint32_t *>(p));
+      } else if constexpr (V == 4) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        w[0] = v.x;
+        w[1] = v.y;
+      } else {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+      }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      x[2 * i] = __uint_as_float(w[i] << 16);
-      x[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+      for (int i = 0; i < V / 2; ++i) {
+        x[2 * i] = __uint_as_float(w[i] << 16);
+        x[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+      }
     }
   } else {
+    // e4m3: pairs of bytes through the FP8 -> half conversion
+    uint32_t h[V > 1 ? V / 2 : 1];
+    if constexpr (V == 1) {
+      h[0] = (uint32_t)__ldg(reinterpret_cast<const unsigned char *>(p));
+    } else if constexpr (V == 2) {
+      h[0] = (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p));
+    } else if constexpr (V == 4) {
+      const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(p));
+      h[0] = w & 0xFFFFu;
+      h[1] = w >> 16;
+    } else {
+      const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+      h[0] = w.x & 0xFFFFu;
+      h[1] = w.x >> 16;
+      h[2] = w.y & 0xFFFFu;
+      h[3] = w.y >> 16;
+    }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const __half2_raw hr =
-            __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
-        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
-        x[4 * i + 2 * h] = f.x;
-        x[4 * i + 2 * h + 1] = f.y;
-      }
+    for (int i = 0; i < (V > 1 ? V / 2 : 1); ++i) {
+      const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)h[i], __NV_E4M3);
+      const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+      x[2 * i] = f.x;
+      if constexpr (V > 1) x[2 * i + 1] = f.y;
     }
   }
 }
 
-template <int DP, int NQ, int E>
-__device__ __forceinline__ void score_batch(const ScanArgs &a, const unsigned char *buf, const uint32_t *meta_row,
-                                            const uint32_t *meta_qm, uint32_t n, const float *qs,
-                                            const uint64_t (&tq)[NQ], int lane, int top, int shift,
-                                            uint32_t dmask, size_t row_stride) {
-  // every lane takes part (the appends below are warp-aggregated); lanes past
-  // the batch score a stale slot of the buffer and pass no query
-  const bool live = (uint32_t)lane < n;
-  const uint32_t row = live ? meta_row[lane] : 0u;
-  const uint32_t qm = live ? meta_qm[lane] : 0u;
-  constexpr int kPer = 16 / elem_bytes(E);  // values per 16-byte chunk
-  const unsigned char *xr = buf + (size_t)lane * row_stride;
-  float acc[NQ];
+// Butterfly over the warp: on entry v[p] is this lane's partial sum of pair p
+// (p < P, P a power of two <= 32); on return every lane holds the full sum of
+// pair lane >> (5 - log2 P).  Step o halves the pairs a lane carries (the lane
+// with bit o set keeps the upper half) until one is left, then plain xor
+// steps finish the remaining offsets; either way lanes differing in bit 4 are
+// added first, then bit 3, ..., bit 0, for every pair.
+template <int P>
+__device__ __forceinline__ float lane_sum(float (&v)[P], int lane) {
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
-#pragma unroll 4
-  for (int k = 0; k < DP; k += kPer) {
-    float x[kPer];
-    chunk_to_f32<E>(*reinterpret_cast<const uint4 *>(xr + (size_t)k * elem_bytes(E)), x);
+  for (int s = 0; s < 5; ++s) {
+    const int o = 16 >> s;
+    const int cnt = P >> s;  // pairs carried before this step
+    if (cnt > 1) {
+      const int h = cnt / 2;
+      const bool up = (lane & o) != 0;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-#pragma unroll
-      for (int v4 = 0; v4 < kPer / 4; ++v4) {
-        const float4 v = *reinterpret_cast<const float4 *>(qs + q * DP + k + 4 * v4);
-        acc[q] = fmaf(x[4 * v4 + 0], v.x, acc[q]);
-        acc[q] = fmaf(x[4 * v4 + 1], v.y, acc[q]);
-        acc[q] = fmaf(x[4 * v4 + 2], v.z, acc[q]);
-        acc[q] = fmaf(x[4 * v4 + 3], v.w, acc[q]);
+      for (int i = 0; i < h; ++i) {
+        const float send = up ? v[i] : v[i + h];
+        const float keep = up ? v[i + h] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
       }
+    } else {
+      v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], o);
     }
   }
-  if constexpr (E == kElemFP8) {  // per-row scale of the e4m3 row
-    const float sc = live ? __ldg(a.xscale + row) : 0.f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] *= sc;
-  }
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const bool pass = (qm >> q) & 1u;
-    const uint64_t key = make_key(acc[q], row);
-    const int g2 = a.q_base + q;
-    if (a.mode == kCollect) {
-      // one counter reservation per warp and query
-      const bool take = pass && key >= tq[q];
-      const uint32_t want = __ballot_sync(0xFFFFFFFFu, take);
-      if (want == 0u) continue;
-      uint32_t base = 0;
-      if (lane == __ffs(want) - 1) base = atomicAdd(&a.buf_cnt[g2], (uint32_t)__popc(want));
-      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(want) - 1);
-      if (take) {
-        const uint32_t p = base + (uint32_t)__popc(want & ((1u << lane) - 1u));
-        if ((int64_t)p < a.buf_cap)
-          a.buf[(size_t)g2 * (size_t)a.buf_cap + p] = key;
-        else
-          atomicOr(&a.overflow[g2], 1u);
-      }
-    } else if (pass && (top >= 64 || (key >> top) == (tq[q] >> top))) {
-      atomicAdd(&a.hist[(size_t)g2 * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
-    }
-  }
+  return v[0];
+}
+
+template <int P>
+__host__ __device__ constexpr int log2_of() {
+  return P >= 32 ? 5 : P >= 16 ? 4 : P >= 8 ? 3 : P >= 4 ? 2 : P >= 2 ? 1 : 0;
 }
 
 template <int DP, int NQ, int E>
-__global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
+__global__ void __launch_bounds__(kWarps * 32) k_scan_gemv(const ScanArgs a) {
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int kRowBytes = DP * elem_bytes(E);
-  constexpr int kChunks = kRowBytes / 16;  // 16-byte chunks per row
-  const int warps = blockDim.x >> 5;
-  const WarpLayout L = warp_layout(DP, elem_bytes(E), NQ, a.n_slots, warps);
+  constexpr int kV = DP / 32;  // values of a row (and of a query) per lane
+  constexpr int kEsz = elem_bytes(E);
+  constexpr int kRowBytes = DP * kEsz;
+  constexpr int kR = rows_per_round<NQ>();
+  constexpr int kP = kR * NQ;  // row-query pairs per round
+  constexpr int kLg = log2_of<kP>();
+  static_assert(kP <= 32 && (kP & (kP - 1)) == 0, "pairs per round: a power of two up to 32");
   const unsigned char *xsrc =
       reinterpret_cast<const unsigned char *>(E == kElemF32 ? static_cast<const void *>(a.X) : a.Xq);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  unsigned char *wbase = smem + (size_t)warp * L.per_warp;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + L.bars);
-  uint32_t *meta = reinterpret_cast<uint32_t *>(wbase + L.meta);  // [buf][row 32 | qmask 32]
-  uint32_t *slot_tab = reinterpret_cast<uint32_t *>(wbase + L.slots);
-  unsigned char *rows = wbase + L.rows;
-  float *qs = reinterpret_cast<float *>(smem + L.queries);
+  unsigned char *wbase = smem + (size_t)warp * warp_bytes(a.n_slots);
+  uint32_t *mrow = reinterpret_cast<uint32_t *>(wbase);  // [32] job ids of the list
+  uint32_t *mqm = mrow + 32;                             // [32] their query masks
+  uint32_t *slot_tab = reinterpret_cast<uint32_t *>(wbase + 256);
   __shared__ bool s_last;
 
-  for (int i = threadIdx.x; i < NQ * DP; i += blockDim.x) {
-    const int q = i / DP;
-    qs[i] = q < a.nq ? a.Q[(size_t)(a.q_base + q) * DP + (i % DP)] : 0.f;
-  }
-  if (lane == 0) {
-    mbar_init(&bar[0], 32);
-    mbar_init(&bar[1], 32);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  // this lane's values of every query of the launch
+  float qv[NQ][kV];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int v = 0; v < kV; ++v)
+      qv[q][v] = q < a.nq ? a.Q[(size_t)(a.q_base + q) * DP + (size_t)lane * kV + v] : 0.f;
 
   const int top = 64 - kFbBits * a.hist_pass;
   const int shift = top - kFbBits > 0 ? top - kFbBits : 0;
   const uint32_t dmask = (1u << (top - shift)) - 1u;
+  // predicate layout: lane q evaluates query q
   const int gq = a.q_base + lane;
   const bool qlive = lane < a.nq && (a.active == nullptr || a.active[gq] != 0u);
-  uint64_t tq[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const int g2 = a.q_base + q;
-    const bool live = q < a.nq && (a.active == nullptr || a.active[g2] != 0u);
-    tq[q] = !live ? 0ull : (a.mode == kCollect ? (a.tau ? a.tau[g2] : 0ull) : a.prefix[g2]);
-  }
+  // scoring layout: after the butterfly this lane holds pair pidx = (row my_r
+  // of the round, query my_q); of the 32 / kP lanes holding it the first reports it
+  const int pidx = lane >> (5 - kLg);
+  const int my_r = pidx / NQ, my_q = pidx % NQ;
+  const bool rep = (lane & ((1 << (5 - kLg)) - 1)) == 0;
+  const int g2 = a.q_base + my_q;
+  const bool my_live = my_q < a.nq && (a.active == nullptr || a.active[g2] != 0u);
+  const uint64_t my_t = !my_live ? 0ull : (a.mode == kCollect ? (a.tau ? a.tau[g2] : 0ull) : a.prefix[g2]);
 
   const int64_t n_items = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
   int64_t item = 0, item_end = 0;
@@ -230,38 +231,82 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
     cp_async_commit();
   };
 
-  unsigned long long my_pass = 0;
-  bool ok = true;
-  int fb = 0;          // buffer being filled
-  uint32_t fill = 0;   // rows placed in it
-  bool prev = false;   // a closed batch waits in buffer fb ^ 1
-  uint32_t prev_n = 0;
-  uint32_t phase[2] = {0u, 0u};
-  auto close_and_score_prev = [&]() {
-    // hand the filled buffer's copies to its barrier, then score the previous batch
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[fb])) : "memory");
-    if (prev) {
-      const int pb = fb ^ 1;
-      if (!mbar_wait(&bar[pb], phase[pb])) ok = false;
-      phase[pb] ^= 1u;
-      __syncwarp();
-      score_batch<DP, NQ, E>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs,
-                             tq, lane, top, shift, dmask, L.row_stride);
-      __syncwarp();
+  // score the list's first n rows: rounds of kR rows, the next round's rows
+  // loaded before the current round is reduced
+  auto score_rows = [&](uint32_t n) {
+    float xa[kR][kV], xb[kR][kV];
+    auto load = [&](uint32_t base, float(&x)[kR][kV]) {
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        const uint32_t i = base + (uint32_t)r;
+        if (i < n) {
+          load_vals<E, kV>(xsrc + (size_t)mrow[i] * kRowBytes + (size_t)lane * (kV * kEsz), x[r]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < kV; ++v) x[r][v] = 0.f;
+        }
+      }
+    };
+    auto process = [&](uint32_t base, const float(&x)[kR][kV]) {
+      float part[kP];
+#pragma unroll
+      for (int r = 0; r < kR; ++r)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          float acc = 0.f;
+#pragma unroll
+          for (int v = 0; v < kV; ++v) acc = fmaf(x[r][v], qv[q][v], acc);
+          part[r * NQ + q] = acc;
+        }
+      float s = lane_sum<kP>(part, lane);
+      const uint32_t i = base + (uint32_t)my_r;
+      const bool valid = i < n;
+      const uint32_t row = valid ? mrow[i] : 0u;
+      const uint32_t qm = valid ? mqm[i] : 0u;
+      const bool pass = rep && ((qm >> my_q) & 1u);
+      if constexpr (E == kElemFP8) s *= pass ? __ldg(a.xscale + row) : 0.f;  // per-row scale of the e4m3 row
+      const uint64_t key = make_key(s, row);
+      if (a.mode == kCollect) {
+        // one counter reservation per warp and query
+        const bool take = pass && key >= my_t;
+        if (__any_sync(0xFFFFFFFFu, take)) {
+          const uint32_t grp = __match_any_sync(0xFFFFFFFFu, take ? (uint32_t)my_q : 64u + (uint32_t)lane);
+          const int leader = __ffs(grp) - 1;
+          uint32_t pos0 = 0;
+          if (take && lane == leader) pos0 = atomicAdd(&a.buf_cnt[g2], (uint32_t)__popc(grp));
+          pos0 = __shfl_sync(0xFFFFFFFFu, pos0, leader);
+          if (take) {
+            const uint32_t p = pos0 + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+            if ((int64_t)p < a.buf_cap)
+              a.buf[(size_t)g2 * (size_t)a.buf_cap + p] = key;
+            else
+              atomicOr(&a.overflow[g2], 1u);
+          }
+        }
+      } else if (pass && (top >= 64 || (key >> top) == (my_t >> top))) {
+        atomicAdd(&a.hist[(size_t)g2 * kFbBins + (uint32_t)((key >> shift) & dmask)], 1u);
+      }
+    };
+    load(0u, xa);
+    for (uint32_t b = 0; b < n; b += 2 * kR) {
+      if (b + kR < n) load(b + kR, xb);
+      process(b, xa);
+      if (b + kR < n) {
+        if (b + 2 * kR < n) load(b + 2 * kR, xa);
+        process(b + kR, xb);
+      }
     }
-    prev = true;
-    prev_n = fill;
-    fb ^= 1;
-    fill = 0;
   };
 
+  unsigned long long my_pass = 0;
+  uint32_t fill = 0;  // rows in the list
   int t = 0;
   int64_t g = next_group();
   if (g >= 0) prefetch(g, 0);
   int64_t gn = g >= 0 ? next_group() : -1;
   if (gn >= 0) prefetch(gn, 1);
   else cp_async_commit();
-  while (g >= 0 && ok) {
+  while (g >= 0) {
     cp_async_wait_group<1>();  // term words of g have landed
     __syncwarp();
     uint32_t pw[8];
@@ -279,7 +324,7 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
 #pragma unroll 1
     for (int w = 0; w < 8; ++w) {
       const int64_t left = a.n - (r0 + w * 32);
-      uint32_t p = pw[w] & (left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u));
+      const uint32_t p = pw[w] & (left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u));
       my_pass += (unsigned long long)__popc(p);
       const uint32_t U = __reduce_or_sync(0xFFFFFFFFu, p);
       if (U == 0u) continue;
@@ -292,38 +337,26 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
       uint32_t done = 0;
       while (done < n) {
         const uint32_t take = (32u - fill) < (n - done) ? (32u - fill) : (n - done);
-        uint32_t *mrow = meta + fb * 64;
         if (((U >> lane) & 1u) && rank >= done && rank < done + take) {
           mrow[fill + rank - done] = (uint32_t)(wrow + lane);
-          mrow[32 + fill + rank - done] = qm;
+          mqm[fill + rank - done] = qm;
         }
-        __syncwarp();  // the slots' job ids are visible to every lane
-        unsigned char *dst = rows + (size_t)fb * L.buf_bytes;
-        for (uint32_t i = lane; i < take * kChunks; i += 32) {
-          const uint32_t k = i / kChunks, c = i % kChunks;
-          cp_async16(dst + (size_t)(fill + k) * L.row_stride + c * 16,
-                     xsrc + (size_t)mrow[fill + k] * kRowBytes + (size_t)c * 16);
-        }
+        __syncwarp();  // the list is visible to every lane
         fill += take;
         done += take;
-        if (fill == 32u) close_and_score_prev();
+        if (fill == 32u) {
+          score_rows(32u);
+          __syncwarp();  // every lane has read the list
+          fill = 0;
+        }
       }
     }
     g = gn;
     gn = gnn;
     t ^= 1;
   }
-  // drain: close the partial batch, score what remains
-  if (fill > 0u) close_and_score_prev();
-  if (prev) {
-    const int pb = fb ^ 1;
-    if (!mbar_wait(&bar[pb], phase[pb])) ok = false;
-    __syncwarp();
-    score_batch<DP, NQ, E>(a, rows + (size_t)pb * L.buf_bytes, meta + pb * 64, meta + pb * 64 + 32, prev_n, qs, tq,
-                           lane, top, shift, dmask, L.row_stride);
-  }
+  if (fill > 0u) score_rows(fill);
   cp_async_wait_all();
-  if (!ok && lane == 0) atomicOr(a.err, kErrTimeout);
   if (qlive && a.pass_cnt != nullptr) atomicAdd(&a.pass_cnt[gq], my_pass);
 
   // grid completion: the last CTA resets the work counter and, in kHist mode,
@@ -347,15 +380,29 @@ __global__ void __launch_bounds__(256, 1) k_scan_gemv(const ScanArgs a) {
 
 template <int DP, int NQ, int E>
 cudaError_t launch_one(const ScanArgs &a, int grid, cudaStream_t s) {
-  const size_t budget = 220u * 1024u;
-  int warps = 8;
-  while (warps > 1 && warp_layout(DP, elem_bytes(E), NQ, a.n_slots, warps).total > budget) --warps;
-  const WarpLayout L = warp_layout(DP, elem_bytes(E), NQ, a.n_slots, warps);
-  if (L.total > budget) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kWarps * warp_bytes(a.n_slots);
+  if (a.n_slots > kGemvMaxSlots || smem > 220u * 1024u) return cudaErrorInvalidValue;
   auto *fn = k_scan_gemv<DP, NQ, E>;
-  cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)L.total);
+  cudaError_t e = allow_dynamic_smem((const void *)fn, smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, warps * 32, L.total, s>>>(a);
+  // CTAs an SM holds at this shared-memory size (looked up once per slot count)
+  static std::atomic<int> per_sm[kGemvMaxSlots + 1];
+  const int ns = a.n_slots > 0 ? a.n_slots : 0;
+  int nb = per_sm[ns].load(std::memory_order_relaxed);
+  if (nb <= 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) nb = 1;
+    per_sm[ns].store(nb, std::memory_order_relaxed);
+  }
+  // grid: the caller's CTAs per pass (at most one per SM) x CTAs per SM, no
+  // more than the work counter hands out chunks to
+  const int64_t n_items = a.g_begin < a.n_groups ? (a.n_groups - a.g_begin + a.g_step - 1) / a.g_step : 0;
+  const int64_t want = (n_items + (int64_t)kChunkGroups * kWarps - 1) / ((int64_t)kChunkGroups * kWarps);
+  int64_t total = (int64_t)grid * nb;
+  if (total > want) total = want;
+  if (total < 1) total = 1;
+  fn<<<(int)total, kWarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
