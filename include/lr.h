@@ -248,6 +248,18 @@ size_t lr_index_device_bytes(const lr_index *index);
  * the top K is finished by an exact radix selection over the whole index.
  * Errors: LR_ERR_INVALID, LR_ERR_WORKSPACE (batch larger than the workspace),
  * LR_ERR_CUDA.
+ *
+ * Debugging aids (read once per process from the environment; the paper has
+ * no counterpart):
+ *   LR_PLAN=gemv|simt|tc|tbr  the plan of every search whose options leave it
+ *                             to the library (LR_PLAN_AUTO); a forced TBR-first
+ *                             plan fails on filters it cannot serve, and is not
+ *                             applied to row-range searches.
+ *   LR_TIMERS=1               each lr_search / lr_search_ex records CUDA events
+ *                             between its stages on `stream`, synchronises the
+ *                             stream before returning and prints one line of
+ *                             stage times (ms) to stderr.
+ * Each stage is also an NVTX range (free when no profiling tool is attached).
  */
 lr_status lr_search(lr_index *index, const float *q, int32_t B, const lr_filters *f, const int32_t *k,
                     int32_t k_all, int32_t *out_ids, float *out_scores, int32_t *out_count, void *stream);

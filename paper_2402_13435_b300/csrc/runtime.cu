@@ -5,8 +5,12 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -186,6 +190,92 @@ struct lr_index {
 };
 
 namespace {
+
+// Debugging aids, read once from the environment:
+//   LR_PLAN=gemv|simt|tc|tbr  the plan of every search that asks for LR_PLAN_AUTO
+//                             (a forced TBR-first plan fails on filters it cannot
+//                             serve, as when the caller forces it);
+//   LR_TIMERS=1               every lr_search times its stages with CUDA events on
+//                             its stream, synchronises the stream at the end and
+//                             prints one line to stderr.
+// NVTX ranges name the host side of each stage (no cost without a tool attached).
+struct DebugEnv {
+  int plan = -1;
+  bool timers = false;
+};
+
+const DebugEnv &debug_env() {
+  static const DebugEnv e = [] {
+    DebugEnv d;
+    if (const char *p = std::getenv("LR_PLAN")) {
+      const std::string v(p);
+      if (v == "gemv" || v == "simt") d.plan = LR_PLAN_GEMV;
+      else if (v == "tc") d.plan = LR_PLAN_TC;
+      else if (v == "tbr") d.plan = LR_PLAN_TBR;
+      else if (v == "auto") d.plan = LR_PLAN_AUTO;
+    }
+    if (const char *t = std::getenv("LR_TIMERS")) d.timers = t[0] != '\0' && t[0] != '0';
+    return d;
+  }();
+  return e;
+}
+
+// Stage marks of one call: mark(name) ends the previous stage and starts
+// `name` (an NVTX range, and with LR_TIMERS an event recorded on the stream);
+// report() waits for the last event and prints the stage times.
+class StageTimer {
+ public:
+  StageTimer(cudaStream_t s, const char *call) : s_(s), call_(call), on_(debug_env().timers) {}
+  StageTimer(const StageTimer &) = delete;
+  StageTimer &operator=(const StageTimer &) = delete;
+  ~StageTimer() {
+    if (open_) nvtxRangePop();
+    for (cudaEvent_t e : ev_) cudaEventDestroy(e);
+  }
+  void mark(const char *name) {
+    if (open_) nvtxRangePop();
+    nvtxRangePushA(name);
+    open_ = true;
+    if (!on_) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s_);
+    ev_.push_back(e);
+    names_.push_back(name);
+  }
+  void report(const std::string &what) {
+    if (open_) nvtxRangePop();
+    open_ = false;
+    if (!on_ || ev_.empty()) return;
+    cudaEvent_t end = nullptr;
+    if (cudaEventCreate(&end) != cudaSuccess) return;
+    cudaEventRecord(end, s_);
+    ev_.push_back(end);
+    if (cudaEventSynchronize(end) != cudaSuccess) return;
+    std::string line = std::string(call_) + " " + what + ":";
+    float total = 0.f;
+    for (size_t i = 0; i + 1 < ev_.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev_[i], ev_[i + 1]);
+      total += ms;
+      char buf[96];
+      std::snprintf(buf, sizeof buf, " %s %.3f", names_[i], ms);
+      line += buf;
+    }
+    char buf[64];
+    std::snprintf(buf, sizeof buf, " | total %.3f ms\n", total);
+    line += buf;
+    std::fputs(line.c_str(), stderr);
+  }
+
+ private:
+  cudaStream_t s_;
+  const char *call_;
+  bool on_;
+  bool open_ = false;
+  std::vector<cudaEvent_t> ev_;
+  std::vector<const char *> names_;
+};
 
 void free_index(lr_index *ix) {
   if (!ix) return;
@@ -1422,7 +1512,7 @@ lr_status run_tbr_search(lr_index *ix, const float *q, int B, const lr_filters *
 
 lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, const int32_t *k, int k_all,
                      int32_t *out_ids, float *out_scores, int32_t *out_count, const lr_search_opts *opts,
-                     const lr_search_stats *stats, cudaStream_t s) {
+                     const lr_search_stats *stats, cudaStream_t s, StageTimer &tm) {
   if (B < 1) return fail(LR_ERR_INVALID, "B must be >= 1");
   if (B > ix->max_batch) return fail(LR_ERR_WORKSPACE, "B exceeds max_batch");
   if (!q || !out_ids || !out_scores) return fail(LR_ERR_INVALID, "null query or output pointer");
@@ -1445,7 +1535,10 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     range_rows = o.row_end - o.row_begin;
   }
   const int64_t range_groups = g1 - g0;
-  if (o.quant_mult != 0) return run_sign_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, o, stats, s);
+  if (o.quant_mult != 0) {
+    tm.mark("sign");
+    return run_sign_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, o, stats, s);
+  }
 
   // pick and wait for a staging buffer
   const int turn = ix->filt_turn;
@@ -1458,6 +1551,10 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   int plan = o.plan;
   if (plan != LR_PLAN_AUTO && plan != LR_PLAN_GEMV && plan != LR_PLAN_TC && plan != LR_PLAN_TBR)
     return fail(LR_ERR_INVALID, "plan must be LR_PLAN_AUTO, LR_PLAN_GEMV, LR_PLAN_TC or LR_PLAN_TBR");
+  // LR_PLAN in the environment decides for the caller that left it to us
+  // (not TBR first for a row range, which that plan does not serve)
+  if (plan == LR_PLAN_AUTO && debug_env().plan > 0 && !(ranged && debug_env().plan == LR_PLAN_TBR))
+    plan = debug_env().plan;
   const bool lowp = ix->elem != kElemF32;
   const bool tc_ok = lowp ? ix->have_tmap_q : ix->have_tmap;
   std::vector<double> est;  // estimated pass rate per filter
@@ -1473,8 +1570,10 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     if (plan == LR_PLAN_TBR && !T.ok)
       return fail(LR_ERR_UNSUPPORTED, "TBR-first plan needs posting lists, a clause per query and a chosen clause "
                                       "with at most the candidate capacity of postings and 16 distinct terms");
-    if (plan == LR_PLAN_TBR || (T.ok && tbr_cheaper(ix, B, T, est, tc_ok)))
+    if (plan == LR_PLAN_TBR || (T.ok && tbr_cheaper(ix, B, T, est, tc_ok))) {
+      tm.mark("tbr");
       return run_tbr_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, stats, s, T, tcap);
+    }
   }
   if (plan == LR_PLAN_AUTO) plan = choose_plan(ix, B, tc_ok, have_est, est);
   if (plan == LR_PLAN_TC && !tc_ok)
@@ -1526,6 +1625,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   }
 
   // ---- device work
+  tm.mark("upload+prep");
   int32_t n_launch = 0, n_scan = 0;
   LR_CK(cudaMemcpyAsync(ix->filt_d, stage, C.bytes, cudaMemcpyHostToDevice, s));
   LR_CK(cudaEventRecord(ix->filt_ev[turn], s));
@@ -1623,6 +1723,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     LR_CK(cudaEventRecord(ix->ev_join, ix->aux));
   }
   // 1. threshold sample
+  tm.mark("sample");
   if (sp.stride > 0 && need_sample) {
     for (const SubBatch &sb : C.subs) {
       ScanArgs a = scan_args(sb);
@@ -1652,6 +1753,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     LR_LAUNCH(launch_threshold(t, B, s));
   }
   // 2. main scan: candidates at or above the threshold, pass counts
+  tm.mark("scan");
   if (early_filter) LR_CK(cudaStreamWaitEvent(s, ix->ev_join, 0));
   if (stats && stats->scan_start) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_start, s));
   // Consecutive sub-batches (full ones of block_q queries, then one more)
@@ -1689,6 +1791,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     ++n_scan;
   }
   if (stats && stats->scan_stop) LR_CK(cudaEventRecord((cudaEvent_t)stats->scan_stop, s));
+  tm.mark("select");
   // 3. final selection into the caller's device outputs, or into workspace
   //    rows that are copied back when the outputs are host memory
   const bool dev_out = is_device_ptr(out_ids) && is_device_ptr(out_scores) &&
@@ -1718,6 +1821,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   fa.err = ix->err;
   fa.id_base = lowp ? 0 : ix->id_base;  // the precision form's rescore reads rows by local id
   LR_LAUNCH(launch_select(fa, B, s));
+  tm.mark("fallback");
   // 4. exact fallback for flagged queries (each launch returns at once when none
   //    is flagged): kFbPasses histogram passes, then the collect, per
   //    sub-batch; the sub-batch's first pass filters its tiles and the list
@@ -1756,6 +1860,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   LR_LAUNCH(launch_select(fb, B, s));
   // 5. precision form: FP32 rescore of the candidates, FP64 re-rank of the near ties
   if (lowp) {
+    tm.mark("rescore");
     RescoreArgs ra{};
     ra.X = ix->X;
     ra.d_pad = ix->d_pad;
@@ -1778,6 +1883,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
   }
 
   // 6. host outputs and statistics
+  tm.mark("outputs");
   bool need_sync = false;
   if (!dev_out) {
     LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
@@ -1812,7 +1918,11 @@ lr_status lr_search_ex(lr_index *index, const float *q, int32_t B, const lr_filt
                        int32_t k_all, int32_t *out_ids, float *out_scores, int32_t *out_count,
                        const lr_search_opts *opts, const lr_search_stats *stats, void *stream) {
   if (!index) return fail(LR_ERR_INVALID, "index is null");
-  return run_search(index, q, B, f, k, k_all, out_ids, out_scores, out_count, opts, stats, (cudaStream_t)stream);
+  StageTimer tm((cudaStream_t)stream, "lr_search");
+  const lr_status st =
+      run_search(index, q, B, f, k, k_all, out_ids, out_scores, out_count, opts, stats, (cudaStream_t)stream, tm);
+  if (st == LR_OK) tm.report("B=" + std::to_string(B) + " K=" + std::to_string(k_all) + " ms");
+  return st;
 }
 
 lr_status lr_search(lr_index *index, const float *q, int32_t B, const lr_filters *f, const int32_t *k,
