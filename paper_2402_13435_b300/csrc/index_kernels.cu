@@ -128,6 +128,7 @@ __global__ void k_scatter_postings(const int64_t *post_off, const uint32_t *post
 __global__ void k_expand_postings(const int64_t *post_off, const uint32_t *post_ids, const int32_t *spans,
                                   int n_spans, int span_log2, const int32_t *terms, uint32_t *bitmaps,
                                   int64_t n_words, int64_t n) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   extern __shared__ __align__(16) uint32_t span_words[];
   const int j = blockIdx.x;
   const int32_t t = terms[blockIdx.y];
@@ -169,6 +170,7 @@ __global__ void k_term_counts(const uint32_t *bitmaps, int64_t n_words, int64_t 
 
 // One warp per query: copy into [B][d_pad] (zero padded), FP32-normalised for cosine.
 __global__ void k_prep_queries(const float *in, float *out, int B, int dim, int d_pad, int cosine, uint32_t *err) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int lane = threadIdx.x & 31;
   const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q >= B) return;
@@ -284,9 +286,9 @@ cudaError_t launch_expand_postings(const int64_t *post_off, const uint32_t *post
   if (smem > 48u * 1024u) return cudaErrorInvalidValue;
   for (int t0 = 0; t0 < n_terms; t0 += 65535) {  // grid.y is limited to 65535
     const int nt = n_terms - t0 < 65535 ? n_terms - t0 : 65535;
-    k_expand_postings<<<dim3((unsigned)n_spans, (unsigned)nt), 256, smem, s>>>(
-        post_off, post_ids, spans, n_spans, span_log2, terms + t0, bitmaps + (size_t)t0 * n_words, n_words, n);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e =
+        launch_pdl(k_expand_postings, dim3((unsigned)n_spans, (unsigned)nt), dim3(256), smem, s, post_off, post_ids,
+                   spans, n_spans, span_log2, terms + t0, bitmaps + (size_t)t0 * n_words, n_words, n);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -302,8 +304,8 @@ cudaError_t launch_prep_queries(const float *q_in, float *q_out, int B, int dim,
                                 uint32_t *err, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   const int wpb = 8;
-  k_prep_queries<<<(B + wpb - 1) / wpb, wpb * 32, 0, s>>>(q_in, q_out, B, dim, d_pad, cosine, err);
-  return cudaGetLastError();
+  return launch_pdl(k_prep_queries, dim3((unsigned)((B + wpb - 1) / wpb)), dim3(wpb * 32), 0, s, q_in, q_out, B, dim,
+                    d_pad, cosine, err);
 }
 
 cudaError_t launch_filter_eval(const ScanArgs &a, unsigned long long *pass_cnt, uint32_t *out_bitmap,

@@ -163,6 +163,34 @@ struct SelectArgs {
   int64_t id_base;               // added to every written job id (row shards of a larger index)
 };
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may be set
+// up on the SMs while the kernel before it in the stream is still finishing,
+// which hides the launch latency between the search's dependent kernels.
+// Such a kernel calls pdl_wait() before it touches global memory; the call
+// returns once the previous kernel has completed and its writes are visible
+// (launched without the attribute, it returns at once).  The kernels never
+// signal early completion, so the next kernel is not placed before every CTA
+// of the previous one has exited.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // Raise a kernel's dynamic shared-memory cap to at least `bytes` on the
 // current device.  The cap is a per-function attribute and setting it is a
 // costly driver call, so each (function, device) is raised only when a launch

@@ -169,6 +169,7 @@ __host__ __device__ constexpr int log2_of() {
 
 template <int DP, int NQ, int E>
 __global__ void __launch_bounds__(kWarps * 32) k_scan_gemv(const ScanArgs a) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int kV = DP / 32;  // values of a row (and of a query) per lane
@@ -402,8 +403,7 @@ cudaError_t launch_one(const ScanArgs &a, int grid, cudaStream_t s) {
   int64_t total = (int64_t)grid * nb;
   if (total > want) total = want;
   if (total < 1) total = 1;
-  fn<<<(int)total, kWarps * 32, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(fn, dim3((unsigned)total), dim3(kWarps * 32), smem, s, a);
 }
 
 template <int DP, int E>

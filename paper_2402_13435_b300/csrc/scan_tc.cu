@@ -179,6 +179,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
 template <int N, int E, int NB>
 __global__ void __launch_bounds__(tc_threads(E, N, NB), 1)
     k_scan_tc(const ScanArgs a, const __grid_constant__ CUtensorMap tmap, int S) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   static_assert(NB == 1 || (NB == 2 && E == kElemF32 && (N == kTc2BlockQ || N == 64)) ||
                     (NB == kBf16Blocks && E != kElemF32 && N == 64),
                 "several query blocks: FP32 rows, two of 48 or 64 queries; BF16 / e4m3 rows, four of 64");
@@ -862,8 +863,7 @@ cudaError_t launch_tc(const ScanArgs &a, const CUtensorMap &tmap, int grid, cuda
   auto *fn = k_scan_tc<N, E, NB>;
   cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)(T.total + 1024));
   if (e != cudaSuccess) return e;
-  fn<<<grid, tc_threads(E, N, NB), T.total + 1024, s>>>(a, tmap, S);
-  return cudaGetLastError();
+  return launch_pdl(fn, dim3((unsigned)grid), dim3(tc_threads(E, N, NB)), (size_t)(T.total + 1024), s, a, tmap, S);
 }
 
 }  // namespace

@@ -250,6 +250,7 @@ __device__ void bitonic_desc_chunks(uint64_t *s, int P) {
 }
 
 __global__ void __launch_bounds__(kSelThreads) k_select(const SelectArgs a) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int q = blockIdx.x;
   if (a.any != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any) == 0u) return;
   if (a.only != nullptr && a.only[q] == 0u) return;
@@ -348,6 +349,7 @@ constexpr int kThrSlices = 32;
 static_assert(kSmemKeys == kThrScratchKeys, "scratch per query = shared-memory key capacity");
 
 __global__ void __launch_bounds__(kSelThreads) k_threshold(const ThrArgs a) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   extern __shared__ __align__(16) uint64_t sbuf[];  // [kSmemKeys] keys
   __shared__ SelShared sh;
   __shared__ bool s_last;
@@ -459,6 +461,7 @@ constexpr int kRsRows = 4;   // candidates a warp scores at once (their rows in 
 // CTA (q, s) takes candidates s * 16 + w (warp w) in steps of kRsSplit * 16
 // warps, kRsRows at a time; lane-strided partial sums, tree reductions.
 __global__ void __launch_bounds__(kRsThreads) k_rescore_scores(const RescoreArgs a) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int q = blockIdx.x, sl = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = a.ccnt[q] < a.c_stride ? a.ccnt[q] : a.c_stride;
@@ -510,6 +513,7 @@ struct TieShared {
 };
 
 __global__ void __launch_bounds__(kRsThreads) k_rescore(const RescoreArgs a) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int q = blockIdx.x;
   extern __shared__ __align__(16) uint64_t sbuf[];  // [kMaxK] FP32 keys, then [kMaxK] sort area
   __shared__ SelShared sh;
@@ -632,8 +636,7 @@ cudaError_t launch_threshold(const ThrArgs &a, int B, cudaStream_t s) {
   const size_t smem = (size_t)kSmemKeys * sizeof(uint64_t);
   cudaError_t e = allow_dynamic_smem((const void *)k_threshold, (size_t)smem);
   if (e != cudaSuccess) return e;
-  k_threshold<<<dim3((unsigned)B, (unsigned)kThrSlices), kSelThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_threshold, dim3((unsigned)B, (unsigned)kThrSlices), dim3(kSelThreads), smem, s, a);
 }
 
 cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s) {
@@ -641,20 +644,17 @@ cudaError_t launch_select(const SelectArgs &a, int B, cudaStream_t s) {
   const size_t smem = (size_t)(kSmemKeys + kMaxK) * sizeof(uint64_t);
   cudaError_t e = allow_dynamic_smem((const void *)k_select, (size_t)smem);
   if (e != cudaSuccess) return e;
-  k_select<<<B, kSelThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_select, dim3((unsigned)B), dim3(kSelThreads), smem, s, a);
 }
 
 cudaError_t launch_rescore(const RescoreArgs &a, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  k_rescore_scores<<<dim3((unsigned)B, (unsigned)kRsSplit), kRsThreads, 0, s>>>(a);
-  const cudaError_t e0 = cudaGetLastError();
+  const cudaError_t e0 = launch_pdl(k_rescore_scores, dim3((unsigned)B, (unsigned)kRsSplit), dim3(kRsThreads), 0, s, a);
   if (e0 != cudaSuccess) return e0;
   const size_t smem = (size_t)2 * kMaxK * sizeof(uint64_t);
   cudaError_t e = allow_dynamic_smem((const void *)k_rescore, (size_t)smem);
   if (e != cudaSuccess) return e;
-  k_rescore<<<B, kRsThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_rescore, dim3((unsigned)B), dim3(kRsThreads), smem, s, a);
 }
 
 }  // namespace lr

@@ -179,6 +179,7 @@ __global__ void k_sign_levels(const uint32_t *hist, int hist_stride, int nbits, 
 // stored over the job id as the selection key.
 __global__ void __launch_bounds__(kSgThreads) k_sign_rescore(const float *X, int d_pad, const float *Q,
                                                              uint64_t *buf, int64_t cap, const uint32_t *cnt) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int q = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int64_t nc = (int64_t)cnt[q] < cap ? (int64_t)cnt[q] : cap;
@@ -265,8 +266,7 @@ cudaError_t launch_sign_rescore(const float *X, int d_pad, const float *Q, uint6
   if (B <= 0) return cudaSuccess;
   int gx = (4 * num_sms + B - 1) / B;
   if (gx < 1) gx = 1;
-  k_sign_rescore<<<dim3((unsigned)gx, (unsigned)B), kSgThreads, 0, s>>>(X, d_pad, Q, buf, cap, cnt);
-  return cudaGetLastError();
+  return launch_pdl(k_sign_rescore, dim3((unsigned)gx, (unsigned)B), dim3(kSgThreads), 0, s, X, d_pad, Q, buf, cap, cnt);
 }
 
 }  // namespace lr

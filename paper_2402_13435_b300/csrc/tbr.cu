@@ -19,6 +19,7 @@ constexpr int kTbrMaxRanges = 16;
 __device__ __forceinline__ bool has_bit(const uint32_t *bm, uint32_t j) { return (__ldg(bm + (j >> 5)) >> (j & 31)) & 1u; }
 
 __global__ void __launch_bounds__(kTbrThreads) k_tbr_collect(const TbrArgs a) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   __shared__ int64_t pre[kTbrMaxRanges + 1];
   __shared__ int64_t beg[kTbrMaxRanges];
   __shared__ const uint32_t *bms[kTbrMaxRanges];
@@ -82,8 +83,7 @@ cudaError_t launch_tbr_collect(const TbrArgs &a, int num_sms, int64_t max_postin
   const int64_t cap_x = (4 * (int64_t)num_sms + a.nq - 1) / a.nq;
   if (gx > cap_x) gx = cap_x;
   if (gx < 1) gx = 1;
-  k_tbr_collect<<<dim3((unsigned)gx, (unsigned)a.nq), kTbrThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_tbr_collect, dim3((unsigned)gx, (unsigned)a.nq), dim3(kTbrThreads), 0, s, a);
 }
 
 }  // namespace lr

@@ -40,6 +40,7 @@ constexpr int kTfAppend = 8;      // groups between a warp's list appends (16 ti
 // W = uint32_t: at most 32 queries, one per lane; uint64_t: up to 64, two per lane.
 template <typename W>
 __global__ void __launch_bounds__(kTfThreads, sizeof(W) == 8 ? 2 : 3) k_tile_filter(const ScanArgs a) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   constexpr bool kTwo = sizeof(W) == 8;
   if (a.any_active != nullptr && *reinterpret_cast<const volatile uint32_t *>(a.any_active) == 0u) return;
   extern __shared__ uint4 tf_smem[];
@@ -244,8 +245,7 @@ cudaError_t launch_tile_filter(const ScanArgs &a, int num_sms, cudaStream_t s) {
     const cudaError_t e = allow_dynamic_smem((const void *)fn, (size_t)smem);
     if (e != cudaSuccess) return e;
   }
-  fn<<<grid, kTfThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(fn, dim3((unsigned)grid), dim3(kTfThreads), smem, s, a);
 }
 
 }  // namespace lr
