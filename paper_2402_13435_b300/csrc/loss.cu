@@ -112,6 +112,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kLossThreads, 1)
     k_loss(const LossArgs a, const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
            const __grid_constant__ CUtensorMap tm_ct) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   constexpr bool kOne = MODE == kFwd || MODE == kKeys;  // the score product only
@@ -606,6 +607,7 @@ struct PrepJob {
 
 __global__ void __launch_bounds__(256) k_loss_prep(const PrepJob j0, const PrepJob j1, int nb0, int elem, int d,
                                                    int dp) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   __shared__ __nv_bfloat16 tile[kPrepTile][kPrepTile + 2];
   const bool second = (int)blockIdx.x >= nb0;
   const PrepJob &J = second ? j1 : j0;
@@ -660,6 +662,7 @@ constexpr int kLseQueries = kLseThreads / 32;
 
 __global__ void __launch_bounds__(kLseThreads) k_loss_lse(const LossArgs a, int splits, float *lse, double *bsum,
                                                           uint32_t *done, float *loss) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   __shared__ double red[kLseQueries];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -711,6 +714,7 @@ __global__ void __launch_bounds__(kLseThreads) k_loss_lse(const LossArgs a, int 
 
 // dQ / dJ = the sum of the split partials; four values of a row per thread.
 __global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int dq4 = (d + 3) / 4;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)B * dq4) return;
@@ -736,6 +740,7 @@ __global__ void k_loss_dq_reduce(const float *part, int splits, size_t split_str
 
 // Per query: the selection's K, and its pass count = the keys listed.
 __global__ void k_hn_setup(int B, int n_neg, const uint32_t *key_cnt, int32_t *kq, unsigned long long *npass) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= B) return;
   kq[q] = n_neg;
@@ -745,6 +750,7 @@ __global__ void k_hn_setup(int B, int n_neg, const uint32_t *key_cnt, int32_t *k
 // The mined negatives as loss mask bits (bit j of row q: job j is one of q's hard
 // negatives); the rows were cleared before.
 __global__ void k_hn_mask(const int32_t *ids, const int32_t *count, int B, int n_neg, int Mw, uint32_t *mask) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int q = blockIdx.y;
   const int n = count[q];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n && i < n_neg; i += gridDim.x * blockDim.x) {
@@ -758,15 +764,14 @@ __global__ void k_hn_mask(const int32_t *ids, const int32_t *count, int B, int n
 cudaError_t launch_hn_setup(int B, int n_neg, const uint32_t *key_cnt, int32_t *kq, unsigned long long *npass,
                             cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  k_hn_setup<<<(B + 255) / 256, 256, 0, s>>>(B, n_neg, key_cnt, kq, npass);
-  return cudaGetLastError();
+  return launch_pdl(k_hn_setup, dim3((unsigned)((B + 255) / 256)), dim3(256), 0, s, B, n_neg, key_cnt, kq, npass);
 }
 
 cudaError_t launch_hn_mask(const int32_t *ids, const int32_t *count, int B, int n_neg, int Mw, uint32_t *mask,
                            cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  k_hn_mask<<<dim3((unsigned)((n_neg + 255) / 256), (unsigned)B), 256, 0, s>>>(ids, count, B, n_neg, Mw, mask);
-  return cudaGetLastError();
+  return launch_pdl(k_hn_mask, dim3((unsigned)((n_neg + 255) / 256), (unsigned)B), dim3(256), 0, s, ids, count, B, n_neg,
+                    Mw, mask);
 }
 
 cudaError_t launch_loss_prep(int elem, int d, int dp, const void *X0, int rows0, int rows_p0, void *P0, void *PT0,
@@ -775,8 +780,7 @@ cudaError_t launch_loss_prep(int elem, int d, int dp, const void *X0, int rows0,
   const PrepJob j1{X1, rows1, rows_p1, (__nv_bfloat16 *)P1, (__nv_bfloat16 *)PT1};
   const int nb0 = (rows_p0 + kPrepTile - 1) / kPrepTile, nb1 = (rows_p1 + kPrepTile - 1) / kPrepTile;
   const dim3 grid((unsigned)(nb0 + nb1), (unsigned)((dp + kPrepTile - 1) / kPrepTile));
-  k_loss_prep<<<grid, 256, 0, s>>>(j0, j1, nb0, elem, d, dp);
-  return cudaGetLastError();
+  return launch_pdl(k_loss_prep, grid, dim3(256), 0, s, j0, j1, nb0, elem, d, dp);
 }
 
 cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y, const void *tm_r, const void *tm_c,
@@ -792,34 +796,29 @@ cudaError_t launch_loss_pass(int mode, const LossArgs &a, int grid_x, int grid_y
     case kFwd:
       e = allow_dynamic_smem((const void *)k_loss<kFwd>, (size_t)smem);
       if (e != cudaSuccess) return e;
-      k_loss<kFwd><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
-      break;
+      return launch_pdl(k_loss<kFwd>, grid, dim3(kLossThreads), smem, s, a, r, c, ct);
     case kDq:
       e = allow_dynamic_smem((const void *)k_loss<kDq>, (size_t)smem);
       if (e != cudaSuccess) return e;
-      k_loss<kDq><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
-      break;
+      return launch_pdl(k_loss<kDq>, grid, dim3(kLossThreads), smem, s, a, r, c, ct);
     case kDj:
       e = allow_dynamic_smem((const void *)k_loss<kDj>, (size_t)smem);
       if (e != cudaSuccess) return e;
-      k_loss<kDj><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
-      break;
+      return launch_pdl(k_loss<kDj>, grid, dim3(kLossThreads), smem, s, a, r, c, ct);
     case kKeys:
       e = allow_dynamic_smem((const void *)k_loss<kKeys>, (size_t)smem);
       if (e != cudaSuccess) return e;
-      k_loss<kKeys><<<grid, kLossThreads, smem, s>>>(a, r, c, ct);
-      break;
+      return launch_pdl(k_loss<kKeys>, grid, dim3(kLossThreads), smem, s, a, r, c, ct);
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_loss_combine(const LossArgs &a, int splits, float *lse, double *bsum, uint32_t *done, float *loss,
                                 cudaStream_t s) {
   if (splits > 64) return cudaErrorInvalidValue;
-  k_loss_lse<<<(unsigned)loss_combine_blocks(a.B), kLseThreads, 0, s>>>(a, splits, lse, bsum, done, loss);
-  return cudaGetLastError();
+  return launch_pdl(k_loss_lse, dim3((unsigned)loss_combine_blocks(a.B)), dim3(kLseThreads), 0, s, a, splits, lse, bsum,
+                    done, loss);
 }
 
 int loss_combine_blocks(int B) { return (B + kLseQueries - 1) / kLseQueries; }
@@ -827,8 +826,8 @@ int loss_combine_blocks(int B) { return (B + kLseQueries - 1) / kLseQueries; }
 cudaError_t launch_loss_dq_reduce(const float *part, int splits, size_t split_stride, int B, int d, int dp, float *dQ,
                                   cudaStream_t s) {
   const int64_t n = (int64_t)B * ((d + 3) / 4);
-  k_loss_dq_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, splits, split_stride, B, d, dp, dQ);
-  return cudaGetLastError();
+  return launch_pdl(k_loss_dq_reduce, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, part, splits, split_stride, B,
+                    d, dp, dQ);
 }
 
 }  // namespace lr

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_topk(const int32_t *ids
                                                               const int32_t *counts, int G, int B, int k_in, int k,
                                                               int32_t *out_ids, float *out_scores,
                                                               int32_t *out_count) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int b = blockIdx.x;
   __shared__ int cnt[kMergeMaxG];
   __shared__ int total;
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_topk(const int32_t *ids
 cudaError_t launch_merge_topk(const int32_t *ids, const float *scores, const int32_t *counts, int G, int B, int k_in,
                               int k, int32_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  k_merge_topk<<<B, kMergeThreads, 0, s>>>(ids, scores, counts, G, B, k_in, k, out_ids, out_scores, out_count);
-  return cudaGetLastError();
+  return launch_pdl(k_merge_topk, dim3((unsigned)B), dim3(kMergeThreads), 0, s, ids, scores, counts, G, B, k_in, k,
+                    out_ids, out_scores, out_count);
 }
 
 namespace {
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_lane_merge(const int32_t *c_i
                                                               const int32_t *lane_of, const int32_t *k_of,
                                                               int32_t *run_ids, float *run_sc, int32_t *run_cnt,
                                                               int run_stride) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   extern __shared__ __align__(16) unsigned char lm_smem[];
   const int b = blockIdx.x;
   const int lane = lane_of[b];
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_lane_merge(const int32_t *c_i
 }
 
 __global__ void k_lane_reset(const int32_t *lanes, int n, int32_t *run_cnt) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) run_cnt[lanes[i]] = 0;
 }
@@ -150,6 +153,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_lane_gather(const int32_t *la
                                                                const float *run_sc, const int32_t *run_cnt,
                                                                int run_stride, int k_stride, int32_t *out_ids,
                                                                float *out_sc, int32_t *out_cnt) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int j = blockIdx.x;
   const int lane = lanes[j];
   const int c = min(run_cnt[lane], k_stride);
@@ -171,24 +175,21 @@ cudaError_t launch_lane_merge(const int32_t *c_ids, const float *c_sc, const int
     const cudaError_t e = allow_dynamic_smem((const void *)k_lane_merge, smem);
     if (e != cudaSuccess) return e;
   }
-  k_lane_merge<<<B, kMergeThreads, smem, s>>>(c_ids, c_sc, c_cnt, c_stride, lane_of, k_of, run_ids, run_sc, run_cnt,
-                                              run_stride);
-  return cudaGetLastError();
+  return launch_pdl(k_lane_merge, dim3((unsigned)B), dim3(kMergeThreads), smem, s, c_ids, c_sc, c_cnt, c_stride, lane_of,
+                    k_of, run_ids, run_sc, run_cnt, run_stride);
 }
 
 cudaError_t launch_lane_reset(const int32_t *lanes, int n, int32_t *run_cnt, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_lane_reset<<<(n + 255) / 256, 256, 0, s>>>(lanes, n, run_cnt);
-  return cudaGetLastError();
+  return launch_pdl(k_lane_reset, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, lanes, n, run_cnt);
 }
 
 cudaError_t launch_lane_gather(const int32_t *lanes, int n, const int32_t *run_ids, const float *run_sc,
                                const int32_t *run_cnt, int run_stride, int k_stride, int32_t *out_ids, float *out_sc,
                                int32_t *out_cnt, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_lane_gather<<<n, kMergeThreads, 0, s>>>(lanes, run_ids, run_sc, run_cnt, run_stride, k_stride, out_ids, out_sc,
-                                            out_cnt);
-  return cudaGetLastError();
+  return launch_pdl(k_lane_gather, dim3((unsigned)n), dim3(kMergeThreads), 0, s, lanes, run_ids, run_sc, run_cnt,
+                    run_stride, k_stride, out_ids, out_sc, out_cnt);
 }
 
 }  // namespace lr

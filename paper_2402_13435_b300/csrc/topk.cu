@@ -86,6 +86,7 @@ __device__ __forceinline__ int bucket_of(float s, float c, float scale, int G) {
 
 __global__ void __launch_bounds__(kTkThreads) k_topk_hist(const float *S, int64_t n, int64_t stride, float c,
                                                           float scale, int G, int k, TopkWs w) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   extern __shared__ uint32_t h[];
   __shared__ bool last;
   const int row = blockIdx.y, nb = 2 * G + 1, tid = threadIdx.x;
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(kTkThreads) k_topk_hist(const float *S, int64_
 __global__ void __launch_bounds__(kTkThreads) k_topk_gather(const float *S, int64_t n, int64_t stride, float c,
                                                             float scale, int G, int use_buckets, TopkWs w,
                                                             int32_t *thr_or_null) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int row = blockIdx.y, lane = threadIdx.x & 31;
   const int l = use_buckets ? w.thr[row] : 0;
   const float *r = S + (size_t)row * (size_t)stride;
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(kTkThreads) k_topk_gather(const float *S, int6
 
 // LR_TOPK_RADIX: no buckets; K and the row length for the selection.
 __global__ void k_topk_setup(int B, int k, int64_t n, TopkWs w) {
+  pdl_wait();  // launched by launch_pdl: the previous kernel's writes are visible from here on
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= B) return;
   w.thr[row] = 0;
@@ -253,15 +256,12 @@ extern "C" lr_status lr_topk(const float *scores, int32_t B, int64_t n, int64_t 
   const float scale = buckets ? 2.0f / (hi - lo) : 1.f;
   if (buckets) {
     const size_t smem = (size_t)(2 * G + 1) * sizeof(uint32_t);
-    k_topk_hist<<<grid, kTkThreads, smem, s>>>(scores, n, row_stride, c, scale, G, k, w);
-    TK_CK(cudaGetLastError());
+    TK_CK(launch_pdl(k_topk_hist, dim3(grid), dim3(kTkThreads), smem, s, scores, n, row_stride, c, scale, G, k, w));
   } else {
-    k_topk_setup<<<(B + 127) / 128, 128, 0, s>>>(B, k, n, w);
-    TK_CK(cudaGetLastError());
+    TK_CK(launch_pdl(k_topk_setup, dim3((unsigned)((B + 127) / 128)), dim3(128), 0, s, B, k, n, w));
   }
-  k_topk_gather<<<grid, kTkThreads, 0, s>>>(scores, n, row_stride, c, scale, G, buckets ? 1 : 0, w,
-                                            out_threshold_bucket);
-  TK_CK(cudaGetLastError());
+  TK_CK(launch_pdl(k_topk_gather, dim3(grid), dim3(kTkThreads), 0, s, scores, n, row_stride, c, scale, G,
+                   buckets ? 1 : 0, w, out_threshold_bucket));
   SelectArgs a{};
   a.mode = 1;
   a.buf = w.cand;
