@@ -249,7 +249,7 @@ class ClockSampler:
         window = "timed region"
         if len(got) < 3 and self.load_end is not None:
             got = [x for x in self.samples if self.window[0] <= x[3] <= self.load_end]
-            window = "timed region + the same workload's steps that follow it (latency and end-to-end steps)"
+            window = "timed region + the same workload's synchronised latency steps that follow it"
         if not got:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
                     "source": self.source, "errors": self.errors[:3]}
@@ -413,7 +413,8 @@ def run_reference(args):
 
 def run_e2e(lr, idx, wl, args, world):
     """The same metric end to end through lr_search with pinned host query and output buffers: every
-    step copies its queries and filters to the device and its rows back inside the timed region."""
+    step copies its queries and filters to the device and its rows back inside the timed region (the
+    copies ordered on the search stream, LR_SEARCH_ASYNC_HOST, one synchronisation at the end)."""
     import torch
     import torch.distributed as dist
 
@@ -423,15 +424,17 @@ def run_e2e(lr, idx, wl, args, world):
     h_ids = torch.empty((B, K), dtype=torch.int32).pin_memory()
     h_sc = torch.empty((B, K), dtype=torch.float32).pin_memory()
     h_cnt = torch.empty(B, dtype=torch.int32).pin_memory()
-    for i in range(args.warmup):
-        lr.lr_search(idx, hq[i % nb], wl["filters"][i % nb], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
+    for i in range(max(args.warmup, 10)):
+        lr.lr_search(idx, hq[i % nb], wl["filters"][i % nb], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt,
+                     host_sync=False)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    for i in range(args.steps):
+    for i in range(args.steps):  # stream-ordered copies into the page-locked outputs, one synchronisation
         j = i % nb
-        lr.lr_search(idx, hq[j], wl["filters"][j], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt)
+        lr.lr_search(idx, hq[j], wl["filters"][j], K, out_ids=h_ids, out_scores=h_sc, out_count=h_cnt,
+                     host_sync=False)
     torch.cuda.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0, world)
     f0 = wl["filters"][0]
@@ -509,8 +512,9 @@ def run_ours(args):
             torch.cuda.synchronize()
             lat.append(e0.elapsed_time(e1))
         clk.mark(h0, h1, time.perf_counter())
-        e2e = None if args.no_e2e else run_e2e(lr, idx, wl, args, world)
-        clk.mark(h0, h1, time.perf_counter())
+    # end to end after the clock sampler has stopped (its polling thread and
+    # nvidia-smi child compete with the host side of the search loop)
+    e2e = None if args.no_e2e else run_e2e(lr, idx, wl, args, world)
     step_ms = lat
     ms = ev0.elapsed_time(ev1)
     args.plan_used = probes[0].plan if probes[0].plan in ("gemv", "tc") else None

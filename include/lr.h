@@ -171,6 +171,9 @@ typedef struct lr_filters {
 } lr_filters;
 
 /* Search options; a zero-initialised struct (or NULL) means defaults. */
+/* lr_search_opts.flags */
+#define LR_SEARCH_ASYNC_HOST 1
+
 typedef struct lr_search_opts {
   int32_t plan;           /* lr_plan                                                  */
   int32_t sample_stride;  /* threshold sample: every n-th 256-row group (0 = auto,
@@ -186,7 +189,12 @@ typedef struct lr_search_opts {
                              level higher if that would exceed 2 * max_quant_k);
                              the result is the exact top K of the kept jobs.  F32
                              indexes only.                                        */
-  int32_t reserved;       /* 0                                                        */
+  int32_t flags;          /* 0, or LR_SEARCH_ASYNC_HOST: outputs in page-locked host
+                             memory (cudaHostAlloc / cudaHostRegister) are copied in
+                             stream order and the call does not synchronise
+                             `stream`; the caller synchronises it before reading them.
+                             Pageable host outputs and host statistics arrays still
+                             make the call synchronise.                            */
   int64_t row_begin;      /* search only job rows [row_begin, row_end) (both 0: every */
   int64_t row_end;        /* row); row_begin a multiple of 256, row_end a multiple of
                              256 or n; ids stay the index's row ids (+ id_base).  The

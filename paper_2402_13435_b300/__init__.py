@@ -25,6 +25,7 @@ LR_F32, LR_BF16, LR_FP8_E4M3 = 0, 1, 2
 _DTYPE = {"f32": LR_F32, "bf16": LR_BF16, "fp8": LR_FP8_E4M3}
 LR_DOT, LR_COSINE = 0, 1
 LR_PLAN_AUTO, LR_PLAN_GEMV, LR_PLAN_TC, LR_PLAN_TBR = 0, 1, 2, 3
+LR_SEARCH_ASYNC_HOST = 1  # lr_search_opts.flags
 _METRIC = {"dot": LR_DOT, "cosine": LR_COSINE}
 _PLAN = {"auto": LR_PLAN_AUTO, "gemv": LR_PLAN_GEMV, "tc": LR_PLAN_TC, "tbr": LR_PLAN_TBR}
 
@@ -57,7 +58,7 @@ class lr_filters(ctypes.Structure):
 
 class lr_search_opts(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_int32), ("sample_stride", ctypes.c_int32), ("cand_cap", ctypes.c_int32),
-                ("force_exact_fallback", ctypes.c_int32), ("quant_mult", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("force_exact_fallback", ctypes.c_int32), ("quant_mult", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64)]
 
 
@@ -263,7 +264,8 @@ class Probe:
 
 def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out_count=None, plan: str = "auto",
               sample_stride: int = 0, cand_cap: int = 0, force_exact_fallback: bool = False, quant_mult: int = 0,
-              stats: bool = False, probe: Optional[Probe] = None, stream=None, row_range=None):
+              stats: bool = False, probe: Optional[Probe] = None, stream=None, row_range=None,
+              host_sync: bool = True):
     """Filtered top-K for the query batch ``q`` [B][dim] FP32 (torch tensor or numpy array, host or device).
 
     ``k`` is an int or a per-query sequence.  Outputs default to new device tensors on q's device
@@ -271,6 +273,8 @@ def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out
     count [B] int32) and, with ``stats=True``, a dict of per-query statistics.  ``probe`` collects
     launch counts and scan-phase CUDA events without a synchronisation.  ``row_range`` = (begin, end)
     restricts the search to job rows [begin, end) (begin a multiple of 256, end a multiple of 256 or n).
+    ``host_sync=False`` (LR_SEARCH_ASYNC_HOST): outputs in page-locked host memory are copied in stream
+    order and the call returns without synchronising; synchronise the stream before reading them.
     """
     import torch
 
@@ -297,7 +301,8 @@ def lr_search(index: Index, q, filters, k, *, out_ids=None, out_scores=None, out
             out_count = torch.empty(B, dtype=torch.int32, device=q.device)
     opts = lr_search_opts(plan=_PLAN[plan], sample_stride=int(sample_stride), cand_cap=int(cand_cap),
                           force_exact_fallback=int(bool(force_exact_fallback)), quant_mult=int(quant_mult),
-                          row_begin=int(row_range[0]) if row_range else 0, row_end=int(row_range[1]) if row_range else 0)
+                          row_begin=int(row_range[0]) if row_range else 0, row_end=int(row_range[1]) if row_range else 0,
+                          flags=0 if host_sync else LR_SEARCH_ASYNC_HOST)
     st = None
     st_arrays = None
     if stats:

@@ -64,6 +64,24 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory: a device-to-host copy into it is ordered on the
+// stream and needs no synchronisation before the call returns.
+bool is_pinned_host(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+// Host outputs need a synchronisation unless the caller asked for stream-ordered
+// copies (LR_SEARCH_ASYNC_HOST) and every output is page-locked.
+bool host_out_sync(bool async_host, const void *ids, const void *scores, const void *count) {
+  return !(async_host && is_pinned_host(ids) && is_pinned_host(scores) && (count == nullptr || is_pinned_host(count)));
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int64_t pow2_ceil(int64_t v) {
@@ -1353,7 +1371,7 @@ lr_status run_sign_search(lr_index *ix, const float *q, int B, const lr_filters 
     LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
     LR_CK(cudaMemcpyAsync(out_scores, ix->o_sc, sizeof(float) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
     if (out_count) LR_CK(cudaMemcpyAsync(out_count, ix->o_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
-    need_sync = true;
+    need_sync = host_out_sync((o.flags & LR_SEARCH_ASYNC_HOST) != 0, out_ids, out_scores, out_count);
   }
   if (stats) {
     if (stats->n_launches) *stats->n_launches = n_launch;
@@ -1378,7 +1396,7 @@ lr_status run_sign_search(lr_index *ix, const float *q, int B, const lr_filters 
 // query's messenger list; only those rows are scored (FP32) and selected.
 lr_status run_tbr_search(lr_index *ix, const float *q, int B, const lr_filters *f, const int32_t *k, int k_all,
                          int32_t *out_ids, float *out_scores, int32_t *out_count, const lr_search_stats *stats,
-                         cudaStream_t s, const TbrPlan &T, int64_t cap) {
+                         cudaStream_t s, const TbrPlan &T, int64_t cap, bool async_host) {
   const int turn = ix->filt_turn;
   ix->filt_turn ^= 1;
   if (ix->filt_ev_live[turn]) LR_CK(cudaEventSynchronize(ix->filt_ev[turn]));
@@ -1490,7 +1508,7 @@ lr_status run_tbr_search(lr_index *ix, const float *q, int B, const lr_filters *
     LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
     LR_CK(cudaMemcpyAsync(out_scores, ix->o_sc, sizeof(float) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
     if (out_count) LR_CK(cudaMemcpyAsync(out_count, ix->o_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
-    need_sync = true;
+    need_sync = host_out_sync(async_host, out_ids, out_scores, out_count);
   }
   if (stats) {
     if (stats->n_launches) *stats->n_launches = n_launch;
@@ -1572,7 +1590,8 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
                                       "with at most the candidate capacity of postings and 16 distinct terms");
     if (plan == LR_PLAN_TBR || (T.ok && tbr_cheaper(ix, B, T, est, tc_ok))) {
       tm.mark("tbr");
-      return run_tbr_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, stats, s, T, tcap);
+      return run_tbr_search(ix, q, B, f, k, k_all, out_ids, out_scores, out_count, stats, s, T, tcap,
+                            (o.flags & LR_SEARCH_ASYNC_HOST) != 0);
     }
   }
   if (plan == LR_PLAN_AUTO) plan = choose_plan(ix, B, tc_ok, have_est, est);
@@ -1889,7 +1908,7 @@ lr_status run_search(lr_index *ix, const float *q, int B, const lr_filters *f, c
     LR_CK(cudaMemcpyAsync(out_ids, ix->o_ids, sizeof(int32_t) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
     LR_CK(cudaMemcpyAsync(out_scores, ix->o_sc, sizeof(float) * (size_t)B * k_all, cudaMemcpyDeviceToHost, s));
     if (out_count) LR_CK(cudaMemcpyAsync(out_count, ix->o_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
-    need_sync = true;
+    need_sync = host_out_sync((o.flags & LR_SEARCH_ASYNC_HOST) != 0, out_ids, out_scores, out_count);
   }
   if (stats) {
     if (stats->n_launches) *stats->n_launches = n_launch;

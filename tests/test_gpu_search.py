@@ -356,3 +356,37 @@ def test_filter_count_host_bitmap_matches_device_bitmap(lr, small):
     bits = ((host_bm[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(B, -1)[:, :c.n].astype(bool)
     assert np.array_equal(bits, ref_mat) and np.array_equal(host_cnt, ref_cnt)
     lr.lr_index_destroy(idx)
+
+
+def test_async_host_outputs(lr, small):
+    """LR_SEARCH_ASYNC_HOST: page-locked host outputs of several calls in a row, read after one
+    synchronisation, equal the device-output rows; pageable outputs still come back synchronously."""
+    c = small
+    B, K = 6, 30
+    po, pid = c.postings()
+    idx = lr.lr_index_create(torch.from_numpy(c.X).cuda(), c.V, post_off=po, post_ids=pid, n_dense_terms=48,
+                             metric="cosine", max_batch=32, max_k=128)
+    try:
+        runs = []
+        for r in range(3):
+            f = _mixed_filters(500 + r, B, c.V, c.df, c.n)
+            Q = datagen.query_embeddings(500 + r, B, c.d)
+            ids_d, sc_d, cnt_d = _run(lr, idx, Q, f, K)
+            runs.append((f, Q, ids_d, sc_d, cnt_d))
+        outs = []
+        for f, Q, *_ in runs:  # three calls back to back, no synchronisation in between
+            # the page-locked query and outputs stay referenced until the synchronisation: the copies
+            # read and write them in stream order after the call has returned
+            h = (torch.empty((B, K), dtype=torch.int32).pin_memory(), torch.empty((B, K), dtype=torch.float32).pin_memory(),
+                 torch.empty(B, dtype=torch.int32).pin_memory(), torch.from_numpy(Q).pin_memory())
+            lr.lr_search(idx, h[3], f, K, out_ids=h[0], out_scores=h[1], out_count=h[2], host_sync=False)
+            outs.append(h)
+        torch.cuda.synchronize()
+        for (f, Q, ids_d, sc_d, cnt_d), h in zip(runs, outs):
+            assert np.array_equal(h[0].numpy(), ids_d) and np.array_equal(h[1].numpy(), sc_d)
+            assert np.array_equal(h[2].numpy(), cnt_d)
+        f, Q, ids_d, sc_d, cnt_d = runs[0]
+        ids, sc, cnt = lr.lr_search(idx, Q, f, K, host_sync=False)  # numpy (pageable) outputs
+        assert np.array_equal(ids, ids_d) and np.array_equal(sc, sc_d) and np.array_equal(cnt, cnt_d)
+    finally:
+        lr.lr_index_destroy(idx)
