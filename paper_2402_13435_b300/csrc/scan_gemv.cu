@@ -162,6 +162,42 @@ __device__ __forceinline__ float lane_sum(float (&v)[P], int lane) {
   return v[0];
 }
 
+// A packed CNF (scan_common.cuh) over one group's words, four terms per step:
+// the step's slot ids come from one register and its loads are independent,
+// while the loop itself stays rolled (fewer registers than eval_packed).
+__device__ __forceinline__ void eval_packed_steps(const PackedCnf &p, const uint32_t *sw, uint32_t (&pw)[8]) {
+  uint32_t cw[8];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    pw[w] = 0xFFFFFFFFu;
+    cw[w] = 0u;
+  }
+#pragma unroll 1
+  for (int t0 = 0; t0 < p.nt; t0 += 4) {
+    const uint32_t ids = t0 < 4 ? p.slot[0] : t0 < 8 ? p.slot[1] : t0 < 12 ? p.slot[2] : p.slot[3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + j;
+      if (t < p.nt) {
+        if (t > 0 && ((p.start >> t) & 1u)) {  // term t opens the next clause
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            pw[w] &= cw[w];
+            cw[w] = 0u;
+          }
+        }
+        const uint4 *src = reinterpret_cast<const uint4 *>(sw + ((ids >> (8 * j)) & 0xFFu) * 8);
+        const uint4 lo = src[0], hi = src[1];
+        cw[0] |= lo.x; cw[1] |= lo.y; cw[2] |= lo.z; cw[3] |= lo.w;
+        cw[4] |= hi.x; cw[5] |= hi.y; cw[6] |= hi.z; cw[7] |= hi.w;
+      }
+    }
+  }
+  if (p.nt > 0)
+#pragma unroll
+    for (int w = 0; w < 8; ++w) pw[w] &= cw[w];
+}
+
 template <int P>
 __host__ __device__ constexpr int log2_of() {
   return P >= 32 ? 5 : P >= 16 ? 4 : P >= 8 ? 3 : P >= 4 ? 2 : P >= 2 ? 1 : 0;
@@ -203,6 +239,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_scan_gemv(const ScanArgs a) {
   // predicate layout: lane q evaluates query q
   const int gq = a.q_base + lane;
   const bool qlive = lane < a.nq && (a.active == nullptr || a.active[gq] != 0u);
+  // One- and two-query launches (latency-bound: few rows, the per-group chain
+  // sets the pace) pack the lane's CNF in registers once (up to 16 terms), so
+  // each group's evaluation issues only independent shared-memory loads
+  // instead of walking the clause lists in global memory, and keep the pass
+  // words in registers; wider launches, bound by instruction issue, keep the
+  // lists (measured: the packed form cost 8-query launches 1-7 %)
+  constexpr bool kPackedEval = NQ <= 2;
+  PackedCnf pcnf{};
+  bool packed = false;
+  if (kPackedEval && qlive) {
+    pcnf = pack_cnf(a, lane);
+    packed = pcnf.ok;
+  }
   // scoring layout: after the butterfly this lane holds pair pidx = (row my_r
   // of the round, query my_q); of the 32 / kP lanes holding it the first reports it
   const int pidx = lane >> (5 - kLg);
@@ -312,7 +361,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_scan_gemv(const ScanArgs a) {
     __syncwarp();
     uint32_t pw[8];
     if (qlive) {
-      eval_cnf(a, lane, slot_tab + (size_t)t * a.n_slots * 8, pw);
+      if (kPackedEval && packed)
+        eval_packed_steps(pcnf, slot_tab + (size_t)t * a.n_slots * 8, pw);
+      else
+        eval_cnf(a, lane, slot_tab + (size_t)t * a.n_slots * 8, pw);
     } else {
 #pragma unroll
       for (int w = 0; w < 8; ++w) pw[w] = 0u;
@@ -325,7 +377,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_scan_gemv(const ScanArgs a) {
 #pragma unroll 1
     for (int w = 0; w < 8; ++w) {
       const int64_t left = a.n - (r0 + w * 32);
-      const uint32_t p = pw[w] & (left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u));
+      // packed form: word w is pw[0], the words shifting down one place per
+      // iteration, so the array stays in registers (no indexing by the rolled
+      // loop's counter)
+      const uint32_t pw_w = kPackedEval ? pw[0] : pw[w];
+      const uint32_t p = pw_w & (left >= 32 ? 0xFFFFFFFFu : (left > 0 ? ((1u << left) - 1u) : 0u));
+      if constexpr (kPackedEval) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) pw[i] = pw[i + 1];
+      }
       my_pass += (unsigned long long)__popc(p);
       const uint32_t U = __reduce_or_sync(0xFFFFFFFFu, p);
       if (U == 0u) continue;
