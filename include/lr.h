@@ -194,7 +194,9 @@ typedef struct lr_search_opts {
                              stream order and the call does not synchronise
                              `stream`; the caller synchronises it before reading them.
                              Pageable host outputs and host statistics arrays still
-                             make the call synchronise.                            */
+                             make the call synchronise.  A page-locked host query
+                             array is then read in stream order too: keep it
+                             unchanged until `stream` has been synchronised.      */
   int64_t row_begin;      /* search only job rows [row_begin, row_end) (both 0: every */
   int64_t row_end;        /* row); row_begin a multiple of 256, row_end a multiple of
                              256 or n; ids stay the index's row ids (+ id_base).  The
